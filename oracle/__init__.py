@@ -1,0 +1,253 @@
+"""FP64 CPU oracle for one GRMHD Runge-Kutta stage (arXiv:2311.04989, Sec. 2-3).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and
+reference legs of ``bench.py`` may import this package.  The product path (the CUDA library and its
+binding) never does, and it shares no code with it.
+
+The numerical work lives in ``grmhd_oracle.cpp`` (plain C++ restating the paper's equations); this
+module compiles it with ``g++`` into ``oracle/_lib/liboracle.so`` and marshals numpy arrays to it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "grmhd_oracle.cpp")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (FP64, no FMA contraction) if the source is newer than the library."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OGeom(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("ng", C.c_int32), ("dx", C.c_double * 3)]
+
+
+class OParams(C.Structure):
+    _fields_ = [("gamma_ad", C.c_double), ("rho_atm", C.c_double), ("p_atm", C.c_double),
+                ("f_thr", C.c_double), ("W_max", C.c_double), ("M_max", C.c_double),
+                ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
+                ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("max_iter", C.c_int32),
+                ("recon", C.c_int32), ("emf", C.c_int32), ("ceiling", C.c_int32),
+                ("interp_order", C.c_int32), ("pad_", C.c_int32)]
+
+
+@dataclass
+class Params:
+    """Physical and numerical parameters of the stage (names follow the paper)."""
+    gamma_ad: float = 2.0
+    rho_atm: float = 1e-13          # f_atm * rho_max   (Sec. 3.6)
+    p_atm: float | None = None      # p(rho_atm); None -> K rho_atm^Gamma
+    K_poly: float = 100.0           # polytropic K used for p_atm (Sec. 2.3)
+    f_thr: float = 1.0              # Sec. 3.6
+    W_max: float = float(np.sqrt(1.0 + 20.0 ** 2))   # u~ <= 20 (Sec. 3.6)
+    M_max: float = 1e4              # B^2/D ceiling (App. A; value is a reading)
+    tol: float = 1e-10              # bracketing tolerance (Sec. 3.6)
+    weno_eps: float = 1e-40
+    rk_g0: float = 0.0
+    rk_g1: float = 1.0
+    rk_beta: float = 1.0
+    max_iter: int = 100
+    recon: int = 1                  # 0 PLM, 1 WENOZ
+    emf: int = 0                    # 0 upwinded corner average, 1 plain mean
+    ceiling: int = 0                # 0 clamp W, 1 atmosphere
+    interp_order: int = 2
+
+    def c(self) -> OParams:
+        p_atm = self.p_atm if self.p_atm is not None else self.K_poly * self.rho_atm ** self.gamma_ad
+        return OParams(self.gamma_ad, self.rho_atm, p_atm, self.f_thr, self.W_max, self.M_max,
+                       self.tol, self.weno_eps, self.rk_g0, self.rk_g1, self.rk_beta,
+                       self.max_iter, self.recon, self.emf, self.ceiling, self.interp_order, 0)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        dp = C.POINTER(C.c_double)
+        u8 = C.POINTER(C.c_uint8)
+        i32 = C.POINTER(C.c_int32)
+        pp = C.POINTER(OParams)
+        L.oracle_prim2con.argtypes = [C.c_int, dp, dp, dp, pp, dp]
+        L.oracle_con2prim.argtypes = [C.c_int, dp, dp, dp, pp, dp, u8, i32]
+        L.oracle_flux_points.argtypes = [C.c_int, C.c_int, dp, dp, dp, pp, dp, dp, dp]
+        L.oracle_face_flux.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, pp, dp]
+        L.oracle_sources.argtypes = [C.c_int, dp, dp, dp, dp, pp, dp]
+        L.oracle_recon1d.argtypes = [C.c_int, C.c_int, dp, C.c_double, dp, dp]
+        ip = C.POINTER(C.c_int32)
+        L.oracle_interp_cells.argtypes = [C.POINTER(OGeom), dp, C.c_int, ip, ip, dp, dp]
+        L.oracle_interp_faces.argtypes = [C.POINTER(OGeom), dp, C.c_int, C.c_int, ip, ip, dp]
+        L.oracle_stage_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                         C.c_double, pp, dp, dp, dp, dp, dp, u8, i32]
+        L.oracle_stage_block.restype = C.c_int
+        L.oracle_divb_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _d(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------------------------
+# pointwise entries
+# ---------------------------------------------------------------------------------------------
+def prim2con(metric, prims, Bdens, P: Params):
+    """Eq. consB_def at points.  metric (n,16), prims (n,5), Bdens (n,3) -> q (n,5)."""
+    metric, prims, Bdens = _f64(metric), _f64(prims), _f64(Bdens)
+    n = prims.shape[0]
+    q = np.zeros((n, 5))
+    cp = P.c()
+    lib().oracle_prim2con(n, _d(metric), _d(prims), _d(Bdens), C.byref(cp), _d(q))
+    return q
+
+
+def con2prim(metric, q, Bdens, P: Params):
+    """Con2prim at points.  Returns (prims (n,5), q_out (n,5), status (n,), iterations (n,))."""
+    metric, Bdens = _f64(metric), _f64(Bdens)
+    q = _f64(q).copy()
+    n = q.shape[0]
+    w = np.zeros((n, 5))
+    st = np.zeros(n, np.uint8)
+    it = np.zeros(n, np.int32)
+    cp = P.c()
+    lib().oracle_con2prim(n, _d(metric), _d(q), _d(Bdens), C.byref(cp), _d(w),
+                          st.ctypes.data_as(C.POINTER(C.c_uint8)),
+                          it.ctypes.data_as(C.POINTER(C.c_int32)))
+    return w, q, st, it
+
+
+def flux_points(d, metric, prims, Bdens, P: Params):
+    """Physical U (n,7), F^d (n,7) and (lam-, lam+) (n,2) of Eq. fluxB_def at points."""
+    metric, prims, Bdens = _f64(metric), _f64(prims), _f64(Bdens)
+    n = prims.shape[0]
+    U = np.zeros((n, 7)); F = np.zeros((n, 7)); lam = np.zeros((n, 2))
+    cp = P.c()
+    lib().oracle_flux_points(n, d, _d(metric), _d(prims), _d(Bdens), C.byref(cp), _d(U), _d(F), _d(lam))
+    return U, F, lam
+
+
+def face_flux(d, metric, wL, BL, wR, BR, P: Params):
+    """HLLE flux (n,7) at faces from left/right states."""
+    metric, wL, BL, wR, BR = map(_f64, (metric, wL, BL, wR, BR))
+    n = wL.shape[0]
+    F = np.zeros((n, 7))
+    cp = P.c()
+    lib().oracle_face_flux(n, d, _d(metric), _d(wL), _d(BL), _d(wR), _d(BR), C.byref(cp), _d(F))
+    return F
+
+
+def sources(metric, dmetric, prims, Bdens, P: Params):
+    """Eq. hydsrc_def at points.  dmetric (n,3,16)."""
+    metric, dmetric, prims, Bdens = map(_f64, (metric, dmetric, prims, Bdens))
+    n = prims.shape[0]
+    s = np.zeros((n, 5))
+    cp = P.c()
+    lib().oracle_sources(n, _d(metric), _d(dmetric), _d(prims), _d(Bdens), C.byref(cp), _d(s))
+    return s
+
+
+def recon1d(method, w, eps=1e-40):
+    """Face states L[f], R[f] between cells f-1 and f, for f in [3, n-3]."""
+    w = _f64(w)
+    n = w.shape[0]
+    L = np.full(n, np.nan); R = np.full(n, np.nan)
+    lib().oracle_recon1d(method, n, _d(w), eps, _d(L), _d(R))
+    return L, R
+
+
+# ---------------------------------------------------------------------------------------------
+# block entries
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class Block:
+    """One ghost-padded MeshBlock in the oracle's layout (see grmhd_oracle.cpp header)."""
+    n: tuple
+    ng: int
+    dx: tuple
+    metric: np.ndarray          # (16, Nz+1, Ny+1, Nx+1)
+    W: np.ndarray               # (5, Nz, Ny, Nx)
+    B: list = field(default_factory=list)   # [Bx (Nz,Ny,Nx+1), By (Nz,Ny+1,Nx), Bz (Nz+1,Ny,Nx)]
+
+    def geom(self) -> OGeom:
+        return OGeom((C.c_int32 * 3)(*self.n), self.ng, (C.c_double * 3)(*self.dx))
+
+
+def _rng3(lo, hi):
+    lo = (lo,) * 3 if np.isscalar(lo) else tuple(lo)
+    hi = (hi,) * 3 if np.isscalar(hi) else tuple(hi)
+    return (C.c_int32 * 3)(*lo), (C.c_int32 * 3)(*hi), int(np.prod(np.subtract(hi, lo)))
+
+
+def interp_cells(blk: Block, order, lo, hi):
+    """Metric values (m,16) and derivatives (m,3,16) at cell centres with index in [lo, hi)
+    per direction (scalars or 3-tuples), x fastest."""
+    g = blk.geom()
+    clo, chi, m = _rng3(lo, hi)
+    val = np.zeros((m, 16)); dval = np.zeros((m, 3, 16))
+    lib().oracle_interp_cells(C.byref(g), _d(_f64(blk.metric)), order, clo, chi, _d(val), _d(dval))
+    return val, dval
+
+
+def interp_faces(blk: Block, order, d, lo, hi):
+    g = blk.geom()
+    clo, chi, m = _rng3(lo, hi)
+    val = np.zeros((m, 16))
+    lib().oracle_interp_faces(C.byref(g), _d(_f64(blk.metric)), order, d, clo, chi, _d(val))
+    return val
+
+
+def stage_block(blk: Block, U, U0, B0, dt, P: Params, return_iters=False):
+    """One RK stage on one block.  Returns (U', [B'x,B'y,B'z], W', status[, iters]).
+
+    Outputs keep the input's ghost-padded shape; ghost entries of U', B', W' are copies of the
+    inputs (U, B, W) and status is 0 there."""
+    g = blk.geom()
+    metric = _f64(blk.metric)
+    W = _f64(blk.W)
+    B = [_f64(b) for b in blk.B]
+    U = _f64(U); U0 = _f64(U0); B0 = [_f64(b) for b in B0]
+    Uo = U.copy(); Wo = W.copy(); Bo = [b.copy() for b in B]
+    st = np.zeros(W.shape[1:], np.uint8)
+    it = np.zeros(W.shape[1:], np.int32)
+    cp = P.c()
+    r = lib().oracle_stage_block(C.byref(g), _d(metric), _d(W), _d(B[0]), _d(B[1]), _d(B[2]),
+                                 _d(U), _d(U0), _d(B0[0]), _d(B0[1]), _d(B0[2]), float(dt),
+                                 C.byref(cp), _d(Uo), _d(Bo[0]), _d(Bo[1]), _d(Bo[2]), _d(Wo),
+                                 st.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                 it.ctypes.data_as(C.POINTER(C.c_int32)))
+    if r != 0:
+        raise ValueError("oracle_stage_block: ghost width too small for the stencil")
+    if return_iters:
+        return Uo, Bo, Wo, st, it
+    return Uo, Bo, Wo, st
+
+
+def divb(blk_n, ng, dx, B):
+    g = OGeom((C.c_int32 * 3)(*blk_n), ng, (C.c_double * 3)(*dx))
+    B = [_f64(b) for b in B]
+    out = np.zeros((blk_n[2] + 2 * ng, blk_n[1] + 2 * ng, blk_n[0] + 2 * ng))
+    lib().oracle_divb_block(C.byref(g), _d(B[0]), _d(B[1]), _d(B[2]), _d(out))
+    return out

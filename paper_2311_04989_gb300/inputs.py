@@ -1,0 +1,363 @@
+"""Seeded synthetic inputs for the GRMHD stage (numpy only).
+
+This module is shared by the tests, the CPU oracle's callers and ``bench.py``.  It holds none of the
+stage's arithmetic: it draws smooth random fields, solves the TOV equations for star initial data,
+and forms the face field as the discrete curl of an edge vector potential so that it is
+divergence-free by construction (the initial-data recipe of Sec. 4.4, Eq. Apotential).
+
+Array layout of one MeshBlock with ``n`` interior cells per direction and ``g`` ghosts
+(``N = n + 2g``, x fastest):
+
+* vertex metric ``(16, Nz+1, Ny+1, Nx+1)``: alpha, beta^i, gamma_{xx,xy,xz,yy,yz,zz}, K_ij
+* primitives ``(5, Nz, Ny, Nx)``: rho, u~^x, u~^y, u~^z, p
+* faces: ``Bx (Nz, Ny, Nx+1)``, ``By (Nz, Ny+1, Nx)``, ``Bz (Nz+1, Ny, Nx)`` (densitised B^i)
+
+Cell index ``i`` in ``[-g, n+g-1]`` has centre ``x0 + (i + 1/2) dx``; vertex and face index ``i`` in
+``[-g, n+g]`` sit at ``x0 + i dx``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2311_04989
+
+
+@dataclass
+class BlockInput:
+    n: tuple            # interior cells (nx, ny, nz)
+    ng: int
+    x0: tuple           # coordinate of vertex index 0
+    dx: tuple
+    metric: np.ndarray  # (16, Nz+1, Ny+1, Nx+1)
+    W: np.ndarray       # (5, Nz, Ny, Nx)
+    B: list = field(default_factory=list)   # [Bx, By, Bz]
+
+    @property
+    def N(self):
+        return tuple(v + 2 * self.ng for v in self.n)
+
+
+# ---------------------------------------------------------------------------------------------
+# coordinates
+# ---------------------------------------------------------------------------------------------
+def _axis(n, g, x0, dx, stagger):
+    """1D coordinates: stagger=0 -> cell centres, 1 -> vertices/faces."""
+    if stagger:
+        return x0 + np.arange(-g, n + g + 1) * dx
+    return x0 + (np.arange(-g, n + g) + 0.5) * dx
+
+
+def grid(n, g, x0, dx, stag=(0, 0, 0)):
+    """Meshgrid (Z, Y, X) arrays of the requested staggering, shaped (z, y, x)."""
+    ax = [_axis(n[d], g, x0[d], dx[d], stag[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return X, Y, Z
+
+
+# ---------------------------------------------------------------------------------------------
+# smooth random fields
+# ---------------------------------------------------------------------------------------------
+class SmoothField:
+    """Sum of a few random Fourier modes on a box of size L, scaled to lie within [-1, 1]."""
+
+    def __init__(self, rng: np.random.Generator, L: float, nmodes: int = 8, kmax: int = 3):
+        self.k = rng.integers(-kmax, kmax + 1, size=(nmodes, 3)).astype(float) * (2 * np.pi / L)
+        self.k[np.all(self.k == 0, axis=1)] = 2 * np.pi / L
+        self.ph = rng.uniform(0, 2 * np.pi, nmodes)
+        self.a = rng.uniform(0.5, 1.0, nmodes)
+        self.a /= self.a.sum()
+
+    def __call__(self, X, Y, Z):
+        out = np.zeros_like(X)
+        for k, ph, a in zip(self.k, self.ph, self.a):
+            out += a * np.sin(k[0] * X + k[1] * Y + k[2] * Z + ph)
+        return out
+
+
+def metric_flat(n, g):
+    m = np.zeros((16,) + tuple(v + 2 * g + 1 for v in n[::-1]))
+    m[0] = 1.0
+    m[4] = m[7] = m[9] = 1.0
+    return m
+
+
+def metric_perturbed(n, g, x0, dx, rng, amp=1e-2, L=1.0, with_K=False):
+    """Flat metric plus smooth perturbations |delta g| <= amp of alpha, beta^i and gamma_ij."""
+    X, Y, Z = grid(n, g, x0, dx, (1, 1, 1))
+    m = metric_flat(n, g)
+    for c in range(10):
+        m[c] = m[c] + amp * SmoothField(rng, L)(X, Y, Z)
+    if with_K:
+        for c in range(10, 16):
+            m[c] = amp * SmoothField(rng, L)(X, Y, Z)
+    return m
+
+
+def curl_B(n, g, x0, dx, A):
+    """Face field B = curl A (discrete) from an edge vector potential.
+
+    ``A(comp, X, Y, Z)`` returns A_comp; A_x lives on x-edges (cell centre in x, vertices in y,z),
+    and cyclically.  The discrete divergence of the result vanishes to round-off."""
+    Nx, Ny, Nz = (v + 2 * g for v in n)
+    # edge arrays over the whole padded range
+    Xe, Ye, Ze = grid(n, g, x0, dx, (0, 1, 1)); Ax = A(0, Xe, Ye, Ze)   # (Nz+1, Ny+1, Nx)
+    Xe, Ye, Ze = grid(n, g, x0, dx, (1, 0, 1)); Ay = A(1, Xe, Ye, Ze)   # (Nz+1, Ny, Nx+1)
+    Xe, Ye, Ze = grid(n, g, x0, dx, (1, 1, 0)); Az = A(2, Xe, Ye, Ze)   # (Nz, Ny+1, Nx+1)
+    Bx = (Az[:, 1:, :] - Az[:, :-1, :]) / dx[1] - (Ay[1:, :, :] - Ay[:-1, :, :]) / dx[2]
+    By = (Ax[1:, :, :] - Ax[:-1, :, :]) / dx[2] - (Az[:, :, 1:] - Az[:, :, :-1]) / dx[0]
+    Bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / dx[0] - (Ax[:, 1:, :] - Ax[:, :-1, :]) / dx[1]
+    assert Bx.shape == (Nz, Ny, Nx + 1) and By.shape == (Nz, Ny + 1, Nx) and Bz.shape == (Nz + 1, Ny, Nx)
+    return [np.ascontiguousarray(Bx), np.ascontiguousarray(By), np.ascontiguousarray(Bz)]
+
+
+def random_block(n=(16, 16, 16), g=3, x0=(0.0, 0.0, 0.0), dx=None, seed=0, L=1.0,
+                 rho_range=(1e-10, 1e-3), u_max=0.5, theta_range=(1e-3, 1e-1),
+                 sigma_range=(1e-3, 10.0), metric_amp=1e-2, with_K=False, flat=False,
+                 fields=None):
+    """Smooth random block.  ``fields`` (a dict of SmoothField) lets several blocks sample the
+    same global functions, so neighbouring blocks agree in their overlap."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    if dx is None:
+        dx = tuple(L / v for v in n)
+    if fields is None:
+        fields = make_fields(rng, L)
+    X, Y, Z = grid(n, g, x0, dx)
+    lr = np.log(rho_range)
+    rho = np.exp(lr[0] + (lr[1] - lr[0]) * 0.5 * (1 + fields["rho"](X, Y, Z)))
+    lt = np.log(theta_range)
+    theta = np.exp(lt[0] + (lt[1] - lt[0]) * 0.5 * (1 + fields["theta"](X, Y, Z)))
+    p = rho * theta
+    W = np.zeros((5,) + X.shape)
+    W[0] = rho
+    for c in range(3):
+        W[1 + c] = u_max * fields[f"u{c}"](X, Y, Z) / np.sqrt(3.0)
+    W[4] = p
+    # field: A_i = sqrt(sigma p) a_i(x) / k, so that |B|^2 ~ sigma p in order of magnitude
+    ls = np.log(sigma_range)
+    kk = 2 * np.pi / L
+
+    def A(comp, Xe, Ye, Ze):
+        rr = np.exp(lr[0] + (lr[1] - lr[0]) * 0.5 * (1 + fields["rho"](Xe, Ye, Ze)))
+        tt = np.exp(lt[0] + (lt[1] - lt[0]) * 0.5 * (1 + fields["theta"](Xe, Ye, Ze)))
+        ss = np.exp(ls[0] + (ls[1] - ls[0]) * 0.5 * (1 + fields["sigma"](Xe, Ye, Ze)))
+        return np.sqrt(ss * rr * tt) * fields[f"a{comp}"](Xe, Ye, Ze) / kk
+
+    B = curl_B(n, g, x0, dx, A)
+    if flat:
+        metric = metric_flat(n, g)
+    else:
+        metric = metric_perturbed(n, g, x0, dx, np.random.default_rng(SEED_BASE + seed + 7919),
+                                  amp=metric_amp, L=L, with_K=with_K)
+        if fields.get("metric") is not None:
+            Xv, Yv, Zv = grid(n, g, x0, dx, (1, 1, 1))
+            metric = metric_flat(n, g)
+            for c in range(16 if with_K else 10):
+                base = 0.0 if c >= 10 else metric[c]
+                metric[c] = base + metric_amp * fields["metric"][c](Xv, Yv, Zv)
+    return BlockInput(tuple(n), g, tuple(x0), tuple(dx), metric, np.ascontiguousarray(W), B)
+
+
+def make_fields(rng, L, shared_metric=False):
+    f = {k: SmoothField(rng, L) for k in ("rho", "theta", "sigma", "u0", "u1", "u2", "a0", "a1", "a2")}
+    f["metric"] = [SmoothField(rng, L) for _ in range(16)] if shared_metric else None
+    return f
+
+
+def uniform_block(n=(8, 8, 8), g=3, dx=(0.1, 0.1, 0.1), rho=1.0, u=(0.1, -0.2, 0.05), p=0.5,
+                  B=(0.3, -0.2, 0.4), metric=None):
+    """A uniform state; ``metric`` is an optional 16-vector of constant metric values."""
+    N = tuple(v + 2 * g for v in n)
+    W = np.zeros((5, N[2], N[1], N[0]))
+    W[0] = rho
+    for c in range(3):
+        W[1 + c] = u[c]
+    W[4] = p
+    m = metric_flat(n, g)
+    if metric is not None:
+        for c in range(16):
+            m[c] = metric[c]
+    Bx = np.full((N[2], N[1], N[0] + 1), B[0])
+    By = np.full((N[2], N[1] + 1, N[0]), B[1])
+    Bz = np.full((N[2] + 1, N[1], N[0]), B[2])
+    return BlockInput(tuple(n), g, (0.0, 0.0, 0.0), tuple(dx), m, W, [Bx, By, Bz])
+
+
+# ---------------------------------------------------------------------------------------------
+# 1D magnetised shock tube along x (16^3 block, Gamma = 5/3)
+# ---------------------------------------------------------------------------------------------
+def shock_tube_block(n=(16, 16, 16), g=3, left=(1.0, 1.0, 1.0), right=(0.125, 0.1, -1.0), Bx=0.5,
+                     x_range=(-0.5, 0.5)):
+    """left/right = (rho, p, B^y); Bx constant; u~ = 0; flat metric; discontinuity at x = 0."""
+    L = x_range[1] - x_range[0]
+    dx = (L / n[0], L / n[0], L / n[0])
+    x0 = (x_range[0], 0.0, 0.0)
+    N = tuple(v + 2 * g for v in n)
+    X, _, _ = grid(n, g, x0, dx)
+    W = np.zeros((5, N[2], N[1], N[0]))
+    isL = X < 0
+    W[0] = np.where(isL, left[0], right[0])
+    W[4] = np.where(isL, left[1], right[1])
+    Bxa = np.full((N[2], N[1], N[0] + 1), Bx)
+    Xy, _, _ = grid(n, g, x0, dx, (0, 1, 0))
+    By = np.where(Xy < 0, left[2], right[2]).astype(float)
+    Bz = np.zeros((N[2] + 1, N[1], N[0]))
+    return BlockInput(tuple(n), g, x0, dx, metric_flat(n, g), W, [Bxa, np.ascontiguousarray(By), Bz])
+
+
+# ---------------------------------------------------------------------------------------------
+# TOV star in isotropic coordinates (initial data of Sec. 4.1: K = 100, Gamma = 2)
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class TOV:
+    rbar: np.ndarray     # isotropic radius grid (interior, increasing)
+    rho: np.ndarray
+    p: np.ndarray
+    alpha: np.ndarray
+    psi4: np.ndarray     # conformal factor^4
+    R_iso: float         # isotropic surface radius
+    M: float             # gravitational mass
+    K: float
+    Gamma: float
+
+    def at(self, r):
+        """(rho, p, alpha, psi4) at isotropic radius r (array)."""
+        r = np.asarray(r, float)
+        inside = r < self.R_iso
+        rho = np.where(inside, np.interp(r, self.rbar, self.rho), 0.0)
+        p = np.where(inside, np.interp(r, self.rbar, self.p), 0.0)
+        rr = np.maximum(r, 0.5 * self.R_iso)   # exterior formulas are used only outside the star
+        a_out = (1 - self.M / (2 * rr)) / (1 + self.M / (2 * rr))
+        psi4_out = (1 + self.M / (2 * rr)) ** 4
+        alpha = np.where(inside, np.interp(r, self.rbar, self.alpha), a_out)
+        psi4 = np.where(inside, np.interp(r, self.rbar, self.psi4), psi4_out)
+        return rho, p, alpha, psi4
+
+
+def solve_tov(rho_c=1.28e-3, K=100.0, Gamma=2.0, npts=4000):
+    """TOV equations in Schwarzschild radius, then mapped to isotropic radius and matched to
+    isotropic Schwarzschild outside."""
+    from scipy.integrate import solve_ivp
+
+    def eps_of(p):
+        rho = (p / K) ** (1 / Gamma)
+        return rho, rho + p / (Gamma - 1)          # rest-mass and total energy density
+
+    p_c = K * rho_c ** Gamma
+
+    def rhs(r, y):
+        m, p, phi, lnrb = y
+        p = max(p, 0.0)
+        rho, e = eps_of(p)
+        if r == 0:
+            return [0, 0, 0, 0]
+        den = r * (r - 2 * m)
+        dp = -(e + p) * (m + 4 * np.pi * r ** 3 * p) / den
+        return [4 * np.pi * r ** 2 * e, dp, (m + 4 * np.pi * r ** 3 * p) / den,
+                1 / (r * np.sqrt(1 - 2 * m / r))]
+
+    def surface(r, y):
+        return y[1] - 1e-14 * p_c
+    surface.terminal = True
+    r0 = 1e-6
+    rho0, e0 = eps_of(p_c)
+    y0 = [4 / 3 * np.pi * r0 ** 3 * e0, p_c, 0.0, np.log(r0)]
+    sol = solve_ivp(rhs, (r0, 100.0), y0, events=surface, rtol=1e-11, atol=1e-14, dense_output=True,
+                    max_step=0.01)
+    R = sol.t[-1]
+    r = np.linspace(r0, R, npts)
+    m, p, phi, lnrb = sol.sol(r)
+    M = m[-1]
+    # isotropic radius: match rbar(R) to the exterior relation r = rbar (1 + M/(2 rbar))^2
+    Rb = 0.5 * (R - M + np.sqrt(R * R - 2 * M * R))
+    rbar = np.exp(lnrb - lnrb[-1]) * Rb
+    # lapse: e^phi with phi(R) = 0.5 ln(1 - 2M/R)
+    phi = phi - phi[-1] + 0.5 * np.log(1 - 2 * M / R)
+    p = np.maximum(p, 0.0)
+    rho = (p / K) ** (1 / Gamma)
+    psi4 = (r / rbar) ** 2
+    rbar = np.concatenate([[0.0], rbar])
+    rho = np.concatenate([[rho_c], rho]); p = np.concatenate([[p_c], p])
+    alpha = np.concatenate([[np.exp(phi[0])], np.exp(phi)])
+    psi4 = np.concatenate([[psi4[0]], psi4])
+    return TOV(rbar, rho, p, alpha, psi4, float(Rb), float(M), K, Gamma)
+
+
+def star_block(n=(64, 64, 64), g=3, half_width=10.02, tov: TOV | None = None, centres=((0.0, 0.0, 0.0),),
+               x0=None, dx=None, A_b=None, B_over_rho=None, f_atm=1e-13, rho_max=None):
+    """Static star(s) in a conformally flat metric with gamma_ij = psi^4 delta_ij, beta = 0, K = 0.
+
+    Several centres superpose the stars as psi = 1 + sum(psi_a - 1), alpha psi = 1 + sum(alpha_a psi_a - 1)
+    (reading of 'analytic superposed metric').  The poloidal field is the curl of
+    A = (-y A_phi, x A_phi, 0) with A_phi = A_b max(p - 0.04 p_max, 0) (Eq. Apotential), taken about each
+    centre.  Density below the atmosphere f_atm rho_max is raised to it."""
+    if tov is None:
+        tov = solve_tov()
+    if dx is None:
+        dx = (2 * half_width / n[0],) * 3
+    if x0 is None:
+        x0 = (-half_width,) * 3
+    rho_max = tov.rho[0] if rho_max is None else rho_max
+    rho_atm = f_atm * rho_max
+    p_atm = tov.K * rho_atm ** tov.Gamma
+
+    def fields_at(X, Y, Z):
+        rho = np.zeros_like(X); p = np.zeros_like(X)
+        psi = np.ones_like(X); apsi = np.ones_like(X)
+        for c in centres:
+            r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+            r_, p_, a_, q4 = tov.at(r)
+            rho += r_; p += p_
+            ps = q4 ** 0.25
+            psi += ps - 1; apsi += a_ * ps - 1
+        return rho, p, apsi / psi, psi ** 4
+
+    Xv, Yv, Zv = grid(n, g, x0, dx, (1, 1, 1))
+    _, _, al, q4 = fields_at(Xv, Yv, Zv)
+    assert np.all(al > 0)
+    m = metric_flat(n, g)
+    m[0] = al
+    m[4] = m[7] = m[9] = q4
+    X, Y, Z = grid(n, g, x0, dx)
+    rho, p, _, _ = fields_at(X, Y, Z)
+    rho = np.maximum(rho, rho_atm)
+    p = np.maximum(p, p_atm)
+    W = np.zeros((5,) + X.shape)
+    W[0] = rho
+    W[4] = p
+    p_max = tov.p[0]
+    if A_b is None:
+        A_b = 0.0
+
+    def A(comp, Xe, Ye, Ze):
+        out = np.zeros_like(Xe)
+        if comp == 2:
+            return out
+        for c in centres:
+            r = np.sqrt((Xe - c[0]) ** 2 + (Ye - c[1]) ** 2 + (Ze - c[2]) ** 2)
+            _, pp, _, _ = tov.at(r)
+            Aphi = A_b * np.maximum(pp - 0.04 * p_max, 0.0)
+            out += (-(Ye - c[1]) * Aphi) if comp == 0 else ((Xe - c[0]) * Aphi)
+        return out
+
+    B = curl_B(n, g, x0, dx, A)
+    return BlockInput(tuple(n), g, tuple(x0), tuple(dx), m, np.ascontiguousarray(W), B)
+
+
+# ---------------------------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------------------------
+def amr_like_batch(nblocks=1024, sizes=(16, 24, 32), g=3, seed=3, L=1.0, levels=3, **kw):
+    """Blocks of uneven sizes drawn from ``sizes``, at ``levels`` refinement levels (dx, dx/2, dx/4),
+    placed at random positions; all sample the same global smooth fields."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    fields = make_fields(rng, L, shared_metric=True)
+    blocks = []
+    for b in range(nblocks):
+        n = int(rng.choice(sizes))
+        lev = int(rng.integers(0, levels))
+        dxb = (L / 64) / (2 ** lev)
+        x0 = tuple(rng.uniform(0, L - n * dxb, 3))
+        blocks.append(random_block((n, n, n), g, x0, (dxb,) * 3, seed=seed, L=L, fields=fields, **kw))
+    return blocks
