@@ -33,6 +33,26 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIBC = os.path.join(_LIBDIR, "liboracle_count.so")
+
+
+def build_count(force: bool = False) -> str:
+    """Operation-counting build of the stage (``real`` = an op-counting scalar, see flopcount.h)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    hdr = os.path.join(_HERE, "flopcount.h")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(hdr))
+    if force or not os.path.exists(_LIBC) or os.path.getmtime(_LIBC) < newest:
+        tmp = _LIBC + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-DORACLE_COUNT_FLOPS", "-I", _HERE, "-o", tmp, _SRC])
+        os.replace(tmp, _LIBC)
+    return _LIBC
+
+
+PHASES = ["cell_metric_and_field", "faces", "cell_efield", "corner_emf", "update_and_sources", "ct",
+          "con2prim"]
+
+
 class OGeom(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("ng", C.c_int32), ("dx", C.c_double * 3)]
 
@@ -243,6 +263,40 @@ def stage_block(blk: Block, U, U0, B0, dt, P: Params, return_iters=False):
     if return_iters:
         return Uo, Bo, Wo, st, it
     return Uo, Bo, Wo, st
+
+
+_libc = None
+
+
+def stage_block_count(blk: Block, U, U0, B0, dt, P: Params):
+    """Run the counting build of the stage on one block; returns {phase: (add, mul, div, sqrt)}."""
+    global _libc
+    if _libc is None:
+        L = C.CDLL(build_count())
+        dp = C.POINTER(C.c_double)
+        L.oracle_stage_block.argtypes = lib().oracle_stage_block.argtypes
+        L.oracle_stage_block.restype = C.c_int
+        L.oracle_flops_get.argtypes = [dp, C.c_int]
+        _libc = L
+    L = _libc
+    g = blk.geom()
+    metric, W = _f64(blk.metric), _f64(blk.W)
+    B = [_f64(b) for b in blk.B]
+    U = _f64(U); U0 = _f64(U0); B0 = [_f64(b) for b in B0]
+    Uo = U.copy(); Wo = W.copy(); Bo = [b.copy() for b in B]
+    st = np.zeros(W.shape[1:], np.uint8)
+    it = np.zeros(W.shape[1:], np.int32)
+    out = np.zeros(35)
+    L.oracle_flops_get(_d(out), 1)
+    cp = P.c()
+    r = L.oracle_stage_block(C.byref(g), _d(metric), _d(W), _d(B[0]), _d(B[1]), _d(B[2]), _d(U), _d(U0),
+                             _d(B0[0]), _d(B0[1]), _d(B0[2]), float(dt), C.byref(cp), _d(Uo), _d(Bo[0]),
+                             _d(Bo[1]), _d(Bo[2]), _d(Wo), st.ctypes.data_as(C.POINTER(C.c_uint8)),
+                             it.ctypes.data_as(C.POINTER(C.c_int32)))
+    if r != 0:
+        raise ValueError("oracle_stage_block (count build) failed")
+    L.oracle_flops_get(_d(out), 1)
+    return {ph: tuple(out[5 * k:5 * k + 4]) for k, ph in enumerate(PHASES)}
 
 
 def divb(blk_n, ng, dx, B):

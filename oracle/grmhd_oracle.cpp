@@ -24,7 +24,14 @@
 #include <vector>
 #include <algorithm>
 
+#ifdef ORACLE_COUNT_FLOPS
+#include "flopcount.h"
+typedef Counted real;
+inline double to_d(const Counted& x) { return x.v; }
+#else
 typedef double real;
+inline double to_d(double x) { return x; }
+#endif
 
 extern "C" {
 
@@ -529,7 +536,10 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     Bu[i] = Bdens[i] / sg;
     finite = finite && std::isfinite(S[i]) && std::isfinite(Bu[i]);
   }
-  const real rho_thr = Q.f_thr * Q.rho_atm;
+  // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A).  Values within 1e-12 relative of it
+  // count as having reached it, so cells that sit at the atmosphere density up to rounding are
+  // reset deterministically.
+  const real rho_thr = Q.f_thr * Q.rho_atm * (1 + 1e-12);
   bool atm = false;
   if (!finite) { st |= 2; atm = true; }
   else if (D < rho_thr) { st |= 1; atm = true; }
@@ -622,8 +632,25 @@ inline void load16(const double* const* mv, long vi, real m[16]) {
 
 }  // namespace
 
+#ifdef ORACLE_COUNT_FLOPS
+OpCount g_ops;
+namespace {
+OpCount g_phase[8];
+void phase_mark(int k, OpCount& last) {
+  g_phase[k].add += g_ops.add - last.add; g_phase[k].mul += g_ops.mul - last.mul;
+  g_phase[k].div += g_ops.div - last.div; g_phase[k].sqrt += g_ops.sqrt - last.sqrt;
+  g_phase[k].cmp += g_ops.cmp - last.cmp;
+  last = g_ops;
+}
+}  // namespace
+#define ORACLE_PHASE(k) phase_mark(k, ops_last)
+#else
+#define ORACLE_PHASE(k)
+#endif
+
 extern "C" {
 
+#ifndef ORACLE_COUNT_FLOPS
 // Primitive -> conserved at np points.  metric: np x 16, prims: np x 5, Bdens: np x 3, q: np x 5.
 void oracle_prim2con(int np, const double* metric, const double* prims, const double* Bdens,
                      const oparams* Q, double* q) {
@@ -736,6 +763,20 @@ void oracle_interp_faces(const ob_geom* G, const double* metric, int order, int 
       }
 }
 
+#else
+// Operation counts per phase of the stage accumulated since the last reset:
+// out[5*k + {0,1,2,3,4}] = (add, mul, div, sqrt, cmp) of phase k, k = 0..6:
+//   0 cell metric + cell field, 1 faces (reconstruction, face metric, HLLE), 2 cell electric field,
+//   3 corner EMFs, 4 flux divergence + sources + update, 5 CT face update, 6 con2prim
+void oracle_flops_get(double* out, int reset) {
+  for (int k = 0; k < 7; ++k) {
+    out[5 * k + 0] = g_phase[k].add; out[5 * k + 1] = g_phase[k].mul; out[5 * k + 2] = g_phase[k].div;
+    out[5 * k + 3] = g_phase[k].sqrt; out[5 * k + 4] = g_phase[k].cmp;
+    if (reset) g_phase[k] = OpCount();
+  }
+}
+#endif
+
 // One Runge-Kutta stage on one MeshBlock.
 //   metric: 16 vertex arrays; W: 5 cell arrays (stage-input prims, ghosts filled); B: 3 face arrays
 //   (densitised, ghosts filled); U, U0: 5 cell arrays (interior read); B0: 3 face arrays.
@@ -760,6 +801,9 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
   const int lo_c = (Q.interp_order == 4) ? -g + 1 : -g;   // cells whose metric is computable
   const int hi_off = (Q.interp_order == 4) ? g - 1 : g;   // ... up to n + hi_off - 1
 
+#ifdef ORACLE_COUNT_FLOPS
+  OpCount ops_last = g_ops;
+#endif
   // a1: metric at cell centres (all computable cells); sqrt(gamma) kept per cell
   std::vector<PM> cm(NC);
   for (int k = lo_c; k < b.n[2] + hi_off; ++k)
@@ -782,6 +826,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
         }
       }
 
+  ORACLE_PHASE(0);
   // a3 + a4: face fluxes on d-faces with normal index 0..n_d and transverse index -1..n_t
   std::vector<Arr> Fq[3], Fb[3];
   for (int d = 0; d < 3; ++d) {
@@ -817,8 +862,9 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
             for (int t = 0; t < 6; ++t) st[t] = w1[v][t];
             recon_face(Q.recon, st, Q.weno_eps, &Lv[v], &Rv[v]);
           }
-          // c6: a bad reconstructed state drops both sides of the face to first order
-          if (Lv[0] < Q.rho_atm || Rv[0] < Q.rho_atm || !(Lv[4] > 0) || !(Rv[4] > 0))
+          // c6: a non-physical reconstructed state (rho <= 0 or p <= 0) drops both sides of the
+          // face to first order
+          if (!(Lv[0] > 0) || !(Rv[0] > 0) || !(Lv[4] > 0) || !(Rv[4] > 0))
             for (int v = 0; v < 7; ++v) { Lv[v] = w1[v][2]; Rv[v] = w1[v][3]; }
           for (int v = 0; v < 5; ++v) { wL[v] = Lv[v]; wR[v] = Rv[v]; }
           cL[0] = Lv[5]; cL[1] = Lv[6]; cR[0] = Rv[5]; cR[1] = Rv[6];
@@ -841,6 +887,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
         }
   }
 
+  ORACLE_PHASE(1);
   // a5: cell-centred E_m = alpha (v~^b B^a - v~^a B^b), (a,b,m) cyclic, on cells -1..n
   Arr Ecc[3] = {Arr(NC), Arr(NC), Arr(NC)};
   for (int k = -1; k <= b.n[2]; ++k)
@@ -857,6 +904,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
           Ecc[m][ci] = cm[ci].alpha * (F.vt_u[bb] * Bd[a] - F.vt_u[a] * Bd[bb]);
         }
       }
+  ORACLE_PHASE(2);
   // a5: edge E_m at (a-face ia, b-face ib, m-cell im).  From an a-face E_m = -F^a_{B^b} (Fb[a][0]);
   // from a b-face E_m = +F^b_{B^a} (Fb[bb][1]).  Gardiner-Stone corner average (c9).
   std::vector<Arr> Ee;
@@ -894,6 +942,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
         }
   }
 
+  ORACLE_PHASE(3);
   // a6: cell update with flux divergence and sources (stage-input prims), Eq. claw
   for (int k = 0; k < b.n[2]; ++k)
     for (int j = 0; j < b.n[1]; ++j)
@@ -915,11 +964,12 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
             p1[d] += 1;
             divF += (Fq[d][v][fidx(b, d, p1)] - Fq[d][v][fidx(b, d, p)]) / b.dx[d];
           }
-          Uo[v * NC + ci] = Q.rk_g0 * U0[v * NC + ci] + Q.rk_g1 * U[v * NC + ci] +
-                            Q.rk_beta * dt * (-divF + s[v]);
+          Uo[v * NC + ci] = to_d(Q.rk_g0 * U0[v * NC + ci] + Q.rk_g1 * U[v * NC + ci] +
+                                 Q.rk_beta * dt * (-divF + s[v]));
         }
       }
 
+  ORACLE_PHASE(4);
   // a7: constrained-transport face update, B'^d = g0 B0 + g1 B - beta dt (curl E)_d
   for (int d = 0; d < 3; ++d) {
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -935,10 +985,11 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
           const real dE2 = (Ee[t2][b.v(a1[0], a1[1], a1[2])] - Ee[t2][b.v(p[0], p[1], p[2])]) / b.dx[t1];
           const real dE1 = (Ee[t1][b.v(a2[0], a2[1], a2[2])] - Ee[t1][b.v(p[0], p[1], p[2])]) / b.dx[t2];
           const long fi = fidx(b, d, p);
-          Bof[d][fi] = Q.rk_g0 * B0f[d][fi] + Q.rk_g1 * Bf[d][fi] - Q.rk_beta * dt * (dE2 - dE1);
+          Bof[d][fi] = to_d(Q.rk_g0 * B0f[d][fi] + Q.rk_g1 * Bf[d][fi] - Q.rk_beta * dt * (dE2 - dE1));
         }
   }
 
+  ORACLE_PHASE(5);
   // a8: con2prim on the updated state (cell field from the updated faces)
   for (int k = 0; k < b.n[2]; ++k)
     for (int j = 0; j < b.n[1]; ++j)
@@ -955,8 +1006,9 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
         int it = 0;
         status[ci] = (uint8_t)con2prim_point(cm[ci], Q, q, Bd, w, &it);
         if (iters) iters[ci] = it;
-        for (int v = 0; v < 5; ++v) { Uo[v * NC + ci] = q[v]; Wo[v * NC + ci] = w[v]; }
+        for (int v = 0; v < 5; ++v) { Uo[v * NC + ci] = to_d(q[v]); Wo[v * NC + ci] = to_d(w[v]); }
       }
+  ORACLE_PHASE(6);
   return 0;
 }
 
@@ -975,7 +1027,7 @@ void oracle_divb_block(const ob_geom* G, const double* Bx, const double* By, con
           p1[d] += 1;
           s += (Bf[d][fidx(b, d, p1)] - Bf[d][fidx(b, d, p)]) / b.dx[d];
         }
-        divb[b.c(i, j, k)] = s;
+        divb[b.c(i, j, k)] = to_d(s);
       }
 }
 

@@ -316,3 +316,18 @@ def test_con2prim_lorentz_factor_clamp():
     P2 = O.Params(gamma_ad=GAMMA, rho_atm=1e-20, ceiling=1)
     w3, q3, st3, _ = O.con2prim(m, q, B, P2)
     assert np.all(st3 & 4) and np.all(w3[:, 0] == P2.rho_atm)
+
+
+def test_con2prim_cells_at_the_atmosphere_density_are_reset_deterministically():
+    """Cells whose density equals f_thr rho_atm up to rounding (1e-12 relative) take the
+    atmosphere branch; cells clearly above it are solved."""
+    P = O.Params(gamma_ad=GAMMA, rho_atm=1e-13, p_atm=1e-24)
+    n = 6
+    m = np.zeros((n, 16)); m[:, 0] = 1; m[:, 4] = m[:, 7] = m[:, 9] = 1
+    w = np.zeros((n, 5))
+    w[:, 0] = 1e-13 * np.array([1 - 1e-15, 1.0, 1 + 1e-15, 1 + 5e-13, 1 + 1e-9, 2.0])
+    w[:, 4] = 1e-24
+    q = O.prim2con(m, w, np.zeros((n, 3)), P)
+    w2, q2, st, _ = O.con2prim(m, q, np.zeros((n, 3)), P)
+    assert list(st & 1) == [1, 1, 1, 1, 0, 0]
+    assert np.all(w2[:4, 4] == 1e-24) and np.all(w2[:4, 0] == 1e-13)
