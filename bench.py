@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: GRMHD cell-updates/s per Runge-Kutta stage on one GB300.
+
+Workload (full-stage throughput): 256^3 cells as 4096 MeshBlocks of 16^3 (3 ghosts) on [-32, 32]^3,
+two Gamma = 2, K = 100 TOV stars (rho_c = 1e-3) at x = +-20 in their superposed conformally flat
+metric, poloidal field with max b^2 / max rho = 1e-2, atmosphere 1e-13 rho_max, WENOZ + HLLE.
+A step is one gr_stage call over all blocks (metric interpolation, reconstruction, HLLE, corner
+EMFs, CT update, flux divergence + sources, con2prim).  Inputs are synthetic (seeded/analytic) and
+resident in HBM (~25 GB, far larger than L2, so no flush is needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is the mixed-precision path (FP32 reconstruction / HLLE / EMF,
+FP64 accumulation, CT and con2prim); the plain FP64 path is reported beside it.  Multi-GPU runs are
+independent replicas (the stage needs no exchange inside a step); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GRMHD cell-updates/s per RK stage"
+UNIT = "cell-updates/s"
+WORKLOAD = "two-star full-stage throughput: 4096 blocks of 16^3 (ng=3), WENOZ+HLLE, CT, con2prim"
+FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of the GB300 (profiling recipe table)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def env_rank():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nb", type=int, default=16, help="blocks per dimension (16 -> 4096 blocks)")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    return a
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on host cores
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(mesh, seconds, nthreads):
+    """Time the oracle's stage on a seeded random sample of blocks with nthreads host threads (the
+    ctypes call releases the GIL).  Returns (cell-updates/s, cells, wall seconds, blocks)."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle as O
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=mesh.rho_atm, p_atm=mesh.p_atm, tol=1e-10)
+    dt = 0.25 * mesh.dx
+    rng = np.random.default_rng(2311_04989)
+    order = rng.permutation(mesh.nb ** 3)
+
+    def prep(b):
+        bi = mesh.block(int(b))
+        blk = O.Block(bi.n, bi.ng, bi.dx, bi.metric, bi.W, bi.B)
+        g = bi.ng
+        val, _ = O.interp_cells(blk, 2, (-g,) * 3, tuple(v + g for v in bi.n))
+        Bx, By, Bz = bi.B
+        Bc = np.stack([0.5 * (Bx[:, :, 1:] + Bx[:, :, :-1]), 0.5 * (By[:, 1:, :] + By[:, :-1, :]),
+                       0.5 * (Bz[1:, :, :] + Bz[:-1, :, :])], -1).reshape(-1, 3)
+        q = O.prim2con(val, np.moveaxis(bi.W, 0, -1).reshape(-1, 5), Bc, P)
+        U = np.ascontiguousarray(np.moveaxis(q.reshape(bi.W.shape[1:] + (5,)), -1, 0))
+        return blk, U
+
+    def one(item):
+        blk, U = item
+        O.stage_block(blk, U, U, blk.B, dt, P)
+        return blk.n[0] * blk.n[1] * blk.n[2]
+
+    O.lib()
+    # estimate the per-block cost on one prepared block, then size the sample to the budget
+    probe = prep(order[0])
+    t = time.perf_counter()
+    one(probe)
+    per_block = max(time.perf_counter() - t, 1e-4)
+    done = int(min(len(order), max(nthreads, seconds * nthreads / per_block)))
+    items = [probe] + [prep(b) for b in order[1:done]]
+    t1 = time.perf_counter()
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        cells = sum(ex.map(one, items))
+    wall = time.perf_counter() - t1
+    return cells / wall, cells, wall, done
+
+
+def run_reference(a):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from paper_2311_04989_gb300 import inputs as I
+    mesh = I.BinaryStarMesh(nb=a.nb, n=16)
+    nthreads = os.cpu_count() or 1
+    per_step = max(1.0, 60.0 / max(1, a.steps + a.warmup))
+    vals = []
+    for s in range(a.warmup + a.steps):
+        v, cells, wall, nblk = oracle_sample(mesh, per_step, nthreads)
+        if s >= a.warmup:
+            vals.append((v, cells, wall, nblk))
+    value = statistics.median([v[0] for v in vals])
+    ms = statistics.median([v[2] / v[1] * (16 ** 3 * a.nb ** 3) * 1e3 for v in vals])
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + " (bounded random sample of blocks per step)",
+                      "blocks": a.nb ** 3, "parallelism": "replicas"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                            "sample": f"{vals[-1][3]} random blocks of 16^3 per step (~{per_step:.0f} s of "
+                                      f"work), oracle FP64 C++ stage, {nthreads} threads"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_04989_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, precision):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, only if it was taken on
+    the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{kernel}:{precision}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2311_04989_gb300 import build as Bld
+    from paper_2311_04989_gb300 import grstage as G
+    from paper_2311_04989_gb300 import inputs as I
+
+    rank, world, lrank = env_rank()
+    torch.cuda.set_device(lrank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    if rank == 0 or world == 1:
+        Bld.build()
+    if dist:
+        dist.barrier()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    # ---- workload ------------------------------------------------------------------------------
+    t_gen = time.time()
+    mesh_in = I.BinaryStarMesh(nb=a.nb, n=16)
+    geoms = mesh_in.blocks()
+    L = G.Layout.of(geoms)
+    Wh, Bh, Mh = mesh_in.pack(L)
+    dev = torch.device("cuda", lrank)
+    W = torch.from_numpy(Wh).to(dev)
+    B = [torch.from_numpy(x).to(dev) for x in Bh]
+    M = torch.from_numpy(Mh).to(dev)
+    del Wh, Bh, Mh
+    t_gen = time.time() - t_gen
+    Mfull = [M[c] for c in range(10)] + [M[0]] * 6          # K_ij unread (k_zero)
+    metric = G.gr_metric()
+    for c in range(16):
+        metric.v[c] = int(Mfull[c].data_ptr())
+    metric.order, metric.k_zero = 2, 1
+    ctx = G.gr_context_create(lrank)
+    mesh = G.gr_mesh_create(ctx, L.descriptors())
+    ws_bytes = G.gr_mesh_workspace_bytes(mesh)
+    stream = torch.cuda.current_stream()
+    U = torch.zeros_like(W)
+    P64 = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_FP64, gamma_ad=2.0,
+                              rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+    G.gr_prim2con(mesh, metric, list(W), B, list(U), P64, stream)
+    Uo = torch.zeros_like(U); Wo = torch.zeros_like(W); Bo = [torch.zeros_like(x) for x in B]
+    st = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
+    state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+    dt = 0.25 * mesh_in.dx
+    cells = L.interior_cells()
+
+    def timed(precision):
+        p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=precision, gamma_ad=2.0,
+                                rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        for _ in range(a.warmup):
+            G.gr_stage(mesh, metric, state, dt, p, stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = ClockSampler(lrank)
+        clk.start()
+        G.gr_profile_begin(mesh, a.steps)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(a.steps):
+            G.gr_stage(mesh, metric, state, dt, p, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        kms, nst = G.gr_profile_end(mesh)
+        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        return ms_t.item() / a.steps, [k / max(1, nst) for k in kms], clocks
+
+    results = {}
+    precs = {"both": ["fp64", "mixed"], "fp64": ["fp64"], "mixed": ["mixed"]}[a.precision]
+    snap = {}
+    for name in precs:
+        prec = G.GR_PREC_FP64 if name == "fp64" else G.GR_PREC_MIXED
+        ms, kms, clocks = timed(prec)
+        results[name] = dict(ms=ms, kernel_ms=kms, clocks=clocks)
+        snap[name] = (Wo[0].clone(), [x.clone() for x in Bo], Uo.clone())
+    # error of the mixed path against the FP64 path (which matches the oracle to 1e-12)
+    err = None
+    if "fp64" in snap and "mixed" in snap:
+        r64, rmx = snap["fp64"][0], snap["mixed"][0]
+        mask = r64 > 0
+        err = {"rho_rel_max": float(((rmx - r64).abs()[mask] / r64[mask]).max().item())}
+        d = G.gr_diag(mesh, list(snap["mixed"][2]), snap["mixed"][1], stream)
+        err["divB_rel_max"] = d[1]
+        err["divB_integrated"] = d[2]
+    head = "mixed" if "mixed" in results else "fp64"
+    ms_head = results[head]["ms"]
+    value = cells * world / (ms_head / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------------
+    e2e = None
+    if not a.no_e2e:
+        p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=(G.GR_PREC_MIXED if head == "mixed" else G.GR_PREC_FP64),
+                                gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        ins = [U, W, M] + B
+        outs = [Uo, Wo, st] + Bo
+        h_in = [x.cpu().pin_memory() for x in ins]
+        h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in outs]
+        bin_ = sum(x.numel() * x.element_size() for x in ins)
+        bout = sum(x.numel() * x.element_size() for x in outs)
+
+        def e2e_step():
+            for d_, h_ in zip(ins, h_in):
+                d_.copy_(h_, non_blocking=True)
+            G.gr_stage(mesh, metric, state, dt, p, stream)
+            for h_, d_ in zip(h_out, outs):
+                h_.copy_(d_, non_blocking=True)
+
+        for _ in range(a.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e = torch.tensor([e0.elapsed_time(e1) / a.steps], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": cells * world / (ms_e.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": bin_,
+               "d2h_bytes_per_step": bout, "ms_per_step": ms_e.item()}
+
+    # ---- roofline of the dominant kernel ---------------------------------------------------------
+    flops = json.load(open(os.path.join(ROOT, "tests", "golden", "flops_binary_star_16cubed.json")))
+    ph = flops["phases"]
+
+    def ph_flops(*names):
+        return sum(ph[n]["add"] + ph[n]["mul"] + ph[n]["div"] + ph[n]["sqrt"] for n in names)
+
+    kernel_phases = {"k_cellprep": ("cell_metric_and_field", "cell_efield"), "k_faces": ("faces",),
+                     "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources", "con2prim")}
+    scale = (a.nb ** 3) / 4096.0
+
+    def roofline(name):
+        kms = results[name]["kernel_ms"]
+        k = max(range(len(kms)), key=lambda i: kms[i])
+        kn = G.KERNEL_NAMES[k]
+        fl = ph_flops(*kernel_phases[kn]) * scale
+        fp32 = name == "mixed" and kn in ("k_faces", "k_edges")
+        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+        ach = fl / (kms[k] / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": load_traffic(kn, name), "kernel": kn,
+                "peak_kind": ("FP32 lanes x 2 x max clock (derived)" if fp32 else "FP64 nominal (recipe table)"),
+                "flops_per_launch": fl, "kernel_ms": kms[k],
+                "kernel_share": kms[k] / sum(kms)}
+
+    # ---- CPU baseline (rank 0, N = 1) ------------------------------------------------------------
+    cpu = None
+    if not a.no_cpu and world == 1 and rank == 0:
+        nthreads = os.cpu_count() or 1
+        v, ncell, wall, nblk = oracle_sample(mesh_in, a.cpu_seconds, nthreads)
+        cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"{nblk} seeded-random blocks of the same workload, FP64 oracle stage, "
+                         f"{nthreads} threads, {wall:.1f} s"}
+
+    launches = a.steps * 5
+    fp64 = None
+    if "fp64" in results and head != "fp64":
+        fp64 = {"value": cells * world / (results["fp64"]["ms"] / 1e3), "ms_per_step": results["fp64"]["ms"],
+                "kernel_ms": dict(zip(G.KERNEL_NAMES, results["fp64"]["kernel_ms"])),
+                "roofline": roofline("fp64"), "clocks": results["fp64"]["clocks"]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms_head, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "blocks": a.nb ** 3, "cells_per_gpu": cells, "recon": "WENOZ",
+                      "riemann": "HLLE", "precision": head, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs ~25 GB >> L2 (no flush)", "workspace_bytes": ws_bytes,
+                      "input_gen_s": round(t_gen, 1)},
+           "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
+           "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
+           "fp64": fp64, "mixed_error_vs_fp64": err,
+           "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    G.gr_mesh_destroy(mesh)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

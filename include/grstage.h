@@ -1,0 +1,175 @@
+/*
+ * grstage.h -- C ABI of the GB300 GRMHD Runge-Kutta stage library (libgrstage.so).
+ *
+ * One stage of the ideal-GRMHD conservative update of GR-Athena++ (arXiv:2311.04989) on a batch of
+ * MeshBlocks with constrained transport in a given 3+1 metric:
+ *   Eq. claw (conservation law), Eq. consB_def (conserved variables), Eq. fluxB_def (fluxes),
+ *   Eq. EMT_MHD and Eq. hydsrc_def (geometric sources), Sec. 3.2 (vertex-to-cell/face Lagrange
+ *   interpolation of the metric), Sec. 3.3 (constrained transport), Sec. 3.4 (PLM / WENOZ
+ *   reconstruction of the primitives incl. pressure), Sec. 3.5 and App. A (conservative-to-primitive
+ *   inversion with atmosphere and limits).  The Riemann solver is HLLE with the approximate
+ *   fast-magnetosonic speeds of Sec. 2.2.
+ *
+ * Conventions
+ *   - All arrays are device pointers owned by the caller; the library never frees them.
+ *   - Every variable lives in its own "pool" (structure of arrays).  Block b's data of a pool start at
+ *     the element offset given in its gr_block.  Within a block, arrays are ghost-padded with ng
+ *     cells on every side and x is the fastest index:
+ *       cell arrays      (nz+2g) x (ny+2g) x (nx+2g)        cell i in [-g, n+g-1]
+ *       x-face arrays    (nz+2g) x (ny+2g) x (nx+2g+1)      face i at the low side of cell i
+ *       y-/z-face arrays likewise with the extra point along y / z
+ *       vertex arrays    (nz+2g+1) x (ny+2g+1) x (nx+2g+1) vertex i in [-g, n+g]
+ *   - Primitives w = (rho, u~^x, u~^y, u~^z, p); conserved q = (D, S_x, S_y, S_z, tau); B^i is the
+ *     densitised face field sqrt(gamma) calB^i.  Metric components in the order
+ *     alpha, beta^x, beta^y, beta^z, gamma_xx, gamma_xy, gamma_xz, gamma_yy, gamma_yz, gamma_zz,
+ *     K_xx, K_xy, K_xz, K_yy, K_yz, K_zz.
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream).  Functions that return host values synchronise that stream.
+ *   - Return value: GR_OK or a negative gr_error.  Pointwise physics problems are not errors; they go
+ *     into the per-cell status bits below.
+ */
+#ifndef GRSTAGE_H
+#define GRSTAGE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GR_ABI_VERSION 1
+
+typedef enum {
+  GR_OK = 0,
+  GR_EINVAL = -1,       /* bad argument, descriptor, size, or ghost width too small for the stencil */
+  GR_ECUDA = -2,        /* a CUDA runtime call failed (message in gr_last_error) */
+  GR_ENOMEM = -3,       /* device allocation failed */
+  GR_ETIMEOUT = -4,     /* a bounded device wait expired */
+  GR_EUNSUPPORTED = -5  /* option combination not built */
+} gr_error;
+
+enum { GR_RECON_PLM = 0, GR_RECON_WENOZ = 1 };          /* Sec. 3.4 */
+enum { GR_PREC_FP64 = 0, GR_PREC_MIXED = 1 };           /* mixed: FP32 reconstruction/HLLE/EMF */
+enum { GR_EMF_UPWIND = 0, GR_EMF_MEAN = 1 };            /* Sec. 3.3 corner electric field */
+enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec. 3.5 reset */
+
+/* con2prim status bits (per cell, uint8) */
+#define GR_ST_ATM_THRESHOLD 0x01  /* rho or D below f_thr rho_atm -> atmosphere (Sec. 3.5, App. A) */
+#define GR_ST_FAILED        0x02  /* non-finite input, no bracket or no convergence -> atmosphere */
+#define GR_ST_W_CLAMPED     0x04  /* Lorentz factor above W_max: clamped (or atmosphere)  (App. A) */
+#define GR_ST_TAU_FLOOR     0x08  /* tau raised to the cold static value (App. A) */
+#define GR_ST_BD_LIMIT      0x10  /* B^2/D above M_max: D rescaled (App. A) */
+#define GR_ST_EOS_CLAMP     0x20  /* eps clamped to the EOS range (App. A) */
+
+/* One MeshBlock: n[] interior cells, ng ghosts, cell widths, and element offsets into the pools. */
+typedef struct {
+  int32_t n[3];
+  int32_t ng;
+  double dx[3];
+  int64_t cell_off;     /* into every cell pool (U, U0, W, Uo, Wo, status) */
+  int64_t face_off[3];  /* into the x-, y-, z-face pools (B, B0, Bo) */
+  int64_t vert_off;     /* into the 16 vertex metric pools */
+} gr_block;
+
+/* The 3+1 metric on vertices (Sec. 3.2).  order: Lagrange interpolation order 2 or 4 (order 4 needs
+ * one ghost more than the reconstruction stencil).  k_zero != 0 declares K_ij = 0 (v[10..15] unread). */
+typedef struct {
+  const double* v[16];
+  int32_t order;
+  int32_t k_zero;
+} gr_metric;
+
+/* Stage state.  Inputs must have their ghost zones filled by the caller (the stage itself exchanges
+ * nothing).  U, U0 and B0 are read on the interior only; W and B on the interior and the ghosts.
+ * Outputs are written on the interior only: Uo (cells), Bo (all faces of interior cells), Wo, status.
+ * Outputs must not alias inputs. */
+typedef struct {
+  const double* U[5];
+  const double* U0[5];   /* RK register; read only where rk_g0 != 0 */
+  const double* B[3];
+  const double* B0[3];   /* read only where rk_g0 != 0 */
+  const double* W[5];
+  double* Uo[5];
+  double* Bo[3];
+  double* Wo[5];
+  uint8_t* status;
+} gr_state;
+
+/* Parameters.  size must be sizeof(gr_params).  Defaults from gr_params_default(). */
+typedef struct {
+  uint32_t size;
+  int32_t recon;        /* GR_RECON_* */
+  int32_t precision;    /* GR_PREC_* */
+  int32_t emf;          /* GR_EMF_* */
+  int32_t ceiling;      /* GR_CEIL_* */
+  int32_t max_iter;     /* root-find iteration cap */
+  double gamma_ad;      /* ideal gas p = rho eps (Gamma - 1), Sec. 2.3 */
+  double rho_atm;       /* f_atm rho_max (Sec. 3.5) */
+  double p_atm;         /* p(rho_atm) */
+  double f_thr;         /* atmosphere threshold factor */
+  double W_max;         /* Lorentz-factor ceiling, sqrt(1 + 20^2) for u~ <= 20 (Sec. 3.5) */
+  double M_max;         /* B^2/D ceiling (App. A) */
+  double tol;           /* relative bracket tolerance (Sec. 3.5: 1e-10) */
+  double weno_eps;      /* WENOZ epsilon */
+  double rk_g0, rk_g1, rk_beta;   /* U' = g0 U0 + g1 U + beta dt L(U) (Shu-Osher stage) */
+} gr_params;
+
+typedef struct gr_ctx gr_ctx;
+typedef struct gr_mesh gr_mesh;
+
+/* Error text of a code; gr_last_error() gives the detail of the last failing call of this thread. */
+const char* gr_strerror(int code);
+const char* gr_last_error(void);
+int gr_abi_version(void);
+void gr_params_default(gr_params* p);
+
+/* A context binds one CUDA device.  Returns GR_EINVAL for a bad device index. */
+int gr_context_create(gr_ctx** ctx, int device);
+int gr_context_destroy(gr_ctx* ctx);
+
+/* A mesh is a batch of blocks resident on the device: the block table, the per-kernel work lists
+ * and the workspace for face fluxes and corner fields (owned by the mesh).  Blocks may differ in
+ * size.  The block descriptors are copied; the caller may free its array afterwards. */
+int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t max_ng,
+                   gr_mesh** mesh);
+int gr_mesh_destroy(gr_mesh* mesh);
+/* Bytes of device workspace held by the mesh. */
+int64_t gr_mesh_workspace_bytes(const gr_mesh* mesh);
+
+/* One Runge-Kutta stage on every block of the mesh (steps of Sec. 3.2-3.5 in order):
+ *   metric interpolation -> reconstruction -> HLLE face fluxes -> corner EMFs -> CT face update
+ *   -> flux divergence + sources -> con2prim with atmosphere.  Fluxes and sources use W (the
+ *   primitives of the stage input); con2prim runs once, on the output. */
+int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+             const gr_params* params, void* stream);
+
+/* Primitive -> conserved (Eq. consB_def) on the interior cells of every block, with the cell-centred
+ * field taken as the mean of the two densitised faces. */
+int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5],
+                const double* const B[3], double* const U[5], const gr_params* params, void* stream);
+
+/* Conserved -> primitive on the interior cells (Sec. 3.5, App. A).  U is rewritten where the
+ * atmosphere or a limit applies.  status may be NULL. */
+int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
+                double* const W[5], uint8_t* status, const gr_params* params, void* stream);
+
+/* Diagnostics (Eq. Mb, Eq. gausslaw).  out[0] = M_b = sum D dV; out[1] = max |div B| min(dx)/max|B|;
+ * out[2] = sum |div B| dV / (max|B| sum dV / min dx); out[3] = max |B| over interior faces.
+ * Synchronises the stream. */
+int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4],
+            void* stream);
+
+/* Per-kernel timing of gr_stage with CUDA events on the launch stream (measurement only).
+ * gr_profile_begin arms the mesh for up to max_stages subsequent gr_stage calls: each records an event
+ * before and after each of its GR_NKERNELS kernels (cell prep, faces, edges, CT, update+con2prim).
+ * gr_profile_end synchronises on the last event and returns, per kernel, the summed milliseconds in
+ * ms[GR_NKERNELS] and the number of profiled stages in *nstages; it disarms the mesh. */
+#define GR_NKERNELS 5
+int gr_profile_begin(gr_mesh* mesh, int32_t max_stages);
+int gr_profile_end(gr_mesh* mesh, double* ms, int32_t* nstages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRSTAGE_H */

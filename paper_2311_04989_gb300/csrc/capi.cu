@@ -1,0 +1,429 @@
+// capi.cu -- host side of the C ABI declared in include/grstage.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace grs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(GR_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// region element counts on the host (mirror of the device decoder)
+long long region_count(int kind, int dir, const DBlock& b) {
+  long long c = 1;
+  for (int a = 0; a < 3; ++a) {
+    long long n;
+    switch (kind) {
+      case R_CELLS_ALL: n = b.N[a]; break;
+      case R_FACES: n = (a == dir) ? b.n[a] + 1 : b.n[a] + 2; break;
+      case R_EDGES: n = (a == dir) ? b.n[a] : b.n[a] + 1; break;
+      case R_CTFACES: n = (a == dir) ? b.n[a] + 1 : b.n[a]; break;
+      default: n = b.n[a]; break;
+    }
+    c *= n;
+  }
+  return c;
+}
+bool region_has_dir(int kind) { return kind == R_FACES || kind == R_EDGES || kind == R_CTFACES; }
+
+}  // namespace
+
+struct gr_ctx {
+  int device;
+};
+
+struct gr_mesh {
+  gr_ctx* ctx = nullptr;
+  int nblocks = 0;
+  int max_ng = 0;
+  std::vector<DBlock> h_blocks;
+  DBlock* d_blocks = nullptr;
+  Work* d_work[R_NREGION] = {};
+  int nwork[R_NREGION] = {};
+  Workspace ws{};
+  double* d_diag = nullptr;
+  std::vector<void*> allocs;
+  int64_t ws_bytes = 0;
+  int min_ng = 0;
+  // profiling: (GR_NKERNELS + 1) events per armed stage
+  std::vector<cudaEvent_t> prof_events;
+  int prof_capacity = 0;
+  int prof_used = 0;
+};
+
+extern "C" {
+
+const char* gr_strerror(int code) {
+  switch (code) {
+    case GR_OK: return "ok";
+    case GR_EINVAL: return "invalid argument";
+    case GR_ECUDA: return "CUDA error";
+    case GR_ENOMEM: return "out of device memory";
+    case GR_ETIMEOUT: return "bounded device wait expired";
+    case GR_EUNSUPPORTED: return "unsupported option";
+    default: return "unknown error";
+  }
+}
+
+const char* gr_last_error(void) { return g_last_error.c_str(); }
+
+int gr_abi_version(void) { return GR_ABI_VERSION; }
+
+void gr_params_default(gr_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->size = sizeof(gr_params);
+  p->recon = GR_RECON_WENOZ;
+  p->precision = GR_PREC_FP64;
+  p->emf = GR_EMF_UPWIND;
+  p->ceiling = GR_CEIL_CLAMP;
+  p->max_iter = 100;
+  p->gamma_ad = 2.0;
+  p->rho_atm = 1e-13;
+  p->p_atm = 100.0 * 1e-26;
+  p->f_thr = 1.0;
+  p->W_max = std::sqrt(1.0 + 400.0);
+  p->M_max = 1e4;
+  p->tol = 1e-10;
+  p->weno_eps = 1e-40;
+  p->rk_g0 = 0.0;
+  p->rk_g1 = 1.0;
+  p->rk_beta = 1.0;
+}
+
+int gr_context_create(gr_ctx** ctx, int device) {
+  if (!ctx) return fail(GR_EINVAL, "gr_context_create: ctx is NULL");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(GR_EINVAL, "gr_context_create: bad device index");
+  DeviceGuard g(device);
+  e = cudaFree(nullptr);   // establish the primary context
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(0)");
+  *ctx = new gr_ctx{device};
+  return GR_OK;
+}
+
+int gr_context_destroy(gr_ctx* ctx) {
+  delete ctx;
+  return GR_OK;
+}
+
+static void prof_release(gr_mesh* m) {
+  for (cudaEvent_t e : m->prof_events) cudaEventDestroy(e);
+  m->prof_events.clear();
+  m->prof_capacity = m->prof_used = 0;
+}
+
+static void mesh_free(gr_mesh* m) {
+  if (!m) return;
+  DeviceGuard g(m->ctx ? m->ctx->device : 0);
+  prof_release(m);
+  for (void* p : m->allocs) cudaFree(p);
+  delete m;
+}
+
+int gr_profile_begin(gr_mesh* mesh, int32_t max_stages) {
+  if (!mesh || max_stages < 1 || max_stages > 100000) return fail(GR_EINVAL, "gr_profile_begin: bad argument");
+  DeviceGuard g(mesh->ctx->device);
+  prof_release(mesh);
+  const int ne = (GR_NKERNELS + 1) * max_stages;
+  mesh->prof_events.resize(ne);
+  for (int i = 0; i < ne; ++i) {
+    cudaError_t e = cudaEventCreate(&mesh->prof_events[i]);
+    if (e != cudaSuccess) {
+      mesh->prof_events.resize(i);
+      prof_release(mesh);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  mesh->prof_capacity = max_stages;
+  mesh->prof_used = 0;
+  return GR_OK;
+}
+
+int gr_profile_end(gr_mesh* mesh, double* ms, int32_t* nstages) {
+  if (!mesh || !ms || !nstages) return fail(GR_EINVAL, "gr_profile_end: NULL argument");
+  DeviceGuard g(mesh->ctx->device);
+  for (int k = 0; k < GR_NKERNELS; ++k) ms[k] = 0.0;
+  *nstages = mesh->prof_used;
+  for (int s = 0; s < mesh->prof_used; ++s) {
+    cudaEvent_t* ev = &mesh->prof_events[(GR_NKERNELS + 1) * s];
+    cudaError_t e = cudaEventSynchronize(ev[GR_NKERNELS]);
+    if (e != cudaSuccess) { prof_release(mesh); return cuda_fail(e, "cudaEventSynchronize"); }
+    for (int k = 0; k < GR_NKERNELS; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      if (e != cudaSuccess) { prof_release(mesh); return cuda_fail(e, "cudaEventElapsedTime"); }
+      ms[k] += t;
+    }
+  }
+  prof_release(mesh);
+  return GR_OK;
+}
+
+int gr_mesh_destroy(gr_mesh* mesh) {
+  mesh_free(mesh);
+  return GR_OK;
+}
+
+int64_t gr_mesh_workspace_bytes(const gr_mesh* mesh) { return mesh ? mesh->ws_bytes : -1; }
+
+int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t max_ng, gr_mesh** out) {
+  (void)max_ng;
+  if (!ctx || !out) return fail(GR_EINVAL, "gr_mesh_create: NULL argument");
+  if (nblocks < 0 || (nblocks > 0 && !blocks)) return fail(GR_EINVAL, "gr_mesh_create: bad block list");
+  DeviceGuard g(ctx->device);
+  gr_mesh* m = new gr_mesh();
+  m->ctx = ctx;
+  m->nblocks = nblocks;
+  m->h_blocks.resize(nblocks);
+  long long wcell = 0, wface[3] = {0, 0, 0}, wvert = 0;
+  m->min_ng = 1 << 30;
+  for (int b = 0; b < nblocks; ++b) {
+    const gr_block& s = blocks[b];
+    DBlock& d = m->h_blocks[b];
+    if (s.ng < 1 || s.ng > 8) { mesh_free(m); return fail(GR_EINVAL, "gr_mesh_create: ng must be in [1, 8]"); }
+    for (int a = 0; a < 3; ++a) {
+      if (s.n[a] < 1 || s.n[a] > 1024) { mesh_free(m); return fail(GR_EINVAL, "gr_mesh_create: n out of range"); }
+      if (!(s.dx[a] > 0) || !std::isfinite(s.dx[a])) { mesh_free(m); return fail(GR_EINVAL, "gr_mesh_create: dx must be positive"); }
+      d.n[a] = s.n[a];
+      d.N[a] = s.n[a] + 2 * s.ng;
+      d.dx[a] = s.dx[a];
+      d.idx[a] = 1.0 / s.dx[a];
+    }
+    if (s.cell_off < 0 || s.vert_off < 0 || s.face_off[0] < 0 || s.face_off[1] < 0 || s.face_off[2] < 0) {
+      mesh_free(m);
+      return fail(GR_EINVAL, "gr_mesh_create: negative pool offset");
+    }
+    d.g = s.ng;
+    m->min_ng = std::min(m->min_ng, (int)s.ng);
+    m->max_ng = std::max(m->max_ng, (int)s.ng);
+    d.cell = s.cell_off;
+    d.vert = s.vert_off;
+    for (int a = 0; a < 3; ++a) d.face[a] = s.face_off[a];
+    const long long nc = (long long)d.N[0] * d.N[1] * d.N[2];
+    d.wcell = wcell;
+    wcell += nc;
+    for (int a = 0; a < 3; ++a) {
+      d.wface[a] = wface[a];
+      wface[a] += (long long)(d.N[0] + (a == 0)) * (d.N[1] + (a == 1)) * (d.N[2] + (a == 2));
+    }
+    d.wvert = wvert;
+    wvert += (long long)(d.N[0] + 1) * (d.N[1] + 1) * (d.N[2] + 1);
+  }
+  // work lists
+  std::vector<Work> wl[R_NREGION];
+  for (int kind = 0; kind < R_NREGION; ++kind) {
+    const int ndir = region_has_dir(kind) ? 3 : 1;
+    for (int b = 0; b < nblocks; ++b)
+      for (int dir = 0; dir < ndir; ++dir) {
+        const long long cnt = region_count(kind, dir, m->h_blocks[b]);
+        for (long long s0 = 0; s0 < cnt; s0 += kTile) wl[kind].push_back(Work{b, dir, (int)s0, 0});
+      }
+    m->nwork[kind] = (int)wl[kind].size();
+  }
+  auto dalloc = [&](size_t bytes, void** p) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) { m->allocs.push_back(*p); m->ws_bytes += (int64_t)bytes; }
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  e = dalloc(sizeof(DBlock) * std::max(1, nblocks), (void**)&m->d_blocks);
+  if (e == cudaSuccess && nblocks)
+    e = cudaMemcpy(m->d_blocks, m->h_blocks.data(), sizeof(DBlock) * nblocks, cudaMemcpyHostToDevice);
+  for (int kind = 0; kind < R_NREGION && e == cudaSuccess; ++kind) {
+    e = dalloc(sizeof(Work) * std::max<size_t>(1, wl[kind].size()), (void**)&m->d_work[kind]);
+    if (e == cudaSuccess && !wl[kind].empty())
+      e = cudaMemcpy(m->d_work[kind], wl[kind].data(), sizeof(Work) * wl[kind].size(), cudaMemcpyHostToDevice);
+  }
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+    e = dalloc(sizeof(double) * wcell, (void**)&m->ws.bcc[a]);
+    if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, (void**)&m->ws.ecc[a]);
+    if (e == cudaSuccess) e = dalloc(sizeof(double) * 7 * wface[a], &m->ws.flux[a]);
+    if (e == cudaSuccess) e = dalloc(sizeof(double) * wvert, &m->ws.edge[a]);
+    m->ws.fstride[a] = wface[a];
+  }
+  m->ws.estride = wvert;
+  if (e == cudaSuccess) e = dalloc(sizeof(double) * 8, (void**)&m->d_diag);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
+    std::string msg = std::string("gr_mesh_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    mesh_free(m);
+    return fail(code, msg);
+  }
+  *out = m;
+  return GR_OK;
+}
+
+static int check_params(const gr_params* p) {
+  if (!p) return fail(GR_EINVAL, "params is NULL");
+  if (p->size != sizeof(gr_params)) return fail(GR_EINVAL, "gr_params.size does not match this library");
+  if (p->recon != GR_RECON_PLM && p->recon != GR_RECON_WENOZ) return fail(GR_EINVAL, "bad recon");
+  if (p->precision != GR_PREC_FP64 && p->precision != GR_PREC_MIXED) return fail(GR_EINVAL, "bad precision");
+  if (p->emf != GR_EMF_UPWIND && p->emf != GR_EMF_MEAN) return fail(GR_EINVAL, "bad emf");
+  if (p->ceiling != GR_CEIL_CLAMP && p->ceiling != GR_CEIL_ATMOSPHERE) return fail(GR_EINVAL, "bad ceiling");
+  if (p->max_iter < 1 || p->max_iter > 10000) return fail(GR_EINVAL, "max_iter out of range");
+  if (!(p->gamma_ad > 1.0) || !(p->W_max >= 1.0) || !(p->M_max > 0) || !(p->tol > 0) ||
+      !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0))
+    return fail(GR_EINVAL, "physical parameter out of range");
+  return GR_OK;
+}
+
+static KParams kparams(const gr_params* p, double dt) {
+  KParams k;
+  k.recon = p->recon; k.emf = p->emf; k.ceiling = p->ceiling; k.max_iter = p->max_iter;
+  k.gamma_ad = p->gamma_ad; k.rho_atm = p->rho_atm; k.p_atm = p->p_atm; k.f_thr = p->f_thr;
+  k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
+  k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
+  k.dt = dt;
+  return k;
+}
+
+static int metric_view(const gr_metric* metric, MetricView& mv, bool need_K) {
+  if (!metric) return fail(GR_EINVAL, "metric is NULL");
+  if (metric->order != 2 && metric->order != 4) return fail(GR_EINVAL, "metric order must be 2 or 4");
+  for (int c = 0; c < 16; ++c) {
+    mv.v[c] = metric->v[c];
+    const bool needed = c < 10 || (need_K && !metric->k_zero);
+    if (needed && !mv.v[c]) return fail(GR_EINVAL, "metric component pointer is NULL");
+  }
+  mv.order = metric->order;
+  mv.k_zero = metric->k_zero;
+  return GR_OK;
+}
+
+int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+             const gr_params* params, void* stream) {
+  if (!mesh || !state) return fail(GR_EINVAL, "gr_stage: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  if (!std::isfinite(dt) || dt < 0) return fail(GR_EINVAL, "gr_stage: dt must be finite and >= 0");
+  MetricView mv;
+  if ((r = metric_view(metric, mv, true))) return r;
+  const int need = (params->recon == GR_RECON_WENOZ ? 3 : 2) + (metric->order == 4 ? 1 : 0);
+  if (mesh->nblocks > 0 && mesh->min_ng < need)
+    return fail(GR_EINVAL, "gr_stage: ghost width too small for the reconstruction / interpolation stencil");
+  StateView s;
+  for (int v = 0; v < 5; ++v) {
+    s.U[v] = state->U[v]; s.U0[v] = state->U0[v]; s.W[v] = state->W[v];
+    s.Uo[v] = state->Uo[v]; s.Wo[v] = state->Wo[v];
+    if (!s.U[v] || !s.W[v] || !s.Uo[v] || !s.Wo[v]) return fail(GR_EINVAL, "gr_stage: NULL state array");
+    if (params->rk_g0 != 0.0 && !s.U0[v]) return fail(GR_EINVAL, "gr_stage: U0 needed when rk_g0 != 0");
+  }
+  for (int d = 0; d < 3; ++d) {
+    s.B[d] = state->B[d]; s.B0[d] = state->B0[d]; s.Bo[d] = state->Bo[d];
+    if (!s.B[d] || !s.Bo[d]) return fail(GR_EINVAL, "gr_stage: NULL face array");
+    if (params->rk_g0 != 0.0 && !s.B0[d]) return fail(GR_EINVAL, "gr_stage: B0 needed when rk_g0 != 0");
+    if ((const double*)s.Bo[d] == s.B[d]) return fail(GR_EINVAL, "gr_stage: Bo must not alias B");
+  }
+  for (int v = 0; v < 5; ++v)
+    if ((const double*)s.Uo[v] == s.U[v] || (const double*)s.Wo[v] == s.W[v])
+      return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
+  s.status = state->status;
+  if (!s.status) return fail(GR_EINVAL, "gr_stage: status is NULL");
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  const Work* work[R_NREGION];
+  for (int k = 0; k < R_NREGION; ++k) work[k] = mesh->d_work[k];
+  cudaEvent_t* ev = nullptr;
+  if (mesh->prof_used < mesh->prof_capacity)
+    ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
+  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, work, mesh->nwork, mv, s, mesh->ws,
+                               kparams(params, dt), (cudaStream_t)stream, ev);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
+  return GR_OK;
+}
+
+int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5], const double* const B[3],
+                double* const U[5], const gr_params* params, void* stream) {
+  if (!mesh || !W || !B || !U) return fail(GR_EINVAL, "gr_prim2con: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  MetricView mv;
+  if ((r = metric_view(metric, mv, false))) return r;
+  for (int v = 0; v < 5; ++v)
+    if (!W[v] || !U[v]) return fail(GR_EINVAL, "gr_prim2con: NULL array");
+  for (int d = 0; d < 3; ++d)
+    if (!B[d]) return fail(GR_EINVAL, "gr_prim2con: NULL face array");
+  if (metric->order == 4 && mesh->min_ng < 1) return fail(GR_EINVAL, "gr_prim2con: order 4 needs a ghost");
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  cudaError_t e = launch_prim2con(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, W,
+                                  B, U, kparams(params, 0.0), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_prim2con launch");
+  return GR_OK;
+}
+
+int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
+                double* const W[5], uint8_t* status, const gr_params* params, void* stream) {
+  if (!mesh || !W || !B || !U) return fail(GR_EINVAL, "gr_con2prim: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  MetricView mv;
+  if ((r = metric_view(metric, mv, false))) return r;
+  for (int v = 0; v < 5; ++v)
+    if (!W[v] || !U[v]) return fail(GR_EINVAL, "gr_con2prim: NULL array");
+  for (int d = 0; d < 3; ++d)
+    if (!B[d]) return fail(GR_EINVAL, "gr_con2prim: NULL face array");
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  cudaError_t e = launch_con2prim(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U,
+                                  B, W, status, kparams(params, 0.0), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_con2prim launch");
+  return GR_OK;
+}
+
+int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4], void* stream) {
+  if (!mesh || !U || !B || !out) return fail(GR_EINVAL, "gr_diag: NULL argument");
+  if (!U[0]) return fail(GR_EINVAL, "gr_diag: NULL D array");
+  for (int d = 0; d < 3; ++d)
+    if (!B[d]) return fail(GR_EINVAL, "gr_diag: NULL face array");
+  DeviceGuard g(mesh->ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_diag(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], U, B,
+                              mesh->d_diag, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_diag launch");
+  double h[8];
+  e = cudaMemcpyAsync(h, mesh->d_diag, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_diag copy");
+  double mindx = 1e300;
+  for (const DBlock& b : mesh->h_blocks) mindx = std::min(mindx, std::min(b.dx[0], std::min(b.dx[1], b.dx[2])));
+  const double Bmax = h[3] > 0 ? h[3] : 1.0;
+  out[0] = h[0];
+  out[1] = h[1] * mindx / Bmax;
+  out[2] = (h[4] > 0) ? h[2] / (Bmax * h[4] / mindx) : 0.0;
+  out[3] = h[3];
+  return GR_OK;
+}
+
+}  // extern "C"

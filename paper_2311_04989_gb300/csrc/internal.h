@@ -1,0 +1,83 @@
+// internal.h -- declarations shared by the host side (capi.cu) and the kernels (stage_kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "grstage.h"
+
+namespace grs {
+
+constexpr int kTile = 128;   // elements per CTA work item (threads per CTA)
+
+// Device copy of one block: geometry, caller pool offsets and workspace offsets (in elements).
+struct DBlock {
+  int n[3];
+  int g;
+  int N[3];            // n + 2g
+  double dx[3];
+  double idx[3];       // 1/dx
+  long long cell, face[3], vert;         // caller pools
+  long long wcell, wface[3], wvert;      // workspace pools
+};
+
+// One CTA's slice of work: elements [start, start + kTile) of region `kind` of block `block`
+// in direction `dir` (faces, edges) or 0.
+struct Work {
+  int block;
+  int dir;
+  int start;
+  int pad;
+};
+
+enum Region { R_CELLS_ALL = 0, R_FACES = 1, R_EDGES = 2, R_CTFACES = 3, R_INTERIOR = 4, R_NREGION = 5 };
+
+// Device views of the caller's pools for one call
+struct MetricView {
+  const double* v[16];
+  int order;
+  int k_zero;
+};
+struct StateView {
+  const double* U[5];
+  const double* U0[5];
+  const double* B[3];
+  const double* B0[3];
+  const double* W[5];
+  double* Uo[5];
+  double* Bo[3];
+  double* Wo[5];
+  uint8_t* status;
+};
+// Workspace pools (owned by the mesh)
+struct Workspace {
+  double* bcc[3];      // undensitised cell-centred field calB^i (cells)
+  double* ecc[3];      // cell-centred electric field E_m (cells, rings -1..n)
+  void* flux[3];       // per direction: 7 arrays of face values (FP64 or FP32), stride fstride[d]
+  void* edge[3];       // corner electric field E_m (vertex-indexed), FP64 or FP32
+  long long fstride[3];
+  long long estride;
+};
+
+struct KParams {   // gr_params flattened for the device
+  int recon, emf, ceiling, max_iter;
+  double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
+  double rk_g0, rk_g1, rk_beta;
+  double dt;
+};
+
+// Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
+// ev: nullptr, or GR_NKERNELS + 1 events recorded before the first kernel and after each kernel
+cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
+                         const int nwork[R_NREGION], const MetricView& m, const StateView& s,
+                         const Workspace& ws, const KParams& kp, cudaStream_t st, cudaEvent_t* ev);
+cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+                            const double* const W[5], const double* const B[3], double* const U[5],
+                            const KParams& kp, cudaStream_t st);
+cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+                            double* const U[5], const double* const B[3], double* const W[5],
+                            uint8_t* status, const KParams& kp, cudaStream_t st);
+cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const double* const U[5],
+                        const double* const B[3], double* dev_out /* 4 + scratch */, cudaStream_t st);
+
+}  // namespace grs

@@ -1,0 +1,620 @@
+// physics.cuh -- device arithmetic of the GRMHD stage (arXiv:2311.04989, Sec. 2-3).
+//
+// Templated on the arithmetic type R of the reconstruction / Riemann / EMF path (double for the
+// FP64 path, float for the mixed path).  Con2prim, the sources and all accumulation are FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace grs {
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+
+template <class R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+template <class R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+
+// symmetric 3x3 packed as xx, xy, xz, yy, yz, zz
+__device__ __forceinline__ int sidx(int i, int j) {
+  // (0,0)0 (0,1)1 (0,2)2 (1,1)3 (1,2)4 (2,2)5
+  return (i <= j) ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
+}
+
+// lower an index with gamma_ij
+template <class R>
+__device__ __forceinline__ void lower3(const R g[6], const R u[3], R l[3]) {
+  l[0] = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  l[1] = g[1] * u[0] + g[3] * u[1] + g[4] * u[2];
+  l[2] = g[2] * u[0] + g[4] * u[1] + g[5] * u[2];
+}
+
+template <class R>
+__device__ __forceinline__ R det3(const R g[6]) {
+  return g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+         g[2] * (g[1] * g[4] - g[3] * g[2]);
+}
+
+// gamma^{dd} = cofactor_dd / det
+template <class R>
+__device__ __forceinline__ R inv_dd(const R g[6], int d, R det) {
+  R c;
+  if (d == 0) c = g[3] * g[5] - g[4] * g[4];
+  else if (d == 1) c = g[0] * g[5] - g[2] * g[2];
+  else c = g[0] * g[3] - g[1] * g[1];
+  return c / det;
+}
+
+// full inverse (FP64 cell path)
+__device__ __forceinline__ void inv3(const double g[6], double det, double gi[6]) {
+  const double id = 1.0 / det;
+  gi[0] = (g[3] * g[5] - g[4] * g[4]) * id;
+  gi[1] = (g[2] * g[4] - g[1] * g[5]) * id;
+  gi[2] = (g[1] * g[4] - g[2] * g[3]) * id;
+  gi[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gi[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gi[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Layout helpers (ghost-padded, x fastest)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ long long cix(const DBlock& b, int i, int j, int k) {
+  return ((long long)(k + b.g) * b.N[1] + (j + b.g)) * b.N[0] + (i + b.g);
+}
+__device__ __forceinline__ long long fix(const DBlock& b, int d, int i, int j, int k) {
+  const int sx = b.N[0] + (d == 0), sy = b.N[1] + (d == 1);
+  return ((long long)(k + b.g) * sy + (j + b.g)) * sx + (i + b.g);
+}
+__device__ __forceinline__ long long vix(const DBlock& b, int i, int j, int k) {
+  return ((long long)(k + b.g) * (b.N[1] + 1) + (j + b.g)) * (b.N[0] + 1) + (i + b.g);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Metric interpolation from vertices (Sec. 3.2): tensor-product Lagrange, order 2 or 4, at the
+// centre of a d-face (face plane = vertex plane p[d]) and at cell centres (with derivatives).
+// ------------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void face_metric(const DBlock& b, const MetricView& m, int order, int d,
+                                            const int p[3], R out[10]) {
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const long long base = b.vert;
+  if (order == 2) {
+    int q[3] = {p[0], p[1], p[2]};
+    const long long v00 = base + vix(b, q[0], q[1], q[2]);
+    q[t1] += 1;
+    const long long v10 = base + vix(b, q[0], q[1], q[2]);
+    q[t2] += 1;
+    const long long v11 = base + vix(b, q[0], q[1], q[2]);
+    q[t1] -= 1;
+    const long long v01 = base + vix(b, q[0], q[1], q[2]);
+#pragma unroll
+    for (int c = 0; c < 10; ++c) {
+      const double* a = m.v[c];
+      out[c] = R(0.25) * (R(a[v00]) + R(a[v10]) + R(a[v01]) + R(a[v11]));
+    }
+  } else {
+    const R w[4] = {R(-1.0 / 16), R(9.0 / 16), R(9.0 / 16), R(-1.0 / 16)};
+#pragma unroll
+    for (int c = 0; c < 10; ++c) out[c] = R(0);
+    for (int s2 = 0; s2 < 4; ++s2)
+      for (int s1 = 0; s1 < 4; ++s1) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[t1] += s1 - 1;
+        q[t2] += s2 - 1;
+        const long long vi = base + vix(b, q[0], q[1], q[2]);
+        const R ww = w[s1] * w[s2];
+#pragma unroll
+        for (int c = 0; c < 10; ++c) out[c] += ww * R(m.v[c][vi]);
+      }
+  }
+}
+
+// Cell-centre value of components [0, nc) and, if dv != nullptr, derivatives d_k of components
+// [0, 10) (alpha, beta, gamma).  The derivative along k is written as vertex differences so that it
+// vanishes exactly on a constant field.
+__device__ __forceinline__ void cell_metric(const DBlock& b, const MetricView& m, int order, int i,
+                                            int j, int k, int nc, double* val, double (*dv)[10]) {
+  const long long base = b.vert;
+  if (order == 2) {
+    long long v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = base + vix(b, i + (t & 1), j + ((t >> 1) & 1), k + (t >> 2));
+    for (int c = 0; c < nc; ++c) {
+      const double* a = m.v[c];
+      double f[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) f[t] = a[v[t]];
+      val[c] = 0.125 * (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])));
+      if (dv && c < 10) {
+        dv[0][c] = 0.25 * (((f[1] - f[0]) + (f[3] - f[2])) + ((f[5] - f[4]) + (f[7] - f[6]))) * b.idx[0];
+        dv[1][c] = 0.25 * (((f[2] - f[0]) + (f[3] - f[1])) + ((f[6] - f[4]) + (f[7] - f[5]))) * b.idx[1];
+        dv[2][c] = 0.25 * (((f[4] - f[0]) + (f[5] - f[1])) + ((f[6] - f[2]) + (f[7] - f[3]))) * b.idx[2];
+      }
+    }
+  } else {
+    const double w[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
+    for (int c = 0; c < nc; ++c) {
+      const double* a = m.v[c];
+      double s = 0, d0 = 0;
+      for (int kk = 0; kk < 4; ++kk)
+        for (int jj = 0; jj < 4; ++jj) {
+          const long long r = base + vix(b, i - 1, j - 1 + jj, k - 1 + kk);
+          const double f0 = a[r], f1 = a[r + 1], f2 = a[r + 2], f3 = a[r + 3];
+          const double wjk = w[jj] * w[kk];
+          s += wjk * (w[0] * f0 + w[1] * f1 + w[2] * f2 + w[3] * f3);
+          if (dv && c < 10) d0 += wjk * (27.0 * (f2 - f1) - (f3 - f0));
+        }
+      val[c] = s;
+      if (dv && c < 10) {
+        dv[0][c] = d0 / (24.0 * b.dx[0]);
+        // y and z derivatives: differences along the axis, interpolation across
+        for (int ax = 1; ax < 3; ++ax) {
+          double acc = 0;
+          for (int u = 0; u < 4; ++u)
+            for (int t = 0; t < 4; ++t) {
+              auto at = [&](int s4) {
+                int q[3] = {i - 1 + t, j - 1 + (ax == 2 ? u : 0), k - 1 + (ax == 1 ? u : 0)};
+                q[ax] = (ax == 1 ? j : k) - 1 + s4;
+                return a[base + vix(b, q[0], q[1], q[2])];
+              };
+              acc += w[t] * w[u] * (27.0 * (at(2) - at(1)) - (at(3) - at(0)));
+            }
+          dv[ax][c] = acc / (24.0 * b.dx[ax]);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Reconstruction (Sec. 3.4): van Leer PLM and WENOZ (Borges et al.).
+// s[0..5] = cells f-3 .. f+2 around the face f (between s[2] and s[3]).
+// ------------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R vl_slope(R wm, R w0, R wp) {
+  const R dL = w0 - wm, dR = wp - w0;
+  const R pr = dL * dR;
+  return pr > R(0) ? R(2) * pr / (dL + dR) : R(0);
+}
+
+template <class R>
+__device__ __forceinline__ R wenoz(R v0, R v1, R v2, R v3, R v4, R eps) {
+  const R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * R(1.0 / 6.0);
+  const R q1 = (-v1 + R(5) * v2 + R(2) * v3) * R(1.0 / 6.0);
+  const R q2 = (R(2) * v2 + R(5) * v3 - v4) * R(1.0 / 6.0);
+  const R a0 = v0 - R(2) * v1 + v2, c0 = v0 - R(4) * v1 + R(3) * v2;
+  const R a1 = v1 - R(2) * v2 + v3, c1 = v1 - v3;
+  const R a2 = v2 - R(2) * v3 + v4, c2 = R(3) * v2 - R(4) * v3 + v4;
+  const R b0 = R(13.0 / 12.0) * a0 * a0 + R(0.25) * c0 * c0;
+  const R b1 = R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
+  const R b2 = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
+  const R t5 = rabs(b0 - b2);
+  const R w0 = R(0.1) * (R(1) + t5 / (b0 + eps));
+  const R w1 = R(0.6) * (R(1) + t5 / (b1 + eps));
+  const R w2 = R(0.3) * (R(1) + t5 / (b2 + eps));
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+// FP32: the stencil is scaled by a power of two near its largest magnitude before the smoothness
+// indicators are formed, so that squares of tiny densities/pressures (atmosphere p ~ 1e-30) do not
+// underflow; the scaling is exact and is undone on the result.
+__device__ __forceinline__ float pow2_scale(float m) {
+  // 2^(-e) with m in [2^e, 2^(e+1)); m > 0 and finite
+  int e;
+  frexpf(m, &e);
+  return ldexpf(1.0f, -e);
+}
+
+template <class R>
+__device__ __forceinline__ void recon(int method, const R s[6], R eps, R* L, R* Rr);
+
+template <>
+__device__ __forceinline__ void recon<double>(int method, const double s[6], double eps, double* L,
+                                              double* Rr) {
+  if (method == GR_RECON_PLM) {
+    *L = s[2] + 0.5 * vl_slope(s[1], s[2], s[3]);
+    *Rr = s[3] - 0.5 * vl_slope(s[2], s[3], s[4]);
+  } else {
+    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
+    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+  }
+}
+
+template <>
+__device__ __forceinline__ void recon<float>(int method, const float s[6], float eps, float* L, float* Rr) {
+  if (method == GR_RECON_PLM) {
+    *L = s[2] + 0.5f * vl_slope(s[1], s[2], s[3]);
+    *Rr = s[3] - 0.5f * vl_slope(s[2], s[3], s[4]);
+  } else {
+    float mx = 0.f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) mx = fmaxf(mx, fabsf(s[t]));
+    if (!(mx > 0.f) || !(mx < 3e38f)) {   // all zero (or non-finite): nothing to scale
+      *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
+      *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+      return;
+    }
+    const float sc = pow2_scale(mx), isc = 1.0f / sc;
+    float t[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) t[u] = s[u] * sc;
+    *L = wenoz(t[0], t[1], t[2], t[3], t[4], eps) * isc;
+    *Rr = wenoz(t[5], t[4], t[3], t[2], t[1], eps) * isc;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// One side of a face: conserved U (D, S_j, tau, B^{t1}, B^{t2}), flux F^d of Eq. fluxB_def and
+// fast speeds (lam-, lam+) (Sec. 2.2, approximate quadratic dispersion relation).
+//   met: alpha, beta^i, gamma_ij at the face; sg = sqrt(gamma); gdd = gamma^{dd}
+//   w: (rho, u~^i, p); Bd: densitised B^i at the face state.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, R gam, const R w[5],
+                                           const R Bd[3], R U[7], R F[7], R* lm, R* lp) {
+  const R alpha = met[0];
+  const R* beta = met + 1;
+  const R* g = met + 4;
+  const R rho = w[0], p = w[4];
+  const R ut[3] = {w[1], w[2], w[3]};
+  R utl[3];
+  lower3(g, ut, utl);
+  const R W = rsqrt_(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R iW = R(1) / W;
+  const R ia = R(1) / alpha;
+  const R isg = R(1) / sg;
+  R v[3], vl[3], vt[3], Bu[3], Bl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    v[i] = ut[i] * iW;
+    vl[i] = utl[i] * iW;
+    vt[i] = v[i] - beta[i] * ia;
+    Bu[i] = Bd[i] * isg;
+  }
+  lower3(g, Bu, Bl);
+  const R Bv = Bu[0] * vl[0] + Bu[1] * vl[1] + Bu[2] * vl[2];
+  const R BB = Bu[0] * Bl[0] + Bu[1] * Bl[1] + Bu[2] * Bl[2];
+  const R ab0 = W * Bv;                          // alpha b^0
+  const R b2 = (ab0 * ab0 + BB) * iW * iW;       // b^2
+  R bl[3];                                       // b_i = calB_i / W + alpha b^0 v_i
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
+  const R rhoh = rho + gam / (gam - R(1)) * p;   // rho h for p = (Gamma-1) rho eps
+  const R e = rhoh + b2;
+  const R pt = p + R(0.5) * b2;
+  // Eq. consB_def
+  U[0] = sg * rho * W;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) U[1 + j] = sg * (e * W * utl[j] - ab0 * bl[j]);
+  U[4] = sg * (e * W * W - rho * W - pt - ab0 * ab0);
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  U[5] = Bd[t1];
+  U[6] = Bd[t2];
+  // Eq. fluxB_def
+  const R avd = alpha * vt[d];
+  const R asg = alpha * sg;
+  const R BdW = Bu[d] * iW;
+  F[0] = U[0] * avd;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) F[1 + j] = U[1 + j] * avd - asg * bl[j] * BdW;
+  F[1 + d] += pt * asg;
+  F[4] = U[4] * avd + asg * (pt * v[d] - ab0 * BdW);
+  F[5] = alpha * (Bd[t1] * vt[d] - Bd[d] * vt[t1]);
+  F[6] = alpha * (Bd[t2] * vt[d] - Bd[d] * vt[t2]);
+  // fast speeds
+  const R cs2 = gam * p / rhoh;
+  const R ca2 = b2 / e;
+  const R c2 = cs2 + ca2 - cs2 * ca2;
+  const R v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
+  R disc = (R(1) - v2) * (gdd * (R(1) - v2 * c2) - v[d] * v[d] * (R(1) - c2));
+  disc = disc > R(0) ? disc : R(0);
+  const R cr = rsqrt_(c2) * rsqrt_(disc);
+  const R iden = R(1) / (R(1) - v2 * c2);
+  const R vc = v[d] * (R(1) - c2);
+  *lp = alpha * (vc + cr) * iden - beta[d];
+  *lm = alpha * (vc - cr) * iden - beta[d];
+}
+
+// HLLE (lam+ = max(0, ...), lam- = min(0, ...); equal speeds give the mean flux)
+template <class R>
+__device__ __forceinline__ void hlle(const R UL[7], const R UR[7], const R FL[7], const R FR[7], R lmL,
+                                     R lpL, R lmR, R lpR, R out[7]) {
+  const R lp = rmax(R(0), rmax(lpL, lpR));
+  const R lm = rmin(R(0), rmin(lmL, lmR));
+  const R den = lp - lm;
+  if (den == R(0)) {
+#pragma unroll
+    for (int v = 0; v < 7; ++v) out[v] = R(0.5) * (FL[v] + FR[v]);
+    return;
+  }
+  const R iden = R(1) / den;
+  const R lpm = lp * lm;
+#pragma unroll
+  for (int v = 0; v < 7; ++v) out[v] = (lp * FL[v] - lm * FR[v] + lpm * (UR[v] - UL[v])) * iden;
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 cell physics: prim -> cons, stress tensor and sources (Eq. EMT_MHD, Eq. hydsrc_def)
+// ------------------------------------------------------------------------------------------------
+struct CellMet {
+  double alpha, beta[3], g[6], K[6], gi[6], sg;
+};
+
+__device__ __forceinline__ void cellmet_from(const double val[16], bool kzero, CellMet& M) {
+  M.alpha = val[0];
+  for (int i = 0; i < 3; ++i) M.beta[i] = val[1 + i];
+  for (int c = 0; c < 6; ++c) {
+    M.g[c] = val[4 + c];
+    M.K[c] = kzero ? 0.0 : val[10 + c];
+  }
+  const double det = det3(M.g);
+  M.sg = sqrt(det);
+  inv3(M.g, det, M.gi);
+}
+
+struct CellFluid {
+  double rho, p, W, rhoh, b2, ab0;
+  double ut[3], utl[3], v[3], vl[3], vt[3];
+  double Bu[3], bl[3];
+};
+
+__device__ __forceinline__ void cell_fluid(const CellMet& M, double gam, const double w[5],
+                                           const double Bd[3], CellFluid& f) {
+  f.rho = w[0];
+  f.p = w[4];
+  for (int i = 0; i < 3; ++i) f.ut[i] = w[1 + i];
+  lower3(M.g, f.ut, f.utl);
+  f.W = sqrt(1.0 + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
+  const double iW = 1.0 / f.W, ia = 1.0 / M.alpha, isg = 1.0 / M.sg;
+  for (int i = 0; i < 3; ++i) {
+    f.v[i] = f.ut[i] * iW;
+    f.vl[i] = f.utl[i] * iW;
+    f.vt[i] = f.v[i] - M.beta[i] * ia;
+    f.Bu[i] = Bd[i] * isg;
+  }
+  double Bl[3];
+  lower3(M.g, f.Bu, Bl);
+  const double Bv = f.Bu[0] * f.vl[0] + f.Bu[1] * f.vl[1] + f.Bu[2] * f.vl[2];
+  const double BB = f.Bu[0] * Bl[0] + f.Bu[1] * Bl[1] + f.Bu[2] * Bl[2];
+  f.ab0 = f.W * Bv;
+  f.b2 = (f.ab0 * f.ab0 + BB) * iW * iW;
+  for (int i = 0; i < 3; ++i) f.bl[i] = Bl[i] * iW + f.ab0 * f.vl[i];
+  f.rhoh = f.rho + gam / (gam - 1.0) * f.p;
+}
+
+__device__ __forceinline__ void cell_cons(const CellMet& M, const CellFluid& f, double q[5]) {
+  const double e = f.rhoh + f.b2, pt = f.p + 0.5 * f.b2;
+  q[0] = M.sg * f.rho * f.W;
+  for (int j = 0; j < 3; ++j) q[1 + j] = M.sg * (e * f.W * f.utl[j] - f.ab0 * f.bl[j]);
+  q[4] = M.sg * (e * f.W * f.W - f.rho * f.W - pt - f.ab0 * f.ab0);
+}
+
+// Eq. hydsrc_def; dm[k][c] = d_k of alpha (c=0), beta^i (1..3), gamma_ij (4..9)
+__device__ __forceinline__ void cell_sources(const CellMet& M, const CellFluid& f, const double dm[3][10],
+                                             bool kzero, double s[5]) {
+  const double a = M.alpha, ia2 = 1.0 / (a * a);
+  // u^mu, b^mu
+  double u[4], b[4];
+  u[0] = f.W / a;
+  for (int i = 0; i < 3; ++i) u[1 + i] = f.W * f.vt[i];
+  b[0] = f.ab0 / a;
+  for (int i = 0; i < 3; ++i) b[1 + i] = f.Bu[i] / f.W + f.ab0 * f.vt[i];
+  const double e = f.rhoh + f.b2, pt = f.p + 0.5 * f.b2;
+  // T^{mu nu} = e u u + pt g^{mu nu} - b b, with g^{00} = -1/a^2, g^{0i} = beta^i/a^2,
+  // g^{ij} = gamma^{ij} - beta^i beta^j / a^2
+  const double T00 = e * u[0] * u[0] - pt * ia2 - b[0] * b[0];
+  double T0i[3], Tij[6];
+  for (int i = 0; i < 3; ++i) T0i[i] = e * u[0] * u[1 + i] + pt * M.beta[i] * ia2 - b[0] * b[1 + i];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      const int c = sidx(i, j);
+      Tij[c] = e * u[1 + i] * u[1 + j] + pt * (M.gi[c] - M.beta[i] * M.beta[j] * ia2) - b[1 + i] * b[1 + j];
+    }
+  // T^0_i = T^{00} beta_i + T^{0j} gamma_ji
+  double betal[3], T0l[3];
+  lower3(M.g, M.beta, betal);
+  lower3(M.g, T0i, T0l);
+  for (int i = 0; i < 3; ++i) T0l[i] += T00 * betal[i];
+  const double asg = a * M.sg;
+  s[0] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double* dg = dm[k] + 4;
+    double bbdg = 0, T0bdg = 0, Tdg = 0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const double dgij = dg[sidx(i, j)];
+        bbdg += M.beta[i] * M.beta[j] * dgij;
+        T0bdg += T0i[i] * M.beta[j] * dgij;
+        Tdg += Tij[sidx(i, j)] * dgij;
+      }
+    const double Tdb = T0l[0] * dm[k][1] + T0l[1] * dm[k][2] + T0l[2] * dm[k][3];
+    s[1 + k] = asg * (T00 * (0.5 * bbdg - a * dm[k][0]) + T0bdg + Tdb + 0.5 * Tdg);
+  }
+  double st = 0;
+  for (int i = 0; i < 3; ++i) st -= (T00 * M.beta[i] + T0i[i]) * dm[i][0];
+  if (!kzero) {
+    double bKb = 0, TK = 0;
+    for (int i = 0; i < 3; ++i) {
+      double bK = 0;
+      for (int j = 0; j < 3; ++j) {
+        const double Kij = M.K[sidx(i, j)];
+        bK += M.beta[j] * Kij;
+        TK += Tij[sidx(i, j)] * Kij;
+      }
+      bKb += M.beta[i] * bK;
+      st += 2.0 * T0i[i] * bK;
+    }
+    st += T00 * bKb + TK;
+  }
+  s[4] = asg * st;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Con2prim (Sec. 3.5, App. A): KKC master function in mu = 1/(hW), Illinois bracketing.
+// ------------------------------------------------------------------------------------------------
+struct C2PInv {
+  double D, q, r2, b2, rb;
+};
+struct C2PVal {
+  double x, rbar2, v2, W, rho, eps, f;
+  bool vcap, eclamp;
+};
+
+__device__ __forceinline__ void c2p_master(const KParams& P, const C2PInv& I, double mu, C2PVal& E) {
+  const double vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
+  E.x = 1.0 / (1.0 + mu * I.b2);
+  E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (1.0 + E.x) * I.rb * I.rb;
+  const double qbar = I.q - 0.5 * I.b2 - 0.5 * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
+  E.v2 = mu * mu * E.rbar2;
+  E.vcap = E.v2 > vmax2;
+  if (E.vcap) E.v2 = vmax2;
+  E.W = 1.0 / sqrt(1.0 - E.v2);
+  E.rho = I.D / E.W;
+  const double qm = qbar - mu * E.rbar2;
+  E.eps = E.W * qm + E.v2 * E.W * E.W / (1.0 + E.W);
+  E.eclamp = E.eps < 0.0;
+  if (E.eclamp) E.eps = 0.0;
+  // ideal gas: a = p/(rho(1+eps)) = (Gamma-1) eps/(1+eps)
+  const double ah = (P.gamma_ad - 1.0) * E.eps / (1.0 + E.eps);
+  const double nuA = (1.0 + ah) * (1.0 + E.eps) / E.W;
+  const double nuB = (1.0 + ah) * (1.0 + qm);
+  const double nu = nuA > nuB ? nuA : nuB;
+  E.f = mu - 1.0 / (nu + mu * E.rbar2);
+}
+
+__device__ __forceinline__ double c2p_aux(const C2PInv& I, double mu) {
+  const double x = 1.0 / (1.0 + mu * I.b2);
+  const double rbar2 = x * x * I.r2 + mu * x * (1.0 + x) * I.rb * I.rb;
+  return mu * sqrt(1.0 + rbar2) - 1.0;
+}
+
+// Illinois on [a,b] (f(a) < 0 < f(b) or reverse).  Returns 0 (root), -1 (no sign change), -2 (cap).
+template <class Fn>
+__device__ __forceinline__ int illinois(Fn f, double a, double b, double fa, double fb, double tol,
+                                        int max_iter, double* root, double* hi_out, int* iters) {
+  *iters = 0;
+  if (fa == 0.0) { *root = a; *hi_out = a; return 0; }
+  if (fb == 0.0) { *root = b; *hi_out = b; return 0; }
+  if ((fa < 0.0) == (fb < 0.0)) return -1;
+  int side = 0;
+  for (int it = 1; it <= max_iter; ++it) {
+    double c = (a * fb - b * fa) / (fb - fa);
+    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    if (!(c > a && c < b)) { *root = c; *hi_out = b; *iters = it; return 0; }
+    const double fc = f(c);
+    *iters = it;
+    if (fc == 0.0) { *root = c; *hi_out = c; return 0; }
+    if ((fc < 0.0) == (fa < 0.0)) {
+      a = c; fa = fc;
+      if (side == -1) fb *= 0.5;
+      side = -1;
+    } else {
+      b = c; fb = fc;
+      if (side == +1) fa *= 0.5;
+      side = +1;
+    }
+    if (b - a <= tol * c) { *root = c; *hi_out = b; return 0; }
+  }
+  *hi_out = b;
+  return -2;
+}
+
+// Full con2prim of one cell.  q: densitised conserved (in/out), Bd: densitised cell field.
+__device__ __forceinline__ int con2prim_cell(const CellMet& M, const KParams& P, double q[5],
+                                             const double Bd[3], double w[5], int* iters) {
+  int st = 0;
+  *iters = 0;
+  const double isg = 1.0 / M.sg;
+  double D = q[0] * isg, tau = q[4] * isg, S[3], Bu[3];
+  bool finite = isfinite(D) && isfinite(tau);
+  for (int i = 0; i < 3; ++i) {
+    S[i] = q[1 + i] * isg;
+    Bu[i] = Bd[i] * isg;
+    finite = finite && isfinite(S[i]) && isfinite(Bu[i]);
+  }
+  // atmosphere threshold; values within 1e-12 relative of it count as having reached it
+  const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-12);
+  bool atm = false;
+  if (!finite) { st |= GR_ST_FAILED; atm = true; }
+  else if (D < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
+  if (!atm) {
+    double Bl[3];
+    lower3(M.g, Bu, Bl);
+    const double BB = Bu[0] * Bl[0] + Bu[1] * Bl[1] + Bu[2] * Bl[2];
+    bool qmod = false;
+    if (BB > P.M_max * D) { D = BB / P.M_max; st |= GR_ST_BD_LIMIT; qmod = true; }
+    const double tau_min = 0.5 * BB;
+    if (tau < tau_min) { tau = tau_min; st |= GR_ST_TAU_FLOOR; qmod = true; }
+    C2PInv I;
+    I.D = D;
+    const double iD = 1.0 / D;
+    I.q = tau * iD;
+    double rl[3], ru[3], bu[3];
+    const double isD = 1.0 / sqrt(D);
+    for (int i = 0; i < 3; ++i) { rl[i] = S[i] * iD; bu[i] = Bu[i] * isD; }
+    ru[0] = M.gi[0] * rl[0] + M.gi[1] * rl[1] + M.gi[2] * rl[2];
+    ru[1] = M.gi[1] * rl[0] + M.gi[3] * rl[1] + M.gi[4] * rl[2];
+    ru[2] = M.gi[2] * rl[0] + M.gi[4] * rl[1] + M.gi[5] * rl[2];
+    I.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
+    I.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
+    I.b2 = BB * iD;
+    // upper bracket from the auxiliary function on (0, 1]
+    double mup = 1.0, root, hi;
+    int it_aux;
+    {
+      const double f1 = c2p_aux(I, 1.0);
+      if (f1 > 0.0) {
+        auto fa = [&](double mu) { return c2p_aux(I, mu); };
+        if (illinois(fa, 0.0, 1.0, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+      }
+    }
+    C2PVal E;
+    auto fm = [&](double mu) { c2p_master(P, I, mu, E); return E.f; };
+    const double f0 = fm(0.0);
+    double fp = fm(mup);
+    if ((f0 < 0.0) == (fp < 0.0) && mup < 1.0) { mup = 1.0; fp = fm(mup); }
+    const int r = illinois(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, iters);
+    if (r != 0) {
+      st |= GR_ST_FAILED;
+      atm = true;
+    } else {
+      const double mu = root;
+      c2p_master(P, I, mu, E);
+      double vu[3];
+      for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);
+      if (E.vcap) {
+        st |= GR_ST_W_CLAMPED;
+        const double s = sqrt(E.v2 / (mu * mu * E.rbar2));
+        for (int i = 0; i < 3; ++i) vu[i] *= s;
+        if (P.ceiling == GR_CEIL_ATMOSPHERE) atm = true;
+      }
+      if (E.eclamp) st |= GR_ST_EOS_CLAMP;
+      if (E.rho < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
+      if (!atm) {
+        w[0] = E.rho;
+        for (int i = 0; i < 3; ++i) w[1 + i] = E.W * vu[i];
+        w[4] = (P.gamma_ad - 1.0) * E.rho * E.eps;
+        if (qmod) { q[0] = M.sg * D; q[4] = M.sg * tau; }
+      }
+    }
+  }
+  if (atm) {
+    w[0] = P.rho_atm;
+    w[1] = w[2] = w[3] = 0.0;
+    w[4] = P.p_atm;
+    CellFluid f;
+    cell_fluid(M, P.gamma_ad, w, Bd, f);
+    cell_cons(M, f, q);
+  }
+  return st;
+}
+
+}  // namespace grs

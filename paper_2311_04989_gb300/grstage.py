@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libgrstage.so (include/grstage.h), same names as the C ABI.
+
+Argument marshalling only: every step of the stage runs in the library's CUDA kernels.  PyTorch
+supplies device memory and streams.  Importing works without a GPU; calling a ``gr_*`` function
+loads the library and raises ``GrstageError`` if it is missing or a call fails -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgrstage.so")
+
+GR_OK, GR_EINVAL, GR_ECUDA, GR_ENOMEM, GR_ETIMEOUT, GR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+GR_RECON_PLM, GR_RECON_WENOZ = 0, 1
+GR_PREC_FP64, GR_PREC_MIXED = 0, 1
+GR_EMF_UPWIND, GR_EMF_MEAN = 0, 1
+GR_CEIL_CLAMP, GR_CEIL_ATMOSPHERE = 0, 1
+GR_ST_ATM_THRESHOLD, GR_ST_FAILED, GR_ST_W_CLAMPED = 0x01, 0x02, 0x04
+GR_ST_TAU_FLOOR, GR_ST_BD_LIMIT, GR_ST_EOS_CLAMP = 0x08, 0x10, 0x20
+
+# every symbol include/grstage.h declares
+EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default", "gr_context_create",
+           "gr_context_destroy", "gr_mesh_create", "gr_mesh_destroy", "gr_mesh_workspace_bytes",
+           "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end"]
+GR_NKERNELS = 5
+KERNEL_NAMES = ["k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
+
+
+class GrstageError(RuntimeError):
+    pass
+
+
+class gr_block(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("ng", C.c_int32), ("dx", C.c_double * 3),
+                ("cell_off", C.c_int64), ("face_off", C.c_int64 * 3), ("vert_off", C.c_int64)]
+
+
+class gr_metric(C.Structure):
+    _fields_ = [("v", C.c_void_p * 16), ("order", C.c_int32), ("k_zero", C.c_int32)]
+
+
+class gr_state(C.Structure):
+    _fields_ = [("U", C.c_void_p * 5), ("U0", C.c_void_p * 5), ("B", C.c_void_p * 3), ("B0", C.c_void_p * 3),
+                ("W", C.c_void_p * 5), ("Uo", C.c_void_p * 5), ("Bo", C.c_void_p * 3), ("Wo", C.c_void_p * 5),
+                ("status", C.c_void_p)]
+
+
+class gr_params(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("recon", C.c_int32), ("precision", C.c_int32), ("emf", C.c_int32),
+                ("ceiling", C.c_int32), ("max_iter", C.c_int32), ("gamma_ad", C.c_double),
+                ("rho_atm", C.c_double), ("p_atm", C.c_double), ("f_thr", C.c_double), ("W_max", C.c_double),
+                ("M_max", C.c_double), ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
+                ("rk_g1", C.c_double), ("rk_beta", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgrstage.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise GrstageError(f"libgrstage.so not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, i32 = C.c_void_p, C.c_int32
+    L.gr_strerror.restype = C.c_char_p
+    L.gr_strerror.argtypes = [C.c_int]
+    L.gr_last_error.restype = C.c_char_p
+    L.gr_abi_version.restype = C.c_int
+    L.gr_params_default.argtypes = [C.POINTER(gr_params)]
+    L.gr_context_create.argtypes = [C.POINTER(vp), C.c_int]
+    L.gr_context_destroy.argtypes = [vp]
+    L.gr_mesh_create.argtypes = [vp, C.POINTER(gr_block), i32, i32, C.POINTER(vp)]
+    L.gr_mesh_destroy.argtypes = [vp]
+    L.gr_mesh_workspace_bytes.argtypes = [vp]
+    L.gr_mesh_workspace_bytes.restype = C.c_int64
+    L.gr_stage.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params), vp]
+    L.gr_prim2con.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5,
+                              C.POINTER(gr_params), vp]
+    L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5, vp,
+                              C.POINTER(gr_params), vp]
+    L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
+    L.gr_profile_begin.argtypes = [vp, i32]
+    L.gr_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
+    for f in EXPORTS:
+        if not hasattr(L, f):
+            raise GrstageError(f"libgrstage.so lacks {f}")
+    if L.gr_abi_version() != 1:
+        raise GrstageError("libgrstage.so ABI version mismatch")
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != GR_OK:
+        L = load()
+        raise GrstageError(f"{what}: {L.gr_strerror(rc).decode()} ({L.gr_last_error().decode()})")
+
+
+def gr_params_default(**kw) -> gr_params:
+    p = gr_params()
+    load().gr_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def gr_context_create(device: int = 0):
+    h = C.c_void_p()
+    _check(load().gr_context_create(C.byref(h), device), "gr_context_create")
+    return h
+
+
+def gr_context_destroy(ctx):
+    load().gr_context_destroy(ctx)
+
+
+def gr_mesh_create(ctx, blocks: list[gr_block]):
+    arr = (gr_block * max(1, len(blocks)))(*blocks)
+    h = C.c_void_p()
+    _check(load().gr_mesh_create(ctx, arr, len(blocks), 0, C.byref(h)), "gr_mesh_create")
+    return h
+
+
+def gr_mesh_destroy(mesh):
+    load().gr_mesh_destroy(mesh)
+
+
+def gr_mesh_workspace_bytes(mesh) -> int:
+    return int(load().gr_mesh_workspace_bytes(mesh))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def gr_stage(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_params, stream=None):
+    _check(load().gr_stage(mesh, C.byref(metric), C.byref(state), float(dt), C.byref(params), _stream(stream)),
+           "gr_stage")
+
+
+def _ptrs(n, ts):
+    return (C.c_void_p * n)(*[int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t) for t in ts])
+
+
+def gr_prim2con(mesh, metric: gr_metric, W, B, U, params: gr_params, stream=None):
+    _check(load().gr_prim2con(mesh, C.byref(metric), _ptrs(5, W), _ptrs(3, B), _ptrs(5, U), C.byref(params),
+                              _stream(stream)), "gr_prim2con")
+
+
+def gr_con2prim(mesh, metric: gr_metric, U, B, W, status, params: gr_params, stream=None):
+    st = int(status.data_ptr()) if status is not None else 0
+    _check(load().gr_con2prim(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), _ptrs(5, W), st,
+                              C.byref(params), _stream(stream)), "gr_con2prim")
+
+
+def gr_diag(mesh, U, B, stream=None):
+    out = (C.c_double * 4)()
+    _check(load().gr_diag(mesh, _ptrs(5, U), _ptrs(3, B), out, _stream(stream)), "gr_diag")
+    return list(out)
+
+
+def gr_profile_begin(mesh, max_stages: int):
+    _check(load().gr_profile_begin(mesh, int(max_stages)), "gr_profile_begin")
+
+
+def gr_profile_end(mesh):
+    """Returns (ms per kernel summed over the profiled stages, number of stages)."""
+    ms = (C.c_double * GR_NKERNELS)()
+    n = C.c_int32()
+    _check(load().gr_profile_end(mesh, ms, C.byref(n)), "gr_profile_end")
+    return list(ms), int(n.value)
+
+
+# ---------------------------------------------------------------------------------------------
+# pool packing (device memory layout of a batch of blocks)
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class Layout:
+    """Element offsets of every block in the cell / face / vertex pools."""
+    n: list
+    ng: list
+    dx: list
+    cell_off: np.ndarray
+    face_off: np.ndarray   # (nb, 3)
+    vert_off: np.ndarray
+    ncell: int
+    nface: tuple
+    nvert: int
+
+    @staticmethod
+    def of(blocks, align: int = 32):
+        """blocks: iterable of objects with .n (3-tuple), .ng, .dx.  Offsets are rounded up to
+        ``align`` elements (256 B for FP64) so every block starts on an aligned address."""
+        n, ng, dx = [], [], []
+        co, fo, vo = [], [], []
+        c = 0; f = [0, 0, 0]; v = 0
+        up = lambda x: (x + align - 1) // align * align
+        for b in blocks:
+            N = [b.n[a] + 2 * b.ng for a in range(3)]
+            n.append(tuple(b.n)); ng.append(b.ng); dx.append(tuple(b.dx))
+            co.append(c); c = up(c + N[0] * N[1] * N[2])
+            fo.append(tuple(f))
+            for a in range(3):
+                f[a] = up(f[a] + (N[0] + (a == 0)) * (N[1] + (a == 1)) * (N[2] + (a == 2)))
+            vo.append(v); v = up(v + (N[0] + 1) * (N[1] + 1) * (N[2] + 1))
+        return Layout(n, ng, dx, np.array(co, np.int64), np.array(fo, np.int64).reshape(-1, 3),
+                      np.array(vo, np.int64), c, tuple(f), v)
+
+    def descriptors(self) -> list[gr_block]:
+        out = []
+        for b in range(len(self.n)):
+            out.append(gr_block((C.c_int32 * 3)(*self.n[b]), self.ng[b], (C.c_double * 3)(*self.dx[b]),
+                                int(self.cell_off[b]), (C.c_int64 * 3)(*[int(x) for x in self.face_off[b]]),
+                                int(self.vert_off[b])))
+        return out
+
+    def interior_cells(self) -> int:
+        return int(sum(n[0] * n[1] * n[2] for n in self.n))
+
+
+def metric_struct(metric_pool, order: int = 2, k_zero: bool = True) -> gr_metric:
+    """metric_pool: (16, nvert) device tensor."""
+    m = gr_metric()
+    for c in range(16):
+        m.v[c] = int(metric_pool[c].data_ptr())
+    m.order = order
+    m.k_zero = 1 if k_zero else 0
+    return m
+
+
+def state_struct(U, U0, B, B0, W, Uo, Bo, Wo, status) -> gr_state:
+    s = gr_state()
+    for v in range(5):
+        s.U[v] = int(U[v].data_ptr())
+        s.U0[v] = int(U0[v].data_ptr()) if U0 is not None else 0
+        s.W[v] = int(W[v].data_ptr())
+        s.Uo[v] = int(Uo[v].data_ptr())
+        s.Wo[v] = int(Wo[v].data_ptr())
+    for d in range(3):
+        s.B[d] = int(B[d].data_ptr())
+        s.B0[d] = int(B0[d].data_ptr()) if B0 is not None else 0
+        s.Bo[d] = int(Bo[d].data_ptr())
+    s.status = int(status.data_ptr())
+    return s

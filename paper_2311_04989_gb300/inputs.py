@@ -361,3 +361,148 @@ def amr_like_batch(nblocks=1024, sizes=(16, 24, 32), g=3, seed=3, L=1.0, levels=
         x0 = tuple(rng.uniform(0, L - n * dxb, 3))
         blocks.append(random_block((n, n, n), g, x0, (dxb,) * 3, seed=seed, L=L, fields=fields, **kw))
     return blocks
+
+
+# ---------------------------------------------------------------------------------------------
+# full-stage throughput workload: two static stars in a superposed metric, nb^3 blocks of n^3
+# ---------------------------------------------------------------------------------------------
+class _Geom:
+    def __init__(self, n, ng, dx):
+        self.n, self.ng, self.dx = n, ng, dx
+
+
+class BinaryStarMesh:
+    """Two Gamma = 2, K = 100 TOV stars (rho_c = 1e-3) at x = +-sep/2 on [-L/2, L/2]^3, cut into
+    nb^3 blocks of n^3 cells with ng ghosts.  Metric: conformally flat superposition (beta = 0,
+    K_ij = 0); field: the poloidal vector potential of Eq. Apotential about each star, scaled so
+    that max b^2 / max rho = b2_over_rho; atmosphere f_atm rho_max.  Fields are evaluated once on
+    the global ghost-extended grid and sliced per block."""
+
+    def __init__(self, nb=16, n=16, ng=3, L=64.0, rho_c=1e-3, sep=40.0, b2_over_rho=1e-2, f_atm=1e-13,
+                 K=100.0, Gamma=2.0):
+        self.nb, self.n, self.ng, self.L = nb, n, ng, L
+        self.dx = L / (nb * n)
+        self.tov = solve_tov(rho_c=rho_c, K=K, Gamma=Gamma)
+        self.rho_max = rho_c
+        self.rho_atm = f_atm * rho_c
+        self.p_atm = K * self.rho_atm ** Gamma
+        self.K, self.Gamma = K, Gamma
+        centres = ((-sep / 2, 0.0, 0.0), (sep / 2, 0.0, 0.0))
+        Ntot = nb * n
+        x0 = -L / 2
+        # global axes (ghost-extended)
+        ac = x0 + (np.arange(-ng, Ntot + ng) + 0.5) * self.dx      # cells
+        av = x0 + np.arange(-ng, Ntot + ng + 1) * self.dx          # vertices / faces
+
+        def star_fields(X, Y, Z, what):
+            out = [np.zeros_like(X) for _ in what]
+            psi = np.ones_like(X) if ("alpha" in what or "psi4" in what) else None
+            apsi = np.ones_like(X) if "alpha" in what else None
+            for c in centres:
+                r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+                r_, p_, a_, q4 = self.tov.at(r)
+                for k, w in enumerate(what):
+                    if w == "rho":
+                        out[k] += r_
+                    elif w == "p":
+                        out[k] += p_
+                if psi is not None:
+                    ps = q4 ** 0.25
+                    psi += ps - 1
+                    if apsi is not None:
+                        apsi += a_ * ps - 1
+            for k, w in enumerate(what):
+                if w == "alpha":
+                    out[k] = apsi / psi
+                elif w == "psi4":
+                    out[k] = psi ** 4
+            return out
+
+        Z, Y, X = np.meshgrid(ac, ac, ac, indexing="ij")
+        rho, p = star_fields(X, Y, Z, ("rho", "p"))
+        del X, Y, Z
+        self.rho = np.maximum(rho, self.rho_atm)
+        self.p = np.maximum(p, self.p_atm)
+        Z, Y, X = np.meshgrid(av, av, av, indexing="ij")
+        self.alpha, self.psi4 = star_fields(X, Y, Z, ("alpha", "psi4"))
+        del X, Y, Z
+        assert np.all(self.alpha > 0)
+        p_max = self.tov.p[0]
+
+        def A(comp, X, Y, Z):
+            out = np.zeros_like(X)
+            for c in centres:
+                r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+                _, pp, _, _ = self.tov.at(r)
+                Aphi = np.maximum(pp - 0.04 * p_max, 0.0)
+                out += (-(Y - c[1]) * Aphi) if comp == 0 else ((X - c[0]) * Aphi)
+            return out
+
+        # edge potentials on the global grid (A_z = 0)
+        Ze, Ye, Xe = np.meshgrid(av, av, ac, indexing="ij"); Ax = A(0, Xe, Ye, Ze)   # (V, V, C)
+        Ze, Ye, Xe = np.meshgrid(av, ac, av, indexing="ij"); Ay = A(1, Xe, Ye, Ze)   # (V, C, V)
+        del Xe, Ye, Ze
+        d = self.dx
+        Bx = -(Ay[1:, :, :] - Ay[:-1, :, :]) / d                         # (C, C, V)
+        By = (Ax[1:, :, :] - Ax[:-1, :, :]) / d                          # (C, V, C)
+        Bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / d - (Ax[:, 1:, :] - Ax[:, :-1, :]) / d   # (V, C, C)
+        del Ax, Ay
+        # b^2 of the static fluid = |calB|^2_gamma = |B|^2 / psi^8 (B densitised, gamma = psi^4 delta)
+        Bc2 = (0.5 * (Bx[:, :, 1:] + Bx[:, :, :-1])) ** 2 + (0.5 * (By[:, 1:, :] + By[:, :-1, :])) ** 2 + \
+              (0.5 * (Bz[1:, :, :] + Bz[:-1, :, :])) ** 2
+        psi4c = 0.125 * sum(self.psi4[a:a + Ntot + 2 * ng, b:b + Ntot + 2 * ng, c:c + Ntot + 2 * ng]
+                            for a in (0, 1) for b in (0, 1) for c in (0, 1))
+        b2max = np.max(Bc2 / psi4c ** 2)
+        s = np.sqrt(b2_over_rho * self.rho.max() / b2max) if b2max > 0 else 0.0
+        self.B = [Bx * s, By * s, Bz * s]
+        self.A_b = s
+
+    def blocks(self):
+        """Per-block geometry objects (n, ng, dx), block id = bi + nb (bj + nb bk)."""
+        return [_Geom((self.n,) * 3, self.ng, (self.dx,) * 3) for _ in range(self.nb ** 3)]
+
+    def _slices(self, b, stag=(0, 0, 0)):
+        nb, n, ng = self.nb, self.n, self.ng
+        bi, bj, bk = b % nb, (b // nb) % nb, b // (nb * nb)
+        N = n + 2 * ng
+        return tuple(slice(o * n, o * n + N + s) for o, s in ((bk, stag[2]), (bj, stag[1]), (bi, stag[0])))
+
+    def block(self, b) -> BlockInput:
+        """Materialise block b as a BlockInput (for the oracle)."""
+        n, ng = self.n, self.ng
+        sc = self._slices(b)
+        sv = self._slices(b, (1, 1, 1))
+        W = np.zeros((5,) + (n + 2 * ng,) * 3)
+        W[0] = self.rho[sc]
+        W[4] = self.p[sc]
+        m = np.zeros((16,) + (n + 2 * ng + 1,) * 3)
+        m[0] = self.alpha[sv]
+        m[4] = m[7] = m[9] = self.psi4[sv]
+        B = [np.ascontiguousarray(self.B[d][self._slices(b, tuple(int(a == d) for a in range(3)))])
+             for d in range(3)]
+        bi, bj, bk = b % self.nb, (b // self.nb) % self.nb, b // (self.nb * self.nb)
+        x0 = tuple(-self.L / 2 + o * n * self.dx for o in (bi, bj, bk))
+        return BlockInput((n,) * 3, ng, x0, (self.dx,) * 3, m, W, B)
+
+    def pack(self, layout):
+        """numpy pools in the library layout: W (5, ncell), B [3 x nface], metric (10, nvert)."""
+        nbk = self.nb ** 3
+        W = np.zeros((5, layout.ncell))
+        Bp = [np.zeros(layout.nface[d]) for d in range(3)]
+        M = np.zeros((10, layout.nvert))
+        for b in range(nbk):
+            sc = self._slices(b)
+            sv = self._slices(b, (1, 1, 1))
+            c0 = layout.cell_off[b]
+            r = self.rho[sc].ravel(); W[0, c0:c0 + r.size] = r
+            W[4, c0:c0 + r.size] = self.p[sc].ravel()
+            v0 = layout.vert_off[b]
+            a = self.alpha[sv].ravel(); M[0, v0:v0 + a.size] = a
+            q = self.psi4[sv].ravel()
+            for c in (4, 7, 9):
+                M[c, v0:v0 + q.size] = q
+            for d in range(3):
+                f = self.B[d][self._slices(b, tuple(int(a_ == d) for a_ in range(3)))].ravel()
+                f0 = layout.face_off[b, d]
+                Bp[d][f0:f0 + f.size] = f
+        return W, Bp, M

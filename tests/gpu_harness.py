@@ -1,0 +1,172 @@
+"""GPU-side test harness: pack seeded blocks into device pools, run the C-ABI stage, unpack, and
+compare with the oracle.  Inputs of both sides come from ``paper_2311_04989_gb300.inputs`` and the
+oracle's prim2con; nothing flows from the CUDA path into the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_2311_04989_gb300 import grstage as G
+from tests import helpers as H
+
+_ctx = None
+
+
+def ctx():
+    global _ctx
+    if _ctx is None:
+        _ctx = G.gr_context_create(0)
+    return _ctx
+
+
+def gr_params_from(P: O.Params, precision=G.GR_PREC_FP64):
+    c = P.c()
+    return G.gr_params_default(recon=P.recon, precision=precision, emf=P.emf, ceiling=P.ceiling,
+                               max_iter=P.max_iter, gamma_ad=P.gamma_ad, rho_atm=P.rho_atm, p_atm=c.p_atm,
+                               f_thr=P.f_thr, W_max=P.W_max, M_max=P.M_max, tol=P.tol, weno_eps=P.weno_eps,
+                               rk_g0=P.rk_g0, rk_g1=P.rk_g1, rk_beta=P.rk_beta)
+
+
+class Pools:
+    """Device pools of a list of BlockInput-like objects (numpy arrays per block)."""
+
+    def __init__(self, blocks, device="cuda"):
+        import torch
+        self.torch = torch
+        self.blocks = blocks
+        self.L = G.Layout.of(blocks)
+        self.device = device
+
+    # numpy (per block, padded shape) -> device pool
+    def cells(self, per_block, nvar, dtype=np.float64):
+        L = self.L
+        h = np.zeros((nvar, max(L.ncell, 1)), dtype)
+        for b, a in enumerate(per_block):
+            a = np.asarray(a).reshape(nvar, -1) if nvar > 1 else np.asarray(a).reshape(1, -1)
+            h[:, L.cell_off[b]:L.cell_off[b] + a.shape[1]] = a
+        return self.torch.from_numpy(h).to(self.device)
+
+    def faces(self, per_block):
+        L = self.L
+        out = []
+        for d in range(3):
+            h = np.zeros(max(L.nface[d], 1))
+            for b, B in enumerate(per_block):
+                a = np.asarray(B[d]).ravel()
+                h[L.face_off[b, d]:L.face_off[b, d] + a.size] = a
+            out.append(self.torch.from_numpy(h).to(self.device))
+        return out
+
+    def verts(self, per_block):
+        L = self.L
+        h = np.zeros((16, max(L.nvert, 1)))
+        for b, m in enumerate(per_block):
+            a = np.asarray(m).reshape(16, -1)
+            h[:, L.vert_off[b]:L.vert_off[b] + a.shape[1]] = a
+        return self.torch.from_numpy(h).to(self.device)
+
+    # device pool -> numpy per block
+    def unpack_cells(self, t, nvar):
+        h = t.cpu().numpy()
+        out = []
+        for b, bi in enumerate(self.blocks):
+            N = [bi.n[a] + 2 * bi.ng for a in range(3)]
+            sz = N[0] * N[1] * N[2]
+            a = h[..., self.L.cell_off[b]:self.L.cell_off[b] + sz]
+            out.append(a.reshape((nvar,) + (N[2], N[1], N[0])) if nvar > 1 else a.reshape(N[2], N[1], N[0]))
+        return out
+
+    def unpack_faces(self, ts):
+        hs = [t.cpu().numpy() for t in ts]
+        out = []
+        for b, bi in enumerate(self.blocks):
+            N = [bi.n[a] + 2 * bi.ng for a in range(3)]
+            fb = []
+            for d in range(3):
+                sh = (N[2] + (d == 2), N[1] + (d == 1), N[0] + (d == 0))
+                sz = sh[0] * sh[1] * sh[2]
+                fb.append(hs[d][self.L.face_off[b, d]:self.L.face_off[b, d] + sz].reshape(sh))
+            out.append(fb)
+        return out
+
+
+def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None, B0=None, order=None,
+              k_zero=True, return_pools=False):
+    """Run gr_stage on a batch; returns a list of (Uo, Bo, Wo, status) per block (numpy)."""
+    import torch
+    order = order or P.interp_order
+    if U is None:
+        U = [H.cons_from_prims(bi, P, order) for bi in blocks]
+    pools = Pools(blocks)
+    Ud = pools.cells(U, 5)
+    U0d = pools.cells(U0 if U0 is not None else U, 5)
+    Wd = pools.cells([bi.W for bi in blocks], 5)
+    Bd = pools.faces([bi.B for bi in blocks])
+    B0d = pools.faces(B0 if B0 is not None else [bi.B for bi in blocks])
+    Md = pools.verts([bi.metric for bi in blocks])
+    Uo = Ud.clone(); Wo = Wd.clone(); Bo = [b.clone() for b in Bd]
+    st = torch.zeros(max(pools.L.ncell, 1), dtype=torch.uint8, device="cuda")
+    mesh = G.gr_mesh_create(ctx(), pools.L.descriptors())
+    try:
+        metric = G.metric_struct(Md, order=order, k_zero=k_zero)
+        state = G.state_struct(Ud, U0d, Bd, B0d, Wd, Uo, Bo, Wo, st)
+        G.gr_stage(mesh, metric, state, dt, gr_params_from(P, precision), torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    finally:
+        G.gr_mesh_destroy(mesh)
+    Uo_b = pools.unpack_cells(Uo, 5)
+    Wo_b = pools.unpack_cells(Wo, 5)
+    st_b = pools.unpack_cells(st, 1)
+    Bo_b = pools.unpack_faces(Bo)
+    out = [dict(U=Uo_b[b], B=Bo_b[b], W=Wo_b[b], status=st_b[b]) for b in range(len(blocks))]
+    return (out, pools) if return_pools else out
+
+
+def oracle_stage(blocks, P: O.Params, dt, U=None, U0=None, B0=None):
+    out = []
+    for b, bi in enumerate(blocks):
+        Ub = U[b] if U is not None else H.cons_from_prims(bi, P, P.interp_order)
+        U0b = U0[b] if U0 is not None else Ub
+        B0b = B0[b] if B0 is not None else bi.B
+        Uo, Bo, Wo, st = O.stage_block(H.to_oracle(bi), Ub, U0b, B0b, dt, P)
+        out.append(dict(U=Uo, B=Bo, W=Wo, status=st))
+    return out
+
+
+REL_FLOOR = {"U0": 0.0, "U4": 0.0, "W0": 0.0, "W4": 0.0}   # D, tau, rho, p: plain relative
+
+
+def compare(gpu, ref, blocks=None):
+    """Max relative error per variable over interior cells / faces of all blocks.  Denominator:
+    max(|ref|, 1e-3 * max|ref of that variable in the block|) for velocity-like variables (they pass
+    through zero), plain |ref| for D, tau, rho, p.  Also counts status mismatches."""
+    errs = {}
+    nmis = 0
+    for b, (g, r) in enumerate(zip(gpu, ref)):
+        n, ng = _geom(g, r, blocks, b)
+        for key, nv in (("U", 5), ("W", 5)):
+            gi = H.interior(g[key], n, ng)
+            ri = H.interior(r[key], n, ng)
+            for v in range(nv):
+                name = f"{key}{v}"
+                scale = np.max(np.abs(ri[v])) if ri[v].size else 0.0
+                floor = REL_FLOOR.get(name, 1e-3) * scale
+                den = np.maximum(np.abs(ri[v]), max(floor, 1e-300))
+                e = float(np.max(np.abs(gi[v] - ri[v]) / den)) if ri[v].size else 0.0
+                errs[name] = max(errs.get(name, 0.0), e)
+        for d, (gf, rf) in enumerate(zip(H.interior_faces(g["B"], n, ng), H.interior_faces(r["B"], n, ng))):
+            scale = np.max(np.abs(rf)) if rf.size else 0.0
+            den = np.maximum(np.abs(rf), max(1e-3 * scale, 1e-300))
+            e = float(np.max(np.abs(gf - rf) / den)) if rf.size else 0.0
+            errs[f"B{d}"] = max(errs.get(f"B{d}", 0.0), e)
+        nmis += int(np.sum(H.interior(g["status"], n, ng) != H.interior(r["status"], n, ng)))
+    errs["status_mismatch"] = nmis
+    return errs
+
+
+def _geom(g, r, blocks, b):
+    if blocks is not None:
+        return blocks[b].n, blocks[b].ng
+    # infer from shapes: status (Nz,Ny,Nx); assume ng = 3
+    Nz, Ny, Nx = r["status"].shape
+    return (Nx - 6, Ny - 6, Nz - 6), 3

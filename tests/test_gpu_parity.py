@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA stage (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bar: FP64 path within 1e-12 relative per variable (denominators in tests/gpu_harness.compare) and
+identical status; the uniform state bitwise; the mixed path (FP32 reconstruction/HLLE/EMF, FP64
+accumulation and con2prim) within 1e-6 relative in rho with div B at round-off."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2311_04989_gb300 import grstage as G
+from paper_2311_04989_gb300 import inputs as I
+from tests import gpu_harness as GH
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_04989_gb300 import build as B
+    B.build()
+
+
+def check64(gpu, ref, blocks, tol=TOL64):
+    e = GH.compare(gpu, ref, blocks)
+    bad = {k: v for k, v in e.items() if k != "status_mismatch" and v > tol}
+    assert not bad and e["status_mismatch"] == 0, e
+    return e
+
+
+@pytest.mark.parametrize("recon", [0, 1])
+def test_uniform_state_bitwise(recon):
+    bi = I.uniform_block(n=(9, 7, 5))
+    P = O.Params(gamma_ad=5.0 / 3.0, recon=recon, rho_atm=1e-10, tol=1e-15)
+    U = H.cons_from_prims(bi, P)
+    out = GH.gpu_stage([bi], P, 0.05, U=[U])[0]
+    n, g = bi.n, bi.ng
+    assert np.array_equal(H.interior(out["U"], n, g), H.interior(U, n, g))
+    for a, b in zip(H.interior_faces(out["B"], n, g), H.interior_faces(bi.B, n, g)):
+        assert np.array_equal(a, b)
+    assert np.all(H.interior(out["status"], n, g) == 0)
+
+
+@pytest.mark.parametrize("recon", [0, 1])
+def test_random_block_fp64_parity(recon):
+    bi = I.random_block(n=(16, 12, 10), g=3, seed=21, metric_amp=0.02)
+    P = O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-14, tol=1e-15, rk_g0=0.5, rk_g1=0.5, rk_beta=0.5)
+    U = H.cons_from_prims(bi, P)
+    U0 = 1.0001 * U
+    dt = 0.2 * bi.dx[0]
+    check64(GH.gpu_stage([bi], P, dt, U=[U], U0=[U0]), GH.oracle_stage([bi], P, dt, U=[U], U0=[U0]), [bi])
+
+
+def test_batch_of_uneven_blocks_fp64_parity():
+    """Several block sizes in one launch, incl. a non-cubic block with a ragged last tile."""
+    sizes = [(8, 8, 8), (12, 12, 12), (16, 16, 16), (13, 7, 9)]
+    fields = I.make_fields(np.random.default_rng(5), 1.0, shared_metric=True)
+    blocks = [I.random_block(n=s, g=3, x0=(0.1 * k, 0.05, 0.2), dx=(1 / 64,) * 3, seed=30, fields=fields)
+              for k, s in enumerate(sizes)]
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    dt = 0.2 / 64
+    check64(GH.gpu_stage(blocks, P, dt), GH.oracle_stage(blocks, P, dt), blocks)
+
+
+def test_shock_tube_block_fp64_parity():
+    """The 1D magnetised shock tube on a 16^3 block (Gamma 5/3, PLM), first stage."""
+    bi = I.shock_tube_block(n=(16, 16, 16), g=3)
+    P = O.Params(gamma_ad=5.0 / 3.0, recon=0, rho_atm=1e-10, tol=1e-15)
+    dt = 0.4 * bi.dx[0]
+    check64(GH.gpu_stage([bi], P, dt), GH.oracle_stage([bi], P, dt), [bi])
+
+
+def test_magnetised_star_fp64_parity():
+    """Static Gamma=2 polytrope in its isotropic TOV metric with a poloidal field and atmosphere,
+    WENOZ (a reduced 32^3 version of the 64^3 star)."""
+    tov = I.solve_tov()
+    bi = I.star_block(n=(32, 32, 32), g=3, half_width=10.02, tov=tov, A_b=0.05)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-15)
+    dt = 0.25 * bi.dx[0]
+    check64(GH.gpu_stage([bi], P, dt), GH.oracle_stage([bi], P, dt), [bi])
+
+
+def test_order4_interpolation_fp64_parity():
+    bi = I.random_block(n=(10, 10, 10), g=4, seed=41, metric_amp=0.05)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15, interp_order=4)
+    dt = 0.2 * bi.dx[0]
+    check64(GH.gpu_stage([bi], P, dt), GH.oracle_stage([bi], P, dt), [bi])
+
+
+def test_nonzero_extrinsic_curvature_fp64_parity():
+    bi = I.random_block(n=(8, 8, 8), g=3, seed=43, metric_amp=0.05, with_K=True)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    dt = 0.2 * bi.dx[0]
+    check64(GH.gpu_stage([bi], P, dt, k_zero=False), GH.oracle_stage([bi], P, dt), [bi])
+
+
+def test_mixed_precision_error_bounds():
+    """FP32 reconstruction/HLLE/EMF with FP64 accumulation: rho within 1e-6 of the FP64 oracle
+    and div B at FP64 round-off."""
+    bi = I.random_block(n=(16, 16, 16), g=3, seed=22, metric_amp=0.02)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    dt = 0.2 * bi.dx[0]
+    out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED)
+    ref = GH.oracle_stage([bi], P, dt)
+    e = GH.compare(out, ref, [bi])
+    assert e["W0"] < 1e-6 and e["U0"] < 1e-6, e
+    n, g = bi.n, bi.ng
+    d = O.divb(n, g, bi.dx, out[0]["B"])
+    Bmax = max(np.max(np.abs(b)) for b in H.interior_faces(out[0]["B"], n, g))
+    assert np.max(np.abs(H.interior(d, n, g))) * bi.dx[0] / Bmax < 1e-14
+
+
+def test_invalid_arguments_are_rejected():
+    import torch
+    bi = I.uniform_block(n=(4, 4, 4), g=2)
+    P = O.Params(gamma_ad=2.0, recon=1)
+    with pytest.raises(G.GrstageError, match="ghost width"):
+        GH.gpu_stage([bi], P, 0.01)
+    with pytest.raises(G.GrstageError, match="invalid argument"):
+        G.gr_mesh_create(GH.ctx(), [G.gr_block((G.C.c_int32 * 3)(0, 4, 4), 3)])
+
+
+def test_empty_mesh_is_a_no_op():
+    import torch
+    mesh = G.gr_mesh_create(GH.ctx(), [])
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    st = torch.zeros(8, dtype=torch.uint8, device="cuda")
+    m = G.metric_struct(torch.zeros((16, 8), dtype=torch.float64, device="cuda"))
+    s = G.state_struct([x] * 5, None, [x] * 3, None, [x] * 5, [x.clone() for _ in range(5)],
+                       [x.clone() for _ in range(3)], [x.clone() for _ in range(5)], st)
+    G.gr_stage(mesh, m, s, 0.1, G.gr_params_default())
+    G.gr_mesh_destroy(mesh)
+
+
+def test_prim2con_and_con2prim_entries():
+    import torch
+    bi = I.random_block(n=(12, 10, 8), g=3, seed=51, metric_amp=0.05)
+    P = O.Params(gamma_ad=2.0, rho_atm=1e-14, tol=1e-15)
+    pools = GH.Pools([bi])
+    Wd = pools.cells([bi.W], 5)
+    Bd = pools.faces([bi.B])
+    Md = pools.verts([bi.metric])
+    Ud = torch.zeros_like(Wd)
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    m = G.metric_struct(Md)
+    gp = GH.gr_params_from(P)
+    G.gr_prim2con(mesh, m, list(Wd), Bd, list(Ud), gp)
+    Uref = H.cons_from_prims(bi, P)
+    Ug = pools.unpack_cells(Ud, 5)[0]
+    n, g = bi.n, bi.ng
+    for v in range(5):
+        r = H.interior(Uref[v], n, g)
+        den = np.maximum(np.abs(r), 1e-3 * np.max(np.abs(r)))
+        assert np.max(np.abs(H.interior(Ug[v], n, g) - r) / den) < 1e-13, v
+    W2 = torch.zeros_like(Wd)
+    st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+    G.gr_con2prim(mesh, m, list(Ud), Bd, list(W2), st, gp)
+    Wg = pools.unpack_cells(W2, 5)[0]
+    assert np.max(np.abs(H.interior(Wg[0] - bi.W[0], n, g)) / H.interior(bi.W[0], n, g)) < 1e-12
+    G.gr_mesh_destroy(mesh)
+
+
+def test_diag_mass_and_divB():
+    import torch
+    bi = I.random_block(n=(16, 16, 16), g=3, seed=52)
+    P = O.Params(gamma_ad=2.0)
+    U = H.cons_from_prims(bi, P)
+    pools = GH.Pools([bi])
+    Ud = pools.cells([U], 5)
+    Bd = pools.faces([bi.B])
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    out = G.gr_diag(mesh, list(Ud), Bd)
+    G.gr_mesh_destroy(mesh)
+    n, g = bi.n, bi.ng
+    Mb = np.sum(H.interior(U[0], n, g)) * np.prod(bi.dx)
+    assert abs(out[0] - Mb) < 1e-12 * Mb
+    assert out[1] < 1e-14 and out[2] < 1e-14
