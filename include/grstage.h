@@ -60,6 +60,10 @@ enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec.
 #define GR_ST_TAU_FLOOR     0x08  /* tau raised to the cold static value (App. A) */
 #define GR_ST_BD_LIMIT      0x10  /* B^2/D above M_max: D rescaled (App. A) */
 #define GR_ST_EOS_CLAMP     0x20  /* eps clamped to the EOS range (App. A) */
+#define GR_ST_GUESS_REJECTED 0x40 /* a proposed root bracket showed no sign change: full bracket used */
+
+/* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change). */
+enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1 };
 
 /* One MeshBlock: n[] interior cells, ng ghosts, cell widths, and element offsets into the pools. */
 typedef struct {
@@ -103,6 +107,7 @@ typedef struct {
   int32_t emf;          /* GR_EMF_* */
   int32_t ceiling;      /* GR_CEIL_* */
   int32_t max_iter;     /* root-find iteration cap */
+  int32_t c2p_guess;    /* GR_GUESS_*: bracket proposal for con2prim */
   double gamma_ad;      /* ideal gas p = rho eps (Gamma - 1), Sec. 2.3 */
   double rho_atm;       /* f_atm rho_max (Sec. 3.5) */
   double p_atm;         /* p(rho_atm) */

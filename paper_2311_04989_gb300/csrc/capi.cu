@@ -68,6 +68,7 @@ struct gr_mesh {
   Work* d_work[R_NREGION] = {};
   int nwork[R_NREGION] = {};
   Workspace ws{};
+  Shadow sh{};
   double* d_diag = nullptr;
   std::vector<void*> allocs;
   int64_t ws_bytes = 0;
@@ -105,6 +106,7 @@ void gr_params_default(gr_params* p) {
   p->emf = GR_EMF_UPWIND;
   p->ceiling = GR_CEIL_CLAMP;
   p->max_iter = 100;
+  p->c2p_guess = GR_GUESS_NONE;
   p->gamma_ad = 2.0;
   p->rho_atm = 1e-13;
   p->p_atm = 100.0 * 1e-26;
@@ -240,11 +242,13 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
     wvert += (long long)(d.N[0] + 1) * (d.N[1] + 1) * (d.N[2] + 1);
   }
   // work lists
+  // work lists, ordered direction-major so that the CTAs resident on an SM at any time mostly run
+  // the same per-direction instantiation (the three bodies would otherwise share the I-cache)
   std::vector<Work> wl[R_NREGION];
   for (int kind = 0; kind < R_NREGION; ++kind) {
     const int ndir = region_has_dir(kind) ? 3 : 1;
-    for (int b = 0; b < nblocks; ++b)
-      for (int dir = 0; dir < ndir; ++dir) {
+    for (int dir = 0; dir < ndir; ++dir)
+      for (int b = 0; b < nblocks; ++b) {
         const long long cnt = region_count(kind, dir, m->h_blocks[b]);
         for (long long s0 = 0; s0 < cnt; s0 += kTile) wl[kind].push_back(Work{b, dir, (int)s0, 0});
       }
@@ -265,13 +269,26 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
       e = cudaMemcpy(m->d_work[kind], wl[kind].data(), sizeof(Work) * wl[kind].size(), cudaMemcpyHostToDevice);
   }
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-    e = dalloc(sizeof(double) * wcell, (void**)&m->ws.bcc[a]);
-    if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, (void**)&m->ws.ecc[a]);
+    e = dalloc(sizeof(double) * wcell, &m->ws.bcc[a]);
+    if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, &m->ws.ecc[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * 7 * wface[a], &m->ws.flux[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * wvert, &m->ws.edge[a]);
     m->ws.fstride[a] = wface[a];
   }
   m->ws.estride = wvert;
+  // FP32 copies of the stage inputs for the mixed path, covering the extent of the caller pools
+  long long ec = 0, ef[3] = {0, 0, 0}, ev = 0;
+  for (const DBlock& d : m->h_blocks) {
+    ec = std::max(ec, d.cell + (long long)d.N[0] * d.N[1] * d.N[2]);
+    for (int a = 0; a < 3; ++a)
+      ef[a] = std::max(ef[a], d.face[a] + (long long)(d.N[0] + (a == 0)) * (d.N[1] + (a == 1)) * (d.N[2] + (a == 2)));
+    ev = std::max(ev, d.vert + (long long)(d.N[0] + 1) * (d.N[1] + 1) * (d.N[2] + 1));
+  }
+  m->sh.ncell = ec; m->sh.nvert = ev;
+  for (int a = 0; a < 3; ++a) m->sh.nface[a] = ef[a];
+  for (int v = 0; v < 5 && e == cudaSuccess; ++v) e = dalloc(sizeof(float) * ec, (void**)&m->sh.W[v]);
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(float) * ef[a], (void**)&m->sh.B[a]);
+  for (int c = 0; c < 16 && e == cudaSuccess; ++c) e = dalloc(sizeof(float) * ev, (void**)&m->sh.M[c]);
   if (e == cudaSuccess) e = dalloc(sizeof(double) * 8, (void**)&m->d_diag);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
@@ -292,6 +309,7 @@ static int check_params(const gr_params* p) {
   if (p->emf != GR_EMF_UPWIND && p->emf != GR_EMF_MEAN) return fail(GR_EINVAL, "bad emf");
   if (p->ceiling != GR_CEIL_CLAMP && p->ceiling != GR_CEIL_ATMOSPHERE) return fail(GR_EINVAL, "bad ceiling");
   if (p->max_iter < 1 || p->max_iter > 10000) return fail(GR_EINVAL, "max_iter out of range");
+  if (p->c2p_guess != GR_GUESS_NONE && p->c2p_guess != GR_GUESS_FP32) return fail(GR_EINVAL, "bad c2p_guess");
   if (!(p->gamma_ad > 1.0) || !(p->W_max >= 1.0) || !(p->M_max > 0) || !(p->tol > 0) ||
       !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0))
     return fail(GR_EINVAL, "physical parameter out of range");
@@ -301,6 +319,7 @@ static int check_params(const gr_params* p) {
 static KParams kparams(const gr_params* p, double dt) {
   KParams k;
   k.recon = p->recon; k.emf = p->emf; k.ceiling = p->ceiling; k.max_iter = p->max_iter;
+  k.c2p_guess = p->c2p_guess;
   k.gamma_ad = p->gamma_ad; k.rho_atm = p->rho_atm; k.p_atm = p->p_atm; k.f_thr = p->f_thr;
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
@@ -358,7 +377,7 @@ int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, doub
   if (mesh->prof_used < mesh->prof_capacity)
     ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
   cudaError_t e = launch_stage(params->precision, mesh->d_blocks, work, mesh->nwork, mv, s, mesh->ws,
-                               kparams(params, dt), (cudaStream_t)stream, ev);
+                               mesh->sh, kparams(params, dt), (cudaStream_t)stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
   return GR_OK;
 }

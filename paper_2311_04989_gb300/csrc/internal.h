@@ -49,10 +49,29 @@ struct StateView {
   double* Wo[5];
   uint8_t* status;
 };
+// Stage inputs seen in the arithmetic type R of a kernel: the caller's FP64 pools (R = double) or
+// the FP32 copies made by the cast pass (R = float).  Same element indexing as the caller pools.
+template <class R>
+struct InView {
+  const R* W[5];
+  const R* B[3];
+  const R* M[16];
+  int order;
+  int k_zero;
+};
+
+// FP32 copies of the stage inputs (owned by the mesh), sized to the extent of the caller pools
+struct Shadow {
+  float* W[5];
+  float* B[3];
+  float* M[16];
+  long long ncell, nface[3], nvert;   // pool extents in elements
+};
+
 // Workspace pools (owned by the mesh)
 struct Workspace {
-  double* bcc[3];      // undensitised cell-centred field calB^i (cells)
-  double* ecc[3];      // cell-centred electric field E_m (cells, rings -1..n)
+  void* bcc[3];        // undensitised cell-centred field calB^i (cells), FP64 or FP32
+  void* ecc[3];        // cell-centred electric field E_m (cells, rings -1..n), FP64 or FP32
   void* flux[3];       // per direction: 7 arrays of face values (FP64 or FP32), stride fstride[d]
   void* edge[3];       // corner electric field E_m (vertex-indexed), FP64 or FP32
   long long fstride[3];
@@ -60,7 +79,7 @@ struct Workspace {
 };
 
 struct KParams {   // gr_params flattened for the device
-  int recon, emf, ceiling, max_iter;
+  int recon, emf, ceiling, max_iter, c2p_guess;
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
   double dt;
@@ -68,9 +87,11 @@ struct KParams {   // gr_params flattened for the device
 
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the first kernel and after each kernel
+// (the mixed path's input cast is timed with the first kernel)
 cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
                          const int nwork[R_NREGION], const MetricView& m, const StateView& s,
-                         const Workspace& ws, const KParams& kp, cudaStream_t st, cudaEvent_t* ev);
+                         const Workspace& ws, const Shadow& sh, const KParams& kp, cudaStream_t st,
+                         cudaEvent_t* ev);
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             const double* const W[5], const double* const B[3], double* const U[5],
                             const KParams& kp, cudaStream_t st);

@@ -18,7 +18,46 @@ template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 
+// a/b: IEEE division in FP64; the fast approximate FP32 division (2 ulp) on the mixed path
+template <class R> __device__ __forceinline__ R rdiv(R a, R b);
+template <> __device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+
 template <class R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+
+// Precision conversions without the FP64 pipe (on GB300 an F2F conversion is an FP64-pipe
+// instruction, ~1/64 of the FP32 rate).  FP64 -> FP32 rounds to nearest (ties away from zero) and
+// flushes magnitudes below the smallest normal float to signed zero; FP32 -> FP64 is exact.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long sgn = u & 0x8000000000000000ull;
+  const unsigned long long a = u ^ sgn;
+  const unsigned int s32 = (unsigned int)(sgn >> 32);
+  const int e = (int)(a >> 52);
+  if (e >= 0x7FF) return __uint_as_float(s32 | (a > 0x7FF0000000000000ull ? 0x7FC00000u : 0x7F800000u));
+  if (e < 897) return __uint_as_float(s32);                      // below 2^-126
+  if (e > 1150) return __uint_as_float(s32 | 0x7F800000u);      // above the float range
+  const unsigned long long r = a + 0x10000000ull;               // half an FP32 ulp
+  const unsigned int fe = (unsigned int)(r >> 52) - 896u;        // 255 after a carry = inf
+  const unsigned int fm = (unsigned int)(r >> 29) & 0x7FFFFFu;
+  return __uint_as_float(s32 | (fe << 23) | fm);
+}
+
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sgn = u & 0x80000000u;
+  const unsigned int a = u ^ sgn;
+  if (a == 0u) return __longlong_as_double((long long)((unsigned long long)sgn << 32));
+  if (a < 0x00800000u || a >= 0x7F800000u) return (double)f;    // subnormal, inf, nan (rare)
+  const unsigned long long bits = ((unsigned long long)sgn << 32) |
+                                  ((unsigned long long)((a >> 23) + 896u) << 52) |
+                                  ((unsigned long long)(a & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+template <class R> __device__ __forceinline__ double to64(R x);
+template <> __device__ __forceinline__ double to64(double x) { return x; }
+template <> __device__ __forceinline__ double to64(float x) { return f2d_exact(x); }
 template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 template <class R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 
@@ -49,12 +88,13 @@ __device__ __forceinline__ R inv_dd(const R g[6], int d, R det) {
   if (d == 0) c = g[3] * g[5] - g[4] * g[4];
   else if (d == 1) c = g[0] * g[5] - g[2] * g[2];
   else c = g[0] * g[3] - g[1] * g[1];
-  return c / det;
+  return rdiv(c, det);
 }
 
-// full inverse (FP64 cell path)
-__device__ __forceinline__ void inv3(const double g[6], double det, double gi[6]) {
-  const double id = 1.0 / det;
+// full inverse
+template <class R>
+__device__ __forceinline__ void inv3(const R g[6], R det, R gi[6]) {
+  const R id = rdiv(R(1), det);
   gi[0] = (g[3] * g[5] - g[4] * g[4]) * id;
   gi[1] = (g[2] * g[4] - g[1] * g[5]) * id;
   gi[2] = (g[1] * g[4] - g[2] * g[3]) * id;
@@ -82,7 +122,7 @@ __device__ __forceinline__ long long vix(const DBlock& b, int i, int j, int k) {
 // centre of a d-face (face plane = vertex plane p[d]) and at cell centres (with derivatives).
 // ------------------------------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void face_metric(const DBlock& b, const MetricView& m, int order, int d,
+__device__ __forceinline__ void face_metric(const DBlock& b, const InView<R>& m, int order, int d,
                                             const int p[3], R out[10]) {
   const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const long long base = b.vert;
@@ -97,8 +137,8 @@ __device__ __forceinline__ void face_metric(const DBlock& b, const MetricView& m
     const long long v01 = base + vix(b, q[0], q[1], q[2]);
 #pragma unroll
     for (int c = 0; c < 10; ++c) {
-      const double* a = m.v[c];
-      out[c] = R(0.25) * (R(a[v00]) + R(a[v10]) + R(a[v01]) + R(a[v11]));
+      const R* a = m.M[c];
+      out[c] = R(0.25) * (a[v00] + a[v10] + a[v01] + a[v11]);
     }
   } else {
     const R w[4] = {R(-1.0 / 16), R(9.0 / 16), R(9.0 / 16), R(-1.0 / 16)};
@@ -112,52 +152,54 @@ __device__ __forceinline__ void face_metric(const DBlock& b, const MetricView& m
         const long long vi = base + vix(b, q[0], q[1], q[2]);
         const R ww = w[s1] * w[s2];
 #pragma unroll
-        for (int c = 0; c < 10; ++c) out[c] += ww * R(m.v[c][vi]);
+        for (int c = 0; c < 10; ++c) out[c] += ww * m.M[c][vi];
       }
   }
 }
 
-// Cell-centre value of components [0, nc) and, if dv != nullptr, derivatives d_k of components
-// [0, 10) (alpha, beta, gamma).  The derivative along k is written as vertex differences so that it
-// vanishes exactly on a constant field.
-__device__ __forceinline__ void cell_metric(const DBlock& b, const MetricView& m, int order, int i,
-                                            int j, int k, int nc, double* val, double (*dv)[10]) {
+// Cell-centre value of components [c0, nc) and, if dv != nullptr, derivatives d_k of components
+// [0, 10) (alpha, beta, gamma), computed in R from the FP64 vertex pools.  The derivative along k is
+// written as vertex differences so that it vanishes exactly on a constant field.
+template <class R>
+__device__ __forceinline__ void cell_metric(const DBlock& b, const InView<R>& m, int order, int i,
+                                            int j, int k, int c0, int nc, R* val, R (*dv)[10]) {
   const long long base = b.vert;
   if (order == 2) {
     long long v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = base + vix(b, i + (t & 1), j + ((t >> 1) & 1), k + (t >> 2));
-    for (int c = 0; c < nc; ++c) {
-      const double* a = m.v[c];
-      double f[8];
+    const R ix = R(0.25 * b.idx[0]), iy = R(0.25 * b.idx[1]), iz = R(0.25 * b.idx[2]);
+#pragma unroll
+    for (int c = c0; c < nc; ++c) {
+      const R* a = m.M[c];
+      R f[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) f[t] = a[v[t]];
-      val[c] = 0.125 * (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])));
+      val[c] = R(0.125) * (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])));
       if (dv && c < 10) {
-        dv[0][c] = 0.25 * (((f[1] - f[0]) + (f[3] - f[2])) + ((f[5] - f[4]) + (f[7] - f[6]))) * b.idx[0];
-        dv[1][c] = 0.25 * (((f[2] - f[0]) + (f[3] - f[1])) + ((f[6] - f[4]) + (f[7] - f[5]))) * b.idx[1];
-        dv[2][c] = 0.25 * (((f[4] - f[0]) + (f[5] - f[1])) + ((f[6] - f[2]) + (f[7] - f[3]))) * b.idx[2];
+        dv[0][c] = (((f[1] - f[0]) + (f[3] - f[2])) + ((f[5] - f[4]) + (f[7] - f[6]))) * ix;
+        dv[1][c] = (((f[2] - f[0]) + (f[3] - f[1])) + ((f[6] - f[4]) + (f[7] - f[5]))) * iy;
+        dv[2][c] = (((f[4] - f[0]) + (f[5] - f[1])) + ((f[6] - f[2]) + (f[7] - f[3]))) * iz;
       }
     }
   } else {
-    const double w[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
-    for (int c = 0; c < nc; ++c) {
-      const double* a = m.v[c];
-      double s = 0, d0 = 0;
+    const R w[4] = {R(-1.0 / 16), R(9.0 / 16), R(9.0 / 16), R(-1.0 / 16)};
+    for (int c = c0; c < nc; ++c) {
+      const R* a = m.M[c];
+      R s = 0, d0 = 0;
       for (int kk = 0; kk < 4; ++kk)
         for (int jj = 0; jj < 4; ++jj) {
           const long long r = base + vix(b, i - 1, j - 1 + jj, k - 1 + kk);
-          const double f0 = a[r], f1 = a[r + 1], f2 = a[r + 2], f3 = a[r + 3];
-          const double wjk = w[jj] * w[kk];
+          const R f0 = a[r], f1 = a[r + 1], f2 = a[r + 2], f3 = a[r + 3];
+          const R wjk = w[jj] * w[kk];
           s += wjk * (w[0] * f0 + w[1] * f1 + w[2] * f2 + w[3] * f3);
-          if (dv && c < 10) d0 += wjk * (27.0 * (f2 - f1) - (f3 - f0));
+          if (dv && c < 10) d0 += wjk * (R(27) * (f2 - f1) - (f3 - f0));
         }
       val[c] = s;
       if (dv && c < 10) {
-        dv[0][c] = d0 / (24.0 * b.dx[0]);
-        // y and z derivatives: differences along the axis, interpolation across
+        dv[0][c] = d0 * R(1.0 / (24.0 * b.dx[0]));
         for (int ax = 1; ax < 3; ++ax) {
-          double acc = 0;
+          R acc = 0;
           for (int u = 0; u < 4; ++u)
             for (int t = 0; t < 4; ++t) {
               auto at = [&](int s4) {
@@ -165,9 +207,9 @@ __device__ __forceinline__ void cell_metric(const DBlock& b, const MetricView& m
                 q[ax] = (ax == 1 ? j : k) - 1 + s4;
                 return a[base + vix(b, q[0], q[1], q[2])];
               };
-              acc += w[t] * w[u] * (27.0 * (at(2) - at(1)) - (at(3) - at(0)));
+              acc += w[t] * w[u] * (R(27) * (at(2) - at(1)) - (at(3) - at(0)));
             }
-          dv[ax][c] = acc / (24.0 * b.dx[ax]);
+          dv[ax][c] = acc * R(1.0 / (24.0 * b.dx[ax]));
         }
       }
     }
@@ -185,22 +227,50 @@ __device__ __forceinline__ R vl_slope(R wm, R w0, R wp) {
   return pr > R(0) ? R(2) * pr / (dL + dR) : R(0);
 }
 
+// smoothness indicators and candidate values shared by both weight forms
 template <class R>
-__device__ __forceinline__ R wenoz(R v0, R v1, R v2, R v3, R v4, R eps) {
-  const R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * R(1.0 / 6.0);
-  const R q1 = (-v1 + R(5) * v2 + R(2) * v3) * R(1.0 / 6.0);
-  const R q2 = (R(2) * v2 + R(5) * v3 - v4) * R(1.0 / 6.0);
+__device__ __forceinline__ void wenoz_parts(R v0, R v1, R v2, R v3, R v4, R q[3], R bk[3]) {
+  q[0] = (R(2) * v0 - R(7) * v1 + R(11) * v2) * R(1.0 / 6.0);
+  q[1] = (-v1 + R(5) * v2 + R(2) * v3) * R(1.0 / 6.0);
+  q[2] = (R(2) * v2 + R(5) * v3 - v4) * R(1.0 / 6.0);
   const R a0 = v0 - R(2) * v1 + v2, c0 = v0 - R(4) * v1 + R(3) * v2;
   const R a1 = v1 - R(2) * v2 + v3, c1 = v1 - v3;
   const R a2 = v2 - R(2) * v3 + v4, c2 = R(3) * v2 - R(4) * v3 + v4;
-  const R b0 = R(13.0 / 12.0) * a0 * a0 + R(0.25) * c0 * c0;
-  const R b1 = R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
-  const R b2 = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
-  const R t5 = rabs(b0 - b2);
-  const R w0 = R(0.1) * (R(1) + t5 / (b0 + eps));
-  const R w1 = R(0.6) * (R(1) + t5 / (b1 + eps));
-  const R w2 = R(0.3) * (R(1) + t5 / (b2 + eps));
-  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+  bk[0] = R(13.0 / 12.0) * a0 * a0 + R(0.25) * c0 * c0;
+  bk[1] = R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
+  bk[2] = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
+}
+
+// WENOZ value at the right edge of the middle cell of v0..v4.
+// FP64: the weights alpha_k = d_k (1 + tau5/e_k), e_k = beta_k + eps, are multiplied through by
+// e_0 e_1 e_2 so that one division normalises them (same weights, one FP64 division instead of
+// four).  FP32: per-weight fast divisions on the power-of-two scaled stencil.
+template <class R>
+__device__ __forceinline__ R wenoz(R v0, R v1, R v2, R v3, R v4, R eps);
+
+template <>
+__device__ __forceinline__ double wenoz<double>(double v0, double v1, double v2, double v3, double v4,
+                                                double eps) {
+  double q[3], bk[3];
+  wenoz_parts(v0, v1, v2, v3, v4, q, bk);
+  const double t5 = fabs(bk[0] - bk[2]);
+  const double e0 = bk[0] + eps, e1 = bk[1] + eps, e2 = bk[2] + eps;
+  const double P = e0 * e1 * e2;
+  const double w0 = 0.1 * (P + t5 * (e1 * e2));
+  const double w1 = 0.6 * (P + t5 * (e0 * e2));
+  const double w2 = 0.3 * (P + t5 * (e0 * e1));
+  return (w0 * q[0] + w1 * q[1] + w2 * q[2]) / (w0 + w1 + w2);
+}
+
+template <>
+__device__ __forceinline__ float wenoz<float>(float v0, float v1, float v2, float v3, float v4, float eps) {
+  float q[3], bk[3];
+  wenoz_parts(v0, v1, v2, v3, v4, q, bk);
+  const float t5 = fabsf(bk[0] - bk[2]);
+  const float w0 = 0.1f * (1.f + __fdividef(t5, bk[0] + eps));
+  const float w1 = 0.6f * (1.f + __fdividef(t5, bk[1] + eps));
+  const float w2 = 0.3f * (1.f + __fdividef(t5, bk[2] + eps));
+  return __fdividef(w0 * q[0] + w1 * q[1] + w2 * q[2], w0 + w1 + w2);
 }
 
 // FP32: the stencil is scaled by a power of two near its largest magnitude before the smoothness
@@ -268,9 +338,9 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   R utl[3];
   lower3(g, ut, utl);
   const R W = rsqrt_(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
-  const R iW = R(1) / W;
-  const R ia = R(1) / alpha;
-  const R isg = R(1) / sg;
+  const R iW = rdiv(R(1), W);
+  const R ia = rdiv(R(1), alpha);
+  const R isg = rdiv(R(1), sg);
   R v[3], vl[3], vt[3], Bu[3], Bl[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -287,7 +357,7 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   R bl[3];                                       // b_i = calB_i / W + alpha b^0 v_i
 #pragma unroll
   for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
-  const R rhoh = rho + gam / (gam - R(1)) * p;   // rho h for p = (Gamma-1) rho eps
+  const R rhoh = rho + gam * rdiv(p, gam - R(1));   // rho h for p = (Gamma-1) rho eps
   const R e = rhoh + b2;
   const R pt = p + R(0.5) * b2;
   // Eq. consB_def
@@ -310,14 +380,14 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   F[5] = alpha * (Bd[t1] * vt[d] - Bd[d] * vt[t1]);
   F[6] = alpha * (Bd[t2] * vt[d] - Bd[d] * vt[t2]);
   // fast speeds
-  const R cs2 = gam * p / rhoh;
-  const R ca2 = b2 / e;
+  const R cs2 = rdiv(gam * p, rhoh);
+  const R ca2 = rdiv(b2, e);
   const R c2 = cs2 + ca2 - cs2 * ca2;
   const R v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
   R disc = (R(1) - v2) * (gdd * (R(1) - v2 * c2) - v[d] * v[d] * (R(1) - c2));
   disc = disc > R(0) ? disc : R(0);
   const R cr = rsqrt_(c2) * rsqrt_(disc);
-  const R iden = R(1) / (R(1) - v2 * c2);
+  const R iden = rdiv(R(1), R(1) - v2 * c2);
   const R vc = v[d] * (R(1) - c2);
   *lp = alpha * (vc + cr) * iden - beta[d];
   *lm = alpha * (vc - cr) * iden - beta[d];
@@ -335,190 +405,233 @@ __device__ __forceinline__ void hlle(const R UL[7], const R UR[7], const R FL[7]
     for (int v = 0; v < 7; ++v) out[v] = R(0.5) * (FL[v] + FR[v]);
     return;
   }
-  const R iden = R(1) / den;
+  const R iden = rdiv(R(1), den);
   const R lpm = lp * lm;
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v] = (lp * FL[v] - lm * FR[v] + lpm * (UR[v] - UL[v])) * iden;
 }
 
 // ------------------------------------------------------------------------------------------------
-// FP64 cell physics: prim -> cons, stress tensor and sources (Eq. EMT_MHD, Eq. hydsrc_def)
+// Cell physics in R: prim -> cons, stress tensor and sources (Eq. EMT_MHD, Eq. hydsrc_def)
 // ------------------------------------------------------------------------------------------------
+template <class R>
 struct CellMet {
-  double alpha, beta[3], g[6], K[6], gi[6], sg;
+  R alpha, beta[3], g[6], K[6], gi[6], sg, det;
 };
 
-__device__ __forceinline__ void cellmet_from(const double val[16], bool kzero, CellMet& M) {
+template <class R>
+__device__ __forceinline__ void cellmet_from(const R val[16], bool kzero, CellMet<R>& M) {
   M.alpha = val[0];
+  #pragma unroll
   for (int i = 0; i < 3; ++i) M.beta[i] = val[1 + i];
+  #pragma unroll
   for (int c = 0; c < 6; ++c) {
     M.g[c] = val[4 + c];
-    M.K[c] = kzero ? 0.0 : val[10 + c];
+    M.K[c] = kzero ? R(0) : val[10 + c];
   }
-  const double det = det3(M.g);
-  M.sg = sqrt(det);
-  inv3(M.g, det, M.gi);
+  M.det = det3(M.g);
+  M.sg = rsqrt_(M.det);
+  inv3(M.g, M.det, M.gi);
 }
 
+template <class R>
 struct CellFluid {
-  double rho, p, W, rhoh, b2, ab0;
-  double ut[3], utl[3], v[3], vl[3], vt[3];
-  double Bu[3], bl[3];
+  R rho, p, W, rhoh, b2, ab0;
+  R ut[3], utl[3], v[3], vl[3], vt[3];
+  R Bu[3], bl[3];
 };
 
-__device__ __forceinline__ void cell_fluid(const CellMet& M, double gam, const double w[5],
-                                           const double Bd[3], CellFluid& f) {
+template <class R>
+__device__ __forceinline__ void cell_fluid(const CellMet<R>& M, R gam, const R w[5], const R Bd[3],
+                                           CellFluid<R>& f) {
   f.rho = w[0];
   f.p = w[4];
+  #pragma unroll
   for (int i = 0; i < 3; ++i) f.ut[i] = w[1 + i];
   lower3(M.g, f.ut, f.utl);
-  f.W = sqrt(1.0 + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
-  const double iW = 1.0 / f.W, ia = 1.0 / M.alpha, isg = 1.0 / M.sg;
+  f.W = rsqrt_(R(1) + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
+  const R iW = rdiv(R(1), f.W), ia = rdiv(R(1), M.alpha), isg = rdiv(R(1), M.sg);
+  #pragma unroll
   for (int i = 0; i < 3; ++i) {
     f.v[i] = f.ut[i] * iW;
     f.vl[i] = f.utl[i] * iW;
     f.vt[i] = f.v[i] - M.beta[i] * ia;
     f.Bu[i] = Bd[i] * isg;
   }
-  double Bl[3];
+  R Bl[3];
   lower3(M.g, f.Bu, Bl);
-  const double Bv = f.Bu[0] * f.vl[0] + f.Bu[1] * f.vl[1] + f.Bu[2] * f.vl[2];
-  const double BB = f.Bu[0] * Bl[0] + f.Bu[1] * Bl[1] + f.Bu[2] * Bl[2];
+  const R Bv = f.Bu[0] * f.vl[0] + f.Bu[1] * f.vl[1] + f.Bu[2] * f.vl[2];
+  const R BB = f.Bu[0] * Bl[0] + f.Bu[1] * Bl[1] + f.Bu[2] * Bl[2];
   f.ab0 = f.W * Bv;
   f.b2 = (f.ab0 * f.ab0 + BB) * iW * iW;
+  #pragma unroll
   for (int i = 0; i < 3; ++i) f.bl[i] = Bl[i] * iW + f.ab0 * f.vl[i];
-  f.rhoh = f.rho + gam / (gam - 1.0) * f.p;
+  f.rhoh = f.rho + gam * rdiv(f.p, gam - R(1));
 }
 
-__device__ __forceinline__ void cell_cons(const CellMet& M, const CellFluid& f, double q[5]) {
-  const double e = f.rhoh + f.b2, pt = f.p + 0.5 * f.b2;
+template <class R>
+__device__ __forceinline__ void cell_cons(const CellMet<R>& M, const CellFluid<R>& f, R q[5]) {
+  const R e = f.rhoh + f.b2, pt = f.p + R(0.5) * f.b2;
   q[0] = M.sg * f.rho * f.W;
+  #pragma unroll
   for (int j = 0; j < 3; ++j) q[1 + j] = M.sg * (e * f.W * f.utl[j] - f.ab0 * f.bl[j]);
   q[4] = M.sg * (e * f.W * f.W - f.rho * f.W - pt - f.ab0 * f.ab0);
 }
 
 // Eq. hydsrc_def; dm[k][c] = d_k of alpha (c=0), beta^i (1..3), gamma_ij (4..9)
-__device__ __forceinline__ void cell_sources(const CellMet& M, const CellFluid& f, const double dm[3][10],
-                                             bool kzero, double s[5]) {
-  const double a = M.alpha, ia2 = 1.0 / (a * a);
+template <class R>
+__device__ __forceinline__ void cell_sources(const CellMet<R>& M, const CellFluid<R>& f, const R dm[3][10],
+                                             bool kzero, R s[5]) {
+  const R a = M.alpha, ia2 = rdiv(R(1), a * a);
   // u^mu, b^mu
-  double u[4], b[4];
-  u[0] = f.W / a;
+  R u[4], b[4];
+  u[0] = f.W * rdiv(R(1), a);
+  #pragma unroll
   for (int i = 0; i < 3; ++i) u[1 + i] = f.W * f.vt[i];
-  b[0] = f.ab0 / a;
-  for (int i = 0; i < 3; ++i) b[1 + i] = f.Bu[i] / f.W + f.ab0 * f.vt[i];
-  const double e = f.rhoh + f.b2, pt = f.p + 0.5 * f.b2;
+  b[0] = f.ab0 * rdiv(R(1), a);
+  const R iW = rdiv(R(1), f.W);
+  #pragma unroll
+  for (int i = 0; i < 3; ++i) b[1 + i] = f.Bu[i] * iW + f.ab0 * f.vt[i];
+  const R e = f.rhoh + f.b2, pt = f.p + R(0.5) * f.b2;
   // T^{mu nu} = e u u + pt g^{mu nu} - b b, with g^{00} = -1/a^2, g^{0i} = beta^i/a^2,
   // g^{ij} = gamma^{ij} - beta^i beta^j / a^2
-  const double T00 = e * u[0] * u[0] - pt * ia2 - b[0] * b[0];
-  double T0i[3], Tij[6];
+  const R T00 = e * u[0] * u[0] - pt * ia2 - b[0] * b[0];
+  R T0i[3], Tij[6];
+  #pragma unroll
   for (int i = 0; i < 3; ++i) T0i[i] = e * u[0] * u[1 + i] + pt * M.beta[i] * ia2 - b[0] * b[1 + i];
+  #pragma unroll
   for (int i = 0; i < 3; ++i)
+    #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int c = sidx(i, j);
       Tij[c] = e * u[1 + i] * u[1 + j] + pt * (M.gi[c] - M.beta[i] * M.beta[j] * ia2) - b[1 + i] * b[1 + j];
     }
   // T^0_i = T^{00} beta_i + T^{0j} gamma_ji
-  double betal[3], T0l[3];
+  R betal[3], T0l[3];
   lower3(M.g, M.beta, betal);
   lower3(M.g, T0i, T0l);
+  #pragma unroll
   for (int i = 0; i < 3; ++i) T0l[i] += T00 * betal[i];
-  const double asg = a * M.sg;
-  s[0] = 0.0;
+  const R asg = a * M.sg;
+  s[0] = R(0);
+  #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double* dg = dm[k] + 4;
-    double bbdg = 0, T0bdg = 0, Tdg = 0;
+    const R* dg = dm[k] + 4;
+    R bbdg = 0, T0bdg = 0, Tdg = 0;
+    #pragma unroll
     for (int i = 0; i < 3; ++i)
+      #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const double dgij = dg[sidx(i, j)];
+        const R dgij = dg[sidx(i, j)];
         bbdg += M.beta[i] * M.beta[j] * dgij;
         T0bdg += T0i[i] * M.beta[j] * dgij;
         Tdg += Tij[sidx(i, j)] * dgij;
       }
-    const double Tdb = T0l[0] * dm[k][1] + T0l[1] * dm[k][2] + T0l[2] * dm[k][3];
-    s[1 + k] = asg * (T00 * (0.5 * bbdg - a * dm[k][0]) + T0bdg + Tdb + 0.5 * Tdg);
+    const R Tdb = T0l[0] * dm[k][1] + T0l[1] * dm[k][2] + T0l[2] * dm[k][3];
+    s[1 + k] = asg * (T00 * (R(0.5) * bbdg - a * dm[k][0]) + T0bdg + Tdb + R(0.5) * Tdg);
   }
-  double st = 0;
+  R st = 0;
+  #pragma unroll
   for (int i = 0; i < 3; ++i) st -= (T00 * M.beta[i] + T0i[i]) * dm[i][0];
   if (!kzero) {
-    double bKb = 0, TK = 0;
+    R bKb = 0, TK = 0;
+    #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      double bK = 0;
+      R bK = 0;
+      #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const double Kij = M.K[sidx(i, j)];
+        const R Kij = M.K[sidx(i, j)];
         bK += M.beta[j] * Kij;
         TK += Tij[sidx(i, j)] * Kij;
       }
       bKb += M.beta[i] * bK;
-      st += 2.0 * T0i[i] * bK;
+      st += R(2) * T0i[i] * bK;
     }
     st += T00 * bKb + TK;
   }
   s[4] = asg * st;
 }
 
+// FP64 spatial metric at a cell centre for con2prim: gamma_ij and sqrt(gamma); the inverse is
+// formed only for cells that are solved
+struct C2PMet {
+  double g[6], sg, det;
+};
+
+__device__ __forceinline__ void c2pmet_from(const double g6[6], C2PMet& M) {
+  for (int c = 0; c < 6; ++c) M.g[c] = g6[c];
+  M.det = det3(M.g);
+  M.sg = sqrt(M.det);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Con2prim (Sec. 3.5, App. A): KKC master function in mu = 1/(hW), Illinois bracketing.
+// Templated so that an FP32 pre-solve can narrow the FP64 bracket.
 // ------------------------------------------------------------------------------------------------
+template <class R>
 struct C2PInv {
-  double D, q, r2, b2, rb;
+  R D, q, r2, b2, rb;
 };
+template <class R>
 struct C2PVal {
-  double x, rbar2, v2, W, rho, eps, f;
+  R x, rbar2, v2, iW, eps, f;
   bool vcap, eclamp;
 };
 
-__device__ __forceinline__ void c2p_master(const KParams& P, const C2PInv& I, double mu, C2PVal& E) {
-  const double vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
-  E.x = 1.0 / (1.0 + mu * I.b2);
-  E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (1.0 + E.x) * I.rb * I.rb;
-  const double qbar = I.q - 0.5 * I.b2 - 0.5 * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
+// f(mu) = mu - 1/(nu + mu rbar^2), nu = max(nu_A, nu_B).  For the ideal gas (1 + a)(1 + eps) =
+// 1 + Gamma eps, so nu_A = (1 + Gamma eps)/W and nu_B = (1 + Gamma eps)(1 + qbar - mu rbar^2)/(1 + eps);
+// eps = W (qbar - mu rbar^2) + v^2 W^2/(1 + W) is formed over the common denominator iW (1 + iW),
+// iW = 1/W = sqrt(1 - v^2).
+template <class R>
+__device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R mu, C2PVal<R>& E) {
+  E.x = rdiv(R(1), R(1) + mu * I.b2);
+  E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (R(1) + E.x) * I.rb * I.rb;
+  const R qbar = I.q - R(0.5) * I.b2 - R(0.5) * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
   E.v2 = mu * mu * E.rbar2;
   E.vcap = E.v2 > vmax2;
   if (E.vcap) E.v2 = vmax2;
-  E.W = 1.0 / sqrt(1.0 - E.v2);
-  E.rho = I.D / E.W;
-  const double qm = qbar - mu * E.rbar2;
-  E.eps = E.W * qm + E.v2 * E.W * E.W / (1.0 + E.W);
-  E.eclamp = E.eps < 0.0;
-  if (E.eclamp) E.eps = 0.0;
-  // ideal gas: a = p/(rho(1+eps)) = (Gamma-1) eps/(1+eps)
-  const double ah = (P.gamma_ad - 1.0) * E.eps / (1.0 + E.eps);
-  const double nuA = (1.0 + ah) * (1.0 + E.eps) / E.W;
-  const double nuB = (1.0 + ah) * (1.0 + qm);
-  const double nu = nuA > nuB ? nuA : nuB;
-  E.f = mu - 1.0 / (nu + mu * E.rbar2);
+  E.iW = rsqrt_(R(1) - E.v2);
+  const R qm = qbar - mu * E.rbar2;
+  E.eps = rdiv(qm * (R(1) + E.iW) + E.v2, E.iW * (R(1) + E.iW));
+  E.eclamp = E.eps < R(0);
+  if (E.eclamp) E.eps = R(0);
+  const R ge = R(1) + gam * E.eps;
+  const R nuA = ge * E.iW;
+  const R nuB = rdiv(ge * (R(1) + qm), R(1) + E.eps);
+  const R nu = nuA > nuB ? nuA : nuB;
+  E.f = mu - rdiv(R(1), nu + mu * E.rbar2);
 }
 
-__device__ __forceinline__ double c2p_aux(const C2PInv& I, double mu) {
-  const double x = 1.0 / (1.0 + mu * I.b2);
-  const double rbar2 = x * x * I.r2 + mu * x * (1.0 + x) * I.rb * I.rb;
-  return mu * sqrt(1.0 + rbar2) - 1.0;
+template <class R>
+__device__ __forceinline__ R c2p_aux(const C2PInv<R>& I, R mu) {
+  const R x = rdiv(R(1), R(1) + mu * I.b2);
+  const R rbar2 = x * x * I.r2 + mu * x * (R(1) + x) * I.rb * I.rb;
+  return mu * rsqrt_(R(1) + rbar2) - R(1);
 }
 
 // Illinois on [a,b] (f(a) < 0 < f(b) or reverse).  Returns 0 (root), -1 (no sign change), -2 (cap).
-template <class Fn>
-__device__ __forceinline__ int illinois(Fn f, double a, double b, double fa, double fb, double tol,
-                                        int max_iter, double* root, double* hi_out, int* iters) {
+template <class R, class Fn>
+__device__ __forceinline__ int illinois(Fn f, R a, R b, R fa, R fb, R tol, int max_iter, R* root, R* hi_out,
+                                        int* iters) {
   *iters = 0;
-  if (fa == 0.0) { *root = a; *hi_out = a; return 0; }
-  if (fb == 0.0) { *root = b; *hi_out = b; return 0; }
-  if ((fa < 0.0) == (fb < 0.0)) return -1;
+  if (fa == R(0)) { *root = a; *hi_out = a; return 0; }
+  if (fb == R(0)) { *root = b; *hi_out = b; return 0; }
+  if ((fa < R(0)) == (fb < R(0))) return -1;
   int side = 0;
   for (int it = 1; it <= max_iter; ++it) {
-    double c = (a * fb - b * fa) / (fb - fa);
-    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    R c = rdiv(a * fb - b * fa, fb - fa);
+    if (!(c > a && c < b)) c = R(0.5) * (a + b);
     if (!(c > a && c < b)) { *root = c; *hi_out = b; *iters = it; return 0; }
-    const double fc = f(c);
+    const R fc = f(c);
     *iters = it;
-    if (fc == 0.0) { *root = c; *hi_out = c; return 0; }
-    if ((fc < 0.0) == (fa < 0.0)) {
+    if (fc == R(0)) { *root = c; *hi_out = c; return 0; }
+    if ((fc < R(0)) == (fa < R(0))) {
       a = c; fa = fc;
-      if (side == -1) fb *= 0.5;
+      if (side == -1) fb *= R(0.5);
       side = -1;
     } else {
       b = c; fb = fc;
-      if (side == +1) fa *= 0.5;
+      if (side == +1) fa *= R(0.5);
       side = +1;
     }
     if (b - a <= tol * c) { *root = c; *hi_out = b; return 0; }
@@ -527,25 +640,51 @@ __device__ __forceinline__ int illinois(Fn f, double a, double b, double fa, dou
   return -2;
 }
 
+// FP32 pre-solve of the master root: returns mu32 > 0, or 0 when it did not converge
+__device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<double>& I64) {
+  C2PInv<float> I;
+  I.D = (float)I64.D; I.q = (float)I64.q; I.r2 = (float)I64.r2; I.b2 = (float)I64.b2; I.rb = (float)I64.rb;
+  if (!(I.D > 0.f) || !isfinite(I.q) || !isfinite(I.r2) || !isfinite(I.b2)) return 0.f;
+  const float gam = (float)P.gamma_ad, vmax2 = (float)(1.0 - 1.0 / (P.W_max * P.W_max));
+  float mup = 1.f, root, hi;
+  int it;
+  const float f1 = c2p_aux<float>(I, 1.f);
+  if (f1 > 0.f) {
+    auto fa = [&](float mu) { return c2p_aux<float>(I, mu); };
+    if (illinois<float>(fa, 0.f, 1.f, -1.f, f1, 1e-3f, 40, &root, &hi, &it) == 0) mup = hi;
+  }
+  C2PVal<float> E;
+  auto fm = [&](float mu) { c2p_master<float>(gam, vmax2, I, mu, E); return E.f; };
+  const float f0 = fm(0.f);
+  float fp = fm(mup);
+  if ((f0 < 0.f) == (fp < 0.f) && mup < 1.f) { mup = 1.f; fp = fm(mup); }
+  if (illinois<float>(fm, 0.f, mup, f0, fp, 1e-6f, 60, &root, &hi, &it) != 0) return 0.f;
+  return root;
+}
+
 // Full con2prim of one cell.  q: densitised conserved (in/out), Bd: densitised cell field.
-__device__ __forceinline__ int con2prim_cell(const CellMet& M, const KParams& P, double q[5],
+// guess: GR_GUESS_NONE (bracket (0, mu+]) or GR_GUESS_FP32 (an FP32 pre-solve proposes a bracket of
+// relative half-width 2e-5 around its root; it is used only if the FP64 master function changes
+// sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set).
+__device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, double q[5],
                                              const double Bd[3], double w[5], int* iters) {
   int st = 0;
   *iters = 0;
-  const double isg = 1.0 / M.sg;
-  double D = q[0] * isg, tau = q[4] * isg, S[3], Bu[3];
-  bool finite = isfinite(D) && isfinite(tau);
-  for (int i = 0; i < 3; ++i) {
-    S[i] = q[1 + i] * isg;
-    Bu[i] = Bd[i] * isg;
-    finite = finite && isfinite(S[i]) && isfinite(Bu[i]);
-  }
+  bool finite = isfinite(q[0]) && isfinite(q[4]);
+  for (int i = 0; i < 3; ++i) finite = finite && isfinite(q[1 + i]) && isfinite(Bd[i]);
   // atmosphere threshold; values within 1e-12 relative of it count as having reached it
   const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-12);
   bool atm = false;
   if (!finite) { st |= GR_ST_FAILED; atm = true; }
-  else if (D < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
+  else if (q[0] < rho_thr * M.sg) { st |= GR_ST_ATM_THRESHOLD; atm = true; }   // D~ < rho_thr
+  double isg = 0.0;
   if (!atm) {
+    isg = 1.0 / M.sg;
+    double D = q[0] * isg, tau = q[4] * isg, S[3], Bu[3];
+    for (int i = 0; i < 3; ++i) {
+      S[i] = q[1 + i] * isg;
+      Bu[i] = Bd[i] * isg;
+    }
     double Bl[3];
     lower3(M.g, Bu, Bl);
     const double BB = Bu[0] * Bl[0] + Bu[1] * Bl[1] + Bu[2] * Bl[2];
@@ -553,41 +692,55 @@ __device__ __forceinline__ int con2prim_cell(const CellMet& M, const KParams& P,
     if (BB > P.M_max * D) { D = BB / P.M_max; st |= GR_ST_BD_LIMIT; qmod = true; }
     const double tau_min = 0.5 * BB;
     if (tau < tau_min) { tau = tau_min; st |= GR_ST_TAU_FLOOR; qmod = true; }
-    C2PInv I;
+    double gi[6];
+    inv3(M.g, M.det, gi);
+    C2PInv<double> I;
     I.D = D;
     const double iD = 1.0 / D;
     I.q = tau * iD;
     double rl[3], ru[3], bu[3];
-    const double isD = 1.0 / sqrt(D);
+    const double isD = sqrt(iD);
     for (int i = 0; i < 3; ++i) { rl[i] = S[i] * iD; bu[i] = Bu[i] * isD; }
-    ru[0] = M.gi[0] * rl[0] + M.gi[1] * rl[1] + M.gi[2] * rl[2];
-    ru[1] = M.gi[1] * rl[0] + M.gi[3] * rl[1] + M.gi[4] * rl[2];
-    ru[2] = M.gi[2] * rl[0] + M.gi[4] * rl[1] + M.gi[5] * rl[2];
+    ru[0] = gi[0] * rl[0] + gi[1] * rl[1] + gi[2] * rl[2];
+    ru[1] = gi[1] * rl[0] + gi[3] * rl[1] + gi[4] * rl[2];
+    ru[2] = gi[2] * rl[0] + gi[4] * rl[1] + gi[5] * rl[2];
     I.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
     I.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     I.b2 = BB * iD;
-    // upper bracket from the auxiliary function on (0, 1]
-    double mup = 1.0, root, hi;
-    int it_aux;
-    {
-      const double f1 = c2p_aux(I, 1.0);
-      if (f1 > 0.0) {
-        auto fa = [&](double mu) { return c2p_aux(I, mu); };
-        if (illinois(fa, 0.0, 1.0, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+    const double gam = P.gamma_ad, vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
+    C2PVal<double> E;
+    auto fm = [&](double mu) { c2p_master<double>(gam, vmax2, I, mu, E); return E.f; };
+    double root = 0.0, hi;
+    int r = -1;
+    if (P.c2p_guess == GR_GUESS_FP32) {
+      const double mu32 = (double)c2p_presolve32(P, I);
+      if (mu32 > 0.0) {
+        const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), 1.0);
+        const double flo = fm(lo), fup = fm(up);
+        if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, iters);
       }
+      if (r != 0) st |= GR_ST_GUESS_REJECTED;
     }
-    C2PVal E;
-    auto fm = [&](double mu) { c2p_master(P, I, mu, E); return E.f; };
-    const double f0 = fm(0.0);
-    double fp = fm(mup);
-    if ((f0 < 0.0) == (fp < 0.0) && mup < 1.0) { mup = 1.0; fp = fm(mup); }
-    const int r = illinois(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, iters);
+    if (r != 0) {
+      // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0], h0 = 1
+      double mup = 1.0;
+      int it_aux;
+      const double f1 = c2p_aux<double>(I, 1.0);
+      if (f1 > 0.0) {
+        auto fa = [&](double mu) { return c2p_aux<double>(I, mu); };
+        if (illinois<double>(fa, 0.0, 1.0, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+      }
+      const double f0 = fm(0.0);
+      double fp = fm(mup);
+      if ((f0 < 0.0) == (fp < 0.0) && mup < 1.0) { mup = 1.0; fp = fm(mup); }
+      r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, iters);
+    }
     if (r != 0) {
       st |= GR_ST_FAILED;
       atm = true;
     } else {
       const double mu = root;
-      c2p_master(P, I, mu, E);
+      c2p_master<double>(gam, vmax2, I, mu, E);
       double vu[3];
       for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);
       if (E.vcap) {
@@ -597,22 +750,30 @@ __device__ __forceinline__ int con2prim_cell(const CellMet& M, const KParams& P,
         if (P.ceiling == GR_CEIL_ATMOSPHERE) atm = true;
       }
       if (E.eclamp) st |= GR_ST_EOS_CLAMP;
-      if (E.rho < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
+      const double rho = D * E.iW;
+      if (rho < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
       if (!atm) {
-        w[0] = E.rho;
-        for (int i = 0; i < 3; ++i) w[1 + i] = E.W * vu[i];
-        w[4] = (P.gamma_ad - 1.0) * E.rho * E.eps;
+        const double W = 1.0 / E.iW;
+        w[0] = rho;
+        for (int i = 0; i < 3; ++i) w[1 + i] = W * vu[i];
+        w[4] = (P.gamma_ad - 1.0) * rho * E.eps;
         if (qmod) { q[0] = M.sg * D; q[4] = M.sg * tau; }
       }
     }
   }
   if (atm) {
+    // atmosphere primitives (Sec. 3.5) and their conserved variables, Eq. consB_def at u~ = 0:
+    // W = 1, b^0 = 0, b^2 = calB^2, so D = sqrt(gamma) rho, S_j = 0,
+    // tau = sqrt(gamma) (p/(Gamma - 1) + calB^2 / 2) = sqrt(gamma) p/(Gamma - 1) + gamma_ij B^i B^j/(2 sqrt(gamma))
     w[0] = P.rho_atm;
     w[1] = w[2] = w[3] = 0.0;
     w[4] = P.p_atm;
-    CellFluid f;
-    cell_fluid(M, P.gamma_ad, w, Bd, f);
-    cell_cons(M, f, q);
+    double Bl[3];
+    lower3(M.g, Bd, Bl);
+    const double BBd = Bd[0] * Bl[0] + Bd[1] * Bl[1] + Bd[2] * Bl[2];
+    q[0] = M.sg * P.rho_atm;
+    q[1] = q[2] = q[3] = 0.0;
+    q[4] = M.sg * (P.p_atm / (P.gamma_ad - 1.0)) + (BBd == 0.0 ? 0.0 : 0.5 * BBd / M.sg);
   }
   return st;
 }

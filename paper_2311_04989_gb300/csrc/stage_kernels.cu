@@ -1,16 +1,20 @@
-// stage_kernels.cu -- the GRMHD stage as five kernels per call (sm_103a).
+// stage_kernels.cu -- the GRMHD stage as a short sequence of kernels per call (sm_103a).
 //
+//   k_cast       (mixed path only) FP32 copies of the stage inputs W, B and the metric, made with
+//                integer bit arithmetic so that no conversion runs on GB300's narrow FP64 pipe
 //   k_cellprep   cell-centred field calB^i = mean of faces / sqrt(gamma) on all cells, and the
 //                cell electric field E_m = alpha (v~^b B^a - v~^a B^b) on the ring -1..n  (Sec. 3.3)
 //   k_faces<R>   reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux (Eq. fluxB_def)
 //                on every face with normal index 0..n and transverse index -1..n
 //   k_edges<R>   upwinded corner electric field from the four adjacent face fluxes (Sec. 3.3)
-//   k_ct         constrained-transport face update B' = g0 B0 + g1 B - beta dt curl E
-//   k_update     flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def), FP64
-//                accumulation, then con2prim with atmosphere on the updated state (Sec. 3.5)
+//   k_ct         constrained-transport face update B' = g0 B0 + g1 B - beta dt curl E  (FP64)
+//   k_update     flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def) accumulated in
+//                FP64, then con2prim with atmosphere on the updated state (Sec. 3.5), FP64
 //
 // Every kernel takes one work item (block, direction, first element) per CTA; blocks of different
-// sizes share one launch.  Face fluxes and corner fields pass through the mesh's workspace.
+// sizes share one launch.  Within a work item the direction is a compile-time constant (one
+// instantiation per direction), so no small array is indexed at run time.  Face fluxes and corner
+// fields pass through the mesh's workspace in the arithmetic type R.
 #include <cstdio>
 
 #include "internal.h"
@@ -21,109 +25,146 @@ namespace grs {
 // ------------------------------------------------------------------------------------------------
 // region decoding
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void region(int kind, int dir, const DBlock& b, int lo[3], int cnt[3]) {
-  for (int a = 0; a < 3; ++a) {
-    switch (kind) {
-      case R_CELLS_ALL: lo[a] = -b.g; cnt[a] = b.N[a]; break;
-      case R_FACES: lo[a] = (a == dir) ? 0 : -1; cnt[a] = (a == dir) ? b.n[a] + 1 : b.n[a] + 2; break;
-      case R_EDGES: lo[a] = 0; cnt[a] = (a == dir) ? b.n[a] : b.n[a] + 1; break;
-      case R_CTFACES: lo[a] = 0; cnt[a] = (a == dir) ? b.n[a] + 1 : b.n[a]; break;
-      default: lo[a] = 0; cnt[a] = b.n[a]; break;
-    }
-  }
-}
-
-// element index of this thread -> (i,j,k); false when past the region's end
-__device__ __forceinline__ bool decode(int kind, const Work& w, const DBlock& b, int p[3]) {
+template <int KIND, int DIR>
+__device__ __forceinline__ bool decode(const Work& w, const DBlock& b, int p[3]) {
   int lo[3], cnt[3];
-  region(kind, w.dir, b, lo, cnt);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (KIND == R_CELLS_ALL) { lo[a] = -b.g; cnt[a] = b.N[a]; }
+    else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a] + 2; }
+    else if (KIND == R_EDGES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] : b.n[a] + 1; }
+    else if (KIND == R_CTFACES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a]; }
+    else { lo[a] = 0; cnt[a] = b.n[a]; }
+  }
   const int e = w.start + threadIdx.x;
-  const int total = cnt[0] * cnt[1] * cnt[2];
-  if (e >= total) return false;
+  if (e >= cnt[0] * cnt[1] * cnt[2]) return false;
   p[0] = lo[0] + e % cnt[0];
   p[1] = lo[1] + (e / cnt[0]) % cnt[1];
   p[2] = lo[2] + e / (cnt[0] * cnt[1]);
   return true;
 }
 
+template <int D>
+__device__ __forceinline__ long long face_stride(const DBlock& b, int of_dir) {
+  // element stride of one step along direction of_dir in the D-face layout
+  return of_dir == 0 ? 1 : (of_dir == 1 ? (long long)(b.N[0] + (D == 0)) : (long long)(b.N[0] + (D == 0)) * (b.N[1] + (D == 1)));
+}
+
+__device__ __forceinline__ long long cell_stride(const DBlock& b, int dir) {
+  return dir == 0 ? 1 : (dir == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+}
+
 // ------------------------------------------------------------------------------------------------
-// k_cellprep
+// k_cast: FP64 -> FP32 copies of up to 24 pools
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTile) k_cellprep(const DBlock* __restrict__ blocks,
-                                                    const Work* __restrict__ work, MetricView m,
-                                                    StateView s, Workspace ws, KParams kp) {
+struct CastList {
+  const double* src[24];
+  float* dst[24];
+  long long n[24];
+  int count;
+};
+
+__global__ void __launch_bounds__(256) k_cast(const __grid_constant__ CastList L) {
+  const int seg = blockIdx.y;
+  if (seg >= L.count) return;
+  const double* __restrict__ s = L.src[seg];
+  float* __restrict__ d = L.dst[seg];
+  const long long n = L.n[seg];
+  const long long step = (long long)gridDim.x * blockDim.x;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if ((((unsigned long long)s) & 15ull) || (((unsigned long long)d) & 7ull)) {   // unaligned pool: scalar
+    for (long long i = i0; i < n; i += step) d[i] = d2f_rn(s[i]);
+    return;
+  }
+  const long long n2 = n / 2;
+  const double2* s2 = reinterpret_cast<const double2*>(s);
+  float2* d2 = reinterpret_cast<float2*>(d);
+  for (long long i = i0; i < n2; i += step) {
+    const double2 v = s2[i];
+    d2[i] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
+  }
+  if (i0 == 0 && (n & 1)) d[n - 1] = d2f_rn(s[n - 1]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// k_cellprep<R>
+// ------------------------------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(kTile) k_cellprep(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    const __grid_constant__ InView<R> in,
+                                                    const __grid_constant__ Workspace ws) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
   int p[3];
-  if (!decode(R_CELLS_ALL, w, b, p)) return;
+  if (!decode<R_CELLS_ALL, 0>(w, b, p)) return;
   const int i = p[0], j = p[1], k = p[2];
-  if (m.order == 4) {
+  if (in.order == 4) {
+#pragma unroll
     for (int a = 0; a < 3; ++a)
       if (p[a] < -b.g + 1 || p[a] > b.n[a] + b.g - 2) return;
   }
-  double val[10];
-  cell_metric(b, m, m.order, i, j, k, 10, val, nullptr);
-  const double g6[6] = {val[4], val[5], val[6], val[7], val[8], val[9]};
-  const double sg = sqrt(det3(g6));
-  double Bd[3];
-  const long long f0 = fix(b, 0, i, j, k), f1 = fix(b, 1, i, j, k), f2 = fix(b, 2, i, j, k);
-  Bd[0] = 0.5 * (s.B[0][b.face[0] + f0] + s.B[0][b.face[0] + f0 + 1]);
-  Bd[1] = 0.5 * (s.B[1][b.face[1] + f1] + s.B[1][b.face[1] + f1 + b.N[0]]);
-  Bd[2] = 0.5 * (s.B[2][b.face[2] + f2] + s.B[2][b.face[2] + f2 + (long long)b.N[0] * b.N[1]]);
+  R val[10];
+  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, nullptr);
+  const R* g6 = val + 4;
+  const R sg = rsqrt_(det3(g6));
+  R Bd[3];
+  const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
+  const long long f2 = b.face[2] + fix(b, 2, i, j, k);
+  Bd[0] = R(0.5) * (in.B[0][f0] + in.B[0][f0 + 1]);
+  Bd[1] = R(0.5) * (in.B[1][f1] + in.B[1][f1 + b.N[0]]);
+  Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
   const long long wc = b.wcell + cix(b, i, j, k);
-  const double isg = 1.0 / sg;
+  const R isg = rdiv(R(1), sg);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ws.bcc[a][wc] = Bd[a] * isg;
+  for (int a = 0; a < 3; ++a) reinterpret_cast<R*>(ws.bcc[a])[wc] = Bd[a] * isg;
   const bool ring = i >= -1 && i <= b.n[0] && j >= -1 && j <= b.n[1] && k >= -1 && k <= b.n[2];
   if (!ring) return;
   const long long c = b.cell + cix(b, i, j, k);
-  const double ut[3] = {s.W[1][c], s.W[2][c], s.W[3][c]};
-  double utl[3];
+  const R ut[3] = {in.W[1][c], in.W[2][c], in.W[3][c]};
+  R utl[3];
   lower3(g6, ut, utl);
-  const double iW = 1.0 / sqrt(1.0 + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
-  const double ia = 1.0 / val[0];
-  double vt[3];
+  const R iW = rdiv(R(1), rsqrt_(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]));
+  const R ia = rdiv(R(1), val[0]);
+  R vt[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) vt[a] = ut[a] * iW - val[1 + a] * ia;
 #pragma unroll
   for (int mm = 0; mm < 3; ++mm) {
     const int a = (mm + 1) % 3, bb = (mm + 2) % 3;
-    ws.ecc[mm][wc] = val[0] * (vt[bb] * Bd[a] - vt[a] * Bd[bb]);
+    reinterpret_cast<R*>(ws.ecc[mm])[wc] = val[0] * (vt[bb] * Bd[a] - vt[a] * Bd[bb]);
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 // k_faces<R>
 // ------------------------------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(kTile) k_faces(const DBlock* __restrict__ blocks,
-                                                 const Work* __restrict__ work, MetricView m,
-                                                 StateView s, Workspace ws, KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
+template <class R, int D>
+__device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const InView<R>& in,
+                                          const Workspace& ws, const KParams& kp) {
   int p[3];
-  if (!decode(R_FACES, w, b, p)) return;
-  const int d = w.dir, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  // stencil cells p[d]-3 .. p[d]+2 along d
-  const long long stride = (d == 0) ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+  if (!decode<R_FACES, D>(w, b, p)) return;
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  // stencil cells p[D]-3 .. p[D]+2 along D
+  const long long stride = cell_stride(b, D);
   int q[3] = {p[0], p[1], p[2]};
-  q[d] -= 3;
+  q[D] -= 3;
   const long long c0 = cix(b, q[0], q[1], q[2]);
   R st[7][6];
-  const int tlo = (b.g >= 3 || kp.recon == GR_RECON_WENOZ) ? 0 : 1;
-  const int thi = (b.g >= 3 || kp.recon == GR_RECON_WENOZ) ? 6 : 5;
+  const bool wide = (b.g >= 3 || kp.recon == GR_RECON_WENOZ);
+  const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]);
+  const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]);
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
-    if (t < tlo || t >= thi) {
+    if (!wide && (t == 0 || t == 5)) {
 #pragma unroll
       for (int v = 0; v < 7; ++v) st[v][t] = R(0);
       continue;
     }
     const long long c = c0 + t * stride;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) st[v][t] = R(s.W[v][b.cell + c]);
-    st[5][t] = R(ws.bcc[t1][b.wcell + c]);
-    st[6][t] = R(ws.bcc[t2][b.wcell + c]);
+    for (int v = 0; v < 5; ++v) st[v][t] = in.W[v][b.cell + c];
+    st[5][t] = bc1[b.wcell + c];
+    st[6][t] = bc2[b.wcell + c];
   }
   const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
   R L[7], Rr[7];
@@ -135,59 +176,65 @@ __global__ void __launch_bounds__(kTile) k_faces(const DBlock* __restrict__ bloc
     for (int v = 0; v < 7; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
   }
   R met[10];
-  face_metric<R>(b, m, m.order, d, p, met);
+  face_metric<R>(b, in, in.order, D, p, met);
   const R det = det3(met + 4);
   const R sg = rsqrt_(det);
-  const R gdd = inv_dd(met + 4, d, det);
-  const long long fi = fix(b, d, p[0], p[1], p[2]);
-  const R Bn = R(s.B[d][b.face[d] + fi]);
+  const R gdd = inv_dd(met + 4, D, det);
+  const long long fi = fix(b, D, p[0], p[1], p[2]);
+  const R Bn = in.B[D][b.face[D] + fi];
   R BL[3], BR[3];
-  BL[d] = Bn; BR[d] = Bn;
+  BL[D] = Bn; BR[D] = Bn;
   BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
   BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
   const R gam = R(kp.gamma_ad);
   R UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
-  face_state<R>(d, met, sg, gdd, gam, L, BL, UL, FL, &lmL, &lpL);
-  face_state<R>(d, met, sg, gdd, gam, Rr, BR, UR, FR, &lmR, &lpR);
+  face_state<R>(D, met, sg, gdd, gam, L, BL, UL, FL, &lmL, &lpL);
+  face_state<R>(D, met, sg, gdd, gam, Rr, BR, UR, FR, &lmR, &lpR);
   R F[7];
   hlle<R>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
-  R* out = reinterpret_cast<R*>(ws.flux[d]);
-  const long long o = b.wface[d] + fi;
+  R* out = reinterpret_cast<R*>(ws.flux[D]);
+  const long long o = b.wface[D] + fi;
 #pragma unroll
-  for (int v = 0; v < 7; ++v) out[v * ws.fstride[d] + o] = F[v];
+  for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                 const __grid_constant__ InView<R> in,
+                                                 const __grid_constant__ Workspace ws,
+                                                 const __grid_constant__ KParams kp) {
+  const Work w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  if (w.dir == 0) face_body<R, 0>(w, b, in, ws, kp);
+  else if (w.dir == 1) face_body<R, 1>(w, b, in, ws, kp);
+  else face_body<R, 2>(w, b, in, ws, kp);
 }
 
 // ------------------------------------------------------------------------------------------------
 // k_edges<R>: corner electric field E_m at (a-face ia, b-face ib, m-cell im), (a, b, m) cyclic
 // ------------------------------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(kTile) k_edges(const DBlock* __restrict__ blocks,
-                                                 const Work* __restrict__ work, Workspace ws,
-                                                 KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
+template <class R, int M>
+__device__ __forceinline__ void edge_body(const Work& w, const DBlock& b, const Workspace& ws,
+                                          const KParams& kp) {
   int e[3];
-  if (!decode(R_EDGES, w, b, e)) return;
-  const int m = w.dir, a = (m + 1) % 3, bb = (m + 2) % 3;
-  const R* Fa = reinterpret_cast<const R*>(ws.flux[a]);
-  const R* Fb = reinterpret_cast<const R*>(ws.flux[bb]);
-  const long long sa = ws.fstride[a], sb = ws.fstride[bb];
-  const int ia = e[a], ib = e[bb];
-  auto pos = [&](int ja, int jb, int r[3]) { r[a] = ja; r[bb] = jb; r[m] = e[m]; };
-  int r[3];
+  if (!decode<R_EDGES, M>(w, b, e)) return;
+  constexpr int A = (M + 1) % 3, BB = (M + 2) % 3;
+  const R* Fa = reinterpret_cast<const R*>(ws.flux[A]);
+  const R* Fb = reinterpret_cast<const R*>(ws.flux[BB]);
+  const long long sa = ws.fstride[A], sb = ws.fstride[BB];
   // a-face values at b-cells ib and ib-1; b-face values at a-cells ia and ia-1
-  pos(ia, ib, r);      const long long fa1 = b.wface[a] + fix(b, a, r[0], r[1], r[2]);
-  pos(ia, ib - 1, r);  const long long fa0 = b.wface[a] + fix(b, a, r[0], r[1], r[2]);
-  pos(ia, ib, r);      const long long fb1 = b.wface[bb] + fix(b, bb, r[0], r[1], r[2]);
-  pos(ia - 1, ib, r);  const long long fb0 = b.wface[bb] + fix(b, bb, r[0], r[1], r[2]);
+  const long long fa1 = b.wface[A] + fix(b, A, e[0], e[1], e[2]);
+  const long long fa0 = fa1 - face_stride<A>(b, BB);
+  const long long fb1 = b.wface[BB] + fix(b, BB, e[0], e[1], e[2]);
+  const long long fb0 = fb1 - face_stride<BB>(b, A);
   const R Ea1 = -Fa[5 * sa + fa1], Ea0 = -Fa[5 * sa + fa0];   // E_m = -F^a_{B^b}
   const R Eb1 = Fb[6 * sb + fb1], Eb0 = Fb[6 * sb + fb0];     // E_m = +F^b_{B^a}
   R E = R(0.25) * (Ea1 + Ea0 + Eb1 + Eb0);
   if (kp.emf == GR_EMF_UPWIND) {
-    pos(ia, ib, r);         const R C11 = R(ws.ecc[m][b.wcell + cix(b, r[0], r[1], r[2])]);
-    pos(ia - 1, ib, r);     const R C01 = R(ws.ecc[m][b.wcell + cix(b, r[0], r[1], r[2])]);
-    pos(ia, ib - 1, r);     const R C10 = R(ws.ecc[m][b.wcell + cix(b, r[0], r[1], r[2])]);
-    pos(ia - 1, ib - 1, r); const R C00 = R(ws.ecc[m][b.wcell + cix(b, r[0], r[1], r[2])]);
+    const R* ecc = reinterpret_cast<const R*>(ws.ecc[M]);
+    const long long c11 = b.wcell + cix(b, e[0], e[1], e[2]);
+    const long long sA = cell_stride(b, A), sB = cell_stride(b, BB);
+    const R C11 = ecc[c11], C01 = ecc[c11 - sA], C10 = ecc[c11 - sB], C00 = ecc[c11 - sA - sB];
     const R va1 = Fa[fa1], va0 = Fa[fa0], vb1 = Fb[fb1], vb0 = Fb[fb0];   // mass fluxes
     auto upw = [](R vel, R lowside, R highside) {
       return vel > R(0) ? lowside : (vel < R(0) ? highside : R(0.5) * (lowside + highside));
@@ -198,73 +245,110 @@ __global__ void __launch_bounds__(kTile) k_edges(const DBlock* __restrict__ bloc
     const R da_lo = upw(vb0, Ea0 - C00, Ea1 - C01);
     E += R(0.25) * (db_lo - db_hi) + R(0.25) * (da_lo - da_hi);
   }
-  R* out = reinterpret_cast<R*>(ws.edge[m]);
-  out[b.wvert + vix(b, e[0], e[1], e[2])] = E;
+  reinterpret_cast<R*>(ws.edge[M])[b.wvert + vix(b, e[0], e[1], e[2])] = E;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTile) k_edges(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                 const __grid_constant__ Workspace ws,
+                                                 const __grid_constant__ KParams kp) {
+  const Work w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  if (w.dir == 0) edge_body<R, 0>(w, b, ws, kp);
+  else if (w.dir == 1) edge_body<R, 1>(w, b, ws, kp);
+  else edge_body<R, 2>(w, b, ws, kp);
 }
 
 // ------------------------------------------------------------------------------------------------
 // k_ct: B'^d on faces of interior cells (FP64)
 // ------------------------------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(kTile) k_ct(const DBlock* __restrict__ blocks,
-                                              const Work* __restrict__ work, StateView s, Workspace ws,
-                                              KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
+template <class R, int D>
+__device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const StateView& s,
+                                        const Workspace& ws, const KParams& kp) {
   int p[3];
-  if (!decode(R_CTFACES, w, b, p)) return;
-  const int d = w.dir, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  if (!decode<R_CTFACES, D>(w, b, p)) return;
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   const R* E2 = reinterpret_cast<const R*>(ws.edge[t2]);
   const R* E1 = reinterpret_cast<const R*>(ws.edge[t1]);
-  int q[3] = {p[0], p[1], p[2]};
-  const long long v0 = b.wvert + vix(b, q[0], q[1], q[2]);
-  q[t1] += 1;
-  const long long v1 = b.wvert + vix(b, q[0], q[1], q[2]);
-  q[t1] -= 1;
-  q[t2] += 1;
-  const long long v2 = b.wvert + vix(b, q[0], q[1], q[2]);
-  const double dE2 = ((double)E2[v1] - (double)E2[v0]) * b.idx[t1];
-  const double dE1 = ((double)E1[v2] - (double)E1[v0]) * b.idx[t2];
-  const long long f = b.face[d] + fix(b, d, p[0], p[1], p[2]);
-  double Bn = kp.rk_g1 * s.B[d][f] - kp.rk_beta * kp.dt * (dE2 - dE1);
-  if (kp.rk_g0 != 0.0) Bn += kp.rk_g0 * s.B0[d][f];
-  s.Bo[d][f] = Bn;
+  const long long v0 = b.wvert + vix(b, p[0], p[1], p[2]);
+  const long long vs1 = t1 == 0 ? 1 : (t1 == 1 ? (long long)(b.N[0] + 1) : (long long)(b.N[0] + 1) * (b.N[1] + 1));
+  const long long vs2 = t2 == 0 ? 1 : (t2 == 1 ? (long long)(b.N[0] + 1) : (long long)(b.N[0] + 1) * (b.N[1] + 1));
+  const double dE2 = (to64(E2[v0 + vs1]) - to64(E2[v0])) * b.idx[t1];
+  const double dE1 = (to64(E1[v0 + vs2]) - to64(E1[v0])) * b.idx[t2];
+  const long long f = b.face[D] + fix(b, D, p[0], p[1], p[2]);
+  double Bn = kp.rk_g1 * s.B[D][f] - kp.rk_beta * kp.dt * (dE2 - dE1);
+  if (kp.rk_g0 != 0.0) Bn += kp.rk_g0 * s.B0[D][f];
+  s.Bo[D][f] = Bn;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTile) k_ct(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                              const __grid_constant__ StateView s,
+                                              const __grid_constant__ Workspace ws,
+                                              const __grid_constant__ KParams kp) {
+  const Work w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  if (w.dir == 0) ct_body<R, 0>(w, b, s, ws, kp);
+  else if (w.dir == 1) ct_body<R, 1>(w, b, s, ws, kp);
+  else ct_body<R, 2>(w, b, s, ws, kp);
 }
 
 // ------------------------------------------------------------------------------------------------
-// k_update: U' and con2prim on interior cells (FP64)
+// k_update<R>: U' (sources in R, FP64 accumulation) and FP64 con2prim on interior cells
 // ------------------------------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blocks,
-                                                  const Work* __restrict__ work, MetricView m,
-                                                  StateView s, Workspace ws, KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  int p[3];
-  if (!decode(R_INTERIOR, w, b, p)) return;
-  const int i = p[0], j = p[1], k = p[2];
-  const bool kzero = m.k_zero != 0;
-  double val[16], dm[3][10];
-  cell_metric(b, m, m.order, i, j, k, kzero ? 10 : 16, val, dm);
-  CellMet M;
-  cellmet_from(val, kzero, M);
-  const long long c = b.cell + cix(b, i, j, k);
-  // stage-input state at the cell: primitives and the mean densitised field of the input faces
-  double wv[5], Bd[3];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) wv[v] = s.W[v][c];
+__device__ __forceinline__ void cell_field(const DBlock& b, const double* const* B, int i, int j, int k,
+                                           double Bd[3]) {
   const long long f0 = b.face[0] + fix(b, 0, i, j, k);
   const long long f1 = b.face[1] + fix(b, 1, i, j, k);
   const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-  const long long sy = b.N[0], sz = (long long)b.N[0] * b.N[1];
-  Bd[0] = 0.5 * (s.B[0][f0] + s.B[0][f0 + 1]);
-  Bd[1] = 0.5 * (s.B[1][f1] + s.B[1][f1 + sy]);
-  Bd[2] = 0.5 * (s.B[2][f2] + s.B[2][f2 + sz]);
-  CellFluid fl;
-  cell_fluid(M, kp.gamma_ad, wv, Bd, fl);
-  double src[5];
-  cell_sources(M, fl, dm, kzero, src);
-  // flux divergence
+  Bd[0] = 0.5 * (B[0][f0] + B[0][f0 + 1]);
+  Bd[1] = 0.5 * (B[1][f1] + B[1][f1 + b.N[0]]);
+  Bd[2] = 0.5 * (B[2][f2] + B[2][f2 + (long long)b.N[0] * b.N[1]]);
+}
+
+// FP64 gamma_ij at a cell centre (con2prim's metric)
+__device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<double>& m, int i, int j, int k,
+                                             C2PMet& M) {
+  double val[10];
+  cell_metric<double>(b, m, m.order, i, j, k, 4, 10, val, nullptr);
+  c2pmet_from(val + 4, M);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                  const __grid_constant__ InView<R> in,
+                                                  const __grid_constant__ InView<double> in64,
+                                                  const __grid_constant__ StateView s,
+                                                  const __grid_constant__ Workspace ws,
+                                                  const __grid_constant__ KParams kp) {
+  const Work w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  int p[3];
+  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
+  const int i = p[0], j = p[1], k = p[2];
+  const bool kzero = in.k_zero != 0;
+  R val[16], dm[3][10];
+  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, dm);
+  if (!kzero) cell_metric<R>(b, in, in.order, i, j, k, 10, 16, val, nullptr);
+  CellMet<R> M;
+  cellmet_from<R>(val, kzero, M);
+  const long long c = b.cell + cix(b, i, j, k);
+  // stage-input state at the cell: primitives and the mean densitised field of the input faces
+  R wv[5], Bd[3];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) wv[v] = in.W[v][c];
+  {
+    const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
+    const long long f2 = b.face[2] + fix(b, 2, i, j, k);
+    Bd[0] = R(0.5) * (in.B[0][f0] + in.B[0][f0 + 1]);
+    Bd[1] = R(0.5) * (in.B[1][f1] + in.B[1][f1 + b.N[0]]);
+    Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
+  }
+  CellFluid<R> fl;
+  cell_fluid<R>(M, R(kp.gamma_ad), wv, Bd, fl);
+  R src[5];
+  cell_sources<R>(M, fl, dm, kzero, src);
+  // flux divergence, accumulated in FP64 (face values widened exactly)
   const R* F0 = reinterpret_cast<const R*>(ws.flux[0]);
   const R* F1 = reinterpret_cast<const R*>(ws.flux[1]);
   const R* F2 = reinterpret_cast<const R*>(ws.flux[2]);
@@ -276,21 +360,30 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
   double q[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double dF = ((double)F0[v * ws.fstride[0] + g0 + 1] - (double)F0[v * ws.fstride[0] + g0]) * b.idx[0] +
-                      ((double)F1[v * ws.fstride[1] + g1 + oy] - (double)F1[v * ws.fstride[1] + g1]) * b.idx[1] +
-                      ((double)F2[v * ws.fstride[2] + g2 + oz] - (double)F2[v * ws.fstride[2] + g2]) * b.idx[2];
-    double u = kp.rk_g1 * s.U[v][c] + bdt * (-dF + src[v]);
+    const R* a0 = F0 + v * ws.fstride[0];
+    const R* a1 = F1 + v * ws.fstride[1];
+    const R* a2 = F2 + v * ws.fstride[2];
+    const double dF = (to64(a0[g0 + 1]) - to64(a0[g0])) * b.idx[0] + (to64(a1[g1 + oy]) - to64(a1[g1])) * b.idx[1] +
+                      (to64(a2[g2 + oz]) - to64(a2[g2])) * b.idx[2];
+    double u = kp.rk_g1 * s.U[v][c] + bdt * (to64(src[v]) - dF);
     if (kp.rk_g0 != 0.0) u += kp.rk_g0 * s.U0[v][c];
     q[v] = u;
   }
-  // con2prim on the updated state; the cell field is the mean of the updated faces
+  // con2prim on the updated state (FP64); the cell field is the mean of the updated faces
+  C2PMet Mc;
+  if (sizeof(R) == sizeof(double)) {
+#pragma unroll
+    for (int t = 0; t < 6; ++t) Mc.g[t] = to64(M.g[t]);
+    Mc.sg = to64(M.sg);
+    Mc.det = to64(M.det);
+  } else {
+    cell_gamma64(b, in64, i, j, k, Mc);
+  }
   double Bn[3];
-  Bn[0] = 0.5 * (s.Bo[0][f0] + s.Bo[0][f0 + 1]);
-  Bn[1] = 0.5 * (s.Bo[1][f1] + s.Bo[1][f1 + sy]);
-  Bn[2] = 0.5 * (s.Bo[2][f2] + s.Bo[2][f2 + sz]);
+  cell_field(b, s.Bo, i, j, k, Bn);
   double wn[5];
   int iters;
-  const int st = con2prim_cell(M, kp, q, Bn, wn, &iters);
+  const int st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     s.Uo[v][c] = q[v];
@@ -300,7 +393,7 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
 }
 
 // ------------------------------------------------------------------------------------------------
-// stand-alone prim2con / con2prim / diagnostics
+// stand-alone prim2con / con2prim / diagnostics (FP64)
 // ------------------------------------------------------------------------------------------------
 struct P2CArgs {
   const double* W[5];
@@ -309,48 +402,38 @@ struct P2CArgs {
   uint8_t* status;
 };
 
-__device__ __forceinline__ void cell_field(const DBlock& b, const double* const* B, int i, int j, int k,
-                                           double Bd[3]) {
-  const long long f0 = b.face[0] + fix(b, 0, i, j, k);
-  const long long f1 = b.face[1] + fix(b, 1, i, j, k);
-  const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-  Bd[0] = 0.5 * (B[0][f0] + B[0][f0 + 1]);
-  Bd[1] = 0.5 * (B[1][f1] + B[1][f1 + b.N[0]]);
-  Bd[2] = 0.5 * (B[2][f2] + B[2][f2 + (long long)b.N[0] * b.N[1]]);
-}
-
-__global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ blocks,
-                                                    const Work* __restrict__ work, MetricView m,
-                                                    P2CArgs a, KParams kp) {
+__global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    const __grid_constant__ InView<double> m,
+                                                    const __grid_constant__ P2CArgs a,
+                                                    const __grid_constant__ KParams kp) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
   int p[3];
-  if (!decode(R_INTERIOR, w, b, p)) return;
+  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
   double val[16];
-  cell_metric(b, m, m.order, p[0], p[1], p[2], 10, val, nullptr);
-  CellMet M;
-  cellmet_from(val, true, M);
+  cell_metric<double>(b, m, m.order, p[0], p[1], p[2], 0, 10, val, nullptr);
+  CellMet<double> M;
+  cellmet_from<double>(val, true, M);
   const long long c = b.cell + cix(b, p[0], p[1], p[2]);
   double wv[5], Bd[3], q[5];
   for (int v = 0; v < 5; ++v) wv[v] = a.W[v][c];
   cell_field(b, a.B, p[0], p[1], p[2], Bd);
-  CellFluid f;
-  cell_fluid(M, kp.gamma_ad, wv, Bd, f);
-  cell_cons(M, f, q);
+  CellFluid<double> f;
+  cell_fluid<double>(M, kp.gamma_ad, wv, Bd, f);
+  cell_cons<double>(M, f, q);
   for (int v = 0; v < 5; ++v) a.U[v][c] = q[v];
 }
 
-__global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ blocks,
-                                                    const Work* __restrict__ work, MetricView m,
-                                                    P2CArgs a, KParams kp) {
+__global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    const __grid_constant__ InView<double> m,
+                                                    const __grid_constant__ P2CArgs a,
+                                                    const __grid_constant__ KParams kp) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
   int p[3];
-  if (!decode(R_INTERIOR, w, b, p)) return;
-  double val[16];
-  cell_metric(b, m, m.order, p[0], p[1], p[2], 10, val, nullptr);
-  CellMet M;
-  cellmet_from(val, true, M);
+  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
+  C2PMet M;
+  cell_gamma64(b, m, p[0], p[1], p[2], M);
   const long long c = b.cell + cix(b, p[0], p[1], p[2]);
   double q[5], Bd[3], wn[5];
   for (int v = 0; v < 5; ++v) q[v] = a.U[v][c];
@@ -368,14 +451,14 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// out: [0] sum D dV, [1] max |divB|, [2] sum |divB| dV, [3] max |B|, [4] sum dV, [5] min dx
-__global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ blocks,
-                                                const Work* __restrict__ work, P2CArgs a, double* out) {
+// out: [0] sum D dV, [1] max |divB|, [2] sum |divB| dV, [3] max |B|, [4] sum dV
+__global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                const __grid_constant__ P2CArgs a, double* out) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
   int p[3];
   double md = 0, dv = 0, mdiv = 0, sdiv = 0, mB = 0;
-  if (decode(R_INTERIOR, w, b, p)) {
+  if (decode<R_INTERIOR, 0>(w, b, p)) {
     const long long c = b.cell + cix(b, p[0], p[1], p[2]);
     dv = b.dx[0] * b.dx[1] * b.dx[2];
     md = a.U[0][c] * dv;
@@ -390,7 +473,6 @@ __global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ block
     sdiv = fabs(div) * dv;
     mB = fmax(fmax(fmax(fabs(bx0), fabs(bx1)), fmax(fabs(by0), fabs(by1))), fmax(fabs(bz0), fabs(bz1)));
   }
-  // warp reductions then one atomic per warp
   for (int o = 16; o > 0; o >>= 1) {
     md += __shfl_down_sync(0xffffffffu, md, o);
     dv += __shfl_down_sync(0xffffffffu, dv, o);
@@ -410,29 +492,69 @@ __global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ block
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
+static InView<double> view64(const MetricView& m, const StateView* s) {
+  InView<double> v;
+  for (int c = 0; c < 16; ++c) v.M[c] = m.v[c];
+  for (int q = 0; q < 5; ++q) v.W[q] = s ? s->W[q] : nullptr;
+  for (int d = 0; d < 3; ++d) v.B[d] = s ? s->B[d] : nullptr;
+  v.order = m.order;
+  v.k_zero = m.k_zero;
+  return v;
+}
+
+static InView<float> view32(const MetricView& m, const Shadow& sh) {
+  InView<float> v;
+  for (int c = 0; c < 16; ++c) v.M[c] = sh.M[c];
+  for (int q = 0; q < 5; ++q) v.W[q] = sh.W[q];
+  for (int d = 0; d < 3; ++d) v.B[d] = sh.B[d];
+  v.order = m.order;
+  v.k_zero = m.k_zero;
+  return v;
+}
+
+static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Shadow& sh, cudaStream_t st) {
+  CastList L;
+  int k = 0;
+  for (int q = 0; q < 5; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
+  for (int d = 0; d < 3; ++d) { L.src[k] = s.B[d]; L.dst[k] = sh.B[d]; L.n[k] = sh.nface[d]; ++k; }
+  const int ncomp = m.k_zero ? 10 : 16;
+  for (int c = 0; c < ncomp; ++c) { L.src[k] = m.v[c]; L.dst[k] = sh.M[c]; L.n[k] = sh.nvert; ++k; }
+  L.count = k;
+  dim3 grid(152 * 2, k);
+  k_cast<<<grid, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
 template <class R>
 static cudaError_t stage_impl(const DBlock* blocks, const Work* const work[R_NREGION],
-                              const int nwork[R_NREGION], const MetricView& m, const StateView& s,
-                              const Workspace& ws, const KParams& kp, cudaStream_t st, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], st);
-  if (nwork[R_CELLS_ALL]) k_cellprep<<<nwork[R_CELLS_ALL], kTile, 0, st>>>(blocks, work[R_CELLS_ALL], m, s, ws, kp);
+                              const int nwork[R_NREGION], const InView<R>& in, const InView<double>& in64,
+                              const StateView& s, const Workspace& ws, const KParams& kp, cudaStream_t st,
+                              cudaEvent_t* ev) {
+  if (nwork[R_CELLS_ALL]) k_cellprep<R><<<nwork[R_CELLS_ALL], kTile, 0, st>>>(blocks, work[R_CELLS_ALL], in, ws);
   if (ev) cudaEventRecord(ev[1], st);
-  if (nwork[R_FACES]) k_faces<R><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], m, s, ws, kp);
+  if (nwork[R_FACES]) k_faces<R><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
   if (ev) cudaEventRecord(ev[2], st);
   if (nwork[R_EDGES]) k_edges<R><<<nwork[R_EDGES], kTile, 0, st>>>(blocks, work[R_EDGES], ws, kp);
   if (ev) cudaEventRecord(ev[3], st);
   if (nwork[R_CTFACES]) k_ct<R><<<nwork[R_CTFACES], kTile, 0, st>>>(blocks, work[R_CTFACES], s, ws, kp);
   if (ev) cudaEventRecord(ev[4], st);
-  if (nwork[R_INTERIOR]) k_update<R><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], m, s, ws, kp);
+  if (nwork[R_INTERIOR]) k_update<R><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
                          const int nwork[R_NREGION], const MetricView& m, const StateView& s,
-                         const Workspace& ws, const KParams& kp, cudaStream_t st, cudaEvent_t* ev) {
-  if (precision == GR_PREC_MIXED) return stage_impl<float>(blocks, work, nwork, m, s, ws, kp, st, ev);
-  return stage_impl<double>(blocks, work, nwork, m, s, ws, kp, st, ev);
+                         const Workspace& ws, const Shadow& sh, const KParams& kp, cudaStream_t st,
+                         cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  const InView<double> in64 = view64(m, &s);
+  if (precision == GR_PREC_MIXED) {
+    cudaError_t e = launch_cast(m, s, sh, st);
+    if (e != cudaSuccess) return e;
+    return stage_impl<float>(blocks, work, nwork, view32(m, sh), in64, s, ws, kp, st, ev);
+  }
+  return stage_impl<double>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev);
 }
 
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
@@ -442,7 +564,7 @@ cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, c
   for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = nullptr;
-  if (nwork) k_prim2con<<<nwork, kTile, 0, st>>>(blocks, work, m, a, kp);
+  if (nwork) k_prim2con<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
@@ -453,7 +575,7 @@ cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, c
   for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = status;
-  if (nwork) k_con2prim<<<nwork, kTile, 0, st>>>(blocks, work, m, a, kp);
+  if (nwork) k_con2prim<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ GR_EMF_UPWIND, GR_EMF_MEAN = 0, 1
 GR_CEIL_CLAMP, GR_CEIL_ATMOSPHERE = 0, 1
 GR_ST_ATM_THRESHOLD, GR_ST_FAILED, GR_ST_W_CLAMPED = 0x01, 0x02, 0x04
 GR_ST_TAU_FLOOR, GR_ST_BD_LIMIT, GR_ST_EOS_CLAMP = 0x08, 0x10, 0x20
+GR_ST_GUESS_REJECTED = 0x40
+GR_GUESS_NONE, GR_GUESS_FP32 = 0, 1
 
 # every symbol include/grstage.h declares
 EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default", "gr_context_create",
@@ -53,7 +55,7 @@ class gr_state(C.Structure):
 
 class gr_params(C.Structure):
     _fields_ = [("size", C.c_uint32), ("recon", C.c_int32), ("precision", C.c_int32), ("emf", C.c_int32),
-                ("ceiling", C.c_int32), ("max_iter", C.c_int32), ("gamma_ad", C.c_double),
+                ("ceiling", C.c_int32), ("max_iter", C.c_int32), ("c2p_guess", C.c_int32), ("gamma_ad", C.c_double),
                 ("rho_atm", C.c_double), ("p_atm", C.c_double), ("f_thr", C.c_double), ("W_max", C.c_double),
                 ("M_max", C.c_double), ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
                 ("rk_g1", C.c_double), ("rk_beta", C.c_double)]

@@ -105,7 +105,7 @@ def test_mixed_precision_error_bounds():
     bi = I.random_block(n=(16, 16, 16), g=3, seed=22, metric_amp=0.02)
     P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
     dt = 0.2 * bi.dx[0]
-    out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED)
+    out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32)
     ref = GH.oracle_stage([bi], P, dt)
     e = GH.compare(out, ref, [bi])
     assert e["W0"] < 1e-6 and e["U0"] < 1e-6, e
@@ -113,6 +113,20 @@ def test_mixed_precision_error_bounds():
     d = O.divb(n, g, bi.dx, out[0]["B"])
     Bmax = max(np.max(np.abs(b)) for b in H.interior_faces(out[0]["B"], n, g))
     assert np.max(np.abs(H.interior(d, n, g))) * bi.dx[0] / Bmax < 1e-14
+
+
+@pytest.mark.parametrize("umax", [0.5, 6.0])
+def test_fp32_presolve_bracket_gives_the_same_root(umax):
+    """con2prim with an FP32 pre-solve proposing the bracket converges to the oracle's root
+    (tight tolerance), and rejects nothing on smooth states."""
+    bi = I.random_block(n=(12, 12, 12), g=3, seed=23, metric_amp=0.05, u_max=umax)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    dt = 0.2 * bi.dx[0]
+    out = GH.gpu_stage([bi], P, dt, c2p_guess=G.GR_GUESS_FP32)
+    ref = GH.oracle_stage([bi], P, dt)
+    check64(out, ref, [bi])
+    st = H.interior(out[0]["status"], bi.n, bi.ng)
+    assert np.mean((st & G.GR_ST_GUESS_REJECTED) != 0) < 0.01
 
 
 def test_invalid_arguments_are_rejected():
