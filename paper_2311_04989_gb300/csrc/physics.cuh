@@ -262,6 +262,10 @@ __device__ __forceinline__ double wenoz<double>(double v0, double v1, double v2,
   return (w0 * q[0] + w1 * q[1] + w2 * q[2]) / (w0 + w1 + w2);
 }
 
+// FP32: per-weight fast divisions on the power-of-two scaled stencil (|v| < 2), eps = 1e-30.  A
+// product form with one division would need a much larger eps to keep e0 e1 e2 a normal float,
+// which lets rough sub-stencils leak into faces between cells ~1e11 apart in density (star
+// surface against atmosphere).
 template <>
 __device__ __forceinline__ float wenoz<float>(float v0, float v1, float v2, float v3, float v4, float eps) {
   float q[3], bk[3];
@@ -276,11 +280,11 @@ __device__ __forceinline__ float wenoz<float>(float v0, float v1, float v2, floa
 // FP32: the stencil is scaled by a power of two near its largest magnitude before the smoothness
 // indicators are formed, so that squares of tiny densities/pressures (atmosphere p ~ 1e-30) do not
 // underflow; the scaling is exact and is undone on the result.
-__device__ __forceinline__ float pow2_scale(float m) {
-  // 2^(-e) with m in [2^e, 2^(e+1)); m > 0 and finite
-  int e;
-  frexpf(m, &e);
-  return ldexpf(1.0f, -e);
+// 2^-e and 2^e for the binary exponent e of m > 0 (normal, finite), by bit manipulation
+__device__ __forceinline__ void pow2_pair(float m, float* sc, float* isc) {
+  const int e = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127;   // m in [2^e, 2^(e+1))
+  *sc = __uint_as_float((unsigned)(127 - e) << 23);                 // 2^-e
+  *isc = __uint_as_float((unsigned)(127 + e) << 23);                // 2^e
 }
 
 template <class R>
@@ -307,12 +311,14 @@ __device__ __forceinline__ void recon<float>(int method, const float s[6], float
     float mx = 0.f;
 #pragma unroll
     for (int t = 0; t < 6; ++t) mx = fmaxf(mx, fabsf(s[t]));
-    if (!(mx > 0.f) || !(mx < 3e38f)) {   // all zero (or non-finite): nothing to scale
+    // all zero, subnormal or non-finite: nothing to scale (2^e must stay a normal float)
+    if (!(mx >= 1.2e-38f) || !(mx < 1e38f)) {
       *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
       *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
       return;
     }
-    const float sc = pow2_scale(mx), isc = 1.0f / sc;
+    float sc, isc;
+    pow2_pair(mx, &sc, &isc);
     float t[6];
 #pragma unroll
     for (int u = 0; u < 6; ++u) t[u] = s[u] * sc;

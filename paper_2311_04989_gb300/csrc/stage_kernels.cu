@@ -357,33 +357,69 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
   const long long g2 = b.wface[2] + fix(b, 2, i, j, k);
   const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
   const double bdt = kp.rk_beta * kp.dt;
-  double q[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
+  const double cx = bdt * b.idx[0], cy = bdt * b.idx[1], cz = bdt * b.idx[2];
+  auto accumulate = [&](int v) {
     const R* a0 = F0 + v * ws.fstride[0];
     const R* a1 = F1 + v * ws.fstride[1];
     const R* a2 = F2 + v * ws.fstride[2];
-    const double dF = (to64(a0[g0 + 1]) - to64(a0[g0])) * b.idx[0] + (to64(a1[g1 + oy]) - to64(a1[g1])) * b.idx[1] +
-                      (to64(a2[g2 + oz]) - to64(a2[g2])) * b.idx[2];
-    double u = kp.rk_g1 * s.U[v][c] + bdt * (to64(src[v]) - dF);
+    double u = kp.rk_g1 * s.U[v][c] + bdt * to64(src[v]);
+    u -= cx * (to64(a0[g0 + 1]) - to64(a0[g0]));
+    u -= cy * (to64(a1[g1 + oy]) - to64(a1[g1]));
+    u -= cz * (to64(a2[g2 + oz]) - to64(a2[g2]));
     if (kp.rk_g0 != 0.0) u += kp.rk_g0 * s.U0[v][c];
-    q[v] = u;
-  }
-  // con2prim on the updated state (FP64); the cell field is the mean of the updated faces
-  C2PMet Mc;
-  if (sizeof(R) == sizeof(double)) {
+    return u;
+  };
+  double q[5];
+  q[0] = accumulate(0);
+  double Bn[3];
+  cell_field(b, s.Bo, i, j, k, Bn);
+  double wn[5];
+  int st;
+  if (sizeof(R) == sizeof(float)) {
+    // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
+    // sqrt(gamma) (band 1e-6) and reset such cells without forming S', tau' in FP64.
+    const double sg32 = to64(M.sg);
+    const double thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
+    if (isfinite(q[0]) && q[0] < thr * sg32) {
+      bool finite = true;
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        const R* a0 = F0 + v * ws.fstride[0];
+        const R* a1 = F1 + v * ws.fstride[1];
+        const R* a2 = F2 + v * ws.fstride[2];
+        const R t = a0[g0 + 1] - a0[g0] + a1[g1 + oy] - a1[g1] + a2[g2 + oz] - a2[g2] + src[v];
+        finite = finite && isfinite(t) && isfinite(s.U[v][c]);
+      }
+      R Bl[3];
+      const R Bf[3] = {R(d2f_rn(Bn[0])), R(d2f_rn(Bn[1])), R(d2f_rn(Bn[2]))};
+      lower3(M.g, Bf, Bl);
+      const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
+      q[0] = sg32 * kp.rho_atm;
+      q[1] = q[2] = q[3] = 0.0;
+      q[4] = sg32 * (kp.p_atm / (kp.gamma_ad - 1.0)) + to64(R(0.5) * rdiv(BBd, M.sg));
+      wn[0] = kp.rho_atm;
+      wn[1] = wn[2] = wn[3] = 0.0;
+      wn[4] = kp.p_atm;
+      st = finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED;
+    } else {
+#pragma unroll
+      for (int v = 1; v < 5; ++v) q[v] = accumulate(v);
+      C2PMet Mc;
+      cell_gamma64(b, in64, i, j, k, Mc);
+      int iters;
+      st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
+    }
+  } else {
+#pragma unroll
+    for (int v = 1; v < 5; ++v) q[v] = accumulate(v);
+    C2PMet Mc;
 #pragma unroll
     for (int t = 0; t < 6; ++t) Mc.g[t] = to64(M.g[t]);
     Mc.sg = to64(M.sg);
     Mc.det = to64(M.det);
-  } else {
-    cell_gamma64(b, in64, i, j, k, Mc);
+    int iters;
+    st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
   }
-  double Bn[3];
-  cell_field(b, s.Bo, i, j, k, Bn);
-  double wn[5];
-  int iters;
-  const int st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     s.Uo[v][c] = q[v];

@@ -115,6 +115,24 @@ def test_mixed_precision_error_bounds():
     assert np.max(np.abs(H.interior(d, n, g))) * bi.dx[0] / Bmax < 1e-14
 
 
+def test_mixed_precision_on_a_star_surface():
+    """The mixed path across the surface of the magnetised star, where a reconstruction stencil spans
+    ~11 decades in density (star against atmosphere): rho within 1e-6 of the FP64 oracle, the same
+    cells set to atmosphere, div B at round-off."""
+    tov = I.solve_tov()
+    bi = I.star_block(n=(32, 32, 32), g=3, half_width=10.02, tov=tov, A_b=0.05)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-10)
+    dt = 0.25 * bi.dx[0]
+    out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32)
+    ref = GH.oracle_stage([bi], P, dt)
+    e = GH.compare(out, ref, [bi])
+    assert e["W0"] < 1e-6 and e["U0"] < 1e-6 and e["status_mismatch"] == 0, e
+    n, g = bi.n, bi.ng
+    d = O.divb(n, g, bi.dx, out[0]["B"])
+    Bmax = max(np.max(np.abs(b)) for b in H.interior_faces(out[0]["B"], n, g))
+    assert np.max(np.abs(H.interior(d, n, g))) * bi.dx[0] / Bmax < 1e-14
+
+
 @pytest.mark.parametrize("umax", [0.5, 6.0])
 def test_fp32_presolve_bracket_gives_the_same_root(umax):
     """con2prim with an FP32 pre-solve proposing the bracket converges to the oracle's root
@@ -124,7 +142,12 @@ def test_fp32_presolve_bracket_gives_the_same_root(umax):
     dt = 0.2 * bi.dx[0]
     out = GH.gpu_stage([bi], P, dt, c2p_guess=G.GR_GUESS_FP32)
     ref = GH.oracle_stage([bi], P, dt)
-    check64(out, ref, [bi])
+    # The iteration path differs from the oracle's (other bracket), so mu agrees to a few ulp; p is
+    # recovered through eps = W (qbar - mu rbar^2) + ..., which cancels by ~W/eps (~1e4 here), so p
+    # is held to 1e-10 and every other variable to 1e-12.
+    e = GH.compare(out, ref, [bi])
+    assert e["W4"] < 1e-10 and e["status_mismatch"] == 0, e
+    assert all(v < TOL64 for k, v in e.items() if k not in ("W4", "status_mismatch")), e
     st = H.interior(out[0]["status"], bi.n, bi.ng)
     assert np.mean((st & G.GR_ST_GUESS_REJECTED) != 0) < 0.01
 
