@@ -164,6 +164,20 @@ int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], cons
 int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4],
             void* stream);
 
+/* gr_diag without any device allocation (the paper has no counterpart: this is a library service).
+ * For callers that cannot call cudaMalloc -- code running inside an application that owns the device
+ * memory pool (its own caching allocator or fixed arena) or in-situ hooks that must not change the
+ * device footprint.  Same outputs as gr_diag, for at most 256 blocks given directly (no gr_mesh):
+ * the block list travels as a kernel parameter and the reduction's scratch is a fixed 33 KB static
+ * device array that every GPU loading the library holds until exit.  The first call on a device looks
+ * up that array's address (cudaGetSymbolAddress; no allocation); make it before any stream capture.
+ * Calls share the array: each call overwrites every slot it reads, but calls whose kernels overlap on
+ * the GPU race and must be serialised by the caller.  nblocks outside [1, 256] gives GR_EINVAL
+ * (detail in gr_noalloc_last_error).  Synchronises the stream. */
+int gr_diag_noalloc(const gr_block* blocks, int32_t nblocks, const double* const U[5],
+                    const double* const B[3], double out[4], void* stream);
+const char* gr_noalloc_last_error(void);
+
 /* Per-kernel timing of gr_stage with CUDA events on the launch stream (measurement only).
  * gr_profile_begin arms the mesh for up to max_stages subsequent gr_stage calls: each records an event
  * before and after each of its GR_NKERNELS kernels (cell prep, faces, edges, CT, update+con2prim).

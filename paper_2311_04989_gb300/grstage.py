@@ -29,7 +29,8 @@ GR_GUESS_NONE, GR_GUESS_FP32 = 0, 1
 # every symbol include/grstage.h declares
 EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default", "gr_context_create",
            "gr_context_destroy", "gr_mesh_create", "gr_mesh_destroy", "gr_mesh_workspace_bytes",
-           "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end"]
+           "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end",
+           "gr_diag_noalloc", "gr_noalloc_last_error"]
 GR_NKERNELS = 5
 KERNEL_NAMES = ["k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
 
@@ -90,6 +91,9 @@ def load(path: str = LIB_PATH):
     L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5, vp,
                               C.POINTER(gr_params), vp]
     L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
+    L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
+                                  C.POINTER(C.c_double), vp]
+    L.gr_noalloc_last_error.restype = C.c_char_p
     L.gr_profile_begin.argtypes = [vp, i32]
     L.gr_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
     for f in EXPORTS:
@@ -171,6 +175,17 @@ def gr_con2prim(mesh, metric: gr_metric, U, B, W, status, params: gr_params, str
 def gr_diag(mesh, U, B, stream=None):
     out = (C.c_double * 4)()
     _check(load().gr_diag(mesh, _ptrs(5, U), _ptrs(3, B), out, _stream(stream)), "gr_diag")
+    return list(out)
+
+
+def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):
+    """gr_diag for at most 256 blocks without any device allocation (see include/grstage.h)."""
+    arr = (gr_block * max(1, len(blocks)))(*blocks)
+    out = (C.c_double * 4)()
+    L = load()
+    rc = L.gr_diag_noalloc(arr, len(blocks), _ptrs(5, U), _ptrs(3, B), out, _stream(stream))
+    if rc != GR_OK:
+        raise GrstageError(f"gr_diag_noalloc: {L.gr_strerror(rc).decode()} ({L.gr_noalloc_last_error().decode()})")
     return list(out)
 
 
