@@ -62,8 +62,9 @@ enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec.
 #define GR_ST_EOS_CLAMP     0x20  /* eps clamped to the EOS range (App. A) */
 #define GR_ST_GUESS_REJECTED 0x40 /* a proposed root bracket showed no sign change: full bracket used */
 
-/* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change). */
-enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1 };
+/* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change):
+ * none, an FP32 pre-solve, or the learned bracket of a small network (gr_mlp_*). */
+enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1, GR_GUESS_MLP = 2 };
 
 /* One MeshBlock: n[] interior cells, ng ghosts, cell widths, and element offsets into the pools. */
 typedef struct {
@@ -117,6 +118,7 @@ typedef struct {
   double tol;           /* relative bracket tolerance (Sec. 3.5: 1e-10) */
   double weno_eps;      /* WENOZ epsilon */
   double rk_g0, rk_g1, rk_beta;   /* U' = g0 U0 + g1 U + beta dt L(U) (Shu-Osher stage) */
+  const float* mlp;     /* device parameter vector of the learned bracket (GR_GUESS_MLP), 16-byte aligned */
 } gr_params;
 
 typedef struct gr_ctx gr_ctx;
@@ -154,15 +156,44 @@ int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5]
                 const double* const B[3], double* const U[5], const gr_params* params, void* stream);
 
 /* Conserved -> primitive on the interior cells (Sec. 3.5, App. A).  U is rewritten where the
- * atmosphere or a limit applies.  status may be NULL. */
+ * atmosphere or a limit applies.  status and evals (the number of FP64 master-function evaluations
+ * per cell) may be NULL. */
 int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
-                double* const W[5], uint8_t* status, const gr_params* params, void* stream);
+                double* const W[5], uint8_t* status, int32_t* evals, const gr_params* params, void* stream);
 
 /* Diagnostics (Eq. Mb, Eq. gausslaw).  out[0] = M_b = sum D dV; out[1] = max |div B| min(dx)/max|B|;
  * out[2] = sum |div B| dV / (max|B| sum dV / min dx); out[3] = max |B| over interior faces.
  * Synchronises the stream. */
 int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4],
             void* stream);
+
+/* ---- learned con2prim bracket (spec pattern; the paper has no counterpart) -------------------
+ * A 4-64-64-1 tanh network predicts log mu at the master-function root from the features
+ * log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2) of the KKC invariants (the reading of
+ * Sec. 3.5's bracketing); con2prim with GR_GUESS_MLP starts at exp(t_hat) and steps outwards by factors
+ * exp(delta 2^k), k = 0..5, until the FP64 master function changes sign, and solves in that bracket;
+ * otherwise it falls back to the full bracket (status GR_ST_GUESS_REJECTED).
+ * Parameter vector: GR_MLP_NPARAM floats, 16-byte aligned device memory:
+ *   [0..3] feature means, [4..7] feature inverse std, [8] target mean, [9] target std,
+ *   [10] first step delta (in log mu), [11..15] unused, [16..] W1 (64x4), b1 (64), W2 (64x64), b2 (64),
+ *   W3 (64), b3 (1), row-major (out, in).  Samples x are rows of 4 floats; targets t are log mu. */
+#define GR_MLP_NPARAM 4561
+int gr_mlp_nparam(void);
+const char* gr_mlp_last_error(void);
+/* Features and log mu of the plain (unguessed) bracketed solve of every interior cell, in the cell-pool
+ * layout; valid = 0 where the cell is not solved or a limit applied. */
+int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[5], const double* const B[3],
+                   const gr_params* params, float* const feats[4], float* target, uint8_t* valid, void* stream);
+/* t[i] = predicted log mu of sample i. */
+int gr_mlp_forward(const float* P, const float* x, int64_t n, float* t, void* stream);
+/* Gradient (4545 floats, the weights after the 16 header entries) and value of the mean loss
+ * (z - zt)^2/2, zt = (t - P[8])/P[9], over n samples; device outputs.  Synchronises the stream. */
+int gr_mlp_grad(const float* P, const float* x, const float* t, int64_t n, float* grad, float* loss, void* stream);
+/* Adam (lr, beta 0.9/0.999) over the samples in order, mini-batches of `batch`, `epochs` passes; updates
+ * the weights of P in place and writes the mean loss of each epoch to the host array losses (may be NULL).
+ * Allocates and frees its own scratch.  Synchronises the stream. */
+int gr_mlp_train(float* P, const float* x, const float* t, int64_t n, int32_t epochs, int32_t batch, float lr,
+                 float* losses, void* stream);
 
 /* gr_diag without any device allocation (the paper has no counterpart: this is a library service).
  * For callers that cannot call cudaMalloc -- code running inside an application that owns the device

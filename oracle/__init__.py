@@ -118,6 +118,10 @@ def lib():
                                          C.c_double, pp, dp, dp, dp, dp, dp, u8, i32]
         L.oracle_stage_block.restype = C.c_int
         L.oracle_divb_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp]
+        L.oracle_c2p_samples.argtypes = [C.c_int, dp, dp, dp, pp, dp, dp, u8]
+        L.oracle_mlp_nparam.restype = C.c_int
+        L.oracle_mlp_forward.argtypes = [dp, dp, C.c_int, dp]
+        L.oracle_mlp_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -305,3 +309,41 @@ def divb(blk_n, ng, dx, B):
     out = np.zeros((blk_n[2] + 2 * ng, blk_n[1] + 2 * ng, blk_n[0] + 2 * ng))
     lib().oracle_divb_block(C.byref(g), _d(B[0]), _d(B[1]), _d(B[2]), _d(out))
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# learned con2prim bracket (FP64 reference of the MLP and its training data)
+# ---------------------------------------------------------------------------------------------
+MLP_H, MLP_IN, MLP_OFF = 64, 4, 16
+MLP_NW = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def c2p_samples(metric, q, Bdens, P: Params):
+    """(features (n,4), log mu at the root (n,), valid (n,) bool) of the bracketed solves."""
+    metric, q, Bdens = _f64(metric), _f64(q), _f64(Bdens)
+    n = q.shape[0]
+    f = np.zeros((n, 4)); t = np.zeros(n); v = np.zeros(n, np.uint8)
+    cp = P.c()
+    lib().oracle_c2p_samples(n, _d(metric), _d(q), _d(Bdens), C.byref(cp), _d(f), _d(t),
+                             v.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return f, t, v.astype(bool)
+
+
+def mlp_nparam():
+    return int(lib().oracle_mlp_nparam())
+
+
+def mlp_forward(P, x):
+    P, x = _f64(P), _f64(x)
+    t = np.zeros(x.shape[0])
+    lib().oracle_mlp_forward(_d(P), _d(x), x.shape[0], _d(t))
+    return t
+
+
+def mlp_loss_grad(P, x, t):
+    """Mean-squared-error loss in normalised units and its gradient w.r.t. the network weights."""
+    P, x, t = _f64(P), _f64(x), _f64(t)
+    g = np.zeros(MLP_NW)
+    L = C.c_double()
+    lib().oracle_mlp_loss_grad(_d(P), _d(x), _d(t), x.shape[0], _d(g), C.byref(L))
+    return L.value, g

@@ -525,7 +525,15 @@ void atmosphere(const oparams& Q, real w[5]) {
 
 // One cell.  q: densitised (D, S_j, tau) in/out (rewritten when limits or atmosphere apply);
 // Bdens: densitised cell-centred B^i; w: prims out.  Returns status bits; *iters = master iterations.
-int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3], real w[5], int* iters) {
+// Invariants and root of the last bracketed solve of con2prim_point (for the learned bracket)
+struct C2PRecord {
+  real q, r2, b2, rb, mu;
+  bool solved;
+};
+
+int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3], real w[5], int* iters,
+                   C2PRecord* rec = nullptr) {
+  if (rec) rec->solved = false;
   int st = 0;
   *iters = 0;
   const real sg = M.sqrtg;
@@ -587,6 +595,7 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     if (r != 0) { st |= 2; atm = true; }
     else {
       const real mu = root;
+      if (rec) { rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->solved = true; }
       c2p_eval(Q, I, mu, E);
       // v^i = mu x (r^i + mu (r.calb) calb^i)
       real v_u[3];
@@ -631,6 +640,143 @@ inline void load16(const double* const* mv, long vi, real m[16]) {
 }
 
 }  // namespace
+
+#ifndef ORACLE_COUNT_FLOPS
+namespace {
+// ------------------------------------------------------------------------------------------------
+// Learned con2prim bracket (not in the paper): features, training target, and a 4-64-64-1 tanh
+// MLP with its mean-squared-error gradient by plain backpropagation, all in FP64.
+//
+// Parameter vector (the layout documented for the library's gr_mlp_* calls):
+//   [0..3] feature means, [4..7] feature inverse standard deviations, [8] target mean,
+//   [9] target standard deviation, [10] bracket half-width in log mu, [11..15] unused,
+//   [16..]  W1 (64 x 4), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
+// Features of a solved cell: log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2 / (r^2 calb^2) (0 if
+// either vanishes); target: log mu at the root.
+// ------------------------------------------------------------------------------------------------
+static const int MLP_H = 64, MLP_IN = 4, MLP_OFF = 16;
+static const int MLP_NW = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+
+void c2p_features(real q, real r2, real b2, real rb, double f[4]) {
+  f[0] = std::log1p(to_d(q));
+  f[1] = std::log1p(to_d(r2));
+  f[2] = std::log1p(to_d(b2));
+  const double den = to_d(r2) * to_d(b2);
+  f[3] = den > 0 ? to_d(rb) * to_d(rb) / den : 0.0;
+}
+
+// z (normalised output) and hidden activations of one sample
+void mlp_forward1(const double* P, const double* x, double h1[64], double h2[64], double* z) {
+  const double* W1 = P + MLP_OFF;
+  const double* b1 = W1 + MLP_H * MLP_IN;
+  const double* W2 = b1 + MLP_H;
+  const double* b2 = W2 + MLP_H * MLP_H;
+  const double* W3 = b2 + MLP_H;
+  const double* b3 = W3 + MLP_H;
+  double xn[4];
+  for (int j = 0; j < 4; ++j) xn[j] = (x[j] - P[j]) * P[4 + j];
+  for (int i = 0; i < MLP_H; ++i) {
+    double a = b1[i];
+    for (int j = 0; j < MLP_IN; ++j) a += W1[i * MLP_IN + j] * xn[j];
+    h1[i] = std::tanh(a);
+  }
+  for (int i = 0; i < MLP_H; ++i) {
+    double a = b2[i];
+    for (int j = 0; j < MLP_H; ++j) a += W2[i * MLP_H + j] * h1[j];
+    h2[i] = std::tanh(a);
+  }
+  double a = b3[0];
+  for (int j = 0; j < MLP_H; ++j) a += W3[j] * h2[j];
+  *z = a;
+}
+
+}  // namespace
+
+extern "C" {
+// Features and log(mu) of the bracketed con2prim solve at np points (valid[n] = 0 when the cell was
+// not solved: atmosphere, failure).
+void oracle_c2p_samples(int np, const double* metric, const double* q, const double* Bdens, const oparams* Q,
+                        double* feats, double* target, uint8_t* valid) {
+  for (int n = 0; n < np; ++n) {
+    PM M;
+    pm_from16(metric + 16 * n, M);
+    real qq[5], w[5];
+    for (int v = 0; v < 5; ++v) qq[v] = q[5 * n + v];
+    int it;
+    C2PRecord rec;
+    con2prim_point(M, *Q, qq, Bdens + 3 * n, w, &it, &rec);
+    valid[n] = rec.solved ? 1 : 0;
+    if (rec.solved) {
+      c2p_features(rec.q, rec.r2, rec.b2, rec.rb, feats + 4 * n);
+      target[n] = std::log(rec.mu);
+    } else {
+      for (int j = 0; j < 4; ++j) feats[4 * n + j] = 0;
+      target[n] = 0;
+    }
+  }
+}
+
+int oracle_mlp_nparam(void) { return MLP_OFF + MLP_NW; }
+
+// Predicted log(mu) at n feature vectors
+void oracle_mlp_forward(const double* P, const double* x, int n, double* t) {
+  double h1[64], h2[64], z;
+  for (int s = 0; s < n; ++s) {
+    mlp_forward1(P, x + 4 * s, h1, h2, &z);
+    t[s] = P[8] + P[9] * z;
+  }
+}
+
+// loss = mean over samples of (z - zt)^2 / 2 with zt = (t - P[8]) / P[9]; grad (MLP_NW) with respect
+// to the network weights (the normalisation entries are constants)
+void oracle_mlp_loss_grad(const double* P, const double* x, const double* t, int n, double* grad, double* loss) {
+  const double* W2 = P + MLP_OFF + MLP_H * MLP_IN + MLP_H;
+  const double* W3 = W2 + MLP_H * MLP_H + MLP_H;
+  double* gW1 = grad;
+  double* gb1 = gW1 + MLP_H * MLP_IN;
+  double* gW2 = gb1 + MLP_H;
+  double* gb2 = gW2 + MLP_H * MLP_H;
+  double* gW3 = gb2 + MLP_H;
+  double* gb3 = gW3 + MLP_H;
+  for (int k = 0; k < MLP_NW; ++k) grad[k] = 0;
+  double L = 0;
+  for (int s = 0; s < n; ++s) {
+    const double* xs = x + 4 * s;
+    double h1[64], h2[64], z;
+    mlp_forward1(P, xs, h1, h2, &z);
+    const double zt = (t[s] - P[8]) / P[9];
+    const double dz = (z - zt) / n;
+    L += 0.5 * (z - zt) * (z - zt) / n;
+    double xn[4];
+    for (int j = 0; j < 4; ++j) xn[j] = (xs[j] - P[j]) * P[4 + j];
+    // output layer
+    double g2[64];
+    for (int j = 0; j < MLP_H; ++j) {
+      gW3[j] += dz * h2[j];
+      g2[j] = dz * W3[j] * (1 - h2[j] * h2[j]);
+    }
+    gb3[0] += dz;
+    // second hidden layer
+    double g1[64];
+    for (int j = 0; j < MLP_H; ++j) g1[j] = 0;
+    for (int i = 0; i < MLP_H; ++i) {
+      gb2[i] += g2[i];
+      for (int j = 0; j < MLP_H; ++j) {
+        gW2[i * MLP_H + j] += g2[i] * h1[j];
+        g1[j] += W2[i * MLP_H + j] * g2[i];
+      }
+    }
+    // first hidden layer
+    for (int i = 0; i < MLP_H; ++i) {
+      const double gi = g1[i] * (1 - h1[i] * h1[i]);
+      gb1[i] += gi;
+      for (int j = 0; j < MLP_IN; ++j) gW1[i * MLP_IN + j] += gi * xn[j];
+    }
+  }
+  *loss = L;
+}
+}  // extern "C"
+#endif
 
 #ifdef ORACLE_COUNT_FLOPS
 OpCount g_ops;

@@ -309,7 +309,10 @@ static int check_params(const gr_params* p) {
   if (p->emf != GR_EMF_UPWIND && p->emf != GR_EMF_MEAN) return fail(GR_EINVAL, "bad emf");
   if (p->ceiling != GR_CEIL_CLAMP && p->ceiling != GR_CEIL_ATMOSPHERE) return fail(GR_EINVAL, "bad ceiling");
   if (p->max_iter < 1 || p->max_iter > 10000) return fail(GR_EINVAL, "max_iter out of range");
-  if (p->c2p_guess != GR_GUESS_NONE && p->c2p_guess != GR_GUESS_FP32) return fail(GR_EINVAL, "bad c2p_guess");
+  if (p->c2p_guess != GR_GUESS_NONE && p->c2p_guess != GR_GUESS_FP32 && p->c2p_guess != GR_GUESS_MLP)
+    return fail(GR_EINVAL, "bad c2p_guess");
+  if (p->c2p_guess == GR_GUESS_MLP && (!p->mlp || (((uintptr_t)p->mlp) & 15u)))
+    return fail(GR_EINVAL, "GR_GUESS_MLP needs a 16-byte aligned device parameter vector in params.mlp");
   if (!(p->gamma_ad > 1.0) || !(p->W_max >= 1.0) || !(p->M_max > 0) || !(p->tol > 0) ||
       !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0))
     return fail(GR_EINVAL, "physical parameter out of range");
@@ -324,6 +327,7 @@ static KParams kparams(const gr_params* p, double dt) {
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
   k.dt = dt;
+  k.mlp = p->c2p_guess == GR_GUESS_MLP ? p->mlp : nullptr;
   return k;
 }
 
@@ -403,7 +407,7 @@ int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5]
 }
 
 int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
-                double* const W[5], uint8_t* status, const gr_params* params, void* stream) {
+                double* const W[5], uint8_t* status, int32_t* evals, const gr_params* params, void* stream) {
   if (!mesh || !W || !B || !U) return fail(GR_EINVAL, "gr_con2prim: NULL argument");
   int r = check_params(params);
   if (r) return r;
@@ -416,8 +420,29 @@ int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], cons
   if (mesh->nblocks == 0) return GR_OK;
   DeviceGuard g(mesh->ctx->device);
   cudaError_t e = launch_con2prim(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U,
-                                  B, W, status, kparams(params, 0.0), (cudaStream_t)stream);
+                                  B, W, status, evals, kparams(params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_con2prim launch");
+  return GR_OK;
+}
+
+int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[5], const double* const B[3],
+                   const gr_params* params, float* const feats[4], float* target, uint8_t* valid, void* stream) {
+  if (!mesh || !U || !B || !feats || !target || !valid) return fail(GR_EINVAL, "gr_c2p_samples: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  MetricView mv;
+  if ((r = metric_view(metric, mv, false))) return r;
+  for (int v = 0; v < 5; ++v)
+    if (!U[v]) return fail(GR_EINVAL, "gr_c2p_samples: NULL array");
+  for (int j = 0; j < 4; ++j)
+    if (!feats[j]) return fail(GR_EINVAL, "gr_c2p_samples: NULL feature array");
+  for (int d = 0; d < 3; ++d)
+    if (!B[d]) return fail(GR_EINVAL, "gr_c2p_samples: NULL face array");
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  cudaError_t e = launch_c2p_samples(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U, B,
+                                     feats, target, valid, kparams(params, 0.0), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_c2p_samples launch");
   return GR_OK;
 }
 

@@ -83,6 +83,7 @@ struct KParams {   // gr_params flattened for the device
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
   double dt;
+  const float* mlp;   // learned-bracket parameters (GR_GUESS_MLP) or nullptr
 };
 
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
@@ -97,7 +98,10 @@ cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, c
                             const KParams& kp, cudaStream_t st);
 cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             double* const U[5], const double* const B[3], double* const W[5],
-                            uint8_t* status, const KParams& kp, cudaStream_t st);
+                            uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st);
+cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+                               const double* const U[5], const double* const B[3], float* const feats[4],
+                               float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
 cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const double* const U[5],
                         const double* const B[3], double* dev_out /* 4 + scratch */, cudaStream_t st);
 

@@ -1,0 +1,71 @@
+// mlp.cuh -- the learned con2prim bracket (spec pattern; the paper has no counterpart).
+//
+// A 4-64-64-1 tanh network maps features of the KKC invariants of a cell to the logarithm of the
+// master-function root mu = 1/(hW).  Con2prim starts its bracket search there and accepts a bracket
+// only where the FP64 master function changes sign.
+//
+// Parameter vector (float, GR_MLP_NPARAM entries, documented in include/grstage.h):
+//   [0..3] feature means, [4..7] feature inverse standard deviations, [8] target mean,
+//   [9] target standard deviation, [10] first bracket step delta in log mu, [11..15] unused,
+//   [16..]  W1 (64 x 4), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace grs {
+
+constexpr int kMlpH = 64, kMlpIn = 4, kMlpOff = 16;
+constexpr int kMlpNW = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;   // 4545
+constexpr int kMlpN = kMlpOff + kMlpNW;                                              // 4561
+constexpr int kW1 = kMlpOff, kB1 = kW1 + kMlpH * kMlpIn, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
+              kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH;
+
+// Features of the KKC invariants: log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2)
+__device__ __forceinline__ void c2p_features(double q, double r2, double b2, double rb, float f[4]) {
+  f[0] = (float)log1p(q);
+  f[1] = (float)log1p(r2);
+  f[2] = (float)log1p(b2);
+  const double den = r2 * b2;
+  f[3] = den > 0.0 ? (float)(rb * rb / den) : 0.f;
+}
+
+// First hidden layer of a normalised input (registers; fully unrolled)
+__device__ __forceinline__ void mlp_layer1(const float* __restrict__ P, const float x[4], float h1[kMlpH]) {
+  float xn[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) xn[j] = (x[j] - __ldg(P + j)) * __ldg(P + 4 + j);
+#pragma unroll
+  for (int i = 0; i < kMlpH; ++i) {
+    float a = __ldg(P + kB1 + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a = fmaf(__ldg(P + kW1 + i * 4 + j), xn[j], a);
+    h1[i] = tanhf(a);
+  }
+}
+
+// Pre-activation of second-layer unit i from h1 (row i of W2 read as float4)
+__device__ __forceinline__ float mlp_row2(const float* __restrict__ P, int i, const float h1[kMlpH]) {
+  const float4* row = reinterpret_cast<const float4*>(P + kW2 + i * kMlpH);
+  float a = __ldg(P + kB2 + i);
+#pragma unroll
+  for (int j4 = 0; j4 < kMlpH / 4; ++j4) {
+    const float4 w = __ldg(row + j4);
+    a = fmaf(w.x, h1[4 * j4 + 0], a);
+    a = fmaf(w.y, h1[4 * j4 + 1], a);
+    a = fmaf(w.z, h1[4 * j4 + 2], a);
+    a = fmaf(w.w, h1[4 * j4 + 3], a);
+  }
+  return a;
+}
+
+// Normalised network output z (the prediction of log mu is P[8] + P[9] z).  Kept out of line so
+// that the con2prim kernel carries one compact copy.
+static __device__ __noinline__ float mlp_z(const float* __restrict__ P, const float x[4]) {
+  float h1[kMlpH];
+  mlp_layer1(P, x, h1);
+  float z = __ldg(P + kB3);
+  for (int i = 0; i < kMlpH; ++i) z = fmaf(__ldg(P + kW3 + i), tanhf(mlp_row2(P, i, h1)), z);
+  return z;
+}
+
+}  // namespace grs

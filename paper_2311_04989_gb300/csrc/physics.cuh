@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "mlp.cuh"
 
 namespace grs {
 
@@ -668,14 +669,22 @@ __device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<d
   return root;
 }
 
+// Invariants and root of a bracketed solve (training samples for the learned bracket)
+struct C2PRecord {
+  double q, r2, b2, rb, mu;
+  bool solved;
+};
+
 // Full con2prim of one cell.  q: densitised conserved (in/out), Bd: densitised cell field.
 // guess: GR_GUESS_NONE (bracket (0, mu+]) or GR_GUESS_FP32 (an FP32 pre-solve proposes a bracket of
 // relative half-width 2e-5 around its root; it is used only if the FP64 master function changes
 // sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set).
 __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, double q[5],
-                                             const double Bd[3], double w[5], int* iters) {
+                                             const double Bd[3], double w[5], int* iters,
+                                             C2PRecord* rec = nullptr) {
   int st = 0;
   *iters = 0;
+  if (rec) rec->solved = false;
   bool finite = isfinite(q[0]) && isfinite(q[4]);
   for (int i = 0; i < 3; ++i) finite = finite && isfinite(q[1 + i]) && isfinite(Bd[i]);
   // atmosphere threshold; values within 1e-12 relative of it count as having reached it
@@ -715,15 +724,50 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     I.b2 = BB * iD;
     const double gam = P.gamma_ad, vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
     C2PVal<double> E;
-    auto fm = [&](double mu) { c2p_master<double>(gam, vmax2, I, mu, E); return E.f; };
+    int nevals = 0;   // FP64 master-function evaluations (reported through *iters)
+    auto fm = [&](double mu) { ++nevals; c2p_master<double>(gam, vmax2, I, mu, E); return E.f; };
     double root = 0.0, hi;
     int r = -1;
+    int it_master = 0;
     if (P.c2p_guess == GR_GUESS_FP32) {
       const double mu32 = (double)c2p_presolve32(P, I);
       if (mu32 > 0.0) {
         const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), 1.0);
         const double flo = fm(lo), fup = fm(up);
-        if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, iters);
+        if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, &it_master);
+      }
+      if (r != 0) st |= GR_ST_GUESS_REJECTED;
+    } else if (P.c2p_guess == GR_GUESS_MLP && P.mlp) {
+      // learned bracket: start at the network's prediction mu_hat of the root and step outwards
+      // geometrically (factor exp(delta 2^k), k = 0..5) in the direction the sign of f points,
+      // until f changes sign; that bracket, verified by the sign change, goes to the Illinois solve
+      float f[4];
+      c2p_features(I.q, I.r2, I.b2, I.rb, f);
+      const float th = __ldg(P.mlp + 8) + __ldg(P.mlp + 9) * mlp_z(P.mlp, f);
+      const double dl = (double)__ldg(P.mlp + 10);
+      double m0 = fmin((double)__expf(th), 1.0);
+      if (m0 > 0.0) {
+        double f0 = fm(m0);
+        if (f0 == 0.0) {
+          root = m0;
+          r = 0;
+        } else {
+          const double dir = f0 < 0.0 ? 1.0 : -1.0;   // f < 0 below the root
+          double step = dl;
+          for (int k = 0; k < 6 && r != 0; ++k, step *= 2.0) {
+            const double m1 = fmin(m0 * exp(dir * step), 1.0);
+            if (!(m1 > 0.0) || m1 == m0) break;
+            const double f1 = fm(m1);
+            if ((f1 < 0.0) != (f0 < 0.0) || f1 == 0.0) {
+              const double a = fmin(m0, m1), bnd = fmax(m0, m1);
+              const double fa = (a == m0) ? f0 : f1, fb = (a == m0) ? f1 : f0;
+              r = illinois<double>(fm, a, bnd, fa, fb, P.tol, P.max_iter, &root, &hi, &it_master);
+              break;
+            }
+            m0 = m1;
+            f0 = f1;
+          }
+        }
       }
       if (r != 0) st |= GR_ST_GUESS_REJECTED;
     }
@@ -739,13 +783,15 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       const double f0 = fm(0.0);
       double fp = fm(mup);
       if ((f0 < 0.0) == (fp < 0.0) && mup < 1.0) { mup = 1.0; fp = fm(mup); }
-      r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, iters);
+      r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, &it_master);
     }
+    *iters = nevals;
     if (r != 0) {
       st |= GR_ST_FAILED;
       atm = true;
     } else {
       const double mu = root;
+      if (rec) { rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->solved = true; }
       c2p_master<double>(gam, vmax2, I, mu, E);
       double vu[3];
       for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);

@@ -436,6 +436,7 @@ struct P2CArgs {
   const double* B[3];
   double* U[5];
   uint8_t* status;
+  int32_t* evals;
 };
 
 __global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
@@ -474,13 +475,51 @@ __global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ b
   double q[5], Bd[3], wn[5];
   for (int v = 0; v < 5; ++v) q[v] = a.U[v][c];
   cell_field(b, a.B, p[0], p[1], p[2], Bd);
-  int iters;
+  int iters = 0;
   const int st = con2prim_cell(M, kp, q, Bd, wn, &iters);
   for (int v = 0; v < 5; ++v) {
     a.U[v][c] = q[v];
     const_cast<double*>(a.W[v])[c] = wn[v];
   }
   if (a.status) a.status[c] = (uint8_t)st;
+  if (a.evals) a.evals[c] = iters;
+}
+
+// Training samples of the learned bracket: features and log(mu) of the plain bracketed solve of each
+// interior cell (valid = 0 where the cell is not solved: atmosphere, limits, failure)
+struct SampleArgs {
+  const double* U[5];
+  const double* B[3];
+  float* feats[4];
+  float* target;
+  uint8_t* valid;
+};
+
+__global__ void __launch_bounds__(kTile) k_c2p_samples(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                       const __grid_constant__ InView<double> m,
+                                                       const __grid_constant__ SampleArgs a,
+                                                       const __grid_constant__ KParams kp) {
+  const Work w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  int p[3];
+  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
+  C2PMet M;
+  cell_gamma64(b, m, p[0], p[1], p[2], M);
+  const long long c = b.cell + cix(b, p[0], p[1], p[2]);
+  double q[5], Bd[3], wn[5];
+  for (int v = 0; v < 5; ++v) q[v] = a.U[v][c];
+  cell_field(b, a.B, p[0], p[1], p[2], Bd);
+  KParams k = kp;
+  k.c2p_guess = GR_GUESS_NONE;
+  int iters;
+  C2PRecord rec;
+  const int st = con2prim_cell(M, k, q, Bd, wn, &iters, &rec);
+  const bool ok = rec.solved && (st & (GR_ST_BD_LIMIT | GR_ST_TAU_FLOOR)) == 0;
+  a.valid[c] = ok ? 1 : 0;
+  float f[4] = {0.f, 0.f, 0.f, 0.f};
+  if (ok) c2p_features(rec.q, rec.r2, rec.b2, rec.rb, f);
+  for (int j = 0; j < 4; ++j) a.feats[j][c] = f[j];
+  a.target[c] = ok ? (float)log(rec.mu) : 0.f;
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
@@ -600,18 +639,33 @@ cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, c
   for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = nullptr;
+  a.evals = nullptr;
   if (nwork) k_prim2con<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             double* const U[5], const double* const B[3], double* const W[5],
-                            uint8_t* status, const KParams& kp, cudaStream_t st) {
+                            uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st) {
   P2CArgs a;
   for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = status;
+  a.evals = evals;
   if (nwork) k_con2prim<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+                               const double* const U[5], const double* const B[3], float* const feats[4],
+                               float* target, uint8_t* valid, const KParams& kp, cudaStream_t st) {
+  SampleArgs a;
+  for (int v = 0; v < 5; ++v) a.U[v] = U[v];
+  for (int d = 0; d < 3; ++d) a.B[d] = B[d];
+  for (int j = 0; j < 4; ++j) a.feats[j] = feats[j];
+  a.target = target;
+  a.valid = valid;
+  if (nwork) k_c2p_samples<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
@@ -621,6 +675,7 @@ cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const
   for (int v = 0; v < 5; ++v) { a.W[v] = nullptr; a.U[v] = const_cast<double*>(U[v]); }
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = nullptr;
+  a.evals = nullptr;
   cudaError_t e = cudaMemsetAsync(dev_out, 0, 8 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   if (nwork) k_diag<<<nwork, kTile, 0, st>>>(blocks, work, a, dev_out);

@@ -24,13 +24,15 @@ GR_CEIL_CLAMP, GR_CEIL_ATMOSPHERE = 0, 1
 GR_ST_ATM_THRESHOLD, GR_ST_FAILED, GR_ST_W_CLAMPED = 0x01, 0x02, 0x04
 GR_ST_TAU_FLOOR, GR_ST_BD_LIMIT, GR_ST_EOS_CLAMP = 0x08, 0x10, 0x20
 GR_ST_GUESS_REJECTED = 0x40
-GR_GUESS_NONE, GR_GUESS_FP32 = 0, 1
+GR_GUESS_NONE, GR_GUESS_FP32, GR_GUESS_MLP = 0, 1, 2
 
 # every symbol include/grstage.h declares
 EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default", "gr_context_create",
            "gr_context_destroy", "gr_mesh_create", "gr_mesh_destroy", "gr_mesh_workspace_bytes",
            "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end",
-           "gr_diag_noalloc", "gr_noalloc_last_error"]
+           "gr_diag_noalloc", "gr_noalloc_last_error", "gr_mlp_nparam", "gr_mlp_last_error", "gr_c2p_samples",
+           "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train"]
+GR_MLP_NPARAM = 4561
 GR_NKERNELS = 5
 KERNEL_NAMES = ["k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
 
@@ -59,7 +61,7 @@ class gr_params(C.Structure):
                 ("ceiling", C.c_int32), ("max_iter", C.c_int32), ("c2p_guess", C.c_int32), ("gamma_ad", C.c_double),
                 ("rho_atm", C.c_double), ("p_atm", C.c_double), ("f_thr", C.c_double), ("W_max", C.c_double),
                 ("M_max", C.c_double), ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
-                ("rk_g1", C.c_double), ("rk_beta", C.c_double)]
+                ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("mlp", C.c_void_p)]
 
 
 _lib = None
@@ -88,12 +90,19 @@ def load(path: str = LIB_PATH):
     L.gr_stage.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params), vp]
     L.gr_prim2con.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5,
                               C.POINTER(gr_params), vp]
-    L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5, vp,
+    L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5, vp, vp,
                               C.POINTER(gr_params), vp]
     L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
     L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
                                   C.POINTER(C.c_double), vp]
     L.gr_noalloc_last_error.restype = C.c_char_p
+    L.gr_mlp_nparam.restype = C.c_int
+    L.gr_mlp_last_error.restype = C.c_char_p
+    L.gr_c2p_samples.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.POINTER(gr_params),
+                                 C.c_void_p * 4, vp, vp, vp]
+    L.gr_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.gr_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
+    L.gr_mlp_train.argtypes = [vp, vp, vp, C.c_int64, i32, i32, C.c_float, C.POINTER(C.c_float), vp]
     L.gr_profile_begin.argtypes = [vp, i32]
     L.gr_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
     for f in EXPORTS:
@@ -166,9 +175,10 @@ def gr_prim2con(mesh, metric: gr_metric, W, B, U, params: gr_params, stream=None
                               _stream(stream)), "gr_prim2con")
 
 
-def gr_con2prim(mesh, metric: gr_metric, U, B, W, status, params: gr_params, stream=None):
+def gr_con2prim(mesh, metric: gr_metric, U, B, W, status, params: gr_params, stream=None, evals=None):
     st = int(status.data_ptr()) if status is not None else 0
-    _check(load().gr_con2prim(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), _ptrs(5, W), st,
+    ev = int(evals.data_ptr()) if evals is not None else 0
+    _check(load().gr_con2prim(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), _ptrs(5, W), st, ev,
                               C.byref(params), _stream(stream)), "gr_con2prim")
 
 
@@ -187,6 +197,41 @@ def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):
     if rc != GR_OK:
         raise GrstageError(f"gr_diag_noalloc: {L.gr_strerror(rc).decode()} ({L.gr_noalloc_last_error().decode()})")
     return list(out)
+
+
+def _mcheck(rc, what):
+    if rc != GR_OK:
+        L = load()
+        raise GrstageError(f"{what}: {L.gr_strerror(rc).decode()} ({L.gr_mlp_last_error().decode()})")
+
+
+def gr_c2p_samples(mesh, metric: gr_metric, U, B, params: gr_params, feats, target, valid, stream=None):
+    _check(load().gr_c2p_samples(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), C.byref(params), _ptrs(4, feats),
+                                 int(target.data_ptr()), int(valid.data_ptr()), _stream(stream)), "gr_c2p_samples")
+
+
+def gr_mlp_forward(P, x, stream=None):
+    import torch
+    t = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _mcheck(load().gr_mlp_forward(int(P.data_ptr()), int(x.data_ptr()), x.shape[0], int(t.data_ptr()),
+                                  _stream(stream)), "gr_mlp_forward")
+    return t
+
+
+def gr_mlp_grad(P, x, t, stream=None):
+    import torch
+    g = torch.empty(GR_MLP_NPARAM - 16, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _mcheck(load().gr_mlp_grad(int(P.data_ptr()), int(x.data_ptr()), int(t.data_ptr()), x.shape[0],
+                               int(g.data_ptr()), int(loss.data_ptr()), _stream(stream)), "gr_mlp_grad")
+    return float(loss.item()), g
+
+
+def gr_mlp_train(P, x, t, epochs, batch=16384, lr=1e-3, stream=None):
+    losses = (C.c_float * epochs)()
+    _mcheck(load().gr_mlp_train(int(P.data_ptr()), int(x.data_ptr()), int(t.data_ptr()), x.shape[0], int(epochs),
+                                int(batch), float(lr), losses, _stream(stream)), "gr_mlp_train")
+    return list(losses)
 
 
 def gr_profile_begin(mesh, max_stages: int):
@@ -272,3 +317,23 @@ def state_struct(U, U0, B, B0, W, Uo, Bo, Wo, status) -> gr_state:
         s.Bo[d] = int(Bo[d].data_ptr())
     s.status = int(status.data_ptr())
     return s
+
+
+def pack_blocks(blocks, device="cuda"):
+    """Device pools (torch) of a list of blocks with numpy arrays W (5,...), B [3], metric (16,...).
+    Returns (layout, W pool, [B pools], metric pool)."""
+    import torch
+    L = Layout.of(blocks)
+    W = np.zeros((5, max(L.ncell, 1)))
+    M = np.zeros((16, max(L.nvert, 1)))
+    Bp = [np.zeros(max(L.nface[d], 1)) for d in range(3)]
+    for b, bi in enumerate(blocks):
+        w = np.asarray(bi.W).reshape(5, -1)
+        W[:, L.cell_off[b]:L.cell_off[b] + w.shape[1]] = w
+        m = np.asarray(bi.metric).reshape(16, -1)
+        M[:, L.vert_off[b]:L.vert_off[b] + m.shape[1]] = m
+        for d in range(3):
+            f = np.asarray(bi.B[d]).ravel()
+            Bp[d][L.face_off[b, d]:L.face_off[b, d] + f.size] = f
+    to = lambda a: torch.from_numpy(a).to(device)
+    return L, to(W), [to(x) for x in Bp], to(M)
