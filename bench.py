@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim bracket-guess timings")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -318,6 +319,75 @@ def main():
     ms_head = results[head]["ms"]
     value = cells * world / (ms_head / 1e3)
 
+    # ---- the same stage replayed as a CUDA graph ------------------------------------------------
+    graph_ms = None
+    if head == "mixed":
+        pg = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        gph = G.gr_graph_capture(mesh, metric, state, dt, pg)
+        for _ in range(a.warmup):
+            G.gr_graph_launch(gph, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            G.gr_graph_launch(gph, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / a.steps
+        G.gr_graph_destroy(gph)
+
+    # ---- con2prim with and without a proposed bracket on the stage's output ------------------
+    c2p = None
+    if not a.no_c2p:
+        from paper_2311_04989_gb300 import learned_bracket as LB
+        p64 = G.gr_params_default(recon=G.GR_RECON_WENOZ, gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm,
+                                  tol=1e-10)
+        Uref = snap[head][2]
+        Bref = snap[head][1]
+        # training samples: the solves of this workload's stage output ("prior solves" of the run)
+        feats = [torch.zeros(L.ncell, dtype=torch.float32, device=dev) for _ in range(4)]
+        tgt = torch.zeros(L.ncell, dtype=torch.float32, device=dev)
+        val = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
+        G.gr_c2p_samples(mesh, metric, list(Uref), Bref, p64, feats, tgt, val, stream)
+        xs, ts = LB.samples_from(feats, tgt, val)
+        t_train = time.time()
+        Pm, losses, delta = LB.train(xs, ts, epochs=20, batch=1024, lr=2e-3)
+        t_train = time.time() - t_train
+        c2p = {"training_samples": int(xs.shape[0]), "mlp_train_s": round(t_train, 2), "mlp_first_step": delta,
+               "mlp_loss_first_last": [losses[0], losses[-1]]}
+        interior = torch.zeros(L.ncell, dtype=torch.bool, device=dev)
+        g_ = mesh_in.ng
+        for b in range(len(geoms)):
+            N = mesh_in.n + 2 * g_
+            m = torch.zeros((N, N, N), dtype=torch.bool, device=dev)
+            m[g_:N - g_, g_:N - g_, g_:N - g_] = True
+            interior[int(L.cell_off[b]):int(L.cell_off[b]) + N ** 3] = m.view(-1)
+        for name, guess in (("none", G.GR_GUESS_NONE), ("fp32", G.GR_GUESS_FP32), ("mlp", G.GR_GUESS_MLP)):
+            pc = G.gr_params_default(recon=G.GR_RECON_WENOZ, gamma_ad=2.0, rho_atm=mesh_in.rho_atm,
+                                     p_atm=mesh_in.p_atm, tol=1e-10, c2p_guess=guess)
+            pc.mlp = int(Pm.data_ptr())
+            Uc = Uref.clone(); Wc = torch.zeros_like(W)
+            stc = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
+            ev = torch.zeros(L.ncell, dtype=torch.int32, device=dev)
+            for _ in range(a.warmup):
+                Uc.copy_(Uref)
+                G.gr_con2prim(mesh, metric, list(Uc), Bref, list(Wc), stc, pc, stream, evals=ev)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(a.steps):
+                Uc.copy_(Uref)
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                G.gr_con2prim(mesh, metric, list(Uc), Bref, list(Wc), stc, pc, stream, evals=ev)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            solved = ((stc.to(torch.int32) & 0x3F) == 0) & interior
+            c2p[name] = {"ms": tot / a.steps, "fp64_evals_per_solved_cell": float(ev[solved].double().mean().item()),
+                         "solved_cells": int(solved.sum().item()),
+                         "rejected": int(((stc.to(torch.int32) & 64) != 0).sum().item())}
+
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None
     if not a.no_e2e:
@@ -400,7 +470,7 @@ def main():
                "sample": f"{nblk} seeded-random blocks of the same workload, FP64 oracle stage, "
                          f"{nthreads} threads, {wall:.1f} s"}
 
-    launches = a.steps * 5
+    launches = a.steps * (6 if head == "mixed" else 5)     # the mixed path adds the FP32 cast kernel
     fp64 = None
     if "fp64" in results and head != "fp64":
         fp64 = {"value": cells * world / (results["fp64"]["ms"] / 1e3), "ms_per_step": results["fp64"]["ms"],
@@ -416,6 +486,7 @@ def main():
            "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
+           "graph_ms_per_step": graph_ms, "con2prim_guess": c2p,
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -150,6 +150,16 @@ int64_t gr_mesh_workspace_bytes(const gr_mesh* mesh);
 int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
              const gr_params* params, void* stream);
 
+/* CUDA graph of one stage: the stage's launches on `stream` captured once, with all arguments (arrays,
+ * dt, params) baked in, and replayed by gr_graph_launch on any stream.  One graph per distinct stage
+ * (RK sub-stage coefficients, buffers, dt); the mesh must outlive the graph.  Profiling events are
+ * not recorded inside a graph. */
+typedef struct gr_graph gr_graph;
+int gr_graph_capture(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                     const gr_params* params, gr_graph** graph);
+int gr_graph_launch(gr_graph* graph, void* stream);
+int gr_graph_destroy(gr_graph* graph);
+
 /* Primitive -> conserved (Eq. consB_def) on the interior cells of every block, with the cell-centred
  * field taken as the mean of the two densitised faces. */
 int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5],

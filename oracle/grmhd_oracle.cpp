@@ -544,10 +544,10 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     Bu[i] = Bdens[i] / sg;
     finite = finite && std::isfinite(S[i]) && std::isfinite(Bu[i]);
   }
-  // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A).  Values within 1e-12 relative of it
-  // count as having reached it, so cells that sit at the atmosphere density up to rounding are
-  // reset deterministically.
-  const real rho_thr = Q.f_thr * Q.rho_atm * (1 + 1e-12);
+  // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A).  Values within 1e-6 relative of it
+  // count as having reached it, so cells that sit at the atmosphere density up to rounding (or up
+  // to an FP32 sqrt(gamma)) are reset deterministically.
+  const real rho_thr = Q.f_thr * Q.rho_atm * (1 + 1e-6);
   bool atm = false;
   if (!finite) { st |= 2; atm = true; }
   else if (D < rho_thr) { st |= 1; atm = true; }

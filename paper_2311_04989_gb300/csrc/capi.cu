@@ -344,8 +344,60 @@ static int metric_view(const gr_metric* metric, MetricView& mv, bool need_K) {
   return GR_OK;
 }
 
+struct gr_graph {
+  int device;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                      const gr_params* params, void* stream, bool allow_profile);
+
 int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
              const gr_params* params, void* stream) {
+  return stage_impl(mesh, metric, state, dt, params, stream, true);
+}
+
+int gr_graph_capture(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                     const gr_params* params, gr_graph** graph) {
+  if (!mesh || !graph) return fail(GR_EINVAL, "gr_graph_capture: NULL argument");
+  DeviceGuard g(mesh->ctx->device);
+  cudaStream_t st;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(st); return cuda_fail(e, "cudaStreamBeginCapture"); }
+  const int r = stage_impl(mesh, metric, state, dt, params, st, false);
+  cudaGraph_t gr = nullptr;
+  e = cudaStreamEndCapture(st, &gr);
+  cudaStreamDestroy(st);
+  if (r != GR_OK) { if (gr) cudaGraphDestroy(gr); return r; }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, gr, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(gr); return cuda_fail(e, "cudaGraphInstantiate"); }
+  *graph = new gr_graph{mesh->ctx->device, gr, ex};
+  return GR_OK;
+}
+
+int gr_graph_launch(gr_graph* graph, void* stream) {
+  if (!graph) return fail(GR_EINVAL, "gr_graph_launch: NULL graph");
+  DeviceGuard g(graph->device);
+  cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int gr_graph_destroy(gr_graph* graph) {
+  if (!graph) return GR_OK;
+  DeviceGuard g(graph->device);
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  delete graph;
+  return GR_OK;
+}
+
+static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                      const gr_params* params, void* stream, bool allow_profile) {
   if (!mesh || !state) return fail(GR_EINVAL, "gr_stage: NULL argument");
   int r = check_params(params);
   if (r) return r;
@@ -378,7 +430,7 @@ int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, doub
   const Work* work[R_NREGION];
   for (int k = 0; k < R_NREGION; ++k) work[k] = mesh->d_work[k];
   cudaEvent_t* ev = nullptr;
-  if (mesh->prof_used < mesh->prof_capacity)
+  if (allow_profile && mesh->prof_used < mesh->prof_capacity)
     ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
   cudaError_t e = launch_stage(params->precision, mesh->d_blocks, work, mesh->nwork, mv, s, mesh->ws,
                                mesh->sh, kparams(params, dt), (cudaStream_t)stream, ev);

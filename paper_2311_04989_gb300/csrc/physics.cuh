@@ -687,8 +687,8 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
   if (rec) rec->solved = false;
   bool finite = isfinite(q[0]) && isfinite(q[4]);
   for (int i = 0; i < 3; ++i) finite = finite && isfinite(q[1 + i]) && isfinite(Bd[i]);
-  // atmosphere threshold; values within 1e-12 relative of it count as having reached it
-  const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-12);
+  // atmosphere threshold; values within 1e-6 relative of it count as having reached it
+  const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-6);
   bool atm = false;
   if (!finite) { st |= GR_ST_FAILED; atm = true; }
   else if (q[0] < rho_thr * M.sg) { st |= GR_ST_ATM_THRESHOLD; atm = true; }   // D~ < rho_thr

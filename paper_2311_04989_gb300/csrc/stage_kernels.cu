@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
   int st;
   if (sizeof(R) == sizeof(float)) {
     // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
-    // sqrt(gamma) (band 1e-6) and reset such cells without forming S', tau' in FP64.
+    // sqrt(gamma) (same 1e-6 band as the FP64 test) and reset such cells without forming S', tau'
+    // in FP64.
     const double sg32 = to64(M.sg);
     const double thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
     if (isfinite(q[0]) && q[0] < thr * sg32) {

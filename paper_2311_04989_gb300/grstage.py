@@ -31,7 +31,8 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_context_destroy", "gr_mesh_create", "gr_mesh_destroy", "gr_mesh_workspace_bytes",
            "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end",
            "gr_diag_noalloc", "gr_noalloc_last_error", "gr_mlp_nparam", "gr_mlp_last_error", "gr_c2p_samples",
-           "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train"]
+           "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
+           "gr_graph_destroy"]
 GR_MLP_NPARAM = 4561
 GR_NKERNELS = 5
 KERNEL_NAMES = ["k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
@@ -103,6 +104,10 @@ def load(path: str = LIB_PATH):
     L.gr_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.gr_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
     L.gr_mlp_train.argtypes = [vp, vp, vp, C.c_int64, i32, i32, C.c_float, C.POINTER(C.c_float), vp]
+    L.gr_graph_capture.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params),
+                                   C.POINTER(vp)]
+    L.gr_graph_launch.argtypes = [vp, vp]
+    L.gr_graph_destroy.argtypes = [vp]
     L.gr_profile_begin.argtypes = [vp, i32]
     L.gr_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
     for f in EXPORTS:
@@ -197,6 +202,21 @@ def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):
     if rc != GR_OK:
         raise GrstageError(f"gr_diag_noalloc: {L.gr_strerror(rc).decode()} ({L.gr_noalloc_last_error().decode()})")
     return list(out)
+
+
+def gr_graph_capture(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_params):
+    h = C.c_void_p()
+    _check(load().gr_graph_capture(mesh, C.byref(metric), C.byref(state), float(dt), C.byref(params), C.byref(h)),
+           "gr_graph_capture")
+    return h
+
+
+def gr_graph_launch(graph, stream=None):
+    _check(load().gr_graph_launch(graph, _stream(stream)), "gr_graph_launch")
+
+
+def gr_graph_destroy(graph):
+    load().gr_graph_destroy(graph)
 
 
 def _mcheck(rc, what):

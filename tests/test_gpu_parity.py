@@ -152,6 +152,37 @@ def test_fp32_presolve_bracket_gives_the_same_root(umax):
     assert np.mean((st & G.GR_ST_GUESS_REJECTED) != 0) < 0.01
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_the_direct_stage_bitwise(precision):
+    import torch
+    bi = I.random_block(n=(12, 12, 12), g=3, seed=24, metric_amp=0.02)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-12)
+    U = H.cons_from_prims(bi, P)
+    pools = GH.Pools([bi])
+    Ud, Wd, Bd, Md = pools.cells([U], 5), pools.cells([bi.W], 5), pools.faces([bi.B]), pools.verts([bi.metric])
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    metric = G.metric_struct(Md)
+    gp = GH.gr_params_from(P, precision, G.GR_GUESS_FP32 if precision else G.GR_GUESS_NONE)
+    outs = []
+    for use_graph in (False, True):
+        Uo, Wo, Bo = Ud.clone(), Wd.clone(), [b.clone() for b in Bd]
+        st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+        state = G.state_struct(Ud, Ud, Bd, Bd, Wd, Uo, Bo, Wo, st)
+        if use_graph:
+            g = G.gr_graph_capture(mesh, metric, state, 0.01, gp)
+            G.gr_graph_launch(g, torch.cuda.current_stream())
+            G.gr_graph_launch(g, torch.cuda.current_stream())    # replays are idempotent
+            torch.cuda.synchronize()
+            G.gr_graph_destroy(g)
+        else:
+            G.gr_stage(mesh, metric, state, 0.01, gp, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+        outs.append([Uo.cpu(), Wo.cpu(), st.cpu()] + [b.cpu() for b in Bo])
+    G.gr_mesh_destroy(mesh)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 def test_invalid_arguments_are_rejected():
     import torch
     bi = I.uniform_block(n=(4, 4, 4), g=2)
