@@ -433,7 +433,7 @@ def main():
     def ph_flops(*names):
         return sum(ph[n]["add"] + ph[n]["mul"] + ph[n]["div"] + ph[n]["sqrt"] for n in names)
 
-    kernel_phases = {"k_cellprep": ("cell_metric_and_field", "cell_efield"), "k_faces": ("faces",),
+    kernel_phases = {"k_cast": (), "k_cellprep": ("cell_metric_and_field", "cell_efield"), "k_faces": ("faces",),
                      "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources", "con2prim")}
     scale = (a.nb ** 3) / 4096.0
 

@@ -221,10 +221,11 @@ const char* gr_noalloc_last_error(void);
 
 /* Per-kernel timing of gr_stage with CUDA events on the launch stream (measurement only).
  * gr_profile_begin arms the mesh for up to max_stages subsequent gr_stage calls: each records an event
- * before and after each of its GR_NKERNELS kernels (cell prep, faces, edges, CT, update+con2prim).
+ * before and after each of its GR_NKERNELS kernels (FP32 input cast of the mixed path, cell prep, faces,
+ * edges, CT, update+con2prim; the FP64 path launches no cast and its first entry is ~0).
  * gr_profile_end synchronises on the last event and returns, per kernel, the summed milliseconds in
  * ms[GR_NKERNELS] and the number of profiled stages in *nstages; it disarms the mesh. */
-#define GR_NKERNELS 5
+#define GR_NKERNELS 6
 int gr_profile_begin(gr_mesh* mesh, int32_t max_stages);
 int gr_profile_end(gr_mesh* mesh, double* ms, int32_t* nstages);
 

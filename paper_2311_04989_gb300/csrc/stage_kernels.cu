@@ -607,15 +607,15 @@ static cudaError_t stage_impl(const DBlock* blocks, const Work* const work[R_NRE
                               const StateView& s, const Workspace& ws, const KParams& kp, cudaStream_t st,
                               cudaEvent_t* ev) {
   if (nwork[R_CELLS_ALL]) k_cellprep<R><<<nwork[R_CELLS_ALL], kTile, 0, st>>>(blocks, work[R_CELLS_ALL], in, ws);
-  if (ev) cudaEventRecord(ev[1], st);
-  if (nwork[R_FACES]) k_faces<R><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
   if (ev) cudaEventRecord(ev[2], st);
-  if (nwork[R_EDGES]) k_edges<R><<<nwork[R_EDGES], kTile, 0, st>>>(blocks, work[R_EDGES], ws, kp);
+  if (nwork[R_FACES]) k_faces<R><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
   if (ev) cudaEventRecord(ev[3], st);
-  if (nwork[R_CTFACES]) k_ct<R><<<nwork[R_CTFACES], kTile, 0, st>>>(blocks, work[R_CTFACES], s, ws, kp);
+  if (nwork[R_EDGES]) k_edges<R><<<nwork[R_EDGES], kTile, 0, st>>>(blocks, work[R_EDGES], ws, kp);
   if (ev) cudaEventRecord(ev[4], st);
-  if (nwork[R_INTERIOR]) k_update<R><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
+  if (nwork[R_CTFACES]) k_ct<R><<<nwork[R_CTFACES], kTile, 0, st>>>(blocks, work[R_CTFACES], s, ws, kp);
   if (ev) cudaEventRecord(ev[5], st);
+  if (nwork[R_INTERIOR]) k_update<R><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
+  if (ev) cudaEventRecord(ev[6], st);
   return cudaGetLastError();
 }
 
@@ -628,8 +628,10 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const 
   if (precision == GR_PREC_MIXED) {
     cudaError_t e = launch_cast(m, s, sh, st);
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
     return stage_impl<float>(blocks, work, nwork, view32(m, sh), in64, s, ws, kp, st, ev);
   }
+  if (ev) cudaEventRecord(ev[1], st);
   return stage_impl<double>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev);
 }
 

@@ -34,8 +34,8 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
            "gr_graph_destroy"]
 GR_MLP_NPARAM = 4561
-GR_NKERNELS = 5
-KERNEL_NAMES = ["k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
+GR_NKERNELS = 6
+KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
 
 
 class GrstageError(RuntimeError):
