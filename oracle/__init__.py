@@ -57,13 +57,38 @@ class OGeom(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("ng", C.c_int32), ("dx", C.c_double * 3)]
 
 
+class OTable(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("pad_", C.c_int32), ("x0", C.c_double * 3), ("dx", C.c_double * 3),
+                ("lp", C.POINTER(C.c_double)), ("le", C.POINTER(C.c_double)), ("cs2", C.POINTER(C.c_double))]
+
+
 class OParams(C.Structure):
     _fields_ = [("gamma_ad", C.c_double), ("rho_atm", C.c_double), ("p_atm", C.c_double),
                 ("f_thr", C.c_double), ("W_max", C.c_double), ("M_max", C.c_double),
                 ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
                 ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("max_iter", C.c_int32),
                 ("recon", C.c_int32), ("emf", C.c_int32), ("ceiling", C.c_int32),
-                ("interp_order", C.c_int32), ("pad_", C.c_int32)]
+                ("interp_order", C.c_int32), ("pad_", C.c_int32),
+                ("eos", C.c_int32), ("pad2_", C.c_int32), ("T_atm", C.c_double), ("Ye_atm", C.c_double),
+                ("h0", C.c_double), ("table", C.POINTER(OTable))]
+
+
+def otable(tab) -> OTable:
+    """C view of an EOS table object (attributes n, x0, dx, lp, le, cs2 with lp/le/cs2 float64 arrays
+    of shape (n_Ye, n_T, n_rho)); the arrays are kept alive on the returned struct."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (tab.lp, tab.le, tab.cs2)]
+    for a in arrs:
+        assert a.shape == (tab.n[2], tab.n[1], tab.n[0])
+    t = OTable((C.c_int32 * 3)(*tab.n), 0, (C.c_double * 3)(*tab.x0), (C.c_double * 3)(*tab.dx),
+               *(a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs))
+    t._keep = arrs
+    return t
+
+
+def table_hmin(tab) -> float:
+    """Minimum specific enthalpy (e + p)/rho over the table's nodes."""
+    t = otable(tab)
+    return float(lib().oracle_table_hmin(C.byref(t)))
 
 
 @dataclass
@@ -86,12 +111,37 @@ class Params:
     emf: int = 0                    # 0 upwinded corner average, 1 plain mean
     ceiling: int = 0                # 0 clamp W, 1 atmosphere
     interp_order: int = 2
+    table: object = None            # EOS table (Sec. 2.3); None -> ideal gas
+    T_atm: float = 1e-6             # atmosphere temperature (table)
+    Ye_atm: float = 0.5             # atmosphere electron fraction (table)
+
+    @property
+    def eos(self) -> int:
+        return 0 if self.table is None else 1
+
+    @property
+    def nw(self) -> int:            # primitives per point
+        return 7 if self.table is not None else 5
+
+    @property
+    def nq(self) -> int:            # conserved per point
+        return 6 if self.table is not None else 5
 
     def c(self) -> OParams:
         p_atm = self.p_atm if self.p_atm is not None else self.K_poly * self.rho_atm ** self.gamma_ad
-        return OParams(self.gamma_ad, self.rho_atm, p_atm, self.f_thr, self.W_max, self.M_max,
-                       self.tol, self.weno_eps, self.rk_g0, self.rk_g1, self.rk_beta,
-                       self.max_iter, self.recon, self.emf, self.ceiling, self.interp_order, 0)
+        o = OParams(self.gamma_ad, self.rho_atm, p_atm, self.f_thr, self.W_max, self.M_max,
+                    self.tol, self.weno_eps, self.rk_g0, self.rk_g1, self.rk_beta,
+                    self.max_iter, self.recon, self.emf, self.ceiling, self.interp_order, 0)
+        if self.table is not None:
+            t = otable(self.table)
+            h0 = getattr(self.table, "_oracle_h0", None)
+            if h0 is None:
+                h0 = float(lib().oracle_table_hmin(C.byref(t)))
+                self.table._oracle_h0 = h0
+            o.eos, o.T_atm, o.Ye_atm, o.h0 = 1, self.T_atm, self.Ye_atm, h0
+            o.table = C.pointer(t)
+            o._keep = t
+        return o
 
 
 _lib = None
@@ -122,6 +172,9 @@ def lib():
         L.oracle_mlp_nparam.restype = C.c_int
         L.oracle_mlp_forward.argtypes = [dp, dp, C.c_int, dp]
         L.oracle_mlp_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp, dp]
+        L.oracle_table_eval.argtypes = [C.c_int, pp, dp, dp, dp, dp]
+        L.oracle_table_hmin.argtypes = [C.POINTER(OTable)]
+        L.oracle_table_hmin.restype = C.c_double
         _lib = L
     return _lib
 
@@ -139,21 +192,24 @@ def _f64(a) -> np.ndarray:
 # pointwise entries
 # ---------------------------------------------------------------------------------------------
 def prim2con(metric, prims, Bdens, P: Params):
-    """Eq. consB_def at points.  metric (n,16), prims (n,5), Bdens (n,3) -> q (n,5)."""
+    """Eq. consB_def at points.  metric (n,16), prims (n,5), Bdens (n,3) -> q (n,5); with a table
+    prims (n,7) = (rho, u~^i, p, Y_e, T; T unread) -> q (n,6)."""
     metric, prims, Bdens = _f64(metric), _f64(prims), _f64(Bdens)
     n = prims.shape[0]
-    q = np.zeros((n, 5))
+    assert prims.shape[1] == P.nw
+    q = np.zeros((n, P.nq))
     cp = P.c()
     lib().oracle_prim2con(n, _d(metric), _d(prims), _d(Bdens), C.byref(cp), _d(q))
     return q
 
 
 def con2prim(metric, q, Bdens, P: Params):
-    """Con2prim at points.  Returns (prims (n,5), q_out (n,5), status (n,), iterations (n,))."""
+    """Con2prim at points.  Returns (prims (n,nw), q_out (n,nq), status (n,), iterations (n,))."""
     metric, Bdens = _f64(metric), _f64(Bdens)
     q = _f64(q).copy()
     n = q.shape[0]
-    w = np.zeros((n, 5))
+    assert q.shape[1] == P.nq
+    w = np.zeros((n, P.nw))
     st = np.zeros(n, np.uint8)
     it = np.zeros(n, np.int32)
     cp = P.c()
@@ -174,10 +230,11 @@ def flux_points(d, metric, prims, Bdens, P: Params):
 
 
 def face_flux(d, metric, wL, BL, wR, BR, P: Params):
-    """HLLE flux (n,7) at faces from left/right states."""
+    """HLLE flux (n,7) at faces from left/right states; with a table (n,8), the D Y_e flux last."""
     metric, wL, BL, wR, BR = map(_f64, (metric, wL, BL, wR, BR))
     n = wL.shape[0]
-    F = np.zeros((n, 7))
+    assert wL.shape[1] == P.nw
+    F = np.zeros((n, 8 if P.table is not None else 7))
     cp = P.c()
     lib().oracle_face_flux(n, d, _d(metric), _d(wL), _d(BL), _d(wR), _d(BR), C.byref(cp), _d(F))
     return F
@@ -314,15 +371,17 @@ def divb(blk_n, ng, dx, B):
 # ---------------------------------------------------------------------------------------------
 # learned con2prim bracket (FP64 reference of the MLP and its training data)
 # ---------------------------------------------------------------------------------------------
-MLP_H, MLP_IN, MLP_OFF = 64, 4, 16
+MLP_H, MLP_IN, MLP_OFF = 64, 6, 16
 MLP_NW = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+MLP_MEAN, MLP_ISTD, MLP_TMEAN, MLP_TSTD, MLP_STEP = 0, 6, 12, 13, 14
 
 
 def c2p_samples(metric, q, Bdens, P: Params):
-    """(features (n,4), log mu at the root (n,), valid (n,) bool) of the bracketed solves."""
+    """(features (n,6), log mu at the root (n,), valid (n,) bool) of the bracketed solves."""
     metric, q, Bdens = _f64(metric), _f64(q), _f64(Bdens)
     n = q.shape[0]
-    f = np.zeros((n, 4)); t = np.zeros(n); v = np.zeros(n, np.uint8)
+    assert q.shape[1] == P.nq
+    f = np.zeros((n, MLP_IN)); t = np.zeros(n); v = np.zeros(n, np.uint8)
     cp = P.c()
     lib().oracle_c2p_samples(n, _d(metric), _d(q), _d(Bdens), C.byref(cp), _d(f), _d(t),
                              v.ctypes.data_as(C.POINTER(C.c_uint8)))
@@ -347,3 +406,16 @@ def mlp_loss_grad(P, x, t):
     L = C.c_double()
     lib().oracle_mlp_loss_grad(_d(P), _d(x), _d(t), x.shape[0], _d(g), C.byref(L))
     return L.value, g
+
+
+# ---------------------------------------------------------------------------------------------
+# tabulated EOS lookups (Sec. 2.3)
+# ---------------------------------------------------------------------------------------------
+def table_eval(P: Params, rho, T, ye):
+    """(p, eps, c_s^2) at (rho, T, Y_e) from the table and the temperature recovered from (rho, p, Y_e)."""
+    rho, T, ye = _f64(rho), _f64(T), _f64(ye)
+    n = rho.shape[0]
+    out = np.zeros((n, 4))
+    cp = P.c()
+    lib().oracle_table_eval(n, C.byref(cp), _d(rho), _d(T), _d(ye), _d(out))
+    return out[:, 0], out[:, 1], out[:, 2], out[:, 3]

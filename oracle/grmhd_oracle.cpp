@@ -14,6 +14,8 @@
 //   metric components: 0 alpha, 1..3 beta^i, 4..9 gamma_{xx,xy,xz,yy,yz,zz}, 10..15 K_ij (same order)
 //   primitives w = (rho, u~^x, u~^y, u~^z, p)                      (Sec. 2.1, after Eq. hydsrc_def)
 //   conserved  q = (D, S_x, S_y, S_z, tau), B^k densitised          (Eq. consB_def)
+//   tabulated EOS (Sec. 2.3): w = (rho, u~^i, p, Y_e, T), q = (D, S_j, tau, D Y_e); the thermodynamic
+//   state of a point is (rho, p, Y_e), T is derived from it (an output of con2prim).
 //
 // Functions whose result has no independent pin say "parity unpinned" in their comment; the pins
 // live in tests/test_oracle_*.py.
@@ -60,7 +62,26 @@ typedef struct {
   int32_t ceiling;   // 0 clamp W (App. A), 1 atmosphere (Sec. 3.6)
   int32_t interp_order;  // 2 or 4
   int32_t pad_;
+  // tabulated EOS (Sec. 2.3); eos = 0 ideal gas (the fields below unused), 1 table
+  int32_t eos;
+  int32_t pad2_;
+  double T_atm;      // atmosphere temperature (App. A)
+  double Ye_atm;     // atmosphere electron fraction (reading: a parameter)
+  double h0;         // minimum enthalpy of the table (from oracle_table_hmin)
+  const struct otable_* table;
 } oparams;
+
+// EOS table (Sec. 2.3): log p, log e (e = rho(1 + eps)) and c_s^2 on a uniform grid in
+// (log rho, log T, Y_e), natural logarithms (the base does not change a linear interpolant).
+typedef struct otable_ {
+  int32_t n[3];       // nodes along log rho, log T, Y_e
+  int32_t pad_;
+  double x0[3];       // first node of each axis
+  double dx[3];       // node spacing of each axis
+  const double* lp;   // node (ir, iT, iy) at index (iy * n[1] + iT) * n[0] + ir
+  const double* le;
+  const double* cs2;
+} otable;
 
 }  // extern "C"
 
@@ -145,10 +166,108 @@ inline real eos_p(const oparams& Q, real rho, real eps) { return (Q.gamma_ad - 1
 inline real eos_cs2(const oparams& Q, real rho, real p, real h) { return Q.gamma_ad * p / (rho * h); }
 
 // ------------------------------------------------------------------------------------------------
+// Tabulated EOS (Sec. 2.3): trilinear interpolation of log p, log e and c_s^2 in (log rho, log T,
+// Y_e).  Values outside the table are moved to the nearest permissible value (App. A).  These
+// lookups work in double (the operation-counting build does not count them).
+// ------------------------------------------------------------------------------------------------
+// Cell index i in [0, n-2] and fraction w in [0, 1] of x on axis ax; clamps x into the axis range.
+void tab_axis(const otable& T, int ax, double x, int* i, double* w, bool* clamped) {
+  const double lo = T.x0[ax], hi = T.x0[ax] + (T.n[ax] - 1) * T.dx[ax];
+  if (!(x >= lo)) { x = lo; *clamped = true; }   // also catches NaN
+  if (x > hi) { x = hi; *clamped = true; }
+  const double sx = (x - lo) / T.dx[ax];
+  int k = (int)std::floor(sx);
+  if (k > T.n[ax] - 2) k = T.n[ax] - 2;
+  if (k < 0) k = 0;
+  *i = k;
+  *w = sx - k;
+}
+inline long tab_idx(const otable& T, int ir, int iT, int iy) {
+  return ((long)iy * T.n[1] + iT) * T.n[0] + ir;
+}
+// Trilinear interpolant of f at the point with cell indices i[3] and fractions w[3]
+double tab_tri(const otable& T, const double* f, const int i[3], const double w[3]) {
+  double s = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+    const double wt = (a ? w[0] : 1 - w[0]) * (b ? w[1] : 1 - w[1]) * (e ? w[2] : 1 - w[2]);
+    s += wt * f[tab_idx(T, i[0] + a, i[1] + b, i[2] + e)];
+  }
+  return s;
+}
+// Interpolant of f at T node k (bilinear in log rho, Y_e)
+double tab_at_T_node(const otable& T, const double* f, const int i[3], const double w[3], int k) {
+  double s = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int a = c & 1, e = (c >> 1) & 1;
+    s += (a ? w[0] : 1 - w[0]) * (e ? w[2] : 1 - w[2]) * f[tab_idx(T, i[0] + a, k, i[2] + e)];
+  }
+  return s;
+}
+// log T at which the interpolant of f (log e or log p, increasing in T) equals y at the (log rho, Y_e)
+// of i, w (the nested temperature root of App. A).  Between T nodes the interpolant is linear in
+// log T, so the root lies on the node interval where the node values cross y and is found there in
+// closed form; y outside the values at the table's T ends gives that end (clamped).
+double tab_inverse_T(const otable& T, const double* f, const int i[3], const double w[3], double y,
+                     bool* clamped) {
+  const int nT = T.n[1];
+  const double g0 = tab_at_T_node(T, f, i, w, 0), gN = tab_at_T_node(T, f, i, w, nT - 1);
+  if (!(y > g0)) { if (y < g0 || !(y == y)) *clamped = true; return T.x0[1]; }
+  if (y >= gN) { if (y > gN) *clamped = true; return T.x0[1] + (nT - 1) * T.dx[1]; }
+  double gk = g0;
+  for (int k = 0; k < nT - 1; ++k) {
+    const double gk1 = tab_at_T_node(T, f, i, w, k + 1);
+    if (gk <= y && y <= gk1) return T.x0[1] + T.dx[1] * (k + (y - gk) / (gk1 - gk));
+    gk = gk1;
+  }
+  return T.x0[1] + (nT - 1) * T.dx[1];   // not reached for a table increasing in T
+}
+
+// Thermodynamics of a point from (rho, p, Y_e): eps, h, c_s^2 and T.  Ideal gas: T = p/rho.
+struct Thermo {
+  real eps, h, cs2, T;
+  bool clamped;
+};
+void eos_from_rho_p(const oparams& Q, real rho, real p, real ye, Thermo& t) {
+  t.clamped = false;
+  if (Q.eos == 0) {
+    t.eps = eos_eps(Q, rho, p);
+    t.h = 1 + t.eps + p / rho;
+    t.cs2 = eos_cs2(Q, rho, p, t.h);
+    t.T = p / rho;
+    return;
+  }
+  const otable& T = *Q.table;
+  int i[3];
+  double w[3];
+  tab_axis(T, 0, std::log(to_d(rho)), &i[0], &w[0], &t.clamped);
+  tab_axis(T, 2, to_d(ye), &i[2], &w[2], &t.clamped);
+  const double lT = tab_inverse_T(T, T.lp, i, w, std::log(to_d(p)), &t.clamped);
+  tab_axis(T, 1, lT, &i[1], &w[1], &t.clamped);
+  const double e = std::exp(tab_tri(T, T.le, i, w));
+  t.eps = real(e) / rho - 1;
+  t.h = (real(e) + p) / rho;
+  t.cs2 = tab_tri(T, T.cs2, i, w);
+  t.T = std::exp(lT);
+}
+// Pressure and eps at (rho, T, Y_e) from the table (atmosphere and temperature floor)
+void eos_table_rho_T(const oparams& Q, real rho, real Tt, real ye, real* p, real* eps) {
+  const otable& T = *Q.table;
+  int i[3];
+  double w[3];
+  bool cl = false;
+  tab_axis(T, 0, std::log(to_d(rho)), &i[0], &w[0], &cl);
+  tab_axis(T, 1, std::log(to_d(Tt)), &i[1], &w[1], &cl);
+  tab_axis(T, 2, to_d(ye), &i[2], &w[2], &cl);
+  *p = std::exp(tab_tri(T, T.lp, i, w));
+  *eps = std::exp(tab_tri(T, T.le, i, w)) / rho - 1;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Fluid and field at a point: the kinematics of Sec. 2.1 and the comoving field of Sec. 2.2
 // ------------------------------------------------------------------------------------------------
 struct FP {
-  real rho, p, eps, h, W;
+  real rho, p, eps, h, W, ye, T, cs2;
   real ut_u[3], ut_d[3];   // u~^i, u~_i
   real v_u[3], v_d[3];     // v^i = u~^i / W
   real vt_u[3];            // v~^i = v^i - beta^i/alpha
@@ -157,10 +276,11 @@ struct FP {
   real b0, b_u[3], b_d[3], b2;
 };
 
-// w = (rho, u~^i, p); Bdens = densitised B^i
-void fluid_point(const PM& M, const oparams& Q, const real w[5], const real Bdens[3], FP& F) {
+// w = (rho, u~^i, p[, Y_e]); Bdens = densitised B^i
+void fluid_point(const PM& M, const oparams& Q, const real w[], const real Bdens[3], FP& F) {
   F.rho = w[0];
   F.p = w[4];
+  F.ye = Q.eos ? w[5] : real(0);
   for (int i = 0; i < 3; ++i) F.ut_u[i] = w[1 + i];
   real uu = 0;
   for (int i = 0; i < 3; ++i) {
@@ -174,8 +294,12 @@ void fluid_point(const PM& M, const oparams& Q, const real w[5], const real Bden
     F.v_d[i] = F.ut_d[i] / F.W;
     F.vt_u[i] = F.v_u[i] - M.beta[i] / M.alpha;
   }
-  F.eps = eos_eps(Q, F.rho, F.p);
-  F.h = 1 + F.eps + F.p / F.rho;
+  Thermo th;
+  eos_from_rho_p(Q, F.rho, F.p, F.ye, th);
+  F.eps = th.eps;
+  F.h = th.h;
+  F.cs2 = th.cs2;
+  F.T = th.T;
   // B^k = sqrt(gamma) calB^k  (Eq. consB_def)
   for (int i = 0; i < 3; ++i) {
     F.Bd_u[i] = Bdens[i];
@@ -207,6 +331,11 @@ void cons_from_fp(const PM& M, const FP& F, real q[5]) {
   for (int j = 0; j < 3; ++j) q[1 + j] = sg * (eb * F.W * F.ut_d[j] - ab0 * F.b_d[j]);
   q[4] = sg * (eb * F.W * F.W - F.rho * F.W - (F.p + 0.5 * F.b2) - ab0 * ab0);
 }
+// All conserved variables of the EOS: with a table also D Y_e (Sec. 2.3)
+void cons_all(const oparams& Q, const PM& M, const FP& F, real q[]) {
+  cons_from_fp(M, F, q);
+  if (Q.eos) q[5] = q[0] * F.ye;
+}
 
 // Fluxes in direction d, Eq. fluxB_def.  Fq = (D, S_j, tau) rows; Fb[0], Fb[1] = induction flux of
 // B^{t1}, B^{t2} with t1 = (d+1)%3, t2 = (d+2)%3:  F^d_{B^k} = alpha (B^k v~^d - B^d v~^k).
@@ -226,7 +355,8 @@ void flux_from_fp(const PM& M, const FP& F, const real q[5], int d, real Fq[5], 
 // c^2 = cs^2 + cA^2 - cs^2 cA^2, cA^2 = b^2/(rho h + b^2), and the 3+1 closed form
 // lam = alpha [v^d (1-c^2) +- c sqrt((1-v^2)(gamma^dd (1 - v^2 c^2) - v^d v^d (1-c^2)))]/(1-v^2c^2) - beta^d
 void speeds_from_fp(const PM& M, const oparams& Q, const FP& F, int d, real* lm, real* lp) {
-  const real cs2 = eos_cs2(Q, F.rho, F.p, F.h);
+  (void)Q;
+  const real cs2 = F.cs2;
   const real ca2 = F.b2 / (F.rho * F.h + F.b2);
   const real c2 = cs2 + ca2 - cs2 * ca2;
   real v2 = 0;
@@ -256,9 +386,12 @@ void hlle(int nv, const real* UL, const real* UR, const real* FL, const real* FR
 }
 
 // Face flux from two primitive states at one face (shared by the stage and the point entry).
-// wL/wR: prims; BL/BR: densitised B^i of the two states (same normal component).
-void face_flux(const PM& M, const oparams& Q, int d, const real wL[5], const real BL[3],
-               const real wR[5], const real BR[3], real Fq[5], real Fb[2]) {
+// wL/wR: prims; BL/BR: densitised B^i of the two states (same normal component).  With a table,
+// Fq[5] is the D Y_e flux: the HLLE D flux times the electron fraction of the upwind state (the
+// D equation multiplied by Y_e, Sec. 2.3; reading: upwinded as in the consistent multi-fluid
+// advection it cites).
+void face_flux(const PM& M, const oparams& Q, int d, const real wL[], const real BL[3],
+               const real wR[], const real BR[3], real Fq[], real Fb[2]) {
   FP L, R;
   fluid_point(M, Q, wL, BL, L);
   fluid_point(M, Q, wR, BR, R);
@@ -278,6 +411,7 @@ void face_flux(const PM& M, const oparams& Q, int d, const real wL[5], const rea
   for (int v = 0; v < 5; ++v) Fq[v] = F[v];
   Fb[0] = F[5];
   Fb[1] = F[6];
+  if (Q.eos) Fq[5] = F[0] * (F[0] > 0 ? L.ye : R.ye);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -452,9 +586,10 @@ void sources(const PM& M, const FP& F, const real dm[3][16], real s[5]) {
 // ------------------------------------------------------------------------------------------------
 struct C2PIn {  // undensitised invariants
   real D, q, r2, b2, rb;  // D~, tau~/D~, r^2, calb^2, r.calb
+  real ye;                // electron fraction (table)
 };
 struct C2PEval {
-  real x, rbar2, qbar, v2, W, rho, eps, p, f;
+  real x, rbar2, qbar, v2, W, rho, eps, p, f, T;
   bool vcap, eclamp;
 };
 
@@ -470,8 +605,28 @@ void c2p_eval(const oparams& Q, const C2PIn& I, real mu, C2PEval& E) {
   E.rho = I.D / E.W;
   E.eps = E.W * (E.qbar - mu * E.rbar2) + E.v2 * E.W * E.W / (1 + E.W);
   E.eclamp = false;
-  if (E.eps < 0) { E.eps = 0; E.eclamp = true; }   // ideal-gas range eps >= 0
-  E.p = eos_p(Q, E.rho, E.eps);
+  if (Q.eos == 0) {
+    if (E.eps < 0) { E.eps = 0; E.eclamp = true; }   // ideal-gas range eps >= 0
+    E.p = eos_p(Q, E.rho, E.eps);
+    E.T = E.p / E.rho;
+  } else {
+    // table: rho into the table's range, then the temperature of e = rho (1 + eps) (the nested
+    // root), eps reset to the table's value when e lies outside the range at this rho (App. A)
+    const otable& T = *Q.table;
+    int i[3];
+    double w[3];
+    bool cl = false;
+    const double lr = std::log(to_d(E.rho));
+    tab_axis(T, 0, lr, &i[0], &w[0], &cl);
+    if (cl) { E.rho = std::exp(T.x0[0] + (lr < T.x0[0] ? 0 : T.n[0] - 1) * T.dx[0]); E.eclamp = true; cl = false; }
+    tab_axis(T, 2, to_d(I.ye), &i[2], &w[2], &cl);
+    const double e = to_d(E.rho * (1 + E.eps));
+    const double lT = tab_inverse_T(T, T.le, i, w, e > 0 ? std::log(e) : -HUGE_VAL, &cl);
+    tab_axis(T, 1, lT, &i[1], &w[1], &cl);
+    if (cl) { E.eps = std::exp(tab_tri(T, T.le, i, w)) / E.rho - 1; E.eclamp = true; }
+    E.p = std::exp(tab_tri(T, T.lp, i, w));
+    E.T = std::exp(lT);
+  }
   const real ah = E.p / (E.rho * (1 + E.eps));
   const real nuA = (1 + ah) * (1 + E.eps) / E.W;
   const real nuB = (1 + ah) * (1 + E.qbar - mu * E.rbar2);
@@ -479,11 +634,12 @@ void c2p_eval(const oparams& Q, const C2PIn& I, real mu, C2PEval& E) {
   E.f = mu - 1 / (nu + mu * E.rbar2);
 }
 
-// Auxiliary function whose root bounds the master root from above: mu sqrt(h0^2 + rbar^2(mu)) - 1
-real c2p_aux(const C2PIn& I, real mu) {
+// Auxiliary function whose root bounds the master root from above: mu sqrt(h0^2 + rbar^2(mu)) - 1,
+// h0 the minimum enthalpy of the EOS (1 for the ideal gas)
+real c2p_aux(const C2PIn& I, real h0, real mu) {
   const real x = 1 / (1 + mu * I.b2);
   const real rbar2 = x * x * I.r2 + mu * x * (1 + x) * I.rb * I.rb;
-  return mu * std::sqrt(1 + rbar2) - 1;
+  return mu * std::sqrt(h0 * h0 + rbar2) - 1;
 }
 
 // Illinois (modified regula falsi) on a sign-changing bracket [a,b].  Returns 0 on convergence,
@@ -518,20 +674,27 @@ int illinois(Fn f, real a, real b, real fa, real fb, real tol, int max_iter, rea
   return -2;
 }
 
-// Atmosphere primitives (Sec. 3.6): rho_atm, p_atm, u~ = 0; B untouched.
-void atmosphere(const oparams& Q, real w[5]) {
+// Atmosphere primitives (Sec. 3.6, App. A): rho_atm, p_atm, u~ = 0; B untouched.  Table:
+// rho_atm, T_atm, Y_e = Y_e,atm, p from the table.
+void atmosphere(const oparams& Q, real w[]) {
   w[0] = Q.rho_atm; w[1] = w[2] = w[3] = 0; w[4] = Q.p_atm;
+  if (Q.eos) {
+    real eps;
+    eos_table_rho_T(Q, Q.rho_atm, Q.T_atm, Q.Ye_atm, &w[4], &eps);
+    w[5] = Q.Ye_atm;
+    w[6] = Q.T_atm;
+  }
 }
 
 // One cell.  q: densitised (D, S_j, tau) in/out (rewritten when limits or atmosphere apply);
 // Bdens: densitised cell-centred B^i; w: prims out.  Returns status bits; *iters = master iterations.
 // Invariants and root of the last bracketed solve of con2prim_point (for the learned bracket)
 struct C2PRecord {
-  real q, r2, b2, rb, mu;
+  real q, r2, b2, rb, mu, D, ye;
   bool solved;
 };
 
-int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3], real w[5], int* iters,
+int con2prim_point(const PM& M, const oparams& Q, real q[], const real Bdens[3], real w[], int* iters,
                    C2PRecord* rec = nullptr) {
   if (rec) rec->solved = false;
   int st = 0;
@@ -544,11 +707,22 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     Bu[i] = Bdens[i] / sg;
     finite = finite && std::isfinite(S[i]) && std::isfinite(Bu[i]);
   }
+  // table: Y_e = (D Y_e)/D from the conserved pair, moved into the table's range (App. A)
+  real ye = 0;
+  bool ye_clamped = false;
+  if (Q.eos) {
+    finite = finite && std::isfinite(q[5]);
+    const otable& T = *Q.table;
+    const double ylo = T.x0[2], yhi = T.x0[2] + (T.n[2] - 1) * T.dx[2];
+    ye = finite && q[0] != 0 ? q[5] / q[0] : real(ylo);
+    if (ye < ylo) { ye = ylo; ye_clamped = true; }
+    if (ye > yhi) { ye = yhi; ye_clamped = true; }
+  }
   // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A).  Values within 1e-6 relative of it
   // count as having reached it, so cells that sit at the atmosphere density up to rounding (or up
   // to an FP32 sqrt(gamma)) are reset deterministically.
   const real rho_thr = Q.f_thr * Q.rho_atm * (1 + 1e-6);
-  bool atm = false;
+  bool atm = false, reprim = false;
   if (!finite) { st |= 2; atm = true; }
   else if (D < rho_thr) { st |= 1; atm = true; }
   if (!atm) {
@@ -561,12 +735,24 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     bool qmod = false;
     // B^2/D > M_max  ->  D = B^2/M_max  (App. A)
     if (BB > Q.M_max * D) { D = BB / Q.M_max; st |= 16; qmod = true; }
-    // tau floor of a static cold fluid with the same field, eps(T=0) = 0 for the ideal gas (c16)
-    const real tau_min = 0.5 * BB;
+    // tau floor of a static cold fluid with the same field (c16): D eps(rho = D, T_min) + B^2/2,
+    // eps(T=0) = 0 for the ideal gas, the table's lowest temperature for a table
+    real eps_min = 0;
+    if (Q.eos) {
+      const otable& T = *Q.table;
+      real pm, rho_c = D;
+      const double lr = std::log(to_d(D));
+      const double lr_lo = T.x0[0], lr_hi = T.x0[0] + (T.n[0] - 1) * T.dx[0];
+      if (lr < lr_lo) rho_c = std::exp(lr_lo);
+      if (lr > lr_hi) rho_c = std::exp(lr_hi);
+      eos_table_rho_T(Q, rho_c, std::exp(T.x0[1]), ye, &pm, &eps_min);
+    }
+    const real tau_min = D * eps_min + 0.5 * BB;
     if (tau < tau_min) { tau = tau_min; st |= 8; qmod = true; }
     C2PIn I;
     I.D = D;
     I.q = tau / D;
+    I.ye = ye;
     real r_d[3], r_u[3], bb_u[3];
     for (int i = 0; i < 3; ++i) { r_d[i] = S[i] / D; bb_u[i] = Bu[i] / std::sqrt(D); }
     I.r2 = 0; I.rb = 0;
@@ -576,26 +762,29 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
     }
     for (int i = 0; i < 3; ++i) { I.r2 += r_d[i] * r_u[i]; I.rb += r_d[i] * bb_u[i]; }
     I.b2 = BB / D;
-    // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0], h0 = 1
-    real mup = 1, root, lo, hi;
+    // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0]
+    const real h0 = Q.eos ? real(Q.h0) : real(1);
+    const real mu_top = 1 / h0;
+    real mup = mu_top, root, lo, hi;
     int it_aux = 0;
     {
-      auto fa = [&](real mu) { return c2p_aux(I, mu); };
-      const real f1 = fa(1.0);
+      auto fa = [&](real mu) { return c2p_aux(I, h0, mu); };
+      const real f1 = fa(mu_top);
       if (f1 > 0) {
-        int r = illinois(fa, 0.0, 1.0, -1.0, f1, 1e-3, Q.max_iter, &root, &lo, &hi, &it_aux);
+        int r = illinois(fa, 0.0, mu_top, -1.0, f1, 1e-3, Q.max_iter, &root, &lo, &hi, &it_aux);
         if (r == 0) mup = hi;
       }
     }
     C2PEval E;
     auto fm = [&](real mu) { c2p_eval(Q, I, mu, E); return E.f; };
     real f0 = fm(0.0), fp = fm(mup);
-    if ((f0 < 0) == (fp < 0) && mup < 1) { mup = 1; fp = fm(mup); }
+    if ((f0 < 0) == (fp < 0) && mup < mu_top) { mup = mu_top; fp = fm(mup); }
     int r = illinois(fm, 0.0, mup, f0, fp, Q.tol, Q.max_iter, &root, &lo, &hi, iters);
     if (r != 0) { st |= 2; atm = true; }
     else {
       const real mu = root;
-      if (rec) { rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->solved = true; }
+      if (rec) { rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->D = D;
+                 rec->ye = ye; rec->solved = true; }
       c2p_eval(Q, I, mu, E);
       // v^i = mu x (r^i + mu (r.calb) calb^i)
       real v_u[3];
@@ -606,21 +795,37 @@ int con2prim_point(const PM& M, const oparams& Q, real q[5], const real Bdens[3]
         for (int i = 0; i < 3; ++i) v_u[i] *= s;
         if (Q.ceiling == 1) atm = true;
       }
-      if (E.eclamp) st |= 32;
+      if (E.eclamp || ye_clamped) st |= 32;
       if (E.rho < rho_thr) { st |= 1; atm = true; }
       if (!atm) {
         w[0] = E.rho;
         for (int i = 0; i < 3; ++i) w[1 + i] = E.W * v_u[i];
         w[4] = E.p;
-        if (qmod) { q[0] = sg * D; q[4] = sg * tau; }
+        if (Q.eos) {
+          w[5] = ye;
+          w[6] = E.T;
+          // temperature floor (App. A): T < T_atm -> T_atm, p recomputed, conserved rebuilt
+          if (E.T < Q.T_atm) {
+            real eps;
+            eos_table_rho_T(Q, E.rho, Q.T_atm, ye, &w[4], &eps);
+            w[6] = Q.T_atm;
+            st |= 32;
+            reprim = true;
+          }
+          if (ye_clamped) qmod = true;
+        }
+        if (qmod) {
+          q[0] = sg * D; q[4] = sg * tau;
+          if (Q.eos) q[5] = q[0] * ye;
+        }
       }
     }
   }
-  if (atm) {
-    atmosphere(Q, w);
+  if (atm) atmosphere(Q, w);
+  if (atm || reprim) {
     FP F;
     fluid_point(M, Q, w, Bdens, F);
-    cons_from_fp(M, F, q);
+    cons_all(Q, M, F, q);
   }
   return st;
 }
@@ -644,25 +849,29 @@ inline void load16(const double* const* mv, long vi, real m[16]) {
 #ifndef ORACLE_COUNT_FLOPS
 namespace {
 // ------------------------------------------------------------------------------------------------
-// Learned con2prim bracket (not in the paper): features, training target, and a 4-64-64-1 tanh
+// Learned con2prim bracket (not in the paper): features, training target, and a 6-64-64-1 tanh
 // MLP with its mean-squared-error gradient by plain backpropagation, all in FP64.
 //
 // Parameter vector (the layout documented for the library's gr_mlp_* calls):
-//   [0..3] feature means, [4..7] feature inverse standard deviations, [8] target mean,
-//   [9] target standard deviation, [10] bracket half-width in log mu, [11..15] unused,
-//   [16..]  W1 (64 x 4), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
+//   [0..5] feature means, [6..11] feature inverse standard deviations, [12] target mean,
+//   [13] target standard deviation, [14] first bracket step in log mu, [15] unused,
+//   [16..]  W1 (64 x 6), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
 // Features of a solved cell: log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2 / (r^2 calb^2) (0 if
-// either vanishes); target: log mu at the root.
+// either vanishes), and for a table log D~ and Y_e (0, 0 for the scale-free ideal gas); target:
+// log mu at the root.
 // ------------------------------------------------------------------------------------------------
-static const int MLP_H = 64, MLP_IN = 4, MLP_OFF = 16;
+static const int MLP_H = 64, MLP_IN = 6, MLP_OFF = 16;
 static const int MLP_NW = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+static const int MLP_MEAN = 0, MLP_ISTD = 6, MLP_TMEAN = 12, MLP_TSTD = 13;
 
-void c2p_features(real q, real r2, real b2, real rb, double f[4]) {
-  f[0] = std::log1p(to_d(q));
-  f[1] = std::log1p(to_d(r2));
-  f[2] = std::log1p(to_d(b2));
-  const double den = to_d(r2) * to_d(b2);
-  f[3] = den > 0 ? to_d(rb) * to_d(rb) / den : 0.0;
+void c2p_features(const oparams& Q, const C2PRecord& r, double f[MLP_IN]) {
+  f[0] = std::log1p(to_d(r.q));
+  f[1] = std::log1p(to_d(r.r2));
+  f[2] = std::log1p(to_d(r.b2));
+  const double den = to_d(r.r2) * to_d(r.b2);
+  f[3] = den > 0 ? to_d(r.rb) * to_d(r.rb) / den : 0.0;
+  f[4] = Q.eos ? std::log(to_d(r.D)) : 0.0;
+  f[5] = Q.eos ? to_d(r.ye) : 0.0;
 }
 
 // z (normalised output) and hidden activations of one sample
@@ -673,8 +882,8 @@ void mlp_forward1(const double* P, const double* x, double h1[64], double h2[64]
   const double* b2 = W2 + MLP_H * MLP_H;
   const double* W3 = b2 + MLP_H;
   const double* b3 = W3 + MLP_H;
-  double xn[4];
-  for (int j = 0; j < 4; ++j) xn[j] = (x[j] - P[j]) * P[4 + j];
+  double xn[MLP_IN];
+  for (int j = 0; j < MLP_IN; ++j) xn[j] = (x[j] - P[MLP_MEAN + j]) * P[MLP_ISTD + j];
   for (int i = 0; i < MLP_H; ++i) {
     double a = b1[i];
     for (int j = 0; j < MLP_IN; ++j) a += W1[i * MLP_IN + j] * xn[j];
@@ -695,22 +904,24 @@ void mlp_forward1(const double* P, const double* x, double h1[64], double h2[64]
 extern "C" {
 // Features and log(mu) of the bracketed con2prim solve at np points (valid[n] = 0 when the cell was
 // not solved: atmosphere, failure).
+// q: np x 5 (ideal gas) or np x 6 (table).
 void oracle_c2p_samples(int np, const double* metric, const double* q, const double* Bdens, const oparams* Q,
                         double* feats, double* target, uint8_t* valid) {
+  const int nq = Q->eos ? 6 : 5;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
-    real qq[5], w[5];
-    for (int v = 0; v < 5; ++v) qq[v] = q[5 * n + v];
+    real qq[6], w[7];
+    for (int v = 0; v < nq; ++v) qq[v] = q[nq * n + v];
     int it;
     C2PRecord rec;
     con2prim_point(M, *Q, qq, Bdens + 3 * n, w, &it, &rec);
     valid[n] = rec.solved ? 1 : 0;
     if (rec.solved) {
-      c2p_features(rec.q, rec.r2, rec.b2, rec.rb, feats + 4 * n);
+      c2p_features(*Q, rec, feats + MLP_IN * n);
       target[n] = std::log(rec.mu);
     } else {
-      for (int j = 0; j < 4; ++j) feats[4 * n + j] = 0;
+      for (int j = 0; j < MLP_IN; ++j) feats[MLP_IN * n + j] = 0;
       target[n] = 0;
     }
   }
@@ -722,8 +933,8 @@ int oracle_mlp_nparam(void) { return MLP_OFF + MLP_NW; }
 void oracle_mlp_forward(const double* P, const double* x, int n, double* t) {
   double h1[64], h2[64], z;
   for (int s = 0; s < n; ++s) {
-    mlp_forward1(P, x + 4 * s, h1, h2, &z);
-    t[s] = P[8] + P[9] * z;
+    mlp_forward1(P, x + MLP_IN * s, h1, h2, &z);
+    t[s] = P[MLP_TMEAN] + P[MLP_TSTD] * z;
   }
 }
 
@@ -741,14 +952,14 @@ void oracle_mlp_loss_grad(const double* P, const double* x, const double* t, int
   for (int k = 0; k < MLP_NW; ++k) grad[k] = 0;
   double L = 0;
   for (int s = 0; s < n; ++s) {
-    const double* xs = x + 4 * s;
+    const double* xs = x + MLP_IN * s;
     double h1[64], h2[64], z;
     mlp_forward1(P, xs, h1, h2, &z);
-    const double zt = (t[s] - P[8]) / P[9];
+    const double zt = (t[s] - P[MLP_TMEAN]) / P[MLP_TSTD];
     const double dz = (z - zt) / n;
     L += 0.5 * (z - zt) * (z - zt) / n;
-    double xn[4];
-    for (int j = 0; j < 4; ++j) xn[j] = (xs[j] - P[j]) * P[4 + j];
+    double xn[MLP_IN];
+    for (int j = 0; j < MLP_IN; ++j) xn[j] = (xs[j] - P[MLP_MEAN + j]) * P[MLP_ISTD + j];
     // output layer
     double g2[64];
     for (int j = 0; j < MLP_H; ++j) {
@@ -797,38 +1008,73 @@ void phase_mark(int k, OpCount& last) {
 extern "C" {
 
 #ifndef ORACLE_COUNT_FLOPS
-// Primitive -> conserved at np points.  metric: np x 16, prims: np x 5, Bdens: np x 3, q: np x 5.
+// Primitive -> conserved at np points.  metric: np x 16, Bdens: np x 3; prims np x 5 and q np x 5
+// (ideal gas) or prims np x 7 (rho, u~^i, p, Y_e, T; T unread) and q np x 6 (table).
 void oracle_prim2con(int np, const double* metric, const double* prims, const double* Bdens,
                      const oparams* Q, double* q) {
+  const int nw = Q->eos ? 7 : 5, nq = Q->eos ? 6 : 5;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
     FP F;
-    fluid_point(M, *Q, prims + 5 * n, Bdens + 3 * n, F);
-    cons_from_fp(M, F, q + 5 * n);
+    fluid_point(M, *Q, prims + nw * n, Bdens + 3 * n, F);
+    cons_all(*Q, M, F, q + nq * n);
   }
 }
 
-// Conserved -> primitive at np points.  q is rewritten in place when a limit or the atmosphere applies.
+// Conserved -> primitive at np points (layouts as oracle_prim2con).  q is rewritten in place when a
+// limit or the atmosphere applies.
 void oracle_con2prim(int np, const double* metric, double* q, const double* Bdens, const oparams* Q,
                      double* prims, uint8_t* status, int32_t* iters) {
+  const int nw = Q->eos ? 7 : 5, nq = Q->eos ? 6 : 5;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
     int it;
-    status[n] = (uint8_t)con2prim_point(M, *Q, q + 5 * n, Bdens + 3 * n, prims + 5 * n, &it);
+    status[n] = (uint8_t)con2prim_point(M, *Q, q + nq * n, Bdens + 3 * n, prims + nw * n, &it);
     if (iters) iters[n] = it;
   }
+}
+
+// Table lookups at np points for the pins: out[4n..4n+3] = p(rho, T, Y_e), eps(rho, T, Y_e),
+// c_s^2(rho, T, Y_e) and the temperature recovered from (rho, that p, Y_e).
+void oracle_table_eval(int np, const oparams* Q, const double* rho, const double* T, const double* ye,
+                       double* out) {
+  for (int n = 0; n < np; ++n) {
+    real p, eps;
+    eos_table_rho_T(*Q, rho[n], T[n], ye[n], &p, &eps);
+    Thermo th;
+    eos_from_rho_p(*Q, rho[n], p, ye[n], th);
+    out[4 * n + 0] = to_d(p);
+    out[4 * n + 1] = to_d(eps);
+    out[4 * n + 2] = to_d(th.cs2);
+    out[4 * n + 3] = to_d(th.T);
+  }
+}
+
+// Minimum over the table's nodes of the specific enthalpy h = (e + p)/rho (the h0 of the bracket)
+double oracle_table_hmin(const otable* T) {
+  double hmin = HUGE_VAL;
+  for (int iy = 0; iy < T->n[2]; ++iy)
+    for (int iT = 0; iT < T->n[1]; ++iT)
+      for (int ir = 0; ir < T->n[0]; ++ir) {
+        const long k = tab_idx(*T, ir, iT, iy);
+        const double lr = T->x0[0] + ir * T->dx[0];
+        const double h = std::exp(T->le[k] - lr) + std::exp(T->lp[k] - lr);
+        if (h < hmin) hmin = h;
+      }
+  return hmin;
 }
 
 // Physical state at np points in direction d: cons U (5 + 2 transverse B), flux F (5 + 2), speeds.
 void oracle_flux_points(int np, int d, const double* metric, const double* prims, const double* Bdens,
                         const oparams* Q, double* U, double* F, double* lam) {
+  const int nw = Q->eos ? 7 : 5;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
     FP P;
-    fluid_point(M, *Q, prims + 5 * n, Bdens + 3 * n, P);
+    fluid_point(M, *Q, prims + nw * n, Bdens + 3 * n, P);
     real q[7], f[7];
     cons_from_fp(M, P, q);
     q[5] = P.Bd_u[(d + 1) % 3];
@@ -839,24 +1085,32 @@ void oracle_flux_points(int np, int d, const double* metric, const double* prims
   }
 }
 
-// HLLE face flux from left/right prims at np faces.  Out: F (np x 7).
+// HLLE face flux from left/right prims at np faces.  Out: F (np x 7): 5 conserved, 2 induction; with
+// a table F (np x 8), the D Y_e flux last, and prims np x 7.
 void oracle_face_flux(int np, int d, const double* metric, const double* wL, const double* BL,
                       const double* wR, const double* BR, const oparams* Q, double* F) {
+  const int nw = Q->eos ? 7 : 5, nf = Q->eos ? 8 : 7;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
-    face_flux(M, *Q, d, wL + 5 * n, BL + 3 * n, wR + 5 * n, BR + 3 * n, F + 7 * n, F + 7 * n + 5);
+    real fq[6], fb[2];
+    face_flux(M, *Q, d, wL + nw * n, BL + 3 * n, wR + nw * n, BR + 3 * n, fq, fb);
+    for (int v = 0; v < 5; ++v) F[nf * n + v] = to_d(fq[v]);
+    F[nf * n + 5] = to_d(fb[0]);
+    F[nf * n + 6] = to_d(fb[1]);
+    if (Q->eos) F[nf * n + 7] = to_d(fq[5]);
   }
 }
 
 // Source terms at np points.  dmetric: np x 3 x 16 (d_k of each metric component).
 void oracle_sources(int np, const double* metric, const double* dmetric, const double* prims,
                     const double* Bdens, const oparams* Q, double* s) {
+  const int nw = Q->eos ? 7 : 5;
   for (int n = 0; n < np; ++n) {
     PM M;
     pm_from16(metric + 16 * n, M);
     FP P;
-    fluid_point(M, *Q, prims + 5 * n, Bdens + 3 * n, P);
+    fluid_point(M, *Q, prims + nw * n, Bdens + 3 * n, P);
     real dm[3][16];
     for (int k = 0; k < 3; ++k)
       for (int c = 0; c < 16; ++c) dm[k][c] = dmetric[48 * n + 16 * k + c];
@@ -926,6 +1180,7 @@ void oracle_flops_get(double* out, int reset) {
 // One Runge-Kutta stage on one MeshBlock.
 //   metric: 16 vertex arrays; W: 5 cell arrays (stage-input prims, ghosts filled); B: 3 face arrays
 //   (densitised, ghosts filled); U, U0: 5 cell arrays (interior read); B0: 3 face arrays.
+//   With a table: W has 7 arrays (rho, u~^i, p, Y_e, T; T unread) and U, U0, Uo 6 (D Y_e last).
 //   Out: Uo (interior cells), Bo (interior faces), Wo (interior prims), status (interior cells).
 // Returns 0, or -1 when the ghost width is too small for the stencil.
 int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, const double* Bx,
@@ -939,6 +1194,8 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
   const int need = (Q.recon == 1 ? 3 : 2) + (Q.interp_order == 4 ? 1 : 0);
   if (g < need) return -1;
   const long NC = b.ncell();
+  const int nq = Q.eos ? 6 : 5, nw = Q.eos ? 7 : 5;
+  const int nrec = Q.eos ? 8 : 7;   // reconstructed: rho, u~^i, p, calB^{t1}, calB^{t2}[, Y_e]
   const double* mv[16];
   for (int c = 0; c < 16; ++c) mv[c] = metric + c * b.nvert();
   const double* Bf[3] = {Bx, By, Bz};
@@ -976,7 +1233,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
   // a3 + a4: face fluxes on d-faces with normal index 0..n_d and transverse index -1..n_t
   std::vector<Arr> Fq[3], Fb[3];
   for (int d = 0; d < 3; ++d) {
-    Fq[d].assign(5, Arr(b.nface(d)));
+    Fq[d].assign(nq, Arr(b.nface(d)));
     Fb[d].assign(2, Arr(b.nface(d)));
   }
   for (int d = 0; d < 3; ++d) {
@@ -989,30 +1246,32 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
       for (p[1] = lo[1]; p[1] < hi[1]; ++p[1])
         for (p[0] = lo[0]; p[0] < hi[0]; ++p[0]) {
           // stencil cells along d: p[d]-3 .. p[d]+2
-          real wL[5], wR[5], cL[2], cR[2];
+          real wL[7], wR[7], cL[2], cR[2];
           real st[6];
           int q[3] = {p[0], p[1], p[2]};
-          real w1[7][6];  // variables x stencil: rho, u~^3, p, calB^{t1}, calB^{t2}
+          real w1[8][6];  // variables x stencil: rho, u~^3, p, calB^{t1}, calB^{t2}[, Y_e]
           for (int t = 0; t < 6; ++t) {
             q[d] = p[d] - 3 + t;
             const bool inside = (q[d] >= -g && q[d] < b.n[d] + g);
-            if (!inside) { for (int v = 0; v < 7; ++v) w1[v][t] = 0; continue; }
+            if (!inside) { for (int v = 0; v < nrec; ++v) w1[v][t] = 0; continue; }
             const long ci = cidx(b, q);
             for (int v = 0; v < 5; ++v) w1[v][t] = W[v * NC + ci];
             const real sgc = cm[ci].sqrtg;
             w1[5][t] = Bcc[t1][ci] / sgc;
             w1[6][t] = Bcc[t2][ci] / sgc;
+            if (Q.eos) w1[7][t] = W[5 * NC + ci];
           }
-          real Lv[7], Rv[7];
-          for (int v = 0; v < 7; ++v) {
+          real Lv[8], Rv[8];
+          for (int v = 0; v < nrec; ++v) {
             for (int t = 0; t < 6; ++t) st[t] = w1[v][t];
             recon_face(Q.recon, st, Q.weno_eps, &Lv[v], &Rv[v]);
           }
           // c6: a non-physical reconstructed state (rho <= 0 or p <= 0) drops both sides of the
           // face to first order
           if (!(Lv[0] > 0) || !(Rv[0] > 0) || !(Lv[4] > 0) || !(Rv[4] > 0))
-            for (int v = 0; v < 7; ++v) { Lv[v] = w1[v][2]; Rv[v] = w1[v][3]; }
+            for (int v = 0; v < nrec; ++v) { Lv[v] = w1[v][2]; Rv[v] = w1[v][3]; }
           for (int v = 0; v < 5; ++v) { wL[v] = Lv[v]; wR[v] = Rv[v]; }
+          if (Q.eos) { wL[5] = Lv[7]; wR[5] = Rv[7]; }
           cL[0] = Lv[5]; cL[1] = Lv[6]; cR[0] = Rv[5]; cR[1] = Rv[6];
           real m[16];
           interp_face(b, mv, Q.interp_order, d, p, m);
@@ -1024,10 +1283,10 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
           BL[d] = BR[d] = Bn;
           BL[t1] = cL[0] * M.sqrtg; BL[t2] = cL[1] * M.sqrtg;
           BR[t1] = cR[0] * M.sqrtg; BR[t2] = cR[1] * M.sqrtg;
-          real fq[5], fb[2];
+          real fq[6], fb[2];
           face_flux(M, Q, d, wL, BL, wR, BR, fq, fb);
           const long fi = fidx(b, d, p);
-          for (int v = 0; v < 5; ++v) Fq[d][v][fi] = fq[v];
+          for (int v = 0; v < nq; ++v) Fq[d][v][fi] = fq[v];
           Fb[d][0][fi] = fb[0];
           Fb[d][1][fi] = fb[1];
         }
@@ -1040,8 +1299,8 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
     for (int j = -1; j <= b.n[1]; ++j)
       for (int i = -1; i <= b.n[0]; ++i) {
         const long ci = b.c(i, j, k);
-        real w[5], Bd[3];
-        for (int v = 0; v < 5; ++v) w[v] = W[v * NC + ci];
+        real w[7], Bd[3];
+        for (int v = 0; v < nw; ++v) w[v] = W[v * NC + ci];
         for (int e = 0; e < 3; ++e) Bd[e] = Bcc[e][ci];
         FP F;
         fluid_point(cm[ci], Q, w, Bd, F);
@@ -1094,16 +1353,17 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
     for (int j = 0; j < b.n[1]; ++j)
       for (int i = 0; i < b.n[0]; ++i) {
         const long ci = b.c(i, j, k);
-        real w[5], Bd[3];
-        for (int v = 0; v < 5; ++v) w[v] = W[v * NC + ci];
+        real w[7], Bd[3];
+        for (int v = 0; v < nw; ++v) w[v] = W[v * NC + ci];
         for (int e = 0; e < 3; ++e) Bd[e] = Bcc[e][ci];
         FP F;
         fluid_point(cm[ci], Q, w, Bd, F);
         real dm[3][16];
         for (int e = 0; e < 3; ++e) interp_cell(b, mv, Q.interp_order, i, j, k, e, dm[e]);
-        real s[5];
+        real s[6];
         sources(cm[ci], F, dm, s);
-        for (int v = 0; v < 5; ++v) {
+        s[5] = 0;   // D Y_e has no source (Sec. 2.3)
+        for (int v = 0; v < nq; ++v) {
           real divF = 0;
           for (int d = 0; d < 3; ++d) {
             int p[3] = {i, j, k}, p1[3] = {i, j, k};
@@ -1142,17 +1402,18 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
       for (int i = 0; i < b.n[0]; ++i) {
         const long ci = b.c(i, j, k);
         const int p[3] = {i, j, k};
-        real Bd[3], q[5], w[5];
+        real Bd[3], q[6], w[7];
         for (int d = 0; d < 3; ++d) {
           int p1[3] = {i, j, k};
           p1[d] += 1;
           Bd[d] = 0.5 * (Bof[d][fidx(b, d, p)] + Bof[d][fidx(b, d, p1)]);
         }
-        for (int v = 0; v < 5; ++v) q[v] = Uo[v * NC + ci];
+        for (int v = 0; v < nq; ++v) q[v] = Uo[v * NC + ci];
         int it = 0;
         status[ci] = (uint8_t)con2prim_point(cm[ci], Q, q, Bd, w, &it);
         if (iters) iters[ci] = it;
-        for (int v = 0; v < 5; ++v) { Uo[v * NC + ci] = to_d(q[v]); Wo[v * NC + ci] = to_d(w[v]); }
+        for (int v = 0; v < nq; ++v) Uo[v * NC + ci] = to_d(q[v]);
+        for (int v = 0; v < nw; ++v) Wo[v * NC + ci] = to_d(w[v]);
       }
   ORACLE_PHASE(6);
   return 0;

@@ -9,7 +9,8 @@ Array layout of one MeshBlock with ``n`` interior cells per direction and ``g`` 
 (``N = n + 2g``, x fastest):
 
 * vertex metric ``(16, Nz+1, Ny+1, Nx+1)``: alpha, beta^i, gamma_{xx,xy,xz,yy,yz,zz}, K_ij
-* primitives ``(5, Nz, Ny, Nx)``: rho, u~^x, u~^y, u~^z, p
+* primitives ``(5, Nz, Ny, Nx)``: rho, u~^x, u~^y, u~^z, p; with a tabulated EOS ``(7, ...)``: rho, u~^i,
+  p, Y_e, T (T as drawn; the stage derives its own from (rho, p, Y_e))
 * faces: ``Bx (Nz, Ny, Nx+1)``, ``By (Nz, Ny+1, Nx)``, ``Bz (Nz+1, Ny, Nx)`` (densitised B^i)
 
 Cell index ``i`` in ``[-g, n+g-1]`` has centre ``x0 + (i + 1/2) dx``; vertex and face index ``i`` in
@@ -115,9 +116,13 @@ def curl_B(n, g, x0, dx, A):
 def random_block(n=(16, 16, 16), g=3, x0=(0.0, 0.0, 0.0), dx=None, seed=0, L=1.0,
                  rho_range=(1e-10, 1e-3), u_max=0.5, theta_range=(1e-3, 1e-1),
                  sigma_range=(1e-3, 10.0), metric_amp=1e-2, with_K=False, flat=False,
-                 fields=None):
+                 fields=None, eos=None, T_range=(1e-5, 1e-2), ye_range=(0.05, 0.5)):
     """Smooth random block.  ``fields`` (a dict of SmoothField) lets several blocks sample the
-    same global functions, so neighbouring blocks agree in their overlap."""
+    same global functions, so neighbouring blocks agree in their overlap.
+
+    ``eos`` (a SyntheticEOS): tabulated-EOS block; T and Y_e are drawn as smooth fields in
+    ``T_range`` (log-uniform) and ``ye_range`` and p = p(rho, T, Y_e) of that EOS (``theta_range``
+    is then unused)."""
     rng = np.random.default_rng(SEED_BASE + seed)
     if dx is None:
         dx = tuple(L / v for v in n)
@@ -127,22 +132,38 @@ def random_block(n=(16, 16, 16), g=3, x0=(0.0, 0.0, 0.0), dx=None, seed=0, L=1.0
     lr = np.log(rho_range)
     rho = np.exp(lr[0] + (lr[1] - lr[0]) * 0.5 * (1 + fields["rho"](X, Y, Z)))
     lt = np.log(theta_range)
-    theta = np.exp(lt[0] + (lt[1] - lt[0]) * 0.5 * (1 + fields["theta"](X, Y, Z)))
-    p = rho * theta
-    W = np.zeros((5,) + X.shape)
+    if eos is not None:
+        if "temp" not in fields:
+            rng2 = np.random.default_rng(SEED_BASE + seed + 104729)
+            fields = dict(fields, temp=SmoothField(rng2, L), ye=SmoothField(rng2, L))
+        lT = np.log(T_range)
+
+        def thermo(Xe, Ye, Ze, rr):
+            T = np.exp(lT[0] + (lT[1] - lT[0]) * 0.5 * (1 + fields["temp"](Xe, Ye, Ze)))
+            ye = ye_range[0] + (ye_range[1] - ye_range[0]) * 0.5 * (1 + fields["ye"](Xe, Ye, Ze))
+            return eos.p(rr, T, ye), T, ye
+    else:
+        def thermo(Xe, Ye, Ze, rr):
+            tt = np.exp(lt[0] + (lt[1] - lt[0]) * 0.5 * (1 + fields["theta"](Xe, Ye, Ze)))
+            return rr * tt, None, None
+    p, T, ye = thermo(X, Y, Z, rho)
+    W = np.zeros((5 if eos is None else 7,) + X.shape)
     W[0] = rho
     for c in range(3):
         W[1 + c] = u_max * fields[f"u{c}"](X, Y, Z) / np.sqrt(3.0)
     W[4] = p
+    if eos is not None:
+        W[5] = ye
+        W[6] = T
     # field: A_i = sqrt(sigma p) a_i(x) / k, so that |B|^2 ~ sigma p in order of magnitude
     ls = np.log(sigma_range)
     kk = 2 * np.pi / L
 
     def A(comp, Xe, Ye, Ze):
         rr = np.exp(lr[0] + (lr[1] - lr[0]) * 0.5 * (1 + fields["rho"](Xe, Ye, Ze)))
-        tt = np.exp(lt[0] + (lt[1] - lt[0]) * 0.5 * (1 + fields["theta"](Xe, Ye, Ze)))
+        pp = thermo(Xe, Ye, Ze, rr)[0]
         ss = np.exp(ls[0] + (ls[1] - ls[0]) * 0.5 * (1 + fields["sigma"](Xe, Ye, Ze)))
-        return np.sqrt(ss * rr * tt) * fields[f"a{comp}"](Xe, Ye, Ze) / kk
+        return np.sqrt(ss * pp) * fields[f"a{comp}"](Xe, Ye, Ze) / kk
 
     B = curl_B(n, g, x0, dx, A)
     if flat:
@@ -506,3 +527,82 @@ class BinaryStarMesh:
                 f0 = layout.face_off[b, d]
                 Bp[d][f0:f0 + f.size] = f
         return W, Bp, M
+
+
+# ---------------------------------------------------------------------------------------------
+# synthetic tabulated EOS (stand-in for the CompOSE table of Sec. 2.3, which is not available)
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class EosTable:
+    """Nodes of log p, log e (e = rho (1 + eps)) and c_s^2 on a uniform grid in (log rho, log T, Y_e)
+    (natural logarithms).  Arrays are (n_Ye, n_T, n_rho), rho fastest."""
+    n: tuple
+    x0: tuple
+    dx: tuple
+    lp: np.ndarray
+    le: np.ndarray
+    cs2: np.ndarray
+    eos: object = None       # the analytic EOS the nodes were sampled from (input generation only)
+
+    def axis(self, a):
+        return self.x0[a] + self.dx[a] * np.arange(self.n[a])
+
+    @property
+    def rho_range(self):
+        return float(np.exp(self.x0[0])), float(np.exp(self.x0[0] + (self.n[0] - 1) * self.dx[0]))
+
+    @property
+    def T_range(self):
+        return float(np.exp(self.x0[1])), float(np.exp(self.x0[1] + (self.n[1] - 1) * self.dx[1]))
+
+    @property
+    def ye_range(self):
+        return float(self.x0[2]), float(self.x0[2] + (self.n[2] - 1) * self.dx[2])
+
+
+class SyntheticEOS:
+    """Cold polytrope + ideal gas + radiation with a composition dependence:
+
+        p = K_Y rho^Gamma + rho T + a T^4,   K_Y = K (1 + 0.1 (Y_e - 0.25)),
+        eps = K_Y rho^(Gamma-1)/(Gamma-1) + 1.5 T + 3 a T^4 / rho,
+
+    T in units of the baryon mass.  eps satisfies the first law (d eps/d rho at fixed T equals
+    (p - T dp/dT)/rho^2), p and e are increasing in T, and c_s^2 = (dp/drho at fixed entropy)/h
+    with h = 1 + eps + p/rho."""
+
+    def __init__(self, K=100.0, Gamma=2.0, a_rad=1.0):
+        self.K, self.Gamma, self.a = K, Gamma, a_rad
+
+    def KY(self, ye):
+        return self.K * (1 + 0.1 * (ye - 0.25))
+
+    def p(self, rho, T, ye):
+        return self.KY(ye) * rho ** self.Gamma + rho * T + self.a * T ** 4
+
+    def eps(self, rho, T, ye):
+        return self.KY(ye) * rho ** (self.Gamma - 1) / (self.Gamma - 1) + 1.5 * T + 3 * self.a * T ** 4 / rho
+
+    def cs2(self, rho, T, ye):
+        G, a, KY = self.Gamma, self.a, self.KY(ye)
+        p, eps = self.p(rho, T, ye), self.eps(rho, T, ye)
+        dp_drho = G * KY * rho ** (G - 1) + T
+        dp_dT = rho + 4 * a * T ** 3
+        deps_drho = KY * rho ** (G - 2) - 3 * a * T ** 4 / rho ** 2
+        deps_dT = 1.5 + 12 * a * T ** 3 / rho
+        dT_drho_s = (p / rho ** 2 - deps_drho) / deps_dT      # along d eps = (p/rho^2) d rho
+        return (dp_drho + dp_dT * dT_drho_s) / (1 + eps + p / rho)
+
+    def table(self, n=(200, 128, 64), rho_range=(1e-15, 1e-2), T_range=(1e-7, 1e-1), ye_range=(0.01, 0.6)):
+        x0 = (float(np.log(rho_range[0])), float(np.log(T_range[0])), float(ye_range[0]))
+        dx = (float((np.log(rho_range[1]) - np.log(rho_range[0])) / (n[0] - 1)),
+              float((np.log(T_range[1]) - np.log(T_range[0])) / (n[1] - 1)),
+              float((ye_range[1] - ye_range[0]) / (n[2] - 1)))
+        lr = x0[0] + dx[0] * np.arange(n[0])
+        lT = x0[1] + dx[1] * np.arange(n[1])
+        ye = x0[2] + dx[2] * np.arange(n[2])
+        Y, T, R = np.meshgrid(ye, np.exp(lT), np.exp(lr), indexing="ij")
+        lp = np.log(self.p(R, T, Y))
+        le = np.log(R * (1 + self.eps(R, T, Y)))
+        cs2 = self.cs2(R, T, Y)
+        return EosTable(tuple(n), x0, dx, np.ascontiguousarray(lp), np.ascontiguousarray(le),
+                        np.ascontiguousarray(cs2), self)

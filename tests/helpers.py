@@ -70,13 +70,13 @@ def cell_B(bi):
 
 
 def cons_from_prims(bi, P: O.Params, order=2):
-    """Conserved variables (5, Nz, Ny, Nx) from the block's prims with the oracle's prim2con;
+    """Conserved variables (5 or 6, Nz, Ny, Nx) from the block's prims with the oracle's prim2con;
     cells without a computable metric are left 0."""
     cm = cell_metric(bi, order)
     Bc = cell_B(bi)
     W = np.moveaxis(bi.W, 0, -1)
     ok = np.isfinite(cm[..., 0])
-    q = np.zeros(W.shape)
+    q = np.zeros(W.shape[:-1] + (P.nq,))
     q[ok] = O.prim2con(cm[ok], W[ok], Bc[ok], P)
     return np.ascontiguousarray(np.moveaxis(q, -1, 0))
 
