@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim bracket-guess timings")
+    ap.add_argument("--no-table", action="store_true", help="skip the tabulated-EOS con2prim workload")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -208,6 +209,86 @@ def load_traffic(kernel, precision):
     return e.get("bytes_per_launch")
 
 
+def con2prim_table_workload(a, ctx, dev, G, I):
+    """Con2prim-heavy workload with the tabulated EOS: 256 blocks of 32^3 (one ghost), synthetic
+    200 x 128 x 64 table, densities from rho_atm to 1e-3, Lorentz factors up to ~5, b^2/p from 1e-4 to
+    1e3.  gr_con2prim is timed with no bracket proposal, the FP32 pre-solve and the learned bracket
+    (trained on the solves of 64 blocks of other seeds)."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2311_04989_gb300 import learned_bracket as LB
+    eos = I.SyntheticEOS()
+    tab = eos.table()
+    h = G.gr_eos_create(ctx, tab)
+    rho_atm, T_atm = 1e-12, 1e-5
+    kw = dict(rho_range=(rho_atm, 1e-3), T_range=(1e-4, 5e-2), ye_range=(0.05, 0.5), u_max=3.0,
+              sigma_range=(1e-4, 1e3), metric_amp=0.02)
+    t_gen = time.time()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        blocks = list(ex.map(lambda k: I.random_block(n=(32, 32, 32), g=1, seed=600 + k, eos=eos, **kw), range(256)))
+        train = list(ex.map(lambda k: I.random_block(n=(16, 16, 16), g=1, seed=900 + k, eos=eos, **kw), range(64)))
+    t_gen = time.time() - t_gen
+    rho = np.concatenate([b.W[0, 1:-1, 1:-1, 1:-1].ravel() for b in blocks])
+    sig = np.concatenate([(((b.B[0][1:-1, 1:-1, 1:-2] + b.B[0][1:-1, 1:-1, 2:-1]) ** 2 +
+                            (b.B[1][1:-1, 1:-2, 1:-1] + b.B[1][1:-1, 2:-1, 1:-1]) ** 2 +
+                            (b.B[2][1:-2, 1:-1, 1:-1] + b.B[2][2:-1, 1:-1, 1:-1]) ** 2) / 4 /
+                           b.W[0, 1:-1, 1:-1, 1:-1]).ravel() for b in blocks])
+    hard = float(np.mean((rho < 10 * rho_atm) | (sig >= 1.0)))
+    p = G.gr_params_default(eos=G.GR_EOS_TABLE, table=int(h), rho_atm=rho_atm, T_atm=T_atm, Ye_atm=0.5, tol=1e-10)
+    Pm, losses, delta = None, [0.0], 0.0
+    t_train = time.time()
+    x, t = LB.collect(ctx, train, p, device=dev)
+    Pm, losses, delta = LB.train(x, t, epochs=400, batch=2048, lr=3e-3)
+    t_train = time.time() - t_train
+    L, W, B, M = G.pack_blocks(blocks, dev)
+    mesh = G.gr_mesh_create(ctx, L.descriptors())
+    metric = G.metric_struct(M)
+    stream = torch.cuda.current_stream()
+    U = torch.zeros((6, W.shape[1]), dtype=torch.float64, device=dev)
+    G.gr_prim2con(mesh, metric, list(W), B, list(U), p, stream)
+    inter = torch.zeros(L.ncell, dtype=torch.bool, device=dev)
+    m = torch.zeros((34, 34, 34), dtype=torch.bool, device=dev)
+    m[1:-1, 1:-1, 1:-1] = True
+    for b in range(len(blocks)):
+        inter[int(L.cell_off[b]):int(L.cell_off[b]) + m.numel()] = m.view(-1)
+    cells = L.interior_cells()
+    out = {"workload": "256 blocks of 32^3, tabulated EOS 200x128x64 (synthetic), b^2/p 1e-4..1e3, u~ <= 3",
+           "cells": cells, "hard_cell_fraction": hard, "input_gen_s": round(t_gen, 1),
+           "mlp_training": {"training_samples": int(x.shape[0]), "train_s": round(t_train, 2), "first_step": delta,
+                            "loss_first_last": [losses[0], losses[-1]]}}
+    for name, guess in (("none", G.GR_GUESS_NONE), ("fp32", G.GR_GUESS_FP32), ("mlp", G.GR_GUESS_MLP)):
+        p.c2p_guess = guess
+        p.mlp = int(Pm.data_ptr())
+        Uc = U.clone()
+        Wc = torch.zeros((7, W.shape[1]), dtype=torch.float64, device=dev)
+        st = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
+        ev = torch.zeros(L.ncell, dtype=torch.int32, device=dev)
+        for _ in range(a.warmup):
+            Uc.copy_(U)
+            G.gr_con2prim(mesh, metric, list(Uc), B, list(Wc), st, p, stream, evals=ev)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(a.steps):
+            Uc.copy_(U)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.gr_con2prim(mesh, metric, list(Uc), B, list(Wc), st, p, stream, evals=ev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        solved = ((st.to(torch.int32) & 0x3F) == 0) & inter
+        ms = tot / a.steps
+        out[name] = {"ms": ms, "cells_per_s": cells / (ms / 1e3),
+                     "fp64_evals_per_solved_cell": float(ev[solved].double().mean().item()),
+                     "solved_cells": int(solved.sum().item()),
+                     "rejected": int(((st.to(torch.int32) & 64) != 0).sum().item())}
+    G.gr_mesh_destroy(mesh)
+    G.gr_eos_destroy(h)
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -346,7 +427,7 @@ def main():
         Uref = snap[head][2]
         Bref = snap[head][1]
         # training samples: the solves of this workload's stage output ("prior solves" of the run)
-        feats = [torch.zeros(L.ncell, dtype=torch.float32, device=dev) for _ in range(4)]
+        feats = [torch.zeros(L.ncell, dtype=torch.float32, device=dev) for _ in range(G.GR_MLP_NIN)]
         tgt = torch.zeros(L.ncell, dtype=torch.float32, device=dev)
         val = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
         G.gr_c2p_samples(mesh, metric, list(Uref), Bref, p64, feats, tgt, val, stream)
@@ -387,6 +468,11 @@ def main():
             c2p[name] = {"ms": tot / a.steps, "fp64_evals_per_solved_cell": float(ev[solved].double().mean().item()),
                          "solved_cells": int(solved.sum().item()),
                          "rejected": int(((stc.to(torch.int32) & 64) != 0).sum().item())}
+
+    # ---- con2prim-heavy workload with the tabulated EOS ------------------------------------------
+    c2p_table = None
+    if not a.no_table and not a.no_c2p:
+        c2p_table = con2prim_table_workload(a, ctx, dev, G, I)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None
@@ -486,7 +572,7 @@ def main():
            "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
-           "graph_ms_per_step": graph_ms, "con2prim_guess": c2p,
+           "graph_ms_per_step": graph_ms, "con2prim_guess": c2p, "con2prim_table": c2p_table,
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
     if rank == 0:
         print(json.dumps(out), flush=True)

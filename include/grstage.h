@@ -20,7 +20,9 @@
  *       y-/z-face arrays likewise with the extra point along y / z
  *       vertex arrays    (nz+2g+1) x (ny+2g+1) x (nx+2g+1) vertex i in [-g, n+g]
  *   - Primitives w = (rho, u~^x, u~^y, u~^z, p); conserved q = (D, S_x, S_y, S_z, tau); B^i is the
- *     densitised face field sqrt(gamma) calB^i.  Metric components in the order
+ *     densitised face field sqrt(gamma) calB^i.  With a tabulated EOS (Sec. 2.3) the primitives are
+ *     (rho, u~^i, p, Y_e, T) and the conserved variables (D, S_j, tau, D Y_e): the thermodynamic state
+ *     of a point is (rho, p, Y_e), and T is an output (written by con2prim, never read).  Metric components in the order
  *     alpha, beta^x, beta^y, beta^z, gamma_xx, gamma_xy, gamma_xz, gamma_yy, gamma_yz, gamma_zz,
  *     K_xx, K_xy, K_xz, K_yy, K_yz, K_zz.
  *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*; NULL is the
@@ -37,7 +39,7 @@
 extern "C" {
 #endif
 
-#define GR_ABI_VERSION 1
+#define GR_ABI_VERSION 2
 
 typedef enum {
   GR_OK = 0,
@@ -52,6 +54,7 @@ enum { GR_RECON_PLM = 0, GR_RECON_WENOZ = 1 };          /* Sec. 3.4 */
 enum { GR_PREC_FP64 = 0, GR_PREC_MIXED = 1 };           /* mixed: FP32 reconstruction/HLLE/EMF */
 enum { GR_EMF_UPWIND = 0, GR_EMF_MEAN = 1 };            /* Sec. 3.3 corner electric field */
 enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec. 3.5 reset */
+enum { GR_EOS_IDEAL = 0, GR_EOS_TABLE = 1 };            /* Sec. 2.3 */
 
 /* con2prim status bits (per cell, uint8) */
 #define GR_ST_ATM_THRESHOLD 0x01  /* rho or D below f_thr rho_atm -> atmosphere (Sec. 3.5, App. A) */
@@ -59,7 +62,7 @@ enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec.
 #define GR_ST_W_CLAMPED     0x04  /* Lorentz factor above W_max: clamped (or atmosphere)  (App. A) */
 #define GR_ST_TAU_FLOOR     0x08  /* tau raised to the cold static value (App. A) */
 #define GR_ST_BD_LIMIT      0x10  /* B^2/D above M_max: D rescaled (App. A) */
-#define GR_ST_EOS_CLAMP     0x20  /* eps clamped to the EOS range (App. A) */
+#define GR_ST_EOS_CLAMP     0x20  /* rho, eps/T or Y_e moved into the EOS range, or T raised to T_atm (App. A) */
 #define GR_ST_GUESS_REJECTED 0x40 /* a proposed root bracket showed no sign change: full bracket used */
 
 /* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change):
@@ -89,16 +92,33 @@ typedef struct {
  * Outputs are written on the interior only: Uo (cells), Bo (all faces of interior cells), Wo, status.
  * Outputs must not alias inputs. */
 typedef struct {
-  const double* U[5];
-  const double* U0[5];   /* RK register; read only where rk_g0 != 0 */
+  const double* U[6];    /* U[5] = D Y_e: tabulated EOS only (NULL otherwise) */
+  const double* U0[6];   /* RK register; read only where rk_g0 != 0 */
   const double* B[3];
   const double* B0[3];   /* read only where rk_g0 != 0 */
-  const double* W[5];
-  double* Uo[5];
+  const double* W[7];    /* W[5] = Y_e read with a table; W[6] = T never read */
+  double* Uo[6];
   double* Bo[3];
-  double* Wo[5];
+  double* Wo[7];         /* Wo[5], Wo[6] = Y_e, T written with a table */
   uint8_t* status;
 } gr_state;
+
+/* Tabulated EOS (Sec. 2.3): log p, log e (e = rho (1 + eps), the total energy density) and c_s^2 on a
+ * uniform grid in (log rho, log T, Y_e), natural logarithms; node (ir, iT, iy) of each host array at
+ * index (iy * n[1] + iT) * n[0] + ir.  The library interpolates trilinearly in those variables; log p
+ * and log e must increase strictly with T along every node column (the temperature is recovered by
+ * inverting the interpolant in log T).  Values outside the table are moved to the nearest table
+ * value (App. A; status GR_ST_EOS_CLAMP in con2prim). */
+typedef struct {
+  int32_t n[3];          /* nodes along log rho, log T, Y_e, each >= 2 */
+  int32_t pad_;
+  double x0[3];          /* first node: log rho_min, log T_min, Y_e,min */
+  double dx[3];          /* node spacing, > 0 */
+  const double* log_p;   /* host arrays of n[0] n[1] n[2] values, copied by gr_eos_create */
+  const double* log_e;
+  const double* cs2;
+} gr_eos_table;
+typedef struct gr_eos gr_eos;
 
 /* Parameters.  size must be sizeof(gr_params).  Defaults from gr_params_default(). */
 typedef struct {
@@ -119,6 +139,11 @@ typedef struct {
   double weno_eps;      /* WENOZ epsilon */
   double rk_g0, rk_g1, rk_beta;   /* U' = g0 U0 + g1 U + beta dt L(U) (Shu-Osher stage) */
   const float* mlp;     /* device parameter vector of the learned bracket (GR_GUESS_MLP), 16-byte aligned */
+  int32_t eos;          /* GR_EOS_*; GR_EOS_TABLE needs `table` on the mesh's device */
+  int32_t pad_;
+  const gr_eos* table;
+  double T_atm;         /* table: atmosphere temperature and temperature floor (App. A) */
+  double Ye_atm;        /* table: electron fraction of the atmosphere (a parameter; the paper is silent) */
 } gr_params;
 
 typedef struct gr_ctx gr_ctx;
@@ -161,15 +186,26 @@ int gr_graph_launch(gr_graph* graph, void* stream);
 int gr_graph_destroy(gr_graph* graph);
 
 /* Primitive -> conserved (Eq. consB_def) on the interior cells of every block, with the cell-centred
- * field taken as the mean of the two densitised faces. */
-int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5],
-                const double* const B[3], double* const U[5], const gr_params* params, void* stream);
+ * field taken as the mean of the two densitised faces.  W[0..4] (+ W[5] = Y_e with a table) are read;
+ * U[0..4] (+ U[5] = D Y_e) written.  Unused trailing entries may be NULL. */
+int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[7],
+                const double* const B[3], double* const U[6], const gr_params* params, void* stream);
 
 /* Conserved -> primitive on the interior cells (Sec. 3.5, App. A).  U is rewritten where the
  * atmosphere or a limit applies.  status and evals (the number of FP64 master-function evaluations
- * per cell) may be NULL. */
-int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
-                double* const W[5], uint8_t* status, int32_t* evals, const gr_params* params, void* stream);
+ * per cell) may be NULL.  With a table U has 6 and W 7 entries (Y_e and T written). */
+int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], const double* const B[3],
+                double* const W[7], uint8_t* status, int32_t* evals, const gr_params* params, void* stream);
+
+/* Device copy of an EOS table on the context's device: the three node arrays in FP64 (con2prim, FP64
+ * path) and in FP32 (mixed path), 36 n0 n1 n2 bytes in all (gr_eos_bytes), plus the table's minimum
+ * enthalpy h0 = min (e + p)/rho over the nodes (the enthalpy bound of the con2prim bracket, gr_eos_h0).
+ * Checks the sizes, finiteness and the strict increase in T; GR_EINVAL otherwise.  Synchronous.  The
+ * table must outlive every call that uses it. */
+int gr_eos_create(gr_ctx* ctx, const gr_eos_table* table, gr_eos** eos);
+int gr_eos_destroy(gr_eos* eos);
+int64_t gr_eos_bytes(const gr_eos* eos);
+double gr_eos_h0(const gr_eos* eos);
 
 /* Diagnostics (Eq. Mb, Eq. gausslaw).  out[0] = M_b = sum D dV; out[1] = max |div B| min(dx)/max|B|;
  * out[2] = sum |div B| dV / (max|B| sum dV / min dx); out[3] = max |B| over interior faces.
@@ -178,26 +214,28 @@ int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], d
             void* stream);
 
 /* ---- learned con2prim bracket (spec pattern; the paper has no counterpart) -------------------
- * A 4-64-64-1 tanh network predicts log mu at the master-function root from the features
- * log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2) of the KKC invariants (the reading of
- * Sec. 3.5's bracketing); con2prim with GR_GUESS_MLP starts at exp(t_hat) and steps outwards by factors
- * exp(delta 2^k), k = 0..5, until the FP64 master function changes sign, and solves in that bracket;
- * otherwise it falls back to the full bracket (status GR_ST_GUESS_REJECTED).
+ * A 6-64-64-1 tanh network predicts log mu at the master-function root from the features
+ * log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2) of the KKC invariants and, with a table,
+ * log D~ and Y_e (0 and 0 for the scale-free ideal gas) (the reading of Sec. 3.5's bracketing);
+ * con2prim with GR_GUESS_MLP starts at exp(t_hat) and steps outwards by factors exp(delta 2^k),
+ * k = 0..5, until the FP64 master function changes sign, and solves in that bracket; otherwise it
+ * falls back to the full bracket (status GR_ST_GUESS_REJECTED).
  * Parameter vector: GR_MLP_NPARAM floats, 16-byte aligned device memory:
- *   [0..3] feature means, [4..7] feature inverse std, [8] target mean, [9] target std,
- *   [10] first step delta (in log mu), [11..15] unused, [16..] W1 (64x4), b1 (64), W2 (64x64), b2 (64),
- *   W3 (64), b3 (1), row-major (out, in).  Samples x are rows of 4 floats; targets t are log mu. */
-#define GR_MLP_NPARAM 4561
+ *   [0..5] feature means, [6..11] feature inverse std, [12] target mean, [13] target std,
+ *   [14] first step delta (in log mu), [15] unused, [16..] W1 (64x6), b1 (64), W2 (64x64), b2 (64),
+ *   W3 (64), b3 (1), row-major (out, in).  Samples x are rows of 6 floats; targets t are log mu. */
+#define GR_MLP_NPARAM 4689
+#define GR_MLP_NIN 6
 int gr_mlp_nparam(void);
 const char* gr_mlp_last_error(void);
 /* Features and log mu of the plain (unguessed) bracketed solve of every interior cell, in the cell-pool
  * layout; valid = 0 where the cell is not solved or a limit applied. */
-int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[5], const double* const B[3],
-                   const gr_params* params, float* const feats[4], float* target, uint8_t* valid, void* stream);
+int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[6], const double* const B[3],
+                   const gr_params* params, float* const feats[6], float* target, uint8_t* valid, void* stream);
 /* t[i] = predicted log mu of sample i. */
 int gr_mlp_forward(const float* P, const float* x, int64_t n, float* t, void* stream);
-/* Gradient (4545 floats, the weights after the 16 header entries) and value of the mean loss
- * (z - zt)^2/2, zt = (t - P[8])/P[9], over n samples; device outputs.  Synchronises the stream. */
+/* Gradient (GR_MLP_NPARAM - 16 floats, the weights after the 16 header entries) and value of the mean
+ * loss (z - zt)^2/2, zt = (t - P[12])/P[13], over n samples; device outputs.  Synchronises the stream. */
 int gr_mlp_grad(const float* P, const float* x, const float* t, int64_t n, float* grad, float* loss, void* stream);
 /* Adam (lr, beta 0.9/0.999) over the samples in order, mini-batches of `batch`, `epochs` passes; updates
  * the weights of P in place and writes the mean loss of each epoch to the host array losses (may be NULL).

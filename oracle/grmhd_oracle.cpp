@@ -167,9 +167,14 @@ inline real eos_cs2(const oparams& Q, real rho, real p, real h) { return Q.gamma
 
 // ------------------------------------------------------------------------------------------------
 // Tabulated EOS (Sec. 2.3): trilinear interpolation of log p, log e and c_s^2 in (log rho, log T,
-// Y_e).  Values outside the table are moved to the nearest permissible value (App. A).  These
-// lookups work in double (the operation-counting build does not count them).
+// Y_e).  The interpolation is written for the specific quantities log(p/rho) = log p - log rho and
+// log(e/rho) = log(1 + eps): log rho is linear along its axis, so their interpolants are exactly the
+// interpolants of log p and log e minus log rho, while their values stay O(1) (no loss of eps to
+// the rest-mass part of e).  Values outside the table are moved to the nearest permissible value
+// (App. A); a density outside the table takes the specific quantities of the nearest table density
+// (reading).  These lookups work in double (the operation-counting build does not count them).
 // ------------------------------------------------------------------------------------------------
+enum { TAB_LP = 0, TAB_LE = 1, TAB_CS2 = 2 };
 // Cell index i in [0, n-2] and fraction w in [0, 1] of x on axis ax; clamps x into the axis range.
 void tab_axis(const otable& T, int ax, double x, int* i, double* w, bool* clamped) {
   const double lo = T.x0[ax], hi = T.x0[ax] + (T.n[ax] - 1) * T.dx[ax];
@@ -185,31 +190,38 @@ void tab_axis(const otable& T, int ax, double x, int* i, double* w, bool* clampe
 inline long tab_idx(const otable& T, int ir, int iT, int iy) {
   return ((long)iy * T.n[1] + iT) * T.n[0] + ir;
 }
-// Trilinear interpolant of f at the point with cell indices i[3] and fractions w[3]
-double tab_tri(const otable& T, const double* f, const int i[3], const double w[3]) {
+// node value of log(p/rho), log(e/rho) or c_s^2
+double tab_node(const otable& T, int f, int ir, int iT, int iy) {
+  const long k = tab_idx(T, ir, iT, iy);
+  const double lrho = T.x0[0] + ir * T.dx[0];
+  if (f == TAB_LP) return T.lp[k] - lrho;
+  if (f == TAB_LE) return T.le[k] - lrho;
+  return T.cs2[k];
+}
+// Trilinear interpolant of field f at the point with cell indices i[3] and fractions w[3]
+double tab_tri(const otable& T, int f, const int i[3], const double w[3]) {
   double s = 0;
   for (int c = 0; c < 8; ++c) {
     const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
     const double wt = (a ? w[0] : 1 - w[0]) * (b ? w[1] : 1 - w[1]) * (e ? w[2] : 1 - w[2]);
-    s += wt * f[tab_idx(T, i[0] + a, i[1] + b, i[2] + e)];
+    s += wt * tab_node(T, f, i[0] + a, i[1] + b, i[2] + e);
   }
   return s;
 }
-// Interpolant of f at T node k (bilinear in log rho, Y_e)
-double tab_at_T_node(const otable& T, const double* f, const int i[3], const double w[3], int k) {
+// Interpolant of field f at T node k (bilinear in log rho, Y_e)
+double tab_at_T_node(const otable& T, int f, const int i[3], const double w[3], int k) {
   double s = 0;
   for (int c = 0; c < 4; ++c) {
     const int a = c & 1, e = (c >> 1) & 1;
-    s += (a ? w[0] : 1 - w[0]) * (e ? w[2] : 1 - w[2]) * f[tab_idx(T, i[0] + a, k, i[2] + e)];
+    s += (a ? w[0] : 1 - w[0]) * (e ? w[2] : 1 - w[2]) * tab_node(T, f, i[0] + a, k, i[2] + e);
   }
   return s;
 }
-// log T at which the interpolant of f (log e or log p, increasing in T) equals y at the (log rho, Y_e)
-// of i, w (the nested temperature root of App. A).  Between T nodes the interpolant is linear in
-// log T, so the root lies on the node interval where the node values cross y and is found there in
-// closed form; y outside the values at the table's T ends gives that end (clamped).
-double tab_inverse_T(const otable& T, const double* f, const int i[3], const double w[3], double y,
-                     bool* clamped) {
+// log T at which the interpolant of field f (increasing in T) equals y at the (log rho, Y_e) of i, w
+// (the nested temperature root of App. A).  Between T nodes the interpolant is linear in log T, so
+// the root lies on the node interval where the node values cross y and is found there in closed
+// form; y outside the values at the table's T ends gives that end (clamped).
+double tab_inverse_T(const otable& T, int f, const int i[3], const double w[3], double y, bool* clamped) {
   const int nT = T.n[1];
   const double g0 = tab_at_T_node(T, f, i, w, 0), gN = tab_at_T_node(T, f, i, w, nT - 1);
   if (!(y > g0)) { if (y < g0 || !(y == y)) *clamped = true; return T.x0[1]; }
@@ -242,15 +254,16 @@ void eos_from_rho_p(const oparams& Q, real rho, real p, real ye, Thermo& t) {
   double w[3];
   tab_axis(T, 0, std::log(to_d(rho)), &i[0], &w[0], &t.clamped);
   tab_axis(T, 2, to_d(ye), &i[2], &w[2], &t.clamped);
-  const double lT = tab_inverse_T(T, T.lp, i, w, std::log(to_d(p)), &t.clamped);
+  // temperature at which the table's p/rho equals this point's
+  const double lT = tab_inverse_T(T, TAB_LP, i, w, std::log(to_d(p / rho)), &t.clamped);
   tab_axis(T, 1, lT, &i[1], &w[1], &t.clamped);
-  const double e = std::exp(tab_tri(T, T.le, i, w));
-  t.eps = real(e) / rho - 1;
-  t.h = (real(e) + p) / rho;
-  t.cs2 = tab_tri(T, T.cs2, i, w);
+  const double l1e = tab_tri(T, TAB_LE, i, w);     // log(1 + eps)
+  t.eps = std::expm1(l1e);
+  t.h = real(std::exp(l1e)) + p / rho;
+  t.cs2 = tab_tri(T, TAB_CS2, i, w);
   t.T = std::exp(lT);
 }
-// Pressure and eps at (rho, T, Y_e) from the table (atmosphere and temperature floor)
+// Pressure and eps at (rho, T, Y_e) from the table (atmosphere, temperature floor, tau floor)
 void eos_table_rho_T(const oparams& Q, real rho, real Tt, real ye, real* p, real* eps) {
   const otable& T = *Q.table;
   int i[3];
@@ -259,8 +272,8 @@ void eos_table_rho_T(const oparams& Q, real rho, real Tt, real ye, real* p, real
   tab_axis(T, 0, std::log(to_d(rho)), &i[0], &w[0], &cl);
   tab_axis(T, 1, std::log(to_d(Tt)), &i[1], &w[1], &cl);
   tab_axis(T, 2, to_d(ye), &i[2], &w[2], &cl);
-  *p = std::exp(tab_tri(T, T.lp, i, w));
-  *eps = std::exp(tab_tri(T, T.le, i, w)) / rho - 1;
+  *p = rho * std::exp(tab_tri(T, TAB_LP, i, w));
+  *eps = std::expm1(tab_tri(T, TAB_LE, i, w));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -610,8 +623,8 @@ void c2p_eval(const oparams& Q, const C2PIn& I, real mu, C2PEval& E) {
     E.p = eos_p(Q, E.rho, E.eps);
     E.T = E.p / E.rho;
   } else {
-    // table: rho into the table's range, then the temperature of e = rho (1 + eps) (the nested
-    // root), eps reset to the table's value when e lies outside the range at this rho (App. A)
+    // table: rho into the table's range, then the temperature of e/rho = 1 + eps (the nested
+    // root), eps reset to the table's value when it lies outside the range at this rho (App. A)
     const otable& T = *Q.table;
     int i[3];
     double w[3];
@@ -620,11 +633,11 @@ void c2p_eval(const oparams& Q, const C2PIn& I, real mu, C2PEval& E) {
     tab_axis(T, 0, lr, &i[0], &w[0], &cl);
     if (cl) { E.rho = std::exp(T.x0[0] + (lr < T.x0[0] ? 0 : T.n[0] - 1) * T.dx[0]); E.eclamp = true; cl = false; }
     tab_axis(T, 2, to_d(I.ye), &i[2], &w[2], &cl);
-    const double e = to_d(E.rho * (1 + E.eps));
-    const double lT = tab_inverse_T(T, T.le, i, w, e > 0 ? std::log(e) : -HUGE_VAL, &cl);
+    const double ope = to_d(E.eps);   // 1 + eps = e/rho, as log(1 + eps)
+    const double lT = tab_inverse_T(T, TAB_LE, i, w, ope > -1 ? std::log1p(ope) : -HUGE_VAL, &cl);
     tab_axis(T, 1, lT, &i[1], &w[1], &cl);
-    if (cl) { E.eps = std::exp(tab_tri(T, T.le, i, w)) / E.rho - 1; E.eclamp = true; }
-    E.p = std::exp(tab_tri(T, T.lp, i, w));
+    if (cl) { E.eps = std::expm1(tab_tri(T, TAB_LE, i, w)); E.eclamp = true; }
+    E.p = E.rho * std::exp(tab_tri(T, TAB_LP, i, w));
     E.T = std::exp(lT);
   }
   const real ah = E.p / (E.rho * (1 + E.eps));
@@ -739,13 +752,8 @@ int con2prim_point(const PM& M, const oparams& Q, real q[], const real Bdens[3],
     // eps(T=0) = 0 for the ideal gas, the table's lowest temperature for a table
     real eps_min = 0;
     if (Q.eos) {
-      const otable& T = *Q.table;
-      real pm, rho_c = D;
-      const double lr = std::log(to_d(D));
-      const double lr_lo = T.x0[0], lr_hi = T.x0[0] + (T.n[0] - 1) * T.dx[0];
-      if (lr < lr_lo) rho_c = std::exp(lr_lo);
-      if (lr > lr_hi) rho_c = std::exp(lr_hi);
-      eos_table_rho_T(Q, rho_c, std::exp(T.x0[1]), ye, &pm, &eps_min);
+      real pm;
+      eos_table_rho_T(Q, D, std::exp(Q.table->x0[1]), ye, &pm, &eps_min);
     }
     const real tau_min = D * eps_min + 0.5 * BB;
     if (tau < tau_min) { tau = tau_min; st |= 8; qmod = true; }

@@ -1,4 +1,5 @@
 // capi.cu -- host side of the C ABI declared in include/grstage.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -58,6 +59,53 @@ bool region_has_dir(int kind) { return kind == R_FACES || kind == R_EDGES || kin
 struct gr_ctx {
   int device;
 };
+
+// Device copy of an EOS table (node arrays of log(p/rho), log(e/rho) = log(1 + eps) and c_s^2 in FP64
+// and FP32) and a host copy of the FP64 arrays for per-call constants (the atmosphere state)
+struct gr_eos {
+  int device;
+  int n[3];
+  double x0[3], dx[3], hi[3];
+  double h0;
+  double* d64[3] = {nullptr, nullptr, nullptr};
+  float* d32[3] = {nullptr, nullptr, nullptr};
+  std::vector<double> host[3];
+  int64_t bytes = 0;
+};
+
+namespace {
+// trilinear interpolant of a host node array at (log rho, log T, Y_e), each moved into the table
+double host_tri(const gr_eos& t, int f, const double x[3]) {
+  int i[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double xc = std::min(std::max(x[a], t.x0[a]), t.hi[a]);
+    const double sx = (xc - t.x0[a]) / t.dx[a];
+    i[a] = std::min((int)sx, t.n[a] - 2);
+    w[a] = sx - i[a];
+  }
+  double s = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+    const double wt = (a ? w[0] : 1 - w[0]) * (b ? w[1] : 1 - w[1]) * (e ? w[2] : 1 - w[2]);
+    s += wt * t.host[f][((size_t)(i[2] + e) * t.n[1] + (i[1] + b)) * t.n[0] + (i[0] + a)];
+  }
+  return s;
+}
+template <class R>
+TabView<R> tab_view(const gr_eos& t, R* const* d) {
+  TabView<R> v;
+  for (int f = 0; f < 3; ++f) v.f[f] = d[f];
+  for (int a = 0; a < 3; ++a) {
+    v.n[a] = t.n[a];
+    v.x0[a] = (R)t.x0[a];
+    v.dx[a] = (R)t.dx[a];
+    v.idx[a] = (R)(1.0 / t.dx[a]);
+    v.hi[a] = (R)t.hi[a];
+  }
+  return v;
+}
+}  // namespace
 
 struct gr_mesh {
   gr_ctx* ctx = nullptr;
@@ -271,7 +319,7 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
     e = dalloc(sizeof(double) * wcell, &m->ws.bcc[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, &m->ws.ecc[a]);
-    if (e == cudaSuccess) e = dalloc(sizeof(double) * 7 * wface[a], &m->ws.flux[a]);
+    if (e == cudaSuccess) e = dalloc(sizeof(double) * 8 * wface[a], &m->ws.flux[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * wvert, &m->ws.edge[a]);
     m->ws.fstride[a] = wface[a];
   }
@@ -286,7 +334,7 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   }
   m->sh.ncell = ec; m->sh.nvert = ev;
   for (int a = 0; a < 3; ++a) m->sh.nface[a] = ef[a];
-  for (int v = 0; v < 5 && e == cudaSuccess; ++v) e = dalloc(sizeof(float) * ec, (void**)&m->sh.W[v]);
+  for (int v = 0; v < 6 && e == cudaSuccess; ++v) e = dalloc(sizeof(float) * ec, (void**)&m->sh.W[v]);
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(float) * ef[a], (void**)&m->sh.B[a]);
   for (int c = 0; c < 16 && e == cudaSuccess; ++c) e = dalloc(sizeof(float) * ev, (void**)&m->sh.M[c]);
   if (e == cudaSuccess) e = dalloc(sizeof(double) * 8, (void**)&m->d_diag);
@@ -316,18 +364,40 @@ static int check_params(const gr_params* p) {
   if (!(p->gamma_ad > 1.0) || !(p->W_max >= 1.0) || !(p->M_max > 0) || !(p->tol > 0) ||
       !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0))
     return fail(GR_EINVAL, "physical parameter out of range");
+  if (p->eos != GR_EOS_IDEAL && p->eos != GR_EOS_TABLE) return fail(GR_EINVAL, "bad eos");
+  if (p->eos == GR_EOS_TABLE) {
+    if (!p->table) return fail(GR_EINVAL, "GR_EOS_TABLE needs params.table (gr_eos_create)");
+    if (!(p->rho_atm > 0) || !(p->T_atm > 0) || !std::isfinite(p->Ye_atm))
+      return fail(GR_EINVAL, "table: rho_atm, T_atm must be positive and Ye_atm finite");
+  }
   return GR_OK;
 }
 
+
 static KParams kparams(const gr_params* p, double dt) {
-  KParams k;
+  KParams k{};
   k.recon = p->recon; k.emf = p->emf; k.ceiling = p->ceiling; k.max_iter = p->max_iter;
   k.c2p_guess = p->c2p_guess;
+  k.eos = p->eos;
   k.gamma_ad = p->gamma_ad; k.rho_atm = p->rho_atm; k.p_atm = p->p_atm; k.f_thr = p->f_thr;
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
   k.dt = dt;
   k.mlp = p->c2p_guess == GR_GUESS_MLP ? p->mlp : nullptr;
+  k.eint_atm = p->p_atm / (p->gamma_ad - 1.0);
+  k.h0 = 1.0;
+  if (p->eos == GR_EOS_TABLE) {
+    const gr_eos& t = *p->table;
+    k.T_atm = p->T_atm;
+    k.Ye_atm = p->Ye_atm;
+    k.h0 = t.h0;
+    // atmosphere state of the table (App. A): rho_atm, T_atm, Ye_atm, its p and rho eps
+    const double x[3] = {std::log(p->rho_atm), std::log(p->T_atm), p->Ye_atm};
+    k.p_atm = p->rho_atm * std::exp(host_tri(t, 0, x));
+    k.eint_atm = p->rho_atm * std::expm1(host_tri(t, 1, x));
+    k.t64 = tab_view<double>(t, t.d64);
+    k.t32 = tab_view<float>(t, t.d32);
+  }
   return k;
 }
 
@@ -408,11 +478,19 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
   if (mesh->nblocks > 0 && mesh->min_ng < need)
     return fail(GR_EINVAL, "gr_stage: ghost width too small for the reconstruction / interpolation stencil");
   StateView s;
-  for (int v = 0; v < 5; ++v) {
-    s.U[v] = state->U[v]; s.U0[v] = state->U0[v]; s.W[v] = state->W[v];
-    s.Uo[v] = state->Uo[v]; s.Wo[v] = state->Wo[v];
-    if (!s.U[v] || !s.W[v] || !s.Uo[v] || !s.Wo[v]) return fail(GR_EINVAL, "gr_stage: NULL state array");
+  const bool tab = params->eos == GR_EOS_TABLE;
+  const int nq = tab ? 6 : 5, nwr = tab ? 6 : 5, nwo = tab ? 7 : 5;
+  if (tab && params->table->device != mesh->ctx->device)
+    return fail(GR_EINVAL, "gr_stage: the EOS table lives on another device");
+  for (int v = 0; v < 6; ++v) {
+    s.U[v] = state->U[v]; s.U0[v] = state->U0[v]; s.Uo[v] = state->Uo[v];
+    if (v >= nq) continue;
+    if (!s.U[v] || !s.Uo[v]) return fail(GR_EINVAL, "gr_stage: NULL state array");
     if (params->rk_g0 != 0.0 && !s.U0[v]) return fail(GR_EINVAL, "gr_stage: U0 needed when rk_g0 != 0");
+  }
+  for (int v = 0; v < 7; ++v) {
+    s.W[v] = state->W[v]; s.Wo[v] = state->Wo[v];
+    if ((v < nwr && !s.W[v]) || (v < nwo && !s.Wo[v])) return fail(GR_EINVAL, "gr_stage: NULL state array");
   }
   for (int d = 0; d < 3; ++d) {
     s.B[d] = state->B[d]; s.B0[d] = state->B0[d]; s.Bo[d] = state->Bo[d];
@@ -420,9 +498,10 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
     if (params->rk_g0 != 0.0 && !s.B0[d]) return fail(GR_EINVAL, "gr_stage: B0 needed when rk_g0 != 0");
     if ((const double*)s.Bo[d] == s.B[d]) return fail(GR_EINVAL, "gr_stage: Bo must not alias B");
   }
-  for (int v = 0; v < 5; ++v)
-    if ((const double*)s.Uo[v] == s.U[v] || (const double*)s.Wo[v] == s.W[v])
-      return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
+  for (int v = 0; v < nq; ++v)
+    if ((const double*)s.Uo[v] == s.U[v]) return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
+  for (int v = 0; v < nwr; ++v)
+    if ((const double*)s.Wo[v] == s.W[v]) return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
   s.status = state->status;
   if (!s.status) return fail(GR_EINVAL, "gr_stage: status is NULL");
   if (mesh->nblocks == 0) return GR_OK;
@@ -438,14 +517,17 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
   return GR_OK;
 }
 
-int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5], const double* const B[3],
-                double* const U[5], const gr_params* params, void* stream) {
+int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[7], const double* const B[3],
+                double* const U[6], const gr_params* params, void* stream) {
   if (!mesh || !W || !B || !U) return fail(GR_EINVAL, "gr_prim2con: NULL argument");
   int r = check_params(params);
   if (r) return r;
   MetricView mv;
   if ((r = metric_view(metric, mv, false))) return r;
-  for (int v = 0; v < 5; ++v)
+  const int n = params->eos == GR_EOS_TABLE ? 6 : 5;
+  if (params->eos == GR_EOS_TABLE && params->table->device != mesh->ctx->device)
+    return fail(GR_EINVAL, "gr_prim2con: the EOS table lives on another device");
+  for (int v = 0; v < n; ++v)
     if (!W[v] || !U[v]) return fail(GR_EINVAL, "gr_prim2con: NULL array");
   for (int d = 0; d < 3; ++d)
     if (!B[d]) return fail(GR_EINVAL, "gr_prim2con: NULL face array");
@@ -458,15 +540,18 @@ int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[5]
   return GR_OK;
 }
 
-int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], const double* const B[3],
-                double* const W[5], uint8_t* status, int32_t* evals, const gr_params* params, void* stream) {
+int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], const double* const B[3],
+                double* const W[7], uint8_t* status, int32_t* evals, const gr_params* params, void* stream) {
   if (!mesh || !W || !B || !U) return fail(GR_EINVAL, "gr_con2prim: NULL argument");
   int r = check_params(params);
   if (r) return r;
   MetricView mv;
   if ((r = metric_view(metric, mv, false))) return r;
-  for (int v = 0; v < 5; ++v)
-    if (!W[v] || !U[v]) return fail(GR_EINVAL, "gr_con2prim: NULL array");
+  const bool tab = params->eos == GR_EOS_TABLE;
+  if (tab && params->table->device != mesh->ctx->device)
+    return fail(GR_EINVAL, "gr_con2prim: the EOS table lives on another device");
+  for (int v = 0; v < (tab ? 7 : 5); ++v)
+    if (!W[v] || (v < (tab ? 6 : 5) && !U[v])) return fail(GR_EINVAL, "gr_con2prim: NULL array");
   for (int d = 0; d < 3; ++d)
     if (!B[d]) return fail(GR_EINVAL, "gr_con2prim: NULL face array");
   if (mesh->nblocks == 0) return GR_OK;
@@ -477,16 +562,18 @@ int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[5], cons
   return GR_OK;
 }
 
-int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[5], const double* const B[3],
-                   const gr_params* params, float* const feats[4], float* target, uint8_t* valid, void* stream) {
+int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U[6], const double* const B[3],
+                   const gr_params* params, float* const feats[6], float* target, uint8_t* valid, void* stream) {
   if (!mesh || !U || !B || !feats || !target || !valid) return fail(GR_EINVAL, "gr_c2p_samples: NULL argument");
   int r = check_params(params);
   if (r) return r;
   MetricView mv;
   if ((r = metric_view(metric, mv, false))) return r;
-  for (int v = 0; v < 5; ++v)
+  if (params->eos == GR_EOS_TABLE && params->table->device != mesh->ctx->device)
+    return fail(GR_EINVAL, "gr_c2p_samples: the EOS table lives on another device");
+  for (int v = 0; v < (params->eos == GR_EOS_TABLE ? 6 : 5); ++v)
     if (!U[v]) return fail(GR_EINVAL, "gr_c2p_samples: NULL array");
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < GR_MLP_NIN; ++j)
     if (!feats[j]) return fail(GR_EINVAL, "gr_c2p_samples: NULL feature array");
   for (int d = 0; d < 3; ++d)
     if (!B[d]) return fail(GR_EINVAL, "gr_c2p_samples: NULL face array");
@@ -495,6 +582,84 @@ int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U
   cudaError_t e = launch_c2p_samples(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U, B,
                                      feats, target, valid, kparams(params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_c2p_samples launch");
+  return GR_OK;
+}
+
+int gr_eos_destroy(gr_eos* t) {
+  if (!t) return GR_OK;
+  DeviceGuard g(t->device);
+  for (int f = 0; f < 3; ++f) {
+    if (t->d64[f]) cudaFree(t->d64[f]);
+    if (t->d32[f]) cudaFree(t->d32[f]);
+  }
+  delete t;
+  return GR_OK;
+}
+
+int64_t gr_eos_bytes(const gr_eos* t) { return t ? t->bytes : -1; }
+double gr_eos_h0(const gr_eos* t) { return t ? t->h0 : -1.0; }
+
+int gr_eos_create(gr_ctx* ctx, const gr_eos_table* in, gr_eos** out) {
+  if (!ctx || !in || !out) return fail(GR_EINVAL, "gr_eos_create: NULL argument");
+  if (!in->log_p || !in->log_e || !in->cs2) return fail(GR_EINVAL, "gr_eos_create: NULL node array");
+  long long nn = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (in->n[a] < 2 || in->n[a] > 100000) return fail(GR_EINVAL, "gr_eos_create: each axis needs 2..100000 nodes");
+    if (!(in->dx[a] > 0) || !std::isfinite(in->dx[a]) || !std::isfinite(in->x0[a]))
+      return fail(GR_EINVAL, "gr_eos_create: axis origin and spacing must be finite, spacing > 0");
+    nn *= in->n[a];
+  }
+  if (nn > (1LL << 28)) return fail(GR_EINVAL, "gr_eos_create: more than 2^28 nodes");
+  gr_eos* t = new gr_eos();
+  t->device = ctx->device;
+  for (int a = 0; a < 3; ++a) {
+    t->n[a] = in->n[a];
+    t->x0[a] = in->x0[a];
+    t->dx[a] = in->dx[a];
+    t->hi[a] = in->x0[a] + (in->n[a] - 1) * in->dx[a];
+  }
+  for (int f = 0; f < 3; ++f) t->host[f].resize(nn);
+  t->h0 = HUGE_VAL;
+  const int n0 = in->n[0], n1 = in->n[1], n2 = in->n[2];
+  for (int iy = 0; iy < n2; ++iy)
+    for (int iT = 0; iT < n1; ++iT)
+      for (int ir = 0; ir < n0; ++ir) {
+        const size_t k = ((size_t)iy * n1 + iT) * n0 + ir;
+        const double lp = in->log_p[k], le = in->log_e[k], c2 = in->cs2[k];
+        if (!std::isfinite(lp) || !std::isfinite(le) || !std::isfinite(c2)) {
+          delete t;
+          return fail(GR_EINVAL, "gr_eos_create: non-finite table value");
+        }
+        if (iT > 0 && !(lp > in->log_p[k - n0] && le > in->log_e[k - n0])) {
+          delete t;
+          return fail(GR_EINVAL, "gr_eos_create: log p and log e must increase strictly with T");
+        }
+        const double lr = in->x0[0] + ir * in->dx[0];
+        t->host[0][k] = lp - lr;      // log(p/rho)
+        t->host[1][k] = le - lr;      // log(e/rho) = log(1 + eps)
+        t->host[2][k] = c2;
+        const double h = std::exp(le - lr) + std::exp(lp - lr);   // (e + p)/rho
+        if (h < t->h0) t->h0 = h;
+      }
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaSuccess;
+  std::vector<float> tmp(nn);
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    e = cudaMalloc(&t->d64[f], sizeof(double) * nn);
+    if (e == cudaSuccess) e = cudaMemcpy(t->d64[f], t->host[f].data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d32[f], sizeof(float) * nn);
+    for (long long k = 0; k < nn && e == cudaSuccess; ++k) tmp[k] = (float)t->host[f][k];
+    if (e == cudaSuccess) e = cudaMemcpy(t->d32[f], tmp.data(), sizeof(float) * nn, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
+    std::string msg = std::string("gr_eos_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    gr_eos_destroy(t);
+    return fail(code, msg);
+  }
+  t->bytes = (int64_t)nn * 3 * (sizeof(double) + sizeof(float));
+  *out = t;
   return GR_OK;
 }
 

@@ -39,21 +39,21 @@ struct MetricView {
   int k_zero;
 };
 struct StateView {
-  const double* U[5];
-  const double* U0[5];
+  const double* U[6];     // [5] = D Y_e (table)
+  const double* U0[6];
   const double* B[3];
   const double* B0[3];
-  const double* W[5];
-  double* Uo[5];
+  const double* W[7];     // [5] = Y_e, [6] = T (table; T unread)
+  double* Uo[6];
   double* Bo[3];
-  double* Wo[5];
+  double* Wo[7];
   uint8_t* status;
 };
 // Stage inputs seen in the arithmetic type R of a kernel: the caller's FP64 pools (R = double) or
 // the FP32 copies made by the cast pass (R = float).  Same element indexing as the caller pools.
 template <class R>
 struct InView {
-  const R* W[5];
+  const R* W[6];          // rho, u~^i, p[, Y_e]
   const R* B[3];
   const R* M[16];
   int order;
@@ -62,7 +62,7 @@ struct InView {
 
 // FP32 copies of the stage inputs (owned by the mesh), sized to the extent of the caller pools
 struct Shadow {
-  float* W[5];
+  float* W[6];
   float* B[3];
   float* M[16];
   long long ncell, nface[3], nvert;   // pool extents in elements
@@ -72,35 +72,52 @@ struct Shadow {
 struct Workspace {
   void* bcc[3];        // undensitised cell-centred field calB^i (cells), FP64 or FP32
   void* ecc[3];        // cell-centred electric field E_m (cells, rings -1..n), FP64 or FP32
-  void* flux[3];       // per direction: 7 arrays of face values (FP64 or FP32), stride fstride[d]
+  void* flux[3];       // per direction: 8 arrays of face values (FP64 or FP32), stride fstride[d]:
+                       // D, S_j, tau, the two induction fluxes, D Y_e
   void* edge[3];       // corner electric field E_m (vertex-indexed), FP64 or FP32
   long long fstride[3];
   long long estride;
 };
 
+// Device view of an EOS table (Sec. 2.3) in precision R: node arrays of log p, log e, c_s^2, node
+// (ir, iT, iy) at (iy * n[1] + iT) * n[0] + ir; uniform axes log rho, log T, Y_e.
+template <class R>
+struct TabView {
+  const R* f[3];      // log p, log e, c_s^2
+  int n[3];
+  R x0[3], dx[3], idx[3], hi[3];   // first node, spacing, 1/spacing, last node of each axis
+};
+
 struct KParams {   // gr_params flattened for the device
-  int recon, emf, ceiling, max_iter, c2p_guess;
+  int recon, emf, ceiling, max_iter, c2p_guess, eos;
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
   double dt;
   const float* mlp;   // learned-bracket parameters (GR_GUESS_MLP) or nullptr
+  // tabulated EOS: atmosphere (rho_atm, T_atm, Ye_atm) with p_atm and eint_atm precomputed from the
+  // table, and the FP64 / FP32 node arrays
+  double T_atm, Ye_atm;
+  double eint_atm;    // internal energy density rho eps of the atmosphere (ideal: p_atm/(Gamma - 1))
+  double h0;          // minimum enthalpy of the EOS (1 for the ideal gas)
+  TabView<double> t64;
+  TabView<float> t32;
 };
 
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
-// ev: nullptr, or GR_NKERNELS + 1 events recorded before the first kernel and after each kernel
-// (the mixed path's input cast is timed with the first kernel)
+// ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after
+// the cast and each kernel
 cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
                          const int nwork[R_NREGION], const MetricView& m, const StateView& s,
                          const Workspace& ws, const Shadow& sh, const KParams& kp, cudaStream_t st,
                          cudaEvent_t* ev);
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                            const double* const W[5], const double* const B[3], double* const U[5],
+                            const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st);
 cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                            double* const U[5], const double* const B[3], double* const W[5],
+                            double* const U[6], const double* const B[3], double* const W[7],
                             uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st);
 cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                               const double* const U[5], const double* const B[3], float* const feats[4],
+                               const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
 cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const double* const U[5],
                         const double* const B[3], double* dev_out /* 4 + scratch */, cudaStream_t st);

@@ -1,7 +1,7 @@
 // mlp.cu -- training and evaluation kernels of the learned con2prim bracket (see mlp.cuh).
 //
 // Training minimises the mean of (z - zt)^2 / 2 over samples, z the network output and
-// zt = (log mu - P[8]) / P[9] the normalised target, with Adam.  One mini-batch is two launches:
+// zt = (log mu - P[12]) / P[13] the normalised target, with Adam.  One mini-batch is two launches:
 //   k_mlp_grad_partial  one CTA per 128 samples: forward, backward, and that CTA's sum of the
 //                       per-sample gradients (reduced over its samples in shared memory)
 //   k_mlp_reduce_adam   one thread per parameter: sum of the CTA partials in a fixed order
@@ -25,7 +25,7 @@ struct GradSmem {
   float H2[kS][kMlpH];
   float G1[kS][kMlpH];
   float G2[kS][kMlpH];
-  float X[kS][4];
+  float X[kS][kMlpIn];
   float dz[kS];
   float loss[kS / 32];
 };
@@ -34,10 +34,10 @@ __global__ void __launch_bounds__(kS) k_mlp_forward(const float* __restrict__ P,
                                                    long long n, float* __restrict__ t) {
   const long long e = blockIdx.x * (long long)kS + threadIdx.x;
   if (e >= n) return;
-  float xe[4];
+  float xe[kMlpIn];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) xe[j] = x[4 * e + j];
-  t[e] = P[8] + P[9] * mlp_z(P, xe);
+  for (int j = 0; j < kMlpIn; ++j) xe[j] = x[kMlpIn * e + j];
+  t[e] = P[kMlpTMean] + P[kMlpTStd] * mlp_z(P, xe);
 }
 
 __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict__ P, const float* __restrict__ x,
@@ -50,14 +50,16 @@ __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict
   const long long e = blockIdx.x * (long long)kS + s;
   const bool valid = e < nb;
   float h1[kMlpH];
-  float xn[4] = {0.f, 0.f, 0.f, 0.f};
+  float xn[kMlpIn];
+#pragma unroll
+  for (int j = 0; j < kMlpIn; ++j) xn[j] = 0.f;
   float dz = 0.f, loss = 0.f;
   if (valid) {
-    float xe[4];
+    float xe[kMlpIn];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) xe[j] = x[4 * (n0 + e) + j];
+    for (int j = 0; j < kMlpIn; ++j) xe[j] = x[kMlpIn * (n0 + e) + j];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) xn[j] = (xe[j] - P[j]) * P[4 + j];
+    for (int j = 0; j < kMlpIn; ++j) xn[j] = (xe[j] - P[kMlpMean + j]) * P[kMlpIStd + j];
     mlp_layer1(P, xe, h1);
     float z = P[kB3];
     for (int i = 0; i < kMlpH; ++i) {
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict
       S.H2[s][i] = h2;
       z = fmaf(P[kW3 + i], h2, z);
     }
-    const float zt = (t[n0 + e] - P[8]) / P[9];
+    const float zt = (t[n0 + e] - P[kMlpTMean]) / P[kMlpTStd];
     dz = (z - zt) * inv_n;
     loss = 0.5f * (z - zt) * (z - zt) * inv_n;
   } else {
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict
     S.G1[s][j] = g1[j] * (1.f - h1[j] * h1[j]);
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) S.X[s][j] = xn[j];
+  for (int j = 0; j < kMlpIn; ++j) S.X[s][j] = xn[j];
   S.dz[s] = dz;
   for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
   if ((s & 31) == 0) S.loss[s >> 5] = loss;
@@ -106,8 +108,8 @@ __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict
   float* out = partial + (long long)blockIdx.x * kMlpNW;
   for (int k = s; k < kMlpNW; k += kS) {
     float acc = 0.f;
-    if (k < kB1 - kMlpOff) {                         // W1 (64 x 4)
-      const int i = k / 4, j = k % 4;
+    if (k < kB1 - kMlpOff) {                         // W1 (64 x kMlpIn)
+      const int i = k / kMlpIn, j = k % kMlpIn;
       for (int q = 0; q < kS; ++q) acc = fmaf(S.G1[q][i], S.X[q][j], acc);
     } else if (k < kW2 - kMlpOff) {                  // b1
       const int i = k - (kB1 - kMlpOff);

@@ -12,16 +12,21 @@
 
 #include <cuda_runtime.h>
 
+#include "grstage.h"
+
 namespace grs {
 
-constexpr int kMlpH = 64, kMlpIn = 4, kMlpOff = 16;
-constexpr int kMlpNW = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;   // 4545
-constexpr int kMlpN = kMlpOff + kMlpNW;                                              // 4561
+constexpr int kMlpH = 64, kMlpIn = 6, kMlpOff = 16;
+constexpr int kMlpNW = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;   // 4673
+constexpr int kMlpN = kMlpOff + kMlpNW;                                              // 4689
+constexpr int kMlpMean = 0, kMlpIStd = 6, kMlpTMean = 12, kMlpTStd = 13, kMlpStep = 14;
+static_assert(kMlpN == GR_MLP_NPARAM && kMlpIn == GR_MLP_NIN, "parameter layout of include/grstage.h");
 constexpr int kW1 = kMlpOff, kB1 = kW1 + kMlpH * kMlpIn, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
               kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH;
 
-// Features of the KKC invariants: log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2)
-__device__ __forceinline__ void c2p_features(double q, double r2, double b2, double rb, float f[4]) {
+// Features 0..3 of the KKC invariants: log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2)
+// (features 4, 5 -- log D~ and Y_e, or 0 for the ideal gas -- are set by the caller)
+__device__ __forceinline__ void c2p_features(double q, double r2, double b2, double rb, float f[kMlpIn]) {
   f[0] = (float)log1p(q);
   f[1] = (float)log1p(r2);
   f[2] = (float)log1p(b2);
@@ -30,15 +35,15 @@ __device__ __forceinline__ void c2p_features(double q, double r2, double b2, dou
 }
 
 // First hidden layer of a normalised input (registers; fully unrolled)
-__device__ __forceinline__ void mlp_layer1(const float* __restrict__ P, const float x[4], float h1[kMlpH]) {
-  float xn[4];
+__device__ __forceinline__ void mlp_layer1(const float* __restrict__ P, const float x[kMlpIn], float h1[kMlpH]) {
+  float xn[kMlpIn];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) xn[j] = (x[j] - __ldg(P + j)) * __ldg(P + 4 + j);
+  for (int j = 0; j < kMlpIn; ++j) xn[j] = (x[j] - __ldg(P + kMlpMean + j)) * __ldg(P + kMlpIStd + j);
 #pragma unroll
   for (int i = 0; i < kMlpH; ++i) {
     float a = __ldg(P + kB1 + i);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a = fmaf(__ldg(P + kW1 + i * 4 + j), xn[j], a);
+    for (int j = 0; j < kMlpIn; ++j) a = fmaf(__ldg(P + kW1 + i * kMlpIn + j), xn[j], a);
     h1[i] = tanhf(a);
   }
 }
@@ -58,9 +63,9 @@ __device__ __forceinline__ float mlp_row2(const float* __restrict__ P, int i, co
   return a;
 }
 
-// Normalised network output z (the prediction of log mu is P[8] + P[9] z).  Kept out of line so
+// Normalised network output z (the prediction of log mu is P[12] + P[13] z).  Kept out of line so
 // that the con2prim kernel carries one compact copy.
-static __device__ __noinline__ float mlp_z(const float* __restrict__ P, const float x[4]) {
+static __device__ __noinline__ float mlp_z(const float* __restrict__ P, const float x[kMlpIn]) {
   float h1[kMlpH];
   mlp_layer1(P, x, h1);
   float z = __ldg(P + kB3);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "eos.cuh"
 #include "internal.h"
 #include "mlp.cuh"
 
@@ -329,13 +330,28 @@ __device__ __forceinline__ void recon<float>(int method, const float s[6], float
 }
 
 // ------------------------------------------------------------------------------------------------
+// EOS at a point from (rho, p[, Y_e]) (Sec. 2.3): rho h and c_s^2.  Ideal gas (reading c3 for c_s):
+// rho h = rho + Gamma p/(Gamma - 1), c_s^2 = Gamma p/(rho h); table: interpolated (eos.cuh).
+// ------------------------------------------------------------------------------------------------
+template <class R, int EOS>
+__device__ __forceinline__ void eos_rhoh_cs2(const KParams& kp, R rho, R p, R ye, R* rhoh, R* cs2) {
+  if constexpr (EOS == GR_EOS_IDEAL) {
+    const R gam = R(kp.gamma_ad);
+    *rhoh = rho + gam * rdiv(p, gam - R(1));
+    *cs2 = rdiv(gam * p, *rhoh);
+  } else {
+    tab_thermo_p<R>(tab_of<R>(kp), rho, p, ye, rhoh, cs2, (R*)nullptr);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // One side of a face: conserved U (D, S_j, tau, B^{t1}, B^{t2}), flux F^d of Eq. fluxB_def and
 // fast speeds (lam-, lam+) (Sec. 2.2, approximate quadratic dispersion relation).
 //   met: alpha, beta^i, gamma_ij at the face; sg = sqrt(gamma); gdd = gamma^{dd}
-//   w: (rho, u~^i, p); Bd: densitised B^i at the face state.
+//   w: (rho, u~^i, p[, Y_e]); Bd: densitised B^i at the face state.
 // ------------------------------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, R gam, const R w[5],
+template <class R, int EOS>
+__device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, const KParams& kp, const R w[6],
                                            const R Bd[3], R U[7], R F[7], R* lm, R* lp) {
   const R alpha = met[0];
   const R* beta = met + 1;
@@ -364,7 +380,8 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   R bl[3];                                       // b_i = calB_i / W + alpha b^0 v_i
 #pragma unroll
   for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
-  const R rhoh = rho + gam * rdiv(p, gam - R(1));   // rho h for p = (Gamma-1) rho eps
+  R rhoh, cs2;
+  eos_rhoh_cs2<R, EOS>(kp, rho, p, EOS ? w[5] : R(0), &rhoh, &cs2);
   const R e = rhoh + b2;
   const R pt = p + R(0.5) * b2;
   // Eq. consB_def
@@ -387,7 +404,6 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   F[5] = alpha * (Bd[t1] * vt[d] - Bd[d] * vt[t1]);
   F[6] = alpha * (Bd[t2] * vt[d] - Bd[d] * vt[t2]);
   // fast speeds
-  const R cs2 = rdiv(gam * p, rhoh);
   const R ca2 = rdiv(b2, e);
   const R c2 = cs2 + ca2 - cs2 * ca2;
   const R v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
@@ -448,8 +464,8 @@ struct CellFluid {
   R Bu[3], bl[3];
 };
 
-template <class R>
-__device__ __forceinline__ void cell_fluid(const CellMet<R>& M, R gam, const R w[5], const R Bd[3],
+template <class R, int EOS>
+__device__ __forceinline__ void cell_fluid(const CellMet<R>& M, const KParams& kp, const R w[6], const R Bd[3],
                                            CellFluid<R>& f) {
   f.rho = w[0];
   f.p = w[4];
@@ -473,7 +489,8 @@ __device__ __forceinline__ void cell_fluid(const CellMet<R>& M, R gam, const R w
   f.b2 = (f.ab0 * f.ab0 + BB) * iW * iW;
   #pragma unroll
   for (int i = 0; i < 3; ++i) f.bl[i] = Bl[i] * iW + f.ab0 * f.vl[i];
-  f.rhoh = f.rho + gam * rdiv(f.p, gam - R(1));
+  R cs2;
+  eos_rhoh_cs2<R, EOS>(kp, f.rho, f.p, EOS ? w[5] : R(0), &f.rhoh, &cs2);
 }
 
 template <class R>
@@ -578,10 +595,12 @@ __device__ __forceinline__ void c2pmet_from(const double g6[6], C2PMet& M) {
 template <class R>
 struct C2PInv {
   R D, q, r2, b2, rb;
+  R ye;     // table: electron fraction (already inside the table's range)
 };
 template <class R>
 struct C2PVal {
   R x, rbar2, v2, iW, eps, f;
+  R rho, p, lT;   // table: density (inside the table), pressure, log T at mu
   bool vcap, eclamp;
 };
 
@@ -609,11 +628,48 @@ __device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R
   E.f = mu - rdiv(R(1), nu + mu * E.rbar2);
 }
 
+// The same master function with the tabulated EOS (Sec. 2.3, App. A): rho = D/W moved into the
+// table, the temperature of e/rho = 1 + eps by the exact inverse of the interpolant (eps reset to the
+// table's value at the nearest end when outside), p from the table; (1 + a)(1 + eps) = h =
+// 1 + eps + p/rho.
 template <class R>
-__device__ __forceinline__ R c2p_aux(const C2PInv<R>& I, R mu) {
+__device__ __forceinline__ void c2p_master_tab(const TabView<R>& t, R vmax2, const C2PInv<R>& I, R mu,
+                                               C2PVal<R>& E) {
+  E.x = rdiv(R(1), R(1) + mu * I.b2);
+  E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (R(1) + E.x) * I.rb * I.rb;
+  const R qbar = I.q - R(0.5) * I.b2 - R(0.5) * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
+  E.v2 = mu * mu * E.rbar2;
+  E.vcap = E.v2 > vmax2;
+  if (E.vcap) E.v2 = vmax2;
+  E.iW = rsqrt_(R(1) - E.v2);
+  const R qm = qbar - mu * E.rbar2;
+  E.eps = rdiv(qm * (R(1) + E.iW) + E.v2, E.iW * (R(1) + E.iW));
+  E.rho = I.D * E.iW;
+  E.eclamp = false;
+  bool cl = false;
+  const R lr = rlog(E.rho);
+  const TabLoc<R> L = tab_loc(t, lr, I.ye, &cl);
+  if (cl) { E.rho = rexp(lr < t.x0[0] ? t.x0[0] : t.hi[0]); E.eclamp = true; cl = false; }
+  int k;
+  R wT;
+  const R y = E.eps > R(-1) ? rlog1p(E.eps) : R(-INFINITY);
+  E.lT = tab_inverse_T(t, t.f[1], L, y, &cl, &k, &wT);
+  if (cl) { E.eps = rexpm1(tab_T(t, t.f[1], L, k, wT)); E.eclamp = true; }
+  E.p = E.rho * rexp(tab_T(t, t.f[0], L, k, wT));
+  const R h = (R(1) + E.eps) + rdiv(E.p, E.rho);
+  const R nuA = h * E.iW;
+  const R nuB = rdiv(h * (R(1) + qm), R(1) + E.eps);
+  const R nu = nuA > nuB ? nuA : nuB;
+  E.f = mu - rdiv(R(1), nu + mu * E.rbar2);
+}
+
+// Auxiliary function mu sqrt(h0^2 + rbar^2(mu)) - 1 whose root bounds the master root from above;
+// h0 = minimum enthalpy of the EOS (1 for the ideal gas), passed squared
+template <class R>
+__device__ __forceinline__ R c2p_aux(const C2PInv<R>& I, R h0sq, R mu) {
   const R x = rdiv(R(1), R(1) + mu * I.b2);
   const R rbar2 = x * x * I.r2 + mu * x * (R(1) + x) * I.rb * I.rb;
-  return mu * rsqrt_(R(1) + rbar2) - R(1);
+  return mu * rsqrt_(h0sq + rbar2) - R(1);
 }
 
 // Illinois on [a,b] (f(a) < 0 < f(b) or reverse).  Returns 0 (root), -1 (no sign change), -2 (cap).
@@ -648,48 +704,85 @@ __device__ __forceinline__ int illinois(Fn f, R a, R b, R fa, R fb, R tol, int m
 }
 
 // FP32 pre-solve of the master root: returns mu32 > 0, or 0 when it did not converge
+template <int EOS>
 __device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<double>& I64) {
   C2PInv<float> I;
   I.D = (float)I64.D; I.q = (float)I64.q; I.r2 = (float)I64.r2; I.b2 = (float)I64.b2; I.rb = (float)I64.rb;
+  I.ye = (float)I64.ye;
   if (!(I.D > 0.f) || !isfinite(I.q) || !isfinite(I.r2) || !isfinite(I.b2)) return 0.f;
   const float gam = (float)P.gamma_ad, vmax2 = (float)(1.0 - 1.0 / (P.W_max * P.W_max));
-  float mup = 1.f, root, hi;
+  const float top = EOS ? (float)(1.0 / P.h0) : 1.f, h0sq = EOS ? (float)(P.h0 * P.h0) : 1.f;
+  float mup = top, root, hi;
   int it;
-  const float f1 = c2p_aux<float>(I, 1.f);
+  const float f1 = c2p_aux<float>(I, h0sq, top);
   if (f1 > 0.f) {
-    auto fa = [&](float mu) { return c2p_aux<float>(I, mu); };
-    if (illinois<float>(fa, 0.f, 1.f, -1.f, f1, 1e-3f, 40, &root, &hi, &it) == 0) mup = hi;
+    auto fa = [&](float mu) { return c2p_aux<float>(I, h0sq, mu); };
+    if (illinois<float>(fa, 0.f, top, -1.f, f1, 1e-3f, 40, &root, &hi, &it) == 0) mup = hi;
   }
   C2PVal<float> E;
-  auto fm = [&](float mu) { c2p_master<float>(gam, vmax2, I, mu, E); return E.f; };
+  auto fm = [&](float mu) {
+    if constexpr (EOS == GR_EOS_IDEAL) c2p_master<float>(gam, vmax2, I, mu, E);
+    else c2p_master_tab<float>(P.t32, vmax2, I, mu, E);
+    return E.f;
+  };
   const float f0 = fm(0.f);
   float fp = fm(mup);
-  if ((f0 < 0.f) == (fp < 0.f) && mup < 1.f) { mup = 1.f; fp = fm(mup); }
+  if ((f0 < 0.f) == (fp < 0.f) && mup < top) { mup = top; fp = fm(mup); }
   if (illinois<float>(fm, 0.f, mup, f0, fp, 1e-6f, 60, &root, &hi, &it) != 0) return 0.f;
   return root;
 }
 
 // Invariants and root of a bracketed solve (training samples for the learned bracket)
 struct C2PRecord {
-  double q, r2, b2, rb, mu;
+  double q, r2, b2, rb, mu, D, ye;
   bool solved;
 };
 
-// Full con2prim of one cell.  q: densitised conserved (in/out), Bd: densitised cell field.
+// Conserved variables of a primitive state at a point with spatial metric M (Eq. consB_def needs
+// only gamma_ij): used to rebuild q after a temperature floor.  w: (rho, u~^i, p[, Y_e]).
+template <int EOS>
+__device__ __forceinline__ void cons_at(const C2PMet& M, const KParams& P, const double w[6], const double Bd[3],
+                                        double q[6]) {
+  CellMet<double> Mc;
+  Mc.alpha = 1.0;
+  for (int i = 0; i < 3; ++i) Mc.beta[i] = 0.0;
+  for (int c = 0; c < 6; ++c) { Mc.g[c] = M.g[c]; Mc.K[c] = 0.0; }
+  Mc.det = M.det;
+  Mc.sg = M.sg;
+  inv3(Mc.g, Mc.det, Mc.gi);
+  CellFluid<double> f;
+  cell_fluid<double, EOS>(Mc, P, w, Bd, f);
+  cell_cons<double>(Mc, f, q);
+  if (EOS) q[5] = q[0] * w[5];
+}
+
+// Full con2prim of one cell.  q: densitised conserved (in/out; q[5] = D Y_e with a table), Bd:
+// densitised cell field, w: primitives out (w[5], w[6] = Y_e, T with a table).
 // guess: GR_GUESS_NONE (bracket (0, mu+]) or GR_GUESS_FP32 (an FP32 pre-solve proposes a bracket of
 // relative half-width 2e-5 around its root; it is used only if the FP64 master function changes
-// sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set).
-__device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, double q[5],
-                                             const double Bd[3], double w[5], int* iters,
+// sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set) or GR_GUESS_MLP.
+template <int EOS>
+__device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, double q[6],
+                                             const double Bd[3], double w[7], int* iters,
                                              C2PRecord* rec = nullptr) {
   int st = 0;
   *iters = 0;
   if (rec) rec->solved = false;
   bool finite = isfinite(q[0]) && isfinite(q[4]);
   for (int i = 0; i < 3; ++i) finite = finite && isfinite(q[1 + i]) && isfinite(Bd[i]);
+  // table: Y_e = (D Y_e)/D moved into the table's range (App. A)
+  double ye = 0.0;
+  bool ye_clamped = false;
+  if constexpr (EOS == GR_EOS_TABLE) {
+    finite = finite && isfinite(q[5]);
+    const double ylo = P.t64.x0[2], yhi = P.t64.hi[2];
+    ye = (finite && q[0] != 0.0) ? q[5] / q[0] : ylo;
+    if (ye < ylo) { ye = ylo; ye_clamped = true; }
+    if (ye > yhi) { ye = yhi; ye_clamped = true; }
+  }
   // atmosphere threshold; values within 1e-6 relative of it count as having reached it
   const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-6);
-  bool atm = false;
+  bool atm = false, reprim = false;
   if (!finite) { st |= GR_ST_FAILED; atm = true; }
   else if (q[0] < rho_thr * M.sg) { st |= GR_ST_ATM_THRESHOLD; atm = true; }   // D~ < rho_thr
   double isg = 0.0;
@@ -705,12 +798,19 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     const double BB = Bu[0] * Bl[0] + Bu[1] * Bl[1] + Bu[2] * Bl[2];
     bool qmod = false;
     if (BB > P.M_max * D) { D = BB / P.M_max; st |= GR_ST_BD_LIMIT; qmod = true; }
-    const double tau_min = 0.5 * BB;
+    // tau floor of a static cold fluid with the same field: D eps(rho = D, T_min) + B^2/2
+    double eps_min = 0.0;
+    if constexpr (EOS == GR_EOS_TABLE) {
+      double pm;
+      tab_p_eps_T<double>(P.t64, D, P.t64.x0[1], ye, &pm, &eps_min);
+    }
+    const double tau_min = D * eps_min + 0.5 * BB;
     if (tau < tau_min) { tau = tau_min; st |= GR_ST_TAU_FLOOR; qmod = true; }
     double gi[6];
     inv3(M.g, M.det, gi);
     C2PInv<double> I;
     I.D = D;
+    I.ye = ye;
     const double iD = 1.0 / D;
     I.q = tau * iD;
     double rl[3], ru[3], bu[3];
@@ -723,16 +823,23 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     I.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     I.b2 = BB * iD;
     const double gam = P.gamma_ad, vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
+    // upper end of the bracket search: mu <= 1/h0
+    const double top = EOS ? 1.0 / P.h0 : 1.0, h0sq = EOS ? P.h0 * P.h0 : 1.0;
     C2PVal<double> E;
     int nevals = 0;   // FP64 master-function evaluations (reported through *iters)
-    auto fm = [&](double mu) { ++nevals; c2p_master<double>(gam, vmax2, I, mu, E); return E.f; };
+    auto fm = [&](double mu) {
+      ++nevals;
+      if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
+      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E);
+      return E.f;
+    };
     double root = 0.0, hi;
     int r = -1;
     int it_master = 0;
     if (P.c2p_guess == GR_GUESS_FP32) {
-      const double mu32 = (double)c2p_presolve32(P, I);
+      const double mu32 = (double)c2p_presolve32<EOS>(P, I);
       if (mu32 > 0.0) {
-        const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), 1.0);
+        const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), top);
         const double flo = fm(lo), fup = fm(up);
         if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, &it_master);
       }
@@ -741,11 +848,13 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       // learned bracket: start at the network's prediction mu_hat of the root and step outwards
       // geometrically (factor exp(delta 2^k), k = 0..5) in the direction the sign of f points,
       // until f changes sign; that bracket, verified by the sign change, goes to the Illinois solve
-      float f[4];
+      float f[kMlpIn];
       c2p_features(I.q, I.r2, I.b2, I.rb, f);
-      const float th = __ldg(P.mlp + 8) + __ldg(P.mlp + 9) * mlp_z(P.mlp, f);
-      const double dl = (double)__ldg(P.mlp + 10);
-      double m0 = fmin((double)__expf(th), 1.0);
+      f[4] = EOS ? (float)log(D) : 0.f;
+      f[5] = EOS ? (float)ye : 0.f;
+      const float th = __ldg(P.mlp + kMlpTMean) + __ldg(P.mlp + kMlpTStd) * mlp_z(P.mlp, f);
+      const double dl = (double)__ldg(P.mlp + kMlpStep);
+      double m0 = fmin((double)__expf(th), top);
       if (m0 > 0.0) {
         double f0 = fm(m0);
         if (f0 == 0.0) {
@@ -755,7 +864,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
           const double dir = f0 < 0.0 ? 1.0 : -1.0;   // f < 0 below the root
           double step = dl;
           for (int k = 0; k < 6 && r != 0; ++k, step *= 2.0) {
-            const double m1 = fmin(m0 * exp(dir * step), 1.0);
+            const double m1 = fmin(m0 * exp(dir * step), top);
             if (!(m1 > 0.0) || m1 == m0) break;
             const double f1 = fm(m1);
             if ((f1 < 0.0) != (f0 < 0.0) || f1 == 0.0) {
@@ -772,17 +881,17 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       if (r != 0) st |= GR_ST_GUESS_REJECTED;
     }
     if (r != 0) {
-      // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0], h0 = 1
-      double mup = 1.0;
+      // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0]
+      double mup = top;
       int it_aux;
-      const double f1 = c2p_aux<double>(I, 1.0);
+      const double f1 = c2p_aux<double>(I, h0sq, top);
       if (f1 > 0.0) {
-        auto fa = [&](double mu) { return c2p_aux<double>(I, mu); };
-        if (illinois<double>(fa, 0.0, 1.0, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+        auto fa = [&](double mu) { return c2p_aux<double>(I, h0sq, mu); };
+        if (illinois<double>(fa, 0.0, top, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
       }
       const double f0 = fm(0.0);
       double fp = fm(mup);
-      if ((f0 < 0.0) == (fp < 0.0) && mup < 1.0) { mup = 1.0; fp = fm(mup); }
+      if ((f0 < 0.0) == (fp < 0.0) && mup < top) { mup = top; fp = fm(mup); }
       r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, &it_master);
     }
     *iters = nevals;
@@ -791,8 +900,12 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       atm = true;
     } else {
       const double mu = root;
-      if (rec) { rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->solved = true; }
-      c2p_master<double>(gam, vmax2, I, mu, E);
+      if (rec) {
+        rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->D = D; rec->ye = ye;
+        rec->solved = true;
+      }
+      if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
+      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E);
       double vu[3];
       for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);
       if (E.vcap) {
@@ -801,22 +914,40 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
         for (int i = 0; i < 3; ++i) vu[i] *= s;
         if (P.ceiling == GR_CEIL_ATMOSPHERE) atm = true;
       }
-      if (E.eclamp) st |= GR_ST_EOS_CLAMP;
-      const double rho = D * E.iW;
+      if (E.eclamp || ye_clamped) st |= GR_ST_EOS_CLAMP;
+      const double rho = EOS ? E.rho : D * E.iW;
       if (rho < rho_thr) { st |= GR_ST_ATM_THRESHOLD; atm = true; }
       if (!atm) {
         const double W = 1.0 / E.iW;
         w[0] = rho;
         for (int i = 0; i < 3; ++i) w[1 + i] = W * vu[i];
-        w[4] = (P.gamma_ad - 1.0) * rho * E.eps;
-        if (qmod) { q[0] = M.sg * D; q[4] = M.sg * tau; }
+        if constexpr (EOS == GR_EOS_IDEAL) {
+          w[4] = (P.gamma_ad - 1.0) * rho * E.eps;
+        } else {
+          w[4] = E.p;
+          w[5] = ye;
+          w[6] = exp(E.lT);
+          // temperature floor (App. A): T below T_atm -> T_atm, p recomputed, conserved rebuilt
+          if (w[6] < P.T_atm) {
+            double eps;
+            tab_p_eps_T<double>(P.t64, rho, log(P.T_atm), ye, &w[4], &eps);
+            w[6] = P.T_atm;
+            st |= GR_ST_EOS_CLAMP;
+            reprim = true;
+          }
+          if (ye_clamped) qmod = true;
+        }
+        if (qmod) {
+          q[0] = M.sg * D; q[4] = M.sg * tau;
+          if (EOS) q[5] = q[0] * ye;
+        }
       }
     }
   }
   if (atm) {
-    // atmosphere primitives (Sec. 3.5) and their conserved variables, Eq. consB_def at u~ = 0:
+    // atmosphere primitives (Sec. 3.5, App. A) and their conserved variables, Eq. consB_def at u~ = 0:
     // W = 1, b^0 = 0, b^2 = calB^2, so D = sqrt(gamma) rho, S_j = 0,
-    // tau = sqrt(gamma) (p/(Gamma - 1) + calB^2 / 2) = sqrt(gamma) p/(Gamma - 1) + gamma_ij B^i B^j/(2 sqrt(gamma))
+    // tau = sqrt(gamma) (rho eps + calB^2 / 2) = sqrt(gamma) rho eps + gamma_ij B^i B^j/(2 sqrt(gamma))
     w[0] = P.rho_atm;
     w[1] = w[2] = w[3] = 0.0;
     w[4] = P.p_atm;
@@ -825,7 +956,14 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     const double BBd = Bd[0] * Bl[0] + Bd[1] * Bl[1] + Bd[2] * Bl[2];
     q[0] = M.sg * P.rho_atm;
     q[1] = q[2] = q[3] = 0.0;
-    q[4] = M.sg * (P.p_atm / (P.gamma_ad - 1.0)) + (BBd == 0.0 ? 0.0 : 0.5 * BBd / M.sg);
+    q[4] = M.sg * P.eint_atm + (BBd == 0.0 ? 0.0 : 0.5 * BBd / M.sg);
+    if constexpr (EOS == GR_EOS_TABLE) {
+      w[5] = P.Ye_atm;
+      w[6] = P.T_atm;
+      q[5] = q[0] * P.Ye_atm;
+    }
+  } else if (reprim) {
+    cons_at<EOS>(M, P, w, Bd, q);
   }
   return st;
 }

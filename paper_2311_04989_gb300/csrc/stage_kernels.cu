@@ -5,12 +5,14 @@
 //   k_cellprep   cell-centred field calB^i = mean of faces / sqrt(gamma) on all cells, and the
 //                cell electric field E_m = alpha (v~^b B^a - v~^a B^b) on the ring -1..n  (Sec. 3.3)
 //   k_faces<R>   reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux (Eq. fluxB_def)
-//                on every face with normal index 0..n and transverse index -1..n
+//                on every face with normal index 0..n and transverse index -1..n; with a tabulated
+//                EOS (Sec. 2.3) also Y_e, and the D Y_e flux = D flux x upwind Y_e
 //   k_edges<R>   upwinded corner electric field from the four adjacent face fluxes (Sec. 3.3)
 //   k_ct         constrained-transport face update B' = g0 B0 + g1 B - beta dt curl E  (FP64)
 //   k_update     flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def) accumulated in
 //                FP64, then con2prim with atmosphere on the updated state (Sec. 3.5), FP64
 //
+// Kernels that evaluate the EOS are instantiated per EOS (ideal gas / table) as well as per R.
 // Every kernel takes one work item (block, direction, first element) per CTA; blocks of different
 // sizes share one launch.  Within a work item the direction is a compile-time constant (one
 // instantiation per direction), so no small array is indexed at run time.  Face fluxes and corner
@@ -138,18 +140,19 @@ __global__ void __launch_bounds__(kTile) k_cellprep(const DBlock* __restrict__ b
 // ------------------------------------------------------------------------------------------------
 // k_faces<R>
 // ------------------------------------------------------------------------------------------------
-template <class R, int D>
+template <class R, int EOS, int D>
 __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const InView<R>& in,
                                           const Workspace& ws, const KParams& kp) {
   int p[3];
   if (!decode<R_FACES, D>(w, b, p)) return;
   constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  constexpr int NV = EOS ? 8 : 7;   // rho, u~^i, p, calB^{t1}, calB^{t2}[, Y_e]
   // stencil cells p[D]-3 .. p[D]+2 along D
   const long long stride = cell_stride(b, D);
   int q[3] = {p[0], p[1], p[2]};
   q[D] -= 3;
   const long long c0 = cix(b, q[0], q[1], q[2]);
-  R st[7][6];
+  R st[NV][6];
   const bool wide = (b.g >= 3 || kp.recon == GR_RECON_WENOZ);
   const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]);
   const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]);
@@ -157,7 +160,7 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   for (int t = 0; t < 6; ++t) {
     if (!wide && (t == 0 || t == 5)) {
 #pragma unroll
-      for (int v = 0; v < 7; ++v) st[v][t] = R(0);
+      for (int v = 0; v < NV; ++v) st[v][t] = R(0);
       continue;
     }
     const long long c = c0 + t * stride;
@@ -165,16 +168,23 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
     for (int v = 0; v < 5; ++v) st[v][t] = in.W[v][b.cell + c];
     st[5][t] = bc1[b.wcell + c];
     st[6][t] = bc2[b.wcell + c];
+    if constexpr (EOS == GR_EOS_TABLE) st[7][t] = in.W[5][b.cell + c];
   }
   const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
-  R L[7], Rr[7];
+  R L[NV], Rr[NV];
 #pragma unroll
-  for (int v = 0; v < 7; ++v) recon<R>(kp.recon, st[v], eps, &L[v], &Rr[v]);
+  for (int v = 0; v < NV; ++v) recon<R>(kp.recon, st[v], eps, &L[v], &Rr[v]);
   // a non-physical reconstructed state (rho <= 0 or p <= 0) drops the face to first order
   if (!(L[0] > R(0)) || !(Rr[0] > R(0)) || !(L[4] > R(0)) || !(Rr[4] > R(0))) {
 #pragma unroll
-    for (int v = 0; v < 7; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
+    for (int v = 0; v < NV; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
   }
+  // face states (rho, u~^i, p[, Y_e])
+  R wl[6], wr[6];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { wl[v] = L[v]; wr[v] = Rr[v]; }
+  wl[5] = EOS ? L[NV - 1] : R(0);
+  wr[5] = EOS ? Rr[NV - 1] : R(0);
   R met[10];
   face_metric<R>(b, in, in.order, D, p, met);
   const R det = det3(met + 4);
@@ -186,28 +196,29 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   BL[D] = Bn; BR[D] = Bn;
   BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
   BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
-  const R gam = R(kp.gamma_ad);
   R UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
-  face_state<R>(D, met, sg, gdd, gam, L, BL, UL, FL, &lmL, &lpL);
-  face_state<R>(D, met, sg, gdd, gam, Rr, BR, UR, FR, &lmR, &lpR);
+  face_state<R, EOS>(D, met, sg, gdd, kp, wl, BL, UL, FL, &lmL, &lpL);
+  face_state<R, EOS>(D, met, sg, gdd, kp, wr, BR, UR, FR, &lmR, &lpR);
   R F[7];
   hlle<R>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
   R* out = reinterpret_cast<R*>(ws.flux[D]);
   const long long o = b.wface[D] + fi;
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
+  // D Y_e: the D equation times Y_e (Sec. 2.3), Y_e taken from the upwind state of the mass flux
+  if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
 }
 
-template <class R>
+template <class R, int EOS>
 __global__ void __launch_bounds__(kTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                  const __grid_constant__ InView<R> in,
                                                  const __grid_constant__ Workspace ws,
                                                  const __grid_constant__ KParams kp) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
-  if (w.dir == 0) face_body<R, 0>(w, b, in, ws, kp);
-  else if (w.dir == 1) face_body<R, 1>(w, b, in, ws, kp);
-  else face_body<R, 2>(w, b, in, ws, kp);
+  if (w.dir == 0) face_body<R, EOS, 0>(w, b, in, ws, kp);
+  else if (w.dir == 1) face_body<R, EOS, 1>(w, b, in, ws, kp);
+  else face_body<R, EOS, 2>(w, b, in, ws, kp);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -314,7 +325,7 @@ __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<doubl
   c2pmet_from(val + 4, M);
 }
 
-template <class R>
+template <class R, int EOS>
 __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                   const __grid_constant__ InView<R> in,
                                                   const __grid_constant__ InView<double> in64,
@@ -334,9 +345,10 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
   cellmet_from<R>(val, kzero, M);
   const long long c = b.cell + cix(b, i, j, k);
   // stage-input state at the cell: primitives and the mean densitised field of the input faces
-  R wv[5], Bd[3];
+  R wv[6], Bd[3];
 #pragma unroll
   for (int v = 0; v < 5; ++v) wv[v] = in.W[v][c];
+  wv[5] = EOS ? in.W[5][c] : R(0);
   {
     const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
     const long long f2 = b.face[2] + fix(b, 2, i, j, k);
@@ -345,9 +357,10 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
     Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
   }
   CellFluid<R> fl;
-  cell_fluid<R>(M, R(kp.gamma_ad), wv, Bd, fl);
-  R src[5];
+  cell_fluid<R, EOS>(M, kp, wv, Bd, fl);
+  R src[6];
   cell_sources<R>(M, fl, dm, kzero, src);
+  src[5] = R(0);   // D Y_e has no source (Sec. 2.3)
   // flux divergence, accumulated in FP64 (face values widened exactly)
   const R* F0 = reinterpret_cast<const R*>(ws.flux[0]);
   const R* F1 = reinterpret_cast<const R*>(ws.flux[1]);
@@ -358,10 +371,12 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
   const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
   const double bdt = kp.rk_beta * kp.dt;
   const double cx = bdt * b.idx[0], cy = bdt * b.idx[1], cz = bdt * b.idx[2];
+  // flux component of conserved variable v: D, S_j, tau at 0..4; D Y_e at 7 (5, 6 are induction)
+  auto comp = [](int v) { return v < 5 ? v : 7; };
   auto accumulate = [&](int v) {
-    const R* a0 = F0 + v * ws.fstride[0];
-    const R* a1 = F1 + v * ws.fstride[1];
-    const R* a2 = F2 + v * ws.fstride[2];
+    const R* a0 = F0 + comp(v) * ws.fstride[0];
+    const R* a1 = F1 + comp(v) * ws.fstride[1];
+    const R* a2 = F2 + comp(v) * ws.fstride[2];
     double u = kp.rk_g1 * s.U[v][c] + bdt * to64(src[v]);
     u -= cx * (to64(a0[g0 + 1]) - to64(a0[g0]));
     u -= cy * (to64(a1[g1 + oy]) - to64(a1[g1]));
@@ -369,11 +384,12 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
     if (kp.rk_g0 != 0.0) u += kp.rk_g0 * s.U0[v][c];
     return u;
   };
-  double q[5];
+  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
+  double q[6];
   q[0] = accumulate(0);
   double Bn[3];
   cell_field(b, s.Bo, i, j, k, Bn);
-  double wn[5];
+  double wn[7];
   int st;
   if (sizeof(R) == sizeof(float)) {
     // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
@@ -384,10 +400,10 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
     if (isfinite(q[0]) && q[0] < thr * sg32) {
       bool finite = true;
 #pragma unroll
-      for (int v = 1; v < 5; ++v) {
-        const R* a0 = F0 + v * ws.fstride[0];
-        const R* a1 = F1 + v * ws.fstride[1];
-        const R* a2 = F2 + v * ws.fstride[2];
+      for (int v = 1; v < NQ; ++v) {
+        const R* a0 = F0 + comp(v) * ws.fstride[0];
+        const R* a1 = F1 + comp(v) * ws.fstride[1];
+        const R* a2 = F2 + comp(v) * ws.fstride[2];
         const R t = a0[g0 + 1] - a0[g0] + a1[g1 + oy] - a1[g1] + a2[g2 + oz] - a2[g2] + src[v];
         finite = finite && isfinite(t) && isfinite(s.U[v][c]);
       }
@@ -397,35 +413,39 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
       const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
       q[0] = sg32 * kp.rho_atm;
       q[1] = q[2] = q[3] = 0.0;
-      q[4] = sg32 * (kp.p_atm / (kp.gamma_ad - 1.0)) + to64(R(0.5) * rdiv(BBd, M.sg));
+      q[4] = sg32 * kp.eint_atm + to64(R(0.5) * rdiv(BBd, M.sg));
       wn[0] = kp.rho_atm;
       wn[1] = wn[2] = wn[3] = 0.0;
       wn[4] = kp.p_atm;
+      if constexpr (EOS == GR_EOS_TABLE) {
+        q[5] = q[0] * kp.Ye_atm;
+        wn[5] = kp.Ye_atm;
+        wn[6] = kp.T_atm;
+      }
       st = finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED;
     } else {
 #pragma unroll
-      for (int v = 1; v < 5; ++v) q[v] = accumulate(v);
+      for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
       C2PMet Mc;
       cell_gamma64(b, in64, i, j, k, Mc);
       int iters;
-      st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
+      st = con2prim_cell<EOS>(Mc, kp, q, Bn, wn, &iters);
     }
   } else {
 #pragma unroll
-    for (int v = 1; v < 5; ++v) q[v] = accumulate(v);
+    for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
     C2PMet Mc;
 #pragma unroll
     for (int t = 0; t < 6; ++t) Mc.g[t] = to64(M.g[t]);
     Mc.sg = to64(M.sg);
     Mc.det = to64(M.det);
     int iters;
-    st = con2prim_cell(Mc, kp, q, Bn, wn, &iters);
+    st = con2prim_cell<EOS>(Mc, kp, q, Bn, wn, &iters);
   }
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    s.Uo[v][c] = q[v];
-    s.Wo[v][c] = wn[v];
-  }
+  for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
+#pragma unroll
+  for (int v = 0; v < NW; ++v) s.Wo[v][c] = wn[v];
   s.status[c] = (uint8_t)st;
 }
 
@@ -433,13 +453,14 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
 // stand-alone prim2con / con2prim / diagnostics (FP64)
 // ------------------------------------------------------------------------------------------------
 struct P2CArgs {
-  const double* W[5];
+  const double* W[7];
   const double* B[3];
-  double* U[5];
+  double* U[6];
   uint8_t* status;
   int32_t* evals;
 };
 
+template <int EOS>
 __global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                     const __grid_constant__ InView<double> m,
                                                     const __grid_constant__ P2CArgs a,
@@ -453,15 +474,18 @@ __global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ b
   CellMet<double> M;
   cellmet_from<double>(val, true, M);
   const long long c = b.cell + cix(b, p[0], p[1], p[2]);
-  double wv[5], Bd[3], q[5];
+  double wv[6], Bd[3], q[6];
   for (int v = 0; v < 5; ++v) wv[v] = a.W[v][c];
+  wv[5] = EOS ? a.W[5][c] : 0.0;
   cell_field(b, a.B, p[0], p[1], p[2], Bd);
   CellFluid<double> f;
-  cell_fluid<double>(M, kp.gamma_ad, wv, Bd, f);
+  cell_fluid<double, EOS>(M, kp, wv, Bd, f);
   cell_cons<double>(M, f, q);
   for (int v = 0; v < 5; ++v) a.U[v][c] = q[v];
+  if (EOS) a.U[5][c] = q[0] * wv[5];
 }
 
+template <int EOS>
 __global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                     const __grid_constant__ InView<double> m,
                                                     const __grid_constant__ P2CArgs a,
@@ -473,15 +497,14 @@ __global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ b
   C2PMet M;
   cell_gamma64(b, m, p[0], p[1], p[2], M);
   const long long c = b.cell + cix(b, p[0], p[1], p[2]);
-  double q[5], Bd[3], wn[5];
-  for (int v = 0; v < 5; ++v) q[v] = a.U[v][c];
+  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
+  double q[6], Bd[3], wn[7];
+  for (int v = 0; v < NQ; ++v) q[v] = a.U[v][c];
   cell_field(b, a.B, p[0], p[1], p[2], Bd);
   int iters = 0;
-  const int st = con2prim_cell(M, kp, q, Bd, wn, &iters);
-  for (int v = 0; v < 5; ++v) {
-    a.U[v][c] = q[v];
-    const_cast<double*>(a.W[v])[c] = wn[v];
-  }
+  const int st = con2prim_cell<EOS>(M, kp, q, Bd, wn, &iters);
+  for (int v = 0; v < NQ; ++v) a.U[v][c] = q[v];
+  for (int v = 0; v < NW; ++v) const_cast<double*>(a.W[v])[c] = wn[v];
   if (a.status) a.status[c] = (uint8_t)st;
   if (a.evals) a.evals[c] = iters;
 }
@@ -489,13 +512,14 @@ __global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ b
 // Training samples of the learned bracket: features and log(mu) of the plain bracketed solve of each
 // interior cell (valid = 0 where the cell is not solved: atmosphere, limits, failure)
 struct SampleArgs {
-  const double* U[5];
+  const double* U[6];
   const double* B[3];
-  float* feats[4];
+  float* feats[kMlpIn];
   float* target;
   uint8_t* valid;
 };
 
+template <int EOS>
 __global__ void __launch_bounds__(kTile) k_c2p_samples(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                        const __grid_constant__ InView<double> m,
                                                        const __grid_constant__ SampleArgs a,
@@ -507,19 +531,25 @@ __global__ void __launch_bounds__(kTile) k_c2p_samples(const DBlock* __restrict_
   C2PMet M;
   cell_gamma64(b, m, p[0], p[1], p[2], M);
   const long long c = b.cell + cix(b, p[0], p[1], p[2]);
-  double q[5], Bd[3], wn[5];
-  for (int v = 0; v < 5; ++v) q[v] = a.U[v][c];
+  constexpr int NQ = EOS ? 6 : 5;
+  double q[6], Bd[3], wn[7];
+  for (int v = 0; v < NQ; ++v) q[v] = a.U[v][c];
   cell_field(b, a.B, p[0], p[1], p[2], Bd);
   KParams k = kp;
   k.c2p_guess = GR_GUESS_NONE;
   int iters;
   C2PRecord rec;
-  const int st = con2prim_cell(M, k, q, Bd, wn, &iters, &rec);
+  const int st = con2prim_cell<EOS>(M, k, q, Bd, wn, &iters, &rec);
   const bool ok = rec.solved && (st & (GR_ST_BD_LIMIT | GR_ST_TAU_FLOOR)) == 0;
   a.valid[c] = ok ? 1 : 0;
-  float f[4] = {0.f, 0.f, 0.f, 0.f};
-  if (ok) c2p_features(rec.q, rec.r2, rec.b2, rec.rb, f);
-  for (int j = 0; j < 4; ++j) a.feats[j][c] = f[j];
+  float f[kMlpIn];
+  for (int j = 0; j < kMlpIn; ++j) f[j] = 0.f;
+  if (ok) {
+    c2p_features(rec.q, rec.r2, rec.b2, rec.rb, f);
+    f[4] = EOS ? (float)log(rec.D) : 0.f;
+    f[5] = EOS ? (float)rec.ye : 0.f;
+  }
+  for (int j = 0; j < kMlpIn; ++j) a.feats[j][c] = f[j];
   a.target[c] = ok ? (float)log(rec.mu) : 0.f;
 }
 
@@ -571,7 +601,7 @@ __global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ block
 static InView<double> view64(const MetricView& m, const StateView* s) {
   InView<double> v;
   for (int c = 0; c < 16; ++c) v.M[c] = m.v[c];
-  for (int q = 0; q < 5; ++q) v.W[q] = s ? s->W[q] : nullptr;
+  for (int q = 0; q < 6; ++q) v.W[q] = s ? s->W[q] : nullptr;
   for (int d = 0; d < 3; ++d) v.B[d] = s ? s->B[d] : nullptr;
   v.order = m.order;
   v.k_zero = m.k_zero;
@@ -581,17 +611,19 @@ static InView<double> view64(const MetricView& m, const StateView* s) {
 static InView<float> view32(const MetricView& m, const Shadow& sh) {
   InView<float> v;
   for (int c = 0; c < 16; ++c) v.M[c] = sh.M[c];
-  for (int q = 0; q < 5; ++q) v.W[q] = sh.W[q];
+  for (int q = 0; q < 6; ++q) v.W[q] = sh.W[q];
   for (int d = 0; d < 3; ++d) v.B[d] = sh.B[d];
   v.order = m.order;
   v.k_zero = m.k_zero;
   return v;
 }
 
-static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Shadow& sh, cudaStream_t st) {
+static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Shadow& sh, int eos,
+                               cudaStream_t st) {
   CastList L;
   int k = 0;
-  for (int q = 0; q < 5; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
+  const int nw = eos == GR_EOS_TABLE ? 6 : 5;   // rho, u~^i, p[, Y_e]
+  for (int q = 0; q < nw; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
   for (int d = 0; d < 3; ++d) { L.src[k] = s.B[d]; L.dst[k] = sh.B[d]; L.n[k] = sh.nface[d]; ++k; }
   const int ncomp = m.k_zero ? 10 : 16;
   for (int c = 0; c < ncomp; ++c) { L.src[k] = m.v[c]; L.dst[k] = sh.M[c]; L.n[k] = sh.nvert; ++k; }
@@ -601,20 +633,21 @@ static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Sh
   return cudaGetLastError();
 }
 
-template <class R>
+template <class R, int EOS>
 static cudaError_t stage_impl(const DBlock* blocks, const Work* const work[R_NREGION],
                               const int nwork[R_NREGION], const InView<R>& in, const InView<double>& in64,
                               const StateView& s, const Workspace& ws, const KParams& kp, cudaStream_t st,
                               cudaEvent_t* ev) {
   if (nwork[R_CELLS_ALL]) k_cellprep<R><<<nwork[R_CELLS_ALL], kTile, 0, st>>>(blocks, work[R_CELLS_ALL], in, ws);
   if (ev) cudaEventRecord(ev[2], st);
-  if (nwork[R_FACES]) k_faces<R><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
+  if (nwork[R_FACES]) k_faces<R, EOS><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
   if (ev) cudaEventRecord(ev[3], st);
   if (nwork[R_EDGES]) k_edges<R><<<nwork[R_EDGES], kTile, 0, st>>>(blocks, work[R_EDGES], ws, kp);
   if (ev) cudaEventRecord(ev[4], st);
   if (nwork[R_CTFACES]) k_ct<R><<<nwork[R_CTFACES], kTile, 0, st>>>(blocks, work[R_CTFACES], s, ws, kp);
   if (ev) cudaEventRecord(ev[5], st);
-  if (nwork[R_INTERIOR]) k_update<R><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
+  if (nwork[R_INTERIOR])
+    k_update<R, EOS><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
   if (ev) cudaEventRecord(ev[6], st);
   return cudaGetLastError();
 }
@@ -625,57 +658,70 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const 
                          cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   const InView<double> in64 = view64(m, &s);
+  const bool tab = kp.eos == GR_EOS_TABLE;
   if (precision == GR_PREC_MIXED) {
-    cudaError_t e = launch_cast(m, s, sh, st);
+    cudaError_t e = launch_cast(m, s, sh, kp.eos, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    return stage_impl<float>(blocks, work, nwork, view32(m, sh), in64, s, ws, kp, st, ev);
+    const InView<float> in32 = view32(m, sh);
+    return tab ? stage_impl<float, GR_EOS_TABLE>(blocks, work, nwork, in32, in64, s, ws, kp, st, ev)
+               : stage_impl<float, GR_EOS_IDEAL>(blocks, work, nwork, in32, in64, s, ws, kp, st, ev);
   }
   if (ev) cudaEventRecord(ev[1], st);
-  return stage_impl<double>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev);
+  return tab ? stage_impl<double, GR_EOS_TABLE>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev)
+             : stage_impl<double, GR_EOS_IDEAL>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev);
 }
 
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                            const double* const W[5], const double* const B[3], double* const U[5],
+                            const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st) {
   P2CArgs a;
-  for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
+  for (int v = 0; v < 7; ++v) a.W[v] = W[v];
+  for (int v = 0; v < 6; ++v) a.U[v] = U[v];
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = nullptr;
   a.evals = nullptr;
-  if (nwork) k_prim2con<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  if (!nwork) return cudaSuccess;
+  if (kp.eos == GR_EOS_TABLE) k_prim2con<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  else k_prim2con<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                            double* const U[5], const double* const B[3], double* const W[5],
+                            double* const U[6], const double* const B[3], double* const W[7],
                             uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st) {
   P2CArgs a;
-  for (int v = 0; v < 5; ++v) { a.W[v] = W[v]; a.U[v] = U[v]; }
+  for (int v = 0; v < 7; ++v) a.W[v] = W[v];
+  for (int v = 0; v < 6; ++v) a.U[v] = U[v];
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = status;
   a.evals = evals;
-  if (nwork) k_con2prim<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  if (!nwork) return cudaSuccess;
+  if (kp.eos == GR_EOS_TABLE) k_con2prim<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  else k_con2prim<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
-                               const double* const U[5], const double* const B[3], float* const feats[4],
+                               const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st) {
   SampleArgs a;
-  for (int v = 0; v < 5; ++v) a.U[v] = U[v];
+  for (int v = 0; v < 6; ++v) a.U[v] = U[v];
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
-  for (int j = 0; j < 4; ++j) a.feats[j] = feats[j];
+  for (int j = 0; j < kMlpIn; ++j) a.feats[j] = feats[j];
   a.target = target;
   a.valid = valid;
-  if (nwork) k_c2p_samples<<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  if (!nwork) return cudaSuccess;
+  if (kp.eos == GR_EOS_TABLE)
+    k_c2p_samples<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  else k_c2p_samples<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const double* const U[5],
                         const double* const B[3], double* dev_out, cudaStream_t st) {
-  P2CArgs a;
-  for (int v = 0; v < 5; ++v) { a.W[v] = nullptr; a.U[v] = const_cast<double*>(U[v]); }
+  P2CArgs a{};
+  for (int v = 0; v < 5; ++v) a.U[v] = const_cast<double*>(U[v]);
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.status = nullptr;
   a.evals = nullptr;

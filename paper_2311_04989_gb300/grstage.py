@@ -21,6 +21,7 @@ GR_RECON_PLM, GR_RECON_WENOZ = 0, 1
 GR_PREC_FP64, GR_PREC_MIXED = 0, 1
 GR_EMF_UPWIND, GR_EMF_MEAN = 0, 1
 GR_CEIL_CLAMP, GR_CEIL_ATMOSPHERE = 0, 1
+GR_EOS_IDEAL, GR_EOS_TABLE = 0, 1
 GR_ST_ATM_THRESHOLD, GR_ST_FAILED, GR_ST_W_CLAMPED = 0x01, 0x02, 0x04
 GR_ST_TAU_FLOOR, GR_ST_BD_LIMIT, GR_ST_EOS_CLAMP = 0x08, 0x10, 0x20
 GR_ST_GUESS_REJECTED = 0x40
@@ -32,8 +33,11 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end",
            "gr_diag_noalloc", "gr_noalloc_last_error", "gr_mlp_nparam", "gr_mlp_last_error", "gr_c2p_samples",
            "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
-           "gr_graph_destroy"]
-GR_MLP_NPARAM = 4561
+           "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0"]
+GR_ABI_VERSION = 2
+GR_MLP_NPARAM = 4689
+GR_MLP_NIN = 6
+MLP_MEAN, MLP_ISTD, MLP_TMEAN, MLP_TSTD, MLP_STEP = 0, 6, 12, 13, 14
 GR_NKERNELS = 6
 KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
 
@@ -52,9 +56,14 @@ class gr_metric(C.Structure):
 
 
 class gr_state(C.Structure):
-    _fields_ = [("U", C.c_void_p * 5), ("U0", C.c_void_p * 5), ("B", C.c_void_p * 3), ("B0", C.c_void_p * 3),
-                ("W", C.c_void_p * 5), ("Uo", C.c_void_p * 5), ("Bo", C.c_void_p * 3), ("Wo", C.c_void_p * 5),
+    _fields_ = [("U", C.c_void_p * 6), ("U0", C.c_void_p * 6), ("B", C.c_void_p * 3), ("B0", C.c_void_p * 3),
+                ("W", C.c_void_p * 7), ("Uo", C.c_void_p * 6), ("Bo", C.c_void_p * 3), ("Wo", C.c_void_p * 7),
                 ("status", C.c_void_p)]
+
+
+class gr_eos_table(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("pad_", C.c_int32), ("x0", C.c_double * 3), ("dx", C.c_double * 3),
+                ("log_p", C.c_void_p), ("log_e", C.c_void_p), ("cs2", C.c_void_p)]
 
 
 class gr_params(C.Structure):
@@ -62,7 +71,8 @@ class gr_params(C.Structure):
                 ("ceiling", C.c_int32), ("max_iter", C.c_int32), ("c2p_guess", C.c_int32), ("gamma_ad", C.c_double),
                 ("rho_atm", C.c_double), ("p_atm", C.c_double), ("f_thr", C.c_double), ("W_max", C.c_double),
                 ("M_max", C.c_double), ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
-                ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("mlp", C.c_void_p)]
+                ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("mlp", C.c_void_p), ("eos", C.c_int32),
+                ("pad_", C.c_int32), ("table", C.c_void_p), ("T_atm", C.c_double), ("Ye_atm", C.c_double)]
 
 
 _lib = None
@@ -89,18 +99,24 @@ def load(path: str = LIB_PATH):
     L.gr_mesh_workspace_bytes.argtypes = [vp]
     L.gr_mesh_workspace_bytes.restype = C.c_int64
     L.gr_stage.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params), vp]
-    L.gr_prim2con.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5,
+    L.gr_prim2con.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 7, C.c_void_p * 3, C.c_void_p * 6,
                               C.POINTER(gr_params), vp]
-    L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.c_void_p * 5, vp, vp,
+    L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 6, C.c_void_p * 3, C.c_void_p * 7, vp, vp,
                               C.POINTER(gr_params), vp]
+    L.gr_eos_create.argtypes = [vp, C.POINTER(gr_eos_table), C.POINTER(vp)]
+    L.gr_eos_destroy.argtypes = [vp]
+    L.gr_eos_bytes.argtypes = [vp]
+    L.gr_eos_bytes.restype = C.c_int64
+    L.gr_eos_h0.argtypes = [vp]
+    L.gr_eos_h0.restype = C.c_double
     L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
     L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
                                   C.POINTER(C.c_double), vp]
     L.gr_noalloc_last_error.restype = C.c_char_p
     L.gr_mlp_nparam.restype = C.c_int
     L.gr_mlp_last_error.restype = C.c_char_p
-    L.gr_c2p_samples.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 5, C.c_void_p * 3, C.POINTER(gr_params),
-                                 C.c_void_p * 4, vp, vp, vp]
+    L.gr_c2p_samples.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 6, C.c_void_p * 3, C.POINTER(gr_params),
+                                 C.c_void_p * 6, vp, vp, vp]
     L.gr_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.gr_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
     L.gr_mlp_train.argtypes = [vp, vp, vp, C.c_int64, i32, i32, C.c_float, C.POINTER(C.c_float), vp]
@@ -113,7 +129,7 @@ def load(path: str = LIB_PATH):
     for f in EXPORTS:
         if not hasattr(L, f):
             raise GrstageError(f"libgrstage.so lacks {f}")
-    if L.gr_abi_version() != 1:
+    if L.gr_abi_version() != GR_ABI_VERSION:
         raise GrstageError("libgrstage.so ABI version mismatch")
     _lib = L
     return L
@@ -172,24 +188,55 @@ def gr_stage(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_par
 
 
 def _ptrs(n, ts):
-    return (C.c_void_p * n)(*[int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t) for t in ts])
+    """Pointer array of n entries from tensors (or ints); missing trailing entries are NULL."""
+    ts = list(ts)[:n]
+    vals = [int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t) for t in ts]
+    return (C.c_void_p * n)(*(vals + [0] * (n - len(vals))))
 
 
 def gr_prim2con(mesh, metric: gr_metric, W, B, U, params: gr_params, stream=None):
-    _check(load().gr_prim2con(mesh, C.byref(metric), _ptrs(5, W), _ptrs(3, B), _ptrs(5, U), C.byref(params),
+    """W: 5 (ideal gas) or 6-7 (table: rho, u~^i, p, Y_e[, T]) cell pools; U: 5 or 6."""
+    _check(load().gr_prim2con(mesh, C.byref(metric), _ptrs(7, W), _ptrs(3, B), _ptrs(6, U), C.byref(params),
                               _stream(stream)), "gr_prim2con")
 
 
 def gr_con2prim(mesh, metric: gr_metric, U, B, W, status, params: gr_params, stream=None, evals=None):
     st = int(status.data_ptr()) if status is not None else 0
     ev = int(evals.data_ptr()) if evals is not None else 0
-    _check(load().gr_con2prim(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), _ptrs(5, W), st, ev,
+    _check(load().gr_con2prim(mesh, C.byref(metric), _ptrs(6, U), _ptrs(3, B), _ptrs(7, W), st, ev,
                               C.byref(params), _stream(stream)), "gr_con2prim")
+
+
+class EosHandle:
+    """gr_eos on a device; keep it alive while params reference it."""
+
+    def __init__(self, h, nbytes, h0):
+        self.h, self.nbytes, self.h0 = h, nbytes, h0
+
+    def __int__(self):
+        return int(self.h.value)
+
+
+def gr_eos_create(ctx, table) -> EosHandle:
+    """table: object with n, x0, dx and float64 arrays lp, le, cs2 of shape (n_Ye, n_T, n_rho)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (table.lp, table.le, table.cs2)]
+    for a in arrs:
+        assert a.shape == (table.n[2], table.n[1], table.n[0])
+    t = gr_eos_table((C.c_int32 * 3)(*table.n), 0, (C.c_double * 3)(*table.x0), (C.c_double * 3)(*table.dx),
+                     *(a.ctypes.data for a in arrs))
+    h = C.c_void_p()
+    L = load()
+    _check(L.gr_eos_create(ctx, C.byref(t), C.byref(h)), "gr_eos_create")
+    return EosHandle(h, int(L.gr_eos_bytes(h)), float(L.gr_eos_h0(h)))
+
+
+def gr_eos_destroy(eos: EosHandle):
+    load().gr_eos_destroy(eos.h)
 
 
 def gr_diag(mesh, U, B, stream=None):
     out = (C.c_double * 4)()
-    _check(load().gr_diag(mesh, _ptrs(5, U), _ptrs(3, B), out, _stream(stream)), "gr_diag")
+    _check(load().gr_diag(mesh, _ptrs(5, list(U)[:5]), _ptrs(3, B), out, _stream(stream)), "gr_diag")
     return list(out)
 
 
@@ -198,7 +245,7 @@ def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):
     arr = (gr_block * max(1, len(blocks)))(*blocks)
     out = (C.c_double * 4)()
     L = load()
-    rc = L.gr_diag_noalloc(arr, len(blocks), _ptrs(5, U), _ptrs(3, B), out, _stream(stream))
+    rc = L.gr_diag_noalloc(arr, len(blocks), _ptrs(5, list(U)[:5]), _ptrs(3, B), out, _stream(stream))
     if rc != GR_OK:
         raise GrstageError(f"gr_diag_noalloc: {L.gr_strerror(rc).decode()} ({L.gr_noalloc_last_error().decode()})")
     return list(out)
@@ -226,7 +273,7 @@ def _mcheck(rc, what):
 
 
 def gr_c2p_samples(mesh, metric: gr_metric, U, B, params: gr_params, feats, target, valid, stream=None):
-    _check(load().gr_c2p_samples(mesh, C.byref(metric), _ptrs(5, U), _ptrs(3, B), C.byref(params), _ptrs(4, feats),
+    _check(load().gr_c2p_samples(mesh, C.byref(metric), _ptrs(6, U), _ptrs(3, B), C.byref(params), _ptrs(6, feats),
                                  int(target.data_ptr()), int(valid.data_ptr()), _stream(stream)), "gr_c2p_samples")
 
 
@@ -324,12 +371,14 @@ def metric_struct(metric_pool, order: int = 2, k_zero: bool = True) -> gr_metric
 
 
 def state_struct(U, U0, B, B0, W, Uo, Bo, Wo, status) -> gr_state:
+    """U, U0, Uo: 5 (or 6 with a table) cell pools; W, Wo: 5 (or 7) cell pools."""
     s = gr_state()
-    for v in range(5):
+    for v in range(len(U)):
         s.U[v] = int(U[v].data_ptr())
         s.U0[v] = int(U0[v].data_ptr()) if U0 is not None else 0
-        s.W[v] = int(W[v].data_ptr())
         s.Uo[v] = int(Uo[v].data_ptr())
+    for v in range(len(W)):
+        s.W[v] = int(W[v].data_ptr())
         s.Wo[v] = int(Wo[v].data_ptr())
     for d in range(3):
         s.B[d] = int(B[d].data_ptr())
@@ -340,15 +389,16 @@ def state_struct(U, U0, B, B0, W, Uo, Bo, Wo, status) -> gr_state:
 
 
 def pack_blocks(blocks, device="cuda"):
-    """Device pools (torch) of a list of blocks with numpy arrays W (5,...), B [3], metric (16,...).
+    """Device pools (torch) of a list of blocks with numpy arrays W (5 or 7,...), B [3], metric (16,...).
     Returns (layout, W pool, [B pools], metric pool)."""
     import torch
     L = Layout.of(blocks)
-    W = np.zeros((5, max(L.ncell, 1)))
+    nw = np.asarray(blocks[0].W).shape[0] if len(blocks) else 5
+    W = np.zeros((nw, max(L.ncell, 1)))
     M = np.zeros((16, max(L.nvert, 1)))
     Bp = [np.zeros(max(L.nface[d], 1)) for d in range(3)]
     for b, bi in enumerate(blocks):
-        w = np.asarray(bi.W).reshape(5, -1)
+        w = np.asarray(bi.W).reshape(nw, -1)
         W[:, L.cell_off[b]:L.cell_off[b] + w.shape[1]] = w
         m = np.asarray(bi.metric).reshape(16, -1)
         M[:, L.vert_off[b]:L.vert_off[b] + m.shape[1]] = m

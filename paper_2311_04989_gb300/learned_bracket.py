@@ -16,16 +16,16 @@ NW = G.GR_MLP_NPARAM - 16
 
 
 def collect(ctx, blocks, params: G.gr_params, device="cuda"):
-    """Features (n,4) and log mu (n,) of the plain bracketed solves of the interior cells of blocks
+    """Features (n,6) and log mu (n,) of the plain bracketed solves of the interior cells of blocks
     (their conserved variables formed from the blocks' primitives by gr_prim2con)."""
     import torch
     L, W, B, M = G.pack_blocks(blocks, device)
     mesh = G.gr_mesh_create(ctx, L.descriptors())
     try:
         metric = G.metric_struct(M)
-        U = torch.zeros_like(W)
+        U = torch.zeros((6 if params.eos == G.GR_EOS_TABLE else 5, W.shape[1]), dtype=W.dtype, device=W.device)
         G.gr_prim2con(mesh, metric, list(W), B, list(U), params)
-        feats = [torch.zeros(L.ncell, dtype=torch.float32, device=device) for _ in range(4)]
+        feats = [torch.zeros(L.ncell, dtype=torch.float32, device=device) for _ in range(G.GR_MLP_NIN)]
         target = torch.zeros(L.ncell, dtype=torch.float32, device=device)
         valid = torch.zeros(L.ncell, dtype=torch.uint8, device=device)
         G.gr_c2p_samples(mesh, metric, list(U), B, params, feats, target, valid)
@@ -47,15 +47,16 @@ def init_params(x, t, seed=0, device="cuda"):
     (Glorot-uniform scale per layer)."""
     import torch
     P = np.zeros(G.GR_MLP_NPARAM, np.float32)
+    nin = G.GR_MLP_NIN
     xm = x.mean(0).cpu().numpy(); xs = x.std(0).cpu().numpy()
-    P[0:4] = xm
-    P[4:8] = 1.0 / np.maximum(xs, 1e-6)
-    P[8] = float(t.mean().item())
-    P[9] = max(float(t.std().item()), 1e-6)
-    P[10] = 1.0
+    P[G.MLP_MEAN:G.MLP_MEAN + nin] = xm
+    P[G.MLP_ISTD:G.MLP_ISTD + nin] = 1.0 / np.maximum(xs, 1e-6)
+    P[G.MLP_TMEAN] = float(t.mean().item())
+    P[G.MLP_TSTD] = max(float(t.std().item()), 1e-6)
+    P[G.MLP_STEP] = 1.0
     rng = np.random.default_rng(2311_04989 + seed)
     off = 16
-    for (nout, nin) in ((64, 4), (64, 64), (1, 64)):
+    for (nout, nin) in ((64, nin), (64, 64), (1, 64)):
         lim = np.sqrt(6.0 / (nin + nout))
         P[off:off + nout * nin] = rng.uniform(-lim, lim, nout * nin)
         off += nout * nin + nout          # biases stay 0
@@ -67,8 +68,8 @@ def set_step(P, x, t, quantile=0.75, floor=1e-5):
     typical error: larger ones are reached by the doubling steps), at least floor."""
     r = (G.gr_mlp_forward(P, x) - t).abs()
     q = float(np.quantile(r.cpu().numpy(), quantile))
-    P[10] = max(q, floor)
-    return float(P[10].item())
+    P[G.MLP_STEP] = max(q, floor)
+    return float(P[G.MLP_STEP].item())
 
 
 def train(x, t, epochs=60, batch=1024, lr=2e-3, seed=0, holdout=0.1):

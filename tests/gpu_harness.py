@@ -19,12 +19,29 @@ def ctx():
     return _ctx
 
 
+_eos = {}
+
+
+def eos_handle(table):
+    """gr_eos of an EOS table object (created once per table object and kept alive)."""
+    key = id(table)
+    if key not in _eos:
+        _eos[key] = (table, G.gr_eos_create(ctx(), table))
+    return _eos[key][1]
+
+
 def gr_params_from(P: O.Params, precision=G.GR_PREC_FP64, c2p_guess=G.GR_GUESS_NONE):
     c = P.c()
-    return G.gr_params_default(recon=P.recon, precision=precision, emf=P.emf, ceiling=P.ceiling, c2p_guess=c2p_guess,
-                               max_iter=P.max_iter, gamma_ad=P.gamma_ad, rho_atm=P.rho_atm, p_atm=c.p_atm,
-                               f_thr=P.f_thr, W_max=P.W_max, M_max=P.M_max, tol=P.tol, weno_eps=P.weno_eps,
-                               rk_g0=P.rk_g0, rk_g1=P.rk_g1, rk_beta=P.rk_beta)
+    p = G.gr_params_default(recon=P.recon, precision=precision, emf=P.emf, ceiling=P.ceiling, c2p_guess=c2p_guess,
+                            max_iter=P.max_iter, gamma_ad=P.gamma_ad, rho_atm=P.rho_atm, p_atm=c.p_atm,
+                            f_thr=P.f_thr, W_max=P.W_max, M_max=P.M_max, tol=P.tol, weno_eps=P.weno_eps,
+                            rk_g0=P.rk_g0, rk_g1=P.rk_g1, rk_beta=P.rk_beta)
+    if P.table is not None:
+        p.eos = G.GR_EOS_TABLE
+        p.table = int(eos_handle(P.table))
+        p.T_atm = P.T_atm
+        p.Ye_atm = P.Ye_atm
+    return p
 
 
 class Pools:
@@ -98,9 +115,10 @@ def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None
     if U is None:
         U = [H.cons_from_prims(bi, P, order) for bi in blocks]
     pools = Pools(blocks)
-    Ud = pools.cells(U, 5)
-    U0d = pools.cells(U0 if U0 is not None else U, 5)
-    Wd = pools.cells([bi.W for bi in blocks], 5)
+    nq, nw = P.nq, P.nw
+    Ud = pools.cells(U, nq)
+    U0d = pools.cells(U0 if U0 is not None else U, nq)
+    Wd = pools.cells([bi.W for bi in blocks], nw)
     Bd = pools.faces([bi.B for bi in blocks])
     B0d = pools.faces(B0 if B0 is not None else [bi.B for bi in blocks])
     Md = pools.verts([bi.metric for bi in blocks])
@@ -114,8 +132,8 @@ def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None
         torch.cuda.synchronize()
     finally:
         G.gr_mesh_destroy(mesh)
-    Uo_b = pools.unpack_cells(Uo, 5)
-    Wo_b = pools.unpack_cells(Wo, 5)
+    Uo_b = pools.unpack_cells(Uo, nq)
+    Wo_b = pools.unpack_cells(Wo, nw)
     st_b = pools.unpack_cells(st, 1)
     Bo_b = pools.unpack_faces(Bo)
     out = [dict(U=Uo_b[b], B=Bo_b[b], W=Wo_b[b], status=st_b[b]) for b in range(len(blocks))]
@@ -136,7 +154,7 @@ def oracle_stage(blocks, P: O.Params, dt, U=None, U0=None, B0=None):
 REL_FLOOR = {"W0": 0.0, "W4": 0.0}   # rho, p: plain relative
 
 
-def compare(gpu, ref, blocks=None):
+def compare(gpu, ref, blocks=None, skip=()):
     """Max relative error per variable over interior cells / faces of all blocks, and the number of
     status mismatches.  Denominators:
       D, rho, p           |ref| (plain relative)
@@ -144,20 +162,23 @@ def compare(gpu, ref, blocks=None):
                           size of the cell's energy density, so rounding differences scale with it
                           (e.g. tau ~ p/(Gamma-1) ~ 1e-30 in the atmosphere is a difference of
                           terms ~ rho ~ 1e-16; S' in a star in equilibrium is a small residual)
-      u~^i, B faces       max(|ref|, 1e-3 max|ref| of the block) (they pass through zero)."""
+      u~^i, B faces       max(|ref|, 1e-3 max|ref| of the block) (they pass through zero)
+      D Y_e, Y_e, T       plain relative (table).  Variables named in skip are left out."""
     errs = {}
     nmis = 0
     for b, (g, r) in enumerate(zip(gpu, ref)):
         n, ng = _geom(g, r, blocks, b)
-        for key, nv in (("U", 5), ("W", 5)):
+        for key in ("U", "W"):
             gi = H.interior(g[key], n, ng)
             ri = H.interior(r[key], n, ng)
             if not ri.size:
                 continue
-            for v in range(nv):
+            for v in range(ri.shape[0]):
                 name = f"{key}{v}"
-                if key == "U" and v == 0:
-                    den = np.maximum(np.abs(ri[0]), 1e-300)
+                if name in skip:
+                    continue
+                if (key == "U" and v in (0, 5)) or (key == "W" and v >= 5):
+                    den = np.maximum(np.abs(ri[v]), 1e-300)
                 elif key == "U":
                     den = np.maximum(np.abs(ri[v]), np.abs(ri[0]) + np.abs(ri[4]))
                 else:

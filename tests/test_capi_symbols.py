@@ -42,7 +42,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_pure_host_entries(lib):
-    assert lib.gr_abi_version() == 1
+    assert lib.gr_abi_version() == G.GR_ABI_VERSION == 2
+    assert lib.gr_mlp_nparam() == G.GR_MLP_NPARAM
     assert lib.gr_strerror(G.GR_EINVAL) == b"invalid argument"
     p = G.gr_params_default()
     assert p.size == __import__("ctypes").sizeof(G.gr_params)
@@ -54,7 +55,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     import ctypes as C
     import subprocess
     structs = {"gr_block": G.gr_block, "gr_metric": G.gr_metric, "gr_state": G.gr_state,
-               "gr_params": G.gr_params}
+               "gr_params": G.gr_params, "gr_eos_table": G.gr_eos_table}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "grstage.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -70,3 +71,10 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert int(out[name]) == C.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_header_constants_match_the_binding():
+    txt = open(os.path.join(ROOT, "include", "grstage.h")).read()
+    for name in ("GR_ABI_VERSION", "GR_MLP_NPARAM", "GR_MLP_NIN", "GR_NKERNELS"):
+        m = re.search(rf"#define {name} (\d+)", txt)
+        assert m and int(m.group(1)) == getattr(G, name), name

@@ -38,7 +38,7 @@ def test_sampler_matches_the_oracle():
     Ud, Bd, Md = pools.cells([U], 5), pools.faces([bi.B]), pools.verts([bi.metric])
     mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
     nc = pools.L.ncell
-    feats = [torch.zeros(nc, dtype=torch.float32, device="cuda") for _ in range(4)]
+    feats = [torch.zeros(nc, dtype=torch.float32, device="cuda") for _ in range(G.GR_MLP_NIN)]
     target = torch.zeros(nc, dtype=torch.float32, device="cuda")
     valid = torch.zeros(nc, dtype=torch.uint8, device="cuda")
     G.gr_c2p_samples(mesh, G.metric_struct(Md), list(Ud), Bd, GH.gr_params_from(P), feats, target, valid)
@@ -60,10 +60,13 @@ def test_forward_and_gradient_match_the_oracle():
     import torch
     rng = np.random.default_rng(71)
     P = np.zeros(G.GR_MLP_NPARAM)
-    P[0:4] = rng.normal(0, 1, 4); P[4:8] = rng.uniform(0.5, 2, 4); P[8], P[9] = -0.7, 0.4
+    nin = G.GR_MLP_NIN
+    P[G.MLP_MEAN:G.MLP_MEAN + nin] = rng.normal(0, 1, nin)
+    P[G.MLP_ISTD:G.MLP_ISTD + nin] = rng.uniform(0.5, 2, nin)
+    P[G.MLP_TMEAN], P[G.MLP_TSTD] = -0.7, 0.4
     P[16:] = rng.normal(0, 0.3, G.GR_MLP_NPARAM - 16)
     P = P.astype(np.float32).astype(np.float64)     # the values the GPU sees
-    x = rng.normal(0, 1, (1000, 4)).astype(np.float32).astype(np.float64)
+    x = rng.normal(0, 1, (1000, nin)).astype(np.float32).astype(np.float64)
     t = rng.normal(-0.7, 0.5, 1000).astype(np.float32).astype(np.float64)
     Pd = torch.tensor(P, dtype=torch.float32, device="cuda")
     xd = torch.tensor(x, dtype=torch.float32, device="cuda")
