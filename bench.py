@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim bracket-guess timings")
     ap.add_argument("--no-table", action="store_true", help="skip the tabulated-EOS con2prim workload")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of gr_autotune's")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -351,6 +352,10 @@ def main():
         guess = G.GR_GUESS_FP32 if precision == G.GR_PREC_MIXED else G.GR_GUESS_NONE
         p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=precision, gamma_ad=2.0, c2p_guess=guess,
                                 rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        # launch shapes per kernel from the library's autotuner (untimed; it runs the stage itself)
+        shapes = None
+        if not a.no_autotune:
+            shapes, _ = G.gr_autotune(mesh, metric, state, dt, p, 1 if precision == G.GR_PREC_FP64 else 3, stream)
         for _ in range(a.warmup):
             G.gr_stage(mesh, metric, state, dt, p, stream)
         torch.cuda.synchronize()
@@ -373,15 +378,16 @@ def main():
         ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
         if dist:
             dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        return ms_t.item() / a.steps, [k / max(1, nst) for k in kms], clocks
+        return ms_t.item() / a.steps, [k / max(1, nst) for k in kms], clocks, shapes
 
     results = {}
     precs = {"both": ["fp64", "mixed"], "fp64": ["fp64"], "mixed": ["mixed"]}[a.precision]
     snap = {}
     for name in precs:
         prec = G.GR_PREC_FP64 if name == "fp64" else G.GR_PREC_MIXED
-        ms, kms, clocks = timed(prec)
-        results[name] = dict(ms=ms, kernel_ms=kms, clocks=clocks)
+        ms, kms, clocks, shapes = timed(prec)
+        results[name] = dict(ms=ms, kernel_ms=kms, clocks=clocks,
+                             shapes=dict(zip(G.KERNEL_NAMES[1:], shapes)) if shapes else None)
         snap[name] = (Wo[0].clone(), [x.clone() for x in Bo], Uo.clone())
         stv = st.to(torch.int32)
         results[name]["status"] = {"atmosphere": int(((stv & 1) != 0).sum().item()),
@@ -519,8 +525,9 @@ def main():
     def ph_flops(*names):
         return sum(ph[n]["add"] + ph[n]["mul"] + ph[n]["div"] + ph[n]["sqrt"] for n in names)
 
-    kernel_phases = {"k_cast": (), "k_cellprep": ("cell_metric_and_field", "cell_efield"), "k_faces": ("faces",),
-                     "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources", "con2prim")}
+    kernel_phases = {"k_cast": (), "k_c2p": ("con2prim",), "k_cellprep": ("cell_metric_and_field", "cell_efield"),
+                     "k_faces": ("faces",),
+                     "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources",)}
     scale = (a.nb ** 3) / 4096.0
 
     def roofline(name):
@@ -556,7 +563,8 @@ def main():
                "sample": f"{nblk} seeded-random blocks of the same workload, FP64 oracle stage, "
                          f"{nthreads} threads, {wall:.1f} s"}
 
-    launches = a.steps * (6 if head == "mixed" else 5)     # the mixed path adds the FP32 cast kernel
+    # cell prep, faces, edges, CT, update, con2prim (+ the FP32 cast on the mixed path) per stage
+    launches = a.steps * (7 if head == "mixed" else 6)
     fp64 = None
     if "fp64" in results and head != "fp64":
         fp64 = {"value": cells * world / (results["fp64"]["ms"] / 1e3), "ms_per_step": results["fp64"]["ms"],
@@ -573,6 +581,7 @@ def main():
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
            "graph_ms_per_step": graph_ms, "con2prim_guess": c2p, "con2prim_table": c2p_table,
+           "launch_shapes": {k: v.get("shapes") for k, v in results.items()},
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -185,6 +185,28 @@ int gr_graph_capture(gr_mesh* mesh, const gr_metric* metric, const gr_state* sta
 int gr_graph_launch(gr_graph* graph, void* stream);
 int gr_graph_destroy(gr_graph* graph);
 
+/* Launch shape of a stage kernel: CTA size tile (64, 128 or 256 threads = elements of one work item),
+ * order of the work list (0: direction-major, 1: block-major) and persistent (0: one CTA per work item;
+ * 1: as many CTAs as fit on the GPU at once, each striding over the list).  The kernels are cell prep,
+ * faces, edges, CT, update and con2prim (the order of con2prim's job list is moot).  Every shape gives
+ * bitwise the same results. */
+#define GR_NSTAGE_KERNELS 6
+typedef struct {
+  int32_t tile;
+  int32_t order;
+  int32_t persistent;
+} gr_shape;
+/* Autotuner (project-written; the paper has no counterpart): runs the stage on this mesh and state with
+ * every shape (3 tiles x 2 orders x 2 grids), reps timed runs each after one warm-up, times each kernel
+ * with CUDA events on `stream`, and keeps per kernel the fastest shape for (params->precision,
+ * params->eos); later gr_stage and gr_graph_capture calls use it.  Writes the stage outputs.
+ * best_ms (may be NULL) receives the mean time of each kernel's chosen shape.  Synchronises the stream. */
+int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
+                int32_t reps, void* stream, double best_ms[GR_NSTAGE_KERNELS]);
+/* Shapes in use for (precision, eos); defaults {128, 0, 0}.  set validates every entry (GR_EINVAL). */
+int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]);
+int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]);
+
 /* Primitive -> conserved (Eq. consB_def) on the interior cells of every block, with the cell-centred
  * field taken as the mean of the two densitised faces.  W[0..4] (+ W[5] = Y_e with a table) are read;
  * U[0..4] (+ U[5] = D Y_e) written.  Unused trailing entries may be NULL. */
@@ -260,10 +282,10 @@ const char* gr_noalloc_last_error(void);
 /* Per-kernel timing of gr_stage with CUDA events on the launch stream (measurement only).
  * gr_profile_begin arms the mesh for up to max_stages subsequent gr_stage calls: each records an event
  * before and after each of its GR_NKERNELS kernels (FP32 input cast of the mixed path, cell prep, faces,
- * edges, CT, update+con2prim; the FP64 path launches no cast and its first entry is ~0).
+ * edges, CT, update, con2prim; the FP64 path launches no cast and its first entry is ~0).
  * gr_profile_end synchronises on the last event and returns, per kernel, the summed milliseconds in
  * ms[GR_NKERNELS] and the number of profiled stages in *nstages; it disarms the mesh. */
-#define GR_NKERNELS 6
+#define GR_NKERNELS 7
 int gr_profile_begin(gr_mesh* mesh, int32_t max_stages);
 int gr_profile_end(gr_mesh* mesh, double* ms, int32_t* nstages);
 

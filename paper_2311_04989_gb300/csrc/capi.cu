@@ -113,8 +113,14 @@ struct gr_mesh {
   int max_ng = 0;
   std::vector<DBlock> h_blocks;
   DBlock* d_blocks = nullptr;
-  Work* d_work[R_NREGION] = {};
+  Work* d_work[R_NREGION] = {};      // work lists of the stand-alone kernels (kTile, direction-major)
   int nwork[R_NREGION] = {};
+  // work lists of the stage kernels per CTA size and order (0 direction-major, 1 block-major)
+  Work* tw[kNumTiles][2][R_NREGION] = {};
+  int tn[kNumTiles][2][R_NREGION] = {};
+  // launch shape of each stage kernel per (precision, EOS), set by gr_autotune or gr_mesh_set_shapes
+  gr_shape shapes[2][2][SK_N];
+  int nint = 0;   // interior cells of all blocks
   Workspace ws{};
   Shadow sh{};
   double* d_diag = nullptr;
@@ -289,19 +295,30 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
     d.wvert = wvert;
     wvert += (long long)(d.N[0] + 1) * (d.N[1] + 1) * (d.N[2] + 1);
   }
-  // work lists
-  // work lists, ordered direction-major so that the CTAs resident on an SM at any time mostly run
-  // the same per-direction instantiation (the three bodies would otherwise share the I-cache)
-  std::vector<Work> wl[R_NREGION];
-  for (int kind = 0; kind < R_NREGION; ++kind) {
-    const int ndir = region_has_dir(kind) ? 3 : 1;
-    for (int dir = 0; dir < ndir; ++dir)
-      for (int b = 0; b < nblocks; ++b) {
-        const long long cnt = region_count(kind, dir, m->h_blocks[b]);
-        for (long long s0 = 0; s0 < cnt; s0 += kTile) wl[kind].push_back(Work{b, dir, (int)s0, 0});
+  // work lists for every CTA size and order.  Direction-major lists keep the CTAs resident on an SM
+  // at any time mostly in the same per-direction instantiation (the three bodies would otherwise
+  // share the I-cache); block-major lists keep a block's data together in L2.
+  std::vector<Work> wl[kNumTiles][2][R_NREGION];
+  for (int t = 0; t < kNumTiles; ++t)
+    for (int order = 0; order < 2; ++order)
+      for (int kind = 0; kind < R_NREGION; ++kind) {
+        if (order == 1 && !region_has_dir(kind)) continue;   // same list as order 0
+        const int ndir = region_has_dir(kind) ? 3 : 1;
+        const int tile = tile_size(t);
+        std::vector<Work>& L = wl[t][order][kind];
+        for (int o1 = 0; o1 < (order == 0 ? ndir : nblocks); ++o1)
+          for (int o2 = 0; o2 < (order == 0 ? nblocks : ndir); ++o2) {
+            const int dir = order == 0 ? o1 : o2, b = order == 0 ? o2 : o1;
+            const long long cnt = region_count(kind, dir, m->h_blocks[b]);
+            for (long long s0 = 0; s0 < cnt; s0 += tile) L.push_back(Work{b, dir, (int)s0, 0});
+          }
       }
-    m->nwork[kind] = (int)wl[kind].size();
-  }
+  const int t128 = 1;   // tile_size(1) == kTile
+  static_assert(tile_size(1) == kTile, "stand-alone kernels use the 128-element lists");
+  for (int kind = 0; kind < R_NREGION; ++kind) m->nwork[kind] = (int)wl[t128][0][kind].size();
+  for (int pr = 0; pr < 2; ++pr)
+    for (int eo = 0; eo < 2; ++eo)
+      for (int k = 0; k < SK_N; ++k) m->shapes[pr][eo][k] = gr_shape{kTile, 0, 0};
   auto dalloc = [&](size_t bytes, void** p) -> cudaError_t {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e == cudaSuccess) { m->allocs.push_back(*p); m->ws_bytes += (int64_t)bytes; }
@@ -311,11 +328,21 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   e = dalloc(sizeof(DBlock) * std::max(1, nblocks), (void**)&m->d_blocks);
   if (e == cudaSuccess && nblocks)
     e = cudaMemcpy(m->d_blocks, m->h_blocks.data(), sizeof(DBlock) * nblocks, cudaMemcpyHostToDevice);
-  for (int kind = 0; kind < R_NREGION && e == cudaSuccess; ++kind) {
-    e = dalloc(sizeof(Work) * std::max<size_t>(1, wl[kind].size()), (void**)&m->d_work[kind]);
-    if (e == cudaSuccess && !wl[kind].empty())
-      e = cudaMemcpy(m->d_work[kind], wl[kind].data(), sizeof(Work) * wl[kind].size(), cudaMemcpyHostToDevice);
-  }
+  for (int t = 0; t < kNumTiles; ++t)
+    for (int order = 0; order < 2; ++order)
+      for (int kind = 0; kind < R_NREGION && e == cudaSuccess; ++kind) {
+        if (order == 1 && !region_has_dir(kind)) {
+          m->tw[t][1][kind] = m->tw[t][0][kind];
+          m->tn[t][1][kind] = m->tn[t][0][kind];
+          continue;
+        }
+        const std::vector<Work>& L = wl[t][order][kind];
+        e = dalloc(sizeof(Work) * std::max<size_t>(1, L.size()), (void**)&m->tw[t][order][kind]);
+        if (e == cudaSuccess && !L.empty())
+          e = cudaMemcpy(m->tw[t][order][kind], L.data(), sizeof(Work) * L.size(), cudaMemcpyHostToDevice);
+        m->tn[t][order][kind] = (int)L.size();
+      }
+  for (int kind = 0; kind < R_NREGION; ++kind) m->d_work[kind] = m->tw[t128][0][kind];
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
     e = dalloc(sizeof(double) * wcell, &m->ws.bcc[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, &m->ws.ecc[a]);
@@ -338,6 +365,12 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(float) * ef[a], (void**)&m->sh.B[a]);
   for (int c = 0; c < 16 && e == cudaSuccess; ++c) e = dalloc(sizeof(float) * ev, (void**)&m->sh.M[c]);
   if (e == cudaSuccess) e = dalloc(sizeof(double) * 8, (void**)&m->d_diag);
+  long long nint = 0;
+  for (const DBlock& d : m->h_blocks) nint += (long long)d.n[0] * d.n[1] * d.n[2];
+  if (nint > (1LL << 31) - 1024) e = cudaErrorInvalidValue;
+  m->nint = (int)nint;
+  if (e == cudaSuccess) e = dalloc(sizeof(int2) * std::max<long long>(1, nint), (void**)&m->ws.jobs);
+  if (e == cudaSuccess) e = dalloc(sizeof(int) * 4, (void**)&m->ws.njobs);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
     std::string msg = std::string("gr_mesh_create: ") + cudaGetErrorString(e);
@@ -466,18 +499,29 @@ int gr_graph_destroy(gr_graph* graph) {
   return GR_OK;
 }
 
-static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
-                      const gr_params* params, void* stream, bool allow_profile) {
+// launches of the five stage kernels for the given shapes
+static void stage_launches(const gr_mesh* mesh, const gr_shape shp[SK_N], KLaunch kl[SK_N]) {
+  for (int k = 0; k < SK_N; ++k) {
+    const int t = shp[k].tile == 64 ? 0 : (shp[k].tile == 256 ? 2 : 1);
+    const int order = shp[k].order ? 1 : 0;
+    kl[k].work = mesh->tw[t][order][kRegionOf[k]];
+    kl[k].nwork = k == SK_C2P ? mesh->nint : mesh->tn[t][order][kRegionOf[k]];
+    kl[k].threads = tile_size(t);
+    kl[k].persistent = shp[k].persistent ? 1 : 0;
+  }
+}
+
+// validation of a stage call; fills the device views
+static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                         const gr_params* params, MetricView& mv, StateView& s) {
   if (!mesh || !state) return fail(GR_EINVAL, "gr_stage: NULL argument");
   int r = check_params(params);
   if (r) return r;
   if (!std::isfinite(dt) || dt < 0) return fail(GR_EINVAL, "gr_stage: dt must be finite and >= 0");
-  MetricView mv;
   if ((r = metric_view(metric, mv, true))) return r;
   const int need = (params->recon == GR_RECON_WENOZ ? 3 : 2) + (metric->order == 4 ? 1 : 0);
   if (mesh->nblocks > 0 && mesh->min_ng < need)
     return fail(GR_EINVAL, "gr_stage: ghost width too small for the reconstruction / interpolation stencil");
-  StateView s;
   const bool tab = params->eos == GR_EOS_TABLE;
   const int nq = tab ? 6 : 5, nwr = tab ? 6 : 5, nwo = tab ? 7 : 5;
   if (tab && params->table->device != mesh->ctx->device)
@@ -504,16 +548,101 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
     if ((const double*)s.Wo[v] == s.W[v]) return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
   s.status = state->status;
   if (!s.status) return fail(GR_EINVAL, "gr_stage: status is NULL");
+  return GR_OK;
+}
+
+static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                      const gr_params* params, void* stream, bool allow_profile) {
+  MetricView mv;
+  StateView s;
+  const int r = stage_prepare(mesh, metric, state, dt, params, mv, s);
+  if (r) return r;
   if (mesh->nblocks == 0) return GR_OK;
   DeviceGuard g(mesh->ctx->device);
-  const Work* work[R_NREGION];
-  for (int k = 0; k < R_NREGION; ++k) work[k] = mesh->d_work[k];
+  KLaunch kl[SK_N];
+  stage_launches(mesh, mesh->shapes[params->precision][params->eos], kl);
   cudaEvent_t* ev = nullptr;
   if (allow_profile && mesh->prof_used < mesh->prof_capacity)
     ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
-  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, work, mesh->nwork, mv, s, mesh->ws,
-                               mesh->sh, kparams(params, dt), (cudaStream_t)stream, ev);
+  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh,
+                               kparams(params, dt), (cudaStream_t)stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
+  return GR_OK;
+}
+
+int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]) {
+  if (!mesh || !out || (precision != GR_PREC_FP64 && precision != GR_PREC_MIXED) ||
+      (eos != GR_EOS_IDEAL && eos != GR_EOS_TABLE))
+    return fail(GR_EINVAL, "gr_mesh_get_shapes: bad argument");
+  for (int k = 0; k < SK_N; ++k) out[k] = mesh->shapes[precision][eos][k];
+  return GR_OK;
+}
+
+int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]) {
+  if (!mesh || !in || (precision != GR_PREC_FP64 && precision != GR_PREC_MIXED) ||
+      (eos != GR_EOS_IDEAL && eos != GR_EOS_TABLE))
+    return fail(GR_EINVAL, "gr_mesh_set_shapes: bad argument");
+  for (int k = 0; k < SK_N; ++k)
+    if ((in[k].tile != 64 && in[k].tile != 128 && in[k].tile != 256) || (in[k].order != 0 && in[k].order != 1) ||
+        (in[k].persistent != 0 && in[k].persistent != 1))
+      return fail(GR_EINVAL, "gr_mesh_set_shapes: tile must be 64, 128 or 256; order and persistent 0 or 1");
+  for (int k = 0; k < SK_N; ++k) mesh->shapes[precision][eos][k] = in[k];
+  return GR_OK;
+}
+
+int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
+                int32_t reps, void* stream, double best_ms[GR_NSTAGE_KERNELS]) {
+  MetricView mv;
+  StateView s;
+  int r = stage_prepare(mesh, metric, state, dt, params, mv, s);
+  if (r) return r;
+  if (reps < 1 || reps > 1000) return fail(GR_EINVAL, "gr_autotune: reps must be in [1, 1000]");
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const KParams kp = kparams(params, dt);
+  // candidates: CTA size x work-list order x persistent grid, the same for all five kernels in one
+  // run; each kernel's time is read from its own events
+  std::vector<gr_shape> cand;
+  for (int tile : {64, 128, 256})
+    for (int order = 0; order < 2; ++order)
+      for (int pers = 0; pers < 2; ++pers) cand.push_back(gr_shape{tile, order, pers});
+  std::vector<cudaEvent_t> ev((size_t)(GR_NKERNELS + 1) * reps);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  std::vector<std::vector<double>> ms(cand.size(), std::vector<double>(SK_N, 0.0));
+  for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+    gr_shape shp[SK_N];
+    for (int k = 0; k < SK_N; ++k) shp[k] = cand[c];
+    KLaunch kl[SK_N];
+    stage_launches(mesh, shp, kl);
+    e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st, nullptr);  // warm-up
+    for (int rp = 0; rp < reps && e == cudaSuccess; ++rp)
+      e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st,
+                       &ev[(size_t)(GR_NKERNELS + 1) * rp]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int rp = 0; rp < reps && e == cudaSuccess; ++rp)
+      for (int k = 0; k < SK_N && e == cudaSuccess; ++k) {
+        float t = 0.f;
+        // event slots: 0 before the cast, 1 after it, 2 + k after stage kernel k
+        e = cudaEventElapsedTime(&t, ev[(size_t)(GR_NKERNELS + 1) * rp + 1 + k], ev[(size_t)(GR_NKERNELS + 1) * rp + 2 + k]);
+        ms[c][k] += t / reps;
+      }
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_autotune");
+  gr_shape* best = mesh->shapes[params->precision][params->eos];
+  for (int k = 0; k < SK_N; ++k) {
+    const bool has_dir = region_has_dir(kRegionOf[k]);
+    int bi = -1;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      if (!has_dir && cand[c].order != 0) continue;   // the order of a direction-less list is moot
+      if (bi < 0 || ms[c][k] < ms[bi][k]) bi = (int)c;
+    }
+    best[k] = cand[bi];
+    if (best_ms) best_ms[k] = ms[bi][k];
+  }
   return GR_OK;
 }
 

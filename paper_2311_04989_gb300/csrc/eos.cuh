@@ -76,9 +76,20 @@ __device__ __forceinline__ R tab_at(const TabView<R>& t, const R* __restrict__ f
 
 // log T at which the interpolant of f (increasing in T) equals y; y beyond the values at the table's
 // T ends gives that end and sets *cl.  *k and *wT receive the T interval and fraction of the result.
+// hint >= 0: an interval to try first (the previous result of a root iteration); if it brackets y
+// (g(hint) <= y < g(hint+1)) it is the interval the search would find, since g is increasing.
 template <class R>
 __device__ __forceinline__ R tab_inverse_T(const TabView<R>& t, const R* __restrict__ f, const TabLoc<R>& L,
-                                           R y, bool* cl, int* k, R* wT) {
+                                           R y, bool* cl, int* k, R* wT, int hint = -1) {
+  if (hint >= 0 && hint < t.n[1] - 1) {
+    const R gk = tab_at(t, f, L, hint), gk1 = tab_at(t, f, L, hint + 1);
+    if (gk <= y && y < gk1) {
+      const R fr = (y - gk) / (gk1 - gk);
+      *k = hint;
+      *wT = fr;
+      return t.x0[1] + t.dx[1] * (R(hint) + fr);
+    }
+  }
   int lo = 0, hi = t.n[1] - 1;
   R glo = tab_at(t, f, L, lo);
   if (!(y > glo)) {

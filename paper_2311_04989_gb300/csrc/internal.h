@@ -8,7 +8,14 @@
 
 namespace grs {
 
-constexpr int kTile = 128;   // elements per CTA work item (threads per CTA)
+constexpr int kTile = 128;   // elements per work item (threads per CTA) of the stand-alone kernels
+// Stage kernels: work items of 64, 128 or 256 elements (one thread each), chosen per kernel
+constexpr int kMaxTile = 256;
+constexpr int kNumTiles = 3;
+constexpr int tile_size(int t) { return 64 << t; }
+enum StageKernel { SK_CELLPREP = 0, SK_FACES = 1, SK_EDGES = 2, SK_CT = 3, SK_UPDATE = 4, SK_C2P = 5, SK_N = 6 };
+// work region of each stage kernel (Region below); k_c2p works on the job list of k_update
+constexpr int kRegionOf[SK_N] = {0, 1, 2, 3, 4, 4};
 
 // Device copy of one block: geometry, caller pool offsets and workspace offsets (in elements).
 struct DBlock {
@@ -21,8 +28,8 @@ struct DBlock {
   long long wcell, wface[3], wvert;      // workspace pools
 };
 
-// One CTA's slice of work: elements [start, start + kTile) of region `kind` of block `block`
-// in direction `dir` (faces, edges) or 0.
+// One CTA's slice of work: elements [start, start + tile) of region `kind` of block `block`
+// in direction `dir` (faces, edges) or 0, tile = the CTA size it was built for.
 struct Work {
   int block;
   int dir;
@@ -77,6 +84,8 @@ struct Workspace {
   void* edge[3];       // corner electric field E_m (vertex-indexed), FP64 or FP32
   long long fstride[3];
   long long estride;
+  int* njobs;          // con2prim job list: cells (block, interior index) that need the root find
+  int2* jobs;
 };
 
 // Device view of an EOS table (Sec. 2.3) in precision R: node arrays of log p, log e, c_s^2, node
@@ -103,13 +112,22 @@ struct KParams {   // gr_params flattened for the device
   TabView<float> t32;
 };
 
+// Launch of one stage kernel: its work list (built for CTAs of `threads`), and whether the grid is
+// persistent (as many CTAs as fit on the device, striding over the list) or one CTA per work item.
+// For k_c2p, work is unused and nwork is the number of interior cells (the job list's capacity).
+struct KLaunch {
+  const Work* work;
+  int nwork;
+  int threads;
+  int persistent;
+};
+
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after
 // the cast and each kernel
-cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
-                         const int nwork[R_NREGION], const MetricView& m, const StateView& s,
-                         const Workspace& ws, const Shadow& sh, const KParams& kp, cudaStream_t st,
-                         cudaEvent_t* ev);
+cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
+                         const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
+                         cudaStream_t st, cudaEvent_t* ev);
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st);

@@ -634,7 +634,7 @@ __device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R
 // 1 + eps + p/rho.
 template <class R>
 __device__ __forceinline__ void c2p_master_tab(const TabView<R>& t, R vmax2, const C2PInv<R>& I, R mu,
-                                               C2PVal<R>& E) {
+                                               C2PVal<R>& E, int* khint) {
   E.x = rdiv(R(1), R(1) + mu * I.b2);
   E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (R(1) + E.x) * I.rb * I.rb;
   const R qbar = I.q - R(0.5) * I.b2 - R(0.5) * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
@@ -653,7 +653,8 @@ __device__ __forceinline__ void c2p_master_tab(const TabView<R>& t, R vmax2, con
   int k;
   R wT;
   const R y = E.eps > R(-1) ? rlog1p(E.eps) : R(-INFINITY);
-  E.lT = tab_inverse_T(t, t.f[1], L, y, &cl, &k, &wT);
+  E.lT = tab_inverse_T(t, t.f[1], L, y, &cl, &k, &wT, *khint);
+  *khint = k;
   if (cl) { E.eps = rexpm1(tab_T(t, t.f[1], L, k, wT)); E.eclamp = true; }
   E.p = E.rho * rexp(tab_T(t, t.f[0], L, k, wT));
   const R h = (R(1) + E.eps) + rdiv(E.p, E.rho);
@@ -720,9 +721,10 @@ __device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<d
     if (illinois<float>(fa, 0.f, top, -1.f, f1, 1e-3f, 40, &root, &hi, &it) == 0) mup = hi;
   }
   C2PVal<float> E;
+  int kh = -1;   // temperature interval of the last evaluation (table)
   auto fm = [&](float mu) {
     if constexpr (EOS == GR_EOS_IDEAL) c2p_master<float>(gam, vmax2, I, mu, E);
-    else c2p_master_tab<float>(P.t32, vmax2, I, mu, E);
+    else c2p_master_tab<float>(P.t32, vmax2, I, mu, E, &kh);
     return E.f;
   };
   const float f0 = fm(0.f);
@@ -754,6 +756,28 @@ __device__ __forceinline__ void cons_at(const C2PMet& M, const KParams& P, const
   cell_fluid<double, EOS>(Mc, P, w, Bd, f);
   cell_cons<double>(Mc, f, q);
   if (EOS) q[5] = q[0] * w[5];
+}
+
+// Atmosphere primitives (Sec. 3.5, App. A) and their conserved variables, Eq. consB_def at u~ = 0:
+// W = 1, b^0 = 0, b^2 = calB^2, so D = sqrt(gamma) rho, S_j = 0,
+// tau = sqrt(gamma) (rho eps + calB^2 / 2) = sqrt(gamma) rho eps + gamma_ij B^i B^j/(2 sqrt(gamma))
+template <int EOS>
+__device__ __forceinline__ void atm_cell(const C2PMet& M, const KParams& P, const double Bd[3], double q[6],
+                                         double w[7]) {
+  w[0] = P.rho_atm;
+  w[1] = w[2] = w[3] = 0.0;
+  w[4] = P.p_atm;
+  double Bl[3];
+  lower3(M.g, Bd, Bl);
+  const double BBd = Bd[0] * Bl[0] + Bd[1] * Bl[1] + Bd[2] * Bl[2];
+  q[0] = M.sg * P.rho_atm;
+  q[1] = q[2] = q[3] = 0.0;
+  q[4] = M.sg * P.eint_atm + (BBd == 0.0 ? 0.0 : 0.5 * BBd / M.sg);
+  if constexpr (EOS == GR_EOS_TABLE) {
+    w[5] = P.Ye_atm;
+    w[6] = P.T_atm;
+    q[5] = q[0] * P.Ye_atm;
+  }
 }
 
 // Full con2prim of one cell.  q: densitised conserved (in/out; q[5] = D Y_e with a table), Bd:
@@ -827,10 +851,11 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     const double top = EOS ? 1.0 / P.h0 : 1.0, h0sq = EOS ? P.h0 * P.h0 : 1.0;
     C2PVal<double> E;
     int nevals = 0;   // FP64 master-function evaluations (reported through *iters)
+    int kh = -1;      // temperature interval of the last evaluation (table)
     auto fm = [&](double mu) {
       ++nevals;
       if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
-      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E);
+      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E, &kh);
       return E.f;
     };
     double root = 0.0, hi;
@@ -905,7 +930,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
         rec->solved = true;
       }
       if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
-      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E);
+      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E, &kh);
       double vu[3];
       for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);
       if (E.vcap) {
@@ -945,23 +970,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     }
   }
   if (atm) {
-    // atmosphere primitives (Sec. 3.5, App. A) and their conserved variables, Eq. consB_def at u~ = 0:
-    // W = 1, b^0 = 0, b^2 = calB^2, so D = sqrt(gamma) rho, S_j = 0,
-    // tau = sqrt(gamma) (rho eps + calB^2 / 2) = sqrt(gamma) rho eps + gamma_ij B^i B^j/(2 sqrt(gamma))
-    w[0] = P.rho_atm;
-    w[1] = w[2] = w[3] = 0.0;
-    w[4] = P.p_atm;
-    double Bl[3];
-    lower3(M.g, Bd, Bl);
-    const double BBd = Bd[0] * Bl[0] + Bd[1] * Bl[1] + Bd[2] * Bl[2];
-    q[0] = M.sg * P.rho_atm;
-    q[1] = q[2] = q[3] = 0.0;
-    q[4] = M.sg * P.eint_atm + (BBd == 0.0 ? 0.0 : 0.5 * BBd / M.sg);
-    if constexpr (EOS == GR_EOS_TABLE) {
-      w[5] = P.Ye_atm;
-      w[6] = P.T_atm;
-      q[5] = q[0] * P.Ye_atm;
-    }
+    atm_cell<EOS>(M, P, Bd, q, w);
   } else if (reprim) {
     cons_at<EOS>(M, P, w, Bd, q);
   }

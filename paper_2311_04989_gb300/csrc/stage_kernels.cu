@@ -92,11 +92,8 @@ __global__ void __launch_bounds__(256) k_cast(const __grid_constant__ CastList L
 // k_cellprep<R>
 // ------------------------------------------------------------------------------------------------
 template <class R>
-__global__ void __launch_bounds__(kTile) k_cellprep(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                    const __grid_constant__ InView<R> in,
-                                                    const __grid_constant__ Workspace ws) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
+__device__ __forceinline__ void cellprep_body(const Work& w, const DBlock& b, const InView<R>& in,
+                                              const Workspace& ws) {
   int p[3];
   if (!decode<R_CELLS_ALL, 0>(w, b, p)) return;
   const int i = p[0], j = p[1], k = p[2];
@@ -134,6 +131,18 @@ __global__ void __launch_bounds__(kTile) k_cellprep(const DBlock* __restrict__ b
   for (int mm = 0; mm < 3; ++mm) {
     const int a = (mm + 1) % 3, bb = (mm + 2) % 3;
     reinterpret_cast<R*>(ws.ecc[mm])[wc] = val[0] * (vt[bb] * Bd[a] - vt[a] * Bd[bb]);
+  }
+}
+
+// Every stage kernel strides over its work list (one work item per CTA and pass): launched with one CTA
+// per item, or persistent with as many CTAs as fit on the GPU.  The CTA size equals the work-item size.
+template <class R>
+__global__ void __launch_bounds__(kMaxTile) k_cellprep(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                       int nwork, const __grid_constant__ InView<R> in,
+                                                       const __grid_constant__ Workspace ws) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    cellprep_body<R>(w, blocks[w.block], in, ws);
   }
 }
 
@@ -210,15 +219,17 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
 }
 
 template <class R, int EOS>
-__global__ void __launch_bounds__(kTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                 const __grid_constant__ InView<R> in,
-                                                 const __grid_constant__ Workspace ws,
-                                                 const __grid_constant__ KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  if (w.dir == 0) face_body<R, EOS, 0>(w, b, in, ws, kp);
-  else if (w.dir == 1) face_body<R, EOS, 1>(w, b, in, ws, kp);
-  else face_body<R, EOS, 2>(w, b, in, ws, kp);
+__global__ void __launch_bounds__(kMaxTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    int nwork, const __grid_constant__ InView<R> in,
+                                                    const __grid_constant__ Workspace ws,
+                                                    const __grid_constant__ KParams kp) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const DBlock b = blocks[w.block];
+    if (w.dir == 0) face_body<R, EOS, 0>(w, b, in, ws, kp);
+    else if (w.dir == 1) face_body<R, EOS, 1>(w, b, in, ws, kp);
+    else face_body<R, EOS, 2>(w, b, in, ws, kp);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -260,14 +271,16 @@ __device__ __forceinline__ void edge_body(const Work& w, const DBlock& b, const 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kTile) k_edges(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                 const __grid_constant__ Workspace ws,
-                                                 const __grid_constant__ KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  if (w.dir == 0) edge_body<R, 0>(w, b, ws, kp);
-  else if (w.dir == 1) edge_body<R, 1>(w, b, ws, kp);
-  else edge_body<R, 2>(w, b, ws, kp);
+__global__ void __launch_bounds__(kMaxTile) k_edges(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    int nwork, const __grid_constant__ Workspace ws,
+                                                    const __grid_constant__ KParams kp) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const DBlock b = blocks[w.block];
+    if (w.dir == 0) edge_body<R, 0>(w, b, ws, kp);
+    else if (w.dir == 1) edge_body<R, 1>(w, b, ws, kp);
+    else edge_body<R, 2>(w, b, ws, kp);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -293,15 +306,17 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
 }
 
 template <class R>
-__global__ void __launch_bounds__(kTile) k_ct(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                              const __grid_constant__ StateView s,
-                                              const __grid_constant__ Workspace ws,
-                                              const __grid_constant__ KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  if (w.dir == 0) ct_body<R, 0>(w, b, s, ws, kp);
-  else if (w.dir == 1) ct_body<R, 1>(w, b, s, ws, kp);
-  else ct_body<R, 2>(w, b, s, ws, kp);
+__global__ void __launch_bounds__(kMaxTile) k_ct(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                 int nwork, const __grid_constant__ StateView s,
+                                                 const __grid_constant__ Workspace ws,
+                                                 const __grid_constant__ KParams kp) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const DBlock b = blocks[w.block];
+    if (w.dir == 0) ct_body<R, 0>(w, b, s, ws, kp);
+    else if (w.dir == 1) ct_body<R, 1>(w, b, s, ws, kp);
+    else ct_body<R, 2>(w, b, s, ws, kp);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -325,17 +340,25 @@ __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<doubl
   c2pmet_from(val + 4, M);
 }
 
+template <int EOS>
+__device__ __forceinline__ void write_cell(const StateView& s, long long c, const double q[6], const double w[7],
+                                           int st) {
+  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
+#pragma unroll
+  for (int v = 0; v < NW; ++v) s.Wo[v][c] = w[v];
+  s.status[c] = (uint8_t)st;
+}
+
+// k_update, per interior cell: flux divergence + sources with FP64 accumulation.  Atmosphere cells are
+// reset here (closed form); every other cell leaves its updated conserved variables in Uo and is
+// returned as a con2prim job (the root find runs in k_c2p on the compacted job list).
 template <class R, int EOS>
-__global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                  const __grid_constant__ InView<R> in,
-                                                  const __grid_constant__ InView<double> in64,
-                                                  const __grid_constant__ StateView s,
-                                                  const __grid_constant__ Workspace ws,
-                                                  const __grid_constant__ KParams kp) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
+__device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, const InView<R>& in,
+                                            const StateView& s, const Workspace& ws, const KParams& kp) {
   int p[3];
-  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
+  if (!decode<R_INTERIOR, 0>(w, b, p)) return false;
   const int i = p[0], j = p[1], k = p[2];
   const bool kzero = in.k_zero != 0;
   R val[16], dm[3][10];
@@ -384,13 +407,10 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
     if (kp.rk_g0 != 0.0) u += kp.rk_g0 * s.U0[v][c];
     return u;
   };
-  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
-  double q[6];
+  constexpr int NQ = EOS ? 6 : 5;
+  double q[6], Bn[3], wn[7];
   q[0] = accumulate(0);
-  double Bn[3];
   cell_field(b, s.Bo, i, j, k, Bn);
-  double wn[7];
-  int st;
   if (sizeof(R) == sizeof(float)) {
     // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
     // sqrt(gamma) (same 1e-6 band as the FP64 test) and reset such cells without forming S', tau'
@@ -422,31 +442,82 @@ __global__ void __launch_bounds__(kTile) k_update(const DBlock* __restrict__ blo
         wn[5] = kp.Ye_atm;
         wn[6] = kp.T_atm;
       }
-      st = finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED;
-    } else {
-#pragma unroll
-      for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
-      C2PMet Mc;
-      cell_gamma64(b, in64, i, j, k, Mc);
-      int iters;
-      st = con2prim_cell<EOS>(Mc, kp, q, Bn, wn, &iters);
+      write_cell<EOS>(s, c, q, wn, finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED);
+      return false;
     }
+#pragma unroll
+    for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
   } else {
 #pragma unroll
     for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
+    // FP64 path: the atmosphere test of con2prim (the same operations, on the same FP64 metric that
+    // k_c2p interpolates), decided here for finite cells
     C2PMet Mc;
 #pragma unroll
     for (int t = 0; t < 6; ++t) Mc.g[t] = to64(M.g[t]);
     Mc.sg = to64(M.sg);
     Mc.det = to64(M.det);
-    int iters;
-    st = con2prim_cell<EOS>(Mc, kp, q, Bn, wn, &iters);
+    bool finite = isfinite(Bn[0]) && isfinite(Bn[1]) && isfinite(Bn[2]);
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) finite = finite && isfinite(q[v]);
+    const double rho_thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
+    if (finite && q[0] < rho_thr * Mc.sg) {
+      atm_cell<EOS>(Mc, kp, Bn, q, wn);
+      write_cell<EOS>(s, c, q, wn, GR_ST_ATM_THRESHOLD);
+      return false;
+    }
   }
 #pragma unroll
   for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
+  return true;
+}
+
+template <class R, int EOS>
+__global__ void __launch_bounds__(kMaxTile) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                     int nwork, const __grid_constant__ InView<R> in,
+                                                     const __grid_constant__ StateView s,
+                                                     const __grid_constant__ Workspace ws,
+                                                     const __grid_constant__ KParams kp) {
+  const unsigned lane = threadIdx.x & 31u;
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const bool queued = update_cell<R, EOS>(w, blocks[w.block], in, s, ws, kp);
+    // warp-aggregated append to the job list: one atomic per warp, slots by rank among queued lanes
+    const unsigned mask = __ballot_sync(0xffffffffu, queued);
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(ws.njobs, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (queued) ws.jobs[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(w.block, w.start + (int)threadIdx.x);
+  }
+}
+
+// k_c2p: FP64 con2prim (Sec. 3.5, App. A) of the queued cells, packed densely into warps whatever the
+// pattern of atmosphere and matter cells: thread t of the grid takes jobs t, t + grid size, ...
+template <int EOS>
+__global__ void __launch_bounds__(kMaxTile) k_c2p(const DBlock* __restrict__ blocks,
+                                                  const __grid_constant__ InView<double> in64,
+                                                  const __grid_constant__ StateView s,
+                                                  const __grid_constant__ Workspace ws,
+                                                  const __grid_constant__ KParams kp) {
+  const int n = *ws.njobs;
+  for (int jdx = blockIdx.x * blockDim.x + threadIdx.x; jdx < n; jdx += gridDim.x * blockDim.x) {
+    const int2 job = ws.jobs[jdx];
+    const DBlock b = blocks[job.x];
+    const int e = job.y;
+    const int i = e % b.n[0], j = (e / b.n[0]) % b.n[1], k = e / (b.n[0] * b.n[1]);
+    const long long c = b.cell + cix(b, i, j, k);
+    constexpr int NQ = EOS ? 6 : 5;
+    double q[6], Bn[3], wn[7];
+    q[5] = 0.0;
 #pragma unroll
-  for (int v = 0; v < NW; ++v) s.Wo[v][c] = wn[v];
-  s.status[c] = (uint8_t)st;
+    for (int v = 0; v < NQ; ++v) q[v] = s.Uo[v][c];
+    cell_field(b, s.Bo, i, j, k, Bn);
+    C2PMet M;
+    cell_gamma64(b, in64, i, j, k, M);
+    int iters;
+    const int st = con2prim_cell<EOS>(M, kp, q, Bn, wn, &iters);
+    write_cell<EOS>(s, c, q, wn, st);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -633,29 +704,57 @@ static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Sh
   return cudaGetLastError();
 }
 
+// Grid of a stage-kernel launch: one CTA per work item, or (persistent) the number of CTAs that are
+// resident at once on the device, capped by the number of work items.
+template <class K>
+static int stage_grid(K kernel, const KLaunch& l, size_t smem) {
+  if (!l.persistent) return l.nwork;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, l.threads, smem);
+  const long long g = (long long)nsm * (occ > 0 ? occ : 1);
+  return (int)(g < l.nwork ? g : l.nwork);
+}
+
 template <class R, int EOS>
-static cudaError_t stage_impl(const DBlock* blocks, const Work* const work[R_NREGION],
-                              const int nwork[R_NREGION], const InView<R>& in, const InView<double>& in64,
-                              const StateView& s, const Workspace& ws, const KParams& kp, cudaStream_t st,
-                              cudaEvent_t* ev) {
-  if (nwork[R_CELLS_ALL]) k_cellprep<R><<<nwork[R_CELLS_ALL], kTile, 0, st>>>(blocks, work[R_CELLS_ALL], in, ws);
+static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], const InView<R>& in,
+                              const InView<double>& in64, const StateView& s, const Workspace& ws, const KParams& kp,
+                              cudaStream_t st, cudaEvent_t* ev) {
+  const KLaunch& a = kl[SK_CELLPREP];
+  if (a.nwork) k_cellprep<R><<<stage_grid(k_cellprep<R>, a, 0), a.threads, 0, st>>>(blocks, a.work, a.nwork, in, ws);
   if (ev) cudaEventRecord(ev[2], st);
-  if (nwork[R_FACES]) k_faces<R, EOS><<<nwork[R_FACES], kTile, 0, st>>>(blocks, work[R_FACES], in, ws, kp);
+  const KLaunch& f = kl[SK_FACES];
+  if (f.nwork)
+    k_faces<R, EOS><<<stage_grid(k_faces<R, EOS>, f, 0), f.threads, 0, st>>>(blocks, f.work, f.nwork, in, ws, kp);
   if (ev) cudaEventRecord(ev[3], st);
-  if (nwork[R_EDGES]) k_edges<R><<<nwork[R_EDGES], kTile, 0, st>>>(blocks, work[R_EDGES], ws, kp);
+  const KLaunch& e = kl[SK_EDGES];
+  if (e.nwork) k_edges<R><<<stage_grid(k_edges<R>, e, 0), e.threads, 0, st>>>(blocks, e.work, e.nwork, ws, kp);
   if (ev) cudaEventRecord(ev[4], st);
-  if (nwork[R_CTFACES]) k_ct<R><<<nwork[R_CTFACES], kTile, 0, st>>>(blocks, work[R_CTFACES], s, ws, kp);
+  const KLaunch& c = kl[SK_CT];
+  if (c.nwork) k_ct<R><<<stage_grid(k_ct<R>, c, 0), c.threads, 0, st>>>(blocks, c.work, c.nwork, s, ws, kp);
   if (ev) cudaEventRecord(ev[5], st);
-  if (nwork[R_INTERIOR])
-    k_update<R, EOS><<<nwork[R_INTERIOR], kTile, 0, st>>>(blocks, work[R_INTERIOR], in, in64, s, ws, kp);
+  const KLaunch& u = kl[SK_UPDATE];
+  cudaError_t e0 = cudaMemsetAsync(ws.njobs, 0, sizeof(int), st);
+  if (e0 != cudaSuccess) return e0;
+  if (u.nwork)
+    k_update<R, EOS><<<stage_grid(k_update<R, EOS>, u, 0), u.threads, 0, st>>>(blocks, u.work, u.nwork, in, s, ws, kp);
   if (ev) cudaEventRecord(ev[6], st);
+  // the job count is known only on the device: one CTA per possible job (the rest exit at once), or
+  // a persistent grid that strides over the list
+  const KLaunch& q = kl[SK_C2P];
+  if (q.nwork) {
+    KLaunch qq = q;
+    qq.nwork = (q.nwork + q.threads - 1) / q.threads;   // q.nwork = the number of interior cells
+    k_c2p<EOS><<<stage_grid(k_c2p<EOS>, qq, 0), q.threads, 0, st>>>(blocks, in64, s, ws, kp);
+  }
+  if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const work[R_NREGION],
-                         const int nwork[R_NREGION], const MetricView& m, const StateView& s,
-                         const Workspace& ws, const Shadow& sh, const KParams& kp, cudaStream_t st,
-                         cudaEvent_t* ev) {
+cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
+                         const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
+                         cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   const InView<double> in64 = view64(m, &s);
   const bool tab = kp.eos == GR_EOS_TABLE;
@@ -664,12 +763,12 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const Work* const 
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     const InView<float> in32 = view32(m, sh);
-    return tab ? stage_impl<float, GR_EOS_TABLE>(blocks, work, nwork, in32, in64, s, ws, kp, st, ev)
-               : stage_impl<float, GR_EOS_IDEAL>(blocks, work, nwork, in32, in64, s, ws, kp, st, ev);
+    return tab ? stage_impl<float, GR_EOS_TABLE>(blocks, kl, in32, in64, s, ws, kp, st, ev)
+               : stage_impl<float, GR_EOS_IDEAL>(blocks, kl, in32, in64, s, ws, kp, st, ev);
   }
   if (ev) cudaEventRecord(ev[1], st);
-  return tab ? stage_impl<double, GR_EOS_TABLE>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev)
-             : stage_impl<double, GR_EOS_IDEAL>(blocks, work, nwork, in64, in64, s, ws, kp, st, ev);
+  return tab ? stage_impl<double, GR_EOS_TABLE>(blocks, kl, in64, in64, s, ws, kp, st, ev)
+             : stage_impl<double, GR_EOS_IDEAL>(blocks, kl, in64, in64, s, ws, kp, st, ev);
 }
 
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,

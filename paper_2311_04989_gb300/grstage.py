@@ -33,13 +33,15 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_stage", "gr_prim2con", "gr_con2prim", "gr_diag", "gr_profile_begin", "gr_profile_end",
            "gr_diag_noalloc", "gr_noalloc_last_error", "gr_mlp_nparam", "gr_mlp_last_error", "gr_c2p_samples",
            "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
-           "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0"]
+           "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
+           "gr_mesh_get_shapes", "gr_mesh_set_shapes"]
 GR_ABI_VERSION = 2
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
 MLP_MEAN, MLP_ISTD, MLP_TMEAN, MLP_TSTD, MLP_STEP = 0, 6, 12, 13, 14
-GR_NKERNELS = 6
-KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update"]
+GR_NKERNELS = 7
+GR_NSTAGE_KERNELS = 6
+KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update", "k_c2p"]
 
 
 class GrstageError(RuntimeError):
@@ -59,6 +61,10 @@ class gr_state(C.Structure):
     _fields_ = [("U", C.c_void_p * 6), ("U0", C.c_void_p * 6), ("B", C.c_void_p * 3), ("B0", C.c_void_p * 3),
                 ("W", C.c_void_p * 7), ("Uo", C.c_void_p * 6), ("Bo", C.c_void_p * 3), ("Wo", C.c_void_p * 7),
                 ("status", C.c_void_p)]
+
+
+class gr_shape(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("order", C.c_int32), ("persistent", C.c_int32)]
 
 
 class gr_eos_table(C.Structure):
@@ -103,6 +109,10 @@ def load(path: str = LIB_PATH):
                               C.POINTER(gr_params), vp]
     L.gr_con2prim.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 6, C.c_void_p * 3, C.c_void_p * 7, vp, vp,
                               C.POINTER(gr_params), vp]
+    L.gr_autotune.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params), i32,
+                              vp, C.POINTER(C.c_double)]
+    L.gr_mesh_get_shapes.argtypes = [vp, i32, i32, C.POINTER(gr_shape)]
+    L.gr_mesh_set_shapes.argtypes = [vp, i32, i32, C.POINTER(gr_shape)]
     L.gr_eos_create.argtypes = [vp, C.POINTER(gr_eos_table), C.POINTER(vp)]
     L.gr_eos_destroy.argtypes = [vp]
     L.gr_eos_bytes.argtypes = [vp]
@@ -256,6 +266,26 @@ def gr_graph_capture(mesh, metric: gr_metric, state: gr_state, dt: float, params
     _check(load().gr_graph_capture(mesh, C.byref(metric), C.byref(state), float(dt), C.byref(params), C.byref(h)),
            "gr_graph_capture")
     return h
+
+
+def gr_autotune(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_params, reps: int = 3, stream=None):
+    """Pick the fastest launch shape of each stage kernel (see include/grstage.h); returns the chosen
+    shapes as (tile, order, persistent) tuples and the mean ms of each kernel with its shape."""
+    ms = (C.c_double * GR_NSTAGE_KERNELS)()
+    _check(load().gr_autotune(mesh, C.byref(metric), C.byref(state), float(dt), C.byref(params), int(reps),
+                              _stream(stream), ms), "gr_autotune")
+    return gr_mesh_get_shapes(mesh, params.precision, params.eos), list(ms)
+
+
+def gr_mesh_get_shapes(mesh, precision, eos=GR_EOS_IDEAL):
+    arr = (gr_shape * GR_NSTAGE_KERNELS)()
+    _check(load().gr_mesh_get_shapes(mesh, int(precision), int(eos), arr), "gr_mesh_get_shapes")
+    return [(a.tile, a.order, a.persistent) for a in arr]
+
+
+def gr_mesh_set_shapes(mesh, precision, eos, shapes):
+    arr = (gr_shape * GR_NSTAGE_KERNELS)(*[gr_shape(*t) for t in shapes])
+    _check(load().gr_mesh_set_shapes(mesh, int(precision), int(eos), arr), "gr_mesh_set_shapes")
 
 
 def gr_graph_launch(graph, stream=None):

@@ -108,7 +108,7 @@ class Pools:
 
 
 def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None, B0=None, order=None,
-              k_zero=True, return_pools=False, c2p_guess=G.GR_GUESS_NONE):
+              k_zero=True, return_pools=False, c2p_guess=G.GR_GUESS_NONE, shapes=None, autotune=False):
     """Run gr_stage on a batch; returns a list of (Uo, Bo, Wo, status) per block (numpy)."""
     import torch
     order = order or P.interp_order
@@ -128,7 +128,12 @@ def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None
     try:
         metric = G.metric_struct(Md, order=order, k_zero=k_zero)
         state = G.state_struct(Ud, U0d, Bd, B0d, Wd, Uo, Bo, Wo, st)
-        G.gr_stage(mesh, metric, state, dt, gr_params_from(P, precision, c2p_guess), torch.cuda.current_stream())
+        gp = gr_params_from(P, precision, c2p_guess)
+        if shapes is not None:
+            G.gr_mesh_set_shapes(mesh, precision, gp.eos, shapes)
+        if autotune:
+            G.gr_autotune(mesh, metric, state, dt, gp, 1, torch.cuda.current_stream())
+        G.gr_stage(mesh, metric, state, dt, gp, torch.cuda.current_stream())
         torch.cuda.synchronize()
     finally:
         G.gr_mesh_destroy(mesh)

@@ -55,7 +55,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     import ctypes as C
     import subprocess
     structs = {"gr_block": G.gr_block, "gr_metric": G.gr_metric, "gr_state": G.gr_state,
-               "gr_params": G.gr_params, "gr_eos_table": G.gr_eos_table}
+               "gr_params": G.gr_params, "gr_eos_table": G.gr_eos_table, "gr_shape": G.gr_shape}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "grstage.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -75,6 +75,6 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
 
 def test_header_constants_match_the_binding():
     txt = open(os.path.join(ROOT, "include", "grstage.h")).read()
-    for name in ("GR_ABI_VERSION", "GR_MLP_NPARAM", "GR_MLP_NIN", "GR_NKERNELS"):
+    for name in ("GR_ABI_VERSION", "GR_MLP_NPARAM", "GR_MLP_NIN", "GR_NKERNELS", "GR_NSTAGE_KERNELS"):
         m = re.search(rf"#define {name} (\d+)", txt)
         assert m and int(m.group(1)) == getattr(G, name), name

@@ -248,3 +248,55 @@ def test_diag_mass_and_divB():
     Mb = np.sum(H.interior(U[0], n, g)) * np.prod(bi.dx)
     assert abs(out[0] - Mb) < 1e-12 * Mb
     assert out[1] < 1e-14 and out[2] < 1e-14
+
+
+@pytest.mark.parametrize("precision", [G.GR_PREC_FP64, G.GR_PREC_MIXED])
+def test_every_launch_shape_gives_bitwise_the_same_stage(precision):
+    """CTA size, work-list order and persistent grids only change who computes what: every shape, and
+    the autotuner's choice, give bitwise the same outputs (uneven batch with star matter and atmosphere)."""
+    blocks = [I.random_block(n=s, g=3, seed=90 + k, rho_range=(1e-14, 1e-3)) for k, s in
+              enumerate([(16, 16, 16), (24, 16, 8), (8, 8, 8), (5, 7, 9)])]
+    P = O.Params(gamma_ad=2.0, rho_atm=1e-12, tol=1e-10)
+    dt = 0.1 * min(blocks[0].dx)
+    guess = G.GR_GUESS_FP32 if precision == G.GR_PREC_MIXED else G.GR_GUESS_NONE
+    ref = GH.gpu_stage(blocks, P, dt, precision=precision, c2p_guess=guess)
+    assert any(np.any(r["status"] == 1) for r in ref) and any(np.any(r["status"] == 0) for r in ref)
+    variants = [[(64, 0, 0)] * 6, [(256, 1, 1)] * 6, [(128, 1, 0)] * 6,
+                [(64, 1, 1), (256, 0, 0), (128, 1, 1), (64, 0, 1), (256, 1, 0), (64, 0, 1)]]
+    for shp in variants:
+        out = GH.gpu_stage(blocks, P, dt, precision=precision, c2p_guess=guess, shapes=shp)
+        for a, b in zip(out, ref):
+            for key in ("U", "W", "status"):
+                assert np.array_equal(a[key], b[key]), (shp, key)
+            for d in range(3):
+                assert np.array_equal(a["B"][d], b["B"][d]), (shp, d)
+    out = GH.gpu_stage(blocks, P, dt, precision=precision, c2p_guess=guess, autotune=True)
+    for a, b in zip(out, ref):
+        assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["W"], b["W"])
+
+
+def test_autotune_and_shape_arguments():
+    import torch
+    blocks = [I.random_block(n=(8, 8, 8), g=3, seed=95)]
+    pools = GH.Pools(blocks)
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    try:
+        assert G.gr_mesh_get_shapes(mesh, G.GR_PREC_MIXED) == [(128, 0, 0)] * 6
+        with pytest.raises(G.GrstageError):
+            G.gr_mesh_set_shapes(mesh, G.GR_PREC_MIXED, 0, [(96, 0, 0)] * 6)
+        with pytest.raises(G.GrstageError):
+            G.gr_mesh_set_shapes(mesh, 7, 0, [(64, 0, 0)] * 6)
+        P = O.Params()
+        U = H.cons_from_prims(blocks[0], P)
+        Ud, Wd = pools.cells([U], 5), pools.cells([blocks[0].W], 5)
+        Bd, Md = pools.faces([blocks[0].B]), pools.verts([blocks[0].metric])
+        Uo, Wo, Bo = Ud.clone(), Wd.clone(), [b.clone() for b in Bd]
+        st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+        state = G.state_struct(Ud, Ud, Bd, Bd, Wd, Uo, Bo, Wo, st)
+        gp = GH.gr_params_from(P, G.GR_PREC_MIXED)
+        shapes, ms = G.gr_autotune(mesh, G.metric_struct(Md), state, 0.01, gp, 2)
+        assert len(shapes) == 6 and all(t in (64, 128, 256) and o in (0, 1) and p in (0, 1) for t, o, p in shapes)
+        assert all(m >= 0 for m in ms)
+        assert G.gr_mesh_get_shapes(mesh, G.GR_PREC_FP64) == [(128, 0, 0)] * 6   # other precision untouched
+    finally:
+        G.gr_mesh_destroy(mesh)
