@@ -123,24 +123,25 @@ __device__ __forceinline__ long long vix(const DBlock& b, int i, int j, int k) {
 // Metric interpolation from vertices (Sec. 3.2): tensor-product Lagrange, order 2 or 4, at the
 // centre of a d-face (face plane = vertex plane p[d]) and at cell centres (with derivatives).
 // ------------------------------------------------------------------------------------------------
+// vertex index within a block (32-bit: a block has fewer than 2^31 vertices)
+__device__ __forceinline__ int vix32(const DBlock& b, int i, int j, int k) {
+  return ((k + b.g) * (b.N[1] + 1) + (j + b.g)) * (b.N[0] + 1) + (i + b.g);
+}
+
 template <class R>
 __device__ __forceinline__ void face_metric(const DBlock& b, const InView<R>& m, int order, int d,
                                             const int p[3], R out[10]) {
   const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const long long base = b.vert;
   if (order == 2) {
-    int q[3] = {p[0], p[1], p[2]};
-    const long long v00 = base + vix(b, q[0], q[1], q[2]);
-    q[t1] += 1;
-    const long long v10 = base + vix(b, q[0], q[1], q[2]);
-    q[t2] += 1;
-    const long long v11 = base + vix(b, q[0], q[1], q[2]);
-    q[t1] -= 1;
-    const long long v01 = base + vix(b, q[0], q[1], q[2]);
+    // the four vertices of the face: offsets within the block, one pointer per component
+    const int v00 = vix32(b, p[0], p[1], p[2]);
+    const int s1 = t1 == 0 ? 1 : (t1 == 1 ? b.N[0] + 1 : (b.N[0] + 1) * (b.N[1] + 1));
+    const int s2 = t2 == 0 ? 1 : (t2 == 1 ? b.N[0] + 1 : (b.N[0] + 1) * (b.N[1] + 1));
 #pragma unroll
     for (int c = 0; c < 10; ++c) {
-      const R* a = m.M[c];
-      out[c] = R(0.25) * (a[v00] + a[v10] + a[v01] + a[v11]);
+      const R* a = m.M[c] + base + v00;
+      out[c] = R(0.25) * ((a[0] + a[s1]) + (a[s2] + a[s1 + s2]));
     }
   } else {
     const R w[4] = {R(-1.0 / 16), R(9.0 / 16), R(9.0 / 16), R(-1.0 / 16)};
@@ -289,12 +290,15 @@ __device__ __forceinline__ void pow2_pair(float m, float* sc, float* isc) {
   *isc = __uint_as_float((unsigned)(127 + e) << 23);                // 2^e
 }
 
-template <class R>
+// SCALE (FP32 only): scale the stencil by a power of two first.  Needed for variables whose values can
+// be so small that their squared differences underflow (density and pressure near the atmosphere);
+// velocities, the cell field and Y_e are O(1e-10) or larger where they matter and skip it.
+template <class R, bool SCALE = true>
 __device__ __forceinline__ void recon(int method, const R s[6], R eps, R* L, R* Rr);
 
 template <>
-__device__ __forceinline__ void recon<double>(int method, const double s[6], double eps, double* L,
-                                              double* Rr) {
+__device__ __forceinline__ void recon<double, true>(int method, const double s[6], double eps, double* L,
+                                                    double* Rr) {
   if (method == GR_RECON_PLM) {
     *L = s[2] + 0.5 * vl_slope(s[1], s[2], s[3]);
     *Rr = s[3] - 0.5 * vl_slope(s[2], s[3], s[4]);
@@ -305,7 +309,24 @@ __device__ __forceinline__ void recon<double>(int method, const double s[6], dou
 }
 
 template <>
-__device__ __forceinline__ void recon<float>(int method, const float s[6], float eps, float* L, float* Rr) {
+__device__ __forceinline__ void recon<double, false>(int method, const double s[6], double eps, double* L,
+                                                     double* Rr) {
+  recon<double, true>(method, s, eps, L, Rr);
+}
+
+template <>
+__device__ __forceinline__ void recon<float, false>(int method, const float s[6], float eps, float* L, float* Rr) {
+  if (method == GR_RECON_PLM) {
+    *L = s[2] + 0.5f * vl_slope(s[1], s[2], s[3]);
+    *Rr = s[3] - 0.5f * vl_slope(s[2], s[3], s[4]);
+  } else {
+    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
+    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+  }
+}
+
+template <>
+__device__ __forceinline__ void recon<float, true>(int method, const float s[6], float eps, float* L, float* Rr) {
   if (method == GR_RECON_PLM) {
     *L = s[2] + 0.5f * vl_slope(s[1], s[2], s[3]);
     *Rr = s[3] - 0.5f * vl_slope(s[2], s[3], s[4]);

@@ -156,15 +156,18 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   if (!decode<R_FACES, D>(w, b, p)) return;
   constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   constexpr int NV = EOS ? 8 : 7;   // rho, u~^i, p, calB^{t1}, calB^{t2}[, Y_e]
-  // stencil cells p[D]-3 .. p[D]+2 along D
-  const long long stride = cell_stride(b, D);
+  // stencil cells p[D]-3 .. p[D]+2 along D; 32-bit offsets within the block, one base pointer per pool
+  const int stride = D == 0 ? 1 : (D == 1 ? b.N[0] : b.N[0] * b.N[1]);
   int q[3] = {p[0], p[1], p[2]};
   q[D] -= 3;
-  const long long c0 = cix(b, q[0], q[1], q[2]);
+  const int c0 = ((q[2] + b.g) * b.N[1] + (q[1] + b.g)) * b.N[0] + (q[0] + b.g);
   R st[NV][6];
   const bool wide = (b.g >= 3 || kp.recon == GR_RECON_WENOZ);
-  const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]);
-  const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]);
+  const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]) + b.wcell;
+  const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]) + b.wcell;
+  const R* wp[6];
+#pragma unroll
+  for (int v = 0; v < 6; ++v) wp[v] = (v < 5 || EOS) ? in.W[v] + b.cell : nullptr;
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     if (!wide && (t == 0 || t == 5)) {
@@ -172,17 +175,22 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
       for (int v = 0; v < NV; ++v) st[v][t] = R(0);
       continue;
     }
-    const long long c = c0 + t * stride;
+    const int c = c0 + t * stride;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) st[v][t] = in.W[v][b.cell + c];
-    st[5][t] = bc1[b.wcell + c];
-    st[6][t] = bc2[b.wcell + c];
-    if constexpr (EOS == GR_EOS_TABLE) st[7][t] = in.W[5][b.cell + c];
+    for (int v = 0; v < 5; ++v) st[v][t] = wp[v][c];
+    st[5][t] = bc1[c];
+    st[6][t] = bc2[c];
+    if constexpr (EOS == GR_EOS_TABLE) st[7][t] = wp[5][c];
   }
   const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
   R L[NV], Rr[NV];
+  // density and pressure with power-of-two scaling in FP32 (they reach the atmosphere values);
+  // velocities, the transverse field and Y_e without
+  recon<R, true>(kp.recon, st[0], eps, &L[0], &Rr[0]);
+  recon<R, true>(kp.recon, st[4], eps, &L[4], &Rr[4]);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) recon<R>(kp.recon, st[v], eps, &L[v], &Rr[v]);
+  for (int v = 1; v < NV; ++v)
+    if (v != 4) recon<R, false>(kp.recon, st[v], eps, &L[v], &Rr[v]);
   // a non-physical reconstructed state (rho <= 0 or p <= 0) drops the face to first order
   if (!(L[0] > R(0)) || !(Rr[0] > R(0)) || !(L[4] > R(0)) || !(Rr[4] > R(0))) {
 #pragma unroll
