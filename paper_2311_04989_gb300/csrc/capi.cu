@@ -548,13 +548,14 @@ static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state*
     if ((const double*)s.Wo[v] == s.W[v]) return fail(GR_EINVAL, "gr_stage: outputs must not alias inputs");
   s.status = state->status;
   if (!s.status) return fail(GR_EINVAL, "gr_stage: status is NULL");
+  s.evals = nullptr;
   return GR_OK;
 }
 
 static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                       const gr_params* params, void* stream, bool allow_profile) {
   MetricView mv;
-  StateView s;
+  StateView s{};
   const int r = stage_prepare(mesh, metric, state, dt, params, mv, s);
   if (r) return r;
   if (mesh->nblocks == 0) return GR_OK;
@@ -593,7 +594,7 @@ int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_s
 int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
                 int32_t reps, void* stream, double best_ms[GR_NSTAGE_KERNELS]) {
   MetricView mv;
-  StateView s;
+  StateView s{};
   int r = stage_prepare(mesh, metric, state, dt, params, mv, s);
   if (r) return r;
   if (reps < 1 || reps > 1000) return fail(GR_EINVAL, "gr_autotune: reps must be in [1, 1000]");
@@ -685,8 +686,8 @@ int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], cons
     if (!B[d]) return fail(GR_EINVAL, "gr_con2prim: NULL face array");
   if (mesh->nblocks == 0) return GR_OK;
   DeviceGuard g(mesh->ctx->device);
-  cudaError_t e = launch_con2prim(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U,
-                                  B, W, status, evals, kparams(params, 0.0), (cudaStream_t)stream);
+  cudaError_t e = launch_con2prim(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mesh->nint,
+                                  mv, U, B, W, status, evals, mesh->ws, kparams(params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_con2prim launch");
   return GR_OK;
 }

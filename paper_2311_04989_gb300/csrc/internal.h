@@ -55,6 +55,7 @@ struct StateView {
   double* Bo[3];
   double* Wo[7];
   uint8_t* status;
+  int32_t* evals;         // FP64 master-function evaluations per cell (gr_con2prim), or nullptr
 };
 // Stage inputs seen in the arithmetic type R of a kernel: the caller's FP64 pools (R = double) or
 // the FP32 copies made by the cast pass (R = float).  Same element indexing as the caller pools.
@@ -131,9 +132,10 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[S
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st);
-cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, int ninterior, const MetricView& m,
                             double* const U[6], const double* const B[3], double* const W[7],
-                            uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st);
+                            uint8_t* status, int32_t* evals, const Workspace& ws, const KParams& kp,
+                            cudaStream_t st);
 cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kS) k_mlp_grad_partial(const float* __restrict
     mlp_layer1(P, xe, h1);
     float z = P[kB3];
     for (int i = 0; i < kMlpH; ++i) {
-      const float h2 = tanhf(mlp_row2(P, i, h1));
+      const float h2 = mlp_tanh(mlp_row2(P, i, h1));
       S.H2[s][i] = h2;
       z = fmaf(P[kW3 + i], h2, z);
     }

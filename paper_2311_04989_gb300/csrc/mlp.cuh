@@ -34,6 +34,11 @@ __device__ __forceinline__ void c2p_features(double q, double r2, double b2, dou
   f[3] = den > 0.0 ? (float)(rb * rb / den) : 0.f;
 }
 
+// tanh from the exponential, tanh x = 1 - 2/(exp(2x) + 1), with the fast hardware exponential and
+// division: absolute error ~1e-6, enough for a bracket proposal that is verified by a sign change
+// (the training kernels use the same function, so the trained network is the evaluated one)
+__device__ __forceinline__ float mlp_tanh(float x) { return 1.f - __fdividef(2.f, __expf(2.f * x) + 1.f); }
+
 // First hidden layer of a normalised input (registers; fully unrolled)
 __device__ __forceinline__ void mlp_layer1(const float* __restrict__ P, const float x[kMlpIn], float h1[kMlpH]) {
   float xn[kMlpIn];
@@ -44,23 +49,24 @@ __device__ __forceinline__ void mlp_layer1(const float* __restrict__ P, const fl
     float a = __ldg(P + kB1 + i);
 #pragma unroll
     for (int j = 0; j < kMlpIn; ++j) a = fmaf(__ldg(P + kW1 + i * kMlpIn + j), xn[j], a);
-    h1[i] = tanhf(a);
+    h1[i] = mlp_tanh(a);
   }
 }
 
-// Pre-activation of second-layer unit i from h1 (row i of W2 read as float4)
+// Pre-activation of second-layer unit i from h1 (row i of W2 read as float4; two partial sums so
+// that the FMA chain is half as long)
 __device__ __forceinline__ float mlp_row2(const float* __restrict__ P, int i, const float h1[kMlpH]) {
   const float4* row = reinterpret_cast<const float4*>(P + kW2 + i * kMlpH);
-  float a = __ldg(P + kB2 + i);
+  float a = __ldg(P + kB2 + i), b = 0.f;
 #pragma unroll
   for (int j4 = 0; j4 < kMlpH / 4; ++j4) {
     const float4 w = __ldg(row + j4);
     a = fmaf(w.x, h1[4 * j4 + 0], a);
-    a = fmaf(w.y, h1[4 * j4 + 1], a);
+    b = fmaf(w.y, h1[4 * j4 + 1], b);
     a = fmaf(w.z, h1[4 * j4 + 2], a);
-    a = fmaf(w.w, h1[4 * j4 + 3], a);
+    b = fmaf(w.w, h1[4 * j4 + 3], b);
   }
-  return a;
+  return a + b;
 }
 
 // Normalised network output z (the prediction of log mu is P[12] + P[13] z).  Kept out of line so
@@ -68,9 +74,17 @@ __device__ __forceinline__ float mlp_row2(const float* __restrict__ P, int i, co
 static __device__ __noinline__ float mlp_z(const float* __restrict__ P, const float x[kMlpIn]) {
   float h1[kMlpH];
   mlp_layer1(P, x, h1);
-  float z = __ldg(P + kB3);
-  for (int i = 0; i < kMlpH; ++i) z = fmaf(__ldg(P + kW3 + i), tanhf(mlp_row2(P, i, h1)), z);
-  return z;
+  // four second-layer units at a time: independent FMA chains for the latency to hide behind
+  float z0 = __ldg(P + kB3), z1 = 0.f, z2 = 0.f, z3 = 0.f;
+  for (int i = 0; i < kMlpH; i += 4) {
+    const float a0 = mlp_row2(P, i, h1), a1 = mlp_row2(P, i + 1, h1);
+    const float a2 = mlp_row2(P, i + 2, h1), a3 = mlp_row2(P, i + 3, h1);
+    z0 = fmaf(__ldg(P + kW3 + i), mlp_tanh(a0), z0);
+    z1 = fmaf(__ldg(P + kW3 + i + 1), mlp_tanh(a1), z1);
+    z2 = fmaf(__ldg(P + kW3 + i + 2), mlp_tanh(a2), z2);
+    z3 = fmaf(__ldg(P + kW3 + i + 3), mlp_tanh(a3), z3);
+  }
+  return (z0 + z1) + (z2 + z3);
 }
 
 }  // namespace grs

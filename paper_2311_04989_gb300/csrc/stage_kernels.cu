@@ -356,7 +356,7 @@ __device__ __forceinline__ void write_cell(const StateView& s, long long c, cons
   for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
 #pragma unroll
   for (int v = 0; v < NW; ++v) s.Wo[v][c] = w[v];
-  s.status[c] = (uint8_t)st;
+  if (s.status) s.status[c] = (uint8_t)st;   // optional for gr_con2prim
 }
 
 // k_update, per interior cell: flux divergence + sources with FP64 accumulation.  Atmosphere cells are
@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(kMaxTile) k_c2p(const DBlock* __restrict__ blo
     int iters;
     const int st = con2prim_cell<EOS>(M, kp, q, Bn, wn, &iters);
     write_cell<EOS>(s, c, q, wn, st);
+    if (s.evals) s.evals[c] = iters;
   }
 }
 
@@ -564,28 +565,45 @@ __global__ void __launch_bounds__(kTile) k_prim2con(const DBlock* __restrict__ b
   if (EOS) a.U[5][c] = q[0] * wv[5];
 }
 
+// gr_con2prim, first pass: atmosphere cells (the threshold test of con2prim on the same FP64 metric)
+// are reset in place; every other cell goes to the job list that k_c2p solves densely.
 template <int EOS>
-__global__ void __launch_bounds__(kTile) k_con2prim(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                    const __grid_constant__ InView<double> m,
-                                                    const __grid_constant__ P2CArgs a,
-                                                    const __grid_constant__ KParams kp) {
+__global__ void __launch_bounds__(kTile) k_con2prim_prep(const DBlock* __restrict__ blocks,
+                                                         const Work* __restrict__ work,
+                                                         const __grid_constant__ InView<double> m,
+                                                         const __grid_constant__ StateView s,
+                                                         const __grid_constant__ Workspace ws,
+                                                         const __grid_constant__ KParams kp) {
   const Work w = work[blockIdx.x];
   const DBlock b = blocks[w.block];
   int p[3];
-  if (!decode<R_INTERIOR, 0>(w, b, p)) return;
-  C2PMet M;
-  cell_gamma64(b, m, p[0], p[1], p[2], M);
-  const long long c = b.cell + cix(b, p[0], p[1], p[2]);
-  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
-  double q[6], Bd[3], wn[7];
-  for (int v = 0; v < NQ; ++v) q[v] = a.U[v][c];
-  cell_field(b, a.B, p[0], p[1], p[2], Bd);
-  int iters = 0;
-  const int st = con2prim_cell<EOS>(M, kp, q, Bd, wn, &iters);
-  for (int v = 0; v < NQ; ++v) a.U[v][c] = q[v];
-  for (int v = 0; v < NW; ++v) const_cast<double*>(a.W[v])[c] = wn[v];
-  if (a.status) a.status[c] = (uint8_t)st;
-  if (a.evals) a.evals[c] = iters;
+  bool queued = false;
+  if (decode<R_INTERIOR, 0>(w, b, p)) {
+    C2PMet M;
+    cell_gamma64(b, m, p[0], p[1], p[2], M);
+    const long long c = b.cell + cix(b, p[0], p[1], p[2]);
+    constexpr int NQ = EOS ? 6 : 5;
+    double q[6], Bd[3], wn[7];
+    q[5] = 0.0;
+    for (int v = 0; v < NQ; ++v) q[v] = s.Uo[v][c];
+    cell_field(b, s.Bo, p[0], p[1], p[2], Bd);
+    bool finite = isfinite(Bd[0]) && isfinite(Bd[1]) && isfinite(Bd[2]);
+    for (int v = 0; v < NQ; ++v) finite = finite && isfinite(q[v]);
+    const double rho_thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
+    if (finite && q[0] < rho_thr * M.sg) {
+      atm_cell<EOS>(M, kp, Bd, q, wn);
+      write_cell<EOS>(s, c, q, wn, GR_ST_ATM_THRESHOLD);
+      if (s.evals) s.evals[c] = 0;
+    } else {
+      queued = true;
+    }
+  }
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xffffffffu, queued);
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(ws.njobs, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (queued) ws.jobs[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(w.block, w.start + (int)threadIdx.x);
 }
 
 // Training samples of the learned bracket: features and log(mu) of the plain bracketed solve of each
@@ -794,18 +812,29 @@ cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
+cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, int ninterior, const MetricView& m,
                             double* const U[6], const double* const B[3], double* const W[7],
-                            uint8_t* status, int32_t* evals, const KParams& kp, cudaStream_t st) {
-  P2CArgs a;
-  for (int v = 0; v < 7; ++v) a.W[v] = W[v];
-  for (int v = 0; v < 6; ++v) a.U[v] = U[v];
-  for (int d = 0; d < 3; ++d) a.B[d] = B[d];
-  a.status = status;
-  a.evals = evals;
+                            uint8_t* status, int32_t* evals, const Workspace& ws, const KParams& kp,
+                            cudaStream_t st) {
   if (!nwork) return cudaSuccess;
-  if (kp.eos == GR_EOS_TABLE) k_con2prim<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
-  else k_con2prim<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, view64(m, nullptr), a, kp);
+  // in place: the state's outputs are the caller's U, W, status
+  StateView s{};
+  for (int v = 0; v < 6; ++v) s.Uo[v] = U[v];
+  for (int v = 0; v < 7; ++v) s.Wo[v] = W[v];
+  for (int d = 0; d < 3; ++d) s.Bo[d] = const_cast<double*>(B[d]);
+  s.status = status;
+  s.evals = evals;
+  cudaError_t e = cudaMemsetAsync(ws.njobs, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const InView<double> in64 = view64(m, nullptr);
+  const int grid2 = (ninterior + kTile - 1) / kTile;
+  if (kp.eos == GR_EOS_TABLE) {
+    k_con2prim_prep<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, in64, s, ws, kp);
+    k_c2p<GR_EOS_TABLE><<<grid2, kTile, 0, st>>>(blocks, in64, s, ws, kp);
+  } else {
+    k_con2prim_prep<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, in64, s, ws, kp);
+    k_c2p<GR_EOS_IDEAL><<<grid2, kTile, 0, st>>>(blocks, in64, s, ws, kp);
+  }
   return cudaGetLastError();
 }
 
