@@ -535,7 +535,8 @@ def main():
         split by the precision the kernel runs them in; the lower-bound time is the sum of
         ops/peak over the two pipes, and peak is the matching effective rate."""
         kms = results[name]["kernel_ms"]
-        k = max(range(len(kms)), key=lambda i: kms[i])
+        # the dominant kernel among those doing the stage's arithmetic (the FP32 cast only copies)
+        k = max((i for i in range(len(kms)) if kernel_phases[G.KERNEL_NAMES[i]]), key=lambda i: kms[i])
         kn = G.KERNEL_NAMES[k]
         mixed = name == "mixed"
         # operations executed in FP32 on the mixed path: everything but con2prim and CT

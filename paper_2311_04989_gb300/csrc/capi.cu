@@ -416,6 +416,7 @@ static KParams kparams(const gr_params* p, double dt) {
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
   k.dt = dt;
+  k.bdt = p->rk_beta * dt;
   k.mlp = p->c2p_guess == GR_GUESS_MLP ? p->mlp : nullptr;
   k.eint_atm = p->p_atm / (p->gamma_ad - 1.0);
   k.h0 = 1.0;

@@ -103,6 +103,7 @@ struct KParams {   // gr_params flattened for the device
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
   double dt;
+  double bdt;         // rk_beta dt
   const float* mlp;   // learned-bracket parameters (GR_GUESS_MLP) or nullptr
   // tabulated EOS: atmosphere (rho_atm, T_atm, Ye_atm) with p_atm and eint_atm precomputed from the
   // table, and the FP64 / FP32 node arrays

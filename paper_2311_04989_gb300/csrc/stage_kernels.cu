@@ -305,11 +305,16 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
   const long long v0 = b.wvert + vix(b, p[0], p[1], p[2]);
   const long long vs1 = t1 == 0 ? 1 : (t1 == 1 ? (long long)(b.N[0] + 1) : (long long)(b.N[0] + 1) * (b.N[1] + 1));
   const long long vs2 = t2 == 0 ? 1 : (t2 == 1 ? (long long)(b.N[0] + 1) : (long long)(b.N[0] + 1) * (b.N[1] + 1));
-  const double dE2 = (to64(E2[v0 + vs1]) - to64(E2[v0])) * b.idx[t1];
-  const double dE1 = (to64(E1[v0 + vs2]) - to64(E1[v0])) * b.idx[t2];
+  // FP64 (the B' differences must stay exact enough for div B at round-off); GB300's FP64 rate is
+  // ~1/64 of FP32, so the operation count is kept minimal: curl = idx1 dE2 - idx2 dE1 by one
+  // multiply and one FMA, then B' = g1 B - beta dt curl by one FMA (no multiply when g1 = 1)
+  const double dE2 = to64(E2[v0 + vs1]) - to64(E2[v0]);
+  const double dE1 = to64(E1[v0 + vs2]) - to64(E1[v0]);
+  const double curl = fma(b.idx[t1], dE2, -(b.idx[t2] * dE1));
   const long long f = b.face[D] + fix(b, D, p[0], p[1], p[2]);
-  double Bn = kp.rk_g1 * s.B[D][f] - kp.rk_beta * kp.dt * (dE2 - dE1);
-  if (kp.rk_g0 != 0.0) Bn += kp.rk_g0 * s.B0[D][f];
+  const double B = s.B[D][f];
+  double Bn = fma(-kp.bdt, curl, kp.rk_g1 == 1.0 ? B : kp.rk_g1 * B);
+  if (kp.rk_g0 != 0.0) Bn = fma(kp.rk_g0, s.B0[D][f], Bn);
   s.Bo[D][f] = Bn;
 }
 
@@ -400,7 +405,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
   const long long g1 = b.wface[1] + fix(b, 1, i, j, k);
   const long long g2 = b.wface[2] + fix(b, 2, i, j, k);
   const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
-  const double bdt = kp.rk_beta * kp.dt;
+  const double bdt = kp.bdt;
   const double cx = bdt * b.idx[0], cy = bdt * b.idx[1], cz = bdt * b.idx[2];
   // flux component of conserved variable v: D, S_j, tau at 0..4; D Y_e at 7 (5, 6 are induction)
   auto comp = [](int v) { return v < 5 ? v : 7; };
@@ -408,7 +413,8 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
     const R* a0 = F0 + comp(v) * ws.fstride[0];
     const R* a1 = F1 + comp(v) * ws.fstride[1];
     const R* a2 = F2 + comp(v) * ws.fstride[2];
-    double u = kp.rk_g1 * s.U[v][c] + bdt * to64(src[v]);
+    const double U = s.U[v][c];
+    double u = fma(bdt, to64(src[v]), kp.rk_g1 == 1.0 ? U : kp.rk_g1 * U);
     u -= cx * (to64(a0[g0 + 1]) - to64(a0[g0]));
     u -= cy * (to64(a1[g1 + oy]) - to64(a1[g1]));
     u -= cz * (to64(a2[g2 + oz]) - to64(a2[g2]));
@@ -418,7 +424,6 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
   constexpr int NQ = EOS ? 6 : 5;
   double q[6], Bn[3], wn[7];
   q[0] = accumulate(0);
-  cell_field(b, s.Bo, i, j, k, Bn);
   if (sizeof(R) == sizeof(float)) {
     // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
     // sqrt(gamma) (same 1e-6 band as the FP64 test) and reset such cells without forming S', tau'
@@ -435,8 +440,15 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
         const R t = a0[g0 + 1] - a0[g0] + a1[g1 + oy] - a1[g1] + a2[g2 + oz] - a2[g2] + src[v];
         finite = finite && isfinite(t) && isfinite(s.U[v][c]);
       }
-      R Bl[3];
-      const R Bf[3] = {R(d2f_rn(Bn[0])), R(d2f_rn(Bn[1])), R(d2f_rn(Bn[2]))};
+      // the cell field of the updated faces in FP32 (the reset needs only calB^2 in FP32)
+      R Bf[3], Bl[3];
+      {
+        const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
+        const long long f2 = b.face[2] + fix(b, 2, i, j, k);
+        Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
+        Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + b.N[0]])));
+        Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + (long long)b.N[0] * b.N[1]])));
+      }
       lower3(M.g, Bf, Bl);
       const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
       q[0] = sg32 * kp.rho_atm;
@@ -458,6 +470,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
   } else {
 #pragma unroll
     for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
+    cell_field(b, s.Bo, i, j, k, Bn);
     // FP64 path: the atmosphere test of con2prim (the same operations, on the same FP64 metric that
     // k_c2p interpolates), decided here for finite cells
     C2PMet Mc;
