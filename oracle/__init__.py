@@ -107,7 +107,7 @@ class Params:
     rk_g1: float = 1.0
     rk_beta: float = 1.0
     max_iter: int = 100
-    recon: int = 1                  # 0 PLM, 1 WENOZ
+    recon: int = 1                  # 0 PLM, 1 WENOZ, 2 WENO5, 3 PPM
     emf: int = 0                    # 0 upwinded corner average, 1 plain mean
     ceiling: int = 0                # 0 clamp W, 1 atmosphere
     interp_order: int = 2

@@ -57,7 +57,7 @@ typedef struct {
   double weno_eps;   // WENOZ epsilon
   double rk_g0, rk_g1, rk_beta;  // stage U' = g0 U0 + g1 U + beta dt L(U)
   int32_t max_iter;  // root-find iteration cap
-  int32_t recon;     // 0 PLM, 1 WENOZ
+  int32_t recon;     // 0 PLM, 1 WENOZ, 2 WENO5, 3 PPM
   int32_t emf;       // 0 upwinded corner average (Gardiner-Stone), 1 plain mean of 4 faces
   int32_t ceiling;   // 0 clamp W (App. A), 1 atmosphere (Sec. 3.6)
   int32_t interp_order;  // 2 or 4
@@ -455,15 +455,92 @@ real wenoz_edge(real v0, real v1, real v2, real v3, real v4, real eps) {
   const real w2 = 0.3 * (1 + tau5 / (s2 + eps));
   return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
 }
+// WENO5 value at the right edge of the middle cell of v[0..4] (Jiang & Shu): the same candidates and
+// smoothness indicators as WENOZ, classic weights alpha_k = d_k / (beta_k + eps)^2
+real weno5_edge(real v0, real v1, real v2, real v3, real v4, real eps) {
+  const real q0 = (2 * v0 - 7 * v1 + 11 * v2) / 6;
+  const real q1 = (-v1 + 5 * v2 + 2 * v3) / 6;
+  const real q2 = (2 * v2 + 5 * v3 - v4) / 6;
+  const real a0 = v0 - 2 * v1 + v2, b0 = v0 - 4 * v1 + 3 * v2;
+  const real a1 = v1 - 2 * v2 + v3, b1 = v1 - v3;
+  const real a2 = v2 - 2 * v3 + v4, b2 = 3 * v2 - 4 * v3 + v4;
+  const real s0 = (13.0 / 12.0) * a0 * a0 + 0.25 * b0 * b0;
+  const real s1 = (13.0 / 12.0) * a1 * a1 + 0.25 * b1 * b1;
+  const real s2 = (13.0 / 12.0) * a2 * a2 + 0.25 * b2 * b2;
+  const real w0 = 0.1 / ((s0 + eps) * (s0 + eps));
+  const real w1 = 0.6 / ((s1 + eps) * (s1 + eps));
+  const real w2 = 0.3 / ((s2 + eps) * (s2 + eps));
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+// PPM (reading of "PPM (Colella et al. 2011, McCorquodale & Colella 2015) as implemented in
+// Athena++"): fourth-order interface values limited by the extremum-preserving criterion of Colella &
+// Sekora, then the parabola of each cell limited the same way at extrema and by the monotonicity
+// conditions elsewhere.  C = 1.25.
+const double PPM_C = 1.25;
+inline real sgn(real x) { return x > 0 ? real(1) : (x < 0 ? real(-1) : real(0)); }
+inline real min3(real a, real b, real c) { return std::min(a, std::min(b, c)); }
+// limited interface value between q1 and q2 (neighbours q0, q3)
+real ppm_iface(real q0, real q1, real q2, real q3) {
+  real qf = (7.0 / 12.0) * (q1 + q2) - (1.0 / 12.0) * (q0 + q3);
+  if ((qf - q1) * (q2 - qf) < 0) {   // not between its neighbours: limit its curvature
+    const real d2f = 3 * (q1 - 2 * qf + q2);
+    const real d2l = q0 - 2 * q1 + q2;
+    const real d2r = q1 - 2 * q2 + q3;
+    real d2lim = 0;
+    if (sgn(d2f) == sgn(d2l) && sgn(d2f) == sgn(d2r) && d2f != 0)
+      d2lim = sgn(d2f) * min3(PPM_C * std::fabs(d2l), PPM_C * std::fabs(d2r), std::fabs(d2f));
+    qf = 0.5 * (q1 + q2) - d2lim / 6;
+  }
+  return qf;
+}
+// left (qm) and right (qp) values of the limited parabola in the middle cell of v[0..4]
+void ppm_cell(real v0, real v1, real v2, real v3, real v4, real* qm, real* qp) {
+  real l = ppm_iface(v0, v1, v2, v3);   // interface v1|v2
+  real r = ppm_iface(v1, v2, v3, v4);   // interface v2|v3
+  const real q = v2;
+  if ((r - q) * (q - l) <= 0 || (v1 - q) * (q - v3) <= 0) {
+    // local extremum: scale the parabola's deviation by the limited curvature
+    const real d2 = 6 * (l - 2 * q + r);
+    const real d2c = v1 - 2 * q + v3;
+    const real d2l = v0 - 2 * v1 + q;
+    const real d2r = q - 2 * v3 + v4;
+    real d2lim = 0;
+    if (sgn(d2) == sgn(d2c) && sgn(d2) == sgn(d2l) && sgn(d2) == sgn(d2r) && d2 != 0)
+      d2lim = sgn(d2) * std::min(min3(PPM_C * std::fabs(d2l), PPM_C * std::fabs(d2r), PPM_C * std::fabs(d2c)),
+                                 std::fabs(d2));
+    if (d2 == 0) { l = q; r = q; }
+    else {
+      l = q + (l - q) * d2lim / d2;
+      r = q + (r - q) * d2lim / d2;
+    }
+  } else {
+    // monotone: keep the parabola from overshooting inside the cell
+    if (std::fabs(r - q) >= 2 * std::fabs(l - q)) r = q - 2 * (l - q);
+    if (std::fabs(l - q) >= 2 * std::fabs(r - q)) l = q - 2 * (r - q);
+  }
+  *qm = l;
+  *qp = r;
+}
+
 // Left/right states at the face between s[2] (left cell) and s[3] (right cell) of a 6-cell stencil
-// s[0..5] = cells f-3 .. f+2.
+// s[0..5] = cells f-3 .. f+2.  Methods: 0 PLM, 1 WENOZ, 2 WENO5, 3 PPM (Sec. 3.4).
 void recon_face(int method, const real s[6], real eps, real* L, real* R) {
   if (method == 0) {
     *L = s[2] + 0.5 * vl_slope(s[1], s[2], s[3]);
     *R = s[3] - 0.5 * vl_slope(s[2], s[3], s[4]);
-  } else {
+  } else if (method == 1) {
     *L = wenoz_edge(s[0], s[1], s[2], s[3], s[4], eps);
     *R = wenoz_edge(s[5], s[4], s[3], s[2], s[1], eps);
+  } else if (method == 2) {
+    *L = weno5_edge(s[0], s[1], s[2], s[3], s[4], eps);
+    *R = weno5_edge(s[5], s[4], s[3], s[2], s[1], eps);
+  } else {
+    real lm, lp, rm, rp;
+    ppm_cell(s[0], s[1], s[2], s[3], s[4], &lm, &lp);   // left cell's parabola: its right value
+    ppm_cell(s[1], s[2], s[3], s[4], s[5], &rm, &rp);   // right cell's parabola: its left value
+    *L = lp;
+    *R = rm;
   }
 }
 
@@ -1199,7 +1276,7 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
   const oparams& Q = *Qp;
   Blk b(G);
   const int g = b.g;
-  const int need = (Q.recon == 1 ? 3 : 2) + (Q.interp_order == 4 ? 1 : 0);
+  const int need = (Q.recon == 0 ? 2 : 3) + (Q.interp_order == 4 ? 1 : 0);
   if (g < need) return -1;
   const long NC = b.ncell();
   const int nq = Q.eos ? 6 : 5, nw = Q.eos ? 7 : 5;

@@ -145,3 +145,68 @@ def test_order2_interpolation_is_not_exact_on_quadratics():
     ax = [x0[d] + (np.arange(0, 3) + 0.5) * dx[d] for d in range(3)]
     Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
     assert np.max(np.abs(val[:, 0] - P(0, X.ravel(), Y.ravel(), Z.ravel()))) > 1e-6
+
+
+# ---- WENO5 (Jiang & Shu) and PPM (Colella-Sekora limited) ------------------------------------------
+def test_weno5_is_the_linear_fifth_order_formula_on_linear_data():
+    """On linear data the three smoothness indicators are equal, so the weights are the linear ones and
+    the value is the upwind fifth-order formula (2 v0 - 13 v1 + 47 v2 + 27 v3 - 3 v4)/60."""
+    rng = np.random.default_rng(4)
+    w = 0.7 + 0.3 * np.arange(20) + 0 * rng.uniform(size=20)
+    L, R = O.recon1d(2, w, eps=1e-40)
+    for f in range(3, 18):
+        v = w[f - 3:f + 2]
+        lin = (2 * v[0] - 13 * v[1] + 47 * v[2] + 27 * v[3] - 3 * v[4]) / 60
+        assert abs(L[f] - lin) < 1e-13
+
+
+@pytest.mark.parametrize("method", [2, 3])
+@pytest.mark.parametrize("coef", [(1.0, 0, 0), (0.3, -2.0, 0), (0.5, 1.0, 4.0)])
+def test_weno5_and_ppm_exact_on_monotone_quadratic_cell_averages(method, coef):
+    """Cell averages of a monotone quadratic: every WENO sub-stencil and the fourth-order PPM interface
+    value are exact, and no PPM limiter engages (no extremum, no overshoot)."""
+    a, b, c = coef
+    F = lambda x: a * x + b * x ** 2 / 2 + c * x ** 3 / 3
+    f = lambda x: a + b * x + c * x ** 2
+    h = 0.02
+    xe = 0.01 + np.arange(31) * h     # f' = b + 2 c x keeps one sign on [0.01, 0.63] for these coefficients
+    w = cell_avg(F, xe[:-1], xe[1:])
+    L, R = O.recon1d(method, w, eps=1e-40)
+    for k in range(3, 28):
+        assert abs(L[k] - f(xe[k])) < 1e-12, (k, L[k], f(xe[k]))
+        assert abs(R[k] - f(xe[k])) < 1e-12
+
+
+@pytest.mark.parametrize("method,min_order", [(2, 4.5), (3, 2.8)])
+def test_weno5_fifth_and_ppm_third_order_on_smooth_data(method, min_order):
+    errs = []
+    for n in (40, 80, 160):
+        h = 1.0 / n
+        xe = np.arange(n + 1) * h
+        w = cell_avg(lambda x: -np.cos(2 * np.pi * x) / (2 * np.pi), xe[:-1], xe[1:])
+        L, R = O.recon1d(method, w, eps=1e-40)
+        k = np.arange(3, n - 2)
+        errs.append(np.mean(np.abs(L[k] - np.sin(2 * np.pi * xe[k])) + np.abs(R[k] - np.sin(2 * np.pi * xe[k]))))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > min_order), orders
+
+
+@pytest.mark.parametrize("method", [2, 3])
+def test_weno5_and_ppm_mirror_symmetric(method):
+    rng = np.random.default_rng(2)
+    w = rng.uniform(0, 1, 40)
+    L, R = O.recon1d(method, w)
+    L2, R2 = O.recon1d(method, w[::-1].copy())
+    for f in range(3, 38):
+        assert abs(L[f] - R2[40 - f]) < 1e-15 and abs(R[f] - L2[40 - f]) < 1e-15
+
+
+def test_ppm_is_monotone_at_a_jump_and_flat_at_an_extremum():
+    w = np.where(np.arange(40) < 20, 1.0, 0.0)
+    L, R = O.recon1d(3, w)
+    k = np.arange(3, 38)
+    assert np.all((L[k] >= 0) & (L[k] <= 1) & (R[k] >= 0) & (R[k] <= 1))
+    # a single-cell spike: the spike cell's parabola is flattened (no overshoot above the spike)
+    s = np.zeros(20); s[10] = 1.0
+    L, R = O.recon1d(3, s)
+    assert L[11] <= 1.0 and R[10] <= 1.0 and np.all(L[3:18] >= 0) and np.all(R[3:18] >= 0)
