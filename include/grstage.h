@@ -50,7 +50,7 @@ typedef enum {
   GR_EUNSUPPORTED = -5  /* option combination not built */
 } gr_error;
 
-enum { GR_RECON_PLM = 0, GR_RECON_WENOZ = 1 };          /* Sec. 3.4 */
+enum { GR_RECON_PLM = 0, GR_RECON_WENOZ = 1, GR_RECON_WENO5 = 2, GR_RECON_PPM = 3 };   /* Sec. 3.4 */
 enum { GR_PREC_FP64 = 0, GR_PREC_MIXED = 1 };           /* mixed: FP32 reconstruction/HLLE/EMF */
 enum { GR_EMF_UPWIND = 0, GR_EMF_MEAN = 1 };            /* Sec. 3.3 corner electric field */
 enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec. 3.5 reset */

@@ -385,7 +385,7 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
 static int check_params(const gr_params* p) {
   if (!p) return fail(GR_EINVAL, "params is NULL");
   if (p->size != sizeof(gr_params)) return fail(GR_EINVAL, "gr_params.size does not match this library");
-  if (p->recon != GR_RECON_PLM && p->recon != GR_RECON_WENOZ) return fail(GR_EINVAL, "bad recon");
+  if (p->recon < GR_RECON_PLM || p->recon > GR_RECON_PPM) return fail(GR_EINVAL, "bad recon");
   if (p->precision != GR_PREC_FP64 && p->precision != GR_PREC_MIXED) return fail(GR_EINVAL, "bad precision");
   if (p->emf != GR_EMF_UPWIND && p->emf != GR_EMF_MEAN) return fail(GR_EINVAL, "bad emf");
   if (p->ceiling != GR_CEIL_CLAMP && p->ceiling != GR_CEIL_ATMOSPHERE) return fail(GR_EINVAL, "bad ceiling");
@@ -520,7 +520,7 @@ static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state*
   if (r) return r;
   if (!std::isfinite(dt) || dt < 0) return fail(GR_EINVAL, "gr_stage: dt must be finite and >= 0");
   if ((r = metric_view(metric, mv, true))) return r;
-  const int need = (params->recon == GR_RECON_WENOZ ? 3 : 2) + (metric->order == 4 ? 1 : 0);
+  const int need = (params->recon == GR_RECON_PLM ? 2 : 3) + (metric->order == 4 ? 1 : 0);
   if (mesh->nblocks > 0 && mesh->min_ng < need)
     return fail(GR_EINVAL, "gr_stage: ghost width too small for the reconstruction / interpolation stencil");
   const bool tab = params->eos == GR_EOS_TABLE;

@@ -1,0 +1,137 @@
+// faces_impl.cuh -- k_faces: reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux
+// (Eq. fluxB_def) on every face with normal index 0..n and transverse index -1..n; with a tabulated EOS
+// (Sec. 2.3) also Y_e and the D Y_e flux = D flux x upwind Y_e.  Instantiated per precision (one
+// translation unit each: faces_f32.cu, faces_f64.cu), EOS and reconstruction method, so each kernel
+// carries the code of one method only.
+#pragma once
+
+#include "internal.h"
+#include "physics.cuh"
+#include "stage_common.cuh"
+
+namespace grs {
+
+// ------------------------------------------------------------------------------------------------
+// k_faces<R>
+// ------------------------------------------------------------------------------------------------
+template <class R, int EOS, int METHOD, int D>
+__device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const InView<R>& in,
+                                          const Workspace& ws, const KParams& kp) {
+  int p[3];
+  if (!decode<R_FACES, D>(w, b, p)) return;
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  constexpr int NV = EOS ? 8 : 7;   // rho, u~^i, p, calB^{t1}, calB^{t2}[, Y_e]
+  // stencil cells p[D]-3 .. p[D]+2 along D; 32-bit offsets within the block, one base pointer per pool
+  const int stride = D == 0 ? 1 : (D == 1 ? b.N[0] : b.N[0] * b.N[1]);
+  int q[3] = {p[0], p[1], p[2]};
+  q[D] -= 3;
+  const int c0 = ((q[2] + b.g) * b.N[1] + (q[1] + b.g)) * b.N[0] + (q[0] + b.g);
+  R st[NV][6];
+  const bool wide = (b.g >= 3 || METHOD != GR_RECON_PLM);
+  const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]) + b.wcell;
+  const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]) + b.wcell;
+  const R* wp[6];
+#pragma unroll
+  for (int v = 0; v < 6; ++v) wp[v] = (v < 5 || EOS) ? in.W[v] + b.cell : nullptr;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    if (!wide && (t == 0 || t == 5)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st[v][t] = R(0);
+      continue;
+    }
+    const int c = c0 + t * stride;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) st[v][t] = wp[v][c];
+    st[5][t] = bc1[c];
+    st[6][t] = bc2[c];
+    if constexpr (EOS == GR_EOS_TABLE) st[7][t] = wp[5][c];
+  }
+  const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
+  R L[NV], Rr[NV];
+  // density and pressure with power-of-two scaling in FP32 (they reach the atmosphere values);
+  // velocities, the transverse field and Y_e without
+  recon<R, METHOD, true>(st[0], eps, &L[0], &Rr[0]);
+  recon<R, METHOD, true>(st[4], eps, &L[4], &Rr[4]);
+#pragma unroll
+  for (int v = 1; v < NV; ++v)
+    if (v != 4) recon<R, METHOD, false>(st[v], eps, &L[v], &Rr[v]);
+  // a non-physical reconstructed state (rho <= 0 or p <= 0) drops the face to first order
+  if (!(L[0] > R(0)) || !(Rr[0] > R(0)) || !(L[4] > R(0)) || !(Rr[4] > R(0))) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
+  }
+  // face states (rho, u~^i, p[, Y_e])
+  R wl[6], wr[6];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { wl[v] = L[v]; wr[v] = Rr[v]; }
+  wl[5] = EOS ? L[NV - 1] : R(0);
+  wr[5] = EOS ? Rr[NV - 1] : R(0);
+  R met[10];
+  face_metric<R>(b, in, in.order, D, p, met);
+  const R det = det3(met + 4);
+  const R sg = rsqrt_(det);
+  const R gdd = inv_dd(met + 4, D, det);
+  const long long fi = fix(b, D, p[0], p[1], p[2]);
+  const R Bn = in.B[D][b.face[D] + fi];
+  R BL[3], BR[3];
+  BL[D] = Bn; BR[D] = Bn;
+  BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
+  BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
+  R UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
+  face_state<R, EOS>(D, met, sg, gdd, kp, wl, BL, UL, FL, &lmL, &lpL);
+  face_state<R, EOS>(D, met, sg, gdd, kp, wr, BR, UR, FR, &lmR, &lpR);
+  R F[7];
+  hlle<R>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
+  R* out = reinterpret_cast<R*>(ws.flux[D]);
+  const long long o = b.wface[D] + fi;
+#pragma unroll
+  for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
+  // D Y_e: the D equation times Y_e (Sec. 2.3), Y_e taken from the upwind state of the mass flux
+  if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
+}
+
+template <class R, int EOS, int METHOD>
+__global__ void __launch_bounds__(kMaxTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+                                                    int nwork, const __grid_constant__ InView<R> in,
+                                                    const __grid_constant__ Workspace ws,
+                                                    const __grid_constant__ KParams kp) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const DBlock b = blocks[w.block];
+    if (w.dir == 0) face_body<R, EOS, METHOD, 0>(w, b, in, ws, kp);
+    else if (w.dir == 1) face_body<R, EOS, METHOD, 1>(w, b, in, ws, kp);
+    else face_body<R, EOS, METHOD, 2>(w, b, in, ws, kp);
+  }
+}
+
+
+template <class R, int EOS, int METHOD>
+static cudaError_t launch_faces_m(const KLaunch& f, const DBlock* blocks, const InView<R>& in, const Workspace& ws,
+                                  const KParams& kp, cudaStream_t st) {
+  k_faces<R, EOS, METHOD><<<stage_grid(k_faces<R, EOS, METHOD>, f, 0), f.threads, 0, st>>>(blocks, f.work, f.nwork,
+                                                                                          in, ws, kp);
+  return cudaGetLastError();
+}
+
+template <class R, int EOS>
+static cudaError_t launch_faces_e(const KLaunch& f, const DBlock* blocks, const InView<R>& in, const Workspace& ws,
+                                  const KParams& kp, cudaStream_t st) {
+  switch (kp.recon) {
+    case GR_RECON_PLM: return launch_faces_m<R, EOS, GR_RECON_PLM>(f, blocks, in, ws, kp, st);
+    case GR_RECON_WENO5: return launch_faces_m<R, EOS, GR_RECON_WENO5>(f, blocks, in, ws, kp, st);
+    case GR_RECON_PPM: return launch_faces_m<R, EOS, GR_RECON_PPM>(f, blocks, in, ws, kp, st);
+    default: return launch_faces_m<R, EOS, GR_RECON_WENOZ>(f, blocks, in, ws, kp, st);
+  }
+}
+
+}  // namespace grs
+
+#define GRS_DEFINE_LAUNCH_FACES(R)                                                                        \
+  namespace grs {                                                                                        \
+  cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<R>& in, const Workspace& ws, \
+                           const KParams& kp, cudaStream_t st) {                                        \
+    return kp.eos == GR_EOS_TABLE ? launch_faces_e<R, GR_EOS_TABLE>(f, blocks, in, ws, kp, st)           \
+                                  : launch_faces_e<R, GR_EOS_IDEAL>(f, blocks, in, ws, kp, st);          \
+  }                                                                                                      \
+  }

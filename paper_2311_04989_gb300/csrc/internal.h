@@ -124,6 +124,12 @@ struct KLaunch {
   int persistent;
 };
 
+// k_faces launchers (faces_f32.cu, faces_f64.cu): one instantiation per EOS and reconstruction method
+cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<float>& in, const Workspace& ws,
+                         const KParams& kp, cudaStream_t st);
+cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<double>& in, const Workspace& ws,
+                         const KParams& kp, cudaStream_t st);
+
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after
 // the cast and each kernel

@@ -290,64 +290,132 @@ __device__ __forceinline__ void pow2_pair(float m, float* sc, float* isc) {
   *isc = __uint_as_float((unsigned)(127 + e) << 23);                // 2^e
 }
 
-// SCALE (FP32 only): scale the stencil by a power of two first.  Needed for variables whose values can
-// be so small that their squared differences underflow (density and pressure near the atmosphere);
-// velocities, the cell field and Y_e are O(1e-10) or larger where they matter and skip it.
-template <class R, bool SCALE = true>
-__device__ __forceinline__ void recon(int method, const R s[6], R eps, R* L, R* Rr);
+// WENO5 (Jiang & Shu) value at the right edge of the middle cell: weights d_k / (beta_k + eps)^2.
+// FP64: multiplied through by the product of the squares so that one division normalises them;
+// FP32: per-weight fast divisions with eps = 1e-18 on the scaled stencil (eps^2 stays a normal float).
+template <class R>
+__device__ __forceinline__ R weno5(R v0, R v1, R v2, R v3, R v4, R eps);
 
 template <>
-__device__ __forceinline__ void recon<double, true>(int method, const double s[6], double eps, double* L,
-                                                    double* Rr) {
-  if (method == GR_RECON_PLM) {
-    *L = s[2] + 0.5 * vl_slope(s[1], s[2], s[3]);
-    *Rr = s[3] - 0.5 * vl_slope(s[2], s[3], s[4]);
-  } else {
-    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
-    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+__device__ __forceinline__ double weno5<double>(double v0, double v1, double v2, double v3, double v4,
+                                                double eps) {
+  double q[3], bk[3];
+  wenoz_parts(v0, v1, v2, v3, v4, q, bk);
+  const double e0 = (bk[0] + eps) * (bk[0] + eps), e1 = (bk[1] + eps) * (bk[1] + eps);
+  const double e2 = (bk[2] + eps) * (bk[2] + eps);
+  const double w0 = 0.1 * (e1 * e2), w1 = 0.6 * (e0 * e2), w2 = 0.3 * (e0 * e1);
+  return (w0 * q[0] + w1 * q[1] + w2 * q[2]) / (w0 + w1 + w2);
+}
+
+template <>
+__device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, float v3, float v4, float eps) {
+  (void)eps;
+  float q[3], bk[3];
+  wenoz_parts(v0, v1, v2, v3, v4, q, bk);
+  const float e = 1e-18f;
+  const float w0 = __fdividef(0.1f, (bk[0] + e) * (bk[0] + e));
+  const float w1 = __fdividef(0.6f, (bk[1] + e) * (bk[1] + e));
+  const float w2 = __fdividef(0.3f, (bk[2] + e) * (bk[2] + e));
+  return __fdividef(w0 * q[0] + w1 * q[1] + w2 * q[2], w0 + w1 + w2);
+}
+
+// PPM: fourth-order interface values limited by the extremum-preserving criterion of Colella & Sekora,
+// then each cell's parabola limited at extrema (curvature) and elsewhere by monotonicity; C = 1.25.
+template <class R> __device__ __forceinline__ R rsgn(R x) { return x > R(0) ? R(1) : (x < R(0) ? R(-1) : R(0)); }
+
+template <class R>
+__device__ __forceinline__ R ppm_iface(R q0, R q1, R q2, R q3) {
+  R qf = R(7.0 / 12.0) * (q1 + q2) - R(1.0 / 12.0) * (q0 + q3);
+  if ((qf - q1) * (q2 - qf) < R(0)) {
+    const R d2f = R(3) * (q1 - R(2) * qf + q2);
+    const R d2l = q0 - R(2) * q1 + q2;
+    const R d2r = q1 - R(2) * q2 + q3;
+    const R sf = rsgn(d2f);
+    R d2lim = R(0);
+    if (sf == rsgn(d2l) && sf == rsgn(d2r) && d2f != R(0))
+      d2lim = sf * rmin(rmin(R(1.25) * rabs(d2l), R(1.25) * rabs(d2r)), rabs(d2f));
+    qf = R(0.5) * (q1 + q2) - d2lim * R(1.0 / 6.0);
   }
+  return qf;
 }
 
-template <>
-__device__ __forceinline__ void recon<double, false>(int method, const double s[6], double eps, double* L,
-                                                     double* Rr) {
-  recon<double, true>(method, s, eps, L, Rr);
-}
-
-template <>
-__device__ __forceinline__ void recon<float, false>(int method, const float s[6], float eps, float* L, float* Rr) {
-  if (method == GR_RECON_PLM) {
-    *L = s[2] + 0.5f * vl_slope(s[1], s[2], s[3]);
-    *Rr = s[3] - 0.5f * vl_slope(s[2], s[3], s[4]);
-  } else {
-    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
-    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
-  }
-}
-
-template <>
-__device__ __forceinline__ void recon<float, true>(int method, const float s[6], float eps, float* L, float* Rr) {
-  if (method == GR_RECON_PLM) {
-    *L = s[2] + 0.5f * vl_slope(s[1], s[2], s[3]);
-    *Rr = s[3] - 0.5f * vl_slope(s[2], s[3], s[4]);
-  } else {
-    float mx = 0.f;
-#pragma unroll
-    for (int t = 0; t < 6; ++t) mx = fmaxf(mx, fabsf(s[t]));
-    // all zero, subnormal or non-finite: nothing to scale (2^e must stay a normal float)
-    if (!(mx >= 1.2e-38f) || !(mx < 1e38f)) {
-      *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
-      *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
-      return;
+template <class R>
+__device__ __forceinline__ void ppm_cell(R v0, R v1, R v2, R v3, R v4, R* qm, R* qp) {
+  R l = ppm_iface(v0, v1, v2, v3), r = ppm_iface(v1, v2, v3, v4);
+  const R q = v2;
+  if ((r - q) * (q - l) <= R(0) || (v1 - q) * (q - v3) <= R(0)) {
+    const R d2 = R(6) * (l - R(2) * q + r);
+    const R d2c = v1 - R(2) * q + v3;
+    const R d2l = v0 - R(2) * v1 + q;
+    const R d2r = q - R(2) * v3 + v4;
+    const R s2 = rsgn(d2);
+    R d2lim = R(0);
+    if (s2 == rsgn(d2c) && s2 == rsgn(d2l) && s2 == rsgn(d2r) && d2 != R(0))
+      d2lim = s2 * rmin(rmin(rmin(R(1.25) * rabs(d2l), R(1.25) * rabs(d2r)), R(1.25) * rabs(d2c)), rabs(d2));
+    if (d2 == R(0)) {
+      l = q;
+      r = q;
+    } else {
+      const R ratio = d2lim / d2;
+      l = q + (l - q) * ratio;
+      r = q + (r - q) * ratio;
     }
-    float sc, isc;
-    pow2_pair(mx, &sc, &isc);
-    float t[6];
-#pragma unroll
-    for (int u = 0; u < 6; ++u) t[u] = s[u] * sc;
-    *L = wenoz(t[0], t[1], t[2], t[3], t[4], eps) * isc;
-    *Rr = wenoz(t[5], t[4], t[3], t[2], t[1], eps) * isc;
+  } else {
+    if (rabs(r - q) >= R(2) * rabs(l - q)) r = q - R(2) * (l - q);
+    if (rabs(l - q) >= R(2) * rabs(r - q)) l = q - R(2) * (r - q);
   }
+  *qm = l;
+  *qp = r;
+}
+
+// Face states of the 6-cell stencil s[0..5] = cells f-3 .. f+2 by method (Sec. 3.4)
+template <class R, int METHOD>
+__device__ __forceinline__ void recon_plain(const R s[6], R eps, R* L, R* Rr) {
+  constexpr int method = METHOD;
+  if constexpr (method == GR_RECON_PLM) {
+    *L = s[2] + R(0.5) * vl_slope(s[1], s[2], s[3]);
+    *Rr = s[3] - R(0.5) * vl_slope(s[2], s[3], s[4]);
+  } else if constexpr (method == GR_RECON_WENOZ) {
+    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
+    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+  } else if constexpr (method == GR_RECON_WENO5) {
+    *L = weno5(s[0], s[1], s[2], s[3], s[4], eps);
+    *Rr = weno5(s[5], s[4], s[3], s[2], s[1], eps);
+  } else {
+    R lm, lp, rm, rp;
+    ppm_cell(s[0], s[1], s[2], s[3], s[4], &lm, &lp);
+    ppm_cell(s[1], s[2], s[3], s[4], s[5], &rm, &rp);
+    *L = lp;
+    *Rr = rm;
+  }
+}
+
+// SCALE (FP32 only): for the WENO and PPM methods, scale the stencil by a power of two near its
+// largest magnitude first (exact, undone on the result).  Needed for variables whose values can be so
+// small that their squared differences underflow (density and pressure near the atmosphere);
+// velocities, the cell field and Y_e are O(1e-10) or larger where they matter and skip it.
+template <class R, int METHOD, bool SCALE = true>
+__device__ __forceinline__ void recon(const R s[6], R eps, R* L, R* Rr) {
+  if constexpr (sizeof(R) == sizeof(float) && SCALE && METHOD != GR_RECON_PLM) {
+    {
+      float mx = 0.f;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) mx = fmaxf(mx, fabsf(s[t]));
+      // all zero, subnormal or non-finite: nothing to scale (2^e must stay a normal float)
+      if (mx >= 1.2e-38f && mx < 1e38f) {
+        float sc, isc;
+        pow2_pair(mx, &sc, &isc);
+        float t[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) t[u] = s[u] * sc;
+        recon_plain<float, METHOD>(t, eps, L, Rr);
+        *L *= isc;
+        *Rr *= isc;
+        return;
+      }
+    }
+  }
+  recon_plain<R, METHOD>(s, eps, L, Rr);
 }
 
 // ------------------------------------------------------------------------------------------------

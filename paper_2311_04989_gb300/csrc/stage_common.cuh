@@ -1,0 +1,57 @@
+// stage_common.cuh -- work-item decoding and launch-grid helpers shared by the stage kernels
+// translation units (stage_kernels.cu, faces_f32.cu, faces_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace grs {
+
+// ------------------------------------------------------------------------------------------------
+// region decoding
+// ------------------------------------------------------------------------------------------------
+template <int KIND, int DIR>
+__device__ __forceinline__ bool decode(const Work& w, const DBlock& b, int p[3]) {
+  int lo[3], cnt[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (KIND == R_CELLS_ALL) { lo[a] = -b.g; cnt[a] = b.N[a]; }
+    else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a] + 2; }
+    else if (KIND == R_EDGES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] : b.n[a] + 1; }
+    else if (KIND == R_CTFACES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a]; }
+    else { lo[a] = 0; cnt[a] = b.n[a]; }
+  }
+  const int e = w.start + threadIdx.x;
+  if (e >= cnt[0] * cnt[1] * cnt[2]) return false;
+  p[0] = lo[0] + e % cnt[0];
+  p[1] = lo[1] + (e / cnt[0]) % cnt[1];
+  p[2] = lo[2] + e / (cnt[0] * cnt[1]);
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ long long face_stride(const DBlock& b, int of_dir) {
+  // element stride of one step along direction of_dir in the D-face layout
+  return of_dir == 0 ? 1 : (of_dir == 1 ? (long long)(b.N[0] + (D == 0)) : (long long)(b.N[0] + (D == 0)) * (b.N[1] + (D == 1)));
+}
+
+__device__ __forceinline__ long long cell_stride(const DBlock& b, int dir) {
+  return dir == 0 ? 1 : (dir == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+}
+
+
+// Grid of a stage-kernel launch: one CTA per work item, or (persistent) the number of CTAs that are
+// resident at once on the device, capped by the number of work items.
+template <class K>
+inline int stage_grid(K kernel, const KLaunch& l, size_t smem) {
+  if (!l.persistent) return l.nwork;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, l.threads, smem);
+  const long long g = (long long)nsm * (occ > 0 ? occ : 1);
+  return (int)(g < l.nwork ? g : l.nwork);
+}
+
+}  // namespace grs

@@ -21,40 +21,9 @@
 
 #include "internal.h"
 #include "physics.cuh"
+#include "stage_common.cuh"
 
 namespace grs {
-
-// ------------------------------------------------------------------------------------------------
-// region decoding
-// ------------------------------------------------------------------------------------------------
-template <int KIND, int DIR>
-__device__ __forceinline__ bool decode(const Work& w, const DBlock& b, int p[3]) {
-  int lo[3], cnt[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (KIND == R_CELLS_ALL) { lo[a] = -b.g; cnt[a] = b.N[a]; }
-    else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a] + 2; }
-    else if (KIND == R_EDGES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] : b.n[a] + 1; }
-    else if (KIND == R_CTFACES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a]; }
-    else { lo[a] = 0; cnt[a] = b.n[a]; }
-  }
-  const int e = w.start + threadIdx.x;
-  if (e >= cnt[0] * cnt[1] * cnt[2]) return false;
-  p[0] = lo[0] + e % cnt[0];
-  p[1] = lo[1] + (e / cnt[0]) % cnt[1];
-  p[2] = lo[2] + e / (cnt[0] * cnt[1]);
-  return true;
-}
-
-template <int D>
-__device__ __forceinline__ long long face_stride(const DBlock& b, int of_dir) {
-  // element stride of one step along direction of_dir in the D-face layout
-  return of_dir == 0 ? 1 : (of_dir == 1 ? (long long)(b.N[0] + (D == 0)) : (long long)(b.N[0] + (D == 0)) * (b.N[1] + (D == 1)));
-}
-
-__device__ __forceinline__ long long cell_stride(const DBlock& b, int dir) {
-  return dir == 0 ? 1 : (dir == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
-}
 
 // ------------------------------------------------------------------------------------------------
 // k_cast: FP64 -> FP32 copies of up to 24 pools
@@ -143,100 +112,6 @@ __global__ void __launch_bounds__(kMaxTile) k_cellprep(const DBlock* __restrict_
   for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
     const Work w = work[it];
     cellprep_body<R>(w, blocks[w.block], in, ws);
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// k_faces<R>
-// ------------------------------------------------------------------------------------------------
-template <class R, int EOS, int D>
-__device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const InView<R>& in,
-                                          const Workspace& ws, const KParams& kp) {
-  int p[3];
-  if (!decode<R_FACES, D>(w, b, p)) return;
-  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
-  constexpr int NV = EOS ? 8 : 7;   // rho, u~^i, p, calB^{t1}, calB^{t2}[, Y_e]
-  // stencil cells p[D]-3 .. p[D]+2 along D; 32-bit offsets within the block, one base pointer per pool
-  const int stride = D == 0 ? 1 : (D == 1 ? b.N[0] : b.N[0] * b.N[1]);
-  int q[3] = {p[0], p[1], p[2]};
-  q[D] -= 3;
-  const int c0 = ((q[2] + b.g) * b.N[1] + (q[1] + b.g)) * b.N[0] + (q[0] + b.g);
-  R st[NV][6];
-  const bool wide = (b.g >= 3 || kp.recon == GR_RECON_WENOZ);
-  const R* bc1 = reinterpret_cast<const R*>(ws.bcc[t1]) + b.wcell;
-  const R* bc2 = reinterpret_cast<const R*>(ws.bcc[t2]) + b.wcell;
-  const R* wp[6];
-#pragma unroll
-  for (int v = 0; v < 6; ++v) wp[v] = (v < 5 || EOS) ? in.W[v] + b.cell : nullptr;
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    if (!wide && (t == 0 || t == 5)) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) st[v][t] = R(0);
-      continue;
-    }
-    const int c = c0 + t * stride;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) st[v][t] = wp[v][c];
-    st[5][t] = bc1[c];
-    st[6][t] = bc2[c];
-    if constexpr (EOS == GR_EOS_TABLE) st[7][t] = wp[5][c];
-  }
-  const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
-  R L[NV], Rr[NV];
-  // density and pressure with power-of-two scaling in FP32 (they reach the atmosphere values);
-  // velocities, the transverse field and Y_e without
-  recon<R, true>(kp.recon, st[0], eps, &L[0], &Rr[0]);
-  recon<R, true>(kp.recon, st[4], eps, &L[4], &Rr[4]);
-#pragma unroll
-  for (int v = 1; v < NV; ++v)
-    if (v != 4) recon<R, false>(kp.recon, st[v], eps, &L[v], &Rr[v]);
-  // a non-physical reconstructed state (rho <= 0 or p <= 0) drops the face to first order
-  if (!(L[0] > R(0)) || !(Rr[0] > R(0)) || !(L[4] > R(0)) || !(Rr[4] > R(0))) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
-  }
-  // face states (rho, u~^i, p[, Y_e])
-  R wl[6], wr[6];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) { wl[v] = L[v]; wr[v] = Rr[v]; }
-  wl[5] = EOS ? L[NV - 1] : R(0);
-  wr[5] = EOS ? Rr[NV - 1] : R(0);
-  R met[10];
-  face_metric<R>(b, in, in.order, D, p, met);
-  const R det = det3(met + 4);
-  const R sg = rsqrt_(det);
-  const R gdd = inv_dd(met + 4, D, det);
-  const long long fi = fix(b, D, p[0], p[1], p[2]);
-  const R Bn = in.B[D][b.face[D] + fi];
-  R BL[3], BR[3];
-  BL[D] = Bn; BR[D] = Bn;
-  BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
-  BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
-  R UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
-  face_state<R, EOS>(D, met, sg, gdd, kp, wl, BL, UL, FL, &lmL, &lpL);
-  face_state<R, EOS>(D, met, sg, gdd, kp, wr, BR, UR, FR, &lmR, &lpR);
-  R F[7];
-  hlle<R>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
-  R* out = reinterpret_cast<R*>(ws.flux[D]);
-  const long long o = b.wface[D] + fi;
-#pragma unroll
-  for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
-  // D Y_e: the D equation times Y_e (Sec. 2.3), Y_e taken from the upwind state of the mass flux
-  if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
-}
-
-template <class R, int EOS>
-__global__ void __launch_bounds__(kMaxTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                    int nwork, const __grid_constant__ InView<R> in,
-                                                    const __grid_constant__ Workspace ws,
-                                                    const __grid_constant__ KParams kp) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const Work w = work[it];
-    const DBlock b = blocks[w.block];
-    if (w.dir == 0) face_body<R, EOS, 0>(w, b, in, ws, kp);
-    else if (w.dir == 1) face_body<R, EOS, 1>(w, b, in, ws, kp);
-    else face_body<R, EOS, 2>(w, b, in, ws, kp);
   }
 }
 
@@ -743,19 +618,6 @@ static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Sh
   return cudaGetLastError();
 }
 
-// Grid of a stage-kernel launch: one CTA per work item, or (persistent) the number of CTAs that are
-// resident at once on the device, capped by the number of work items.
-template <class K>
-static int stage_grid(K kernel, const KLaunch& l, size_t smem) {
-  if (!l.persistent) return l.nwork;
-  int dev = 0, nsm = 0, occ = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, l.threads, smem);
-  const long long g = (long long)nsm * (occ > 0 ? occ : 1);
-  return (int)(g < l.nwork ? g : l.nwork);
-}
-
 template <class R, int EOS>
 static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], const InView<R>& in,
                               const InView<double>& in64, const StateView& s, const Workspace& ws, const KParams& kp,
@@ -764,8 +626,10 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
   if (a.nwork) k_cellprep<R><<<stage_grid(k_cellprep<R>, a, 0), a.threads, 0, st>>>(blocks, a.work, a.nwork, in, ws);
   if (ev) cudaEventRecord(ev[2], st);
   const KLaunch& f = kl[SK_FACES];
-  if (f.nwork)
-    k_faces<R, EOS><<<stage_grid(k_faces<R, EOS>, f, 0), f.threads, 0, st>>>(blocks, f.work, f.nwork, in, ws, kp);
+  if (f.nwork) {
+    const cudaError_t e = launch_faces(f, blocks, in, ws, kp, st);
+    if (e != cudaSuccess) return e;
+  }
   if (ev) cudaEventRecord(ev[3], st);
   const KLaunch& e = kl[SK_EDGES];
   if (e.nwork) k_edges<R><<<stage_grid(k_edges<R>, e, 0), e.threads, 0, st>>>(blocks, e.work, e.nwork, ws, kp);

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgrstage.so")
 
 GR_OK, GR_EINVAL, GR_ECUDA, GR_ENOMEM, GR_ETIMEOUT, GR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-GR_RECON_PLM, GR_RECON_WENOZ = 0, 1
+GR_RECON_PLM, GR_RECON_WENOZ, GR_RECON_WENO5, GR_RECON_PPM = 0, 1, 2, 3
 GR_PREC_FP64, GR_PREC_MIXED = 0, 1
 GR_EMF_UPWIND, GR_EMF_MEAN = 0, 1
 GR_CEIL_CLAMP, GR_CEIL_ATMOSPHERE = 0, 1

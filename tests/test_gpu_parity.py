@@ -33,7 +33,7 @@ def check64(gpu, ref, blocks, tol=TOL64):
     return e
 
 
-@pytest.mark.parametrize("recon", [0, 1])
+@pytest.mark.parametrize("recon", [0, 1, 2, 3])
 def test_uniform_state_bitwise(recon):
     bi = I.uniform_block(n=(9, 7, 5))
     P = O.Params(gamma_ad=5.0 / 3.0, recon=recon, rho_atm=1e-10, tol=1e-15)
@@ -46,7 +46,7 @@ def test_uniform_state_bitwise(recon):
     assert np.all(H.interior(out["status"], n, g) == 0)
 
 
-@pytest.mark.parametrize("recon", [0, 1])
+@pytest.mark.parametrize("recon", [0, 1, 2, 3])
 def test_random_block_fp64_parity(recon):
     bi = I.random_block(n=(16, 12, 10), g=3, seed=21, metric_amp=0.02)
     P = O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-14, tol=1e-15, rk_g0=0.5, rk_g1=0.5, rk_beta=0.5)
@@ -99,11 +99,12 @@ def test_nonzero_extrinsic_curvature_fp64_parity():
     check64(GH.gpu_stage([bi], P, dt, k_zero=False), GH.oracle_stage([bi], P, dt), [bi])
 
 
-def test_mixed_precision_error_bounds():
+@pytest.mark.parametrize("recon", [1, 2, 3])
+def test_mixed_precision_error_bounds(recon):
     """FP32 reconstruction/HLLE/EMF with FP64 accumulation: rho within 1e-6 of the FP64 oracle
-    and div B at FP64 round-off."""
+    and div B at FP64 round-off (WENOZ, WENO5, PPM)."""
     bi = I.random_block(n=(16, 16, 16), g=3, seed=22, metric_amp=0.02)
-    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    P = O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-14, tol=1e-15)
     dt = 0.2 * bi.dx[0]
     out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32)
     ref = GH.oracle_stage([bi], P, dt)
@@ -115,18 +116,23 @@ def test_mixed_precision_error_bounds():
     assert np.max(np.abs(H.interior(d, n, g))) * bi.dx[0] / Bmax < 1e-14
 
 
-def test_mixed_precision_on_a_star_surface():
+@pytest.mark.parametrize("recon", [1, 3])
+def test_mixed_precision_on_a_star_surface(recon):
     """The mixed path across the surface of the magnetised star, where a reconstruction stencil spans
     ~11 decades in density (star against atmosphere): rho within 1e-6 of the FP64 oracle, the same
-    cells set to atmosphere, div B at round-off."""
+    cells set to atmosphere, div B at round-off (WENOZ and PPM).  PPM's limiter takes sign decisions on
+    products of differences; at the surface an FP32 rounding can flip one and move a face value by a
+    limiter correction instead of a rounding, so its bound is 1e-5 (WENOZ's weights vary smoothly)."""
     tov = I.solve_tov()
     bi = I.star_block(n=(32, 32, 32), g=3, half_width=10.02, tov=tov, A_b=0.05)
-    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-10)
+    P = O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-13 * tov.rho[0], tol=1e-10)
     dt = 0.25 * bi.dx[0]
     out = GH.gpu_stage([bi], P, dt, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32)
     ref = GH.oracle_stage([bi], P, dt)
     e = GH.compare(out, ref, [bi])
-    assert e["W0"] < 1e-6 and e["U0"] < 1e-6 and e["status_mismatch"] == 0, e
+    bound = 1e-6 if recon == 1 else 1e-5
+    print(f"star surface, mixed, recon {recon}: rho {e['W0']:.2e}, D {e['U0']:.2e}")
+    assert e["W0"] < bound and e["U0"] < bound and e["status_mismatch"] == 0, e
     n, g = bi.n, bi.ng
     d = O.divb(n, g, bi.dx, out[0]["B"])
     Bmax = max(np.max(np.abs(b)) for b in H.interior_faces(out[0]["B"], n, g))
