@@ -606,3 +606,64 @@ class SyntheticEOS:
         cs2 = self.cs2(R, T, Y)
         return EosTable(tuple(n), x0, dx, np.ascontiguousarray(lp), np.ascontiguousarray(le),
                         np.ascontiguousarray(cs2), self)
+
+
+# ---------------------------------------------------------------------------------------------
+# same-level block topology (ghost exchange of a multi-block RK step)
+# ---------------------------------------------------------------------------------------------
+def neighbour_slot(ox, oy, oz):
+    """Index of the direction (ox, oy, oz) in {-1,0,1}^3 within a block's 27 neighbour entries."""
+    return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)
+
+
+def block_grid_neighbours(nb, periodic=(True, True, True)):
+    """Neighbour table of an nb[0] x nb[1] x nb[2] grid of equal blocks, block index
+    (bz * nb[1] + by) * nb[0] + bx: nbr[b, neighbour_slot(o)] = the block adjacent in direction o, or -1
+    at a non-periodic (outflow) boundary.  Slot 13 (o = 0) is the block itself."""
+    nbx, nby, nbz = nb
+    nbr = np.full((nbx * nby * nbz, 27), -1, np.int32)
+    for bz in range(nbz):
+        for by in range(nby):
+            for bx in range(nbx):
+                b = (bz * nby + by) * nbx + bx
+                for oz in (-1, 0, 1):
+                    for oy in (-1, 0, 1):
+                        for ox in (-1, 0, 1):
+                            c = [bx + ox, by + oy, bz + oz]
+                            ok = True
+                            for a in range(3):
+                                if not 0 <= c[a] < nb[a]:
+                                    if periodic[a]:
+                                        c[a] %= nb[a]
+                                    else:
+                                        ok = False
+                            if ok:
+                                nbr[b, neighbour_slot(ox, oy, oz)] = (c[2] * nby + c[1]) * nbx + c[0]
+    return nbr
+
+
+def split_block(bi: BlockInput, nb):
+    """Cut a ghost-padded block into nb[0] x nb[1] x nb[2] equal sub-blocks (same ghost width) by copying
+    windows of its arrays: ghost regions of the pieces are the neighbours' interiors (or the big block's
+    own ghosts at its boundary).  Block order as in block_grid_neighbours."""
+    n = [bi.n[a] // nb[a] for a in range(3)]
+    assert all(n[a] * nb[a] == bi.n[a] for a in range(3))
+    g = bi.ng
+    out = []
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                o = (bx * n[0], by * n[1], bz * n[2])
+                sc = (slice(o[2], o[2] + n[2] + 2 * g), slice(o[1], o[1] + n[1] + 2 * g), slice(o[0], o[0] + n[0] + 2 * g))
+                sv = tuple(slice(s.start, s.stop + 1) for s in sc)
+                W = np.ascontiguousarray(bi.W[(slice(None),) + sc])
+                M = np.ascontiguousarray(bi.metric[(slice(None),) + sv])
+                B = []
+                for d in range(3):
+                    sf = list(sc)
+                    ax = 2 - d
+                    sf[ax] = slice(sc[ax].start, sc[ax].stop + 1)
+                    B.append(np.ascontiguousarray(bi.B[d][tuple(sf)]))
+                x0 = tuple(bi.x0[a] + o[a] * bi.dx[a] for a in range(3))
+                out.append(BlockInput(tuple(n), g, x0, bi.dx, M, W, B))
+    return out
