@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim bracket-guess timings")
     ap.add_argument("--no-table", action="store_true", help="skip the tabulated-EOS con2prim workload")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of gr_autotune's")
+    ap.add_argument("--no-rk", action="store_true", help="skip the timing of a whole RK3 driver step")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -424,6 +425,38 @@ def main():
         graph_ms = e0.elapsed_time(e1) / a.steps
         G.gr_graph_destroy(gph)
 
+    # ---- a whole RK3 step (ghost exchange + dt + 3 stages) replayed as one CUDA graph -------------
+    rk = None
+    if head == "mixed" and not a.no_rk:
+        pr = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        nbr = I.block_grid_neighbours((a.nb,) * 3, periodic=(False,) * 3)
+        drv = G.gr_driver_create(mesh, nbr)
+        Ur, Wr, Br = U.clone(), W.clone(), [x.clone() for x in B]
+        str_ = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
+        gph = G.gr_driver_capture(drv, metric, list(Ur), list(Wr), Br, str_, pr, 0.25, G.GR_DT_GRID, 3)
+        for _ in range(a.warmup):
+            G.gr_graph_launch(gph, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            G.gr_graph_launch(gph, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_rk = e0.elapsed_time(e1) / a.steps
+        stv = str_.to(torch.int32)
+        rk = {"ms_per_rk3_step": ms_rk, "stages": 3, "cfl": 0.25, "dt": G.gr_driver_dt(drv),
+              "cell_updates_per_s_per_stage": 3 * cells * world / (ms_rk / 1e3),
+              "launches_per_step": 2 + 1 + 3 * 7 + 2 * 2,
+              "failed_cells_after": int(((stv & 2) != 0).sum().item()),
+              "note": "graph of ghost fill (2 kernels) + grid dt (1) + 3 x (7 stage kernels) + 2 inter-stage ghost "
+                      "fills; outflow boundaries; the state evolves over warm-up and timed steps"}
+        G.gr_graph_destroy(gph)
+        G.gr_driver_destroy(drv)
+        del Ur, Wr, Br, str_
+        torch.cuda.empty_cache()
+
     # ---- con2prim with and without a proposed bracket on the stage's output ------------------
     c2p = None
     if not a.no_c2p:
@@ -581,7 +614,7 @@ def main():
            "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
-           "graph_ms_per_step": graph_ms, "con2prim_guess": c2p, "con2prim_table": c2p_table,
+           "graph_ms_per_step": graph_ms, "rk3_driver": rk, "con2prim_guess": c2p, "con2prim_table": c2p_table,
            "launch_shapes": {k: v.get("shapes") for k, v in results.items()},
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
     if rank == 0:

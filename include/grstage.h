@@ -207,6 +207,38 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
 int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]);
 int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]);
 
+/* ---- RK driver: a full time step of a set of same-level blocks -----------------------------------------
+ * (the third-order Runge-Kutta integrator used for every test of Sec. 4-8, stated at the start of
+ * Sec. 4; the global time step of Sec. 3.1)
+ * nbr[27 b + (oz+1) 9 + (oy+1) 3 + (ox+1)] = the block adjacent to block b in direction (ox, oy, oz) in
+ * {-1,0,1}^3, or -1 at an outflow boundary; entry 13 is b itself; neighbours have b's n and ng.  The
+ * driver owns two sets of stage buffers (U, W, B pools of the mesh's pool extents) and dt on the device.
+ * gr_ghost_fill copies every ghost cell of the nw cell pools W and every ghost face of B from the owning
+ * neighbour (outflow: from the nearest owned element of the same block).
+ * gr_cfl_dt: dt = cfl min over interior cells and directions of dx_d / max(|lambda-_d|, |lambda+_d|)
+ * (the fast speeds of Sec. 2.2), reduced on the device into dt_dev (NULL: the driver's own).
+ * dt_mode of a step: GR_DT_GRID, the paper's rule dt = cfl min dx over the mesh (CFL 0.25 on the finest
+ * spacing, Sec. 3.1), or GR_DT_SIGNAL, the wave-speed rule of gr_cfl_dt.
+ * gr_driver_step: ghost fill, dt, then the rk_order (2 or 3) stages of SSP-RK2/RK3 with ghost fills in
+ * between; U, W, B (and status, of the last stage) are updated in place; nothing is synchronised, so
+ * gr_driver_capture records the whole step as one CUDA graph.  gr_driver_dt copies the last dt to the
+ * host (synchronous). */
+typedef struct gr_driver gr_driver;
+enum { GR_DT_GRID = 0, GR_DT_SIGNAL = 1 };
+int gr_driver_create(gr_mesh* mesh, const int32_t* nbr, gr_driver** driver);
+int gr_driver_destroy(gr_driver* driver);
+int gr_ghost_fill(gr_driver* driver, double* const W[7], int32_t nw, double* const B[3], void* stream);
+int gr_cfl_dt(gr_driver* driver, const gr_metric* metric, const double* const W[7], const double* const B[3],
+              const gr_params* params, double cfl, double* dt_dev, void* stream);
+int gr_driver_step(gr_driver* driver, const gr_metric* metric, double* const U[6], double* const W[7],
+                   double* const B[3], uint8_t* status, const gr_params* params, double cfl, int32_t dt_mode,
+                   int32_t rk_order, void* stream);
+int gr_driver_capture(gr_driver* driver, const gr_metric* metric, double* const U[6], double* const W[7],
+                      double* const B[3], uint8_t* status, const gr_params* params, double cfl, int32_t dt_mode,
+                      int32_t rk_order, gr_graph** graph);
+int gr_driver_dt(const gr_driver* driver, double* dt);
+const double* gr_driver_dt_device(const gr_driver* driver);
+
 /* Primitive -> conserved (Eq. consB_def) on the interior cells of every block, with the cell-centred
  * field taken as the mean of the two densitised faces.  W[0..4] (+ W[5] = Y_e with a table) are read;
  * U[0..4] (+ U[5] = D Y_e) written.  Unused trailing entries may be NULL. */

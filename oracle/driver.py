@@ -1,11 +1,15 @@
-"""One Runge-Kutta step of a set of same-level MeshBlocks: ghost exchange, CFL time step, stages
-(Sec. 3.1 time integration with the method-of-lines stages of Sec. 3.2-3.5).
+"""One Runge-Kutta step of a set of same-level MeshBlocks: ghost exchange, time step, stages.
+
+The third-order Runge-Kutta integrator is the one stated at the start of Sec. 4 for every test of the
+paper; the global time step is the CFL factor times the finest grid spacing (Sec. 3.1); each stage is
+the method-of-lines update of Sec. 3.2-3.5.
 
 TEST INFRASTRUCTURE ONLY (part of the oracle: only tests/, smoke() and bench.py's CPU legs use it).
 Plain numpy around the oracle's stage: every ghost cell and ghost face is copied from the block the
 neighbour table names (or, at an outflow boundary, from the nearest interior element of the same
-block); dt = CFL min over interior cells and directions of dx_d / max |lambda_d|; the stages are the
-Shu-Osher forms of SSP-RK2 and SSP-RK3.
+block); dt is either CFL min dx over the blocks (dt_mode "grid", Sec. 3.1) or CFL min over interior
+cells and directions of dx_d / max |lambda_d| (dt_mode "signal"); the stages are the Shu-Osher forms
+of SSP-RK2 and SSP-RK3.
 """
 from __future__ import annotations
 
@@ -91,14 +95,19 @@ def cfl_dt(blocks, W, B, P: O.Params, cfl):
     return cfl / rate
 
 
-def rk_step(blocks, U, nbr, P: O.Params, cfl, order=3):
+def grid_dt(blocks, cfl):
+    """dt = cfl * the finest grid spacing over the blocks (Sec. 3.1)."""
+    return cfl * min(min(bi.dx) for bi in blocks)
+
+
+def rk_step(blocks, U, nbr, P: O.Params, cfl, order=3, dt_mode="signal"):
     """One RK step in place of the blocks' W, B and the conserved U (list of (nq, Nz, Ny, Nx)).
     Returns (dt, statuses of the last stage)."""
     n, g = blocks[0].n, blocks[0].ng
     W = [bi.W for bi in blocks]
     Bf = [bi.B for bi in blocks]
     ghost_fill(W, Bf, nbr, n, g)
-    dt = cfl_dt(blocks, W, Bf, P, cfl)
+    dt = cfl_dt(blocks, W, Bf, P, cfl) if dt_mode == "signal" else grid_dt(blocks, cfl)
     U0 = [u.copy() for u in U]
     B0 = [[f.copy() for f in bb] for bb in Bf]
     st = None

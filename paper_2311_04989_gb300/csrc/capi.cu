@@ -46,13 +46,16 @@ long long region_count(int kind, int dir, const DBlock& b) {
       case R_FACES: n = (a == dir) ? b.n[a] + 1 : b.n[a] + 2; break;
       case R_EDGES: n = (a == dir) ? b.n[a] : b.n[a] + 1; break;
       case R_CTFACES: n = (a == dir) ? b.n[a] + 1 : b.n[a]; break;
+      case R_FACES_ALL: n = b.N[a] + (a == dir); break;
       default: n = b.n[a]; break;
     }
     c *= n;
   }
   return c;
 }
-bool region_has_dir(int kind) { return kind == R_FACES || kind == R_EDGES || kind == R_CTFACES; }
+bool region_has_dir(int kind) {
+  return kind == R_FACES || kind == R_EDGES || kind == R_CTFACES || kind == R_FACES_ALL;
+}
 
 }  // namespace
 
@@ -713,6 +716,234 @@ int gr_c2p_samples(gr_mesh* mesh, const gr_metric* metric, const double* const U
   cudaError_t e = launch_c2p_samples(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mv, U, B,
                                      feats, target, valid, kparams(params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_c2p_samples launch");
+  return GR_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// RK driver: ghost exchange, CFL dt, SSP-RK2/RK3 steps
+// ------------------------------------------------------------------------------------------------
+struct gr_driver {
+  gr_mesh* mesh = nullptr;
+  int device = 0;
+  int* d_nbr = nullptr;
+  double* d_rate = nullptr;
+  double* d_dt = nullptr;
+  double* U[2][6] = {};
+  double* W[2][7] = {};
+  double* B[2][3] = {};
+  uint8_t* status = nullptr;
+  std::vector<void*> allocs;
+};
+
+static void driver_free(gr_driver* d) {
+  if (!d) return;
+  DeviceGuard g(d->device);
+  for (void* p : d->allocs) cudaFree(p);
+  delete d;
+}
+
+int gr_driver_destroy(gr_driver* d) {
+  driver_free(d);
+  return GR_OK;
+}
+
+int gr_driver_create(gr_mesh* mesh, const int32_t* nbr, gr_driver** out) {
+  if (!mesh || !nbr || !out) return fail(GR_EINVAL, "gr_driver_create: NULL argument");
+  const int nb = mesh->nblocks;
+  for (int b = 0; b < nb; ++b) {
+    if (nbr[27 * b + 13] != b) return fail(GR_EINVAL, "gr_driver_create: entry 13 of a block must be the block itself");
+    for (int k = 0; k < 27; ++k) {
+      const int s = nbr[27 * b + k];
+      if (s < -1 || s >= nb) return fail(GR_EINVAL, "gr_driver_create: neighbour index out of range");
+      if (s >= 0) {
+        const DBlock& x = mesh->h_blocks[b];
+        const DBlock& y = mesh->h_blocks[s];
+        if (x.g != y.g || x.n[0] != y.n[0] || x.n[1] != y.n[1] || x.n[2] != y.n[2])
+          return fail(GR_EINVAL, "gr_driver_create: neighbours must have the same size and ghost width");
+        // a ghost layer is copied from the neighbour's owned cells only when it is at least g cells deep
+        const int o[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+        for (int a = 0; a < 3; ++a)
+          if (o[a] != 0 && x.n[a] < x.g)
+            return fail(GR_EINVAL, "gr_driver_create: a block with a neighbour along an axis needs n >= ghost width");
+      }
+    }
+  }
+  DeviceGuard g(mesh->ctx->device);
+  gr_driver* d = new gr_driver();
+  d->mesh = mesh;
+  d->device = mesh->ctx->device;
+  auto dalloc = [&](size_t bytes, void** p) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) d->allocs.push_back(*p);
+    return e;
+  };
+  cudaError_t e = dalloc(sizeof(int) * 27 * std::max(1, nb), (void**)&d->d_nbr);
+  if (e == cudaSuccess && nb) e = cudaMemcpy(d->d_nbr, nbr, sizeof(int) * 27 * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(sizeof(double) * 2, (void**)&d->d_rate);
+  if (e == cudaSuccess) e = dalloc(sizeof(double) * 2, (void**)&d->d_dt);
+  const long long nc = mesh->sh.ncell;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int v = 0; v < 6 && e == cudaSuccess; ++v) e = dalloc(sizeof(double) * nc, (void**)&d->U[k][v]);
+    for (int v = 0; v < 7 && e == cudaSuccess; ++v) e = dalloc(sizeof(double) * nc, (void**)&d->W[k][v]);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(double) * mesh->sh.nface[a], (void**)&d->B[k][a]);
+  }
+  if (e == cudaSuccess) e = dalloc(std::max<long long>(nc, 1), (void**)&d->status);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
+    std::string msg = std::string("gr_driver_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    driver_free(d);
+    return fail(code, msg);
+  }
+  *out = d;
+  return GR_OK;
+}
+
+int gr_ghost_fill(gr_driver* d, double* const W[7], int32_t nw, double* const B[3], void* stream) {
+  if (!d || !W || !B || nw < 0 || nw > 7) return fail(GR_EINVAL, "gr_ghost_fill: bad argument");
+  for (int v = 0; v < nw; ++v)
+    if (!W[v]) return fail(GR_EINVAL, "gr_ghost_fill: NULL cell pool");
+  for (int a = 0; a < 3; ++a)
+    if (!B[a]) return fail(GR_EINVAL, "gr_ghost_fill: NULL face pool");
+  gr_mesh* m = d->mesh;
+  if (m->nblocks == 0) return GR_OK;
+  DeviceGuard g(d->device);
+  cudaError_t e = launch_ghost_fill(m->d_blocks, m->d_work[R_CELLS_ALL], m->nwork[R_CELLS_ALL], m->d_work[R_FACES_ALL],
+                                    m->nwork[R_FACES_ALL], d->d_nbr, W, nw, B, (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_ghost_fill");
+}
+
+int gr_cfl_dt(gr_driver* d, const gr_metric* metric, const double* const W[7], const double* const B[3],
+              const gr_params* params, double cfl, double* dt_dev, void* stream) {
+  if (!d || !W || !B) return fail(GR_EINVAL, "gr_cfl_dt: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  MetricView mv;
+  if ((r = metric_view(metric, mv, false))) return r;
+  if (!(cfl > 0) || !std::isfinite(cfl)) return fail(GR_EINVAL, "gr_cfl_dt: cfl must be positive");
+  gr_mesh* m = d->mesh;
+  DeviceGuard g(d->device);
+  cudaError_t e = launch_cfl_dt(m->d_blocks, m->d_work[R_INTERIOR], m->nwork[R_INTERIOR], mv, W, B, kparams(params, 0.0),
+                                cfl, d->d_rate, dt_dev ? dt_dev : d->d_dt, (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_cfl_dt");
+}
+
+static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const U[6], double* const W[7],
+                            double* const B[3], uint8_t* status, const gr_params* params, double cfl,
+                            int32_t dt_mode, int32_t rk_order, void* stream) {
+  if (!d || !U || !W || !B || !status) return fail(GR_EINVAL, "gr_driver_step: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  if (rk_order != 2 && rk_order != 3) return fail(GR_EINVAL, "gr_driver_step: rk_order must be 2 or 3");
+  if (dt_mode != GR_DT_GRID && dt_mode != GR_DT_SIGNAL) return fail(GR_EINVAL, "gr_driver_step: bad dt_mode");
+  if (!(cfl > 0) || !std::isfinite(cfl)) return fail(GR_EINVAL, "gr_driver_step: cfl must be positive");
+  gr_mesh* m = d->mesh;
+  const bool tab = params->eos == GR_EOS_TABLE;
+  const int nq = tab ? 6 : 5, nw = tab ? 7 : 5;
+  for (int v = 0; v < nq; ++v)
+    if (!U[v]) return fail(GR_EINVAL, "gr_driver_step: NULL conserved pool");
+  for (int v = 0; v < nw; ++v)
+    if (!W[v]) return fail(GR_EINVAL, "gr_driver_step: NULL primitive pool");
+  // (g0, g1, beta) per stage: SSP-RK2 / SSP-RK3 in Shu-Osher form
+  static const double rk2[2][3] = {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}};
+  static const double rk3[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+  const double (*co)[3] = rk_order == 2 ? rk2 : rk3;
+  DeviceGuard g(d->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // ghosts of the step's input state, then dt from it
+  if ((r = gr_ghost_fill(d, W, nw, B, stream))) return r;
+  if (dt_mode == GR_DT_SIGNAL) {
+    if ((r = gr_cfl_dt(d, metric, W, B, params, cfl, nullptr, stream))) return r;
+  } else {
+    double mindx = HUGE_VAL;
+    for (const DBlock& b : m->h_blocks) mindx = std::min(mindx, std::min(b.dx[0], std::min(b.dx[1], b.dx[2])));
+    const cudaError_t e = launch_set_scalar(d->d_dt, cfl * mindx, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step dt");
+  }
+  double* inU[6];
+  double* inW[7];
+  double* inB[3];
+  for (int v = 0; v < 6; ++v) inU[v] = v < nq ? U[v] : nullptr;
+  for (int v = 0; v < 7; ++v) inW[v] = v < nw ? W[v] : nullptr;
+  for (int a = 0; a < 3; ++a) inB[a] = B[a];
+  for (int s = 0; s < rk_order; ++s) {
+    const bool last = s == rk_order - 1;
+    gr_params ps = *params;
+    ps.rk_g0 = co[s][0];
+    ps.rk_g1 = co[s][1];
+    ps.rk_beta = co[s][2];
+    gr_state state{};
+    for (int v = 0; v < nq; ++v) {
+      state.U[v] = inU[v];
+      state.U0[v] = U[v];
+      state.Uo[v] = last ? U[v] : d->U[s % 2][v];
+    }
+    for (int v = 0; v < nw; ++v) {
+      state.W[v] = inW[v];
+      state.Wo[v] = last ? W[v] : d->W[s % 2][v];
+    }
+    for (int a = 0; a < 3; ++a) {
+      state.B[a] = inB[a];
+      state.B0[a] = B[a];
+      state.Bo[a] = last ? B[a] : d->B[s % 2][a];
+    }
+    state.status = last ? status : d->status;
+    MetricView mv;
+    StateView sv{};
+    // the last stage writes over the step's input (also its U0, B0): each thread reads U0, B0 of
+    // its own element before writing it, and the stage's W and B inputs are the previous stage's
+    if ((r = stage_prepare(m, metric, &state, 0.0, &ps, mv, sv))) return r;
+    KLaunch kl[SK_N];
+    stage_launches(m, m->shapes[params->precision][params->eos], kl);
+    KParams kp = kparams(&ps, 0.0);
+    kp.dt_dev = d->d_dt;
+    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step stage");
+    if (!last) {
+      for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];
+      for (int v = 0; v < nw; ++v) inW[v] = d->W[s % 2][v];
+      for (int a = 0; a < 3; ++a) inB[a] = d->B[s % 2][a];
+      if ((r = gr_ghost_fill(d, inW, nw, inB, stream))) return r;
+    }
+  }
+  return GR_OK;
+}
+
+int gr_driver_step(gr_driver* d, const gr_metric* metric, double* const U[6], double* const W[7], double* const B[3],
+                   uint8_t* status, const gr_params* params, double cfl, int32_t dt_mode, int32_t rk_order,
+                   void* stream) {
+  return driver_step_impl(d, metric, U, W, B, status, params, cfl, dt_mode, rk_order, stream);
+}
+
+int gr_driver_dt(const gr_driver* d, double* dt) {
+  if (!d || !dt) return fail(GR_EINVAL, "gr_driver_dt: NULL argument");
+  DeviceGuard g(d->device);
+  cudaError_t e = cudaMemcpy(dt, d->d_dt, sizeof(double), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_driver_dt");
+}
+
+const double* gr_driver_dt_device(const gr_driver* d) { return d ? d->d_dt : nullptr; }
+
+int gr_driver_capture(gr_driver* d, const gr_metric* metric, double* const U[6], double* const W[7],
+                      double* const B[3], uint8_t* status, const gr_params* params, double cfl, int32_t dt_mode,
+                      int32_t rk_order, gr_graph** graph) {
+  if (!d || !graph) return fail(GR_EINVAL, "gr_driver_capture: NULL argument");
+  DeviceGuard g(d->device);
+  cudaStream_t st;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(st); return cuda_fail(e, "cudaStreamBeginCapture"); }
+  const int r = driver_step_impl(d, metric, U, W, B, status, params, cfl, dt_mode, rk_order, st);
+  cudaGraph_t gr = nullptr;
+  e = cudaStreamEndCapture(st, &gr);
+  cudaStreamDestroy(st);
+  if (r != GR_OK) { if (gr) cudaGraphDestroy(gr); return r; }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, gr, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(gr); return cuda_fail(e, "cudaGraphInstantiate"); }
+  *graph = new gr_graph{d->device, gr, ex};
   return GR_OK;
 }
 

@@ -37,7 +37,9 @@ struct Work {
   int pad;
 };
 
-enum Region { R_CELLS_ALL = 0, R_FACES = 1, R_EDGES = 2, R_CTFACES = 3, R_INTERIOR = 4, R_NREGION = 5 };
+// R_FACES_ALL: every face of a block's d-face array, ghosts included (ghost exchange)
+enum Region { R_CELLS_ALL = 0, R_FACES = 1, R_EDGES = 2, R_CTFACES = 3, R_INTERIOR = 4, R_FACES_ALL = 5,
+              R_NREGION = 6 };
 
 // Device views of the caller's pools for one call
 struct MetricView {
@@ -104,6 +106,7 @@ struct KParams {   // gr_params flattened for the device
   double rk_g0, rk_g1, rk_beta;
   double dt;
   double bdt;         // rk_beta dt
+  const double* dt_dev;   // dt on the device (the RK driver's CFL reduction), or nullptr: use dt
   const float* mlp;   // learned-bracket parameters (GR_GUESS_MLP) or nullptr
   // tabulated EOS: atmosphere (rho_atm, T_atm, Ye_atm) with p_atm and eint_atm precomputed from the
   // table, and the FP64 / FP32 node arrays
@@ -146,6 +149,13 @@ cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, i
 cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
+// RK driver (driver.cu): ghost exchange between same-level blocks, CFL dt on the device
+cudaError_t launch_ghost_fill(const DBlock* blocks, const Work* wc, int nwc, const Work* wf, int nwf, const int* nbr,
+                              double* const W[7], int nw, double* const B[3], cudaStream_t st);
+cudaError_t launch_cfl_dt(const DBlock* blocks, const Work* wi, int nwi, const MetricView& m,
+                          const double* const W[7], const double* const B[3], const KParams& kp, double cfl,
+                          double* rate, double* dt, cudaStream_t st);
+cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
 cudaError_t launch_diag(const DBlock* blocks, const Work* work, int nwork, const double* const U[5],
                         const double* const B[3], double* dev_out /* 4 + scratch */, cudaStream_t st);
 

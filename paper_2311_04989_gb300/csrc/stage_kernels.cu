@@ -188,7 +188,7 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
   const double curl = fma(b.idx[t1], dE2, -(b.idx[t2] * dE1));
   const long long f = b.face[D] + fix(b, D, p[0], p[1], p[2]);
   const double B = s.B[D][f];
-  double Bn = fma(-kp.bdt, curl, kp.rk_g1 == 1.0 ? B : kp.rk_g1 * B);
+  double Bn = fma(-stage_bdt(kp), curl, kp.rk_g1 == 1.0 ? B : kp.rk_g1 * B);
   if (kp.rk_g0 != 0.0) Bn = fma(kp.rk_g0, s.B0[D][f], Bn);
   s.Bo[D][f] = Bn;
 }
@@ -280,7 +280,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
   const long long g1 = b.wface[1] + fix(b, 1, i, j, k);
   const long long g2 = b.wface[2] + fix(b, 2, i, j, k);
   const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
-  const double bdt = kp.bdt;
+  const double bdt = stage_bdt(kp);
   const double cx = bdt * b.idx[0], cy = bdt * b.idx[1], cz = bdt * b.idx[2];
   // flux component of conserved variable v: D, S_j, tau at 0..4; D Y_e at 7 (5, 6 are induction)
   auto comp = [](int v) { return v < 5 ? v : 7; };

@@ -34,13 +34,15 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_diag_noalloc", "gr_noalloc_last_error", "gr_mlp_nparam", "gr_mlp_last_error", "gr_c2p_samples",
            "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
            "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
-           "gr_mesh_get_shapes", "gr_mesh_set_shapes"]
+           "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
+           "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device"]
 GR_ABI_VERSION = 2
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
 MLP_MEAN, MLP_ISTD, MLP_TMEAN, MLP_TSTD, MLP_STEP = 0, 6, 12, 13, 14
 GR_NKERNELS = 7
 GR_NSTAGE_KERNELS = 6
+GR_DT_GRID, GR_DT_SIGNAL = 0, 1
 KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update", "k_c2p"]
 
 
@@ -136,6 +138,18 @@ def load(path: str = LIB_PATH):
     L.gr_graph_destroy.argtypes = [vp]
     L.gr_profile_begin.argtypes = [vp, i32]
     L.gr_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
+    L.gr_driver_create.argtypes = [vp, vp, C.POINTER(vp)]
+    L.gr_driver_destroy.argtypes = [vp]
+    L.gr_ghost_fill.argtypes = [vp, C.c_void_p * 7, i32, C.c_void_p * 3, vp]
+    L.gr_cfl_dt.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 7, C.c_void_p * 3, C.POINTER(gr_params),
+                            C.c_double, vp, vp]
+    L.gr_driver_step.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 6, C.c_void_p * 7, C.c_void_p * 3, vp,
+                                 C.POINTER(gr_params), C.c_double, i32, i32, vp]
+    L.gr_driver_capture.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 6, C.c_void_p * 7, C.c_void_p * 3, vp,
+                                    C.POINTER(gr_params), C.c_double, i32, i32, C.POINTER(vp)]
+    L.gr_driver_dt.argtypes = [vp, C.POINTER(C.c_double)]
+    L.gr_driver_dt_device.argtypes = [vp]
+    L.gr_driver_dt_device.restype = vp
     for f in EXPORTS:
         if not hasattr(L, f):
             raise GrstageError(f"libgrstage.so lacks {f}")
@@ -294,6 +308,61 @@ def gr_graph_launch(graph, stream=None):
 
 def gr_graph_destroy(graph):
     load().gr_graph_destroy(graph)
+
+
+def gr_driver_create(mesh, nbr):
+    """nbr: int32 array (n_blocks, 27) on the host; slot (oz+1)*9 + (oy+1)*3 + (ox+1) names the block
+    across that face, edge or corner, -1 for an outflow side."""
+    a = np.ascontiguousarray(nbr, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load().gr_driver_create(mesh, a.ctypes.data, C.byref(h)), "gr_driver_create")
+    return h
+
+
+def gr_driver_destroy(driver):
+    load().gr_driver_destroy(driver)
+
+
+def gr_ghost_fill(driver, W, B, stream=None):
+    W = list(W)
+    _check(load().gr_ghost_fill(driver, _ptrs(7, W), len(W), _ptrs(3, B), _stream(stream)), "gr_ghost_fill")
+
+
+def gr_cfl_dt(driver, metric: gr_metric, W, B, params: gr_params, cfl: float, dt_dev=None, stream=None):
+    dp = int(dt_dev.data_ptr()) if dt_dev is not None else 0
+    _check(load().gr_cfl_dt(driver, C.byref(metric), _ptrs(7, W), _ptrs(3, B), C.byref(params), float(cfl), dp,
+                            _stream(stream)), "gr_cfl_dt")
+
+
+def _step_args(metric, U, W, B, status, params, cfl, dt_mode, rk_order):
+    st = int(status.data_ptr()) if status is not None else 0
+    return (C.byref(metric), _ptrs(6, U), _ptrs(7, W), _ptrs(3, B), st, C.byref(params), float(cfl), int(dt_mode),
+            int(rk_order))
+
+
+def gr_driver_step(driver, metric: gr_metric, U, W, B, status, params: gr_params, cfl: float,
+                   dt_mode: int = GR_DT_GRID, rk_order: int = 3, stream=None):
+    _check(load().gr_driver_step(driver, *_step_args(metric, U, W, B, status, params, cfl, dt_mode, rk_order),
+                                 _stream(stream)), "gr_driver_step")
+
+
+def gr_driver_capture(driver, metric: gr_metric, U, W, B, status, params: gr_params, cfl: float,
+                      dt_mode: int = GR_DT_GRID, rk_order: int = 3):
+    h = C.c_void_p()
+    _check(load().gr_driver_capture(driver, *_step_args(metric, U, W, B, status, params, cfl, dt_mode, rk_order),
+                                    C.byref(h)), "gr_driver_capture")
+    return h
+
+
+def gr_driver_dt(driver) -> float:
+    """dt of the driver's last step (synchronises with the device)."""
+    v = C.c_double()
+    _check(load().gr_driver_dt(driver, C.byref(v)), "gr_driver_dt")
+    return float(v.value)
+
+
+def gr_driver_dt_device(driver) -> int:
+    return int(load().gr_driver_dt_device(driver) or 0)
 
 
 def _mcheck(rc, what):

@@ -86,3 +86,21 @@ def test_cfl_dt_of_a_static_fluid_is_the_sound_crossing_time():
     cs = np.sqrt(gam * p / (rho * h))
     dt = DR.cfl_dt([bi], [bi.W], [bi.B], P, 0.3)
     assert abs(dt / (0.3 * 0.05 / cs) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_rk_stages_reproduce_the_taylor_polynomial_of_a_linear_ode(order):
+    # on u' = lam u an explicit s-stage method of order s = 2, 3 is exactly the degree-s Taylor
+    # polynomial of exp(z), z = lam dt (a dropped or misplaced coefficient changes it)
+    for z in (-0.7, -0.1, 0.3, 1.2):
+        u0, u = 1.0, 1.0
+        for g0, g1, beta in DR.RK_STAGES[order]:
+            u = g0 * u0 + g1 * u + beta * z * u
+        taylor = sum(z ** k / np.prod(range(1, k + 1)) for k in range(order + 1))
+        assert abs(u - taylor) < 1e-15
+
+
+def test_grid_dt_is_the_cfl_factor_times_the_finest_spacing():
+    a = I.uniform_block(n=(4, 4, 4), g=3, dx=(0.1, 0.05, 0.2))
+    b = I.uniform_block(n=(4, 4, 4), g=3, dx=(0.025, 0.3, 0.1))
+    assert DR.grid_dt([a, b], 0.25) == 0.25 * 0.025
