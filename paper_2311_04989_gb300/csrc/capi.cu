@@ -46,7 +46,6 @@ long long region_count(int kind, int dir, const DBlock& b) {
       case R_FACES: n = (a == dir) ? b.n[a] + 1 : b.n[a] + 2; break;
       case R_EDGES: n = (a == dir) ? b.n[a] : b.n[a] + 1; break;
       case R_CTFACES: n = (a == dir) ? b.n[a] + 1 : b.n[a]; break;
-      case R_FACES_ALL: n = b.N[a] + (a == dir); break;
       default: n = b.n[a]; break;
     }
     c *= n;
@@ -54,7 +53,7 @@ long long region_count(int kind, int dir, const DBlock& b) {
   return c;
 }
 bool region_has_dir(int kind) {
-  return kind == R_FACES || kind == R_EDGES || kind == R_CTFACES || kind == R_FACES_ALL;
+  return kind == R_FACES || kind == R_EDGES || kind == R_CTFACES;
 }
 
 }  // namespace
@@ -808,8 +807,7 @@ int gr_ghost_fill(gr_driver* d, double* const W[7], int32_t nw, double* const B[
   gr_mesh* m = d->mesh;
   if (m->nblocks == 0) return GR_OK;
   DeviceGuard g(d->device);
-  cudaError_t e = launch_ghost_fill(m->d_blocks, m->d_work[R_CELLS_ALL], m->nwork[R_CELLS_ALL], m->d_work[R_FACES_ALL],
-                                    m->nwork[R_FACES_ALL], d->d_nbr, W, nw, B, (cudaStream_t)stream);
+  cudaError_t e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, W, nw, B, (cudaStream_t)stream);
   return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_ghost_fill");
 }
 

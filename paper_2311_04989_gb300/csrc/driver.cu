@@ -2,10 +2,11 @@
 // the time step on the device (the RK3 integration stated at the start of Sec. 4; the global CFL time
 // step of Sec. 3.1, or a wave-speed rule).
 //
-//   k_ghost_cells / k_ghost_faces  every ghost cell and ghost face of every block is copied from the
-//                block that the neighbour table names for its direction (or, at an outflow boundary,
-//                from the nearest owned element of the same block).  Sources are always owned
-//                elements, so copies never race with each other.
+//   k_ghost      every ghost cell and ghost face of every block is copied from the block that the
+//                neighbour table names for its direction (or, at an outflow boundary, from the
+//                nearest owned element of the same block); one CTA per block and element kind
+//                striding over the ghost shell only.  Sources are always owned elements, so copies
+//                never race with each other.
 //   k_cfl_rate   max over interior cells and directions of max(|lambda-|, |lambda+|)/dx_d (the fast
 //                speeds of Sec. 2.2 at the cell state), warp-reduced, one atomic max per warp
 //   k_cfl_dt     dt = CFL / rate, left on the device for the stages to read
@@ -24,74 +25,135 @@ struct GhostArgs {
 
 __device__ __forceinline__ int nbr_slot(const int o[3]) { return (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1); }
 
-__global__ void __launch_bounds__(kTile) k_ghost_cells(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                       const __grid_constant__ GhostArgs a) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  int p[3];
-  if (!decode<R_CELLS_ALL, 0>(w, b, p)) return;
-  int o[3];
-  bool ghost = false;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    o[d] = p[d] < 0 ? -1 : (p[d] >= b.n[d] ? 1 : 0);
-    ghost = ghost || o[d] != 0;
-  }
-  if (!ghost) return;
-  const int src = a.nbr[27 * w.block + nbr_slot(o)];
-  int q[3];
-  long long cs;
-  if (src >= 0) {
-    const DBlock& sb = blocks[src];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = p[d] - o[d] * b.n[d];
-    cs = sb.cell + cix(sb, q[0], q[1], q[2]);
-  } else {   // outflow: nearest interior cell of this block
-#pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = min(max(p[d], 0), b.n[d] - 1);
-    cs = b.cell + cix(b, q[0], q[1], q[2]);
-  }
-  const long long c = b.cell + cix(b, p[0], p[1], p[2]);
-  for (int v = 0; v < a.nw; ++v) a.W[v][c] = a.W[v][cs];
+// Ghost shell of a box: the elements of the full array (extent F[a] from -g) outside the owned box
+// (extent O[a] from 0), F[a] - O[a] = 2g.  Enumerated as the two z slabs (full x-y planes), then the
+// two y slabs of each owned z (full x rows), then the two x runs of each owned (y, z) row, so that
+// consecutive threads touch consecutive x wherever the rows are long.
+__host__ __device__ __forceinline__ int shell_count(const int F[3], const int O[3]) {
+  return F[0] * F[1] * F[2] - O[0] * O[1] * O[2];
 }
 
+__device__ __forceinline__ void shell_decode(int e, const int F[3], const int O[3], int g, int p[3]) {
+  const int nz = (F[2] - O[2]) * F[1] * F[0];
+  if (e < nz) {
+    const int t = e / (F[1] * F[0]), r = e - t * F[1] * F[0];
+    p[2] = t < g ? t - g : O[2] + t - g;
+    p[1] = r / F[0] - g;
+    p[0] = r % F[0] - g;
+    return;
+  }
+  e -= nz;
+  const int ny = O[2] * (F[1] - O[1]) * F[0];
+  if (e < ny) {
+    const int row = e / F[0];
+    p[0] = e - row * F[0] - g;
+    const int t = row % (F[1] - O[1]);
+    p[1] = t < g ? t - g : O[1] + t - g;
+    p[2] = row / (F[1] - O[1]);
+    return;
+  }
+  e -= ny;
+  const int w = F[0] - O[0];
+  const int row = e / w, t = e - row * w;
+  p[0] = t < g ? t - g : O[0] + t - g;
+  p[1] = row % O[1];
+  p[2] = row / O[1];
+}
+
+// side of coordinate x of an axis with owned extent own: -1 below, 0 inside, +1 above
+__device__ __forceinline__ int side(int x, int own) { return x < 0 ? -1 : (x >= own ? 1 : 0); }
+
+// One CTA per (block, kind), kind 0 = cells, 1 + D = D-faces; its threads stride over the block's
+// ghost shell.  Neighbours have the block's own sizes (checked when the driver is made), so a source
+// element is the neighbour's base offset plus this block's index of the shifted coordinate: the 27
+// base offsets are staged in shared memory once, and each element costs one load and one store per
+// field, all independent.
+// source and destination offsets (within the pool) of ghost element e of the shell
 template <int D>
-__device__ __forceinline__ void ghost_face(const Work& w, const DBlock& b, const DBlock* blocks, const GhostArgs& a) {
-  int p[3];
-  if (!decode<R_FACES_ALL, D>(w, b, p)) return;
-  // owned faces: 0..n along D, 0..n-1 across
-  int o[3];
-  bool ghost = false;
+__device__ __forceinline__ void ghost_pair(const DBlock& b, const long long* sbase, long long own, const int F[3],
+                                           const int O[3], int e, long long* dst, long long* src) {
+  int p[3], o[3], q[3];
+  shell_decode(e, F, O, b.g, p);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int own = b.n[d] + (d == D);
-    o[d] = p[d] < 0 ? -1 : (p[d] >= own ? 1 : 0);
-    ghost = ghost || o[d] != 0;
-  }
-  if (!ghost) return;
-  const int src = a.nbr[27 * w.block + nbr_slot(o)];
-  int q[3];
-  long long fs;
-  if (src >= 0) {
-    const DBlock& sb = blocks[src];
+  for (int d = 0; d < 3; ++d) o[d] = side(p[d], O[d]);
+  long long base = sbase[nbr_slot(o)];
+  if (base >= 0) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) q[d] = p[d] - o[d] * b.n[d];
-    fs = sb.face[D] + fix(sb, D, q[0], q[1], q[2]);
-  } else {
+  } else {   // outflow: nearest owned element of this block
+    base = own;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = min(max(p[d], 0), b.n[d] - (d == D ? 0 : 1));
-    fs = b.face[D] + fix(b, D, q[0], q[1], q[2]);
+    for (int d = 0; d < 3; ++d) q[d] = min(max(p[d], 0), O[d] - 1);
   }
-  a.B[D][b.face[D] + fix(b, D, p[0], p[1], p[2])] = a.B[D][fs];
+  if constexpr (D < 0) {
+    *dst = own + cix(b, p[0], p[1], p[2]);
+    *src = base + cix(b, q[0], q[1], q[2]);
+  } else {
+    *dst = own + fix(b, D, p[0], p[1], p[2]);
+    *src = base + fix(b, D, q[0], q[1], q[2]);
+  }
 }
 
-__global__ void __launch_bounds__(kTile) k_ghost_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
-                                                       const __grid_constant__ GhostArgs a) {
-  const Work w = work[blockIdx.x];
-  const DBlock b = blocks[w.block];
-  if (w.dir == 0) ghost_face<0>(w, b, blocks, a);
-  else if (w.dir == 1) ghost_face<1>(w, b, blocks, a);
-  else ghost_face<2>(w, b, blocks, a);
+// Each thread copies U elements per pass, all loads before all stores: sources are owned elements
+// and destinations ghosts, so they never alias, but the compiler cannot know that and would
+// otherwise wait for each store before the next load.
+template <int D>
+__device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sbase, const GhostArgs& a) {
+  constexpr int U = D < 0 ? 2 : 6;
+  int F[3], O[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d] = b.N[d] + (d == D);
+    O[d] = b.n[d] + (d == D);
+  }
+  const int cnt = shell_count(F, O);
+  const long long own = D < 0 ? b.cell : b.face[D < 0 ? 0 : D];
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kGhostTile) {
+    long long dst[U], src[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kGhostTile;
+      if (e < cnt) ghost_pair<D>(b, sbase, own, F, O, e, dst + u, src + u);
+      else dst[u] = -1;
+    }
+    if constexpr (D < 0) {
+      double v[U][7];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (k < a.nw && dst[u] >= 0) v[u][k] = a.W[k][src[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (k < a.nw && dst[u] >= 0) a.W[k][dst[u]] = v[u][k];
+    } else {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u] >= 0) v[u] = a.B[D][src[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u] >= 0) a.B[D][dst[u]] = v[u];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kGhostTile) k_ghost(const DBlock* __restrict__ blocks,
+                                                      const __grid_constant__ GhostArgs a) {
+  __shared__ long long sbase[27];   // base offset of the source block per direction, -1: outflow
+  const int blk = blockIdx.x >> 2, kind = (int)(blockIdx.x & 3);
+  const DBlock b = blocks[blk];
+  if (threadIdx.x < 27) {
+    const int src = __ldg(a.nbr + 27 * blk + threadIdx.x);
+    sbase[threadIdx.x] = src < 0 ? -1 : (kind == 0 ? blocks[src].cell : blocks[src].face[kind - 1]);
+  }
+  __syncthreads();
+  if (kind == 0) ghost_body<-1>(b, sbase, a);
+  else if (kind == 1) ghost_body<0>(b, sbase, a);
+  else if (kind == 2) ghost_body<1>(b, sbase, a);
+  else ghost_body<2>(b, sbase, a);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -160,15 +222,14 @@ __global__ void k_cfl_dt(const double* rate, double cfl, double* dt) {
   *dt = r > 0.0 ? cfl / r : 0.0;
 }
 
-cudaError_t launch_ghost_fill(const DBlock* blocks, const Work* wc, int nwc, const Work* wf, int nwf, const int* nbr,
-                              double* const W[7], int nw, double* const B[3], cudaStream_t st) {
+cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
+                              double* const B[3], cudaStream_t st) {
   GhostArgs a{};
   for (int v = 0; v < 7; ++v) a.W[v] = v < nw ? W[v] : nullptr;
   a.nw = nw;
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.nbr = nbr;
-  if (nwc) k_ghost_cells<<<nwc, kTile, 0, st>>>(blocks, wc, a);
-  if (nwf) k_ghost_faces<<<nwf, kTile, 0, st>>>(blocks, wf, a);
+  if (nblocks) k_ghost<<<4 * nblocks, kGhostTile, 0, st>>>(blocks, a);
   return cudaGetLastError();
 }
 

@@ -37,9 +37,7 @@ struct Work {
   int pad;
 };
 
-// R_FACES_ALL: every face of a block's d-face array, ghosts included (ghost exchange)
-enum Region { R_CELLS_ALL = 0, R_FACES = 1, R_EDGES = 2, R_CTFACES = 3, R_INTERIOR = 4, R_FACES_ALL = 5,
-              R_NREGION = 6 };
+enum Region { R_CELLS_ALL = 0, R_FACES = 1, R_EDGES = 2, R_CTFACES = 3, R_INTERIOR = 4, R_NREGION = 5 };
 
 // Device views of the caller's pools for one call
 struct MetricView {
@@ -150,8 +148,9 @@ cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
 // RK driver (driver.cu): ghost exchange between same-level blocks, CFL dt on the device
-cudaError_t launch_ghost_fill(const DBlock* blocks, const Work* wc, int nwc, const Work* wf, int nwf, const int* nbr,
-                              double* const W[7], int nw, double* const B[3], cudaStream_t st);
+constexpr int kGhostTile = 512;
+cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
+                              double* const B[3], cudaStream_t st);
 cudaError_t launch_cfl_dt(const DBlock* blocks, const Work* wi, int nwi, const MetricView& m,
                           const double* const W[7], const double* const B[3], const KParams& kp, double cfl,
                           double* rate, double* dt, cudaStream_t st);

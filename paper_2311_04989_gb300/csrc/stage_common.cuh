@@ -25,7 +25,6 @@ __device__ __forceinline__ bool decode(const Work& w, const DBlock& b, int p[3])
     else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a] + 2; }
     else if (KIND == R_EDGES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] : b.n[a] + 1; }
     else if (KIND == R_CTFACES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a]; }
-    else if (KIND == R_FACES_ALL) { lo[a] = -b.g; cnt[a] = b.N[a] + (a == DIR); }
     else { lo[a] = 0; cnt[a] = b.n[a]; }
   }
   const int e = w.start + threadIdx.x;
