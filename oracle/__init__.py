@@ -175,6 +175,9 @@ def lib():
         L.oracle_table_eval.argtypes = [C.c_int, pp, dp, dp, dp, dp]
         L.oracle_table_hmin.argtypes = [C.POINTER(OTable)]
         L.oracle_table_hmin.restype = C.c_double
+        L.oracle_adm_points.argtypes = [C.c_int, dp, dp, dp, pp, dp]
+        L.oracle_adm_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp, dp, pp, C.c_int, dp]
+        L.oracle_adm_block.restype = C.c_int
         _lib = L
     return _lib
 
@@ -419,3 +422,37 @@ def table_eval(P: Params, rho, T, ye):
     cp = P.c()
     lib().oracle_table_eval(n, C.byref(cp), _d(rho), _d(T), _d(ye), _d(out))
     return out[:, 0], out[:, 1], out[:, 2], out[:, 3]
+
+
+# ---------------------------------------------------------------------------------------------
+# matter sources of the spacetime equations (Sec. 2.1, 2.2) and their cell-to-vertex
+# interpolation (Sec. 3.2)
+# ---------------------------------------------------------------------------------------------
+ADM_NAMES = ("rho_ADM", "S_x", "S_y", "S_z", "S_xx", "S_xy", "S_xz", "S_yy", "S_yz", "S_zz")
+
+
+def adm_points(metric, prims, Bdens, P: Params):
+    """(rho_ADM, S_i, S_ij) at points (n,10); layouts as prim2con."""
+    metric, prims, Bdens = _f64(metric), _f64(prims), _f64(Bdens)
+    n = prims.shape[0]
+    assert prims.shape[1] == P.nw
+    out = np.zeros((n, 10))
+    cp = P.c()
+    lib().oracle_adm_points(n, _d(metric), _d(prims), _d(Bdens), C.byref(cp), _d(out))
+    return out
+
+
+def adm_block(blk: Block, P: Params, vc_order: int = 2):
+    """Matter sources of a block at its owned vertices (10, Nz+1, Ny+1, Nx+1); other vertices NaN."""
+    g = blk.geom()
+    N = [v + 2 * blk.ng for v in blk.n]
+    out = np.full((10, N[2] + 1, N[1] + 1, N[0] + 1), np.nan)
+    W = _f64(blk.W)
+    assert W.shape[0] == P.nw
+    Bx, By, Bz = (_f64(b) for b in blk.B)
+    cp = P.c()
+    rc = lib().oracle_adm_block(C.byref(g), _d(_f64(blk.metric)), _d(W), _d(Bx), _d(By), _d(Bz), C.byref(cp),
+                                int(vc_order), _d(out))
+    if rc != 0:
+        raise ValueError("adm_block: ghost width too small for the interpolation orders")
+    return out

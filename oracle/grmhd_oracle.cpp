@@ -1524,3 +1524,107 @@ void oracle_divb_block(const ob_geom* G, const double* Bx, const double* By, con
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Matter sources of the spacetime equations (Sec. 2.1 hydro form, Sec. 2.2 MHD form) and their
+// cell-to-vertex interpolation (Sec. 3.2)
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// out = (rho_ADM, S_x, S_y, S_z, S_xx, S_xy, S_xz, S_yy, S_yz, S_zz) at one point:
+//   rho_ADM = (rho h + b^2) W^2 - (p + b^2/2) - (alpha b^0)^2
+//   S_i     = (rho h + b^2) W^2 v_i - alpha b^0 b_i
+//   S_ij    = (rho h + b^2) W^2 v_i v_j + (p + b^2/2) gamma_ij - b_i b_j
+// (at B = 0 these are the hydro forms rho h W^2 - p, rho h W^2 v_i, rho h W^2 v_i v_j + p gamma_ij)
+void adm_point(const PM& M, const FP& F, real out[10]) {
+  const real e = F.rho * F.h + F.b2, pt = F.p + F.b2 / 2, ab0 = M.alpha * F.b0;
+  const real eW2 = e * F.W * F.W;
+  out[0] = eW2 - pt - ab0 * ab0;
+  for (int i = 0; i < 3; ++i) out[1 + i] = eW2 * F.v_d[i] - ab0 * F.b_d[i];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) out[4 + SYM[i][j]] = eW2 * F.v_d[i] * F.v_d[j] + pt * M.g[i][j] - F.b_d[i] * F.b_d[j];
+}
+
+}  // namespace
+
+extern "C" {
+
+#ifndef ORACLE_COUNT_FLOPS
+// Matter sources at np points; prims and Bdens as oracle_prim2con; out np x 10.
+void oracle_adm_points(int np, const double* metric, const double* prims, const double* Bdens, const oparams* Q,
+                       double* out) {
+  const int nw = Q->eos ? 7 : 5;
+  for (int n = 0; n < np; ++n) {
+    PM M;
+    pm_from16(metric + 16 * n, M);
+    FP F;
+    fluid_point(M, *Q, prims + nw * n, Bdens + 3 * n, F);
+    real o[10];
+    adm_point(M, F, o);
+    for (int c = 0; c < 10; ++c) out[10 * n + c] = to_d(o[c]);
+  }
+}
+
+// Matter sources of one block at its owned vertices 0..n (per axis), interpolated from the cell
+// centres with the Lagrange interpolant of order vc_order (2: the 2 nearest cells per axis, 4: the
+// 4 nearest), the same midpoint weights as the metric's vertex-to-cell interpolation.  The cell
+// values use the metric interpolated to the cell centre (order Q.interp_order), the cell field
+// (mean of the two densitised faces) and the cell's primitives.  out: 10 x nvert (vertex layout of
+// the metric); entries at other vertices are left untouched.  Returns -1 if the ghost width is too
+// small for the cells the interpolation reads.
+int oracle_adm_block(const ob_geom* G, const double* metric, const double* W, const double* Bx, const double* By,
+                     const double* Bz, const oparams* Q, int vc_order, double* out) {
+  Blk b(G);
+  real wi[4];
+  int off, np;
+  mid_w(vc_order, wi, &off, &np);
+  const int r = np / 2;                            // cells -r .. n + r - 1 per axis
+  const int mg = Q->interp_order == 4 ? 1 : 0;     // extra vertices the cell metric reads
+  if (b.g < r + mg) return -1;
+  const int nw = Q->eos ? 7 : 5;
+  const double* mv[16];
+  for (int c = 0; c < 16; ++c) mv[c] = metric + c * b.nvert();
+  const double* Bf[3] = {Bx, By, Bz};
+  const int C[3] = {b.n[0] + 2 * r, b.n[1] + 2 * r, b.n[2] + 2 * r};
+  std::vector<real> cellv((size_t)10 * C[0] * C[1] * C[2]);
+  auto at = [&](int c, int i, int j, int k) -> real& {
+    return cellv[(((size_t)c * C[2] + (k + r)) * C[1] + (j + r)) * C[0] + (i + r)];
+  };
+  for (int k = -r; k < b.n[2] + r; ++k)
+    for (int j = -r; j < b.n[1] + r; ++j)
+      for (int i = -r; i < b.n[0] + r; ++i) {
+        real m[16];
+        interp_cell(b, mv, Q->interp_order, i, j, k, -1, m);
+        PM M;
+        pm_from16(m, M);
+        const int p[3] = {i, j, k};
+        real Bc[3], w[7];
+        for (int d = 0; d < 3; ++d) {
+          int p1[3] = {i, j, k};
+          p1[d] += 1;
+          Bc[d] = (Bf[d][fidx(b, d, p)] + Bf[d][fidx(b, d, p1)]) / 2;
+        }
+        for (int v = 0; v < nw; ++v) w[v] = W[v * b.ncell() + cidx(b, p)];
+        FP F;
+        fluid_point(M, *Q, w, Bc, F);
+        real o[10];
+        adm_point(M, F, o);
+        for (int c = 0; c < 10; ++c) at(c, i, j, k) = o[c];
+      }
+  // vertex (i, j, k) lies between cells i-1 and i along x (and likewise in y, z)
+  for (int k = 0; k <= b.n[2]; ++k)
+    for (int j = 0; j <= b.n[1]; ++j)
+      for (int i = 0; i <= b.n[0]; ++i)
+        for (int c = 0; c < 10; ++c) {
+          real s = 0;
+          for (int kk = 0; kk < np; ++kk)
+            for (int jj = 0; jj < np; ++jj)
+              for (int ii = 0; ii < np; ++ii)
+                s += wi[ii] * wi[jj] * wi[kk] * at(c, i - 1 + off + ii, j - 1 + off + jj, k - 1 + off + kk);
+          out[c * b.nvert() + b.v(i, j, k)] = to_d(s);
+        }
+  return 0;
+}
+#endif
+
+}  // extern "C"
