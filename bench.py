@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the tabulated-EOS con2prim workload")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of gr_autotune's")
     ap.add_argument("--no-rk", action="store_true", help="skip the timing of a whole RK3 driver step")
+    ap.add_argument("--no-adm", action="store_true", help="skip the timing of the matter-source outputs")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -473,6 +474,31 @@ def main():
         del Ur, Wr, Br, str_
         torch.cuda.empty_cache()
 
+    # ---- matter sources of the spacetime equations at the vertices ------------------------------
+    adm = None
+    if not a.no_adm:
+        outv = torch.empty((10, L.nvert), dtype=torch.float64, device=dev)
+        adm = {}
+        for vo, pname in ((2, "fp64"), (4, "fp64"), (2, "mixed"), (4, "mixed")):
+            pa = G.gr_params_default(recon=G.GR_RECON_WENOZ, gamma_ad=2.0, rho_atm=mesh_in.rho_atm,
+                                     p_atm=mesh_in.p_atm,
+                                     precision=G.GR_PREC_FP64 if pname == "fp64" else G.GR_PREC_MIXED)
+            G.gr_adm_sources(mesh, metric, list(W), B, pa, vo, list(outv), stream)   # first call makes the lists
+            for _ in range(a.warmup):
+                G.gr_adm_sources(mesh, metric, list(W), B, pa, vo, list(outv), stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                G.gr_adm_sources(mesh, metric, list(W), B, pa, vo, list(outv), stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_a = e0.elapsed_time(e1) / a.steps
+            nv = sum((gm.n[0] + 1) * (gm.n[1] + 1) * (gm.n[2] + 1) for gm in geoms)
+            adm[f"{pname}_order{vo}"] = {"ms": ms_a, "owned_vertices": nv, "vertices_per_s": nv / (ms_a / 1e3)}
+        del outv
+        torch.cuda.empty_cache()
+
     # ---- con2prim with and without a proposed bracket on the stage's output ------------------
     c2p = None
     if not a.no_c2p:
@@ -630,7 +656,7 @@ def main():
            "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
-           "graph_ms_per_step": graph_ms, "rk3_driver": rk, "con2prim_guess": c2p, "con2prim_table": c2p_table,
+           "graph_ms_per_step": graph_ms, "rk3_driver": rk, "adm_sources": adm, "con2prim_guess": c2p, "con2prim_table": c2p_table,
            "launch_shapes": {k: v.get("shapes") for k, v in results.items()},
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None}
     if rank == 0:

@@ -207,6 +207,30 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
 int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]);
 int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]);
 
+/* ---- matter sources of the spacetime equations -----------------------------------------------------
+ * gr_adm_sources: rho_ADM, S_i and S_ij, the projections of the stress-energy tensor that the spacetime
+ * equations take as sources (the hydro forms of Sec. 2.1, the MHD forms with the comoving field b of
+ * Sec. 2.2), at every owned vertex (0..n per axis) of every block:
+ *   rho_ADM = (rho h + b^2) W^2 - (p + b^2/2) - (alpha b^0)^2
+ *   S_i     = (rho h + b^2) W^2 v_i - alpha b^0 b_i
+ *   S_ij    = (rho h + b^2) W^2 v_i v_j + (p + b^2/2) gamma_ij - b_i b_j
+ * They are formed at cell centres (metric from its vertex-to-cell interpolant of metric->order, cell
+ * field = mean of the two densitised faces, h from the EOS at (rho, p[, Y_e])) and carried to the
+ * vertices by the Lagrange interpolant of order vc_order (2: the 2 nearest cells per axis, 4: the 4
+ * nearest), the cell-to-vertex transfer of Sec. 3.2.  params->precision GR_PREC_FP64: all arithmetic
+ * in FP64; GR_PREC_MIXED: inputs rounded to FP32 on load, FP32 arithmetic and workspace, FP64 output
+ * (relative error ~1e-7 of each source's scale).
+ *   W       5 (ideal gas) or 6 (table: rho, u~^i, p, Y_e) cell pools; cells -vc_order/2 .. n +
+ *           vc_order/2 - 1 of every block are read, so those ghost cells must hold valid states
+ *   B       densitised face fields, read on the faces of those cells
+ *   out     10 vertex pools in the layout of the metric (rho_ADM, S_x, S_y, S_z, S_xx, S_xy, S_xz,
+ *           S_yy, S_yz, S_zz); only owned vertices are written
+ * The mesh keeps a workspace of 10 cell pools, allocated on the first call.  Errors: GR_EINVAL (NULL
+ * pointer, bad order, ghost width below vc_order/2 + (metric->order == 4)), GR_EUNSUPPORTED (a block
+ * too wide for one shared-memory vertex plane), GR_ENOMEM, GR_ECUDA. */
+int gr_adm_sources(gr_mesh* mesh, const gr_metric* metric, const double* const W[7], const double* const B[3],
+                   const gr_params* params, int32_t vc_order, double* const out[10], void* stream);
+
 /* ---- RK driver: a full time step of a set of same-level blocks -----------------------------------------
  * (the third-order Runge-Kutta integrator used for every test of Sec. 4-8, stated at the start of
  * Sec. 4; the global time step of Sec. 3.1)

@@ -129,6 +129,15 @@ struct gr_mesh {
   std::vector<void*> allocs;
   int64_t ws_bytes = 0;
   int min_ng = 0;
+  // matter-source outputs (gr_adm_sources): cell-layout workspace (FP64-sized) and work lists per
+  // (precision, order 2 / 4), made on first use
+  void* adm_cv[10] = {};
+  Work* adm_cw[2][2] = {};
+  int adm_ncw[2][2] = {};
+  Work* adm_vw[2][2] = {};
+  int adm_nvw[2][2] = {};
+  size_t adm_smem[2][2] = {};
+  bool adm_ready[2][2] = {};
   // profiling: (GR_NKERNELS + 1) events per armed stage
   std::vector<cudaEvent_t> prof_events;
   int prof_capacity = 0;
@@ -671,6 +680,83 @@ int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[7]
                                   B, U, kparams(params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_prim2con launch");
   return GR_OK;
+}
+
+// work lists of the matter-source kernels for one interpolation order (see adm.cu)
+static int adm_prepare(gr_mesh* m, int precision, int vc_order) {
+  const int o = vc_order == 4 ? 1 : 0, pr = precision == GR_PREC_MIXED ? 1 : 0;
+  const size_t elem = pr ? sizeof(float) : sizeof(double);
+  if (m->adm_ready[pr][o]) return GR_OK;
+  const int np = vc_order, r = np / 2;
+  std::vector<Work> cw, vw;
+  size_t smem = 0;
+  for (int bi = 0; bi < m->nblocks; ++bi) {
+    const DBlock& b = m->h_blocks[bi];
+    for (int k = -r; k < b.n[2] + r; ++k) cw.push_back(Work{bi, 0, k, 0});   // one CTA per cell plane
+    if (adm_smem_bytes(b.n, 1, np, elem) > kAdmSmemMax)
+      return fail(GR_EUNSUPPORTED, "gr_adm_sources: block too wide for the interpolation's shared-memory slab");
+    const int planes = b.n[2] + 1;
+    int zfit = 1;
+    while (zfit < planes && adm_smem_bytes(b.n, zfit + 1, np, elem) <= kAdmSmemTarget) ++zfit;
+    const int nslab = (planes + zfit - 1) / zfit, Z = (planes + nslab - 1) / nslab;
+    for (int z0 = 0; z0 < planes; z0 += Z) {
+      const int zc = std::min(Z, planes - z0);
+      vw.push_back(Work{bi, zc, z0, 0});
+      smem = std::max(smem, adm_smem_bytes(b.n, zc, np, elem));
+    }
+  }
+  DeviceGuard g(m->ctx->device);
+  auto upload = [&](const std::vector<Work>& v, Work** dst) -> cudaError_t {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(Work) * std::max<size_t>(v.size(), 1));
+    if (e != cudaSuccess) return e;
+    m->allocs.push_back(*dst);
+    return v.empty() ? cudaSuccess : cudaMemcpy(*dst, v.data(), sizeof(Work) * v.size(), cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = upload(cw, &m->adm_cw[pr][o]);
+  if (e == cudaSuccess) e = upload(vw, &m->adm_vw[pr][o]);
+  for (int c = 0; c < 10 && e == cudaSuccess && !m->adm_cv[c]; ++c) {
+    e = cudaMalloc(&m->adm_cv[c], sizeof(double) * std::max<long long>(m->sh.ncell, 1));
+    if (e == cudaSuccess) m->allocs.push_back(m->adm_cv[c]);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA,
+                std::string("gr_adm_sources: ") + cudaGetErrorString(e));
+  }
+  m->adm_ncw[pr][o] = (int)cw.size();
+  m->adm_nvw[pr][o] = (int)vw.size();
+  m->adm_smem[pr][o] = smem;
+  m->adm_ready[pr][o] = true;
+  return GR_OK;
+}
+
+int gr_adm_sources(gr_mesh* mesh, const gr_metric* metric, const double* const W[7], const double* const B[3],
+                   const gr_params* params, int32_t vc_order, double* const out[10], void* stream) {
+  if (!mesh || !W || !B || !out) return fail(GR_EINVAL, "gr_adm_sources: NULL argument");
+  int r = check_params(params);
+  if (r) return r;
+  MetricView mv;
+  if ((r = metric_view(metric, mv, false))) return r;
+  if (vc_order != 2 && vc_order != 4) return fail(GR_EINVAL, "gr_adm_sources: vc_order must be 2 or 4");
+  const bool tab = params->eos == GR_EOS_TABLE;
+  if (tab && params->table->device != mesh->ctx->device)
+    return fail(GR_EINVAL, "gr_adm_sources: the EOS table lives on another device");
+  for (int v = 0; v < (tab ? 6 : 5); ++v)
+    if (!W[v]) return fail(GR_EINVAL, "gr_adm_sources: NULL primitive array");
+  for (int d = 0; d < 3; ++d)
+    if (!B[d]) return fail(GR_EINVAL, "gr_adm_sources: NULL face array");
+  for (int c = 0; c < 10; ++c)
+    if (!out[c]) return fail(GR_EINVAL, "gr_adm_sources: NULL output array");
+  if (mesh->nblocks == 0) return GR_OK;
+  if (mesh->min_ng < vc_order / 2 + (metric->order == 4 ? 1 : 0))
+    return fail(GR_EINVAL, "gr_adm_sources: ghost width too small for the interpolation orders");
+  if ((r = adm_prepare(mesh, params->precision, vc_order))) return r;
+  const int o = vc_order == 4 ? 1 : 0, pr = params->precision == GR_PREC_MIXED ? 1 : 0;
+  DeviceGuard g(mesh->ctx->device);
+  cudaError_t e = launch_adm(params->precision, mesh->d_blocks, mesh->adm_cw[pr][o], mesh->adm_ncw[pr][o],
+                             mesh->adm_vw[pr][o], mesh->adm_nvw[pr][o], mesh->adm_smem[pr][o], mv, W, B,
+                             kparams(params, 0.0), vc_order, mesh->adm_cv, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_adm_sources launch");
 }
 
 int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], const double* const B[3],

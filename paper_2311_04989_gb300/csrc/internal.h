@@ -148,6 +148,13 @@ cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
 // RK driver (driver.cu): ghost exchange between same-level blocks, CFL dt on the device
+constexpr int kAdmThreads = 256;
+constexpr size_t kAdmSmemTarget = 96 * 1024;    // shared memory a k_adm_verts slab aims for
+constexpr size_t kAdmSmemMax = 200 * 1024;      // ... and may not exceed (one vertex plane)
+size_t adm_smem_bytes(const int n[3], int Z, int np, size_t elem);
+cudaError_t launch_adm(int precision, const DBlock* blocks, const Work* cw, int ncw, const Work* vw, int nvw,
+                       size_t smem, const MetricView& m, const double* const W[7], const double* const B[3],
+                       const KParams& kp, int vc_order, void* const cv[10], double* const out[10], cudaStream_t st);
 constexpr int kGhostTile = 512;
 cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
                               double* const B[3], cudaStream_t st);

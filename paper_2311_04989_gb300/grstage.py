@@ -35,7 +35,8 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_mlp_forward", "gr_mlp_grad", "gr_mlp_train", "gr_graph_capture", "gr_graph_launch",
            "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
-           "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device"]
+           "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
+           "gr_adm_sources"]
 GR_ABI_VERSION = 2
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
@@ -150,6 +151,8 @@ def load(path: str = LIB_PATH):
     L.gr_driver_dt.argtypes = [vp, C.POINTER(C.c_double)]
     L.gr_driver_dt_device.argtypes = [vp]
     L.gr_driver_dt_device.restype = vp
+    L.gr_adm_sources.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 7, C.c_void_p * 3, C.POINTER(gr_params), i32,
+                                 C.c_void_p * 10, vp]
     for f in EXPORTS:
         if not hasattr(L, f):
             raise GrstageError(f"libgrstage.so lacks {f}")
@@ -308,6 +311,15 @@ def gr_graph_launch(graph, stream=None):
 
 def gr_graph_destroy(graph):
     load().gr_graph_destroy(graph)
+
+
+ADM_NAMES = ("rho_ADM", "S_x", "S_y", "S_z", "S_xx", "S_xy", "S_xz", "S_yy", "S_yz", "S_zz")
+
+
+def gr_adm_sources(mesh, metric: gr_metric, W, B, params: gr_params, vc_order, out, stream=None):
+    """rho_ADM, S_i, S_ij at the owned vertices into the 10 vertex pools ``out`` (see include/grstage.h)."""
+    _check(load().gr_adm_sources(mesh, C.byref(metric), _ptrs(7, W), _ptrs(3, B), C.byref(params), int(vc_order),
+                                 _ptrs(10, out), _stream(stream)), "gr_adm_sources")
 
 
 def gr_driver_create(mesh, nbr):
