@@ -167,6 +167,8 @@ def lib():
         L.oracle_stage_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp, dp, dp, dp, dp, dp, dp,
                                          C.c_double, pp, dp, dp, dp, dp, dp, u8, i32]
         L.oracle_stage_block.restype = C.c_int
+        L.oracle_stage_block_ex.argtypes = L.oracle_stage_block.argtypes + [dp, dp, dp, dp]
+        L.oracle_stage_block_ex.restype = C.c_int
         L.oracle_divb_block.argtypes = [C.POINTER(OGeom), dp, dp, dp, dp]
         L.oracle_c2p_samples.argtypes = [C.c_int, dp, dp, dp, pp, dp, dp, u8]
         L.oracle_mlp_nparam.restype = C.c_int
@@ -327,6 +329,53 @@ def stage_block(blk: Block, U, U0, B0, dt, P: Params, return_iters=False):
     if return_iters:
         return Uo, Bo, Wo, st, it
     return Uo, Bo, Wo, st
+
+
+def stage_fluxes(blk: Block, U, U0, B0, dt, P: Params):
+    """The face fluxes and corner EMFs one stage of this block computes: (F, E) with F[d] of shape
+    (nq, *d-face array shape) and E[m] of the vertex-array shape (edge indexed by its low corner)."""
+    return _stage_ex(blk, U, U0, B0, dt, P, None, None)[4:]
+
+
+def stage_block_with(blk: Block, U, U0, B0, dt, P: Params, F, E):
+    """One RK stage with the face fluxes F and corner EMFs E (layouts of stage_fluxes) taking the place
+    of the block's own; returns (U', B', W', status) like stage_block."""
+    return _stage_ex(blk, U, U0, B0, dt, P, F, E)[:4]
+
+
+def _stage_ex(blk, U, U0, B0, dt, P, F_in, E_in):
+    g = blk.geom()
+    metric = _f64(blk.metric)
+    W = _f64(blk.W)
+    B = [_f64(b) for b in blk.B]
+    U = _f64(U); U0 = _f64(U0); B0 = [_f64(b) for b in B0]
+    Uo = U.copy(); Wo = W.copy(); Bo = [b.copy() for b in B]
+    st = np.zeros(W.shape[1:], np.uint8)
+    it = np.zeros(W.shape[1:], np.int32)
+    nq = P.nq
+    N = [v + 2 * blk.ng for v in blk.n]
+    fshape = [(N[2] + (d == 2), N[1] + (d == 1), N[0] + (d == 0)) for d in range(3)]
+    vshape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    Fout = np.zeros(sum(nq * int(np.prod(f)) for f in fshape))
+    Eout = np.zeros(3 * int(np.prod(vshape)))
+    Fin = np.concatenate([_f64(F_in[d]).ravel() for d in range(3)]) if F_in is not None else None
+    Ein = np.concatenate([_f64(E_in[m]).ravel() for m in range(3)]) if E_in is not None else None
+    cp = P.c()
+    r = lib().oracle_stage_block_ex(C.byref(g), _d(metric), _d(W), _d(B[0]), _d(B[1]), _d(B[2]),
+                                    _d(U), _d(U0), _d(B0[0]), _d(B0[1]), _d(B0[2]), float(dt),
+                                    C.byref(cp), _d(Uo), _d(Bo[0]), _d(Bo[1]), _d(Bo[2]), _d(Wo),
+                                    st.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    it.ctypes.data_as(C.POINTER(C.c_int32)), _d(Fout), _d(Eout),
+                                    _d(Fin) if Fin is not None else None, _d(Ein) if Ein is not None else None)
+    if r != 0:
+        raise ValueError("oracle_stage_block_ex: ghost width too small for the stencil")
+    F, o = [], 0
+    for d in range(3):
+        sz = nq * int(np.prod(fshape[d]))
+        F.append(Fout[o:o + sz].reshape((nq,) + fshape[d]))
+        o += sz
+    E = [Eout[m * int(np.prod(vshape)):(m + 1) * int(np.prod(vshape))].reshape(vshape) for m in range(3)]
+    return Uo, Bo, Wo, st, F, E
 
 
 _libc = None

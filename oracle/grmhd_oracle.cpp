@@ -1268,11 +1268,33 @@ void oracle_flops_get(double* out, int reset) {
 //   With a table: W has 7 arrays (rho, u~^i, p, Y_e, T; T unread) and U, U0, Uo 6 (D Y_e last).
 //   Out: Uo (interior cells), Bo (interior faces), Wo (interior prims), status (interior cells).
 // Returns 0, or -1 when the ghost width is too small for the stencil.
+int oracle_stage_block_ex(const ob_geom* G, const double* metric, const double* W, const double* Bx,
+                          const double* By, const double* Bz, const double* U, const double* U0,
+                          const double* B0x, const double* B0y, const double* B0z, double dt,
+                          const oparams* Qp, double* Uo, double* Box, double* Boy, double* Boz, double* Wo,
+                          uint8_t* status, int32_t* iters, double* flux_out, double* emf_out,
+                          const double* flux_in, const double* emf_in);
+
 int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, const double* Bx,
                        const double* By, const double* Bz, const double* U, const double* U0,
                        const double* B0x, const double* B0y, const double* B0z, double dt,
                        const oparams* Qp, double* Uo, double* Box, double* Boy, double* Boz, double* Wo,
                        uint8_t* status, int32_t* iters) {
+  return oracle_stage_block_ex(G, metric, W, Bx, By, Bz, U, U0, B0x, B0y, B0z, dt, Qp, Uo, Box, Boy, Boz, Wo, status,
+                               iters, nullptr, nullptr, nullptr, nullptr);
+}
+
+// The stage of one block, with the face fluxes and corner EMFs exposed for the level-boundary
+// corrections of a refined mesh (Sec. 3.3, last paragraph): flux_out / emf_out (if not NULL) receive the
+// block's fluxes (for d = 0..2, for each conserved variable v, the block's d-face array) and corner
+// EMFs (E_m for m = 0..2, each vertex-indexed by the edge's low corner); flux_in / emf_in (if not
+// NULL, same layouts) replace them before the cell update and the CT update.
+int oracle_stage_block_ex(const ob_geom* G, const double* metric, const double* W, const double* Bx,
+                          const double* By, const double* Bz, const double* U, const double* U0,
+                          const double* B0x, const double* B0y, const double* B0z, double dt,
+                          const oparams* Qp, double* Uo, double* Box, double* Boy, double* Boz, double* Wo,
+                          uint8_t* status, int32_t* iters, double* flux_out, double* emf_out,
+                          const double* flux_in, const double* emf_in) {
   const oparams& Q = *Qp;
   Blk b(G);
   const int g = b.g;
@@ -1430,6 +1452,21 @@ int oracle_stage_block(const ob_geom* G, const double* metric, const double* W, 
           const real da_lo = upw(Vb(ia - 1), Ea(ib - 1) - Ec(ia - 1, ib - 1), Ea(ib) - Ec(ia - 1, ib));
           Ee[m][b.v(e[0], e[1], e[2])] = avg + 0.25 * (db_lo - db_hi) + 0.25 * (da_lo - da_hi);
         }
+  }
+
+  {
+    long off = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < nq; ++v, off += b.nface(d))
+        for (long f = 0; f < b.nface(d); ++f) {
+          if (flux_out) flux_out[off + f] = to_d(Fq[d][v][f]);
+          if (flux_in) Fq[d][v][f] = flux_in[off + f];
+        }
+    for (int m = 0; m < 3; ++m)
+      for (long e = 0; e < b.nvert(); ++e) {
+        if (emf_out) emf_out[m * b.nvert() + e] = to_d(Ee[m][e]);
+        if (emf_in) Ee[m][e] = emf_in[m * b.nvert() + e];
+      }
   }
 
   ORACLE_PHASE(3);

@@ -131,3 +131,93 @@ def evolve(bi, P, dt, nsteps, fill, order=2, rk=2):
             bi.B = Bo
             fill(bi)
     return U, bi
+
+
+def two_level_periodic(seed=0, g=3, bmag=0.05):
+    """A periodic two-level mesh: one coarse block C (8^3 cells of 2h) and four fine blocks F (8^3 cells
+    of h, a 2 x 2 layer along y, z) on its +x side, on [0, 24h) x [0, 16h)^2, h = 1/16.  Every field is
+    generated once on the fine grid (periodic, ghost width 2g) and each block takes its window: fine
+    blocks directly, the coarse block as means over 2^3 cells (W), 2^2 faces (B, from a vector potential
+    whose coarse edge values are means of the two fine edge values, so that the coarse faces equal the
+    means of the fine faces to rounding) and every second vertex (metric).  Ghosts come from the same
+    global field (an AMR code would fill the fine ghosts by prolongation).
+    Returns (blocks [C, F00, F10, F01, F11], records) with records (coarse, fine, d, side, o1, o2)."""
+    from paper_2311_04989_gb300.inputs import BlockInput
+    rng = np.random.default_rng(seed)
+    h = 1.0 / 16
+    nf = (24, 16, 16)
+    G = 2 * g                        # ghost width of the global fine arrays
+    L = (nf[0] * h, nf[1] * h, nf[2] * h)
+    ph = rng.uniform(0, 2 * np.pi, 16)
+    modes = rng.integers(-1, 2, (16, 2, 3))
+    modes[:, :, 0] = np.where(np.all(modes == 0, axis=2), 1, modes[:, :, 0])
+
+    def wave(x, y, z, k):
+        """two plane waves with integer mode numbers on each axis's own period (periodic)"""
+        out = 0.0
+        for q in range(2):
+            m = modes[k, q]
+            out = out + np.sin(2 * np.pi * (m[0] * x / L[0] + m[1] * y / L[1] + m[2] * z / L[2]) + ph[k] + q)
+        return 0.5 * out
+
+    ax = [(np.arange(-G, nf[a] + G) + 0.5) * h for a in range(3)]      # cell centres
+    av = [np.arange(-G, nf[a] + G + 1) * h for a in range(3)]          # vertices
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    W = np.zeros((5,) + X.shape)
+    W[0] = 1e-3 * (1 + 0.3 * wave(X, Y, Z, 0))
+    W[1] = 0.1 * wave(X, Y, Z, 3)
+    W[2] = 0.1 * wave(X, Y, Z, 6)
+    W[3] = 0.05 * wave(X, Y, Z, 9)
+    W[4] = 1e-4 * (1 + 0.3 * wave(X, Y, Z, 1))
+    Zv, Yv, Xv = np.meshgrid(av[2], av[1], av[0], indexing="ij")
+    M = np.zeros((16,) + Xv.shape)
+    M[0] = 1 + 0.01 * wave(Xv, Yv, Zv, 2)
+    M[4] = M[7] = M[9] = 1 + 0.01 * wave(Xv, Yv, Zv, 4)
+    M[5] = 0.002 * wave(Xv, Yv, Zv, 5)
+    # edge vector potential (periodic): A_x at (cell x, vertex y, vertex z), A_y at (vertex x, cell y,
+    # vertex z), A_z at (vertex x, vertex y, cell z)
+    def pot(comp, Xe, Ye, Ze):
+        return bmag * h * 16 * wave(Xe, Ye, Ze, 7 + comp) / (2 * np.pi)
+    Zz, Yy, Xx = np.meshgrid(av[2], av[1], ax[0], indexing="ij"); Axf = pot(0, Xx, Yy, Zz)
+    Zz, Yy, Xx = np.meshgrid(av[2], ax[1], av[0], indexing="ij"); Ayf = pot(1, Xx, Yy, Zz)
+    Zz, Yy, Xx = np.meshgrid(ax[2], av[1], av[0], indexing="ij"); Azf = pot(2, Xx, Yy, Zz)
+
+    def curl(Ax, Ay, Az, d):
+        Bx = (Az[:, 1:, :] - Az[:, :-1, :]) / d - (Ay[1:, :, :] - Ay[:-1, :, :]) / d
+        By = (Ax[1:, :, :] - Ax[:-1, :, :]) / d - (Az[:, :, 1:] - Az[:, :, :-1]) / d
+        Bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / d - (Ax[:, 1:, :] - Ax[:, :-1, :]) / d
+        return [Bx, By, Bz]
+
+    Bf = curl(Axf, Ayf, Azf, h)
+    # coarse potentials: means of the two fine edges along each coarse edge (coarse vertex = even fine
+    # vertex); the coarse grid starts at fine index 0, with G/2 = g coarse ghosts
+    Axc = 0.5 * (Axf[::2, ::2, 0::2] + Axf[::2, ::2, 1::2])
+    Ayc = 0.5 * (Ayf[::2, 0::2, ::2] + Ayf[::2, 1::2, ::2])
+    Azc = 0.5 * (Azf[0::2, ::2, ::2] + Azf[1::2, ::2, ::2])
+    Bc = curl(Axc, Ayc, Azc, 2 * h)
+    Wc = W.reshape(5, W.shape[1] // 2, 2, W.shape[2] // 2, 2, W.shape[3] // 2, 2)
+    Wc = 0.125 * (((Wc[:, :, 0, :, 0, :, 0] + Wc[:, :, 0, :, 0, :, 1]) + (Wc[:, :, 0, :, 1, :, 0] + Wc[:, :, 0, :, 1, :, 1]))
+                  + ((Wc[:, :, 1, :, 0, :, 0] + Wc[:, :, 1, :, 0, :, 1]) + (Wc[:, :, 1, :, 1, :, 0] + Wc[:, :, 1, :, 1, :, 1])))
+    Mc = M[:, ::2, ::2, ::2]
+
+    def cut(a, lo, n, Goff, stag=(0, 0, 0)):
+        s = tuple(slice(lo[ax_] - g + Goff, lo[ax_] + n[ax_] + g + stag[ax_] + Goff) for ax_ in (2, 1, 0))
+        return np.ascontiguousarray(a[(Ellipsis,) + s])
+
+    blocks = []
+    n = (8, 8, 8)
+    gc_off = G // 2                   # coarse global arrays: index 0 is coarse position -g
+    blocks.append(BlockInput(n, g, (0.0, 0.0, 0.0), (2 * h,) * 3, cut(Mc, (0, 0, 0), n, gc_off, (1, 1, 1)),
+                             cut(Wc, (0, 0, 0), n, gc_off),
+                             [cut(Bc[d], (0, 0, 0), n, gc_off, tuple(int(a == d) for a in range(3))) for d in range(3)]))
+    records = []
+    for k in (0, 1):
+        for j in (0, 1):
+            lo = (16, 8 * j, 8 * k)
+            blocks.append(BlockInput(n, g, (lo[0] * h, lo[1] * h, lo[2] * h), (h,) * 3,
+                                     cut(M, lo, n, G, (1, 1, 1)), cut(W, lo, n, G),
+                                     [cut(Bf[d], lo, n, G, tuple(int(a == d) for a in range(3))) for d in range(3)]))
+            f = len(blocks) - 1
+            records.append((0, f, 0, +1, 4 * j, 4 * k))
+            records.append((0, f, 0, -1, 4 * j, 4 * k))   # periodic wrap: the fine +x side meets the coarse -x side
+    return blocks, records

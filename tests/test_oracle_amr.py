@@ -1,0 +1,147 @@
+"""Pins of the oracle's level-boundary operators (Sec. 3.3, last paragraph).
+
+* cell restriction of the cell prolongation is the identity; prolongation is exact on linear fields
+  and stays within the coarse neighbours' range (limited)
+* face restriction of the face prolongation is the identity; every prolonged fine cell is
+  divergence-free; prolongation is exact on linear divergence-free fields, also with unequal spacings
+* on a periodic two-level mesh, one stage with the flux and EMF corrections conserves the total mass
+  to rounding and keeps every coarse face on the level boundary equal to the mean of the fine faces on
+  it; without them both fail (so the test can see the corrections)"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import amr as A
+from tests import helpers as H
+
+
+def _coarse_cells(rng, n=(4, 4, 4), g=2, nvar=2):
+    return rng.uniform(0.5, 2.0, (nvar,) + tuple(v + 2 * g for v in n[::-1]))
+
+
+def test_cell_restriction_of_prolongation_is_identity_and_limited():
+    rng = np.random.default_rng(1)
+    g = 2
+    c = _coarse_cells(rng, g=g)
+    fine = np.zeros((2, 8 + 2 * g, 8 + 2 * g, 8 + 2 * g))
+    A.prolong_cells(c, g, fine, g, (0, 0, 0), (0, 0, 0), (8, 8, 8))
+    back = np.zeros_like(c)
+    A.restrict_cells(fine, g, back, g, (0, 0, 0), (0, 0, 0), (4, 4, 4))
+    s = (slice(None), slice(g, g + 4), slice(g, g + 4), slice(g, g + 4))
+    assert np.max(np.abs(back[s] - c[s])) < 1e-15
+    # every fine value lies within the range of its coarse cell and the cell's face neighbours
+    for k in range(8):
+        for j in range(8):
+            for i in range(8):
+                C = (i // 2 + g, j // 2 + g, k // 2 + g)
+                nb = [c[:, C[2], C[1], C[0]]]
+                for a in range(3):
+                    for s_ in (-1, 1):
+                        q = list(C)
+                        q[a] += s_
+                        nb.append(c[:, q[2], q[1], q[0]])
+                nb = np.array(nb)
+                v = fine[:, k + g, j + g, i + g]
+                assert np.all(v <= nb.max(axis=0) + 1e-15) and np.all(v >= nb.min(axis=0) - 1e-15)
+
+
+def test_cell_prolongation_is_exact_on_linear_fields():
+    g = 2
+    xc = (np.arange(-g, 4 + g) + 0.5) * 2.0     # coarse centres (spacing 2), fine spacing 1
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    c = (1.0 + 0.3 * X - 0.2 * Y + 0.1 * Z)[None]
+    fine = np.zeros((1, 8 + 2 * g, 8 + 2 * g, 8 + 2 * g))
+    A.prolong_cells(c, g, fine, g, (0, 0, 0), (0, 0, 0), (8, 8, 8))
+    xf = np.arange(0, 8) + 0.5
+    Zf, Yf, Xf = np.meshgrid(xf, xf, xf, indexing="ij")
+    assert np.max(np.abs(fine[0, g:g + 8, g:g + 8, g:g + 8] - (1.0 + 0.3 * Xf - 0.2 * Yf + 0.1 * Zf))) < 1e-14
+
+
+def _div(B, n, g, dx):
+    return O.divb(n, g, dx, B)
+
+
+def _coarse_faces_from_potential(rng, n, g, dx):
+    """a divergence-free coarse face field (discrete curl of random edge values)"""
+    N = [v + 2 * g for v in n]
+    Ax = rng.normal(size=(N[2] + 1, N[1] + 1, N[0]))
+    Ay = rng.normal(size=(N[2] + 1, N[1], N[0] + 1))
+    Az = rng.normal(size=(N[2], N[1] + 1, N[0] + 1))
+    Bx = (Az[:, 1:, :] - Az[:, :-1, :]) / dx[1] - (Ay[1:, :, :] - Ay[:-1, :, :]) / dx[2]
+    By = (Ax[1:, :, :] - Ax[:-1, :, :]) / dx[2] - (Az[:, :, 1:] - Az[:, :, :-1]) / dx[0]
+    Bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / dx[0] - (Ax[:, 1:, :] - Ax[:, :-1, :]) / dx[1]
+    return [Bx, By, Bz]
+
+
+@pytest.mark.parametrize("dx", [(1.0, 1.0, 1.0), (1.0, 0.5, 2.0)])
+def test_face_prolongation_restores_the_coarse_faces_and_is_divergence_free(dx):
+    rng = np.random.default_rng(2)
+    n, g = (4, 4, 4), 2
+    dxc = tuple(2 * v for v in dx)
+    Bc = _coarse_faces_from_potential(rng, n, g, dxc)
+    nf = (8, 8, 8)
+    Bf = [np.zeros((nf[2] + 2 * g + (d == 2), nf[1] + 2 * g + (d == 1), nf[0] + 2 * g + (d == 0))) for d in range(3)]
+    A.prolong_faces(Bc, g, Bf, g, (0, 0, 0), (0, 0, 0), nf, dx)
+    div = _div(Bf, nf, g, dx)
+    scale = max(np.max(np.abs(b)) for b in Bf) / min(dx)
+    assert np.max(np.abs(div[g:g + 8, g:g + 8, g:g + 8])) < 1e-13 * scale
+    back = [b.copy() for b in Bc]
+    A.restrict_faces(Bf, g, back, g, (0, 0, 0), (0, 0, 0), n)
+    for d in range(3):
+        s = tuple(slice(g, g + n[a] + (a == d)) for a in (2, 1, 0))
+        assert np.max(np.abs(back[d][s] - Bc[d][s])) < 1e-13 * np.max(np.abs(Bc[d]))
+
+
+def test_face_prolongation_is_exact_on_linear_divergence_free_fields():
+    # B = (a + 2y - z - x, 3 + x + 0.5 z + y, 1 + 2x - y); div = -1 + 1 + 0 = 0
+    g, n, nf = 2, (4, 4, 4), (8, 8, 8)
+    dx = (1.0, 1.0, 1.0)
+
+    def field(d, X, Y, Z):
+        return (0.7 + 2 * Y - Z - X, 3 + X + 0.5 * Z + Y, 1 + 2 * X - Y)[d]
+
+    def faces(nn, h):
+        out = []
+        for d in range(3):
+            ax = [(np.arange(-g, nn[a] + g + (a == d)) + (0.0 if a == d else 0.5)) * h for a in range(3)]
+            Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+            out.append(field(d, X, Y, Z))
+        return out
+
+    Bc = faces(n, 2.0)
+    Bf = [np.zeros_like(b) for b in faces(nf, 1.0)]
+    A.prolong_faces(Bc, g, Bf, g, (0, 0, 0), (0, 0, 0), nf, dx)
+    exact = faces(nf, 1.0)
+    for d in range(3):
+        s = tuple(slice(g, g + nf[a] + (a == d)) for a in (2, 1, 0))
+        assert np.max(np.abs(Bf[d][s] - exact[d][s])) < 1e-12
+
+
+def _mass(blocks, U):
+    return sum(np.sum(H.interior(u[0], b.n, b.ng)) * np.prod(b.dx) for u, b in zip(U, blocks))
+
+
+@pytest.mark.parametrize("correct", [True, False])
+def test_two_level_stage_conserves_mass_and_keeps_the_level_faces_consistent(correct):
+    blocks, records = H.two_level_periodic(seed=5)
+    P = O.Params(gamma_ad=5.0 / 3.0, rho_atm=1e-12, tol=1e-14, recon=1)
+    U = [H.cons_from_prims(b, P) for b in blocks]
+    dt = 0.25 * blocks[1].dx[0]
+    out = A.two_level_stage(blocks, U, records, P, dt, correct=correct)
+    m0, m1 = _mass(blocks, U), _mass(blocks, [o[0] for o in out])
+    g = blocks[0].ng
+    worst = 0.0
+    for (c, f, d, side, o1, o2) in records:
+        pc, pf = (8, 0) if side > 0 else (0, 8)
+        cB = out[c][1][0][g + o2:g + o2 + 4, g + o1:g + o1 + 4, g + pc]
+        fB = out[f][1][0][g:g + 8, g:g + 8, g + pf]
+        fm = 0.25 * ((fB[0::2, 0::2] + fB[0::2, 1::2]) + (fB[1::2, 0::2] + fB[1::2, 1::2]))
+        worst = max(worst, float(np.max(np.abs(cB - fm)) / np.max(np.abs(cB))))
+    print(f"two-level stage, corrections {correct}: mass change {abs(m1 / m0 - 1):.2e}, "
+          f"level-face mismatch {worst:.2e}")
+    for o, b in zip(out, blocks):
+        assert np.all(H.interior(o[3], b.n, b.ng) == 0)
+    if correct:
+        assert abs(m1 / m0 - 1) < 1e-14 and worst < 1e-13
+    else:
+        assert abs(m1 / m0 - 1) > 1e-10 and worst > 1e-9
