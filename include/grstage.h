@@ -231,6 +231,48 @@ int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_s
 int gr_adm_sources(gr_mesh* mesh, const gr_metric* metric, const double* const W[7], const double* const B[3],
                    const gr_params* params, int32_t vc_order, double* const out[10], void* stream);
 
+/* ---- level boundaries of a refined mesh (refinement ratio 2) --------------------------------------
+ * The operators that keep a mesh of two refinement levels consistent (Sec. 3.3, last paragraph): the
+ * restriction and the divergence-preserving prolongation of the face field (and of cell fields), and
+ * the flux and electric-field corrections at refinement boundaries.  A fine block's cell i along an
+ * axis covers half of coarse cell off + floor(i/2); its spacings must be half the coarse block's.
+ *
+ * gr_level_face: fine block `fine` touches the side-`side` (+1 high, -1 low) dir-face of block
+ * `coarse` and covers the coarse face cells o1 .. o1 + n_fine[t1]/2 - 1 along t1 = (dir+1)%3 and
+ * o2 .. o2 + n_fine[t2]/2 - 1 along t2 = (dir+2)%3.  With level faces set, every gr_stage on the mesh
+ * replaces, after computing them, the coarse block's fluxes of the conserved variables on those faces
+ * by the mean of the 4 fine-face fluxes on each, and its corner EMFs on those faces' edges by the mean
+ * of the 2 fine edge EMFs along each; total D is then conserved across the levels and each coarse face
+ * stays the mean of the fine faces on it.  (Conserved to FP64 rounding on the FP64 path; the mixed path
+ * stores the means in its FP32 workspace, so there they hold to FP32 rounding of the flux.)  A coarse
+ * edge shared by two fine patches is written by both with the same value when the fine blocks' shared
+ * edge values agree (same-level ghost copies); records must not chain three levels at one edge.
+ *
+ * gr_level_map: a coarse block, a fine block, the fine block's offset `off` in coarse cells and an
+ * element range lo .. hi-1 (per axis; faces along d include index hi[d]).  Restriction maps: the range
+ * is in coarse cells, each set to the mean of its 8 fine cells (cells) or the mean of the 4 fine faces
+ * on each of its faces (B).  Prolongation maps: the range is in fine cells, each set from the coarse
+ * data: cells by limited linear reconstruction (minmod of the one-sided coarse differences), faces on
+ * a coarse face plane from the coarse value and its limited transverse slopes, faces inside a coarse
+ * cell by the minimal-norm correction, to the mean of the two opposite outer fine faces, that makes the
+ * 8 fine cells divergence-free.  Every coarse cell a prolongation reads must have its 6 face
+ * neighbours inside the coarse block's ghost-padded array (checked).
+ *
+ * gr_mesh_set_levels copies the tables to the device (checked: indices, spacings, ranges); n = 0 clears.
+ * gr_restrict / gr_prolong apply the stored maps to nvar (<= 8) cell pools and, if B is not NULL, to the
+ * three face pools; maps run concurrently, so their destinations must not overlap.  Errors:
+ * GR_EINVAL (bad table, NULL pool), GR_ENOMEM, GR_ECUDA. */
+typedef struct {
+  int32_t coarse, fine, dir, side, o1, o2;
+} gr_level_face;
+typedef struct {
+  int32_t coarse, fine, off[3], lo[3], hi[3];
+} gr_level_map;
+int gr_mesh_set_levels(gr_mesh* mesh, const gr_level_face* faces, int32_t nfaces, const gr_level_map* restrict_maps,
+                       int32_t nrestrict, const gr_level_map* prolong_maps, int32_t nprolong);
+int gr_restrict(gr_mesh* mesh, double* const cells[8], int32_t nvar, double* const B[3], void* stream);
+int gr_prolong(gr_mesh* mesh, double* const cells[8], int32_t nvar, double* const B[3], void* stream);
+
 /* ---- RK driver: a full time step of a set of same-level blocks -----------------------------------------
  * (the third-order Runge-Kutta integrator used for every test of Sec. 4-8, stated at the start of
  * Sec. 4; the global time step of Sec. 3.1)

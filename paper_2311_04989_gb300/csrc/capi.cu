@@ -129,6 +129,15 @@ struct gr_mesh {
   std::vector<void*> allocs;
   int64_t ws_bytes = 0;
   int min_ng = 0;
+  // level boundaries (gr_mesh_set_levels): level faces for the stage, restriction / prolongation maps
+  // with their work lists (cell items first: ncw_* of them)
+  LevelFace* d_lvl = nullptr;
+  LevelMap* d_rmap = nullptr;
+  LevelMap* d_pmap = nullptr;
+  Work* d_rwork = nullptr;
+  Work* d_pwork = nullptr;
+  int nrwork = 0, npwork = 0, ncw_r = 0, ncw_p = 0;
+  std::vector<void*> lvl_allocs;
   // matter-source outputs (gr_adm_sources): cell-layout workspace (FP64-sized) and work lists per
   // (precision, order 2 / 4), made on first use
   void* adm_cv[10] = {};
@@ -209,10 +218,22 @@ static void prof_release(gr_mesh* m) {
   m->prof_capacity = m->prof_used = 0;
 }
 
+static void levels_free(gr_mesh* m) {
+  for (void* p : m->lvl_allocs) cudaFree(p);
+  m->lvl_allocs.clear();
+  m->d_lvl = nullptr;
+  m->d_rmap = m->d_pmap = nullptr;
+  m->d_rwork = m->d_pwork = nullptr;
+  m->nrwork = m->npwork = m->ncw_r = m->ncw_p = 0;
+  m->ws.lvl = nullptr;
+  m->ws.nlvl = 0;
+}
+
 static void mesh_free(gr_mesh* m) {
   if (!m) return;
   DeviceGuard g(m->ctx ? m->ctx->device : 0);
   prof_release(m);
+  levels_free(m);
   for (void* p : m->allocs) cudaFree(p);
   delete m;
 }
@@ -757,6 +778,136 @@ int gr_adm_sources(gr_mesh* mesh, const gr_metric* metric, const double* const W
                              mesh->adm_vw[pr][o], mesh->adm_nvw[pr][o], mesh->adm_smem[pr][o], mv, W, B,
                              kparams(params, 0.0), vc_order, mesh->adm_cv, out, (cudaStream_t)stream);
   return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_adm_sources launch");
+}
+
+// ---- level boundaries ---------------------------------------------------------------------------
+static bool half_spacing(const DBlock& c, const DBlock& f) {
+  for (int a = 0; a < 3; ++a)
+    if (!(std::fabs(2.0 * f.dx[a] - c.dx[a]) <= 1e-12 * c.dx[a])) return false;
+  return true;
+}
+static int floor2h(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
+
+static int check_map(const gr_mesh* m, const gr_level_map& mp, bool prolong) {
+  if (mp.coarse < 0 || mp.coarse >= m->nblocks || mp.fine < 0 || mp.fine >= m->nblocks || mp.coarse == mp.fine)
+    return fail(GR_EINVAL, "gr_mesh_set_levels: map block index out of range");
+  const DBlock& c = m->h_blocks[mp.coarse];
+  const DBlock& f = m->h_blocks[mp.fine];
+  if (!half_spacing(c, f)) return fail(GR_EINVAL, "gr_mesh_set_levels: fine spacing must be half the coarse one");
+  for (int a = 0; a < 3; ++a) {
+    if (mp.hi[a] <= mp.lo[a]) return fail(GR_EINVAL, "gr_mesh_set_levels: empty map range");
+    if (!prolong) {
+      // coarse cells lo..hi-1 (faces to hi) and the fine cells 2(p - off) + {0, 1}
+      if (mp.lo[a] < -c.g || mp.hi[a] > c.n[a] + c.g)
+        return fail(GR_EINVAL, "gr_mesh_set_levels: restriction range outside the coarse block");
+      if (2 * (mp.lo[a] - mp.off[a]) < -f.g || 2 * (mp.hi[a] - mp.off[a]) > f.n[a] + f.g)
+        return fail(GR_EINVAL, "gr_mesh_set_levels: restriction reads outside the fine block");
+    } else {
+      if (mp.lo[a] < -f.g || mp.hi[a] > f.n[a] + f.g)
+        return fail(GR_EINVAL, "gr_mesh_set_levels: prolongation range outside the fine block");
+      const int c0 = floor2h(mp.lo[a]) + mp.off[a] - 1, c1 = floor2h(mp.hi[a] - 1) + mp.off[a] + 1;
+      if (c0 < -c.g || c1 > c.n[a] + c.g - 1)
+        return fail(GR_EINVAL, "gr_mesh_set_levels: prolongation reads outside the coarse block");
+    }
+  }
+  return GR_OK;
+}
+
+int gr_mesh_set_levels(gr_mesh* m, const gr_level_face* faces, int32_t nfaces, const gr_level_map* rmaps,
+                       int32_t nr, const gr_level_map* pmaps, int32_t np) {
+  if (!m || nfaces < 0 || nr < 0 || np < 0 || (nfaces && !faces) || (nr && !rmaps) || (np && !pmaps))
+    return fail(GR_EINVAL, "gr_mesh_set_levels: bad argument");
+  for (int i = 0; i < nfaces; ++i) {
+    const gr_level_face& r = faces[i];
+    if (r.coarse < 0 || r.coarse >= m->nblocks || r.fine < 0 || r.fine >= m->nblocks || r.coarse == r.fine ||
+        r.dir < 0 || r.dir > 2 || (r.side != 1 && r.side != -1))
+      return fail(GR_EINVAL, "gr_mesh_set_levels: bad level face");
+    const DBlock& c = m->h_blocks[r.coarse];
+    const DBlock& f = m->h_blocks[r.fine];
+    if (!half_spacing(c, f)) return fail(GR_EINVAL, "gr_mesh_set_levels: fine spacing must be half the coarse one");
+    const int t1 = (r.dir + 1) % 3, t2 = (r.dir + 2) % 3;
+    if (f.n[t1] % 2 || f.n[t2] % 2 || r.o1 < 0 || r.o2 < 0 || r.o1 + f.n[t1] / 2 > c.n[t1] ||
+        r.o2 + f.n[t2] / 2 > c.n[t2])
+      return fail(GR_EINVAL, "gr_mesh_set_levels: level face patch outside the coarse face");
+  }
+  for (int i = 0; i < nr; ++i)
+    if (int e = check_map(m, rmaps[i], false)) return e;
+  for (int i = 0; i < np; ++i)
+    if (int e = check_map(m, pmaps[i], true)) return e;
+  // work lists: cell items first, then the d-face items, per map
+  auto build = [](const gr_level_map* maps, int n, std::vector<Work>& w) {
+    int ncell = 0;
+    for (int kind = 0; kind < 4; ++kind)
+      for (int i = 0; i < n; ++i) {
+        long long cnt = 1;
+        for (int a = 0; a < 3; ++a) cnt *= maps[i].hi[a] - maps[i].lo[a] + (a == kind - 1);
+        for (long long s0 = 0; s0 < cnt; s0 += kTile) w.push_back(Work{i, kind, (int)s0, 0});
+        if (kind == 0) ncell = (int)w.size();
+      }
+    return ncell;
+  };
+  std::vector<Work> rw, pw;
+  const int ncr = build(rmaps, nr, rw), ncp = build(pmaps, np, pw);
+  DeviceGuard g(m->ctx->device);
+  levels_free(m);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](const void* src, size_t bytes, void** dst) {
+    if (e != cudaSuccess || !bytes) return;
+    e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return;
+    m->lvl_allocs.push_back(*dst);
+    e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  static_assert(sizeof(LevelFace) == sizeof(gr_level_face) && sizeof(LevelMap) == sizeof(gr_level_map),
+                "level record layouts");
+  up(faces, sizeof(LevelFace) * nfaces, (void**)&m->d_lvl);
+  up(rmaps, sizeof(LevelMap) * nr, (void**)&m->d_rmap);
+  up(pmaps, sizeof(LevelMap) * np, (void**)&m->d_pmap);
+  up(rw.data(), sizeof(Work) * rw.size(), (void**)&m->d_rwork);
+  up(pw.data(), sizeof(Work) * pw.size(), (void**)&m->d_pwork);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    levels_free(m);
+    return fail(e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA,
+                std::string("gr_mesh_set_levels: ") + cudaGetErrorString(e));
+  }
+  m->ws.lvl = m->d_lvl;
+  m->ws.nlvl = nfaces;
+  m->nrwork = (int)rw.size();
+  m->npwork = (int)pw.size();
+  m->ncw_r = ncr;
+  m->ncw_p = ncp;
+  return GR_OK;
+}
+
+static int amr_apply(gr_mesh* m, bool prolong, double* const cells[8], int32_t nvar, double* const B[3],
+                     void* stream) {
+  const char* what = prolong ? "gr_prolong" : "gr_restrict";
+  if (!m || nvar < 0 || nvar > 8 || (nvar && !cells)) return fail(GR_EINVAL, std::string(what) + ": bad argument");
+  for (int v = 0; v < nvar; ++v)
+    if (!cells[v]) return fail(GR_EINVAL, std::string(what) + ": NULL cell pool");
+  if (B)
+    for (int d = 0; d < 3; ++d)
+      if (!B[d]) return fail(GR_EINVAL, std::string(what) + ": NULL face pool");
+  DeviceGuard g(m->ctx->device);
+  const Work* w = prolong ? m->d_pwork : m->d_rwork;
+  const int nall = prolong ? m->npwork : m->nrwork, ncell = prolong ? m->ncw_p : m->ncw_r;
+  double* cv[8] = {};
+  for (int v = 0; v < nvar; ++v) cv[v] = cells[v];
+  // without face pools only the cell items run (they come first); without cell pools only the faces
+  const Work* w0 = nvar ? w : w + ncell;
+  const int n = (nvar ? (B ? nall : ncell) : (B ? nall - ncell : 0));
+  const cudaError_t e = launch_amr(prolong, m->d_blocks, prolong ? m->d_pmap : m->d_rmap, w0, n, cv, nvar, B,
+                                   (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, what);
+}
+
+int gr_restrict(gr_mesh* m, double* const cells[8], int32_t nvar, double* const B[3], void* stream) {
+  return amr_apply(m, false, cells, nvar, B, stream);
+}
+
+int gr_prolong(gr_mesh* m, double* const cells[8], int32_t nvar, double* const B[3], void* stream) {
+  return amr_apply(m, true, cells, nvar, B, stream);
 }
 
 int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], const double* const B[3],

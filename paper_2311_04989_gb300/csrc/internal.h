@@ -76,6 +76,14 @@ struct Shadow {
   long long ncell, nface[3], nvert;   // pool extents in elements
 };
 
+// Level-boundary records (same layouts as gr_level_face / gr_level_map)
+struct LevelFace {
+  int coarse, fine, dir, side, o1, o2;
+};
+struct LevelMap {
+  int coarse, fine, off[3], lo[3], hi[3];
+};
+
 // Workspace pools (owned by the mesh)
 struct Workspace {
   void* bcc[3];        // undensitised cell-centred field calB^i (cells), FP64 or FP32
@@ -85,6 +93,8 @@ struct Workspace {
   void* edge[3];       // corner electric field E_m (vertex-indexed), FP64 or FP32
   long long fstride[3];
   long long estride;
+  const LevelFace* lvl;   // level-boundary faces whose coarse fluxes / EMFs the stage corrects
+  int nlvl;
   int* njobs;          // con2prim job list: cells (block, interior index) that need the root find
   int2* jobs;
 };
@@ -148,6 +158,10 @@ cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
 // RK driver (driver.cu): ghost exchange between same-level blocks, CFL dt on the device
+cudaError_t launch_level_fix(int precision, const DBlock* blocks, const LevelFace* lf, int nlf, const Workspace& ws,
+                             int table, cudaStream_t st);
+cudaError_t launch_amr(bool prolong, const DBlock* blocks, const LevelMap* maps, const Work* work, int nwork,
+                       double* const cells[8], int nvar, double* const B[3], cudaStream_t st);
 constexpr int kAdmThreads = 256;
 constexpr size_t kAdmSmemTarget = 96 * 1024;    // shared memory a k_adm_verts slab aims for
 constexpr size_t kAdmSmemMax = 200 * 1024;      // ... and may not exceed (one vertex plane)

@@ -633,6 +633,11 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
   if (ev) cudaEventRecord(ev[3], st);
   const KLaunch& e = kl[SK_EDGES];
   if (e.nwork) k_edges<R><<<stage_grid(k_edges<R>, e, 0), e.threads, 0, st>>>(blocks, e.work, e.nwork, ws, kp);
+  if (ws.nlvl) {   // refined mesh: coarse fluxes and EMFs on level boundaries from the fine ones
+    const cudaError_t el = launch_level_fix(sizeof(R) == sizeof(float) ? GR_PREC_MIXED : GR_PREC_FP64, blocks, ws.lvl,
+                                            ws.nlvl, ws, EOS == GR_EOS_TABLE, st);
+    if (el != cudaSuccess) return el;
+  }
   if (ev) cudaEventRecord(ev[4], st);
   const KLaunch& c = kl[SK_CT];
   if (c.nwork) k_ct<R><<<stage_grid(k_ct<R>, c, 0), c.threads, 0, st>>>(blocks, c.work, c.nwork, s, ws, kp);

@@ -36,7 +36,7 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
            "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
-           "gr_adm_sources"]
+           "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong"]
 GR_ABI_VERSION = 2
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
@@ -68,6 +68,16 @@ class gr_state(C.Structure):
 
 class gr_shape(C.Structure):
     _fields_ = [("tile", C.c_int32), ("order", C.c_int32), ("persistent", C.c_int32)]
+
+
+class gr_level_face(C.Structure):
+    _fields_ = [("coarse", C.c_int32), ("fine", C.c_int32), ("dir", C.c_int32), ("side", C.c_int32),
+                ("o1", C.c_int32), ("o2", C.c_int32)]
+
+
+class gr_level_map(C.Structure):
+    _fields_ = [("coarse", C.c_int32), ("fine", C.c_int32), ("off", C.c_int32 * 3), ("lo", C.c_int32 * 3),
+                ("hi", C.c_int32 * 3)]
 
 
 class gr_eos_table(C.Structure):
@@ -151,6 +161,10 @@ def load(path: str = LIB_PATH):
     L.gr_driver_dt.argtypes = [vp, C.POINTER(C.c_double)]
     L.gr_driver_dt_device.argtypes = [vp]
     L.gr_driver_dt_device.restype = vp
+    L.gr_mesh_set_levels.argtypes = [vp, C.POINTER(gr_level_face), i32, C.POINTER(gr_level_map), i32,
+                                     C.POINTER(gr_level_map), i32]
+    L.gr_restrict.argtypes = [vp, C.c_void_p * 8, i32, vp, vp]
+    L.gr_prolong.argtypes = [vp, C.c_void_p * 8, i32, vp, vp]
     L.gr_adm_sources.argtypes = [vp, C.POINTER(gr_metric), C.c_void_p * 7, C.c_void_p * 3, C.POINTER(gr_params), i32,
                                  C.c_void_p * 10, vp]
     for f in EXPORTS:
@@ -320,6 +334,38 @@ def gr_adm_sources(mesh, metric: gr_metric, W, B, params: gr_params, vc_order, o
     """rho_ADM, S_i, S_ij at the owned vertices into the 10 vertex pools ``out`` (see include/grstage.h)."""
     _check(load().gr_adm_sources(mesh, C.byref(metric), _ptrs(7, W), _ptrs(3, B), C.byref(params), int(vc_order),
                                  _ptrs(10, out), _stream(stream)), "gr_adm_sources")
+
+
+def _level_array(cls, items):
+    items = list(items)
+    arr = (cls * max(1, len(items)))()
+    for k, it in enumerate(items):
+        arr[k] = it if isinstance(it, cls) else cls(*[(C.c_int32 * 3)(*x) if isinstance(x, (tuple, list)) else x
+                                                     for x in it])
+    return arr, len(items)
+
+
+def gr_mesh_set_levels(mesh, faces=(), restrict_maps=(), prolong_maps=()):
+    """faces: (coarse, fine, dir, side, o1, o2) tuples; maps: (coarse, fine, off, lo, hi) with 3-tuples."""
+    fa, nf = _level_array(gr_level_face, faces)
+    ra, nr = _level_array(gr_level_map, restrict_maps)
+    pa, npr = _level_array(gr_level_map, prolong_maps)
+    _check(load().gr_mesh_set_levels(mesh, fa, nf, ra, nr, pa, npr), "gr_mesh_set_levels")
+
+
+def _amr(fn, name, mesh, cells, B, stream):
+    cells = list(cells)
+    bp = _ptrs(3, B) if B is not None else None
+    _check(fn(mesh, _ptrs(8, cells), len(cells), C.cast(bp, C.c_void_p) if bp is not None else None,
+              _stream(stream)), name)
+
+
+def gr_restrict(mesh, cells, B=None, stream=None):
+    _amr(load().gr_restrict, "gr_restrict", mesh, cells, B, stream)
+
+
+def gr_prolong(mesh, cells, B=None, stream=None):
+    _amr(load().gr_prolong, "gr_prolong", mesh, cells, B, stream)
 
 
 def gr_driver_create(mesh, nbr):

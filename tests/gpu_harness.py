@@ -108,7 +108,8 @@ class Pools:
 
 
 def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None, B0=None, order=None,
-              k_zero=True, return_pools=False, c2p_guess=G.GR_GUESS_NONE, shapes=None, autotune=False):
+              k_zero=True, return_pools=False, c2p_guess=G.GR_GUESS_NONE, shapes=None, autotune=False,
+              level_faces=None):
     """Run gr_stage on a batch; returns a list of (Uo, Bo, Wo, status) per block (numpy)."""
     import torch
     order = order or P.interp_order
@@ -131,6 +132,8 @@ def gpu_stage(blocks, P: O.Params, dt, precision=G.GR_PREC_FP64, U=None, U0=None
         gp = gr_params_from(P, precision, c2p_guess)
         if shapes is not None:
             G.gr_mesh_set_shapes(mesh, precision, gp.eos, shapes)
+        if level_faces:
+            G.gr_mesh_set_levels(mesh, faces=level_faces)
         if autotune:
             G.gr_autotune(mesh, metric, state, dt, gp, 1, torch.cuda.current_stream())
         G.gr_stage(mesh, metric, state, dt, gp, torch.cuda.current_stream())
@@ -159,7 +162,7 @@ def oracle_stage(blocks, P: O.Params, dt, U=None, U0=None, B0=None):
 REL_FLOOR = {"W0": 0.0, "W4": 0.0}   # rho, p: plain relative
 
 
-def compare(gpu, ref, blocks=None, skip=()):
+def compare(gpu, ref, blocks=None, skip=(), floors=None):
     """Max relative error per variable over interior cells / faces of all blocks, and the number of
     status mismatches.  Denominators:
       D, rho, p           |ref| (plain relative)
@@ -168,7 +171,8 @@ def compare(gpu, ref, blocks=None, skip=()):
                           (e.g. tau ~ p/(Gamma-1) ~ 1e-30 in the atmosphere is a difference of
                           terms ~ rho ~ 1e-16; S' in a star in equilibrium is a small residual)
       u~^i, B faces       max(|ref|, 1e-3 max|ref| of the block) (they pass through zero)
-      D Y_e, Y_e, T       plain relative (table).  Variables named in skip are left out."""
+      D Y_e, Y_e, T       plain relative (table).  Variables named in skip are left out; floors
+                          overrides the 1e-3 of a variable (name -> fraction of the block maximum)."""
     errs = {}
     nmis = 0
     for b, (g, r) in enumerate(zip(gpu, ref)):
@@ -188,7 +192,8 @@ def compare(gpu, ref, blocks=None, skip=()):
                     den = np.maximum(np.abs(ri[v]), np.abs(ri[0]) + np.abs(ri[4]))
                 else:
                     scale = np.max(np.abs(ri[v]))
-                    den = np.maximum(np.abs(ri[v]), max(REL_FLOOR.get(name, 1e-3) * scale, 1e-300))
+                    fl = (floors or {}).get(name, REL_FLOOR.get(name, 1e-3))
+                    den = np.maximum(np.abs(ri[v]), max(fl * scale, 1e-300))
                 e = float(np.max(np.abs(gi[v] - ri[v]) / den))
                 errs[name] = max(errs.get(name, 0.0), e)
         for d, (gf, rf) in enumerate(zip(H.interior_faces(g["B"], n, ng), H.interior_faces(r["B"], n, ng))):

@@ -55,7 +55,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     import ctypes as C
     import subprocess
     structs = {"gr_block": G.gr_block, "gr_metric": G.gr_metric, "gr_state": G.gr_state,
-               "gr_params": G.gr_params, "gr_eos_table": G.gr_eos_table, "gr_shape": G.gr_shape}
+               "gr_params": G.gr_params, "gr_eos_table": G.gr_eos_table, "gr_shape": G.gr_shape,
+               "gr_level_face": G.gr_level_face, "gr_level_map": G.gr_level_map}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "grstage.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
