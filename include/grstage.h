@@ -256,7 +256,13 @@ int gr_adm_sources(gr_mesh* mesh, const gr_metric* metric, const double* const W
  * a coarse face plane from the coarse value and its limited transverse slopes, faces inside a coarse
  * cell by the minimal-norm correction, to the mean of the two opposite outer fine faces, that makes the
  * 8 fine cells divergence-free.  Every coarse cell a prolongation reads must have its 6 face
- * neighbours inside the coarse block's ghost-padded array (checked).
+ * neighbours inside the coarse block's ghost-padded array (checked).  A map whose range lies wholly
+ * outside its destination block along d (a ghost slab) does not write that block's own d-face planes
+ * 0 and n (they belong to the block and to the level-boundary corrections).
+ *
+ * With restriction or prolongation maps set, the RK driver fills ghosts in three passes before every
+ * stage: same-level copies (its neighbour table; a side toward another level is marked outflow, -1),
+ * then the restriction maps, then the prolongation maps, on the primitive pools and B.
  *
  * gr_mesh_set_levels copies the tables to the device (checked: indices, spacings, ranges); n = 0 clears.
  * gr_restrict / gr_prolong apply the stored maps to nvar (<= 8) cell pools and, if B is not NULL, to the

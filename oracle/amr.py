@@ -57,9 +57,14 @@ def restrict_cells(fine, gf, coarse, gc, off, lo, hi):
                 coarse[..., k + gc, j + gc, i + gc] = 0.125 * s
 
 
-def restrict_faces(fineB, gf, coarseB, gc, off, lo, hi):
+def _ghost_plane(lo, hi, n, d, p):
+    """A range wholly outside the destination block along d leaves the block's own d-face planes."""
+    return n is not None and (hi[d] <= 0 or lo[d] >= n[d]) and p[d] in (0, n[d])
+
+
+def restrict_faces(fineB, gf, coarseB, gc, off, lo, hi, nc=None):
     """Coarse d-faces with index lo..hi-1 (hi along d inclusive of the last face: hi[d] + 1) = mean of
-    the 4 fine d-faces on each."""
+    the 4 fine d-faces on each.  nc: the coarse block size (ghost-slab rule of _ghost_plane)."""
     for d in range(3):
         t1, t2 = (d + 1) % 3, (d + 2) % 3
         hid = list(hi)
@@ -68,6 +73,8 @@ def restrict_faces(fineB, gf, coarseB, gc, off, lo, hi):
             for j in range(lo[1], hid[1]):
                 for i in range(lo[0], hid[0]):
                     c = (i, j, k)
+                    if _ghost_plane(lo, hi, nc, d, c):
+                        continue
                     f0 = [2 * (c[a] - off[a]) for a in range(3)]
                     s = 0.0
                     for u in (0, 1):
@@ -168,11 +175,12 @@ def prolong_cell_faces(coarseB, gc, c, dxf):
     return {k: v / area[k[0]] for k, v in phi.items()}
 
 
-def prolong_faces(coarseB, gc, fineB, gf, off, lo, hi, dxf):
+def prolong_faces(coarseB, gc, fineB, gf, off, lo, hi, dxf, nf=None):
     """Fine d-faces of fine cells lo..hi-1 (fine indices; the high face of the last cell along d
     included) from the divergence-preserving prolongation of the coarse faces.  A fine face on a
     coarse face plane (even index along d) depends on that coarse plane only; a fine face inside a
-    coarse cell (odd index) on all six faces of the cell."""
+    coarse cell (odd index) on all six faces of the cell.  nf: the fine block size (ghost-slab rule
+    of _ghost_plane)."""
     cache = {}
     for d in range(3):
         t1, t2 = (d + 1) % 3, (d + 2) % 3
@@ -182,6 +190,8 @@ def prolong_faces(coarseB, gc, fineB, gf, off, lo, hi, dxf):
             for j in range(lo[1], hid[1]):
                 for i in range(lo[0], hid[0]):
                     f = (i, j, k)
+                    if _ghost_plane(lo, hi, nf, d, f):
+                        continue
                     if f[d] % 2 == 0:
                         cf = [0, 0, 0]
                         cf[d] = f[d] // 2 + off[d]
@@ -244,13 +254,15 @@ def correct_level_face(Fc, Ec, nc, gc, Ff, Ef, nf, gf, d, side, o1, o2):
             Ec[t2][cidx(pc, J, K, gc)] = 0.5 * (fa + fb)
 
 
-def two_level_stage(blocks, U, records, P: O.Params, dt, correct=True):
+def two_level_stage(blocks, U, records, P: O.Params, dt, correct=True, U0=None, B0=None):
     """One stage of every block of a two-level mesh with the level-boundary corrections.
-    records: (coarse, fine, d, side, o1, o2) per fine block touching a coarse block's face.
-    Returns [(U', B', W', status)] per block."""
+    records: (coarse, fine, d, side, o1, o2) per fine block touching a coarse block's face; U0, B0:
+    the RK registers (default: the stage input).  Returns [(U', B', W', status)] per block."""
+    U0 = U0 if U0 is not None else U
+    B0 = B0 if B0 is not None else [bi.B for bi in blocks]
     F, E = [], []
     for b, bi in enumerate(blocks):
-        f, e = O.stage_fluxes(O.Block(bi.n, bi.ng, bi.dx, bi.metric, bi.W, bi.B), U[b], U[b], bi.B, dt, P)
+        f, e = O.stage_fluxes(O.Block(bi.n, bi.ng, bi.dx, bi.metric, bi.W, bi.B), U[b], U0[b], B0[b], dt, P)
         F.append(f)
         E.append(e)
     if correct:
@@ -259,6 +271,45 @@ def two_level_stage(blocks, U, records, P: O.Params, dt, correct=True):
                                o1, o2)
     out = []
     for b, bi in enumerate(blocks):
-        out.append(O.stage_block_with(O.Block(bi.n, bi.ng, bi.dx, bi.metric, bi.W, bi.B), U[b], U[b], bi.B, dt, P,
+        out.append(O.stage_block_with(O.Block(bi.n, bi.ng, bi.dx, bi.metric, bi.W, bi.B), U[b], U0[b], B0[b], dt, P,
                                       F[b], E[b]))
     return out
+
+
+def fill_two_level(blocks, nbr, restrict_maps, prolong_maps):
+    """Ghosts of a two-level mesh: same-level copies (neighbour table; sides toward the other level
+    are -1), then the restriction maps, then the prolongation maps (primitives and B).
+    maps: (coarse, fine, off, lo, hi)."""
+    from oracle import driver as DR
+    n, g = blocks[0].n, blocks[0].ng
+    DR.ghost_fill([b.W for b in blocks], [b.B for b in blocks], nbr, n, g)
+    for (c, f, off, lo, hi) in restrict_maps:
+        cb, fb = blocks[c], blocks[f]
+        restrict_cells(fb.W, fb.ng, cb.W, cb.ng, off, lo, hi)
+        restrict_faces(fb.B, fb.ng, cb.B, cb.ng, off, lo, hi, nc=cb.n)
+    for (c, f, off, lo, hi) in prolong_maps:
+        cb, fb = blocks[c], blocks[f]
+        prolong_cells(cb.W, cb.ng, fb.W, fb.ng, off, lo, hi)
+        prolong_faces(cb.B, cb.ng, fb.B, fb.ng, off, lo, hi, fb.dx, nf=fb.n)
+
+
+def two_level_rk_step(blocks, U, nbr, restrict_maps, prolong_maps, records, P: O.Params, cfl, order=3):
+    """One RK step of a two-level mesh (ghost fill of fill_two_level before every stage, the grid time
+    step of the finest spacing, SSP-RK stages with the level-boundary corrections), in place of the
+    blocks' W, B and U.  Returns dt."""
+    from oracle import driver as DR
+    fill_two_level(blocks, nbr, restrict_maps, prolong_maps)
+    dt = DR.grid_dt(blocks, cfl)
+    U0 = [u.copy() for u in U]
+    B0 = [[f.copy() for f in b.B] for b in blocks]
+    for s_i, (g0, g1, beta) in enumerate(DR.RK_STAGES[order]):
+        if s_i > 0:
+            fill_two_level(blocks, nbr, restrict_maps, prolong_maps)
+        Pst = O.Params(**{**P.__dict__, "rk_g0": g0, "rk_g1": g1, "rk_beta": beta})
+        out = two_level_stage(blocks, U, records, Pst, dt, U0=U0, B0=B0)
+        for b, (Uo, Bo, Wo, st) in enumerate(out):
+            U[b][...] = Uo
+            blocks[b].W[...] = Wo
+            for d in range(3):
+                blocks[b].B[d][...] = Bo[d]
+    return dt

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(kTile) k_restrict(const DBlock* __restrict__ b
       a.cells[v][cc] = 0.125 * s;
     }
   } else {
+    // a range wholly outside the block along D (a ghost slab) leaves the block's own face planes 0, n
+    if ((mp.hi[D] <= 0 || mp.lo[D] >= c.n[D]) && (p[D] == 0 || p[D] == c.n[D])) return;
     const int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
     double s = 0.0;
 #pragma unroll
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(kTile) k_prolong(const DBlock* __restrict__ bl
     }
     return;
   }
+  if ((mp.hi[D] <= 0 || mp.lo[D] >= f.n[D]) && (p[D] == 0 || p[D] == f.n[D])) return;   // as in k_restrict
   const int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   double val;
   if ((p[D] & 1) == 0) {   // on a coarse face plane

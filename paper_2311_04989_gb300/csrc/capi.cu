@@ -1063,6 +1063,19 @@ int gr_cfl_dt(gr_driver* d, const gr_metric* metric, const double* const W[7], c
   return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_cfl_dt");
 }
 
+// ghosts of the driver's state: same-level copies, then (on a refined mesh) restriction into coarse
+// ghosts and prolongation into fine ghosts
+static int driver_fill(gr_driver* d, double* const W[7], int nw, double* const B[3], void* stream) {
+  int r = gr_ghost_fill(d, W, nw, B, stream);
+  if (r) return r;
+  gr_mesh* m = d->mesh;
+  double* cells[8] = {};
+  for (int v = 0; v < nw; ++v) cells[v] = W[v];
+  if (m->nrwork && (r = amr_apply(m, false, cells, nw, B, stream))) return r;
+  if (m->npwork && (r = amr_apply(m, true, cells, nw, B, stream))) return r;
+  return GR_OK;
+}
+
 static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const U[6], double* const W[7],
                             double* const B[3], uint8_t* status, const gr_params* params, double cfl,
                             int32_t dt_mode, int32_t rk_order, void* stream) {
@@ -1086,7 +1099,7 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
   DeviceGuard g(d->device);
   cudaStream_t st = (cudaStream_t)stream;
   // ghosts of the step's input state, then dt from it
-  if ((r = gr_ghost_fill(d, W, nw, B, stream))) return r;
+  if ((r = driver_fill(d, W, nw, B, stream))) return r;
   if (dt_mode == GR_DT_SIGNAL) {
     if ((r = gr_cfl_dt(d, metric, W, B, params, cfl, nullptr, stream))) return r;
   } else {
@@ -1138,7 +1151,7 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
       for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];
       for (int v = 0; v < nw; ++v) inW[v] = d->W[s % 2][v];
       for (int a = 0; a < 3; ++a) inB[a] = d->B[s % 2][a];
-      if ((r = gr_ghost_fill(d, inW, nw, inB, stream))) return r;
+      if ((r = driver_fill(d, inW, nw, inB, stream))) return r;
     }
   }
   return GR_OK;

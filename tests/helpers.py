@@ -221,3 +221,38 @@ def two_level_periodic(seed=0, g=3, bmag=0.05):
             records.append((0, f, 0, +1, 4 * j, 4 * k))
             records.append((0, f, 0, -1, 4 * j, 4 * k))   # periodic wrap: the fine +x side meets the coarse -x side
     return blocks, records
+
+
+def two_level_periodic_tables():
+    """Ghost-fill tables of two_level_periodic's mesh (coarse block 0, fine blocks 1 + j + 2k):
+    the same-level neighbour table (sides toward the other level -1), the restriction maps that fill
+    the coarse block's x ghosts from the fine layer (periodic images included), the prolongation maps
+    that fill the fine blocks' x ghost slabs from the coarse block, and the level-face records.
+    Period: 12 coarse cells along x (8 coarse + 4 under the fine layer), 8 along y and z."""
+    from paper_2311_04989_gb300.inputs import neighbour_slot
+    fid = lambda j, k: 1 + (j % 2) + 2 * (k % 2)
+    nbr = np.full((5, 27), -1, np.int32)
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            s = neighbour_slot(0, oy, oz)
+            nbr[0, s] = 0
+            for k in (0, 1):
+                for j in (0, 1):
+                    nbr[fid(j, k), s] = fid(j + oy, k + oz)
+    pieces = [((-3, 0), 1, -4), ((0, 4), 0, 0), ((4, 8), 1, 4), ((8, 11), 0, 8)]   # (range, fine index, offset)
+    rmaps = []
+    for (xlo, xhi), offx in (((8, 11), 8), ((-3, 0), -4)):
+        for (ylo, yhi), j, offy in pieces:
+            for (zlo, zhi), k, offz in pieces:
+                rmaps.append((0, fid(j, k), (offx, offy, offz), (xlo, ylo, zlo), (xhi, yhi, zhi)))
+    pmaps = []
+    for k in (0, 1):
+        for j in (0, 1):
+            pmaps.append((0, fid(j, k), (8, 4 * j, 4 * k), (-3, -3, -3), (0, 11, 11)))
+            pmaps.append((0, fid(j, k), (-4, 4 * j, 4 * k), (8, -3, -3), (11, 11, 11)))
+    records = []
+    for k in (0, 1):
+        for j in (0, 1):
+            records.append((0, fid(j, k), 0, +1, 4 * j, 4 * k))
+            records.append((0, fid(j, k), 0, -1, 4 * j, 4 * k))
+    return nbr, rmaps, pmaps, records

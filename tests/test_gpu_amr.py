@@ -172,3 +172,42 @@ def test_level_tables_are_checked():
         G.gr_mesh_set_levels(mesh)            # clears
     finally:
         G.gr_mesh_destroy(mesh)
+
+
+def test_two_level_driver_steps_match_the_oracle_and_keep_div_b():
+    # the RK driver on a refined mesh: cross-level ghost fill (same-level copies, restriction,
+    # prolongation) before every stage and the level corrections inside it; two RK3 steps against the
+    # oracle's two-level RK step, then the invariants on the GPU's own state
+    import copy
+    from tests.helpers import two_level_periodic_tables
+    from tests.test_gpu_driver import Run
+    blocks, _ = H.two_level_periodic(seed=9)
+    nbr, rmaps, pmaps, records = two_level_periodic_tables()
+    P = O.Params(gamma_ad=5.0 / 3.0, rho_atm=1e-12, tol=1e-14, recon=1)
+    ref = copy.deepcopy(blocks)
+    Uref = [H.cons_from_prims(b, P) for b in ref]
+    run = Run(blocks, nbr, P, U=[u.copy() for u in Uref])
+    m0 = _mass(ref, Uref)
+    try:
+        G.gr_mesh_set_levels(run.mesh, faces=_level_faces(records), restrict_maps=rmaps, prolong_maps=pmaps)
+        for _ in range(2):
+            run.step(0.25, G.GR_DT_GRID, 3)
+            got = run.result()
+            dt_ref = A.two_level_rk_step(ref, Uref, nbr, rmaps, pmaps, records, P, 0.25, order=3)
+            assert G.gr_driver_dt(run.drv) == dt_ref
+    finally:
+        run.close()
+    refs = [dict(U=Uref[b], B=ref[b].B, W=ref[b].W, status=np.zeros_like(got[b]["status"])) for b in range(len(ref))]
+    errs = GH.compare(got, refs, blocks=blocks, floors={"W1": 1e-2, "W2": 1e-2, "W3": 1e-2})
+    dm = abs(_mass(blocks, [g["U"] for g in got]) / m0 - 1)
+    divs = []
+    for b, g in zip(blocks, got):
+        div = O.divb(b.n, b.ng, b.dx, g["B"])
+        divs.append(np.max(np.abs(H.interior(div, b.n, b.ng))) * min(b.dx) / max(np.max(np.abs(f)) for f in g["B"]))
+    mis = _face_mismatch(blocks, got, records)
+    print(f"two-level GPU driver, 2 RK3 steps: max err vs oracle "
+          f"{max(v for k, v in errs.items() if k != 'status_mismatch'):.2e}, mass change {dm:.2e}, "
+          f"max div B {max(divs):.2e}, level faces {mis:.2e}")
+    assert errs.pop("status_mismatch") == 0
+    assert max(errs.values()) < 1e-12, errs
+    assert dm < 1e-14 and max(divs) < 1e-14 and mis < 1e-13

@@ -145,3 +145,34 @@ def test_two_level_stage_conserves_mass_and_keeps_the_level_faces_consistent(cor
         assert abs(m1 / m0 - 1) < 1e-14 and worst < 1e-13
     else:
         assert abs(m1 / m0 - 1) > 1e-10 and worst > 1e-9
+
+
+def test_two_level_rk3_evolution_conserves_mass_and_keeps_div_b_at_roundoff():
+    # the paper reports div B at round-off with refinement; here two RK3 steps of a periodic two-level
+    # mesh with the cross-level ghost fill (same-level copies, restriction, prolongation) and the
+    # level-boundary corrections: total D conserved, every block's div B at round-off, level faces
+    # consistent
+    from tests.helpers import two_level_periodic_tables
+    blocks, _ = H.two_level_periodic(seed=8)
+    nbr, rmaps, pmaps, records = two_level_periodic_tables()
+    P = O.Params(gamma_ad=5.0 / 3.0, rho_atm=1e-12, tol=1e-14, recon=1)
+    U = [H.cons_from_prims(b, P) for b in blocks]
+    m0 = _mass(blocks, U)
+    for _ in range(2):
+        A.two_level_rk_step(blocks, U, nbr, rmaps, pmaps, records, P, 0.25, order=3)
+        dm = abs(_mass(blocks, U) / m0 - 1)
+        divs = []
+        for b in blocks:
+            div = O.divb(b.n, b.ng, b.dx, b.B)
+            bmax = max(np.max(np.abs(f)) for f in b.B)
+            divs.append(np.max(np.abs(H.interior(div, b.n, b.ng))) * min(b.dx) / bmax)
+        g = blocks[0].ng
+        worst = 0.0
+        for (c, f, d, side, o1, o2) in records:
+            pc, pf = (8, 0) if side > 0 else (0, 8)
+            cB = blocks[c].B[0][g + o2:g + o2 + 4, g + o1:g + o1 + 4, g + pc]
+            fB = blocks[f].B[0][g:g + 8, g:g + 8, g + pf]
+            fm = 0.25 * ((fB[0::2, 0::2] + fB[0::2, 1::2]) + (fB[1::2, 0::2] + fB[1::2, 1::2]))
+            worst = max(worst, float(np.max(np.abs(cB - fm)) / np.max(np.abs(cB))))
+        print(f"two-level RK3 step: mass change {dm:.2e}, max div B {max(divs):.2e}, level faces {worst:.2e}")
+        assert dm < 1e-14 and max(divs) < 1e-14 and worst < 1e-13
