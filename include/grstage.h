@@ -339,7 +339,7 @@ double gr_eos_h0(const gr_eos* eos);
 int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4],
             void* stream);
 
-/* ---- learned con2prim bracket (spec pattern; the paper has no counterpart) -------------------
+/* ---- learned con2prim bracket (not in the paper: a bracket proposal for the root find of Sec. 3.5) --
  * A 6-64-64-1 tanh network predicts log mu at the master-function root from the features
  * log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2) of the KKC invariants and, with a table,
  * log D~ and Y_e (0 and 0 for the scale-free ideal gas) (the reading of Sec. 3.5's bracketing);

@@ -1,4 +1,4 @@
-// mlp.cuh -- the learned con2prim bracket (spec pattern; the paper has no counterpart).
+// mlp.cuh -- the learned con2prim bracket (not in the paper: a bracket proposal for the root find of Sec. 3.5).
 //
 // A 4-64-64-1 tanh network maps features of the KKC invariants of a cell to the logarithm of the
 // master-function root mu = 1/(hW).  Con2prim starts its bracket search there and accepts a bracket

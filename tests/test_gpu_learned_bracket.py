@@ -1,4 +1,4 @@
-"""Learned con2prim bracket on the GPU (spec pattern; the paper has no counterpart).
+"""Learned con2prim bracket on the GPU (not in the paper: a bracket proposal for the root find of Sec. 3.5).
 
 * the sampler's features and log mu equal the oracle's for the same conserved states
 * the network's forward pass and its backpropagated gradient equal the FP64 oracle's

@@ -1,4 +1,4 @@
-"""Pins of the oracle's learned-bracket pieces (spec pattern; the paper has no counterpart):
+"""Pins of the oracle's learned-bracket pieces (not in the paper: a bracket proposal for the root find of Sec. 3.5):
 backpropagated gradients against central finite differences, and the recorded root equal to the
 definition mu = 1/(h W) of the state the conserved variables came from."""
 import numpy as np
