@@ -109,6 +109,9 @@ TabView<R> tab_view(const gr_eos& t, R* const* d) {
 }
 }  // namespace
 
+struct HostStage;
+static void host_stage_free(HostStage* h);
+
 struct gr_mesh {
   gr_ctx* ctx = nullptr;
   int nblocks = 0;
@@ -129,6 +132,8 @@ struct gr_mesh {
   std::vector<void*> allocs;
   int64_t ws_bytes = 0;
   int min_ng = 0;
+  // gr_host_stage: staging pools, batch sub-meshes, streams (made on first use)
+  struct HostStage* hs = nullptr;
   // level boundaries (gr_mesh_set_levels): level faces for the stage, restriction / prolongation maps
   // with their work lists (cell items first: ncw_* of them)
   LevelFace* d_lvl = nullptr;
@@ -234,6 +239,8 @@ static void mesh_free(gr_mesh* m) {
   DeviceGuard g(m->ctx ? m->ctx->device : 0);
   prof_release(m);
   levels_free(m);
+  host_stage_free(m->hs);
+  m->hs = nullptr;
   for (void* p : m->allocs) cudaFree(p);
   delete m;
 }
@@ -488,6 +495,8 @@ struct gr_graph {
 
 static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                       const gr_params* params, void* stream, bool allow_profile);
+static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
+                         const gr_params* params, MetricView& mv, StateView& s);
 
 int gr_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
              const gr_params* params, void* stream) {
@@ -530,6 +539,254 @@ int gr_graph_destroy(gr_graph* graph) {
   cudaGraphDestroy(graph->graph);
   delete graph;
   return GR_OK;
+}
+
+}  // extern "C"
+
+// ---- one stage on host-resident pools ---------------------------------------------------------
+// The mesh keeps device copies of the pools (its own layout) and one sub-mesh per batch of consecutive
+// blocks; copies in, stages and copies out run on three streams so that one batch's copies overlap
+// another batch's stage.
+struct HostStage {
+  int nbatch = 0;
+  std::vector<gr_mesh*> sub;
+  // per batch: element ranges [lo, hi) in the parent pools; kind 0 cells, 1..3 faces, 4 vertices
+  std::vector<long long> lo[5], hi[5];
+  cudaStream_t st[3] = {};                // copies in, stages, copies out
+  std::vector<cudaEvent_t> ev_in, ev_out;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  double *U[6] = {}, *U0[6] = {}, *W[7] = {}, *Uo[6] = {}, *Wo[7] = {}, *B[3] = {}, *B0[3] = {}, *Bo[3] = {};
+  double* M[16] = {};
+  uint8_t* status = nullptr;
+  std::vector<void*> allocs;
+};
+
+static void host_batches_free(HostStage* h) {
+  for (gr_mesh* s : h->sub) mesh_free(s);
+  h->sub.clear();
+  for (cudaEvent_t e : h->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
+  h->ev_in.clear();
+  h->ev_out.clear();
+  for (int t = 0; t < 5; ++t) { h->lo[t].clear(); h->hi[t].clear(); }
+  h->nbatch = 0;
+}
+
+static void host_stage_free(HostStage* h) {
+  if (!h) return;
+  host_batches_free(h);
+  for (int i = 0; i < 3; ++i)
+    if (h->st[i]) cudaStreamDestroy(h->st[i]);
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->ev_end) cudaEventDestroy(h->ev_end);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+// Batches of consecutive blocks with about equal cell counts.  Each batch is a mesh of its own whose
+// block offsets are rebased to the batch's first element, so that it runs on the parent-layout staging
+// pools advanced by those first offsets (its workspace and FP32 shadows cover the batch only).
+static int host_stage_setup(gr_mesh* m, int nbatch) {
+  if (m->hs && m->hs->nbatch == nbatch) return GR_OK;
+  // batches are ranges of the pools: blocks must be laid out in increasing order without overlap
+  for (int b = 0; b + 1 < m->nblocks; ++b) {
+    const DBlock& x = m->h_blocks[b];
+    const DBlock& y = m->h_blocks[b + 1];
+    bool ok = x.cell + (long long)x.N[0] * x.N[1] * x.N[2] <= y.cell &&
+              x.vert + (long long)(x.N[0] + 1) * (x.N[1] + 1) * (x.N[2] + 1) <= y.vert;
+    for (int a = 0; a < 3; ++a)
+      ok = ok && x.face[a] + (long long)(x.N[0] + (a == 0)) * (x.N[1] + (a == 1)) * (x.N[2] + (a == 2)) <= y.face[a];
+    if (!ok) return fail(GR_EUNSUPPORTED, "gr_host_stage: pools must hold the blocks in increasing order");
+  }
+  if (m->hs) {
+    host_batches_free(m->hs);
+  } else {
+    m->hs = new HostStage();
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&m->hs->st[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hs->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hs->ev_end, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      host_stage_free(m->hs);
+      m->hs = nullptr;
+      return cuda_fail(e, "gr_host_stage setup");
+    }
+  }
+  HostStage* h = m->hs;
+  long long total = 0;
+  for (const DBlock& b : m->h_blocks) total += (long long)b.N[0] * b.N[1] * b.N[2];
+  std::vector<int> first(1, 0);
+  long long acc = 0;
+  for (int b = 0; b < m->nblocks; ++b) {
+    acc += (long long)m->h_blocks[b].N[0] * m->h_blocks[b].N[1] * m->h_blocks[b].N[2];
+    const int k = (int)first.size();
+    if (k < nbatch && acc * nbatch >= total * k && b + 1 < m->nblocks) first.push_back(b + 1);
+  }
+  first.push_back(m->nblocks);
+  const int nb = (int)first.size() - 1;
+  const long long ext[5] = {m->sh.ncell, m->sh.nface[0], m->sh.nface[1], m->sh.nface[2], m->sh.nvert};
+  for (int k = 0; k < nb; ++k) {
+    const DBlock& a = m->h_blocks[first[k]];
+    const bool last = first[k + 1] >= m->nblocks;
+    const DBlock* z = last ? nullptr : &m->h_blocks[first[k + 1]];
+    const long long l[5] = {a.cell, a.face[0], a.face[1], a.face[2], a.vert};
+    const long long u[5] = {last ? ext[0] : z->cell, last ? ext[1] : z->face[0], last ? ext[2] : z->face[1],
+                            last ? ext[3] : z->face[2], last ? ext[4] : z->vert};
+    for (int t = 0; t < 5; ++t) { h->lo[t].push_back(l[t]); h->hi[t].push_back(u[t]); }
+    std::vector<gr_block> blk;
+    for (int b = first[k]; b < first[k + 1]; ++b) {
+      const DBlock& d = m->h_blocks[b];
+      gr_block g{};
+      for (int ax = 0; ax < 3; ++ax) {
+        g.n[ax] = d.n[ax];
+        g.dx[ax] = d.dx[ax];
+        g.face_off[ax] = d.face[ax] - l[1 + ax];
+      }
+      g.ng = d.g;
+      g.cell_off = d.cell - l[0];
+      g.vert_off = d.vert - l[4];
+      blk.push_back(g);
+    }
+    gr_mesh* sm = nullptr;
+    int r = gr_mesh_create(m->ctx, blk.data(), (int)blk.size(), 0, &sm);
+    if (r) { host_batches_free(h); return r; }
+    h->sub.push_back(sm);
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ea, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->ev_in.push_back(ea);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eb, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->ev_out.push_back(eb);
+    if (e != cudaSuccess) { host_batches_free(h); return cuda_fail(e, "gr_host_stage events"); }
+  }
+  h->nbatch = nbatch;
+  return GR_OK;
+}
+
+static int host_pool(HostStage* h, double** slot, long long n) {
+  if (*slot) return GR_OK;
+  cudaError_t e = cudaMalloc((void**)slot, sizeof(double) * std::max<long long>(n, 1));
+  if (e != cudaSuccess) {
+    *slot = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA, "gr_host_stage: staging pool");
+  }
+  h->allocs.push_back(*slot);
+  return GR_OK;
+}
+
+extern "C" {
+
+int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
+                  int32_t nbatch, void* stream) {
+  if (!mesh || !metric || !state) return fail(GR_EINVAL, "gr_host_stage: NULL argument");
+  if (nbatch < 1 || nbatch > 1024) return fail(GR_EINVAL, "gr_host_stage: nbatch must be 1..1024");
+  if (mesh->ws.nlvl) return fail(GR_EUNSUPPORTED, "gr_host_stage: not with level faces (batches would split them)");
+  // the host arrays pass the same checks as a device stage
+  MetricView mv0;
+  StateView sv0{};
+  int r = stage_prepare(mesh, metric, state, dt, params, mv0, sv0);
+  if (r) return r;
+  if (mesh->nblocks == 0) return GR_OK;
+  DeviceGuard g(mesh->ctx->device);
+  if ((r = host_stage_setup(mesh, nbatch))) return r;
+  HostStage* h = mesh->hs;
+  const bool tab = params->eos == GR_EOS_TABLE;
+  const int nq = tab ? 6 : 5, nwr = tab ? 6 : 5, nwo = tab ? 7 : 5, nm = metric->k_zero ? 10 : 16;
+  const bool g0 = params->rk_g0 != 0.0;
+  const long long nc = mesh->sh.ncell, nv = mesh->sh.nvert;
+  bool u0_alias = true, b0_alias = true;
+  for (int v = 0; v < nq; ++v) u0_alias = u0_alias && state->U0[v] == state->U[v];
+  for (int a = 0; a < 3; ++a) b0_alias = b0_alias && state->B0[a] == state->B[a];
+  // staging pools (device copies in the parent layout)
+  for (int v = 0; v < nq; ++v)
+    if ((r = host_pool(h, &h->U[v], nc)) || (r = host_pool(h, &h->Uo[v], nc))) return r;
+  for (int v = 0; v < nwo; ++v)
+    if ((r = host_pool(h, &h->W[v], nc)) || (r = host_pool(h, &h->Wo[v], nc))) return r;
+  for (int a = 0; a < 3; ++a)
+    if ((r = host_pool(h, &h->B[a], mesh->sh.nface[a])) || (r = host_pool(h, &h->Bo[a], mesh->sh.nface[a]))) return r;
+  for (int c = 0; c < nm; ++c)
+    if ((r = host_pool(h, &h->M[c], nv))) return r;
+  if (g0 && !u0_alias)
+    for (int v = 0; v < nq; ++v)
+      if ((r = host_pool(h, &h->U0[v], nc))) return r;
+  if (g0 && !b0_alias)
+    for (int a = 0; a < 3; ++a)
+      if ((r = host_pool(h, &h->B0[a], mesh->sh.nface[a]))) return r;
+  if (!h->status) {
+    cudaError_t ea = cudaMalloc((void**)&h->status, std::max<long long>(nc, 1));
+    if (ea != cudaSuccess) { cudaGetLastError(); return fail(GR_ENOMEM, "gr_host_stage: staging pool"); }
+    h->allocs.push_back(h->status);
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaError_t e = cudaEventRecord(h->ev_start, user);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->st[i], h->ev_start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "gr_host_stage");
+  auto copy = [&](void* dst, const void* src, long long lo, long long hi, size_t el, cudaMemcpyKind kd,
+                  cudaStream_t s) {
+    if (e != cudaSuccess || hi <= lo) return;
+    e = cudaMemcpyAsync((char*)dst + lo * el, (const char*)src + lo * el, (hi - lo) * el, kd, s);
+  };
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+  const int nb = (int)h->sub.size();
+  for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+    const long long c0 = h->lo[0][k], c1 = h->hi[0][k], v0 = h->lo[4][k], v1 = h->hi[4][k];
+    long long f0[3], f1[3];
+    for (int a = 0; a < 3; ++a) { f0[a] = h->lo[1 + a][k]; f1[a] = h->hi[1 + a][k]; }
+    // inputs of this batch
+    for (int v = 0; v < nq; ++v) copy(h->U[v], state->U[v], c0, c1, 8, H2D, h->st[0]);
+    for (int v = 0; v < nwo; ++v)   // W[6] (T with a table) only seeds the output's ghosts, if given
+      if (v < nwr || state->W[v]) copy(h->W[v], state->W[v], c0, c1, 8, H2D, h->st[0]);
+    for (int a = 0; a < 3; ++a) copy(h->B[a], state->B[a], f0[a], f1[a], 8, H2D, h->st[0]);
+    for (int c = 0; c < nm; ++c) copy(h->M[c], metric->v[c], v0, v1, 8, H2D, h->st[0]);
+    if (g0 && !u0_alias)
+      for (int v = 0; v < nq; ++v) copy(h->U0[v], state->U0[v], c0, c1, 8, H2D, h->st[0]);
+    if (g0 && !b0_alias)
+      for (int a = 0; a < 3; ++a) copy(h->B0[a], state->B0[a], f0[a], f1[a], 8, H2D, h->st[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[k], h->st[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st[1], h->ev_in[k], 0);
+    // outputs start as the inputs (the stage writes interior elements only), status as 0
+    const cudaMemcpyKind D2D = cudaMemcpyDeviceToDevice;
+    for (int v = 0; v < nq; ++v) copy(h->Uo[v], h->U[v], c0, c1, 8, D2D, h->st[1]);
+    for (int v = 0; v < nwo; ++v) {
+      if (v < nwr || state->W[v]) copy(h->Wo[v], h->W[v], c0, c1, 8, D2D, h->st[1]);
+      else if (e == cudaSuccess) e = cudaMemsetAsync(h->Wo[v] + c0, 0, (c1 - c0) * 8, h->st[1]);
+    }
+    for (int a = 0; a < 3; ++a) copy(h->Bo[a], h->B[a], f0[a], f1[a], 8, D2D, h->st[1]);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status + c0, 0, c1 - c0, h->st[1]);
+    if (e != cudaSuccess) break;
+    // its stage, on the staging pools advanced to the batch's first elements
+    gr_metric md = *metric;
+    for (int c = 0; c < 16; ++c) md.v[c] = c < nm ? h->M[c] + v0 : nullptr;
+    gr_state sd{};
+    for (int v = 0; v < nq; ++v) {
+      sd.U[v] = h->U[v] + c0;
+      sd.U0[v] = (g0 && !u0_alias ? h->U0[v] : h->U[v]) + c0;
+      sd.Uo[v] = h->Uo[v] + c0;
+    }
+    for (int v = 0; v < nwo; ++v) {
+      sd.W[v] = h->W[v] + c0;
+      sd.Wo[v] = h->Wo[v] + c0;
+    }
+    for (int a = 0; a < 3; ++a) {
+      sd.B[a] = h->B[a] + f0[a];
+      sd.B0[a] = (g0 && !b0_alias ? h->B0[a] : h->B[a]) + f0[a];
+      sd.Bo[a] = h->Bo[a] + f0[a];
+    }
+    sd.status = h->status + c0;
+    gr_mesh* sm = h->sub[k];
+    std::memcpy(sm->shapes, mesh->shapes, sizeof(mesh->shapes));
+    if ((r = stage_impl(sm, &md, &sd, dt, params, h->st[1], false))) return r;
+    e = cudaEventRecord(h->ev_out[k], h->st[1]);
+    // its outputs
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st[2], h->ev_out[k], 0);
+    for (int v = 0; v < nq; ++v) copy(state->Uo[v], h->Uo[v], c0, c1, 8, D2H, h->st[2]);
+    for (int v = 0; v < nwo; ++v) copy(state->Wo[v], h->Wo[v], c0, c1, 8, D2H, h->st[2]);
+    for (int a = 0; a < 3; ++a) copy(state->Bo[a], h->Bo[a], f0[a], f1[a], 8, D2H, h->st[2]);
+    copy(state->status, h->status, c0, c1, 1, D2H, h->st[2]);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_end, h->st[2]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_end, 0);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_host_stage");
 }
 
 // launches of the five stage kernels for the given shapes

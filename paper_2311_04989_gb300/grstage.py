@@ -36,7 +36,7 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
            "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
-           "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong"]
+           "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong", "gr_host_stage"]
 GR_ABI_VERSION = 2
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
@@ -161,6 +161,8 @@ def load(path: str = LIB_PATH):
     L.gr_driver_dt.argtypes = [vp, C.POINTER(C.c_double)]
     L.gr_driver_dt_device.argtypes = [vp]
     L.gr_driver_dt_device.restype = vp
+    L.gr_host_stage.argtypes = [vp, C.POINTER(gr_metric), C.POINTER(gr_state), C.c_double, C.POINTER(gr_params), i32,
+                                vp]
     L.gr_mesh_set_levels.argtypes = [vp, C.POINTER(gr_level_face), i32, C.POINTER(gr_level_map), i32,
                                      C.POINTER(gr_level_map), i32]
     L.gr_restrict.argtypes = [vp, C.c_void_p * 8, i32, vp, vp]
@@ -290,6 +292,13 @@ def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):
     if rc != GR_OK:
         raise GrstageError(f"gr_diag_noalloc: {L.gr_strerror(rc).decode()} ({L.gr_noalloc_last_error().decode()})")
     return list(out)
+
+
+def gr_host_stage(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_params, nbatch: int = 8,
+                  stream=None):
+    """gr_stage on host-resident (pinned) pools: metric and state hold host pointers (see include/grstage.h)."""
+    _check(load().gr_host_stage(mesh, C.byref(metric), C.byref(state), float(dt), C.byref(params), int(nbatch),
+                                _stream(stream)), "gr_host_stage")
 
 
 def gr_graph_capture(mesh, metric: gr_metric, state: gr_state, dt: float, params: gr_params):

@@ -189,6 +189,53 @@ def test_graph_replay_equals_the_direct_stage_bitwise(precision):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("precision,nbatch,rk", [(G.GR_PREC_FP64, 1, False), (G.GR_PREC_MIXED, 3, False),
+                                                  (G.GR_PREC_MIXED, 2, True)])
+def test_host_stage_equals_the_device_stage_bitwise(precision, nbatch, rk):
+    # gr_host_stage on pinned host pools (batched copies in, stages, copies out on three streams) gives
+    # gr_stage's results on device copies of the same data, for uneven blocks and an RK register stage
+    import torch
+    blocks = [I.random_block(n=n, g=3, seed=70 + k, metric_amp=0.02) for k, n in
+              enumerate([(8, 8, 8), (16, 8, 12), (12, 12, 12), (8, 16, 8)])]
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-12)
+    if rk:
+        P.rk_g0, P.rk_g1, P.rk_beta = 0.75, 0.25, 0.25
+    pools = GH.Pools(blocks)
+    U = pools.cells([H.cons_from_prims(b, P) for b in blocks], 5)
+    U0 = U * (1 + 1e-3) if rk else U
+    Wd, Bd, Md = pools.cells([b.W for b in blocks], 5), pools.faces([b.B for b in blocks]), pools.verts(
+        [b.metric for b in blocks])
+    B0 = [b * (1 - 1e-3) for b in Bd] if rk else Bd
+    gp = GH.gr_params_from(P, precision, G.GR_GUESS_FP32 if precision else G.GR_GUESS_NONE)
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    try:
+        # device stage
+        Uo, Wo, Bo = U.clone(), Wd.clone(), [b.clone() for b in Bd]
+        st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+        G.gr_stage(mesh, G.metric_struct(Md), G.state_struct(U, U0, Bd, B0, Wd, Uo, Bo, Wo, st), 0.01, gp,
+                   torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ref = [Uo.cpu(), Wo.cpu(), st.cpu()] + [b.cpu() for b in Bo]
+        # the same on pinned host pools
+        pin = lambda t: t.cpu().pin_memory()
+        hU, hW, hM = pin(U), pin(Wd), pin(Md)
+        hU0 = pin(U0) if rk else hU
+        hB = [pin(b) for b in Bd]
+        hB0 = [pin(b) for b in B0] if rk else hB
+        hUo, hWo = torch.zeros_like(hU).pin_memory(), torch.zeros_like(hW).pin_memory()
+        hBo = [torch.zeros_like(b).pin_memory() for b in hB]
+        hst = torch.zeros(pools.L.ncell, dtype=torch.uint8).pin_memory()
+        for _ in range(2):   # the second call reuses the staging pools and batches
+            G.gr_host_stage(mesh, G.metric_struct(hM), G.state_struct(hU, hU0, hB, hB0, hW, hUo, hBo, hWo, hst), 0.01,
+                            gp, nbatch, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            got = [hUo, hWo, hst] + hBo
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b)
+    finally:
+        G.gr_mesh_destroy(mesh)
+
+
 def test_invalid_arguments_are_rejected():
     import torch
     bi = I.uniform_block(n=(4, 4, 4), g=2)
