@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of gr_autotune's")
     ap.add_argument("--no-rk", action="store_true", help="skip the timing of a whole RK3 driver step")
     ap.add_argument("--no-adm", action="store_true", help="skip the timing of the matter-source outputs")
+    ap.add_argument("--e2e-batches", type=int, default=8, help="block batches of the host-buffer stage")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -582,7 +583,7 @@ def main():
         hstate = G.state_struct(hU, hU, hB, hB, hW, hUo, hBo, hWo, hst)
         bin_ = sum(x.numel() * x.element_size() for x in [hU, hW, hM] + hB)
         bout = sum(x.numel() * x.element_size() for x in [hUo, hWo, hst] + hBo)
-        nbatch = 8
+        nbatch = a.e2e_batches
 
         def e2e_step():
             G.gr_host_stage(mesh, hmetric, hstate, dt, p, nbatch, stream)
