@@ -581,8 +581,12 @@ def main():
             hmetric.v[c] = int(hM[c].data_ptr())
         hmetric.order, hmetric.k_zero = 2, 1
         hstate = G.state_struct(hU, hU, hB, hB, hW, hUo, hBo, hWo, hst)
-        bin_ = sum(x.numel() * x.element_size() for x in [hU, hW, hM] + hB)
-        bout = sum(x.numel() * x.element_size() for x in [hUo, hWo, hst] + hBo)
+        # bytes that cross the host link per step: W, B and the metric whole (ghosts included), U on
+        # interior cells; out: U', W', status on interior cells, B' on the faces of interior cells
+        nint = L.interior_cells()
+        nctf = sum((gm.n[0] + (d == 0)) * (gm.n[1] + (d == 1)) * (gm.n[2] + (d == 2)) for gm in geoms for d in range(3))
+        bin_ = sum(x.numel() * x.element_size() for x in [hW, hM] + hB) + hU.shape[0] * nint * 8
+        bout = (hUo.shape[0] + hWo.shape[0]) * nint * 8 + nint + nctf * 8
         nbatch = a.e2e_batches
 
         def e2e_step():

@@ -208,19 +208,21 @@ int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_s
 int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]);
 
 /* ---- one stage on host-resident pools ----------------------------------------------------------------
- * gr_host_stage: the stage of gr_stage on a mesh whose pools live in host memory (pinned, page-locked
- * memory gives full copy bandwidth).  metric and state hold HOST pointers in the layouts of gr_stage.
- * The mesh keeps device copies of the pools (allocated on the first call: about the size of the pools)
- * and splits the blocks into nbatch groups of consecutive blocks; each group's inputs (U, W, B, the
- * metric, U0 and B0 where rk_g0 != 0 and they are separate arrays) are copied to the device, its stage
- * runs, and its outputs (U', W', B', status) are copied back, on three streams, so that the copies of
- * one group overlap the stage of another.  The whole block arrays of the outputs are written: interior
- * elements by the stage, ghost elements with the inputs' values (U', W', B' ghosts = U, W, B; with a
- * table W'[6] from W[6] if given, else 0; status 0), which is what gr_stage gives when its outputs
- * start as copies of the inputs; results then equal gr_stage's, bitwise.  Asynchronous: it is ordered after earlier work on `stream`, and `stream` waits for its end;
- * the host outputs are complete once `stream` is synchronised.  Calls on one mesh must be ordered (one
- * stream).  Errors: those of gr_stage; GR_EINVAL (nbatch outside 1..1024), GR_EUNSUPPORTED (a mesh with
- * level faces, or pools that do not hold the blocks in increasing order), GR_ENOMEM. */
+ * gr_host_stage: the stage of gr_stage on a mesh whose pools live in host memory.  metric and state hold
+ * HOST pointers in the layouts of gr_stage, to pinned (page-locked, device-mapped) memory, e.g. from
+ * cudaHostAlloc; pageable memory is rejected.  The mesh keeps device copies of the pools (allocated on
+ * the first call: about the size of the pools) and splits the blocks into nbatch groups of consecutive
+ * blocks; each group's inputs are brought to the device, its stage runs, and its outputs are written
+ * back, on three streams, so that the transfers of one group overlap the stage of another.  Only the
+ * elements the stage reads or writes cross the host link: W, B and the metric with their ghosts (copy
+ * engines), U (and U0 where rk_g0 != 0) on interior cells and B0 on the faces of interior cells, and of
+ * the outputs the interior cells of U', W', status and the faces of interior cells of B' (kernels that
+ * access the mapped host memory).  Output ghost entries are left untouched, as by gr_stage, and the
+ * results equal gr_stage's bitwise.  Asynchronous: ordered after earlier work on `stream`, and `stream`
+ * waits for its end; the host outputs are complete once `stream` is synchronised.  Calls on one mesh
+ * must be ordered (one stream).  Errors: those of gr_stage; GR_EINVAL (nbatch outside 1..1024, a host
+ * pool that is not pinned), GR_EUNSUPPORTED (a mesh with level faces, or pools that do not hold the
+ * blocks in increasing order), GR_ENOMEM. */
 int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
                   int32_t nbatch, void* stream);
 

@@ -676,6 +676,16 @@ static int host_pool(HostStage* h, double** slot, long long n) {
 
 extern "C" {
 
+static bool host_mapped(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
+
 int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
                   int32_t nbatch, void* stream) {
   if (!mesh || !metric || !state) return fail(GR_EINVAL, "gr_host_stage: NULL argument");
@@ -687,16 +697,30 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
   int r = stage_prepare(mesh, metric, state, dt, params, mv0, sv0);
   if (r) return r;
   if (mesh->nblocks == 0) return GR_OK;
-  DeviceGuard g(mesh->ctx->device);
-  if ((r = host_stage_setup(mesh, nbatch))) return r;
-  HostStage* h = mesh->hs;
   const bool tab = params->eos == GR_EOS_TABLE;
   const int nq = tab ? 6 : 5, nwr = tab ? 6 : 5, nwo = tab ? 7 : 5, nm = metric->k_zero ? 10 : 16;
   const bool g0 = params->rk_g0 != 0.0;
-  const long long nc = mesh->sh.ncell, nv = mesh->sh.nvert;
   bool u0_alias = true, b0_alias = true;
   for (int v = 0; v < nq; ++v) u0_alias = u0_alias && state->U0[v] == state->U[v];
   for (int a = 0; a < 3; ++a) b0_alias = b0_alias && state->B0[a] == state->B[a];
+  // every host pool is read or written by the transfer kernels: pinned, device-mapped memory only
+  {
+    bool ok = host_mapped(state->status);
+    for (int v = 0; v < nq; ++v) ok = ok && host_mapped(state->U[v]) && host_mapped(state->Uo[v]);
+    for (int v = 0; v < nwr; ++v) ok = ok && host_mapped(state->W[v]);
+    for (int v = 0; v < nwo; ++v) ok = ok && host_mapped(state->Wo[v]);
+    for (int a = 0; a < 3; ++a) ok = ok && host_mapped(state->B[a]) && host_mapped(state->Bo[a]);
+    for (int c = 0; c < nm; ++c) ok = ok && host_mapped(metric->v[c]);
+    if (g0 && !u0_alias)
+      for (int v = 0; v < nq; ++v) ok = ok && host_mapped(state->U0[v]);
+    if (g0 && !b0_alias)
+      for (int a = 0; a < 3; ++a) ok = ok && host_mapped(state->B0[a]);
+    if (!ok) return fail(GR_EINVAL, "gr_host_stage: host pools must be pinned (page-locked, device-mapped) memory");
+  }
+  DeviceGuard g(mesh->ctx->device);
+  if ((r = host_stage_setup(mesh, nbatch))) return r;
+  HostStage* h = mesh->hs;
+  const long long nc = mesh->sh.ncell, nv = mesh->sh.nvert;
   // staging pools (device copies in the parent layout)
   for (int v = 0; v < nq; ++v)
     if ((r = host_pool(h, &h->U[v], nc)) || (r = host_pool(h, &h->Uo[v], nc))) return r;
@@ -721,38 +745,38 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
   cudaError_t e = cudaEventRecord(h->ev_start, user);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->st[i], h->ev_start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "gr_host_stage");
-  auto copy = [&](void* dst, const void* src, long long lo, long long hi, size_t el, cudaMemcpyKind kd,
-                  cudaStream_t s) {
+  auto copy = [&](void* dst, const void* src, long long lo, long long hi, cudaStream_t s) {
     if (e != cudaSuccess || hi <= lo) return;
-    e = cudaMemcpyAsync((char*)dst + lo * el, (const char*)src + lo * el, (hi - lo) * el, kd, s);
+    e = cudaMemcpyAsync((double*)dst + lo, (const double*)src + lo, (hi - lo) * 8, cudaMemcpyHostToDevice, s);
   };
-  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
   const int nb = (int)h->sub.size();
   for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+    gr_mesh* sm = h->sub[k];
     const long long c0 = h->lo[0][k], c1 = h->hi[0][k], v0 = h->lo[4][k], v1 = h->hi[4][k];
     long long f0[3], f1[3];
     for (int a = 0; a < 3; ++a) { f0[a] = h->lo[1 + a][k]; f1[a] = h->hi[1 + a][k]; }
-    // inputs of this batch
-    for (int v = 0; v < nq; ++v) copy(h->U[v], state->U[v], c0, c1, 8, H2D, h->st[0]);
-    for (int v = 0; v < nwo; ++v)   // W[6] (T with a table) only seeds the output's ghosts, if given
-      if (v < nwr || state->W[v]) copy(h->W[v], state->W[v], c0, c1, 8, H2D, h->st[0]);
-    for (int a = 0; a < 3; ++a) copy(h->B[a], state->B[a], f0[a], f1[a], 8, H2D, h->st[0]);
-    for (int c = 0; c < nm; ++c) copy(h->M[c], metric->v[c], v0, v1, 8, H2D, h->st[0]);
-    if (g0 && !u0_alias)
-      for (int v = 0; v < nq; ++v) copy(h->U0[v], state->U0[v], c0, c1, 8, H2D, h->st[0]);
-    if (g0 && !b0_alias)
-      for (int a = 0; a < 3; ++a) copy(h->B0[a], state->B0[a], f0[a], f1[a], 8, H2D, h->st[0]);
+    // inputs of this batch: W, B, the metric (ghosts included) by the copy engines; U (and U0) on the
+    // interior cells only, B0 on the faces of interior cells only, by the transfer kernels
+    for (int v = 0; v < nwr; ++v) copy(h->W[v], state->W[v], c0, c1, h->st[0]);
+    for (int a = 0; a < 3; ++a) copy(h->B[a], state->B[a], f0[a], f1[a], h->st[0]);
+    for (int c = 0; c < nm; ++c) copy(h->M[c], metric->v[c], v0, v1, h->st[0]);
+    const void* src[8];
+    void* dst[8];
+    for (int v = 0; v < nq; ++v) { src[v] = state->U[v] + c0; dst[v] = h->U[v] + c0; }
+    if (e == cudaSuccess)
+      e = launch_io_cells(sm->d_blocks, sm->d_work[R_INTERIOR], sm->nwork[R_INTERIOR], src, dst, nq, 8, h->st[0]);
+    if (g0 && !u0_alias) {
+      for (int v = 0; v < nq; ++v) { src[v] = state->U0[v] + c0; dst[v] = h->U0[v] + c0; }
+      if (e == cudaSuccess)
+        e = launch_io_cells(sm->d_blocks, sm->d_work[R_INTERIOR], sm->nwork[R_INTERIOR], src, dst, nq, 8, h->st[0]);
+    }
+    if (g0 && !b0_alias && e == cudaSuccess) {
+      const double* fs[3] = {state->B0[0] + f0[0], state->B0[1] + f0[1], state->B0[2] + f0[2]};
+      double* fd[3] = {h->B0[0] + f0[0], h->B0[1] + f0[1], h->B0[2] + f0[2]};
+      e = launch_io_faces(sm->d_blocks, sm->d_work[R_CTFACES], sm->nwork[R_CTFACES], fs, fd, h->st[0]);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[k], h->st[0]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st[1], h->ev_in[k], 0);
-    // outputs start as the inputs (the stage writes interior elements only), status as 0
-    const cudaMemcpyKind D2D = cudaMemcpyDeviceToDevice;
-    for (int v = 0; v < nq; ++v) copy(h->Uo[v], h->U[v], c0, c1, 8, D2D, h->st[1]);
-    for (int v = 0; v < nwo; ++v) {
-      if (v < nwr || state->W[v]) copy(h->Wo[v], h->W[v], c0, c1, 8, D2D, h->st[1]);
-      else if (e == cudaSuccess) e = cudaMemsetAsync(h->Wo[v] + c0, 0, (c1 - c0) * 8, h->st[1]);
-    }
-    for (int a = 0; a < 3; ++a) copy(h->Bo[a], h->B[a], f0[a], f1[a], 8, D2D, h->st[1]);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->status + c0, 0, c1 - c0, h->st[1]);
     if (e != cudaSuccess) break;
     // its stage, on the staging pools advanced to the batch's first elements
     gr_metric md = *metric;
@@ -773,16 +797,27 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
       sd.Bo[a] = h->Bo[a] + f0[a];
     }
     sd.status = h->status + c0;
-    gr_mesh* sm = h->sub[k];
     std::memcpy(sm->shapes, mesh->shapes, sizeof(mesh->shapes));
     if ((r = stage_impl(sm, &md, &sd, dt, params, h->st[1], false))) return r;
     e = cudaEventRecord(h->ev_out[k], h->st[1]);
-    // its outputs
+    // its outputs, the elements the stage writes: interior cells of U', W', status, faces of interior
+    // cells of B'
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st[2], h->ev_out[k], 0);
-    for (int v = 0; v < nq; ++v) copy(state->Uo[v], h->Uo[v], c0, c1, 8, D2H, h->st[2]);
-    for (int v = 0; v < nwo; ++v) copy(state->Wo[v], h->Wo[v], c0, c1, 8, D2H, h->st[2]);
-    for (int a = 0; a < 3; ++a) copy(state->Bo[a], h->Bo[a], f0[a], f1[a], 8, D2H, h->st[2]);
-    copy(state->status, h->status, c0, c1, 1, D2H, h->st[2]);
+    for (int v = 0; v < nq; ++v) { src[v] = h->Uo[v] + c0; dst[v] = state->Uo[v] + c0; }
+    if (e == cudaSuccess)
+      e = launch_io_cells(sm->d_blocks, sm->d_work[R_INTERIOR], sm->nwork[R_INTERIOR], src, dst, nq, 8, h->st[2]);
+    for (int v = 0; v < nwo; ++v) { src[v] = h->Wo[v] + c0; dst[v] = state->Wo[v] + c0; }
+    if (e == cudaSuccess)
+      e = launch_io_cells(sm->d_blocks, sm->d_work[R_INTERIOR], sm->nwork[R_INTERIOR], src, dst, nwo, 8, h->st[2]);
+    src[0] = h->status + c0;
+    dst[0] = state->status + c0;
+    if (e == cudaSuccess)
+      e = launch_io_cells(sm->d_blocks, sm->d_work[R_INTERIOR], sm->nwork[R_INTERIOR], src, dst, 1, 1, h->st[2]);
+    if (e == cudaSuccess) {
+      const double* fs[3] = {h->Bo[0] + f0[0], h->Bo[1] + f0[1], h->Bo[2] + f0[2]};
+      double* fd[3] = {state->Bo[0] + f0[0], state->Bo[1] + f0[1], state->Bo[2] + f0[2]};
+      e = launch_io_faces(sm->d_blocks, sm->d_work[R_CTFACES], sm->nwork[R_CTFACES], fs, fd, h->st[2]);
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_end, h->st[2]);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_end, 0);

@@ -162,6 +162,11 @@ cudaError_t launch_level_fix(int precision, const DBlock* blocks, const LevelFac
                              int table, cudaStream_t st);
 cudaError_t launch_amr(bool prolong, const DBlock* blocks, const LevelMap* maps, const Work* work, int nwork,
                        double* const cells[8], int nvar, double* const B[3], cudaStream_t st);
+// gr_host_stage transfers of interior cells / faces of interior cells (pinned, device-mapped host memory)
+cudaError_t launch_io_cells(const DBlock* blocks, const Work* work, int nwork, const void* const* src, void* const* dst,
+                            int n, int elem, cudaStream_t st);
+cudaError_t launch_io_faces(const DBlock* blocks, const Work* work, int nwork, const double* const src[3],
+                            double* const dst[3], cudaStream_t st);
 constexpr int kAdmThreads = 256;
 constexpr size_t kAdmSmemTarget = 96 * 1024;    // shared memory a k_adm_verts slab aims for
 constexpr size_t kAdmSmemMax = 200 * 1024;      // ... and may not exceed (one vertex plane)

@@ -192,8 +192,9 @@ def test_graph_replay_equals_the_direct_stage_bitwise(precision):
 @pytest.mark.parametrize("precision,nbatch,rk", [(G.GR_PREC_FP64, 1, False), (G.GR_PREC_MIXED, 3, False),
                                                   (G.GR_PREC_MIXED, 2, True)])
 def test_host_stage_equals_the_device_stage_bitwise(precision, nbatch, rk):
-    # gr_host_stage on pinned host pools (batched copies in, stages, copies out on three streams) gives
-    # gr_stage's results on device copies of the same data, for uneven blocks and an RK register stage
+    # gr_host_stage on pinned host pools (batched transfers in, stages, transfers out on three streams)
+    # gives gr_stage's results on device copies of the same data, for uneven blocks and an RK register
+    # stage, ghosts of the outputs untouched
     import torch
     blocks = [I.random_block(n=n, g=3, seed=70 + k, metric_amp=0.02) for k, n in
               enumerate([(8, 8, 8), (16, 8, 12), (12, 12, 12), (8, 16, 8)])]
@@ -222,9 +223,14 @@ def test_host_stage_equals_the_device_stage_bitwise(precision, nbatch, rk):
         hU0 = pin(U0) if rk else hU
         hB = [pin(b) for b in Bd]
         hB0 = [pin(b) for b in B0] if rk else hB
-        hUo, hWo = torch.zeros_like(hU).pin_memory(), torch.zeros_like(hW).pin_memory()
-        hBo = [torch.zeros_like(b).pin_memory() for b in hB]
+        # outputs start as the device outputs did (the stages write interior elements only)
+        hUo, hWo = pin(U), pin(Wd)
+        hBo = [pin(b) for b in Bd]
         hst = torch.zeros(pools.L.ncell, dtype=torch.uint8).pin_memory()
+        if not rk:   # pageable host pools are refused before anything runs
+            with pytest.raises(G.GrstageError):
+                G.gr_host_stage(mesh, G.metric_struct(hM), G.state_struct(U.cpu(), U.cpu(), hB, hB, hW, hUo, hBo, hWo,
+                                                                          hst), 0.01, gp, nbatch)
         for _ in range(2):   # the second call reuses the staging pools and batches
             G.gr_host_stage(mesh, G.metric_struct(hM), G.state_struct(hU, hU0, hB, hB0, hW, hUo, hBo, hWo, hst), 0.01,
                             gp, nbatch, torch.cuda.current_stream())
