@@ -415,6 +415,55 @@ def main():
     ms_head = results[head]["ms"]
     value = cells * world / (ms_head / 1e3)
 
+    # ---- end to end through the C ABI with host buffers ---------------------------------------
+    e2e = None
+    if not a.no_e2e:
+        hm = head == "mixed"
+        p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=(G.GR_PREC_MIXED if hm else G.GR_PREC_FP64),
+                                c2p_guess=(G.GR_GUESS_FP32 if hm else G.GR_GUESS_NONE),
+                                gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+        # the host-buffer entry: pinned host pools in, pinned host pools out; the library copies batches
+        # of blocks in, runs their stages and copies them out on three overlapping streams
+        hU, hW, hM = U.cpu().pin_memory(), W.cpu().pin_memory(), M.cpu().pin_memory()
+        hB = [x.cpu().pin_memory() for x in B]
+        hUo, hWo = torch.empty_like(hU).pin_memory(), torch.empty_like(hW).pin_memory()
+        hBo = [torch.empty_like(x).pin_memory() for x in hB]
+        hst = torch.empty(st.shape, dtype=st.dtype, pin_memory=True)
+        hmetric = G.gr_metric()
+        for c in range(10):
+            hmetric.v[c] = int(hM[c].data_ptr())
+        hmetric.order, hmetric.k_zero = 2, 1
+        hstate = G.state_struct(hU, hU, hB, hB, hW, hUo, hBo, hWo, hst)
+        # bytes that cross the host link per step: W, B and the metric whole (ghosts included), U on
+        # interior cells; out: U', W', status on interior cells, B' on the faces of interior cells
+        nint = L.interior_cells()
+        nctf = sum((gm.n[0] + (d == 0)) * (gm.n[1] + (d == 1)) * (gm.n[2] + (d == 2)) for gm in geoms for d in range(3))
+        bin_ = sum(x.numel() * x.element_size() for x in [hW, hM] + hB) + hU.shape[0] * nint * 8
+        bout = (hUo.shape[0] + hWo.shape[0]) * nint * 8 + nint + nctf * 8
+        nbatch = a.e2e_batches
+
+        def e2e_step():
+            G.gr_host_stage(mesh, hmetric, hstate, dt, p, nbatch, stream)
+
+        for _ in range(a.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e = torch.tensor([e0.elapsed_time(e1) / a.steps], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": cells * world / (ms_e.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": bin_,
+               "d2h_bytes_per_step": bout, "ms_per_step": ms_e.item(), "api": "gr_host_stage",
+               "batches": nbatch}
+        del hU, hW, hM, hB, hUo, hWo, hBo, hst
+
     # ---- the same stage replayed as a CUDA graph ------------------------------------------------
     graph_ms = None
     if head == "mixed":
@@ -561,55 +610,6 @@ def main():
     c2p_table = None
     if not a.no_table and not a.no_c2p:
         c2p_table = con2prim_table_workload(a, ctx, dev, G, I)
-
-    # ---- end to end through the C ABI with host buffers ---------------------------------------
-    e2e = None
-    if not a.no_e2e:
-        hm = head == "mixed"
-        p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=(G.GR_PREC_MIXED if hm else G.GR_PREC_FP64),
-                                c2p_guess=(G.GR_GUESS_FP32 if hm else G.GR_GUESS_NONE),
-                                gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
-        # the host-buffer entry: pinned host pools in, pinned host pools out; the library copies batches
-        # of blocks in, runs their stages and copies them out on three overlapping streams
-        hU, hW, hM = U.cpu().pin_memory(), W.cpu().pin_memory(), M.cpu().pin_memory()
-        hB = [x.cpu().pin_memory() for x in B]
-        hUo, hWo = torch.empty_like(hU).pin_memory(), torch.empty_like(hW).pin_memory()
-        hBo = [torch.empty_like(x).pin_memory() for x in hB]
-        hst = torch.empty(st.shape, dtype=st.dtype, pin_memory=True)
-        hmetric = G.gr_metric()
-        for c in range(10):
-            hmetric.v[c] = int(hM[c].data_ptr())
-        hmetric.order, hmetric.k_zero = 2, 1
-        hstate = G.state_struct(hU, hU, hB, hB, hW, hUo, hBo, hWo, hst)
-        # bytes that cross the host link per step: W, B and the metric whole (ghosts included), U on
-        # interior cells; out: U', W', status on interior cells, B' on the faces of interior cells
-        nint = L.interior_cells()
-        nctf = sum((gm.n[0] + (d == 0)) * (gm.n[1] + (d == 1)) * (gm.n[2] + (d == 2)) for gm in geoms for d in range(3))
-        bin_ = sum(x.numel() * x.element_size() for x in [hW, hM] + hB) + hU.shape[0] * nint * 8
-        bout = (hUo.shape[0] + hWo.shape[0]) * nint * 8 + nint + nctf * 8
-        nbatch = a.e2e_batches
-
-        def e2e_step():
-            G.gr_host_stage(mesh, hmetric, hstate, dt, p, nbatch, stream)
-
-        for _ in range(a.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms_e = torch.tensor([e0.elapsed_time(e1) / a.steps], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
-        e2e = {"value": cells * world / (ms_e.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": bin_,
-               "d2h_bytes_per_step": bout, "ms_per_step": ms_e.item(), "api": "gr_host_stage",
-               "batches": nbatch}
-        del hU, hW, hM, hB, hUo, hWo, hBo, hst
 
     # ---- roofline of the dominant kernel ---------------------------------------------------------
     flops = json.load(open(os.path.join(ROOT, "tests", "golden", "flops_binary_star_16cubed.json")))

@@ -1437,7 +1437,8 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
     stage_launches(m, m->shapes[params->precision][params->eos], kl);
     KParams kp = kparams(&ps, 0.0);
     kp.dt_dev = d->d_dt;
-    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr);
+    // the stages of a step share the metric: its FP32 shadow (mixed path) is made by the first one
+    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr, s == 0);
     if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step stage");
     if (!last) {
       for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];

@@ -143,10 +143,11 @@ cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<do
 
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after
-// the cast and each kernel
+// the cast and each kernel.  cast_metric = false reuses the FP32 metric shadow of the previous mixed
+// stage on this mesh (the RK driver, whose stages share one metric).
 cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
                          const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
-                         cudaStream_t st, cudaEvent_t* ev);
+                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric = true);
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st);

@@ -604,13 +604,13 @@ static InView<float> view32(const MetricView& m, const Shadow& sh) {
 }
 
 static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Shadow& sh, int eos,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool cast_metric) {
   CastList L;
   int k = 0;
   const int nw = eos == GR_EOS_TABLE ? 6 : 5;   // rho, u~^i, p[, Y_e]
   for (int q = 0; q < nw; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
   for (int d = 0; d < 3; ++d) { L.src[k] = s.B[d]; L.dst[k] = sh.B[d]; L.n[k] = sh.nface[d]; ++k; }
-  const int ncomp = m.k_zero ? 10 : 16;
+  const int ncomp = cast_metric ? (m.k_zero ? 10 : 16) : 0;
   for (int c = 0; c < ncomp; ++c) { L.src[k] = m.v[c]; L.dst[k] = sh.M[c]; L.n[k] = sh.nvert; ++k; }
   L.count = k;
   dim3 grid(152 * 2, k);
@@ -662,12 +662,12 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
 
 cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
                          const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
-                         cudaStream_t st, cudaEvent_t* ev) {
+                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric) {
   if (ev) cudaEventRecord(ev[0], st);
   const InView<double> in64 = view64(m, &s);
   const bool tab = kp.eos == GR_EOS_TABLE;
   if (precision == GR_PREC_MIXED) {
-    cudaError_t e = launch_cast(m, s, sh, kp.eos, st);
+    cudaError_t e = launch_cast(m, s, sh, kp.eos, st, cast_metric);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     const InView<float> in32 = view32(m, sh);
