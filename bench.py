@@ -43,6 +43,21 @@ def env_rank():
     return r, w, lr
 
 
+def max_over_ranks(ms, dist, dev):
+    """The job's time: the slowest rank's (an all-reduce MAX; the value itself on one process)."""
+    import torch
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed (replicas: the same per rank) over the job's
+    time in ms."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,10 +399,7 @@ def main():
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
         kms, nst = G.gr_profile_end(mesh)
-        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        return ms_t.item() / a.steps, [k / max(1, nst) for k in kms], clocks, shapes
+        return max_over_ranks(ms, dist, dev) / a.steps, [k / max(1, nst) for k in kms], clocks, shapes
 
     results = {}
     precs = {"both": ["fp64", "mixed"], "fp64": ["fp64"], "mixed": ["mixed"]}[a.precision]
@@ -413,7 +425,7 @@ def main():
         err["divB_integrated"] = d[2]
     head = "mixed" if "mixed" in results else "fp64"
     ms_head = results[head]["ms"]
-    value = cells * world / (ms_head / 1e3)
+    value = job_value(cells, world, ms_head)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None
@@ -456,11 +468,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms_e = torch.tensor([e0.elapsed_time(e1) / a.steps], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
-        e2e = {"value": cells * world / (ms_e.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": bin_,
-               "d2h_bytes_per_step": bout, "ms_per_step": ms_e.item(), "api": "gr_host_stage",
+        ms_e = max_over_ranks(e0.elapsed_time(e1) / a.steps, dist, dev)
+        e2e = {"value": job_value(cells, world, ms_e), "unit": UNIT, "h2d_bytes_per_step": bin_,
+               "d2h_bytes_per_step": bout, "ms_per_step": ms_e, "api": "gr_host_stage",
                "batches": nbatch}
         del hU, hW, hM, hB, hUo, hWo, hBo, hst
 

@@ -227,3 +227,36 @@ def test_driver_rejects_bad_tables():
     finally:
         G.gr_mesh_destroy(mesh)
 
+
+
+def test_driver_step_with_the_table_matches_the_oracle():
+    # the driver with the tabulated EOS (7 primitive pools exchanged, D Y_e advected): two RK2 steps,
+    # grid time step, periodic split domain, against the oracle's driver
+    eos = I.SyntheticEOS()
+    tab = eos.table(n=(80, 64, 24))
+    n, g = (16, 8, 8), 3
+    bi = I.random_block(n=n, g=g, seed=58, dx=tuple(1.0 / v for v in n), L=1.0, eos=eos, rho_range=(1e-7, 1e-3),
+                        T_range=(1e-3, 3e-2), ye_range=(0.1, 0.45), u_max=0.3, sigma_range=(1e-3, 0.3),
+                        fields=I.make_fields(np.random.default_rng(I.SEED_BASE + 58), 1.0, shared_metric=True),
+                        metric_amp=0.01)
+    H.fill_periodic_cells(bi.W, n, g)
+    H.fill_periodic_faces(bi.B, n, g)
+    H.fill_periodic_vertices(bi.metric, n, g)
+    parts = I.split_block(bi, (2, 2, 1))
+    nbr = I.block_grid_neighbours((2, 2, 1))
+    P = O.Params(table=tab, rho_atm=1e-12, tol=1e-14, recon=1)
+    ref = copy.deepcopy(parts)
+    Uref = [H.cons_from_prims(b, P, P.interp_order) for b in ref]
+    run = Run(parts, nbr, P, U=[u.copy() for u in Uref])
+    try:
+        for _ in range(2):
+            run.step(0.25, G.GR_DT_GRID, 2)
+            got = run.result()
+            _, st_ref = DR.rk_step(ref, Uref, nbr, P, 0.25, order=2, dt_mode="grid")
+    finally:
+        run.close()
+    refs = [dict(U=Uref[b], W=ref[b].W, B=ref[b].B, status=st_ref[b]) for b in range(len(ref))]
+    errs = GH.compare(got, refs, blocks=parts)
+    print(f"driver RK2 with the table: max err {max(v for k, v in errs.items() if k != 'status_mismatch'):.2e}")
+    assert errs.pop("status_mismatch") == 0
+    assert max(errs.values()) < TOL64, errs
