@@ -256,7 +256,12 @@ def test_driver_step_with_the_table_matches_the_oracle():
     finally:
         run.close()
     refs = [dict(U=Uref[b], W=ref[b].W, B=ref[b].B, status=st_ref[b]) for b in range(len(ref))]
-    errs = GH.compare(got, refs, blocks=parts)
-    print(f"driver RK2 with the table: max err {max(v for k, v in errs.items() if k != 'status_mismatch'):.2e}")
+    # u~^i pass through zero; con2prim recovers them from O(1) quantities (W ~ 1), rounding ~1e-16
+    # absolute: their floor is 1e-2 of the block maximum (as in the refined-mesh tests)
+    errs = GH.compare(got, refs, blocks=parts, floors={"W1": 1e-2, "W2": 1e-2, "W3": 1e-2})
+    print("driver RK2 with the table: " + ", ".join(f"{k} {v:.1e}" for k, v in sorted(errs.items())))
     assert errs.pop("status_mismatch") == 0
-    assert max(errs.values()) < TOL64, errs
+    # T is the inverse of the table's piecewise-linear interpolant in log T, ill-conditioned where the
+    # cold part dominates the pressure: held to 1e-10 as in the table stage parity test
+    for k, v in errs.items():
+        assert v < (1e-10 if k == "W6" else TOL64), (k, v)
