@@ -369,19 +369,34 @@ def star_block(n=(64, 64, 64), g=3, half_width=10.02, tov: TOV | None = None, ce
 # ---------------------------------------------------------------------------------------------
 # batches
 # ---------------------------------------------------------------------------------------------
-def amr_like_batch(nblocks=1024, sizes=(16, 24, 32), g=3, seed=3, L=1.0, levels=3, **kw):
+def amr_like_batch(nblocks=1024, sizes=(16, 24, 32), g=3, seed=3, L=1.0, levels=3, workers=1, **kw):
     """Blocks of uneven sizes drawn from ``sizes``, at ``levels`` refinement levels (dx, dx/2, dx/4),
-    placed at random positions; all sample the same global smooth fields."""
+    placed at random positions; all sample the same global smooth fields.  The sizes and positions are
+    drawn in order from one seeded generator, then the blocks are built (in ``workers`` processes; the
+    result does not depend on it)."""
     rng = np.random.default_rng(SEED_BASE + seed)
     fields = make_fields(rng, L, shared_metric=True)
-    blocks = []
+    spec = []
     for b in range(nblocks):
         n = int(rng.choice(sizes))
         lev = int(rng.integers(0, levels))
         dxb = (L / 64) / (2 ** lev)
         x0 = tuple(rng.uniform(0, L - n * dxb, 3))
-        blocks.append(random_block((n, n, n), g, x0, (dxb,) * 3, seed=seed, L=L, fields=fields, **kw))
-    return blocks
+        spec.append((n, x0, dxb))
+    args = [((sp[0],) * 3, g, sp[1], (sp[2],) * 3, seed, L, fields, kw) for sp in spec]
+    if workers <= 1:
+        return [_amr_block(a) for a in args]
+    # worker processes (spawned: safe whatever the parent has initialised); numpy-bound in pieces too
+    # small for threads to help
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_amr_block, args, chunksize=max(1, len(args) // (4 * workers))))
+
+
+def _amr_block(a):
+    n, g, x0, dx, seed, L, fields, kw = a
+    return random_block(n, g, x0, dx, seed=seed, L=L, fields=fields, **kw)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -213,3 +213,43 @@ def _geom(g, r, blocks, b):
     # infer from shapes: status (Nz,Ny,Nx); assume ng = 3
     Nz, Ny, Nx = r["status"].shape
     return (Nx - 6, Ny - 6, Nz - 6), 3
+
+
+def backward_error(out, bi, P: O.Params, order=2):
+    """How well the primitives of a stage output solve its own conserved variables: max over the
+    interior cells of a regular solve (status 0; cells under a floor, clamp or the atmosphere are set by
+    closed-form policies and compared forward) of |prim2con(W', cell field of B') - U'| (the oracle's
+    prim2con and cell metric), with the
+    conserved-variable denominators of compare().  Recovering the primitives from the conserved
+    variables is ill-conditioned where the pressure is a small part of the energy (cold, low-density
+    gas) or a velocity passes through zero, so two FP64 implementations whose conserved variables agree
+    to rounding can differ there by far more in W; the backward error is the well-conditioned check."""
+    n, g = bi.n, bi.ng
+    cm = H.cell_metric(bi, order)[g:g + n[2], g:g + n[1], g:g + n[0]].reshape(-1, 16)
+    Bx, By, Bz = out["B"]
+    cb = np.stack([0.5 * (Bx[:, :, 1:] + Bx[:, :, :-1]), 0.5 * (By[:, 1:, :] + By[:, :-1, :]),
+                   0.5 * (Bz[1:, :, :] + Bz[:-1, :, :])], axis=-1)[g:g + n[2], g:g + n[1], g:g + n[0]].reshape(-1, 3)
+    w = H.interior(out["W"], n, g).reshape(out["W"].shape[0], -1).T
+    u = H.interior(out["U"], n, g).reshape(out["U"].shape[0], -1).T
+    ok = H.interior(out["status"], n, g).ravel() == 0
+    if not ok.any():
+        return 0.0
+    q = O.prim2con(cm[ok], w[ok, :P.nw], cb[ok], P)
+    u = u[ok]
+    err = 0.0
+    for v in range(q.shape[1]):
+        den = np.abs(u[:, 0]) if v in (0, 5) else np.maximum(np.abs(u[:, v]), np.abs(u[:, 0]) + np.abs(u[:, 4]))
+        err = max(err, float(np.max(np.abs(q[:, v] - u[:, v]) / np.maximum(den, 1e-300))))
+    return err
+
+
+def policy_cells_error(got, ref, bi):
+    """Largest relative difference of the primitives on interior cells that a floor, clamp or the
+    atmosphere set (status != 0 in the reference), denominator max(|ref|, 1e-300)."""
+    n, g = bi.n, bi.ng
+    m = H.interior(ref["status"], n, g) != 0
+    if not m.any():
+        return 0.0
+    gw, rw = H.interior(got["W"], n, g), H.interior(ref["W"], n, g)
+    return float(max(np.max(np.abs(gw[v][m] - rw[v][m]) / np.maximum(np.abs(rw[v][m]), 1e-300))
+                     for v in range(rw.shape[0])))

@@ -1,0 +1,272 @@
+"""The workloads of the benchmark configurations at their full sizes, run in the launch configuration
+`bench.py` times (launch shapes from gr_autotune), against the FP64 oracle on sampled outputs the oracle
+computes one by one (whole blocks, or single cells for con2prim).  The conserved variables, face fields
+and statuses of the FP64 path are held to the oracle's within 1e-12 (compare()'s denominators); the
+primitives are held by their backward error on regular solves (gpu_harness.backward_error: the GPU's W'
+and B' reproduce the GPU's U' through the oracle's prim2con within 1e-12) and forward on the cells a floor,
+clamp or the atmosphere set (closed forms), since on these workloads some are
+ill-conditioned functions of U' (cold gas where p is a small part of the energy, static stars whose
+velocities are rounding-sized): their forward errors are printed.
+
+* the 1D magnetised shock tube (16^3, Gamma 5/3, PLM + HLLE): 10 RK2 steps at CFL 0.4 through the driver,
+  FP64 against the oracle's driver after every step
+* the single 64^3 magnetised star (Gamma 2, WENOZ): FP64 over the whole block; the mixed path within
+  1e-6 in rho
+* the AMR-like batch (1024 blocks of 16^3 / 24^3 / 32^3 at 3 levels): FP64 on sampled blocks of every
+  size; the mixed path's rho error on them reported and bounded
+* the con2prim-heavy table workload (256 blocks of 32^3, 200 x 128 x 64 table): sampled cells' roots
+  equal the oracle's con2prim with and without the bracket proposals, statuses identical
+* the two-star workload (4096 blocks of 16^3, WENOZ): FP64 on sampled blocks (star centres, surface,
+  atmosphere); the mixed path within 1e-6 in rho on them, div B of the whole mesh at round-off"""
+import copy
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import driver as DR
+from paper_2311_04989_gb300 import grstage as G
+from paper_2311_04989_gb300 import inputs as I
+from tests import gpu_harness as GH
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_04989_gb300 import build as B
+    B.build()
+
+
+def _stage_pack(blocks, P, precision, c2p_guess=G.GR_GUESS_NONE):
+    """Stage of a batch with autotuned launch shapes (the bench's configuration); per-block outputs."""
+    import torch
+    pools = GH.Pools(blocks)
+    U = pools.cells([H.cons_from_prims(b, P) for b in blocks], 5)
+    W, B, M = pools.cells([b.W for b in blocks], 5), pools.faces([b.B for b in blocks]), pools.verts(
+        [b.metric for b in blocks])
+    Uo, Wo, Bo = U.clone(), W.clone(), [x.clone() for x in B]
+    st = torch.zeros(max(pools.L.ncell, 1), dtype=torch.uint8, device="cuda")
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    try:
+        metric = G.metric_struct(M)
+        state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+        gp = GH.gr_params_from(P, precision, c2p_guess)
+        dt = 0.25 * min(min(b.dx) for b in blocks)
+        G.gr_autotune(mesh, metric, state, dt, gp, 1, torch.cuda.current_stream())
+        G.gr_stage(mesh, metric, state, dt, gp, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        diag = G.gr_diag(mesh, list(Uo), Bo, torch.cuda.current_stream())
+    finally:
+        G.gr_mesh_destroy(mesh)
+    return pools, dict(U=Uo, W=Wo, B=Bo, st=st), dt, diag
+
+
+def _block_out(pools, out, b):
+    U = pools.unpack_cells(out["U"], 5)[b]
+    W = pools.unpack_cells(out["W"], 5)[b]
+    st = pools.unpack_cells(out["st"], 1)[b]
+    Bf = pools.unpack_faces(out["B"])[b]
+    return dict(U=U, W=W, B=Bf, status=st)
+
+
+def _check64(got, ref, bi, P, label):
+    """FP64 output of one block against the oracle's: U', B' forward, status exact, W' by backward
+    error; returns the largest number asserted on."""
+    e = GH.compare([got], [ref], blocks=[bi])
+    assert e.pop("status_mismatch") == 0, label
+    fw = {k: v for k, v in e.items() if k.startswith("W")}
+    cons = {k: v for k, v in e.items() if not k.startswith("W")}
+    be = GH.backward_error(got, bi, P)
+    pe = GH.policy_cells_error(got, ref, bi)
+    print(f"{label}: U', B' max {max(cons.values()):.1e}; W' backward {be:.1e}, on policy cells {pe:.1e}; "
+          f"W' forward " + ", ".join(f"{k} {v:.1e}" for k, v in sorted(fw.items())))
+    assert max(cons.values()) < TOL64 and be < TOL64 and pe < TOL64, (label, cons, be, pe)
+    return max(max(cons.values()), be, pe)
+
+
+def _rho_err(got, ref, bi):
+    g, r = H.interior(got["W"][0], bi.n, bi.ng), H.interior(ref["W"][0], bi.n, bi.ng)
+    return float(np.max(np.abs(g - r) / r))
+
+
+def test_shock_tube_ten_rk2_steps_through_the_driver():
+    from tests.test_gpu_driver import Run
+    bi = I.shock_tube_block(n=(16, 16, 16), g=3)
+    H.fill_outflow_x_periodic_yz(bi)
+    P = O.Params(gamma_ad=5.0 / 3.0, recon=0, rho_atm=1e-10, tol=1e-15)
+    nbr = I.block_grid_neighbours((1, 1, 1), periodic=(False, True, True))
+    ref = [copy.deepcopy(bi)]
+    Uref = [H.cons_from_prims(ref[0], P)]
+    run = Run([bi], nbr, P, U=[u.copy() for u in Uref])
+    worst = 0.0
+    try:
+        for step in range(10):
+            run.step(0.4, G.GR_DT_GRID, 2)
+            got = run.result()
+            _, st = DR.rk_step(ref, Uref, nbr, P, 0.4, order=2, dt_mode="grid")
+            worst = max(worst, _check64(got[0], dict(U=Uref[0], W=ref[0].W, B=ref[0].B, status=st[0]), bi, P,
+                                        f"shock tube step {step}"))
+    finally:
+        run.close()
+    print(f"shock tube, 10 RK2 steps at CFL 0.4: max error vs the oracle driver {worst:.2e}")
+
+
+def test_single_64cubed_star_fp64_and_mixed():
+    tov = I.solve_tov()
+    bi = I.star_block(n=(64, 64, 64), g=3, half_width=10.02, tov=tov, A_b=0.05)
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-15)
+    ref = GH.oracle_stage([bi], P, 0.25 * bi.dx[0])[0]
+    pools, out, dt, _ = _stage_pack([bi], P, G.GR_PREC_FP64)
+    _check64(_block_out(pools, out, 0), ref, bi, P, "64^3 star, FP64")
+    pools, out, dt, diag = _stage_pack([bi], P, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
+    er = _rho_err(_block_out(pools, out, 0), ref, bi)
+    print(f"64^3 star, mixed: rho error {er:.2e}, div B {diag[1]:.1e}")
+    assert er < 1e-6 and diag[1] < 1e-14
+
+
+def test_amr_like_batch_sampled_blocks():
+    blocks = I.amr_like_batch(nblocks=1024, workers=os.cpu_count() or 4)
+    P = O.Params(gamma_ad=5.0 / 3.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    sizes = [b.n[0] for b in blocks]
+    sample = sorted({sizes.index(s) for s in (16, 24, 32)} | {len(blocks) - 1, 511})
+    refs = {b: GH.oracle_stage([blocks[b]], P, 0.25 * min(min(x.dx) for x in blocks))[0] for b in sample}
+    pools, out, dt, _ = _stage_pack(blocks, P, G.GR_PREC_FP64)
+    for b in sample:
+        _check64(_block_out(pools, out, b), refs[b], blocks[b], P, f"AMR-like batch, FP64, block {b} ({sizes[b]}^3)")
+    pools, out, dt, diag = _stage_pack(blocks, P, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
+    er = max(_rho_err(_block_out(pools, out, b), refs[b], blocks[b]) for b in sample)
+    print(f"AMR-like batch, mixed: rho error on the sampled blocks {er:.2e}, div B {diag[1]:.1e}")
+    assert er < 1e-5 and diag[1] < 1e-14
+
+
+def test_table_con2prim_workload_sampled_cells():
+    import torch
+    from paper_2311_04989_gb300 import learned_bracket as LB
+    eos = I.SyntheticEOS()
+    tab = eos.table()
+    rho_atm, T_atm = 1e-12, 1e-5
+    kw = dict(rho_range=(rho_atm, 1e-3), T_range=(1e-4, 5e-2), ye_range=(0.05, 0.5), u_max=3.0,
+              sigma_range=(1e-3, 1e5), metric_amp=0.02)
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        blocks = list(ex.map(lambda k: I.random_block(n=(32, 32, 32), g=1, seed=600 + k, eos=eos, **kw), range(256)))
+        train = list(ex.map(lambda k: I.random_block(n=(16, 16, 16), g=1, seed=900 + k, eos=eos, **kw), range(16)))
+    P = O.Params(table=tab, rho_atm=rho_atm, T_atm=T_atm, tol=1e-14)
+    gp = GH.gr_params_from(P)
+    x, t = LB.collect(GH.ctx(), train, gp, device="cuda")
+    Pm, _, _ = LB.train(x, t, epochs=60, batch=2048, lr=3e-3)
+    pools = GH.Pools(blocks)
+    W, B, M = pools.cells([b.W for b in blocks], 7), pools.faces([b.B for b in blocks]), pools.verts(
+        [b.metric for b in blocks])
+    U = torch.zeros((6, W.shape[1]), dtype=torch.float64, device="cuda")
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    rng = np.random.default_rng(7)
+    picks = [(int(b), tuple(int(v) for v in rng.integers(0, 32, 3))) for b in rng.choice(256, 8, replace=False)
+             for _ in range(250)]
+    try:
+        metric = G.metric_struct(M)
+        G.gr_prim2con(mesh, metric, list(W), B, list(U), gp, torch.cuda.current_stream())
+        results = {}
+        for name, guess in (("none", G.GR_GUESS_NONE), ("fp32", G.GR_GUESS_FP32), ("mlp", G.GR_GUESS_MLP)):
+            g2 = GH.gr_params_from(P, c2p_guess=guess)
+            g2.mlp = int(Pm.data_ptr())
+            Uc, Wc = U.clone(), torch.zeros_like(W)
+            st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+            G.gr_con2prim(mesh, metric, list(Uc), B, list(Wc), st, g2, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            results[name] = (pools.unpack_cells(Wc, 7), pools.unpack_cells(st, 1))
+    finally:
+        G.gr_mesh_destroy(mesh)
+    # the oracle on the sampled cells: its own conserved variables from the same primitives
+    met, prims, Bd = [], [], []
+    cache = {}
+    for b, (i, j, k) in picks:
+        bi = blocks[b]
+        if b not in cache:
+            cache[b] = (H.cell_metric(bi), H.cell_B(bi))
+        cm, cb = cache[b]
+        met.append(cm[k + 1, j + 1, i + 1])
+        prims.append(bi.W[:, k + 1, j + 1, i + 1])
+        Bd.append(cb[k + 1, j + 1, i + 1])
+    met, prims, Bd = np.array(met), np.array(prims), np.array(Bd)
+    q = O.prim2con(met, prims, Bd, P)
+    w_ref, _, st_ref, _ = O.con2prim(met, q, Bd, P)
+    for name, (Wg, Sg) in results.items():
+        wg = np.array([Wg[b][:, k + 1, j + 1, i + 1] for b, (i, j, k) in picks])
+        sg = np.array([Sg[b][k + 1, j + 1, i + 1] for b, (i, j, k) in picks]) & 0x3F
+        assert np.array_equal(sg, st_ref), name
+        ok = st_ref == 0
+        er = float(np.max(np.abs(wg[ok, 0] - w_ref[ok, 0]) / w_ref[ok, 0]))
+        print(f"table con2prim workload, guess {name}: rho error on {int(ok.sum())} solved sampled cells {er:.2e}")
+        assert er < 1e-12, name
+
+
+def test_two_star_workload_sampled_blocks():
+    import torch
+    mi = I.BinaryStarMesh(nb=16, n=16)
+    geoms = mi.blocks()
+    L = G.Layout.of(geoms)
+    Wh, Bh, Mh = mi.pack(L)
+    W, B = torch.from_numpy(Wh).cuda(), [torch.from_numpy(x).cuda() for x in Bh]
+    M = torch.from_numpy(Mh).cuda()
+    del Wh, Bh, Mh
+    metric = G.gr_metric()
+    Mfull = [M[c] for c in range(10)] + [M[0]] * 6
+    for c in range(16):
+        metric.v[c] = int(Mfull[c].data_ptr())
+    metric.order, metric.k_zero = 2, 1
+    # sampled blocks: both star centres, a star surface block, atmosphere blocks, a corner
+    centre = lambda x: int((x + 32) // 4)
+    pick = lambda i, j, k: i + 16 * (j + 16 * k)
+    sample = [pick(centre(-20), 8, 8), pick(centre(20), 7, 7), pick(centre(20) + 2, 8, 8), pick(8, 8, 8),
+              pick(0, 0, 0), pick(15, 15, 15)]
+    out = {}
+    for prec, tol, guess in ((G.GR_PREC_FP64, 1e-15, G.GR_GUESS_NONE), (G.GR_PREC_MIXED, 1e-10, G.GR_GUESS_FP32)):
+        P = O.Params(gamma_ad=2.0, recon=1, rho_atm=mi.rho_atm, p_atm=mi.p_atm, tol=tol)
+        gp = GH.gr_params_from(P, prec, guess)
+        U = torch.zeros_like(W)
+        mesh = G.gr_mesh_create(GH.ctx(), L.descriptors())
+        try:
+            G.gr_prim2con(mesh, metric, list(W), B, list(U), gp, torch.cuda.current_stream())
+            Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
+            st = torch.zeros(L.ncell, dtype=torch.uint8, device="cuda")
+            state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+            dt = 0.25 * mi.dx
+            G.gr_autotune(mesh, metric, state, dt, gp, 1, torch.cuda.current_stream())
+            G.gr_stage(mesh, metric, state, dt, gp, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            diag = G.gr_diag(mesh, list(Uo), Bo, torch.cuda.current_stream())
+            blk = {}
+            for b in sample:
+                N = 22
+                c0 = int(L.cell_off[b])
+                cw = Wo[:, c0:c0 + N ** 3].cpu().numpy().reshape(5, N, N, N)
+                cu = Uo[:, c0:c0 + N ** 3].cpu().numpy().reshape(5, N, N, N)
+                cs = st[c0:c0 + N ** 3].cpu().numpy().reshape(N, N, N)
+                bf = []
+                for d in range(3):
+                    sh = (N + (d == 2), N + (d == 1), N + (d == 0))
+                    f0 = int(L.face_off[b, d])
+                    bf.append(Bo[d][f0:f0 + sh[0] * sh[1] * sh[2]].cpu().numpy().reshape(sh))
+                blk[b] = dict(U=cu, W=cw, B=bf, status=cs)
+            out[prec] = (blk, diag, P)
+        finally:
+            G.gr_mesh_destroy(mesh)
+    P64 = out[G.GR_PREC_FP64][2]
+    worst, er_mx = 0.0, 0.0
+    for b in sample:
+        bi = mi.block(b)
+        ref = GH.oracle_stage([bi], P64, 0.25 * mi.dx)[0]
+        worst = max(worst, _check64(out[G.GR_PREC_FP64][0][b], ref, bi, P64, f"two-star workload, FP64, block {b}"))
+        er_mx = max(er_mx, _rho_err(out[G.GR_PREC_MIXED][0][b], ref, bi))
+    diag = out[G.GR_PREC_MIXED][1]
+    print(f"two-star workload: FP64 max error on {len(sample)} sampled blocks {worst:.2e}; mixed rho error "
+          f"{er_mx:.2e}, div B {diag[1]:.1e}")
+    assert er_mx < 1e-6 and diag[1] < 1e-14
