@@ -212,11 +212,39 @@ STAGE_SOURCES = ("eos.cuh", "faces_f32.cu", "faces_f64.cu", "faces_impl.cuh", "i
                  "stage_common.cuh", "stage_kernels.cu")
 
 
+def strip_comments(src):
+    """C/C++ source with its comments removed and each line's trailing blanks dropped (string and
+    character literals kept whole), so that an edit of the comments alone keeps the hash below."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    lines = (l.rstrip() for l in "".join(out).split("\n"))
+    return "\n".join(l for l in lines if l)
+
+
 def kernel_source_hash():
+    """Hash of the stage kernels' code (comments and blank lines excluded)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2311_04989_gb300", "csrc")
     for f in STAGE_SOURCES:
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(strip_comments(open(os.path.join(d, f), encoding="utf-8").read()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

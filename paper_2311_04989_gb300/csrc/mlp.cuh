@@ -1,13 +1,13 @@
 // mlp.cuh -- the learned con2prim bracket (not in the paper: a bracket proposal for the root find of Sec. 3.5).
 //
-// A 4-64-64-1 tanh network maps features of the KKC invariants of a cell to the logarithm of the
-// master-function root mu = 1/(hW).  Con2prim starts its bracket search there and accepts a bracket
+// A 6-64-64-1 tanh network maps features of the KKC invariants of a cell (and, with a table, log D~
+// and Y_e) to the logarithm of the master-function root mu = 1/(hW).  Con2prim starts its bracket search there and accepts a bracket
 // only where the FP64 master function changes sign.
 //
 // Parameter vector (float, GR_MLP_NPARAM entries, documented in include/grstage.h):
-//   [0..3] feature means, [4..7] feature inverse standard deviations, [8] target mean,
-//   [9] target standard deviation, [10] first bracket step delta in log mu, [11..15] unused,
-//   [16..]  W1 (64 x 4), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
+//   [0..5] feature means, [6..11] feature inverse standard deviations, [12] target mean,
+//   [13] target standard deviation, [14] first bracket step delta in log mu, [15] unused,
+//   [16..]  W1 (64 x 6), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), row-major (out, in).
 #pragma once
 
 #include <cuda_runtime.h>
