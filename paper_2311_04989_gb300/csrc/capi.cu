@@ -454,6 +454,8 @@ static KParams kparams(const gr_params* p, double dt) {
   k.gamma_ad = p->gamma_ad; k.rho_atm = p->rho_atm; k.p_atm = p->p_atm; k.f_thr = p->f_thr;
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
+  k.rk_form = (p->rk_g0 != 0.0 ? RK_G0 : 0) | (p->rk_g1 != 1.0 ? RK_G1 : 0);
+  k.rho_thr = p->f_thr * p->rho_atm * (1.0 + 1e-6);
   k.dt = dt;
   k.bdt = p->rk_beta * dt;
   k.mlp = p->c2p_guess == GR_GUESS_MLP ? p->mlp : nullptr;

@@ -108,10 +108,14 @@ struct TabView {
   R x0[3], dx[3], idx[3], hi[3];   // first node, spacing, 1/spacing, last node of each axis
 };
 
+enum { RK_G0 = 1, RK_G1 = 2 };   // bits of KParams::rk_form
+
 struct KParams {   // gr_params flattened for the device
   int recon, emf, ceiling, max_iter, c2p_guess, eos;
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
+  int rk_form;        // RK_G0 | RK_G1: which of rk_g0 != 0, rk_g1 != 1 hold (set on the host)
+  double rho_thr;     // atmosphere threshold f_thr rho_atm (1 + 1e-6): within 1e-6 of it counts as reached
   double dt;
   double bdt;         // rk_beta dt
   const double* dt_dev;   // dt on the device (the RK driver's CFL reduction), or nullptr: use dt

@@ -894,7 +894,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     if (ye > yhi) { ye = yhi; ye_clamped = true; }
   }
   // atmosphere threshold; values within 1e-6 relative of it count as having reached it
-  const double rho_thr = P.f_thr * P.rho_atm * (1.0 + 1e-6);
+  const double rho_thr = P.rho_thr;
   bool atm = false, reprim = false;
   if (!finite) { st |= GR_ST_FAILED; atm = true; }
   else if (q[0] < rho_thr * M.sg) { st |= GR_ST_ATM_THRESHOLD; atm = true; }   // D~ < rho_thr

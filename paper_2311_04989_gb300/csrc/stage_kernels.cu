@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kMaxTile) k_edges(const DBlock* __restrict__ b
 // ------------------------------------------------------------------------------------------------
 // k_ct: B'^d on faces of interior cells (FP64)
 // ------------------------------------------------------------------------------------------------
-template <class R, int D>
+template <class R, int D, int RKF>
 __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const StateView& s,
                                         const Workspace& ws, const KParams& kp) {
   int p[3];
@@ -182,15 +182,28 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
   const long long vs2 = t2 == 0 ? 1 : (t2 == 1 ? (long long)(b.N[0] + 1) : (long long)(b.N[0] + 1) * (b.N[1] + 1));
   // FP64 (the B' differences must stay exact enough for div B at round-off); GB300's FP64 rate is
   // ~1/64 of FP32, so the operation count is kept minimal: curl = idx1 dE2 - idx2 dE1 by one
-  // multiply and one FMA, then B' = g1 B - beta dt curl by one FMA (no multiply when g1 = 1)
+  // multiply and one FMA, then B' = g1 B - beta dt curl by one FMA, with the RK form (RKF) fixed at
+  // compile time so that g1 = 1 and g0 = 0 cost no FP64 instruction
   const double dE2 = to64(E2[v0 + vs1]) - to64(E2[v0]);
   const double dE1 = to64(E1[v0 + vs2]) - to64(E1[v0]);
   const double curl = fma(b.idx[t1], dE2, -(b.idx[t2] * dE1));
   const long long f = b.face[D] + fix(b, D, p[0], p[1], p[2]);
   const double B = s.B[D][f];
-  double Bn = fma(-stage_bdt(kp), curl, kp.rk_g1 == 1.0 ? B : kp.rk_g1 * B);
-  if (kp.rk_g0 != 0.0) Bn = fma(kp.rk_g0, s.B0[D][f], Bn);
+  double Bn = fma(-stage_bdt(kp), curl, (RKF & RK_G1) ? kp.rk_g1 * B : B);
+  if constexpr ((RKF & RK_G0) != 0) Bn = fma(kp.rk_g0, s.B0[D][f], Bn);
   s.Bo[D][f] = Bn;
+}
+
+template <class R, int RKF>
+__device__ __forceinline__ void ct_loop(const DBlock* __restrict__ blocks, const Work* __restrict__ work, int nwork,
+                                        const StateView& s, const Workspace& ws, const KParams& kp) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const Work w = work[it];
+    const DBlock b = blocks[w.block];
+    if (w.dir == 0) ct_body<R, 0, RKF>(w, b, s, ws, kp);
+    else if (w.dir == 1) ct_body<R, 1, RKF>(w, b, s, ws, kp);
+    else ct_body<R, 2, RKF>(w, b, s, ws, kp);
+  }
 }
 
 template <class R>
@@ -198,12 +211,11 @@ __global__ void __launch_bounds__(kMaxTile) k_ct(const DBlock* __restrict__ bloc
                                                  int nwork, const __grid_constant__ StateView s,
                                                  const __grid_constant__ Workspace ws,
                                                  const __grid_constant__ KParams kp) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const Work w = work[it];
-    const DBlock b = blocks[w.block];
-    if (w.dir == 0) ct_body<R, 0>(w, b, s, ws, kp);
-    else if (w.dir == 1) ct_body<R, 1>(w, b, s, ws, kp);
-    else ct_body<R, 2>(w, b, s, ws, kp);
+  switch (kp.rk_form) {   // uniform over the grid: one branch, taken once
+    case 0: ct_loop<R, 0>(blocks, work, nwork, s, ws, kp); break;
+    case RK_G0: ct_loop<R, RK_G0>(blocks, work, nwork, s, ws, kp); break;
+    case RK_G1: ct_loop<R, RK_G1>(blocks, work, nwork, s, ws, kp); break;
+    default: ct_loop<R, RK_G0 | RK_G1>(blocks, work, nwork, s, ws, kp); break;
   }
 }
 
@@ -239,112 +251,124 @@ __device__ __forceinline__ void write_cell(const StateView& s, long long c, cons
   if (s.status) s.status[c] = (uint8_t)st;   // optional for gr_con2prim
 }
 
-// k_update, per interior cell: flux divergence + sources with FP64 accumulation.  Atmosphere cells are
-// reset here (closed form); every other cell leaves its updated conserved variables in Uo and is
-// returned as a con2prim job (the root find runs in k_c2p on the compacted job list).
+// Conserved variable v of interior cell (i, j, k) after the stage: g1 U + g0 U0 + beta dt (src - div F),
+// the face fluxes widened exactly and the sum accumulated in FP64.  Flux component of v: D, S_j, tau at
+// 0..4; D Y_e at 7 (5, 6 are the induction fluxes).
+template <class R>
+__device__ __forceinline__ double accumulate_cell(const DBlock& b, const StateView& s, const Workspace& ws,
+                                                  const KParams& kp, int i, int j, int k, long long c, int v,
+                                                  R src) {
+  const int cv = v < 5 ? v : 7;
+  const R* a0 = reinterpret_cast<const R*>(ws.flux[0]) + cv * ws.fstride[0] + b.wface[0] + fix(b, 0, i, j, k);
+  const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
+  const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
+  const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
+  const double bdt = stage_bdt(kp);
+  const double U = s.U[v][c];
+  double u = fma(bdt, to64(src), (kp.rk_form & RK_G1) ? kp.rk_g1 * U : U);
+  u -= (bdt * b.idx[0]) * (to64(a0[1]) - to64(a0[0]));
+  u -= (bdt * b.idx[1]) * (to64(a1[oy]) - to64(a1[0]));
+  u -= (bdt * b.idx[2]) * (to64(a2[oz]) - to64(a2[0]));
+  if (kp.rk_form & RK_G0) u += kp.rk_g0 * s.U0[v][c];
+  return u;
+}
+
+// U' of every conserved variable of interior cell (i, j, k): the stage-input metric (values and first
+// derivatives), primitives and mean densitised field of the input faces give the geometric sources
+// (Eq. hydsrc_def; none for D and D Y_e) in R, then accumulate_cell.  M: the cell metric, for the caller.
+template <class R, int EOS>
+__device__ __forceinline__ void update_all(const DBlock& b, const InView<R>& in, const StateView& s,
+                                           const Workspace& ws, const KParams& kp, int i, int j, int k,
+                                           long long c, double q[6], CellMet<R>& M) {
+  const bool kzero = in.k_zero != 0;
+  R val[16], dm[3][10];
+  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, dm);
+  if (!kzero) cell_metric<R>(b, in, in.order, i, j, k, 10, 16, val, nullptr);
+  cellmet_from<R>(val, kzero, M);
+  R wv[6], Bd[3];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) wv[v] = in.W[v][c];
+  wv[5] = EOS ? in.W[5][c] : R(0);
+  const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
+  const long long f2 = b.face[2] + fix(b, 2, i, j, k);
+  Bd[0] = R(0.5) * (in.B[0][f0] + in.B[0][f0 + 1]);
+  Bd[1] = R(0.5) * (in.B[1][f1] + in.B[1][f1 + b.N[0]]);
+  Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
+  CellFluid<R> fl;
+  cell_fluid<R, EOS>(M, kp, wv, Bd, fl);
+  R src[6];
+  cell_sources<R>(M, fl, dm, kzero, src);
+  src[5] = R(0);   // D Y_e has no source (Sec. 2.3)
+  constexpr int NQ = EOS ? 6 : 5;
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) q[v] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, v, src[v]);
+}
+
+// k_update, per interior cell: the stage update and the atmosphere test (Sec. 3.5, App. A).
+// Atmosphere cells are reset here (closed form); every other cell is returned as a con2prim job (the
+// root find runs in k_c2p on the compacted job list).
+// FP64 path: U' of all variables here, left in Uo for k_c2p.
+// Mixed path: D has no source, so D' and the atmosphere test need only the fluxes and sqrt(gamma) of
+// the FP32 metric (same 1e-6 band as the FP64 test); gamma_ij and sqrt(gamma) are the values
+// cellmet_from forms, so the test is the one the full metric would give.  The other variables of a
+// matter cell are formed in k_c2p (update_all), densely packed, so that this kernel carries neither the
+// metric derivatives nor the sources.
 template <class R, int EOS>
 __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, const InView<R>& in,
                                             const StateView& s, const Workspace& ws, const KParams& kp) {
   int p[3];
   if (!decode<R_INTERIOR, 0>(w, b, p)) return false;
   const int i = p[0], j = p[1], k = p[2];
-  const bool kzero = in.k_zero != 0;
-  R val[16], dm[3][10];
-  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, dm);
-  if (!kzero) cell_metric<R>(b, in, in.order, i, j, k, 10, 16, val, nullptr);
-  CellMet<R> M;
-  cellmet_from<R>(val, kzero, M);
   const long long c = b.cell + cix(b, i, j, k);
-  // stage-input state at the cell: primitives and the mean densitised field of the input faces
-  R wv[6], Bd[3];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) wv[v] = in.W[v][c];
-  wv[5] = EOS ? in.W[5][c] : R(0);
-  {
-    const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
-    const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-    Bd[0] = R(0.5) * (in.B[0][f0] + in.B[0][f0 + 1]);
-    Bd[1] = R(0.5) * (in.B[1][f1] + in.B[1][f1 + b.N[0]]);
-    Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
-  }
-  CellFluid<R> fl;
-  cell_fluid<R, EOS>(M, kp, wv, Bd, fl);
-  R src[6];
-  cell_sources<R>(M, fl, dm, kzero, src);
-  src[5] = R(0);   // D Y_e has no source (Sec. 2.3)
-  // flux divergence, accumulated in FP64 (face values widened exactly)
-  const R* F0 = reinterpret_cast<const R*>(ws.flux[0]);
-  const R* F1 = reinterpret_cast<const R*>(ws.flux[1]);
-  const R* F2 = reinterpret_cast<const R*>(ws.flux[2]);
-  const long long g0 = b.wface[0] + fix(b, 0, i, j, k);
-  const long long g1 = b.wface[1] + fix(b, 1, i, j, k);
-  const long long g2 = b.wface[2] + fix(b, 2, i, j, k);
-  const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
-  const double bdt = stage_bdt(kp);
-  const double cx = bdt * b.idx[0], cy = bdt * b.idx[1], cz = bdt * b.idx[2];
-  // flux component of conserved variable v: D, S_j, tau at 0..4; D Y_e at 7 (5, 6 are induction)
-  auto comp = [](int v) { return v < 5 ? v : 7; };
-  auto accumulate = [&](int v) {
-    const R* a0 = F0 + comp(v) * ws.fstride[0];
-    const R* a1 = F1 + comp(v) * ws.fstride[1];
-    const R* a2 = F2 + comp(v) * ws.fstride[2];
-    const double U = s.U[v][c];
-    double u = fma(bdt, to64(src[v]), kp.rk_g1 == 1.0 ? U : kp.rk_g1 * U);
-    u -= cx * (to64(a0[g0 + 1]) - to64(a0[g0]));
-    u -= cy * (to64(a1[g1 + oy]) - to64(a1[g1]));
-    u -= cz * (to64(a2[g2 + oz]) - to64(a2[g2]));
-    if (kp.rk_g0 != 0.0) u += kp.rk_g0 * s.U0[v][c];
-    return u;
-  };
   constexpr int NQ = EOS ? 6 : 5;
-  double q[6], Bn[3], wn[7];
-  q[0] = accumulate(0);
-  if (sizeof(R) == sizeof(float)) {
-    // Mixed path: take the atmosphere test (Sec. 3.5, App. A) on D' with the FP32 metric's
-    // sqrt(gamma) (same 1e-6 band as the FP64 test) and reset such cells without forming S', tau'
-    // in FP64.
-    const double sg32 = to64(M.sg);
-    const double thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
-    if (isfinite(q[0]) && q[0] < thr * sg32) {
-      bool finite = true;
+  double q[6], wn[7];
+  if constexpr (sizeof(R) == sizeof(float)) {
+    R gv[10];
+    cell_metric<R>(b, in, in.order, i, j, k, 4, 10, gv, nullptr);
+    const R* gam = gv + 4;
+    const R sg = rsqrt_(det3(gam));
+    q[0] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, 0, R(0));
+    const double sg32 = to64(sg);
+    if (!(isfinite(q[0]) && q[0] < kp.rho_thr * sg32)) return true;
+    // atmosphere: failed instead if any other variable's update is not finite
+    bool finite = true;
 #pragma unroll
-      for (int v = 1; v < NQ; ++v) {
-        const R* a0 = F0 + comp(v) * ws.fstride[0];
-        const R* a1 = F1 + comp(v) * ws.fstride[1];
-        const R* a2 = F2 + comp(v) * ws.fstride[2];
-        const R t = a0[g0 + 1] - a0[g0] + a1[g1 + oy] - a1[g1] + a2[g2 + oz] - a2[g2] + src[v];
-        finite = finite && isfinite(t) && isfinite(s.U[v][c]);
-      }
-      // the cell field of the updated faces in FP32 (the reset needs only calB^2 in FP32)
-      R Bf[3], Bl[3];
-      {
-        const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
-        const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-        Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
-        Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + b.N[0]])));
-        Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + (long long)b.N[0] * b.N[1]])));
-      }
-      lower3(M.g, Bf, Bl);
-      const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
-      q[0] = sg32 * kp.rho_atm;
-      q[1] = q[2] = q[3] = 0.0;
-      q[4] = sg32 * kp.eint_atm + to64(R(0.5) * rdiv(BBd, M.sg));
-      wn[0] = kp.rho_atm;
-      wn[1] = wn[2] = wn[3] = 0.0;
-      wn[4] = kp.p_atm;
-      if constexpr (EOS == GR_EOS_TABLE) {
-        q[5] = q[0] * kp.Ye_atm;
-        wn[5] = kp.Ye_atm;
-        wn[6] = kp.T_atm;
-      }
-      write_cell<EOS>(s, c, q, wn, finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED);
-      return false;
+    for (int v = 1; v < NQ; ++v) {
+      const int cv = v < 5 ? v : 7;
+      const R* a0 = reinterpret_cast<const R*>(ws.flux[0]) + cv * ws.fstride[0] + b.wface[0] + fix(b, 0, i, j, k);
+      const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
+      const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
+      const R t = a0[1] - a0[0] + a1[b.N[0]] - a1[0] + a2[(long long)b.N[0] * b.N[1]] - a2[0];
+      finite = finite && isfinite(t) && isfinite(s.U[v][c]);
     }
-#pragma unroll
-    for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
+    // the cell field of the updated faces in FP32 (the reset needs only calB^2 in FP32)
+    R Bf[3], Bl[3];
+    {
+      const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
+      const long long f2 = b.face[2] + fix(b, 2, i, j, k);
+      Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
+      Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + b.N[0]])));
+      Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + (long long)b.N[0] * b.N[1]])));
+    }
+    lower3(gam, Bf, Bl);
+    const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
+    q[0] = sg32 * kp.rho_atm;
+    q[1] = q[2] = q[3] = 0.0;
+    q[4] = sg32 * kp.eint_atm + to64(R(0.5) * rdiv(BBd, sg));
+    wn[0] = kp.rho_atm;
+    wn[1] = wn[2] = wn[3] = 0.0;
+    wn[4] = kp.p_atm;
+    if constexpr (EOS == GR_EOS_TABLE) {
+      q[5] = q[0] * kp.Ye_atm;
+      wn[5] = kp.Ye_atm;
+      wn[6] = kp.T_atm;
+    }
+    write_cell<EOS>(s, c, q, wn, finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED);
+    return false;
   } else {
-#pragma unroll
-    for (int v = 1; v < NQ; ++v) q[v] = accumulate(v);
+    CellMet<R> M;
+    update_all<R, EOS>(b, in, s, ws, kp, i, j, k, c, q, M);
+    double Bn[3];
     cell_field(b, s.Bo, i, j, k, Bn);
     // FP64 path: the atmosphere test of con2prim (the same operations, on the same FP64 metric that
     // k_c2p interpolates), decided here for finite cells
@@ -356,16 +380,15 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
     bool finite = isfinite(Bn[0]) && isfinite(Bn[1]) && isfinite(Bn[2]);
 #pragma unroll
     for (int v = 0; v < NQ; ++v) finite = finite && isfinite(q[v]);
-    const double rho_thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
-    if (finite && q[0] < rho_thr * Mc.sg) {
+    if (finite && q[0] < kp.rho_thr * Mc.sg) {
       atm_cell<EOS>(Mc, kp, Bn, q, wn);
       write_cell<EOS>(s, c, q, wn, GR_ST_ATM_THRESHOLD);
       return false;
     }
-  }
 #pragma unroll
-  for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
-  return true;
+    for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
+    return true;
+  }
 }
 
 template <class R, int EOS>
@@ -389,8 +412,11 @@ __global__ void __launch_bounds__(kMaxTile) k_update(const DBlock* __restrict__ 
 
 // k_c2p: FP64 con2prim (Sec. 3.5, App. A) of the queued cells, packed densely into warps whatever the
 // pattern of atmosphere and matter cells: thread t of the grid takes jobs t, t + grid size, ...
-template <int EOS>
+// R = float (the mixed stage): the cell's U' is formed here first (update_all on the FP32 inputs);
+// R = double: U' is read from Uo (left there by k_update or by the caller of gr_con2prim).
+template <int EOS, class R = double>
 __global__ void __launch_bounds__(kMaxTile) k_c2p(const DBlock* __restrict__ blocks,
+                                                  const __grid_constant__ InView<R> in,
                                                   const __grid_constant__ InView<double> in64,
                                                   const __grid_constant__ StateView s,
                                                   const __grid_constant__ Workspace ws,
@@ -405,8 +431,13 @@ __global__ void __launch_bounds__(kMaxTile) k_c2p(const DBlock* __restrict__ blo
     constexpr int NQ = EOS ? 6 : 5;
     double q[6], Bn[3], wn[7];
     q[5] = 0.0;
+    if constexpr (sizeof(R) == sizeof(float)) {
+      CellMet<R> M32;
+      update_all<R, EOS>(b, in, s, ws, kp, i, j, k, c, q, M32);
+    } else {
 #pragma unroll
-    for (int v = 0; v < NQ; ++v) q[v] = s.Uo[v][c];
+      for (int v = 0; v < NQ; ++v) q[v] = s.Uo[v][c];
+    }
     cell_field(b, s.Bo, i, j, k, Bn);
     C2PMet M;
     cell_gamma64(b, in64, i, j, k, M);
@@ -477,7 +508,7 @@ __global__ void __launch_bounds__(kTile) k_con2prim_prep(const DBlock* __restric
     cell_field(b, s.Bo, p[0], p[1], p[2], Bd);
     bool finite = isfinite(Bd[0]) && isfinite(Bd[1]) && isfinite(Bd[2]);
     for (int v = 0; v < NQ; ++v) finite = finite && isfinite(q[v]);
-    const double rho_thr = kp.f_thr * kp.rho_atm * (1.0 + 1e-6);
+    const double rho_thr = kp.rho_thr;
     if (finite && q[0] < rho_thr * M.sg) {
       atm_cell<EOS>(M, kp, Bd, q, wn);
       write_cell<EOS>(s, c, q, wn, GR_ST_ATM_THRESHOLD);
@@ -654,7 +685,7 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
   if (q.nwork) {
     KLaunch qq = q;
     qq.nwork = (q.nwork + q.threads - 1) / q.threads;   // q.nwork = the number of interior cells
-    k_c2p<EOS><<<stage_grid(k_c2p<EOS>, qq, 0), q.threads, 0, st>>>(blocks, in64, s, ws, kp);
+    k_c2p<EOS, R><<<stage_grid(k_c2p<EOS, R>, qq, 0), q.threads, 0, st>>>(blocks, in, in64, s, ws, kp);
   }
   if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();
@@ -712,10 +743,10 @@ cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, i
   const int grid2 = (ninterior + kTile - 1) / kTile;
   if (kp.eos == GR_EOS_TABLE) {
     k_con2prim_prep<GR_EOS_TABLE><<<nwork, kTile, 0, st>>>(blocks, work, in64, s, ws, kp);
-    k_c2p<GR_EOS_TABLE><<<grid2, kTile, 0, st>>>(blocks, in64, s, ws, kp);
+    k_c2p<GR_EOS_TABLE><<<grid2, kTile, 0, st>>>(blocks, in64, in64, s, ws, kp);
   } else {
     k_con2prim_prep<GR_EOS_IDEAL><<<nwork, kTile, 0, st>>>(blocks, work, in64, s, ws, kp);
-    k_c2p<GR_EOS_IDEAL><<<grid2, kTile, 0, st>>>(blocks, in64, s, ws, kp);
+    k_c2p<GR_EOS_IDEAL><<<grid2, kTile, 0, st>>>(blocks, in64, in64, s, ws, kp);
   }
   return cudaGetLastError();
 }
