@@ -382,6 +382,21 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
         m->tn[t][order][kind] = (int)L.size();
       }
   for (int kind = 0; kind < R_NREGION; ++kind) m->d_work[kind] = m->tw[t128][0][kind];
+  // k_cellprep sweep tiles: the x-y cell plane of each block in tiles of TX <= 32 columns (equal
+  // shares of N0) by TY = kSweepThreads / TX rows
+  std::vector<SweepWork> sw;
+  for (int b = 0; b < nblocks; ++b) {
+    const DBlock& d = m->h_blocks[b];
+    const int nxt = (d.N[0] + 31) / 32;
+    const int TX = (d.N[0] + nxt - 1) / nxt, TY = kSweepThreads / TX;
+    if ((TX + 1) * (TY + 1) > kSweepVerts) { e = cudaErrorInvalidValue; break; }
+    for (int y0 = 0; y0 < d.N[1]; y0 += TY)
+      for (int x0 = 0; x0 < d.N[0]; x0 += TX) sw.push_back(SweepWork{b, x0, y0, TX | (TY << 16)});
+  }
+  if (e == cudaSuccess) e = dalloc(sizeof(SweepWork) * std::max<size_t>(1, sw.size()), (void**)&m->ws.sweep);
+  if (e == cudaSuccess && !sw.empty())
+    e = cudaMemcpy((void*)m->ws.sweep, sw.data(), sizeof(SweepWork) * sw.size(), cudaMemcpyHostToDevice);
+  m->ws.nsweep = (int)sw.size();
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
     e = dalloc(sizeof(double) * wcell, &m->ws.bcc[a]);
     if (e == cudaSuccess) e = dalloc(sizeof(double) * wcell, &m->ws.ecc[a]);

@@ -76,6 +76,14 @@ struct Shadow {
   long long ncell, nface[3], nvert;   // pool extents in elements
 };
 
+// k_cellprep sweep (order-2 metric): a TX x TY tile of the x-y cell plane of one block, swept along z;
+// txy = TX | TY << 16 with TX <= 32, TX * TY <= kSweepThreads, (TX + 1)(TY + 1) <= kSweepVerts
+constexpr int kSweepThreads = 256;
+constexpr int kSweepVerts = 344;
+struct SweepWork {
+  int block, x0, y0, txy;
+};
+
 // Level-boundary records (same layouts as gr_level_face / gr_level_map)
 struct LevelFace {
   int coarse, fine, dir, side, o1, o2;
@@ -95,6 +103,8 @@ struct Workspace {
   long long estride;
   const LevelFace* lvl;   // level-boundary faces whose coarse fluxes / EMFs the stage corrects
   int nlvl;
+  const SweepWork* sweep;  // k_cellprep sweep tiles of all blocks (order-2 metric)
+  int nsweep;
   int* njobs;          // con2prim job list: cells (block, interior index) that need the root find
   int2* jobs;
 };

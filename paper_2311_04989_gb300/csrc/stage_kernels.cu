@@ -58,21 +58,12 @@ __global__ void __launch_bounds__(256) k_cast(const __grid_constant__ CastList L
 }
 
 // ------------------------------------------------------------------------------------------------
-// k_cellprep<R>
+// k_cellprep<R>: undensitised cell field calB^i = mean of the face values / sqrt(gamma) on every cell,
+// and the cell-centred electric field E_m = alpha (vt x calB)_m on cells -1..n (the EMF input)
 // ------------------------------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void cellprep_body(const Work& w, const DBlock& b, const InView<R>& in,
-                                              const Workspace& ws) {
-  int p[3];
-  if (!decode<R_CELLS_ALL, 0>(w, b, p)) return;
-  const int i = p[0], j = p[1], k = p[2];
-  if (in.order == 4) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (p[a] < -b.g + 1 || p[a] > b.n[a] + b.g - 2) return;
-  }
-  R val[10];
-  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, nullptr);
+__device__ __forceinline__ void cellprep_cell(const DBlock& b, const InView<R>& in, const Workspace& ws, int i,
+                                              int j, int k, const R val[10]) {
   const R* g6 = val + 4;
   const R sg = rsqrt_(det3(g6));
   R Bd[3];
@@ -103,6 +94,21 @@ __device__ __forceinline__ void cellprep_body(const Work& w, const DBlock& b, co
   }
 }
 
+template <class R>
+__device__ __forceinline__ void cellprep_body(const Work& w, const DBlock& b, const InView<R>& in,
+                                              const Workspace& ws) {
+  int p[3];
+  if (!decode<R_CELLS_ALL, 0>(w, b, p)) return;
+  if (in.order == 4) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (p[a] < -b.g + 1 || p[a] > b.n[a] + b.g - 2) return;
+  }
+  R val[10];
+  cell_metric<R>(b, in, in.order, p[0], p[1], p[2], 0, 10, val, nullptr);
+  cellprep_cell<R>(b, in, ws, p[0], p[1], p[2], val);
+}
+
 // Every stage kernel strides over its work list (one work item per CTA and pass): launched with one CTA
 // per item, or persistent with as many CTAs as fit on the GPU.  The CTA size equals the work-item size.
 template <class R>
@@ -113,6 +119,102 @@ __global__ void __launch_bounds__(kMaxTile) k_cellprep(const DBlock* __restrict_
     const Work w = work[it];
     cellprep_body<R>(w, blocks[w.block], in, ws);
   }
+}
+
+// k_cellprep_sweep<R> (order-2 metric): the same outputs, bitwise, with each vertex of the metric read
+// from memory once per tile instead of by each of its eight cells.  One CTA per SweepWork tile walks the
+// block along z; the vertex planes z and z + 1 of the tile (with its +1 halo in x and y) sit in shared
+// memory (cp.async, two buffers), and each thread carries the 2 x 2 plane sums of its cell column from one
+// cell to the next: the cell value is 1/8 ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) in the
+// order cell_metric sums it, the first bracket being the previous cell's second.
+template <class R>
+__device__ __forceinline__ void sweep_copy(R* dst, const R* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(R)) : "memory");
+}
+__device__ __forceinline__ void sweep_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void sweep_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <class R>
+__global__ void __launch_bounds__(kSweepThreads) k_cellprep_sweep(const DBlock* __restrict__ blocks,
+                                                                  const SweepWork* __restrict__ work,
+                                                                  const __grid_constant__ InView<R> in,
+                                                                  const __grid_constant__ Workspace ws) {
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
+  R* sm = reinterpret_cast<R*>(sweep_smem);   // [buffer 2][component 10][kSweepVerts]
+  const SweepWork w = work[blockIdx.x];
+  const DBlock b = blocks[w.block];
+  const int TX = w.txy & 0xFFFF, TY = w.txy >> 16;
+  const int VX = TX + 1, NV = VX * (TY + 1);
+  const int tx = (int)threadIdx.x % TX, ty = (int)threadIdx.x / TX;
+  const bool act = ty < TY && w.x0 + tx < b.N[0] && w.y0 + ty < b.N[1];
+  const int i = w.x0 + tx - b.g, j = w.y0 + ty - b.g;
+  // the (at most two) tile vertices this thread copies: offsets within a vertex plane, or -1
+  const long long VP = (long long)(b.N[0] + 1) * (b.N[1] + 1);
+  long long voff[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int t = (int)threadIdx.x + m * kSweepThreads;
+    const int X = w.x0 + t % VX, Y = w.y0 + t / VX;
+    voff[m] = (t < NV && X <= b.N[0] && Y <= b.N[1]) ? (long long)Y * (b.N[0] + 1) + X : -1;
+  }
+  auto load_plane = [&](int kv, int buf) {   // vertex plane kv (0..N2) into buffer buf, one commit group
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+      if (voff[m] >= 0) {
+        const long long vi = b.vert + kv * VP + voff[m];
+        const int t = (int)threadIdx.x + m * kSweepThreads;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) sweep_copy<R>(sm + (buf * 10 + c) * kSweepVerts + t, in.M[c] + vi);
+      }
+    sweep_commit();
+  };
+  auto plane_sum = [&](int buf, R S[10]) {   // (f(i,j) + f(i+1,j)) + (f(i,j+1) + f(i+1,j+1))
+    const int o = ty * VX + tx;
+#pragma unroll
+    for (int c = 0; c < 10; ++c) {
+      const R* a = sm + (buf * 10 + c) * kSweepVerts + o;
+      S[c] = (a[0] + a[1]) + (a[VX] + a[VX + 1]);
+    }
+  };
+  const int N2 = b.N[2];
+  load_plane(0, 0);
+  load_plane(1, 1);
+  sweep_wait1();
+  __syncthreads();
+  R S0[10], S1[10];
+  if (act) plane_sum(0, S0);
+  for (int kc = 0; kc < N2; ++kc) {
+    __syncthreads();   // every thread is done with buffer kc & 1 (plane kc)
+    if (kc + 2 <= N2) load_plane(kc + 2, kc & 1);
+    else sweep_commit();   // an empty group keeps wait_group 1 meaning "plane kc + 1 has landed"
+    sweep_wait1();
+    __syncthreads();
+    if (act) {
+      plane_sum((kc + 1) & 1, S1);
+      R val[10];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) {
+        val[c] = R(0.125) * (S0[c] + S1[c]);
+        S0[c] = S1[c];
+      }
+      cellprep_cell<R>(b, in, ws, i, j, kc - b.g, val);
+    }
+  }
+}
+
+template <class R>
+static cudaError_t launch_cellprep_sweep(const DBlock* blocks, const InView<R>& in, const Workspace& ws,
+                                         cudaStream_t st) {
+  constexpr size_t smem = sizeof(R) * 2 * 10 * kSweepVerts;
+  static bool attr = false;
+  if (!attr && smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_cellprep_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_cellprep_sweep<R><<<ws.nsweep, kSweepThreads, smem, st>>>(blocks, ws.sweep, in, ws);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -654,7 +756,12 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
                               const InView<double>& in64, const StateView& s, const Workspace& ws, const KParams& kp,
                               cudaStream_t st, cudaEvent_t* ev) {
   const KLaunch& a = kl[SK_CELLPREP];
-  if (a.nwork) k_cellprep<R><<<stage_grid(k_cellprep<R>, a, 0), a.threads, 0, st>>>(blocks, a.work, a.nwork, in, ws);
+  if (in.order == 2 && ws.nsweep) {   // the order-2 metric: the z sweep (same results, any launch shape)
+    const cudaError_t es = launch_cellprep_sweep<R>(blocks, in, ws, st);
+    if (es != cudaSuccess) return es;
+  } else if (a.nwork) {
+    k_cellprep<R><<<stage_grid(k_cellprep<R>, a, 0), a.threads, 0, st>>>(blocks, a.work, a.nwork, in, ws);
+  }
   if (ev) cudaEventRecord(ev[2], st);
   const KLaunch& f = kl[SK_FACES];
   if (f.nwork) {

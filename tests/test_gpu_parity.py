@@ -67,6 +67,19 @@ def test_batch_of_uneven_blocks_fp64_parity():
     check64(GH.gpu_stage(blocks, P, dt), GH.oracle_stage(blocks, P, dt), blocks)
 
 
+def test_cellprep_sweep_tilings_fp64_parity():
+    """The order-2 cell preparation walks each block along z in tiles of its x-y cell plane (at most 32
+    columns, 256 cells): two x tiles of 23 (N0 = 46) with a ragged y tile, x tiles of 20 and 19 (N0 = 39)
+    with ragged y tiles, and a thin block of one 7-column tile (N0 = 7)."""
+    sizes = [(40, 6, 5), (33, 9, 3), (1, 20, 4)]
+    fields = I.make_fields(np.random.default_rng(6), 1.0, shared_metric=True)
+    blocks = [I.random_block(n=s, g=3, x0=(0.1 * k, 0.05, 0.2), dx=(1 / 64,) * 3, seed=31, fields=fields)
+              for k, s in enumerate(sizes)]
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-14, tol=1e-15)
+    dt = 0.2 / 64
+    check64(GH.gpu_stage(blocks, P, dt), GH.oracle_stage(blocks, P, dt), blocks)
+
+
 def test_shock_tube_block_fp64_parity():
     """The 1D magnetised shock tube on a 16^3 block (Gamma 5/3, PLM), first stage."""
     bi = I.shock_tube_block(n=(16, 16, 16), g=3)
