@@ -20,7 +20,7 @@
  *       y-/z-face arrays likewise with the extra point along y / z
  *       vertex arrays    (nz+2g+1) x (ny+2g+1) x (nx+2g+1) vertex i in [-g, n+g]
  *   - Primitives w = (rho, u~^x, u~^y, u~^z, p); conserved q = (D, S_x, S_y, S_z, tau); B^i is the
- *     densitised face field sqrt(gamma) calB^i.  With a tabulated EOS (Sec. 2.3) the primitives are
+ *     densitised face field sqrt(gamma) calB^i.  With a tabulated EOS (Sec. 2.2.1) the primitives are
  *     (rho, u~^i, p, Y_e, T) and the conserved variables (D, S_j, tau, D Y_e): the thermodynamic state
  *     of a point is (rho, p, Y_e), and T is an output (written by con2prim, never read).  Metric components in the order
  *     alpha, beta^x, beta^y, beta^z, gamma_xx, gamma_xy, gamma_xz, gamma_yy, gamma_yz, gamma_zz,
@@ -54,7 +54,7 @@ enum { GR_RECON_PLM = 0, GR_RECON_WENOZ = 1, GR_RECON_WENO5 = 2, GR_RECON_PPM = 
 enum { GR_PREC_FP64 = 0, GR_PREC_MIXED = 1 };           /* mixed: FP32 reconstruction/HLLE/EMF */
 enum { GR_EMF_UPWIND = 0, GR_EMF_MEAN = 1 };            /* Sec. 3.3 corner electric field */
 enum { GR_CEIL_CLAMP = 0, GR_CEIL_ATMOSPHERE = 1 };     /* App. A clamp, or Sec. 3.5 reset */
-enum { GR_EOS_IDEAL = 0, GR_EOS_TABLE = 1 };            /* Sec. 2.3 */
+enum { GR_EOS_IDEAL = 0, GR_EOS_TABLE = 1 };            /* Sec. 2.2.1 */
 
 /* con2prim status bits (per cell, uint8) */
 #define GR_ST_ATM_THRESHOLD 0x01  /* rho or D below f_thr rho_atm -> atmosphere (Sec. 3.5, App. A) */
@@ -103,7 +103,7 @@ typedef struct {
   uint8_t* status;
 } gr_state;
 
-/* Tabulated EOS (Sec. 2.3): log p, log e (e = rho (1 + eps), the total energy density) and c_s^2 on a
+/* Tabulated EOS (Sec. 2.2.1): log p, log e (e = rho (1 + eps), the total energy density) and c_s^2 on a
  * uniform grid in (log rho, log T, Y_e), natural logarithms; node (ir, iT, iy) of each host array at
  * index (iy * n[1] + iT) * n[0] + ir.  The library interpolates trilinearly in those variables; log p
  * and log e must increase strictly with T along every node column (the temperature is recovered by
@@ -129,7 +129,7 @@ typedef struct {
   int32_t ceiling;      /* GR_CEIL_* */
   int32_t max_iter;     /* root-find iteration cap */
   int32_t c2p_guess;    /* GR_GUESS_*: bracket proposal for con2prim */
-  double gamma_ad;      /* ideal gas p = rho eps (Gamma - 1), Sec. 2.3 */
+  double gamma_ad;      /* ideal gas p = rho eps (Gamma - 1), Sec. 2.2.1 */
   double rho_atm;       /* f_atm rho_max (Sec. 3.5) */
   double p_atm;         /* p(rho_atm) */
   double f_thr;         /* atmosphere threshold factor */

@@ -95,13 +95,13 @@ def table_hmin(tab) -> float:
 class Params:
     """Physical and numerical parameters of the stage (names follow the paper)."""
     gamma_ad: float = 2.0
-    rho_atm: float = 1e-13          # f_atm * rho_max   (Sec. 3.6)
+    rho_atm: float = 1e-13          # f_atm * rho_max   (Sec. 3.5)
     p_atm: float | None = None      # p(rho_atm); None -> K rho_atm^Gamma
-    K_poly: float = 100.0           # polytropic K used for p_atm (Sec. 2.3)
-    f_thr: float = 1.0              # Sec. 3.6
-    W_max: float = float(np.sqrt(1.0 + 20.0 ** 2))   # u~ <= 20 (Sec. 3.6)
+    K_poly: float = 100.0           # polytropic K used for p_atm (Sec. 2.2.1)
+    f_thr: float = 1.0              # Sec. 3.5
+    W_max: float = float(np.sqrt(1.0 + 20.0 ** 2))   # u~ <= 20 (Sec. 3.5)
     M_max: float = 1e4              # B^2/D ceiling (App. A; value is a reading)
-    tol: float = 1e-10              # bracketing tolerance (Sec. 3.6)
+    tol: float = 1e-10              # bracketing tolerance (Sec. 3.5)
     weno_eps: float = 1e-40
     rk_g0: float = 0.0
     rk_g1: float = 1.0
@@ -111,7 +111,7 @@ class Params:
     emf: int = 0                    # 0 upwinded corner average, 1 plain mean
     ceiling: int = 0                # 0 clamp W, 1 atmosphere
     interp_order: int = 2
-    table: object = None            # EOS table (Sec. 2.3); None -> ideal gas
+    table: object = None            # EOS table (Sec. 2.2.1); None -> ideal gas
     T_atm: float = 1e-6             # atmosphere temperature (table)
     Ye_atm: float = 0.5             # atmosphere electron fraction (table)
 
@@ -461,7 +461,7 @@ def mlp_loss_grad(P, x, t):
 
 
 # ---------------------------------------------------------------------------------------------
-# tabulated EOS lookups (Sec. 2.3)
+# tabulated EOS lookups (Sec. 2.2.1)
 # ---------------------------------------------------------------------------------------------
 def table_eval(P: Params, rho, T, ye):
     """(p, eps, c_s^2) at (rho, T, Y_e) from the table and the temperature recovered from (rho, p, Y_e)."""

@@ -14,7 +14,7 @@
 //   metric components: 0 alpha, 1..3 beta^i, 4..9 gamma_{xx,xy,xz,yy,yz,zz}, 10..15 K_ij (same order)
 //   primitives w = (rho, u~^x, u~^y, u~^z, p)                      (Sec. 2.1, after Eq. hydsrc_def)
 //   conserved  q = (D, S_x, S_y, S_z, tau), B^k densitised          (Eq. consB_def)
-//   tabulated EOS (Sec. 2.3): w = (rho, u~^i, p, Y_e, T), q = (D, S_j, tau, D Y_e); the thermodynamic
+//   tabulated EOS (Sec. 2.2.1): w = (rho, u~^i, p, Y_e, T), q = (D, S_j, tau, D Y_e); the thermodynamic
 //   state of a point is (rho, p, Y_e), T is derived from it (an output of con2prim).
 //
 // Functions whose result has no independent pin say "parity unpinned" in their comment; the pins
@@ -47,22 +47,22 @@ typedef struct {
 } ob_geom;
 
 typedef struct {
-  double gamma_ad;   // ideal-gas Gamma, p = rho*eps*(Gamma-1)  (Sec. 2.3)
-  double rho_atm;    // atmosphere density f_atm*rho_max        (Sec. 3.6)
-  double p_atm;      // atmosphere pressure p(rho_atm)           (Sec. 3.6)
-  double f_thr;      // atmosphere threshold factor              (Sec. 3.6)
+  double gamma_ad;   // ideal-gas Gamma, p = rho*eps*(Gamma-1)  (Sec. 2.2.1)
+  double rho_atm;    // atmosphere density f_atm*rho_max        (Sec. 3.5)
+  double p_atm;      // atmosphere pressure p(rho_atm)           (Sec. 3.5)
+  double f_thr;      // atmosphere threshold factor              (Sec. 3.5)
   double W_max;      // Lorentz-factor ceiling                   (App. A)
   double M_max;      // B^2/D ceiling                            (App. A)
-  double tol;        // relative bracket tolerance of the root find (Sec. 3.6: 1e-10)
+  double tol;        // relative bracket tolerance of the root find (Sec. 3.5: 1e-10)
   double weno_eps;   // WENOZ epsilon
   double rk_g0, rk_g1, rk_beta;  // stage U' = g0 U0 + g1 U + beta dt L(U)
   int32_t max_iter;  // root-find iteration cap
   int32_t recon;     // 0 PLM, 1 WENOZ, 2 WENO5, 3 PPM
   int32_t emf;       // 0 upwinded corner average (Gardiner-Stone), 1 plain mean of 4 faces
-  int32_t ceiling;   // 0 clamp W (App. A), 1 atmosphere (Sec. 3.6)
+  int32_t ceiling;   // 0 clamp W (App. A), 1 atmosphere (Sec. 3.5)
   int32_t interp_order;  // 2 or 4
   int32_t pad_;
-  // tabulated EOS (Sec. 2.3); eos = 0 ideal gas (the fields below unused), 1 table
+  // tabulated EOS (Sec. 2.2.1); eos = 0 ideal gas (the fields below unused), 1 table
   int32_t eos;
   int32_t pad2_;
   double T_atm;      // atmosphere temperature (App. A)
@@ -71,7 +71,7 @@ typedef struct {
   const struct otable_* table;
 } oparams;
 
-// EOS table (Sec. 2.3): log p, log e (e = rho(1 + eps)) and c_s^2 on a uniform grid in
+// EOS table (Sec. 2.2.1): log p, log e (e = rho(1 + eps)) and c_s^2 on a uniform grid in
 // (log rho, log T, Y_e), natural logarithms (the base does not change a linear interpolant).
 typedef struct otable_ {
   int32_t n[3];       // nodes along log rho, log T, Y_e
@@ -158,7 +158,7 @@ void pm_from16(const real m[16], PM& P) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Ideal-gas EOS, p = rho*eps*(Gamma - 1)  (Sec. 2.3).  Minimum enthalpy h0 = 1, eps >= 0.
+// Ideal-gas EOS, p = rho*eps*(Gamma - 1)  (Sec. 2.2.1).  Minimum enthalpy h0 = 1, eps >= 0.
 // ------------------------------------------------------------------------------------------------
 inline real eos_eps(const oparams& Q, real rho, real p) { return p / ((Q.gamma_ad - 1) * rho); }
 inline real eos_p(const oparams& Q, real rho, real eps) { return (Q.gamma_ad - 1) * rho * eps; }
@@ -166,7 +166,7 @@ inline real eos_p(const oparams& Q, real rho, real eps) { return (Q.gamma_ad - 1
 inline real eos_cs2(const oparams& Q, real rho, real p, real h) { return Q.gamma_ad * p / (rho * h); }
 
 // ------------------------------------------------------------------------------------------------
-// Tabulated EOS (Sec. 2.3): trilinear interpolation of log p, log e and c_s^2 in (log rho, log T,
+// Tabulated EOS (Sec. 2.2.1): trilinear interpolation of log p, log e and c_s^2 in (log rho, log T,
 // Y_e).  The interpolation is written for the specific quantities log(p/rho) = log p - log rho and
 // log(e/rho) = log(1 + eps): log rho is linear along its axis, so their interpolants are exactly the
 // interpolants of log p and log e minus log rho, while their values stay O(1) (no loss of eps to
@@ -344,7 +344,7 @@ void cons_from_fp(const PM& M, const FP& F, real q[5]) {
   for (int j = 0; j < 3; ++j) q[1 + j] = sg * (eb * F.W * F.ut_d[j] - ab0 * F.b_d[j]);
   q[4] = sg * (eb * F.W * F.W - F.rho * F.W - (F.p + 0.5 * F.b2) - ab0 * ab0);
 }
-// All conserved variables of the EOS: with a table also D Y_e (Sec. 2.3)
+// All conserved variables of the EOS: with a table also D Y_e (Sec. 2.2.1)
 void cons_all(const oparams& Q, const PM& M, const FP& F, real q[]) {
   cons_from_fp(M, F, q);
   if (Q.eos) q[5] = q[0] * F.ye;
@@ -364,7 +364,7 @@ void flux_from_fp(const PM& M, const FP& F, const real q[5], int d, real Fq[5], 
   Fb[1] = a * (F.Bd_u[t2] * F.vt_u[d] - F.Bd_u[d] * F.vt_u[t2]);
 }
 
-// Fast speeds along d (reading c2 of the "approximate quadratic dispersion relation" of Sec. 2.2):
+// Fast speeds along d (reading c2 of the approximate quadratic dispersion relation of Sec. 2.2):
 // c^2 = cs^2 + cA^2 - cs^2 cA^2, cA^2 = b^2/(rho h + b^2), and the 3+1 closed form
 // lam = alpha [v^d (1-c^2) +- c sqrt((1-v^2)(gamma^dd (1 - v^2 c^2) - v^d v^d (1-c^2)))]/(1-v^2c^2) - beta^d
 void speeds_from_fp(const PM& M, const oparams& Q, const FP& F, int d, real* lm, real* lp) {
@@ -401,7 +401,7 @@ void hlle(int nv, const real* UL, const real* UR, const real* FL, const real* FR
 // Face flux from two primitive states at one face (shared by the stage and the point entry).
 // wL/wR: prims; BL/BR: densitised B^i of the two states (same normal component).  With a table,
 // Fq[5] is the D Y_e flux: the HLLE D flux times the electron fraction of the upwind state (the
-// D equation multiplied by Y_e, Sec. 2.3; reading: upwinded as in the consistent multi-fluid
+// D equation multiplied by Y_e, Sec. 2.2.1; reading: upwinded as in the consistent multi-fluid
 // advection it cites).
 void face_flux(const PM& M, const oparams& Q, int d, const real wL[], const real BL[3],
                const real wR[], const real BR[3], real Fq[], real Fb[2]) {
@@ -670,7 +670,7 @@ void sources(const PM& M, const FP& F, const real dm[3][16], real s[5]) {
 
 // ------------------------------------------------------------------------------------------------
 // Con2prim: KKC master function in mu = 1/(hW) with the PrimitiveSolver error policy (App. A) and
-// the atmosphere of Sec. 3.6.  Readings c13-c16, c18.  Status bits:
+// the atmosphere of Sec. 3.5.  Readings c13-c16, c18.  Status bits:
 //   1 atmosphere by threshold, 2 failure -> atmosphere, 4 W clamped (or ceiling -> atmosphere),
 //   8 tau floored, 16 B^2/D limited, 32 EOS bound clamp.
 // ------------------------------------------------------------------------------------------------
@@ -764,7 +764,7 @@ int illinois(Fn f, real a, real b, real fa, real fb, real tol, int max_iter, rea
   return -2;
 }
 
-// Atmosphere primitives (Sec. 3.6, App. A): rho_atm, p_atm, u~ = 0; B untouched.  Table:
+// Atmosphere primitives (Sec. 3.5, App. A): rho_atm, p_atm, u~ = 0; B untouched.  Table:
 // rho_atm, T_atm, Y_e = Y_e,atm, p from the table.
 void atmosphere(const oparams& Q, real w[]) {
   w[0] = Q.rho_atm; w[1] = w[2] = w[3] = 0; w[4] = Q.p_atm;
@@ -1484,7 +1484,7 @@ int oracle_stage_block_ex(const ob_geom* G, const double* metric, const double* 
         for (int e = 0; e < 3; ++e) interp_cell(b, mv, Q.interp_order, i, j, k, e, dm[e]);
         real s[6];
         sources(cm[ci], F, dm, s);
-        s[5] = 0;   // D Y_e has no source (Sec. 2.3)
+        s[5] = 0;   // D Y_e has no source (Sec. 2.2.1)
         for (int v = 0; v < nq; ++v) {
           real divF = 0;
           for (int d = 0; d < 3; ++d) {

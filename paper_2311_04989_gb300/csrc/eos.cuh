@@ -1,4 +1,4 @@
-// eos.cuh -- tabulated equation of state on the device (arXiv:2311.04989, Sec. 2.3; App. A for the
+// eos.cuh -- tabulated equation of state on the device (arXiv:2311.04989, Sec. 2.2.1; App. A for the
 // temperature root and the bounds policy).
 //
 // The table holds log p, log e (e = rho (1 + eps)) and c_s^2 on a uniform grid in (log rho, log T,

@@ -1,6 +1,6 @@
 // faces_impl.cuh -- k_faces: reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux
 // (Eq. fluxB_def) on every face with normal index 0..n and transverse index -1..n; with a tabulated EOS
-// (Sec. 2.3) also Y_e and the D Y_e flux = D flux x upwind Y_e.  Instantiated per precision (one
+// (Sec. 2.2.1) also Y_e and the D Y_e flux = D flux x upwind Y_e.  Instantiated per precision (one
 // translation unit each: faces_f32.cu, faces_f64.cu), EOS and reconstruction method, so each kernel
 // carries the code of one method only.
 #pragma once
@@ -87,7 +87,7 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   const long long o = b.wface[D] + fi;
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
-  // D Y_e: the D equation times Y_e (Sec. 2.3), Y_e taken from the upwind state of the mass flux
+  // D Y_e: the D equation times Y_e (Sec. 2.2.1), Y_e taken from the upwind state of the mass flux
   if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
 }
 

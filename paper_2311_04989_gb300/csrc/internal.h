@@ -109,7 +109,7 @@ struct Workspace {
   int2* jobs;
 };
 
-// Device view of an EOS table (Sec. 2.3) in precision R: node arrays of log p, log e, c_s^2, node
+// Device view of an EOS table (Sec. 2.2.1) in precision R: node arrays of log p, log e, c_s^2, node
 // (ir, iT, iy) at (iy * n[1] + iT) * n[0] + ir; uniform axes log rho, log T, Y_e.
 template <class R>
 struct TabView {

@@ -419,7 +419,7 @@ __device__ __forceinline__ void recon(const R s[6], R eps, R* L, R* Rr) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// EOS at a point from (rho, p[, Y_e]) (Sec. 2.3): rho h and c_s^2.  Ideal gas (reading c3 for c_s):
+// EOS at a point from (rho, p[, Y_e]) (Sec. 2.2.1): rho h and c_s^2.  Ideal gas (reading c3 for c_s):
 // rho h = rho + Gamma p/(Gamma - 1), c_s^2 = Gamma p/(rho h); table: interpolated (eos.cuh).
 // ------------------------------------------------------------------------------------------------
 template <class R, int EOS>
@@ -717,7 +717,7 @@ __device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R
   E.f = mu - rdiv(R(1), nu + mu * E.rbar2);
 }
 
-// The same master function with the tabulated EOS (Sec. 2.3, App. A): rho = D/W moved into the
+// The same master function with the tabulated EOS (Sec. 2.2.1, App. A): rho = D/W moved into the
 // table, the temperature of e/rho = 1 + eps by the exact inverse of the interpolant (eps reset to the
 // table's value at the nearest end when outside), p from the table; (1 + a)(1 + eps) = h =
 // 1 + eps + p/rho.

@@ -6,7 +6,7 @@
 //                cell electric field E_m = alpha (v~^b B^a - v~^a B^b) on the ring -1..n  (Sec. 3.3)
 //   k_faces<R>   reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux (Eq. fluxB_def)
 //                on every face with normal index 0..n and transverse index -1..n; with a tabulated
-//                EOS (Sec. 2.3) also Y_e, and the D Y_e flux = D flux x upwind Y_e
+//                EOS (Sec. 2.2.1) also Y_e, and the D Y_e flux = D flux x upwind Y_e
 //   k_edges<R>   upwinded corner electric field from the four adjacent face fluxes (Sec. 3.3)
 //   k_ct         constrained-transport face update B' = g0 B0 + g1 B - beta dt curl E  (FP64)
 //   k_update     flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def) accumulated in
@@ -400,7 +400,7 @@ __device__ __forceinline__ void update_all(const DBlock& b, const InView<R>& in,
   cell_fluid<R, EOS>(M, kp, wv, Bd, fl);
   R src[6];
   cell_sources<R>(M, fl, dm, kzero, src);
-  src[5] = R(0);   // D Y_e has no source (Sec. 2.3)
+  src[5] = R(0);   // D Y_e has no source (Sec. 2.2.1)
   constexpr int NQ = EOS ? 6 : 5;
 #pragma unroll
   for (int v = 0; v < NQ; ++v) q[v] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, v, src[v]);

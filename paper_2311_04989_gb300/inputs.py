@@ -310,7 +310,7 @@ def star_block(n=(64, 64, 64), g=3, half_width=10.02, tov: TOV | None = None, ce
     """Static star(s) in a conformally flat metric with gamma_ij = psi^4 delta_ij, beta = 0, K = 0.
 
     Several centres superpose the stars as psi = 1 + sum(psi_a - 1), alpha psi = 1 + sum(alpha_a psi_a - 1)
-    (reading of 'analytic superposed metric').  The poloidal field is the curl of
+    (the reading of the paper's analytic superposition of the two stars' metrics).  The poloidal field is the curl of
     A = (-y A_phi, x A_phi, 0) with A_phi = A_b max(p - 0.04 p_max, 0) (Eq. Apotential), taken about each
     centre.  Density below the atmosphere f_atm rho_max is raised to it."""
     if tov is None:
@@ -545,7 +545,7 @@ class BinaryStarMesh:
 
 
 # ---------------------------------------------------------------------------------------------
-# synthetic tabulated EOS (stand-in for the CompOSE table of Sec. 2.3, which is not available)
+# synthetic tabulated EOS (stand-in for the CompOSE table of Sec. 2.2.1, which is not available)
 # ---------------------------------------------------------------------------------------------
 @dataclass
 class EosTable:

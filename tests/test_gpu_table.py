@@ -1,4 +1,4 @@
-"""Tabulated EOS on the GPU (Sec. 2.3; App. A) against the FP64 oracle, through the C ABI.
+"""Tabulated EOS on the GPU (Sec. 2.2.1; App. A) against the FP64 oracle, through the C ABI.
 
 * gr_prim2con / gr_con2prim with the table: same conserved variables, primitives, Y_e, T and status
   as the oracle, including temperature-floor, Y_e-clamp, limit and atmosphere cells

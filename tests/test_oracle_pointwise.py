@@ -1,7 +1,7 @@
 """Pins of the oracle's pointwise physics against closed forms and 4D-covariant identities.
 
 Eq. consB_def, Eq. fluxB_def, Eq. EMT_MHD, Eq. hydsrc_def (Sec. 2); wave speeds (Sec. 2.2, reading c2);
-HLLE (reading c1); con2prim with the App. A policy (Sec. 3.6, App. A)."""
+HLLE (reading c1); con2prim with the App. A policy (Sec. 3.5, App. A)."""
 import numpy as np
 import pytest
 
@@ -262,7 +262,7 @@ def test_con2prim_tight_tolerance_reaches_round_off():
 
 
 def test_con2prim_atmosphere_threshold_resets_and_recomputes_cons():
-    """D below f_thr rho_atm -> atmosphere prims and cons recomputed from them (Sec. 3.6)."""
+    """D below f_thr rho_atm -> atmosphere prims and cons recomputed from them (Sec. 3.5)."""
     rng = np.random.default_rng(62)
     n = 20
     m = random_metric(rng, n, amp=0.1)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's tabulated EOS (Sec. 2.3; App. A for the nested temperature root and the
+"""Pins of the oracle's tabulated EOS (Sec. 2.2.1; App. A for the nested temperature root and the
 error policy).
 
 * trilinear interpolation in (log rho, log T, Y_e) reproduces a function that is trilinear in those
