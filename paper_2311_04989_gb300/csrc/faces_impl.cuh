@@ -91,8 +91,10 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
 }
 
+// FP32: at most 85 registers (three 256-thread CTAs per SM); the packed reconstruction would otherwise
+// take ~94 and the lost occupancy costs more than the few spilled words (measured)
 template <class R, int EOS, int METHOD>
-__global__ void __launch_bounds__(kMaxTile) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+__global__ void __launch_bounds__(kMaxTile, sizeof(R) == sizeof(float) ? 3 : 0) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                     int nwork, const __grid_constant__ InView<R> in,
                                                     const __grid_constant__ Workspace ws,
                                                     const __grid_constant__ KParams kp) {

@@ -368,6 +368,48 @@ __device__ __forceinline__ void ppm_cell(R v0, R v1, R v2, R v3, R v4, R* qm, R*
   *qp = r;
 }
 
+// WENOZ of both face states at once in FP32 (packed FP32x2 arithmetic: one instruction per operation
+// for both).  Lane x: the L state, wenoz of cells f-3 .. f+1; lane y: the R state, wenoz of the mirror
+// image f+2 .. f-2.  Both lanes take the same operations, so a mirror-symmetric stencil still gives
+// L == R bitwise.  Weights d_k (1 + tau5/(beta_k + eps)) from the fast reciprocal of beta_k + eps.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk1(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 prcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+
+__device__ __forceinline__ void wenoz_pair(const float s[6], float eps, float* L, float* Rr) {
+  const float2 v0 = pk(s[0], s[5]), v1 = pk(s[1], s[4]), v2 = pk(s[2], s[3]);
+  const float2 v3 = pk(s[3], s[2]), v4 = pk(s[4], s[1]);
+  const float2 sixth = pk1(1.f / 6.f);
+  // candidates (2 v0 - 7 v1 + 11 v2)/6, (-v1 + 5 v2 + 2 v3)/6, (2 v2 + 5 v3 - v4)/6
+  const float2 q0 = __fmul2_rn(__ffma2_rn(pk1(11.f), v2, __ffma2_rn(pk1(-7.f), v1, __fmul2_rn(pk1(2.f), v0))), sixth);
+  const float2 q1 = __fmul2_rn(__ffma2_rn(pk1(2.f), v3, __ffma2_rn(pk1(5.f), v2, __fmul2_rn(pk1(-1.f), v1))), sixth);
+  const float2 q2 = __fmul2_rn(__ffma2_rn(pk1(-1.f), v4, __ffma2_rn(pk1(5.f), v3, __fmul2_rn(pk1(2.f), v2))), sixth);
+  // smoothness indicators 13/12 a^2 + 1/4 c^2
+  const float2 a0 = __fadd2_rn(__ffma2_rn(pk1(-2.f), v1, v0), v2);
+  const float2 c0 = __ffma2_rn(pk1(3.f), v2, __ffma2_rn(pk1(-4.f), v1, v0));
+  const float2 a1 = __fadd2_rn(__ffma2_rn(pk1(-2.f), v2, v1), v3);
+  const float2 c1 = __ffma2_rn(pk1(-1.f), v3, v1);
+  const float2 a2 = __fadd2_rn(__ffma2_rn(pk1(-2.f), v3, v2), v4);
+  const float2 c2 = __ffma2_rn(pk1(3.f), v2, __ffma2_rn(pk1(-4.f), v3, v4));
+  const float2 k13 = pk1(13.f / 12.f), k14 = pk1(0.25f);
+  const float2 b0 = __ffma2_rn(__fmul2_rn(k13, a0), a0, __fmul2_rn(__fmul2_rn(k14, c0), c0));
+  const float2 b1 = __ffma2_rn(__fmul2_rn(k13, a1), a1, __fmul2_rn(__fmul2_rn(k14, c1), c1));
+  const float2 b2 = __ffma2_rn(__fmul2_rn(k13, a2), a2, __fmul2_rn(__fmul2_rn(k14, c2), c2));
+  const float2 d02 = __fadd2_rn(b0, __fmul2_rn(pk1(-1.f), b2));
+  const float2 t5 = pk(fabsf(d02.x), fabsf(d02.y));
+  const float2 e2 = pk1(eps);
+  const float2 r0 = __fmul2_rn(t5, prcp(__fadd2_rn(b0, e2)));
+  const float2 r1 = __fmul2_rn(t5, prcp(__fadd2_rn(b1, e2)));
+  const float2 r2 = __fmul2_rn(t5, prcp(__fadd2_rn(b2, e2)));
+  const float2 w0 = __ffma2_rn(pk1(0.1f), r0, pk1(0.1f));
+  const float2 w1 = __ffma2_rn(pk1(0.6f), r1, pk1(0.6f));
+  const float2 w2 = __ffma2_rn(pk1(0.3f), r2, pk1(0.3f));
+  const float2 num = __ffma2_rn(w2, q2, __ffma2_rn(w1, q1, __fmul2_rn(w0, q0)));
+  const float2 den = __fadd2_rn(__fadd2_rn(w0, w1), w2);
+  *L = __fdividef(num.x, den.x);
+  *Rr = __fdividef(num.y, den.y);
+}
+
 // Face states of the 6-cell stencil s[0..5] = cells f-3 .. f+2 by method (Sec. 3.4)
 template <class R, int METHOD>
 __device__ __forceinline__ void recon_plain(const R s[6], R eps, R* L, R* Rr) {
@@ -376,8 +418,12 @@ __device__ __forceinline__ void recon_plain(const R s[6], R eps, R* L, R* Rr) {
     *L = s[2] + R(0.5) * vl_slope(s[1], s[2], s[3]);
     *Rr = s[3] - R(0.5) * vl_slope(s[2], s[3], s[4]);
   } else if constexpr (method == GR_RECON_WENOZ) {
-    *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
-    *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+    if constexpr (sizeof(R) == sizeof(float)) {
+      wenoz_pair(s, eps, L, Rr);
+    } else {
+      *L = wenoz(s[0], s[1], s[2], s[3], s[4], eps);
+      *Rr = wenoz(s[5], s[4], s[3], s[2], s[1], eps);
+    }
   } else if constexpr (method == GR_RECON_WENO5) {
     *L = weno5(s[0], s[1], s[2], s[3], s[4], eps);
     *Rr = weno5(s[5], s[4], s[3], s[2], s[1], eps);

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kMaxTile) k_update(const DBlock* __restrict__ 
 // R = float (the mixed stage): the cell's U' is formed here first (update_all on the FP32 inputs);
 // R = double: U' is read from Uo (left there by k_update or by the caller of gr_con2prim).
 template <int EOS, class R = double>
-__global__ void __launch_bounds__(kMaxTile) k_c2p(const DBlock* __restrict__ blocks,
+__global__ void __maxnreg__(168) k_c2p(const DBlock* __restrict__ blocks,
                                                   const __grid_constant__ InView<R> in,
                                                   const __grid_constant__ InView<double> in64,
                                                   const __grid_constant__ StateView s,
