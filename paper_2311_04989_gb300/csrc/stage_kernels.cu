@@ -493,8 +493,9 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
   }
 }
 
+// FP32: at most 64 registers (four 256-thread CTAs per SM): the mixed update is bound by load latency
 template <class R, int EOS>
-__global__ void __launch_bounds__(kMaxTile) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+__global__ void __launch_bounds__(kMaxTile, sizeof(R) == sizeof(float) ? 4 : 0) k_update(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                      int nwork, const __grid_constant__ InView<R> in,
                                                      const __grid_constant__ StateView s,
                                                      const __grid_constant__ Workspace ws,
