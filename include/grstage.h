@@ -188,8 +188,9 @@ int gr_graph_destroy(gr_graph* graph);
 /* Launch shape of a stage kernel: CTA size tile (64, 128 or 256 threads = elements of one work item),
  * order of the work list (0: direction-major, 1: block-major) and persistent (0: one CTA per work item;
  * 1: as many CTAs as fit on the GPU at once, each striding over the list).  The kernels are cell prep,
- * faces, edges, CT, update and con2prim (the order of con2prim's job list is moot).  Every shape gives
- * bitwise the same results. */
+ * faces, edges, CT, update and con2prim (the order of con2prim's job list is moot).  With the order-2
+ * metric the cell prep runs as a z sweep over fixed tiles of each block's x-y plane and its shape is
+ * unused.  Every shape gives bitwise the same results. */
 #define GR_NSTAGE_KERNELS 6
 typedef struct {
   int32_t tile;
