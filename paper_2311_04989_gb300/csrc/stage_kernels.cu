@@ -207,11 +207,13 @@ template <class R>
 static cudaError_t launch_cellprep_sweep(const DBlock* blocks, const InView<R>& in, const Workspace& ws,
                                          cudaStream_t st) {
   constexpr size_t smem = sizeof(R) * 2 * 10 * kSweepVerts;
-  static bool attr = false;
-  if (!attr && smem > 48 * 1024) {
+  // above the default 48 KB: the opt-in is per device (set once on each, one bit per device)
+  static unsigned long long attr = 0;
+  int dev = 0;
+  if (smem > 48 * 1024 && cudaGetDevice(&dev) == cudaSuccess && dev < 64 && !((attr >> dev) & 1ull)) {
     const cudaError_t e = cudaFuncSetAttribute(k_cellprep_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr |= 1ull << dev;
   }
   k_cellprep_sweep<R><<<ws.nsweep, kSweepThreads, smem, st>>>(blocks, ws.sweep, in, ws);
   return cudaGetLastError();
@@ -747,7 +749,11 @@ static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Sh
   const int ncomp = cast_metric ? (m.k_zero ? 10 : 16) : 0;
   for (int c = 0; c < ncomp; ++c) { L.src[k] = m.v[c]; L.dst[k] = sh.M[c]; L.n[k] = sh.nvert; ++k; }
   L.count = k;
-  dim3 grid(152 * 2, k);
+  // two 256-thread CTAs per SM and pool, striding over it
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+  dim3 grid(2 * nsm, k);
   k_cast<<<grid, 256, 0, st>>>(L);
   return cudaGetLastError();
 }
