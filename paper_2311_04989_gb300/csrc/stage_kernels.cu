@@ -3,20 +3,26 @@
 //   k_cast       (mixed path only) FP32 copies of the stage inputs W, B and the metric, made with
 //                integer bit arithmetic so that no conversion runs on GB300's narrow FP64 pipe
 //   k_cellprep   cell-centred field calB^i = mean of faces / sqrt(gamma) on all cells, and the
-//                cell electric field E_m = alpha (v~^b B^a - v~^a B^b) on the ring -1..n  (Sec. 3.3)
+//                cell electric field E_m = alpha (v~^b B^a - v~^a B^b) on the ring -1..n  (Sec. 3.3);
+//                with the order-2 metric k_cellprep_sweep: the same per tile of a block's x-y plane,
+//                walked along z with the vertex planes in shared memory
 //   k_faces<R>   reconstruction (Sec. 3.4) + face metric (Sec. 3.2) + HLLE flux (Eq. fluxB_def)
 //                on every face with normal index 0..n and transverse index -1..n; with a tabulated
-//                EOS (Sec. 2.2.1) also Y_e, and the D Y_e flux = D flux x upwind Y_e
+//                EOS (Sec. 2.2.1) also Y_e, and the D Y_e flux = D flux x upwind Y_e (faces_impl.cuh;
+//                the mixed WENOZ evaluates both face states in packed FP32x2)
 //   k_edges<R>   upwinded corner electric field from the four adjacent face fluxes (Sec. 3.3)
 //   k_ct         constrained-transport face update B' = g0 B0 + g1 B - beta dt curl E  (FP64)
-//   k_update     flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def) accumulated in
-//                FP64, then con2prim with atmosphere on the updated state (Sec. 3.5), FP64
+//   k_update     FP64 path: flux divergence + geometric sources (Eq. claw, Eq. hydsrc_def)
+//                accumulated in FP64 and the atmosphere test (Sec. 3.5); mixed path: D' and the
+//                atmosphere test only; atmosphere cells are reset, the others queued for k_c2p
+//   k_c2p        on the compacted job list: (mixed path) the cell's U' as above, then FP64 con2prim
+//                (Sec. 3.5, App. A)
 //
 // Kernels that evaluate the EOS are instantiated per EOS (ideal gas / table) as well as per R.
-// Every kernel takes one work item (block, direction, first element) per CTA; blocks of different
-// sizes share one launch.  Within a work item the direction is a compile-time constant (one
-// instantiation per direction), so no small array is indexed at run time.  Face fluxes and corner
-// fields pass through the mesh's workspace in the arithmetic type R.
+// Every kernel but the sweep and k_c2p takes one work item (block, direction, first element) per CTA;
+// blocks of different sizes share one launch.  Within a work item the direction is a compile-time
+// constant (one instantiation per direction), so no small array is indexed at run time.  Face fluxes
+// and corner fields pass through the mesh's workspace in the arithmetic type R.
 #include <cstdio>
 
 #include "internal.h"
