@@ -32,8 +32,18 @@ sys.path.insert(0, ROOT)
 METRIC = "GRMHD cell-updates/s per RK stage"
 UNIT = "cell-updates/s"
 WORKLOAD = "two-star full-stage throughput: 4096 blocks of 16^3 (ng=3), WENOZ+HLLE, CT, con2prim"
-FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of the GB300 (profiling recipe table)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_NOMINAL_TFLOPS = 1.25      # nominal dense FP64 of the GB300 (context only; the roofline uses the measured rate)
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of this machine's GPUs (GB/s) and where it came from."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+MEASURED_HBM_GBS, HBM_PEAK_SOURCE = _hbm_peak()
 
 
 def env_rank():
@@ -126,6 +136,54 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# arithmetic-pipe peaks, measured on this GPU (FFMA, packed FFMA2, DFMA throughput loops)
+# ---------------------------------------------------------------------------------------------
+def measure_alu_peaks(G, torch, dev, seconds=1.5):
+    """Peak FP32 (FFMA and packed FFMA2) and FP64 (DFMA) rates of the GPU: gr_peak_alu's loops of
+    independent FMA chains on every SM (8 CTAs of 256 threads per SM), sized to run ~0.3 s per launch,
+    timed with CUDA events over ~`seconds` per pipe, with the SM clock sampled meanwhile."""
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    blocks, threads = 8 * nsm, 256
+    sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"sm_count": nsm, "blocks": blocks, "threads": threads, "source": "measured: gr_peak_alu loops"}
+    names = {0: "fp32_ffma", 1: "fp32x2_ffma2", 2: "fp64_dfma"}
+    clk = ClockSampler(dev.index if dev.index is not None else 0)
+    clk.start()
+    for kind, name in names.items():
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        iters = 1 << 12
+        while True:   # calibrate: one launch of ~0.3 s
+            e0.record(stream)
+            G.gr_peak_alu(kind, blocks, threads, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms > 100 or iters > (1 << 30):
+                break
+            iters *= 4
+        iters = max(1, int(iters * 300.0 / ms))
+        reps = max(1, int(seconds * 1e3 / 300.0))
+        fl = 0.0
+        e0.record(stream)
+        for _ in range(reps):
+            fl += G.gr_peak_alu(kind, blocks, threads, iters, sink, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "launches": reps}
+    out["clocks"] = clk.stop()
+    mhz = out["clocks"].get("sm_mhz")
+    if mhz:
+        for name in names.values():
+            out[name]["flops_per_sm_per_clock"] = out[name]["tflops"] * 1e12 / (nsm * mhz * 1e6)
+    out["fp32_tflops"] = max(out["fp32_ffma"]["tflops"], out["fp32x2_ffma2"]["tflops"])
+    out["fp64_tflops"] = out["fp64_dfma"]["tflops"]
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -403,7 +461,8 @@ def main():
     def timed(precision):
         guess = G.GR_GUESS_FP32 if precision == G.GR_PREC_MIXED else G.GR_GUESS_NONE
         p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=precision, gamma_ad=2.0, c2p_guess=guess,
-                                rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+                                rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
+                                atm_band=G.GR_MIXED_ATM_BAND if precision == G.GR_PREC_MIXED else 1e-12)
         # launch shapes per kernel from the library's autotuner (untimed; it runs the stage itself)
         shapes = None
         if not a.no_autotune:
@@ -429,6 +488,8 @@ def main():
         kms, nst = G.gr_profile_end(mesh)
         return max_over_ranks(ms, dist, dev) / a.steps, [k / max(1, nst) for k in kms], clocks, shapes
 
+    # measured arithmetic peaks of this GPU (the ALU rooflines divide by them)
+    peaks = measure_alu_peaks(G, torch, dev)
     results = {}
     precs = {"both": ["fp64", "mixed"], "fp64": ["fp64"], "mixed": ["mixed"]}[a.precision]
     snap = {}
@@ -461,7 +522,8 @@ def main():
         hm = head == "mixed"
         p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=(G.GR_PREC_MIXED if hm else G.GR_PREC_FP64),
                                 c2p_guess=(G.GR_GUESS_FP32 if hm else G.GR_GUESS_NONE),
-                                gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+                                gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
+                                atm_band=G.GR_MIXED_ATM_BAND if hm else 1e-12)
         # the host-buffer entry: pinned host pools in, pinned host pools out; the library copies batches
         # of blocks in, runs their stages and copies them out on three overlapping streams
         hU, hW, hM = U.cpu().pin_memory(), W.cpu().pin_memory(), M.cpu().pin_memory()
@@ -506,7 +568,8 @@ def main():
     graph_ms = None
     if head == "mixed":
         pg = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
-                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
+                                 atm_band=G.GR_MIXED_ATM_BAND)
         gph = G.gr_graph_capture(mesh, metric, state, dt, pg)
         for _ in range(a.warmup):
             G.gr_graph_launch(gph, stream)
@@ -524,7 +587,8 @@ def main():
     rk = None
     if head == "mixed" and not a.no_rk:
         pr = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
-                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10)
+                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
+                                 atm_band=G.GR_MIXED_ATM_BAND)
         nbr = I.block_grid_neighbours((a.nb,) * 3, periodic=(False,) * 3)
         drv = G.gr_driver_create(mesh, nbr)
         Ur, Wr, Br = U.clone(), W.clone(), [x.clone() for x in B]
@@ -656,35 +720,76 @@ def main():
     def ph_flops(*names):
         return sum(ph[n]["add"] + ph[n]["mul"] + ph[n]["div"] + ph[n]["sqrt"] for n in names)
 
-    kernel_phases = {"k_cast": (), "k_c2p": ("con2prim",), "k_cellprep": ("cell_metric_and_field", "cell_efield"),
-                     "k_faces": ("faces",),
-                     "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources",)}
     scale = (a.nb ** 3) / 4096.0
+    # phases of the oracle's count -> the kernel that runs them, and the pipe they run on
+    # FP64 path: every phase in FP64; the atmosphere resets are decided and done in k_update
+    phases64 = {"k_cellprep": ("cell_metric_and_field", "cell_efield"), "k_faces": ("faces",),
+                "k_edges": ("corner_emf",), "k_ct": ("ct",), "k_update": ("update_and_sources", "con2prim_atmosphere"),
+                "k_c2p": ("con2prim",)}
 
-    def roofline(name):
-        """ALU roofline of the dominant kernel.  Its algorithmic operations (oracle-counted) are
-        split by the precision the kernel runs them in; the lower-bound time is the sum of
-        ops/peak over the two pipes, and peak is the matching effective rate."""
+    def kernel_ops(kn, mixed, solved_frac):
+        """(FP32 ops, FP64 ops) of one launch of kernel kn on this workload (oracle-counted).  Mixed
+        path: the cell prep, faces and corner EMFs run in FP32; CT, con2prim and the atmosphere resets
+        in FP64; the flux divergence and sources of the solved (matter) cells run in k_c2p (sources in
+        FP32, accumulation in FP64: counted as FP32), those of the atmosphere cells are skipped (their
+        reset overrides them)."""
+        if not mixed:
+            return 0.0, sum(ph_flops(p_) for p_ in phases64.get(kn, ())) * scale
+        if kn in ("k_cellprep", "k_faces", "k_edges"):
+            return sum(ph_flops(p_) for p_ in phases64[kn]) * scale, 0.0
+        if kn == "k_ct":
+            return 0.0, ph_flops("ct") * scale
+        if kn == "k_update":
+            return 0.0, ph_flops("con2prim_atmosphere") * scale
+        if kn == "k_c2p":
+            return ph_flops("update_and_sources") * solved_frac * scale, ph_flops("con2prim") * scale
+        return 0.0, 0.0
+
+    def kernel_rooflines(name, peaks):
+        """ALU roofline of every stage kernel against the measured FP32 and FP64 peaks: the time lower
+        bound is FP32 ops / FP32 peak + FP64 ops / FP64 peak, and peak is the matching effective rate."""
         kms = results[name]["kernel_ms"]
-        # the dominant kernel among those doing the stage's arithmetic (the FP32 cast only copies)
-        k = max((i for i in range(len(kms)) if kernel_phases[G.KERNEL_NAMES[i]]), key=lambda i: kms[i])
-        kn = G.KERNEL_NAMES[k]
         mixed = name == "mixed"
-        # operations executed in FP32 on the mixed path: everything but con2prim and CT
-        fp32_phases = {"cell_metric_and_field", "cell_efield", "faces", "corner_emf", "update_and_sources"}
-        f32 = sum(ph_flops(p_) for p_ in kernel_phases[kn] if mixed and p_ in fp32_phases) * scale
-        f64 = sum(ph_flops(p_) for p_ in kernel_phases[kn] if not (mixed and p_ in fp32_phases)) * scale
-        t_lb = f32 / (FP32_PEAK_TFLOPS * 1e12) + f64 / (FP64_PEAK_TFLOPS * 1e12)
-        fl = f32 + f64
-        peak = fl / t_lb / 1e12
-        ach = fl / (kms[k] / 1e3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": load_traffic(kn, name), "kernel": kn,
-                "peak_kind": ("FP64 nominal 1.25 TFLOP/s (recipe table) and FP32 152x128x2x2.07 GHz = "
-                              "80.5 TFLOP/s (derived), combined as the time lower bound of the kernel's "
-                              "FP32 and FP64 operation counts"),
-                "flops_per_launch": fl, "fp32_flops": f32, "fp64_flops": f64, "kernel_ms": kms[k],
-                "kernel_share": kms[k] / sum(kms)}
+        stc = results[name]["status"]
+        solved_frac = max(0.0, 1.0 - (stc["atmosphere"] + stc["failed"]) / cells)
+        rows = {}
+        for i, kn in enumerate(G.KERNEL_NAMES):
+            f32, f64 = kernel_ops(kn, mixed, solved_frac)
+            if f32 + f64 <= 0 or kms[i] <= 0:
+                continue
+            t_lb = f32 / (peaks["fp32_tflops"] * 1e12) + f64 / (peaks["fp64_tflops"] * 1e12)
+            fl = f32 + f64
+            rows[kn] = {"ms": kms[i], "fp32_flops": f32, "fp64_flops": f64, "achieved_tflops": fl / (kms[i] / 1e3) / 1e12,
+                        "peak_tflops": fl / t_lb / 1e12, "frac": t_lb / (kms[i] / 1e3)}
+        return rows
+
+    def roofline(name, peaks):
+        """The dominant kernel's ALU roofline (of measured peaks)."""
+        rows = kernel_rooflines(name, peaks)
+        kms = results[name]["kernel_ms"]
+        kn = max(rows, key=lambda k: rows[k]["ms"])
+        r = rows[kn]
+        return {"bound": "alu", "achieved": r["achieved_tflops"], "peak": r["peak_tflops"], "unit": "TFLOP/s",
+                "frac": r["frac"], "traffic": load_traffic(kn, name), "kernel": kn,
+                "peak_source": "measured",
+                "peak_kind": (f"measured FP32 {peaks['fp32_tflops']:.2f} TFLOP/s and FP64 {peaks['fp64_tflops']:.3f} "
+                              "TFLOP/s (gr_peak_alu loops on this GPU), combined as the time lower bound of the "
+                              "kernel's oracle-counted FP32 and FP64 operations"),
+                "flops_per_launch": r["fp32_flops"] + r["fp64_flops"], "fp32_flops": r["fp32_flops"],
+                "fp64_flops": r["fp64_flops"], "kernel_ms": r["ms"], "kernel_share": r["ms"] / sum(kms)}
+
+    def stage_hbm(name):
+        """The whole stage against the measured copy bandwidth, with the compulsory bytes of this
+        workload: U (5), B (3), W (5) read and U', B', W' (13 words) and the status byte written per
+        interior cell, plus the 10 metric words per vertex (K_ij declared zero and unread; one vertex per
+        cell, the mesh's unique vertices); the first RK stage form (g0 = 0) reads no U0 / B0."""
+        nvert = (a.nb * 16 + 1) ** 3
+        bytes_ = cells * (13 * 8 + 13 * 8 + 1) + nvert * 10 * 8
+        ms = results[name]["ms"]
+        ach = bytes_ / (ms / 1e3) / 1e9
+        pk = MEASURED_HBM_GBS
+        return {"compulsory_bytes": bytes_, "bytes_per_cell": bytes_ / cells, "achieved_GBps": ach, "peak_GBps": pk,
+                "frac": ach / pk, "peak_source": f"{HBM_PEAK_SOURCE} copy bandwidth (hbm_gbs)"}
 
     # ---- CPU baseline (rank 0, N = 1) ------------------------------------------------------------
     cpu = None
@@ -701,7 +806,8 @@ def main():
     if "fp64" in results and head != "fp64":
         fp64 = {"value": cells * world / (results["fp64"]["ms"] / 1e3), "ms_per_step": results["fp64"]["ms"],
                 "kernel_ms": dict(zip(G.KERNEL_NAMES, results["fp64"]["kernel_ms"])),
-                "roofline": roofline("fp64"), "clocks": results["fp64"]["clocks"]}
+                "roofline": roofline("fp64", peaks), "kernel_rooflines": kernel_rooflines("fp64", peaks),
+                "stage_hbm": stage_hbm("fp64"), "clocks": results["fp64"]["clocks"]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms_head, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
@@ -709,7 +815,8 @@ def main():
                       "riemann": "HLLE", "precision": head, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs ~25 GB >> L2 (no flush)", "workspace_bytes": ws_bytes,
                       "input_gen_s": round(t_gen, 1)},
-           "roofline": roofline(head), "clocks": results[head]["clocks"], "e2e": e2e, "gpu_launches": launches,
+           "roofline": roofline(head, peaks), "clocks": results[head]["clocks"], "alu_peaks": peaks,
+           "stage_hbm": stage_hbm(head), "kernel_rooflines": kernel_rooflines(head, peaks), "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err, "status_counts": results[head].get("status"),
            "graph_ms_per_step": graph_ms, "rk3_driver": rk, "adm_sources": adm, "con2prim_guess": c2p, "con2prim_table": c2p_table,

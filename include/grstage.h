@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define GR_ABI_VERSION 2
+#define GR_ABI_VERSION 3
 
 typedef enum {
   GR_OK = 0,
@@ -68,6 +68,11 @@ enum { GR_EOS_IDEAL = 0, GR_EOS_TABLE = 1 };            /* Sec. 2.2.1 */
 /* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change):
  * none, an FP32 pre-solve, or the learned bracket of a small network (gr_mlp_*). */
 enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1, GR_GUESS_MLP = 2 };
+
+/* Atmosphere band (gr_params.atm_band) for the mixed path: its atmosphere test compares D' with the
+ * threshold times an FP32 sqrt(gamma) (relative error ~1e-7), so a band of 1e-6 classifies the cells at
+ * the atmosphere density the same way as an FP64 test with the same band.  The default band is 1e-12. */
+#define GR_MIXED_ATM_BAND 1e-6
 
 /* One MeshBlock: n[] interior cells, ng ghosts, cell widths, and element offsets into the pools. */
 typedef struct {
@@ -144,6 +149,11 @@ typedef struct {
   const gr_eos* table;
   double T_atm;         /* table: atmosphere temperature and temperature floor (App. A) */
   double Ye_atm;        /* table: electron fraction of the atmosphere (a parameter; the paper is silent) */
+  double atm_band;      /* rho or D below f_thr rho_atm (1 + atm_band) is atmosphere (Sec. 3.5 resets below
+                           f_thr rho_atm).  Default 1e-12: values equal to the threshold up to FP64 rounding
+                           are reset, everything above is solved.  The mixed path tests D' against its FP32
+                           sqrt(gamma) (relative error ~1e-7), so it classifies atmosphere cells the same way
+                           on every input only with a band of ~1e-6; that is its documented tolerance. */
 } gr_params;
 
 typedef struct gr_ctx gr_ctx;
@@ -359,6 +369,13 @@ double gr_eos_h0(const gr_eos* eos);
 int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4],
             void* stream);
 
+/* FP32 copy of an FP64 device array, the conversion the mixed path applies to its inputs: IEEE round
+ * to nearest, ties to even, with float subnormals and overflow to infinity (NaN stays NaN), computed in
+ * integer arithmetic (on GB300 a hardware FP64 -> FP32 conversion runs on the narrow FP64 pipe).
+ * src and dst are device arrays of n elements on the current device (no alignment needed); asynchronous on
+ * `stream`.  GR_EINVAL for n < 0 or a NULL pointer with n > 0. */
+int gr_cast_f32(const double* src, float* dst, int64_t n, void* stream);
+
 /* ---- learned con2prim bracket (not in the paper: a bracket proposal for the root find of Sec. 3.5) --
  * A 6-64-64-1 tanh network predicts log mu at the master-function root from the features
  * log(1+q), log(1+r^2), log(1+calb^2), (r.calb)^2/(r^2 calb^2) of the KKC invariants and, with a table,
@@ -394,14 +411,25 @@ int gr_mlp_train(float* P, const float* x, const float* t, int64_t n, int32_t ep
  * memory pool (its own caching allocator or fixed arena) or in-situ hooks that must not change the
  * device footprint.  Same outputs as gr_diag, for at most 256 blocks given directly (no gr_mesh):
  * the block list travels as a kernel parameter and the reduction's scratch is a fixed 33 KB static
- * device array that every GPU loading the library holds until exit.  The first call on a device looks
- * up that array's address (cudaGetSymbolAddress; no allocation); make it before any stream capture.
+ * device array that every GPU loading the library holds until exit.  Every call looks up that array's
+ * address in the CUDA context current on the calling thread (cudaGetSymbolAddress, which allocates
+ * nothing), so callers with their own contexts and calls after cudaDeviceReset are served.
  * Calls share the array: each call overwrites every slot it reads, but calls whose kernels overlap on
  * the GPU race and must be serialised by the caller.  nblocks outside [1, 256] gives GR_EINVAL
  * (detail in gr_noalloc_last_error).  Synchronises the stream. */
 int gr_diag_noalloc(const gr_block* blocks, int32_t nblocks, const double* const U[5],
                     const double* const B[3], double out[4], void* stream);
 const char* gr_noalloc_last_error(void);
+
+/* ---- measurement -----------------------------------------------------------------------------------
+ * gr_peak_alu: one launch of an arithmetic throughput loop (the paper has no counterpart: it measures
+ * the pipe peaks that ALU-bound kernels are compared with).  kind 0: FP32 FMA, 1: packed FP32x2 FMA,
+ * 2: FP64 FMA; `blocks` CTAs of `threads` (32..256, a multiple of 32) threads, each running 16
+ * independent FMA chains for `iters` rounds.  *flops receives the floating-point operations of the
+ * launch (2 per FMA); time it with events on `stream`.  sink: a device float per CTA, written only in a
+ * case that never occurs (keeps the loop).  GR_EINVAL for bad arguments, GR_ECUDA if the launch fails. */
+int gr_peak_alu(int32_t kind, int32_t blocks, int32_t threads, int64_t iters, float* sink, double* flops,
+                void* stream);
 
 /* Per-kernel timing of gr_stage with CUDA events on the launch stream (measurement only).
  * gr_profile_begin arms the mesh for up to max_stages subsequent gr_stage calls: each records an event

@@ -50,7 +50,7 @@ def build_count(force: bool = False) -> str:
 
 
 PHASES = ["cell_metric_and_field", "faces", "cell_efield", "corner_emf", "update_and_sources", "ct",
-          "con2prim"]
+          "con2prim", "con2prim_atmosphere"]
 
 
 class OGeom(C.Structure):
@@ -70,7 +70,7 @@ class OParams(C.Structure):
                 ("recon", C.c_int32), ("emf", C.c_int32), ("ceiling", C.c_int32),
                 ("interp_order", C.c_int32), ("pad_", C.c_int32),
                 ("eos", C.c_int32), ("pad2_", C.c_int32), ("T_atm", C.c_double), ("Ye_atm", C.c_double),
-                ("h0", C.c_double), ("table", C.POINTER(OTable))]
+                ("h0", C.c_double), ("table", C.POINTER(OTable)), ("atm_band", C.c_double)]
 
 
 def otable(tab) -> OTable:
@@ -114,6 +114,7 @@ class Params:
     table: object = None            # EOS table (Sec. 2.2.1); None -> ideal gas
     T_atm: float = 1e-6             # atmosphere temperature (table)
     Ye_atm: float = 0.5             # atmosphere electron fraction (table)
+    atm_band: float = 1e-12         # relative band above f_thr rho_atm that counts as reached (Sec. 3.5)
 
     @property
     def eos(self) -> int:
@@ -132,6 +133,7 @@ class Params:
         o = OParams(self.gamma_ad, self.rho_atm, p_atm, self.f_thr, self.W_max, self.M_max,
                     self.tol, self.weno_eps, self.rk_g0, self.rk_g1, self.rk_beta,
                     self.max_iter, self.recon, self.emf, self.ceiling, self.interp_order, 0)
+        o.atm_band = self.atm_band
         if self.table is not None:
             t = otable(self.table)
             h0 = getattr(self.table, "_oracle_h0", None)
@@ -399,7 +401,7 @@ def stage_block_count(blk: Block, U, U0, B0, dt, P: Params):
     Uo = U.copy(); Wo = W.copy(); Bo = [b.copy() for b in B]
     st = np.zeros(W.shape[1:], np.uint8)
     it = np.zeros(W.shape[1:], np.int32)
-    out = np.zeros(35)
+    out = np.zeros(40)
     L.oracle_flops_get(_d(out), 1)
     cp = P.c()
     r = L.oracle_stage_block(C.byref(g), _d(metric), _d(W), _d(B[0]), _d(B[1]), _d(B[2]), _d(U), _d(U0),

@@ -69,6 +69,10 @@ typedef struct {
   double Ye_atm;     // atmosphere electron fraction (reading: a parameter)
   double h0;         // minimum enthalpy of the table (from oracle_table_hmin)
   const struct otable_* table;
+  // Atmosphere band: rho or D below f_thr rho_atm (1 + atm_band) takes the atmosphere branch.  The
+  // paper resets only below the threshold (Sec. 3.5, App. A); atm_band = 1e-12 (the default) only
+  // takes values equal to the threshold up to FP64 rounding off the knife-edge of a strict test.
+  double atm_band;
 } oparams;
 
 // EOS table (Sec. 2.2.1): log p, log e (e = rho(1 + eps)) and c_s^2 on a uniform grid in
@@ -808,10 +812,9 @@ int con2prim_point(const PM& M, const oparams& Q, real q[], const real Bdens[3],
     if (ye < ylo) { ye = ylo; ye_clamped = true; }
     if (ye > yhi) { ye = yhi; ye_clamped = true; }
   }
-  // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A).  Values within 1e-6 relative of it
-  // count as having reached it, so cells that sit at the atmosphere density up to rounding (or up
-  // to an FP32 sqrt(gamma)) are reset deterministically.
-  const real rho_thr = Q.f_thr * Q.rho_atm * (1 + 1e-6);
+  // Atmosphere threshold f_thr rho_atm (Sec. 3.5, App. A), widened by the relative band atm_band:
+  // cells that sit at the atmosphere density up to rounding are reset deterministically.
+  const real rho_thr = Q.f_thr * Q.rho_atm * (1 + Q.atm_band);
   bool atm = false, reprim = false;
   if (!finite) { st |= 2; atm = true; }
   else if (D < rho_thr) { st |= 1; atm = true; }
@@ -1084,10 +1087,33 @@ void phase_mark(int k, OpCount& last) {
   g_phase[k].cmp += g_ops.cmp - last.cmp;
   last = g_ops;
 }
+// con2prim of cells that take the atmosphere branch before any root find (no iteration): their
+// operations are moved from phase 6 to phase 7, so the two kinds of cell can be told apart
+OpCount g_c2p_cell_start, g_c2p_atm;
+void c2p_cell_begin() { g_c2p_cell_start = g_ops; }
+void c2p_cell_end(int iterations) {
+  if (iterations != 0) return;
+  g_c2p_atm.add += g_ops.add - g_c2p_cell_start.add; g_c2p_atm.mul += g_ops.mul - g_c2p_cell_start.mul;
+  g_c2p_atm.div += g_ops.div - g_c2p_cell_start.div; g_c2p_atm.sqrt += g_ops.sqrt - g_c2p_cell_start.sqrt;
+  g_c2p_atm.cmp += g_ops.cmp - g_c2p_cell_start.cmp;
+}
+void c2p_split() {
+  g_phase[6].add -= g_c2p_atm.add; g_phase[6].mul -= g_c2p_atm.mul; g_phase[6].div -= g_c2p_atm.div;
+  g_phase[6].sqrt -= g_c2p_atm.sqrt; g_phase[6].cmp -= g_c2p_atm.cmp;
+  g_phase[7].add += g_c2p_atm.add; g_phase[7].mul += g_c2p_atm.mul; g_phase[7].div += g_c2p_atm.div;
+  g_phase[7].sqrt += g_c2p_atm.sqrt; g_phase[7].cmp += g_c2p_atm.cmp;
+  g_c2p_atm = OpCount();
+}
 }  // namespace
 #define ORACLE_PHASE(k) phase_mark(k, ops_last)
+#define ORACLE_C2P_CELL_BEGIN() c2p_cell_begin()
+#define ORACLE_C2P_CELL_END(it) c2p_cell_end(it)
+#define ORACLE_C2P_SPLIT() c2p_split()
 #else
 #define ORACLE_PHASE(k)
+#define ORACLE_C2P_CELL_BEGIN()
+#define ORACLE_C2P_CELL_END(it)
+#define ORACLE_C2P_SPLIT()
 #endif
 
 extern "C" {
@@ -1250,11 +1276,12 @@ void oracle_interp_faces(const ob_geom* G, const double* metric, int order, int 
 
 #else
 // Operation counts per phase of the stage accumulated since the last reset:
-// out[5*k + {0,1,2,3,4}] = (add, mul, div, sqrt, cmp) of phase k, k = 0..6:
+// out[5*k + {0,1,2,3,4}] = (add, mul, div, sqrt, cmp) of phase k, k = 0..7:
 //   0 cell metric + cell field, 1 faces (reconstruction, face metric, HLLE), 2 cell electric field,
-//   3 corner EMFs, 4 flux divergence + sources + update, 5 CT face update, 6 con2prim
+//   3 corner EMFs, 4 flux divergence + sources + update, 5 CT face update, 6 con2prim of the cells
+//   that run the root find, 7 con2prim of the cells reset to the atmosphere without one
 void oracle_flops_get(double* out, int reset) {
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < 8; ++k) {
     out[5 * k + 0] = g_phase[k].add; out[5 * k + 1] = g_phase[k].mul; out[5 * k + 2] = g_phase[k].div;
     out[5 * k + 3] = g_phase[k].sqrt; out[5 * k + 4] = g_phase[k].cmp;
     if (reset) g_phase[k] = OpCount();
@@ -1532,12 +1559,15 @@ int oracle_stage_block_ex(const ob_geom* G, const double* metric, const double* 
         }
         for (int v = 0; v < nq; ++v) q[v] = Uo[v * NC + ci];
         int it = 0;
+        ORACLE_C2P_CELL_BEGIN();
         status[ci] = (uint8_t)con2prim_point(cm[ci], Q, q, Bd, w, &it);
+        ORACLE_C2P_CELL_END(it);
         if (iters) iters[ci] = it;
         for (int v = 0; v < nq; ++v) Uo[v * NC + ci] = to_d(q[v]);
         for (int v = 0; v < nw; ++v) Wo[v * NC + ci] = to_d(w[v]);
       }
   ORACLE_PHASE(6);
+  ORACLE_C2P_SPLIT();
   return 0;
 }
 

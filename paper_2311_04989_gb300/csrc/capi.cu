@@ -197,6 +197,7 @@ void gr_params_default(gr_params* p) {
   p->rk_g0 = 0.0;
   p->rk_g1 = 1.0;
   p->rk_beta = 1.0;
+  p->atm_band = 1e-12;
 }
 
 int gr_context_create(gr_ctx** ctx, int device) {
@@ -449,7 +450,8 @@ static int check_params(const gr_params* p) {
   if (p->c2p_guess == GR_GUESS_MLP && (!p->mlp || (((uintptr_t)p->mlp) & 15u)))
     return fail(GR_EINVAL, "GR_GUESS_MLP needs a 16-byte aligned device parameter vector in params.mlp");
   if (!(p->gamma_ad > 1.0) || !(p->W_max >= 1.0) || !(p->M_max > 0) || !(p->tol > 0) ||
-      !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0))
+      !(p->rho_atm >= 0) || !(p->p_atm >= 0) || !(p->f_thr >= 0) || !(p->weno_eps > 0) ||
+      !(p->atm_band >= 0 && p->atm_band <= 1e-3))
     return fail(GR_EINVAL, "physical parameter out of range");
   if (p->eos != GR_EOS_IDEAL && p->eos != GR_EOS_TABLE) return fail(GR_EINVAL, "bad eos");
   if (p->eos == GR_EOS_TABLE) {
@@ -470,7 +472,7 @@ static KParams kparams(const gr_params* p, double dt) {
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
   k.rk_form = (p->rk_g0 != 0.0 ? RK_G0 : 0) | (p->rk_g1 != 1.0 ? RK_G1 : 0);
-  k.rho_thr = p->f_thr * p->rho_atm * (1.0 + 1e-6);
+  k.rho_thr = p->f_thr * p->rho_atm * (1.0 + p->atm_band);
   k.dt = dt;
   k.bdt = p->rk_beta * dt;
   k.mlp = p->c2p_guess == GR_GUESS_MLP ? p->mlp : nullptr;
@@ -1583,6 +1585,14 @@ int gr_eos_create(gr_ctx* ctx, const gr_eos_table* in, gr_eos** out) {
   return GR_OK;
 }
 
+int gr_cast_f32(const double* src, float* dst, int64_t n, void* stream) {
+  if (n < 0) return fail(GR_EINVAL, "gr_cast_f32: n < 0");
+  if (n == 0) return GR_OK;
+  if (!src || !dst) return fail(GR_EINVAL, "gr_cast_f32: NULL pointer");
+  cudaError_t e = launch_cast_pool(src, dst, n, (cudaStream_t)stream);
+  return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_cast_f32 launch");
+}
+
 int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], double out[4], void* stream) {
   if (!mesh || !U || !B || !out) return fail(GR_EINVAL, "gr_diag: NULL argument");
   if (!U[0]) return fail(GR_EINVAL, "gr_diag: NULL D array");
@@ -1599,7 +1609,7 @@ int gr_diag(gr_mesh* mesh, const double* const U[5], const double* const B[3], d
   if (e != cudaSuccess) return cuda_fail(e, "gr_diag copy");
   double mindx = 1e300;
   for (const DBlock& b : mesh->h_blocks) mindx = std::min(mindx, std::min(b.dx[0], std::min(b.dx[1], b.dx[2])));
-  const double Bmax = h[3] > 0 ? h[3] : 1.0;
+  const double Bmax = (h[3] > 0 || std::isnan(h[3])) ? h[3] : 1.0;   // a NaN field stays NaN
   out[0] = h[0];
   out[1] = h[1] * mindx / Bmax;
   out[2] = (h[4] > 0) ? h[2] / (Bmax * h[4] / mindx) : 0.0;

@@ -125,7 +125,7 @@ struct KParams {   // gr_params flattened for the device
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
   double rk_g0, rk_g1, rk_beta;
   int rk_form;        // RK_G0 | RK_G1: which of rk_g0 != 0, rk_g1 != 1 hold (set on the host)
-  double rho_thr;     // atmosphere threshold f_thr rho_atm (1 + 1e-6): within 1e-6 of it counts as reached
+  double rho_thr;     // atmosphere threshold f_thr rho_atm (1 + atm_band): within the band counts as reached
   double dt;
   double bdt;         // rk_beta dt
   const double* dt_dev;   // dt on the device (the RK driver's CFL reduction), or nullptr: use dt
@@ -172,6 +172,8 @@ cudaError_t launch_con2prim(const DBlock* blocks, const Work* work, int nwork, i
 cudaError_t launch_c2p_samples(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                                const double* const U[6], const double* const B[3], float* const feats[6],
                                float* target, uint8_t* valid, const KParams& kp, cudaStream_t st);
+// FP32 copy of one FP64 pool by the mixed path's input conversion (d2f_rn)
+cudaError_t launch_cast_pool(const double* src, float* dst, long long n, cudaStream_t st);
 // RK driver (driver.cu): ghost exchange between same-level blocks, CFL dt on the device
 cudaError_t launch_level_fix(int precision, const DBlock* blocks, const LevelFace* lf, int nlf, const Workspace& ws,
                              int table, cudaStream_t st);

@@ -12,7 +12,6 @@
 // whose kernels overlap on the GPU (different streams, or different host threads) race on it and
 // must be serialised by the caller.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -45,7 +44,8 @@ struct NaArgs {
   double* scratch;   // device address of g_na_scratch on the current device
 };
 
-__device__ __forceinline__ void na_max(double& a, double b) { a = b > a ? b : a; }
+// maximum that keeps a NaN, like gr_diag: a field that has gone NaN must not read as finite
+__device__ __forceinline__ void na_max(double& a, double b) { a = (b > a || b != b) ? b : a; }
 
 // slots: 0 sum D dV, 1 max |div B|, 2 sum |div B| dV, 3 max |B|, 4 sum dV
 __global__ void __launch_bounds__(kNaThreads) k_na_partial(const __grid_constant__ NaArgs a) {
@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kNaThreads) k_na_partial(const __grid_constant
     s0 += a.D[c] * dv;
     na_max(s1, fabs(div));
     s2 += fabs(div) * dv;
-    na_max(s3, fmax(fmax(fmax(fabs(bx0), fabs(bx1)), fmax(fabs(by0), fabs(by1))), fmax(fabs(bz0), fabs(bz1))));
+    na_max(s3, fabs(bx0)); na_max(s3, fabs(bx1)); na_max(s3, fabs(by0));
+    na_max(s3, fabs(by1)); na_max(s3, fabs(bz0)); na_max(s3, fabs(bz1));
     s4 += dv;
   }
   __shared__ double sh[kNaThreads / 32][5];
@@ -115,11 +116,6 @@ __global__ void __launch_bounds__(32) k_na_final(double* scratch) {
     fin[0] = s0; fin[1] = s1; fin[2] = s2; fin[3] = s3; fin[4] = s4;
   }
 }
-
-// device address of g_na_scratch, looked up once per device with that device current
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mutex;
-double* g_na_ptr[kNaMaxDevices] = {};
 
 thread_local std::string g_na_error;
 
@@ -167,21 +163,13 @@ extern "C" int gr_diag_noalloc(const gr_block* blocks, int32_t nblocks, const do
   a.total = first;
   a.D = U[0];
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(GR_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kNaMaxDevices) return na_fail(GR_EUNSUPPORTED, "gr_diag_noalloc: device index above 63");
-  {
-    // first call on this device: look up the scratch array's device address (no allocation)
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_na_scratch);
-      if (e != cudaSuccess) return na_fail(GR_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_na_ptr[dev] = static_cast<double*>(p);
-    }
-    a.scratch = g_na_ptr[dev];
-  }
+  // The scratch array's device address belongs to the CUDA context that is current now (the caller's
+  // device, possibly a context of its own, or a fresh one after cudaDeviceReset), so it is looked up on
+  // every call rather than cached; the lookup allocates nothing.
+  void* sp = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&sp, g_na_scratch);
+  if (e != cudaSuccess) return na_fail(GR_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  a.scratch = static_cast<double*>(sp);
   cudaStream_t st = (cudaStream_t)stream;
   k_na_partial<<<kNaCtas, kNaThreads, 0, st>>>(a);
   k_na_final<<<1, 32, 0, st>>>(a.scratch);
@@ -191,7 +179,7 @@ extern "C" int gr_diag_noalloc(const gr_block* blocks, int32_t nblocks, const do
   e = cudaMemcpyAsync(h, a.scratch + (long long)kNaCtas * kNaStride, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return na_fail(GR_ECUDA, std::string("gr_diag_noalloc copy: ") + cudaGetErrorString(e));
-  const double Bmax = h[3] > 0 ? h[3] : 1.0;
+  const double Bmax = (h[3] > 0 || std::isnan(h[3])) ? h[3] : 1.0;   // a NaN field stays NaN
   out[0] = h[0];
   out[1] = h[1] * mindx / Bmax;
   out[2] = (h[4] > 0) ? h[2] / (Bmax * h[4] / mindx) : 0.0;

@@ -28,21 +28,33 @@ template <> __device__ __forceinline__ float rdiv(float a, float b) { return __f
 template <class R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 
 // Precision conversions without the FP64 pipe (on GB300 an F2F conversion is an FP64-pipe
-// instruction, ~1/64 of the FP32 rate).  FP64 -> FP32 rounds to nearest (ties away from zero) and
-// flushes magnitudes below the smallest normal float to signed zero; FP32 -> FP64 is exact.
+// instruction, ~1/64 of the FP32 rate), in integer arithmetic on the IEEE-754 encodings.
+// FP64 -> FP32: round to nearest, ties to even, with gradual underflow (float subnormals) and
+// overflow to infinity, i.e. the IEEE conversion; NaN becomes the canonical quiet NaN of its sign.
+// FP32 -> FP64 is exact.
 __device__ __forceinline__ float d2f_rn(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned long long sgn = u & 0x8000000000000000ull;
   const unsigned long long a = u ^ sgn;
   const unsigned int s32 = (unsigned int)(sgn >> 32);
-  const int e = (int)(a >> 52);
-  if (e >= 0x7FF) return __uint_as_float(s32 | (a > 0x7FF0000000000000ull ? 0x7FC00000u : 0x7F800000u));
-  if (e < 897) return __uint_as_float(s32);                      // below 2^-126
-  if (e > 1150) return __uint_as_float(s32 | 0x7F800000u);      // above the float range
-  const unsigned long long r = a + 0x10000000ull;               // half an FP32 ulp
-  const unsigned int fe = (unsigned int)(r >> 52) - 896u;        // 255 after a carry = inf
-  const unsigned int fm = (unsigned int)(r >> 29) & 0x7FFFFFu;
-  return __uint_as_float(s32 | (fe << 23) | fm);
+  if (a >= 0x7FF0000000000000ull) return __uint_as_float(s32 | (a > 0x7FF0000000000000ull ? 0x7FC00000u : 0x7F800000u));
+  const int e = (int)(a >> 52);                                 // biased binary exponent of |x|
+  if (e >= 1151) return __uint_as_float(s32 | 0x7F800000u);     // |x| >= 2^128
+  if (e >= 897) {                                               // |x| >= 2^-126: a normal float
+    // drop the low 29 significand bits, rounding to nearest even; a carry out of the significand
+    // steps the exponent (and turns 2^128 into infinity); rebias the exponent by 1023 - 127
+    const unsigned long long r = a + 0x0FFFFFFFull + ((a >> 29) & 1ull);
+    return __uint_as_float(s32 | (unsigned int)((r >> 29) - (896ull << 23)));
+  }
+  if (e < 873) return __uint_as_float(s32);                     // |x| < 2^-150: rounds to zero
+  // a float subnormal: |x| = M 2^(e - 1075) with the 53-bit significand M, in units of 2^-149 that is
+  // M / 2^s with s = 926 - e in [30, 53]; round the quotient to nearest even (2^23 is the smallest normal)
+  const int s = 926 - e;
+  const unsigned long long M = (a & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  unsigned long long q = M >> s;
+  const unsigned long long rem = M & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  return __uint_as_float(s32 | (unsigned int)q);
 }
 
 __device__ __forceinline__ double f2d_exact(float f) {
@@ -939,7 +951,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     if (ye < ylo) { ye = ylo; ye_clamped = true; }
     if (ye > yhi) { ye = yhi; ye_clamped = true; }
   }
-  // atmosphere threshold; values within 1e-6 relative of it count as having reached it
+  // atmosphere threshold f_thr rho_atm (1 + atm_band); values within the band count as having reached it
   const double rho_thr = P.rho_thr;
   bool atm = false, reprim = false;
   if (!finite) { st |= GR_ST_FAILED; atm = true; }

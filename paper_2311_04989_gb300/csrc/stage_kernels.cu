@@ -419,7 +419,7 @@ __device__ __forceinline__ void update_all(const DBlock& b, const InView<R>& in,
 // root find runs in k_c2p on the compacted job list).
 // FP64 path: U' of all variables here, left in Uo for k_c2p.
 // Mixed path: D has no source, so D' and the atmosphere test need only the fluxes and sqrt(gamma) of
-// the FP32 metric (same 1e-6 band as the FP64 test); gamma_ij and sqrt(gamma) are the values
+// the FP32 metric (the same band atm_band as the FP64 test); gamma_ij and sqrt(gamma) are the values
 // cellmet_from forms, so the test is the one the full metric would give.  The other variables of a
 // matter cell are formed in k_c2p (update_all), densely packed, so that this kernel carries neither the
 // metric derivatives nor the sources.
@@ -684,7 +684,11 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// out: [0] sum D dV, [1] max |divB|, [2] sum |divB| dV, [3] max |B|, [4] sum dV
+// maximum that keeps a NaN (fmax would drop it and hide a field that has gone NaN)
+__device__ __forceinline__ double max_nan(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// out: [0] sum D dV, [1] max |divB|, [2] sum |divB| dV, [3] max |B|, [4] sum dV; a NaN anywhere in B
+// reaches [1] - [3] (the bit-pattern atomicMax orders a positive NaN above every finite value)
 __global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                 const __grid_constant__ P2CArgs a, double* out) {
   const Work w = work[blockIdx.x];
@@ -704,14 +708,15 @@ __global__ void __launch_bounds__(kTile) k_diag(const DBlock* __restrict__ block
     const double div = (bx1 - bx0) * b.idx[0] + (by1 - by0) * b.idx[1] + (bz1 - bz0) * b.idx[2];
     mdiv = fabs(div);
     sdiv = fabs(div) * dv;
-    mB = fmax(fmax(fmax(fabs(bx0), fabs(bx1)), fmax(fabs(by0), fabs(by1))), fmax(fabs(bz0), fabs(bz1)));
+    mB = max_nan(max_nan(max_nan(fabs(bx0), fabs(bx1)), max_nan(fabs(by0), fabs(by1))),
+                 max_nan(fabs(bz0), fabs(bz1)));
   }
   for (int o = 16; o > 0; o >>= 1) {
     md += __shfl_down_sync(0xffffffffu, md, o);
     dv += __shfl_down_sync(0xffffffffu, dv, o);
     sdiv += __shfl_down_sync(0xffffffffu, sdiv, o);
-    mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
-    mB = fmax(mB, __shfl_down_sync(0xffffffffu, mB, o));
+    mdiv = max_nan(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
+    mB = max_nan(mB, __shfl_down_sync(0xffffffffu, mB, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(out + 0, md);
@@ -761,6 +766,19 @@ static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Sh
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
   dim3 grid(2 * nsm, k);
   k_cast<<<grid, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_pool(const double* src, float* dst, long long n, cudaStream_t st) {
+  CastList L{};
+  L.src[0] = src;
+  L.dst[0] = dst;
+  L.n[0] = n;
+  L.count = 1;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+  k_cast<<<dim3(2 * nsm, 1), 256, 0, st>>>(L);
   return cudaGetLastError();
 }
 

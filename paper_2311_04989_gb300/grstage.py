@@ -36,14 +36,16 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_graph_destroy", "gr_eos_create", "gr_eos_destroy", "gr_eos_bytes", "gr_eos_h0", "gr_autotune",
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
            "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
-           "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong", "gr_host_stage"]
-GR_ABI_VERSION = 2
+           "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong", "gr_host_stage", "gr_cast_f32",
+           "gr_peak_alu"]
+GR_ABI_VERSION = 3
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
 MLP_MEAN, MLP_ISTD, MLP_TMEAN, MLP_TSTD, MLP_STEP = 0, 6, 12, 13, 14
 GR_NKERNELS = 7
 GR_NSTAGE_KERNELS = 6
 GR_DT_GRID, GR_DT_SIGNAL = 0, 1
+GR_MIXED_ATM_BAND = 1e-6
 KERNEL_NAMES = ["k_cast", "k_cellprep", "k_faces", "k_edges", "k_ct", "k_update", "k_c2p"]
 
 
@@ -91,7 +93,8 @@ class gr_params(C.Structure):
                 ("rho_atm", C.c_double), ("p_atm", C.c_double), ("f_thr", C.c_double), ("W_max", C.c_double),
                 ("M_max", C.c_double), ("tol", C.c_double), ("weno_eps", C.c_double), ("rk_g0", C.c_double),
                 ("rk_g1", C.c_double), ("rk_beta", C.c_double), ("mlp", C.c_void_p), ("eos", C.c_int32),
-                ("pad_", C.c_int32), ("table", C.c_void_p), ("T_atm", C.c_double), ("Ye_atm", C.c_double)]
+                ("pad_", C.c_int32), ("table", C.c_void_p), ("T_atm", C.c_double), ("Ye_atm", C.c_double),
+                ("atm_band", C.c_double)]
 
 
 _lib = None
@@ -133,6 +136,8 @@ def load(path: str = LIB_PATH):
     L.gr_eos_h0.argtypes = [vp]
     L.gr_eos_h0.restype = C.c_double
     L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
+    L.gr_cast_f32.argtypes = [vp, vp, C.c_int64, vp]
+    L.gr_peak_alu.argtypes = [i32, i32, i32, C.c_int64, vp, C.POINTER(C.c_double), vp]
     L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
                                   C.POINTER(C.c_double), vp]
     L.gr_noalloc_last_error.restype = C.c_char_p
@@ -281,6 +286,26 @@ def gr_diag(mesh, U, B, stream=None):
     out = (C.c_double * 4)()
     _check(load().gr_diag(mesh, _ptrs(5, list(U)[:5]), _ptrs(3, B), out, _stream(stream)), "gr_diag")
     return list(out)
+
+
+def gr_cast_f32(src, dst, stream=None):
+    """dst[:] = FP32 copy of the FP64 device tensor src (same number of elements), by the mixed path's
+    conversion (IEEE round to nearest even)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("gr_cast_f32: size mismatch")
+    _check(load().gr_cast_f32(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), C.c_int64(n),
+                              _stream(stream)), "gr_cast_f32")
+
+
+def gr_peak_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream=None) -> float:
+    """Launch one throughput loop (0 FP32 FMA, 1 packed FP32x2 FMA, 2 FP64 FMA); returns its flops."""
+    f = C.c_double()
+    rc = load().gr_peak_alu(kind, blocks, threads, C.c_int64(iters), C.c_void_p(sink.data_ptr()), C.byref(f),
+                            _stream(stream))
+    if rc != GR_OK:
+        raise GrstageError(f"gr_peak_alu: {load().gr_strerror(rc).decode()}")
+    return f.value
 
 
 def gr_diag_noalloc(blocks: list[gr_block], U, B, stream=None):

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_pure_host_entries(lib):
-    assert lib.gr_abi_version() == G.GR_ABI_VERSION == 2
+    assert lib.gr_abi_version() == G.GR_ABI_VERSION == 3
     assert lib.gr_mlp_nparam() == G.GR_MLP_NPARAM
     assert lib.gr_strerror(G.GR_EINVAL) == b"invalid argument"
     p = G.gr_params_default()

@@ -92,11 +92,6 @@ def _check64(got, ref, bi, P, label):
     return max(max(cons.values()), be, pe)
 
 
-def _rho_err(got, ref, bi):
-    g, r = H.interior(got["W"][0], bi.n, bi.ng), H.interior(ref["W"][0], bi.n, bi.ng)
-    return float(np.max(np.abs(g - r) / r))
-
-
 def test_shock_tube_ten_rk2_steps_through_the_driver():
     from tests.test_gpu_driver import Run
     bi = I.shock_tube_block(n=(16, 16, 16), g=3)
@@ -126,10 +121,12 @@ def test_single_64cubed_star_fp64_and_mixed():
     ref = GH.oracle_stage([bi], P, 0.25 * bi.dx[0])[0]
     pools, out, dt, _ = _stage_pack([bi], P, G.GR_PREC_FP64)
     _check64(_block_out(pools, out, 0), ref, bi, P, "64^3 star, FP64")
-    pools, out, dt, diag = _stage_pack([bi], P, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
-    er = _rho_err(_block_out(pools, out, 0), ref, bi)
-    print(f"64^3 star, mixed: rho error {er:.2e}, div B {diag[1]:.1e}")
-    assert er < 1e-6 and diag[1] < 1e-14
+    Pm = GH.mixed_params(P)
+    refm = GH.oracle_stage([bi], Pm, 0.25 * bi.dx[0])[0]
+    pools, out, dt, diag = _stage_pack([bi], Pm, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
+    GH.check_mixed([_block_out(pools, out, 0)], [refm], [bi], GH.MIXED_BOUNDS["star"], "64^3 star, mixed")
+    print(f"64^3 star, mixed: div B {diag[1]:.1e}")
+    assert diag[1] < 1e-14
 
 
 def test_amr_like_batch_sampled_blocks():
@@ -141,10 +138,15 @@ def test_amr_like_batch_sampled_blocks():
     pools, out, dt, _ = _stage_pack(blocks, P, G.GR_PREC_FP64)
     for b in sample:
         _check64(_block_out(pools, out, b), refs[b], blocks[b], P, f"AMR-like batch, FP64, block {b} ({sizes[b]}^3)")
-    pools, out, dt, diag = _stage_pack(blocks, P, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
-    er = max(_rho_err(_block_out(pools, out, b), refs[b], blocks[b]) for b in sample)
-    print(f"AMR-like batch, mixed: rho error on the sampled blocks {er:.2e}, div B {diag[1]:.1e}")
-    assert er < 1e-5 and diag[1] < 1e-14
+    Pm = GH.mixed_params(P)
+    dtm = 0.25 * min(min(x.dx) for x in blocks)
+    pools, out, dt, diag = _stage_pack(blocks, Pm, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
+    got = [_block_out(pools, out, b) for b in sample]
+    refm = [GH.oracle_stage([blocks[b]], Pm, dtm)[0] for b in sample]
+    GH.check_mixed(got, refm, [blocks[b] for b in sample], GH.MIXED_BOUNDS["random"],
+                   "AMR-like batch, mixed, sampled blocks")
+    print(f"AMR-like batch, mixed: div B {diag[1]:.1e}")
+    assert diag[1] < 1e-14
 
 
 def test_table_con2prim_workload_sampled_cells():
@@ -230,6 +232,8 @@ def test_two_star_workload_sampled_blocks():
     out = {}
     for prec, tol, guess in ((G.GR_PREC_FP64, 1e-15, G.GR_GUESS_NONE), (G.GR_PREC_MIXED, 1e-10, G.GR_GUESS_FP32)):
         P = O.Params(gamma_ad=2.0, recon=1, rho_atm=mi.rho_atm, p_atm=mi.p_atm, tol=tol)
+        if prec == G.GR_PREC_MIXED:
+            P = GH.mixed_params(P)
         gp = GH.gr_params_from(P, prec, guess)
         U = torch.zeros_like(W)
         mesh = G.gr_mesh_create(GH.ctx(), L.descriptors())
@@ -259,14 +263,17 @@ def test_two_star_workload_sampled_blocks():
             out[prec] = (blk, diag, P)
         finally:
             G.gr_mesh_destroy(mesh)
-    P64 = out[G.GR_PREC_FP64][2]
-    worst, er_mx = 0.0, 0.0
+    P64, Pmx = out[G.GR_PREC_FP64][2], out[G.GR_PREC_MIXED][2]
+    worst = 0.0
+    bis, got_mx, ref_mx = [], [], []
     for b in sample:
         bi = mi.block(b)
         ref = GH.oracle_stage([bi], P64, 0.25 * mi.dx)[0]
         worst = max(worst, _check64(out[G.GR_PREC_FP64][0][b], ref, bi, P64, f"two-star workload, FP64, block {b}"))
-        er_mx = max(er_mx, _rho_err(out[G.GR_PREC_MIXED][0][b], ref, bi))
+        bis.append(bi)
+        got_mx.append(out[G.GR_PREC_MIXED][0][b])
+        ref_mx.append(GH.oracle_stage([bi], Pmx, 0.25 * mi.dx)[0])
+    GH.check_mixed(got_mx, ref_mx, bis, GH.MIXED_BOUNDS["star"], "two-star workload, mixed, sampled blocks")
     diag = out[G.GR_PREC_MIXED][1]
-    print(f"two-star workload: FP64 max error on {len(sample)} sampled blocks {worst:.2e}; mixed rho error "
-          f"{er_mx:.2e}, div B {diag[1]:.1e}")
-    assert er_mx < 1e-6 and diag[1] < 1e-14
+    print(f"two-star workload: FP64 max error on {len(sample)} sampled blocks {worst:.2e}; mixed div B {diag[1]:.1e}")
+    assert diag[1] < 1e-14

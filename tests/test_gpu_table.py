@@ -150,23 +150,15 @@ def test_table_density_outside_the_table_takes_the_nearest_density(eos):
 def test_table_stage_mixed_precision_error_bound(eos, tab):
     import torch
     blocks = [table_block(eos, (16, 16, 16), 330), table_block(eos, (12, 16, 10), 331)]
-    P = O.Params(table=tab, rho_atm=1e-12, T_atm=1e-4, tol=1e-10)
+    P = GH.mixed_params(O.Params(table=tab, rho_atm=1e-12, T_atm=1e-4, tol=1e-10))
     dt = 0.2 * min(blocks[0].dx)
-    g64 = GH.gpu_stage(blocks, P, dt)
     gmx = GH.gpu_stage(blocks, P, dt, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32)
-    worst = 0.0
+    ref = GH.oracle_stage(blocks, P, dt)
+    GH.check_mixed(gmx, ref, blocks, GH.MIXED_BOUNDS["table"], "table stage, mixed vs the oracle")
     for b, bi in enumerate(blocks):
-        r64 = H.interior(g64[b]["W"][0], bi.n, bi.ng)
-        rmx = H.interior(gmx[b]["W"][0], bi.n, bi.ng)
-        worst = max(worst, float(np.max(np.abs(rmx - r64) / r64)))
-        ye64 = H.interior(g64[b]["W"][5], bi.n, bi.ng)
-        yemx = H.interior(gmx[b]["W"][5], bi.n, bi.ng)
-        assert np.max(np.abs(yemx - ye64)) < 1e-6
         div = O.divb(bi.n, bi.ng, bi.dx, gmx[b]["B"])
         bmax = max(np.max(np.abs(x)) for x in gmx[b]["B"])
         assert np.max(np.abs(H.interior(div, bi.n, bi.ng))) * min(bi.dx) / bmax < 1e-14
-    print(f"table stage, mixed vs FP64: max relative rho error {worst:.2e}")
-    assert worst < 2e-6
 
 
 def test_table_learned_bracket_saves_evaluations(eos, tab):

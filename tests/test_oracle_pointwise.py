@@ -319,15 +319,23 @@ def test_con2prim_lorentz_factor_clamp():
 
 
 def test_con2prim_cells_at_the_atmosphere_density_are_reset_deterministically():
-    """Cells whose density equals f_thr rho_atm to within 1e-6 relative take the atmosphere branch;
-    cells clearly above it are solved."""
-    P = O.Params(gamma_ad=GAMMA, rho_atm=1e-13, p_atm=1e-24)
-    n = 6
+    """Sec. 3.5 resets a cell whose density falls below f_thr rho_atm.  At the default band (1e-12)
+    cells equal to the threshold up to FP64 rounding take the atmosphere branch and every cell above
+    it by more than that is solved (1 + 1e-9 included); a wider band, passed as a parameter (the mixed
+    path's FP32 sqrt(gamma) classification tolerance, 1e-6), takes the cells within it too."""
+    n = 7
     m = np.zeros((n, 16)); m[:, 0] = 1; m[:, 4] = m[:, 7] = m[:, 9] = 1
     w = np.zeros((n, 5))
-    w[:, 0] = 1e-13 * np.array([1 - 1e-15, 1.0, 1 + 1e-15, 1 + 5e-7, 1 + 1e-5, 2.0])
+    w[:, 0] = 1e-13 * np.array([1 - 1e-15, 1.0, 1 + 1e-15, 1 + 1e-9, 1 + 5e-7, 1 + 1e-5, 2.0])
     w[:, 4] = 1e-24
-    q = O.prim2con(m, w, np.zeros((n, 3)), P)
-    w2, q2, st, _ = O.con2prim(m, q, np.zeros((n, 3)), P)
-    assert list(st & 1) == [1, 1, 1, 1, 0, 0]
-    assert np.all(w2[:4, 4] == 1e-24) and np.all(w2[:4, 0] == 1e-13)
+    for band, expect in ((None, [1, 1, 1, 0, 0, 0, 0]), (1e-6, [1, 1, 1, 1, 1, 0, 0])):
+        P = O.Params(gamma_ad=GAMMA, rho_atm=1e-13, p_atm=1e-24)
+        if band is not None:
+            P.atm_band = band
+        q = O.prim2con(m, w, np.zeros((n, 3)), P)
+        w2, q2, st, _ = O.con2prim(m, q, np.zeros((n, 3)), P)
+        assert list(st & 1) == expect, (band, st)
+        k = int(np.sum(expect))
+        assert np.all(w2[:k, 4] == 1e-24) and np.all(w2[:k, 0] == 1e-13)
+        # solved cells keep their density (flat metric, at rest: rho = D exactly up to the solve)
+        assert np.allclose(w2[k:, 0], w[k:, 0], rtol=1e-12, atol=0)

@@ -158,3 +158,20 @@ def test_periodic_block_conserves(flat):
         assert np.all(np.abs(s1 - s0) < 1e-14 * scale)
     d = H.interior(Uo - U, n, g)
     assert np.max(np.abs(d[0])) > 1e-8 * np.max(np.abs(H.interior(U, n, g)[0]))   # it did evolve
+
+
+def test_operation_counts_split_con2prim_by_kind_of_cell():
+    """The counting build of the stage (algorithmic operations per phase, for the rooflines) books the
+    con2prim of cells reset to the atmosphere without a root find apart from the cells it solves."""
+    P = O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-10, tol=1e-12)
+    matter = I.uniform_block(n=(4, 4, 4), g=3, rho=1e-3, p=1e-5)
+    atm = I.uniform_block(n=(4, 4, 4), g=3, rho=1e-10, u=(0.0, 0.0, 0.0), p=P.K_poly * 1e-20, B=(0.0, 0.0, 0.0))
+    for bi, solved in ((matter, True), (atm, False)):
+        U = H.cons_from_prims(bi, P)
+        c = O.stage_block_count(H.to_oracle(bi), U, U, bi.B, 0.01, P)
+        assert set(c) == set(O.PHASES)
+        n_solve, n_atm = sum(c["con2prim"]), sum(c["con2prim_atmosphere"])
+        assert (n_solve > 0, n_atm == 0) == (solved, solved), (bi is matter, c)
+        assert sum(c["faces"]) > 0 and sum(c["update_and_sources"]) > 0
+        Uo, Bo, Wo, st = run_stage(bi, P, 0.01, U=U)
+        assert bool(np.any(H.interior(st, bi.n, bi.ng) & 1)) != solved
