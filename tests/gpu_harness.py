@@ -214,35 +214,81 @@ def compare(gpu, ref, blocks=None, skip=(), floors=None):
     return errs
 
 
+def mixed_errors(gpu, ref, blocks):
+    """Per-variable error of a mixed-path output against the oracle's, over interior cells / faces of all
+    blocks, each in the measure natural to it:
+      D, rho, p (and D Y_e, T with a table)   relative |x - x_ref| / |x_ref|
+      S_j, tau                                 relative to the cell's energy scale, max(|x_ref|, D + |tau|)
+      u~^i (and Y_e)                           absolute (u~ = W v in units of c): they pass through zero, and
+                                               the rounding of an FP32 flux moves them by an amount set by
+                                               the flux, not by their own size
+      B^d                                      |B - B_ref| / max |B_ref| of the block
+    and the number of cells whose status (physics bits) differs."""
+    names_u = ["D", "S_x", "S_y", "S_z", "tau", "DYe"]
+    names_w = ["rho", "u_x", "u_y", "u_z", "p", "Ye", "T"]
+    errs = {}
+    nmis = 0
+    for b, (g, r) in enumerate(zip(gpu, ref)):
+        n, ng = _geom(g, r, blocks, b)
+        gu, ru = H.interior(g["U"], n, ng), H.interior(r["U"], n, ng)
+        gw, rw = H.interior(g["W"], n, ng), H.interior(r["W"], n, ng)
+        if not ru.size:
+            continue
+        for v in range(ru.shape[0]):
+            if v in (0, 5):
+                den = np.maximum(np.abs(ru[v]), 1e-300)
+            else:
+                den = np.maximum(np.abs(ru[v]), np.abs(ru[0]) + np.abs(ru[4]))
+            errs[names_u[v]] = max(errs.get(names_u[v], 0.0), float(np.max(np.abs(gu[v] - ru[v]) / den)))
+        for v in range(rw.shape[0]):
+            d = np.abs(gw[v] - rw[v])
+            e = float(np.max(d)) if v in (1, 2, 3, 5) else float(np.max(d / np.maximum(np.abs(rw[v]), 1e-300)))
+            errs[names_w[v]] = max(errs.get(names_w[v], 0.0), e)
+        for d, (gf, rf) in enumerate(zip(H.interior_faces(g["B"], n, ng), H.interior_faces(r["B"], n, ng))):
+            scale = max(float(np.max(np.abs(rf))), 1e-300) if rf.size else 1.0
+            e = float(np.max(np.abs(gf - rf))) / scale if rf.size else 0.0
+            errs[f"B_{'xyz'[d]}"] = max(errs.get(f"B_{'xyz'[d]}", 0.0), e)
+        nmis += int(np.sum((H.interior(g["status"], n, ng) & 0x3F) != H.interior(r["status"], n, ng)))
+    errs["status_mismatch"] = nmis
+    return errs
+
+
 # Bounds of the mixed path (FP32 reconstruction, HLLE and EMFs; FP64 accumulation, CT and con2prim)
-# against the FP64 oracle at the same atmosphere band, per variable with compare()'s denominators, per
-# kind of workload.  rho and D carry the stated 1e-6; the others are set a few times above what the GPU
-# measured (printed by every test that uses them): FP32 fluxes carry a relative rounding of ~1e-7 of the
-# largest terms in a face's flux, which reaches the conserved variables scaled by dt/dx and the
-# primitives through con2prim's conditioning (the pressure of cold gas, velocities of near-static
-# matter).
-_M = dict(U0=1e-6, W0=1e-6)
+# against the FP64 oracle at the same atmosphere band, in mixed_errors()'s measures, per kind of
+# workload.  rho and D carry the stated 1e-6; the others sit a few times above what the GPU measured
+# (every test prints its numbers).  An FP32 flux carries a relative rounding of ~1e-7 of its largest
+# terms, which reaches the conserved variables scaled by dt/dx, the pressure through con2prim's
+# conditioning (cold gas, where p is a small part of the energy, magnifies it), and the velocities as an
+# absolute amount.  Static stars add one more effect: the corner EMF takes its upwind correction from the
+# side the face mass flux points to, and in a star in equilibrium that flux is rounding noise, whose sign
+# differs between FP32 and FP64 fluxes; the two choices differ by the correction itself, so B' there
+# agrees to the size of the upwind correction (a truncation-level amount, ~1e-4 of max |B|), not to
+# rounding (test_single_64cubed_star_fp64_and_mixed shows the plain-mean EMF, which has no switch,
+# agreeing to rounding).
+_M = dict(D=1e-6, rho=1e-6, S_x=2e-7, S_y=2e-7, S_z=2e-7, tau=3e-7)
 MIXED_BOUNDS = {
-    "random": dict(_M, U1=1e-3, U2=1e-3, U3=1e-3, U4=1e-3, W1=1e-3, W2=1e-3, W3=1e-3, W4=1e-3,
-                   B0=1e-3, B1=1e-3, B2=1e-3),
-    "star": dict(_M, U1=1e-3, U2=1e-3, U3=1e-3, U4=1e-3, W1=1e-3, W2=1e-3, W3=1e-3, W4=1e-3,
-                 B0=1e-3, B1=1e-3, B2=1e-3),
-    # PPM's limiter can take the other branch where two candidates agree to FP32 rounding (star surface)
-    "star_ppm": dict(U0=1e-5, W0=1e-5, U1=1e-3, U2=1e-3, U3=1e-3, U4=1e-3, W1=1e-3, W2=1e-3, W3=1e-3,
-                     W4=1e-3, B0=1e-3, B1=1e-3, B2=1e-3),
-    "driver": dict(_M, U1=1e-3, U2=1e-3, U3=1e-3, U4=1e-3, W1=1e-3, W2=1e-3, W3=1e-3, W4=1e-3,
-                   B0=1e-3, B1=1e-3, B2=1e-3),
-    "table": dict(_M, U1=1e-3, U2=1e-3, U3=1e-3, U4=1e-3, U5=1e-6, W1=1e-3, W2=1e-3, W3=1e-3, W4=1e-3,
-                  W5=1e-6, W6=1e-3, B0=1e-3, B1=1e-3, B2=1e-3),
+    # measured (GB300): u~ <= 3.4e-8, p <= 5.3e-6, B <= 3.3e-8, S <= 3.4e-8, tau <= 4.4e-8
+    "random": dict(_M, u_x=1e-7, u_y=1e-7, u_z=1e-7, p=2e-5, B_x=1e-7, B_y=1e-7, B_z=1e-7),
+    # one RK3 step: u~ <= 1.8e-8, p <= 2.1e-6, B <= 1.6e-8
+    "driver": dict(_M, u_x=1e-7, u_y=1e-7, u_z=1e-7, p=1e-5, B_x=1e-7, B_y=1e-7, B_z=1e-7),
+    # u~ <= 6.4e-8, p <= 1.2e-5, T <= 1.0e-5, Y_e <= 3.6e-8, D Y_e <= 2.7e-7, S <= 7.2e-8, tau <= 9.5e-8
+    "table": dict(_M, DYe=1e-6, u_x=2e-7, u_y=2e-7, u_z=2e-7, p=5e-5, Ye=1e-7, T=5e-5, B_x=1e-7, B_y=1e-7,
+                  B_z=1e-7),
+    # stars in equilibrium: p <= 9.1e-4 (cold outer layers), B <= 5.2e-4 (EMF upwind switch), u~ <= 9.1e-9
+    "star": dict(_M, u_x=1e-7, u_y=1e-7, u_z=1e-7, p=3e-3, B_x=2e-3, B_y=2e-3, B_z=2e-3),
+    # PPM's limiter can take the other branch where two candidates agree to FP32 rounding (star surface):
+    # rho <= 5.2e-6, p <= 1.8e-4, B <= 3.4e-4, u~ <= 4.1e-8
+    "star_ppm": dict(_M, D=2e-5, rho=2e-5, u_x=2e-7, u_y=2e-7, u_z=2e-7, p=1e-3, B_x=1e-3, B_y=1e-3, B_z=1e-3),
 }
 
 
 def check_mixed(out, ref, blocks, bounds, label=""):
     """Mixed-path output against the oracle's: statuses equal (physics bits), and every variable named
-    in bounds within its bound.  Prints the per-variable errors; returns them."""
-    e = compare(out, ref, blocks)
+    in bounds within its bound (mixed_errors()'s measures).  Prints the per-variable errors; returns
+    them."""
+    e = mixed_errors(out, ref, blocks)
     mis = e.pop("status_mismatch")
-    print(f"{label}: " + ", ".join(f"{k} {v:.1e}" for k, v in sorted(e.items())) + f"; status mismatches {mis}")
+    print(f"{label}: " + ", ".join(f"{k} {v:.1e}" for k, v in e.items()) + f"; status mismatches {mis}")
     assert mis == 0, (label, mis)
     bad = {k: (e[k], b) for k, b in bounds.items() if k in e and not e[k] < b}
     assert not bad, (label, bad)
