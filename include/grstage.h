@@ -85,17 +85,30 @@ typedef struct {
 } gr_block;
 
 /* The 3+1 metric on vertices (Sec. 3.2).  order: Lagrange interpolation order 2 or 4 (order 4 needs
- * one ghost more than the reconstruction stencil).  k_zero != 0 declares K_ij = 0 (v[10..15] unread). */
+ * one ghost more than the reconstruction stencil).  k_zero != 0 declares K_ij = 0 (v[10..15] unread).
+ * v32 (mixed path only, optional): FP32 copies of the components in the same layout, equal to
+ * gr_cast_f32 of v (e.g. made once for a metric that does not change between stages); with v32[0] != NULL
+ * every component the stage reads must be given (10, or 16 with K_ij) and the stage converts nothing of
+ * the metric.  All NULL: the stage makes its own FP32 copy. */
 typedef struct {
   const double* v[16];
   int32_t order;
   int32_t k_zero;
+  const float* v32[16];
 } gr_metric;
 
 /* Stage state.  Inputs must have their ghost zones filled by the caller (the stage itself exchanges
  * nothing).  U, U0 and B0 are read on the interior only; W and B on the interior and the ghosts.
  * Outputs are written on the interior only: Uo (cells), Bo (all faces of interior cells), Wo, status.
- * Outputs must not alias inputs. */
+ * Outputs must not alias inputs.
+ * FP32 copies (mixed path only; the FP64 path ignores them).  The mixed path reconstructs from FP32
+ * copies of W and B; by default it makes them itself at the start of every stage.  W32/B32 (optional)
+ * hand it ready copies instead: every element the stage reads (interior and ghosts) must equal
+ * gr_cast_f32 of the FP64 value, so the results are those of the default path bitwise.  Wo32/Bo32
+ * (optional) ask the stage to write FP32 copies of its outputs Wo/Bo wherever it writes them (the next
+ * stage's W32/B32 once their ghosts are filled).  Each group is all or none: W32[0] != NULL needs W32 of
+ * every primitive the stage reads (5, or 6 with a table) and B32[0..2]; likewise Wo32 (5 or 6: T has no
+ * copy) and Bo32.  They must not alias W32/B32. */
 typedef struct {
   const double* U[6];    /* U[5] = D Y_e: tabulated EOS only (NULL otherwise) */
   const double* U0[6];   /* RK register; read only where rk_g0 != 0 */
@@ -106,6 +119,10 @@ typedef struct {
   double* Bo[3];
   double* Wo[7];         /* Wo[5], Wo[6] = Y_e, T written with a table */
   uint8_t* status;
+  const float* W32[6];   /* optional FP32 copies of W[0..5] and B (mixed path) */
+  const float* B32[3];
+  float* Wo32[6];        /* optional FP32 copies of Wo[0..5] and Bo, written with them (mixed path) */
+  float* Bo32[3];
 } gr_state;
 
 /* Tabulated EOS (Sec. 2.2.1): log p, log e (e = rho (1 + eps), the total energy density) and c_s^2 on a

@@ -496,10 +496,13 @@ static KParams kparams(const gr_params* p, double dt) {
 static int metric_view(const gr_metric* metric, MetricView& mv, bool need_K) {
   if (!metric) return fail(GR_EINVAL, "metric is NULL");
   if (metric->order != 2 && metric->order != 4) return fail(GR_EINVAL, "metric order must be 2 or 4");
+  const bool has32 = metric->v32[0] != nullptr;
   for (int c = 0; c < 16; ++c) {
     mv.v[c] = metric->v[c];
+    mv.v32[c] = has32 ? metric->v32[c] : nullptr;
     const bool needed = c < 10 || (need_K && !metric->k_zero);
     if (needed && !mv.v[c]) return fail(GR_EINVAL, "metric component pointer is NULL");
+    if (needed && has32 && !mv.v32[c]) return fail(GR_EINVAL, "metric: v32 given for some components only");
   }
   mv.order = metric->order;
   mv.k_zero = metric->k_zero;
@@ -710,6 +713,8 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
   if (!mesh || !metric || !state) return fail(GR_EINVAL, "gr_host_stage: NULL argument");
   if (nbatch < 1 || nbatch > 1024) return fail(GR_EINVAL, "gr_host_stage: nbatch must be 1..1024");
   if (mesh->ws.nlvl) return fail(GR_EUNSUPPORTED, "gr_host_stage: not with level faces (batches would split them)");
+  if (metric->v32[0] || state->W32[0] || state->Wo32[0])
+    return fail(GR_EUNSUPPORTED, "gr_host_stage: FP32 copies of the pools are not taken from host memory");
   // the host arrays pass the same checks as a device stage
   MetricView mv0;
   StateView sv0{};
@@ -800,6 +805,7 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
     // its stage, on the staging pools advanced to the batch's first elements
     gr_metric md = *metric;
     for (int c = 0; c < 16; ++c) md.v[c] = c < nm ? h->M[c] + v0 : nullptr;
+    for (int c = 0; c < 16; ++c) md.v32[c] = nullptr;
     gr_state sd{};
     for (int v = 0; v < nq; ++v) {
       sd.U[v] = h->U[v] + c0;
@@ -893,6 +899,30 @@ static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state*
   s.status = state->status;
   if (!s.status) return fail(GR_EINVAL, "gr_stage: status is NULL");
   s.evals = nullptr;
+  // optional FP32 copies of the inputs and outputs (mixed path; all of a group or none)
+  const int n32 = tab ? 6 : 5;
+  if (params->precision == GR_PREC_MIXED) {
+    if (state->W32[0]) {
+      for (int v = 0; v < n32; ++v)
+        if (!state->W32[v]) return fail(GR_EINVAL, "gr_stage: W32 given for some primitives only");
+      for (int d = 0; d < 3; ++d)
+        if (!state->B32[d]) return fail(GR_EINVAL, "gr_stage: W32 needs B32");
+      for (int v = 0; v < n32; ++v) s.W32[v] = state->W32[v];
+      for (int d = 0; d < 3; ++d) s.B32[d] = state->B32[d];
+    }
+    if (state->Wo32[0]) {
+      for (int v = 0; v < n32; ++v)
+        if (!state->Wo32[v]) return fail(GR_EINVAL, "gr_stage: Wo32 given for some primitives only");
+      for (int d = 0; d < 3; ++d)
+        if (!state->Bo32[d]) return fail(GR_EINVAL, "gr_stage: Wo32 needs Bo32");
+      for (int v = 0; v < n32; ++v) s.Wo32[v] = state->Wo32[v];
+      for (int d = 0; d < 3; ++d) s.Bo32[d] = state->Bo32[d];
+      for (int v = 0; v < n32; ++v)
+        if ((const float*)s.Wo32[v] == s.W32[v]) return fail(GR_EINVAL, "gr_stage: Wo32 must not alias W32");
+      for (int d = 0; d < 3; ++d)
+        if ((const float*)s.Bo32[d] == s.B32[d]) return fail(GR_EINVAL, "gr_stage: Bo32 must not alias B32");
+    }
+  }
   return GR_OK;
 }
 
@@ -1278,6 +1308,10 @@ struct gr_driver {
   double* U[2][6] = {};
   double* W[2][7] = {};
   double* B[2][3] = {};
+  // mixed path: FP32 copies of the stage buffers' W and B, written by the stage that produces them and
+  // ghost-filled with them, so that a later stage of the step converts nothing
+  float* W32[2][6] = {};
+  float* B32[2][3] = {};
   uint8_t* status = nullptr;
   std::vector<void*> allocs;
 };
@@ -1333,6 +1367,9 @@ int gr_driver_create(gr_mesh* mesh, const int32_t* nbr, gr_driver** out) {
     for (int v = 0; v < 6 && e == cudaSuccess; ++v) e = dalloc(sizeof(double) * nc, (void**)&d->U[k][v]);
     for (int v = 0; v < 7 && e == cudaSuccess; ++v) e = dalloc(sizeof(double) * nc, (void**)&d->W[k][v]);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(double) * mesh->sh.nface[a], (void**)&d->B[k][a]);
+    // FP32 copies of the stage buffers' W and B for the mixed path (made here: a step may be captured)
+    for (int v = 0; v < 6 && e == cudaSuccess; ++v) e = dalloc(sizeof(float) * nc, (void**)&d->W32[k][v]);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = dalloc(sizeof(float) * mesh->sh.nface[a], (void**)&d->B32[k][a]);
   }
   if (e == cudaSuccess) e = dalloc(std::max<long long>(nc, 1), (void**)&d->status);
   if (e != cudaSuccess) {
@@ -1419,6 +1456,8 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
     const cudaError_t e = launch_set_scalar(d->d_dt, cfl * mindx, st);
     if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step dt");
   }
+  // mixed path on a mesh without level maps: FP32 copies chained between the stages
+  const bool chain32 = params->precision == GR_PREC_MIXED && !m->nrwork && !m->npwork;
   double* inU[6];
   double* inW[7];
   double* inB[3];
@@ -1447,6 +1486,16 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
       state.Bo[a] = last ? B[a] : d->B[s % 2][a];
     }
     state.status = last ? status : d->status;
+    if (chain32) {
+      if (s > 0) {   // the previous stage's outputs, FP32 copies included, ghosts filled below
+        for (int v = 0; v < 6; ++v) state.W32[v] = d->W32[(s - 1) % 2][v];
+        for (int a = 0; a < 3; ++a) state.B32[a] = d->B32[(s - 1) % 2][a];
+      }
+      if (!last) {
+        for (int v = 0; v < 6; ++v) state.Wo32[v] = d->W32[s % 2][v];
+        for (int a = 0; a < 3; ++a) state.Bo32[a] = d->B32[s % 2][a];
+      }
+    }
     MetricView mv;
     StateView sv{};
     // the last stage writes over the step's input (also its U0, B0): each thread reads U0, B0 of
@@ -1463,7 +1512,12 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
       for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];
       for (int v = 0; v < nw; ++v) inW[v] = d->W[s % 2][v];
       for (int a = 0; a < 3; ++a) inB[a] = d->B[s % 2][a];
-      if ((r = driver_fill(d, inW, nw, inB, stream))) return r;
+      if (chain32) {   // same-level ghosts of the FP64 buffers and their FP32 copies in one pass
+        e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, inW, nw, inB, st, d->W32[s % 2], d->B32[s % 2]);
+        if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step ghost fill");
+      } else if ((r = driver_fill(d, inW, nw, inB, stream))) {
+        return r;
+      }
     }
   }
   return GR_OK;

@@ -21,6 +21,8 @@ struct GhostArgs {
   int nw;
   double* B[3];
   const int* nbr;   // 27 entries per block
+  float* W32[6];    // optional FP32 copies of W[0..5] and B (the mixed path's reconstruction input): their
+  float* B32[3];    // ghosts get the FP32 conversion of the copied FP64 value
 };
 
 __device__ __forceinline__ int nbr_slot(const int o[3]) { return (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1); }
@@ -128,6 +130,13 @@ __device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sba
 #pragma unroll
         for (int k = 0; k < 7; ++k)
           if (k < a.nw && dst[u] >= 0) a.W[k][dst[u]] = v[u][k];
+      if (a.W32[0]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            if (k < a.nw && dst[u] >= 0) a.W32[k][dst[u]] = d2f_rn(v[u][k]);
+      }
     } else {
       double v[U];
 #pragma unroll
@@ -136,6 +145,11 @@ __device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sba
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (dst[u] >= 0) a.B[D][dst[u]] = v[u];
+      if (a.B32[D]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (dst[u] >= 0) a.B32[D][dst[u]] = d2f_rn(v[u]);
+      }
     }
   }
 }
@@ -223,12 +237,16 @@ __global__ void k_cfl_dt(const double* rate, double cfl, double* dt) {
 }
 
 cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
-                              double* const B[3], cudaStream_t st) {
+                              double* const B[3], cudaStream_t st, float* const* W32, float* const* B32) {
   GhostArgs a{};
   for (int v = 0; v < 7; ++v) a.W[v] = v < nw ? W[v] : nullptr;
   a.nw = nw;
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];
   a.nbr = nbr;
+  if (W32 && B32) {
+    for (int v = 0; v < 6; ++v) a.W32[v] = v < nw ? W32[v] : nullptr;
+    for (int d = 0; d < 3; ++d) a.B32[d] = B32[d];
+  }
   if (nblocks) k_ghost<<<4 * nblocks, kGhostTile, 0, st>>>(blocks, a);
   return cudaGetLastError();
 }

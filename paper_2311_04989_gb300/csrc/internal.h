@@ -44,6 +44,7 @@ struct MetricView {
   const double* v[16];
   int order;
   int k_zero;
+  const float* v32[16];   // caller's FP32 copies (mixed path) or nullptr
 };
 struct StateView {
   const double* U[6];     // [5] = D Y_e (table)
@@ -56,6 +57,10 @@ struct StateView {
   double* Wo[7];
   uint8_t* status;
   int32_t* evals;         // FP64 master-function evaluations per cell (gr_con2prim), or nullptr
+  const float* W32[6];    // caller's FP32 copies of W, B (mixed path) or nullptr
+  const float* B32[3];
+  float* Wo32[6];         // FP32 copies of Wo, Bo to write (mixed path) or nullptr
+  float* Bo32[3];
 };
 // Stage inputs seen in the arithmetic type R of a kernel: the caller's FP64 pools (R = double) or
 // the FP32 copies made by the cast pass (R = float).  Same element indexing as the caller pools.
@@ -192,8 +197,10 @@ cudaError_t launch_adm(int precision, const DBlock* blocks, const Work* cw, int 
                        size_t smem, const MetricView& m, const double* const W[7], const double* const B[3],
                        const KParams& kp, int vc_order, void* const cv[10], double* const out[10], cudaStream_t st);
 constexpr int kGhostTile = 512;
+// W32/B32 (optional): FP32 copies of W (up to 6 pools) and B whose ghosts get the converted copied values
 cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
-                              double* const B[3], cudaStream_t st);
+                              double* const B[3], cudaStream_t st, float* const* W32 = nullptr,
+                              float* const* B32 = nullptr);
 cudaError_t launch_cfl_dt(const DBlock* blocks, const Work* wi, int nwi, const MetricView& m,
                           const double* const W[7], const double* const B[3], const KParams& kp, double cfl,
                           double* rate, double* dt, cudaStream_t st);

@@ -302,6 +302,7 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
   double Bn = fma(-stage_bdt(kp), curl, (RKF & RK_G1) ? kp.rk_g1 * B : B);
   if constexpr ((RKF & RK_G0) != 0) Bn = fma(kp.rk_g0, s.B0[D][f], Bn);
   s.Bo[D][f] = Bn;
+  if (s.Bo32[D]) s.Bo32[D][f] = d2f_rn(Bn);
 }
 
 template <class R, int RKF>
@@ -353,11 +354,15 @@ __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<doubl
 template <int EOS>
 __device__ __forceinline__ void write_cell(const StateView& s, long long c, const double q[6], const double w[7],
                                            int st) {
-  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5;
+  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5, N32 = EOS ? 6 : 5;
 #pragma unroll
   for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
 #pragma unroll
   for (int v = 0; v < NW; ++v) s.Wo[v][c] = w[v];
+  if (s.Wo32[0]) {   // FP32 copies of the new primitives (the next stage's reconstruction input)
+#pragma unroll
+    for (int v = 0; v < N32; ++v) s.Wo32[v][c] = d2f_rn(w[v]);
+  }
   if (s.status) s.status[c] = (uint8_t)st;   // optional for gr_con2prim
 }
 
@@ -740,26 +745,33 @@ static InView<double> view64(const MetricView& m, const StateView* s) {
   return v;
 }
 
-static InView<float> view32(const MetricView& m, const Shadow& sh) {
+// FP32 inputs of the mixed path: the caller's copies where given (metric->v32, state W32/B32), else the
+// mesh's own, which launch_cast fills
+static InView<float> view32(const MetricView& m, const StateView& s, const Shadow& sh) {
   InView<float> v;
-  for (int c = 0; c < 16; ++c) v.M[c] = sh.M[c];
-  for (int q = 0; q < 6; ++q) v.W[q] = sh.W[q];
-  for (int d = 0; d < 3; ++d) v.B[d] = sh.B[d];
+  for (int c = 0; c < 16; ++c) v.M[c] = m.v32[0] ? m.v32[c] : sh.M[c];
+  for (int q = 0; q < 6; ++q) v.W[q] = s.W32[0] ? s.W32[q] : sh.W[q];
+  for (int d = 0; d < 3; ++d) v.B[d] = s.W32[0] ? s.B32[d] : sh.B[d];
   v.order = m.order;
   v.k_zero = m.k_zero;
   return v;
 }
 
+// the conversions a mixed stage needs: W and B unless the caller gave copies, the metric unless the
+// caller gave one or (cast_metric = false) the previous stage on this mesh made it
 static cudaError_t launch_cast(const MetricView& m, const StateView& s, const Shadow& sh, int eos,
                                cudaStream_t st, bool cast_metric) {
   CastList L;
   int k = 0;
   const int nw = eos == GR_EOS_TABLE ? 6 : 5;   // rho, u~^i, p[, Y_e]
-  for (int q = 0; q < nw; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
-  for (int d = 0; d < 3; ++d) { L.src[k] = s.B[d]; L.dst[k] = sh.B[d]; L.n[k] = sh.nface[d]; ++k; }
-  const int ncomp = cast_metric ? (m.k_zero ? 10 : 16) : 0;
+  if (!s.W32[0]) {
+    for (int q = 0; q < nw; ++q) { L.src[k] = s.W[q]; L.dst[k] = sh.W[q]; L.n[k] = sh.ncell; ++k; }
+    for (int d = 0; d < 3; ++d) { L.src[k] = s.B[d]; L.dst[k] = sh.B[d]; L.n[k] = sh.nface[d]; ++k; }
+  }
+  const int ncomp = (cast_metric && !m.v32[0]) ? (m.k_zero ? 10 : 16) : 0;
   for (int c = 0; c < ncomp; ++c) { L.src[k] = m.v[c]; L.dst[k] = sh.M[c]; L.n[k] = sh.nvert; ++k; }
   L.count = k;
+  if (k == 0) return cudaSuccess;
   // two 256-thread CTAs per SM and pool, striding over it
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -839,7 +851,7 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[S
     cudaError_t e = launch_cast(m, s, sh, kp.eos, st, cast_metric);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    const InView<float> in32 = view32(m, sh);
+    const InView<float> in32 = view32(m, s, sh);
     return tab ? stage_impl<float, GR_EOS_TABLE>(blocks, kl, in32, in64, s, ws, kp, st, ev)
                : stage_impl<float, GR_EOS_IDEAL>(blocks, kl, in32, in64, s, ws, kp, st, ev);
   }

@@ -59,13 +59,14 @@ class gr_block(C.Structure):
 
 
 class gr_metric(C.Structure):
-    _fields_ = [("v", C.c_void_p * 16), ("order", C.c_int32), ("k_zero", C.c_int32)]
+    _fields_ = [("v", C.c_void_p * 16), ("order", C.c_int32), ("k_zero", C.c_int32), ("v32", C.c_void_p * 16)]
 
 
 class gr_state(C.Structure):
     _fields_ = [("U", C.c_void_p * 6), ("U0", C.c_void_p * 6), ("B", C.c_void_p * 3), ("B0", C.c_void_p * 3),
                 ("W", C.c_void_p * 7), ("Uo", C.c_void_p * 6), ("Bo", C.c_void_p * 3), ("Wo", C.c_void_p * 7),
-                ("status", C.c_void_p)]
+                ("status", C.c_void_p), ("W32", C.c_void_p * 6), ("B32", C.c_void_p * 3), ("Wo32", C.c_void_p * 6),
+                ("Bo32", C.c_void_p * 3)]
 
 
 class gr_shape(C.Structure):
@@ -551,14 +552,32 @@ class Layout:
         return int(sum(n[0] * n[1] * n[2] for n in self.n))
 
 
-def metric_struct(metric_pool, order: int = 2, k_zero: bool = True) -> gr_metric:
-    """metric_pool: (16, nvert) device tensor."""
+def metric_struct(metric_pool, order: int = 2, k_zero: bool = True, metric32=None) -> gr_metric:
+    """metric_pool: (16, nvert) device tensor; metric32: optional FP32 copy of it (mixed path)."""
     m = gr_metric()
     for c in range(16):
         m.v[c] = int(metric_pool[c].data_ptr())
+        if metric32 is not None:
+            m.v32[c] = int(metric32[c].data_ptr())
     m.order = order
     m.k_zero = 1 if k_zero else 0
     return m
+
+
+def set_fp32_copies(state: gr_state, W32=None, B32=None, Wo32=None, Bo32=None) -> gr_state:
+    """Point the optional FP32 copies of a gr_state (mixed path) at device tensors: W32 / Wo32 up to 6
+    cell pools, B32 / Bo32 three face pools (None leaves a group unset)."""
+    if W32 is not None:
+        for v in range(min(6, len(W32))):
+            state.W32[v] = int(W32[v].data_ptr())
+        for d in range(3):
+            state.B32[d] = int(B32[d].data_ptr())
+    if Wo32 is not None:
+        for v in range(min(6, len(Wo32))):
+            state.Wo32[v] = int(Wo32[v].data_ptr())
+        for d in range(3):
+            state.Bo32[d] = int(Bo32[d].data_ptr())
+    return state
 
 
 def state_struct(U, U0, B, B0, W, Uo, Bo, Wo, status) -> gr_state:

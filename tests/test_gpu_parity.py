@@ -200,6 +200,68 @@ def test_graph_replay_equals_the_direct_stage_bitwise(precision):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("recon", [1, 0])
+def test_fp32_copies_give_bitwise_the_same_mixed_stage(recon):
+    """The mixed stage from caller-given FP32 copies of W, B and the metric (gr_cast_f32 of the FP64
+    inputs) equals the stage that converts them itself, bitwise, on uneven blocks; the FP32 copies of
+    its outputs it is asked to write are gr_cast_f32 of the FP64 outputs wherever those are written, and
+    untouched elsewhere."""
+    import torch
+    blocks = [I.random_block(n=n, g=3, seed=90 + k, metric_amp=0.02) for k, n in
+              enumerate([(8, 8, 8), (16, 8, 12), (12, 12, 12)])]
+    P = GH.mixed_params(O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-14, tol=1e-12))
+    pools = GH.Pools(blocks)
+    U = pools.cells([H.cons_from_prims(b, P) for b in blocks], 5)
+    W, B, M = pools.cells([b.W for b in blocks], 5), pools.faces([b.B for b in blocks]), pools.verts(
+        [b.metric for b in blocks])
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    gp = GH.gr_params_from(P, G.GR_PREC_MIXED, G.GR_GUESS_FP32)
+    s = torch.cuda.current_stream()
+
+    def f32(x):
+        y = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+        G.gr_cast_f32(x.contiguous(), y, s)
+        return y
+
+    W32, B32, M32 = f32(W), [f32(b) for b in B], f32(M)
+    outs = []
+    try:
+        for copies in (False, True):
+            Uo, Wo, Bo = U.clone(), W.clone(), [b.clone() for b in B]
+            st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+            state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+            metric = G.metric_struct(M, metric32=M32 if copies else None)
+            sentinel = -7.0
+            Wo32 = torch.full(W.shape, sentinel, dtype=torch.float32, device="cuda")
+            Bo32 = [torch.full(b.shape, sentinel, dtype=torch.float32, device="cuda") for b in B]
+            if copies:
+                G.set_fp32_copies(state, W32=W32, B32=B32, Wo32=Wo32, Bo32=Bo32)
+            G.gr_stage(mesh, metric, state, 0.01, gp, s)
+            torch.cuda.synchronize()
+            outs.append([Uo.cpu(), Wo.cpu(), st.cpu()] + [b.cpu() for b in Bo])
+    finally:
+        G.gr_mesh_destroy(mesh)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    # the written FP32 copies: the conversion of the outputs on interior cells / faces of interior cells
+    inter = torch.zeros(pools.L.ncell, dtype=torch.bool)
+    for b_, bi in enumerate(blocks):
+        g, n = bi.ng, bi.n
+        m = torch.zeros((n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g), dtype=torch.bool)
+        m[g:g + n[2], g:g + n[1], g:g + n[0]] = True
+        inter[int(pools.L.cell_off[b_]):int(pools.L.cell_off[b_]) + m.numel()] = m.view(-1)
+    Wo64 = outs[1][1].cuda()
+    ref32 = f32(Wo64).cpu()
+    got32 = Wo32.cpu()
+    assert torch.equal(got32[:, inter], ref32[:, inter])
+    assert torch.all(got32[:, ~inter] == sentinel)
+    for d in range(3):
+        written = Bo32[d].cpu() != sentinel
+        assert torch.equal(Bo32[d].cpu()[written], f32(outs[1][3 + d].cuda()).cpu()[written])
+        assert int(written.sum()) == sum((b.n[0] + (d == 0)) * (b.n[1] + (d == 1)) * (b.n[2] + (d == 2))
+                                         for b in blocks)
+
+
 @pytest.mark.parametrize("precision,nbatch,rk", [(G.GR_PREC_FP64, 1, False), (G.GR_PREC_MIXED, 3, False),
                                                   (G.GR_PREC_MIXED, 2, True)])
 def test_host_stage_equals_the_device_stage_bitwise(precision, nbatch, rk):
