@@ -758,6 +758,34 @@ def main():
     ms_head = results[head]["ms"]
     value = job_value(cells, world, ms_head)
 
+    # ---- the mixed stage through each path: separate kernels and the fused sweep ------------------
+    paths = None
+    if "mixed" in results:
+        chosen = G.gr_mesh_get_fused(mesh)
+        pm = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
+                                 atm_band=G.GR_MIXED_ATM_BAND)
+        paths = {"autotuner_chose": "fused sweep" if chosen == 1 else "separate kernels"}
+        try:
+            for name_, f in (("separate_kernels", False), ("fused_sweep", True)):
+                G.gr_mesh_set_fused(mesh, f)
+                for _ in range(a.warmup):
+                    G.gr_stage(mesh, metric32, state32, dt, pm, stream)
+                G.gr_profile_begin(mesh, a.steps)
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(a.steps):
+                    G.gr_stage(mesh, metric32, state32, dt, pm, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                kms_, nst_ = G.gr_profile_end(mesh)
+                paths[name_] = {"ms_per_step": e0.elapsed_time(e1) / a.steps,
+                                "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst_) for k in kms_]))}
+        except G.GrstageError as ex:
+            paths["fused_sweep"] = {"unavailable": str(ex)}
+        G.gr_mesh_set_fused(mesh, chosen == 1)
+
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None
     if not a.no_e2e:
@@ -1080,7 +1108,7 @@ def main():
            "stage_hbm": stage_hbm(head), "kernel_rooflines": kernel_rooflines(head, peaks), "e2e": e2e, "gpu_launches": launches,
            "cpu_baseline": cpu, "kernel_ms": dict(zip(G.KERNEL_NAMES, results[head]["kernel_ms"])),
            "fp64": fp64, "mixed_error_vs_fp64": err,
-           "mixed_error_vs_oracle": mixed_vs_oracle, "configs": configs_out, "status_counts": results[head].get("status"),
+           "mixed_error_vs_oracle": mixed_vs_oracle, "configs": configs_out, "stage_paths": paths, "status_counts": results[head].get("status"),
            "graph_ms_per_step": graph_ms, "rk3_driver": rk, "adm_sources": adm, "con2prim_guess": c2p, "con2prim_table": c2p_table,
            "launch_shapes": {k: v.get("shapes") for k, v in results.items()},
            "ratio_mixed_over_fp64": (results["fp64"]["ms"] / results["mixed"]["ms"]) if fp64 else None,

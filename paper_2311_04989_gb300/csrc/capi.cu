@@ -125,6 +125,10 @@ struct gr_mesh {
   int tn[kNumTiles][2][R_NREGION] = {};
   // launch shape of each stage kernel per (precision, EOS), set by gr_autotune or gr_mesh_set_shapes
   gr_shape shapes[2][2][SK_N];
+  // fused sweep of the mixed path (ideal gas, order-2 metric): every block qualifies (fused_ok), and the
+  // path is in use (fused: set by gr_autotune where it is faster, or by gr_mesh_set_fused)
+  bool fused_ok = false;
+  int fused = 0;
   int nint = 0;   // interior cells of all blocks
   Workspace ws{};
   Shadow sh{};
@@ -424,6 +428,8 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   for (const DBlock& d : m->h_blocks) nint += (long long)d.n[0] * d.n[1] * d.n[2];
   if (nint > (1LL << 31) - 1024) e = cudaErrorInvalidValue;
   m->nint = (int)nint;
+  m->fused_ok = nblocks > 0;
+  for (const DBlock& d : m->h_blocks) m->fused_ok = m->fused_ok && fused_block_ok(d);
   if (e == cudaSuccess) e = dalloc(sizeof(int2) * std::max<long long>(1, nint), (void**)&m->ws.jobs);
   if (e == cudaSuccess) e = dalloc(sizeof(int) * 4, (void**)&m->ws.njobs);
   if (e != cudaSuccess) {
@@ -517,6 +523,14 @@ struct gr_graph {
 
 static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                       const gr_params* params, void* stream, bool allow_profile);
+
+// blocks of the fused sweep for a call (0: the separate kernels): the mesh qualifies, the mixed path with
+// the ideal gas and the order-2 metric, no level-boundary corrections, and `want` (the mesh's choice)
+static int fused_blocks(const gr_mesh* mesh, const gr_params* p, const MetricView& mv, int want) {
+  const bool ok = want && mesh->fused_ok && p->precision == GR_PREC_MIXED && p->eos == GR_EOS_IDEAL &&
+                  mv.order == 2 && mesh->ws.nlvl == 0 && mesh->ws.nsweep > 0;
+  return ok ? mesh->nblocks : 0;
+}
 static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                          const gr_params* params, MetricView& mv, StateView& s);
 
@@ -823,6 +837,7 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
     }
     sd.status = h->status + c0;
     std::memcpy(sm->shapes, mesh->shapes, sizeof(mesh->shapes));
+    sm->fused = mesh->fused;
     if ((r = stage_impl(sm, &md, &sd, dt, params, h->st[1], false))) return r;
     e = cudaEventRecord(h->ev_out[k], h->st[1]);
     // its outputs, the elements the stage writes: interior cells of U', W', status, faces of interior
@@ -940,10 +955,21 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
   if (allow_profile && mesh->prof_used < mesh->prof_capacity)
     ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
   cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh,
-                               kparams(params, dt), (cudaStream_t)stream, ev);
+                               kparams(params, dt), (cudaStream_t)stream, ev, true,
+                               fused_blocks(mesh, params, mv, mesh->fused));
   if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
   return GR_OK;
 }
+
+int gr_mesh_set_fused(gr_mesh* mesh, int32_t enable) {
+  if (!mesh || (enable != 0 && enable != 1)) return fail(GR_EINVAL, "gr_mesh_set_fused: bad argument");
+  if (enable && !mesh->fused_ok)
+    return fail(GR_EUNSUPPORTED, "gr_mesh_set_fused: a block is wider than 16 cells in x or y or has ghosts != 3");
+  mesh->fused = enable;
+  return GR_OK;
+}
+
+int gr_mesh_get_fused(const gr_mesh* mesh) { return mesh ? mesh->fused : -1; }
 
 int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]) {
   if (!mesh || !out || (precision != GR_PREC_FP64 && precision != GR_PREC_MIXED) ||
@@ -1017,6 +1043,30 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
     }
     best[k] = cand[bi];
     if (best_ms) best_ms[k] = ms[bi][k];
+  }
+  // where the fused sweep applies: the whole stage through it against the separate kernels in their
+  // chosen shapes; the faster is kept for later stages on this mesh
+  if (fused_blocks(mesh, params, mv, 1)) {
+    KLaunch kl[SK_N];
+    stage_launches(mesh, best, kl);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    float tm[2] = {0.f, 0.f};
+    for (int path = 0; path < 2 && e == cudaSuccess; ++path) {
+      const int nf = path ? mesh->nblocks : 0;
+      e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st, nullptr, true, nf);
+      if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+      for (int rp = 0; rp < reps && e == cudaSuccess; ++rp)
+        e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st, nullptr, true, nf);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&tm[path], t0, t1);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_autotune (fused sweep)");
+    mesh->fused = tm[1] < tm[0] ? 1 : 0;
   }
   return GR_OK;
 }
@@ -1506,7 +1556,8 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
     KParams kp = kparams(&ps, 0.0);
     kp.dt_dev = d->d_dt;
     // the stages of a step share the metric: its FP32 shadow (mixed path) is made by the first one
-    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr, s == 0);
+    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr, s == 0,
+                                 fused_blocks(m, &ps, mv, m->fused));
     if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step stage");
     if (!last) {
       for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];

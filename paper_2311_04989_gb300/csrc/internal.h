@@ -160,13 +160,21 @@ cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<fl
 cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<double>& in, const Workspace& ws,
                          const KParams& kp, cudaStream_t st);
 
+// Fused sweep of the mixed path (fused.cu): faces, corner EMFs, CT and the update of every block in one
+// launch (one CTA per block); the blocks must satisfy fused_block_ok (ghost width 3, at most 16 x 16 cells
+// in x-y), the EOS be the ideal gas and the metric of order 2.
+cudaError_t launch_fused(const DBlock* blocks, int nblocks, const InView<float>& in, const StateView& s,
+                         const Workspace& ws, const KParams& kp, cudaStream_t st);
+bool fused_block_ok(const DBlock& b);
+
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after
 // the cast and each kernel.  cast_metric = false reuses the FP32 metric shadow of the previous mixed
 // stage on this mesh (the RK driver, whose stages share one metric).
+// nfused > 0: the mixed path through the fused sweep over nfused blocks (the caller checked that it applies).
 cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
                          const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
-                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric = true);
+                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric = true, int nfused = 0);
 cudaError_t launch_prim2con(const DBlock* blocks, const Work* work, int nwork, const MetricView& m,
                             const double* const W[7], const double* const B[3], double* const U[6],
                             const KParams& kp, cudaStream_t st);

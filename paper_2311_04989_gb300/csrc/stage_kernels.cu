@@ -28,6 +28,7 @@
 #include "internal.h"
 #include "physics.cuh"
 #include "stage_common.cuh"
+#include "update_common.cuh"
 
 namespace grs {
 
@@ -333,16 +334,6 @@ __global__ void __launch_bounds__(kMaxTile) k_ct(const DBlock* __restrict__ bloc
 // ------------------------------------------------------------------------------------------------
 // k_update<R>: U' (sources in R, FP64 accumulation) and FP64 con2prim on interior cells
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cell_field(const DBlock& b, const double* const* B, int i, int j, int k,
-                                           double Bd[3]) {
-  const long long f0 = b.face[0] + fix(b, 0, i, j, k);
-  const long long f1 = b.face[1] + fix(b, 1, i, j, k);
-  const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-  Bd[0] = 0.5 * (B[0][f0] + B[0][f0 + 1]);
-  Bd[1] = 0.5 * (B[1][f1] + B[1][f1 + b.N[0]]);
-  Bd[2] = 0.5 * (B[2][f2] + B[2][f2 + (long long)b.N[0] * b.N[1]]);
-}
-
 // FP64 gamma_ij at a cell centre (con2prim's metric)
 __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<double>& m, int i, int j, int k,
                                              C2PMet& M) {
@@ -351,24 +342,8 @@ __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<doubl
   c2pmet_from(val + 4, M);
 }
 
-template <int EOS>
-__device__ __forceinline__ void write_cell(const StateView& s, long long c, const double q[6], const double w[7],
-                                           int st) {
-  constexpr int NQ = EOS ? 6 : 5, NW = EOS ? 7 : 5, N32 = EOS ? 6 : 5;
-#pragma unroll
-  for (int v = 0; v < NQ; ++v) s.Uo[v][c] = q[v];
-#pragma unroll
-  for (int v = 0; v < NW; ++v) s.Wo[v][c] = w[v];
-  if (s.Wo32[0]) {   // FP32 copies of the new primitives (the next stage's reconstruction input)
-#pragma unroll
-    for (int v = 0; v < N32; ++v) s.Wo32[v][c] = d2f_rn(w[v]);
-  }
-  if (s.status) s.status[c] = (uint8_t)st;   // optional for gr_con2prim
-}
-
-// Conserved variable v of interior cell (i, j, k) after the stage: g1 U + g0 U0 + beta dt (src - div F),
-// the face fluxes widened exactly and the sum accumulated in FP64.  Flux component of v: D, S_j, tau at
-// 0..4; D Y_e at 7 (5, 6 are the induction fluxes).
+// Conserved variable v of interior cell (i, j, k) after the stage from the workspace's face fluxes
+// (component of v: D, S_j, tau at 0..4; D Y_e at 7 -- 5, 6 are the induction fluxes)
 template <class R>
 __device__ __forceinline__ double accumulate_cell(const DBlock& b, const StateView& s, const Workspace& ws,
                                                   const KParams& kp, int i, int j, int k, long long c, int v,
@@ -378,42 +353,17 @@ __device__ __forceinline__ double accumulate_cell(const DBlock& b, const StateVi
   const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
   const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
   const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
-  const double bdt = stage_bdt(kp);
-  const double U = s.U[v][c];
-  double u = fma(bdt, to64(src), (kp.rk_form & RK_G1) ? kp.rk_g1 * U : U);
-  u -= (bdt * b.idx[0]) * (to64(a0[1]) - to64(a0[0]));
-  u -= (bdt * b.idx[1]) * (to64(a1[oy]) - to64(a1[0]));
-  u -= (bdt * b.idx[2]) * (to64(a2[oz]) - to64(a2[0]));
-  if (kp.rk_form & RK_G0) u += kp.rk_g0 * s.U0[v][c];
-  return u;
+  return accumulate_vals<R>(b, s, kp, c, v, src, a0[0], a0[1], a1[0], a1[oy], a2[0], a2[oz]);
 }
 
-// U' of every conserved variable of interior cell (i, j, k): the stage-input metric (values and first
-// derivatives), primitives and mean densitised field of the input faces give the geometric sources
-// (Eq. hydsrc_def; none for D and D Y_e) in R, then accumulate_cell.  M: the cell metric, for the caller.
+// U' of every conserved variable of interior cell (i, j, k): the geometric sources (cell_sources_at), then
+// accumulate_cell.  M: the cell metric, for the caller.
 template <class R, int EOS>
 __device__ __forceinline__ void update_all(const DBlock& b, const InView<R>& in, const StateView& s,
                                            const Workspace& ws, const KParams& kp, int i, int j, int k,
                                            long long c, double q[6], CellMet<R>& M) {
-  const bool kzero = in.k_zero != 0;
-  R val[16], dm[3][10];
-  cell_metric<R>(b, in, in.order, i, j, k, 0, 10, val, dm);
-  if (!kzero) cell_metric<R>(b, in, in.order, i, j, k, 10, 16, val, nullptr);
-  cellmet_from<R>(val, kzero, M);
-  R wv[6], Bd[3];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) wv[v] = in.W[v][c];
-  wv[5] = EOS ? in.W[5][c] : R(0);
-  const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
-  const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-  Bd[0] = R(0.5) * (in.B[0][f0] + in.B[0][f0 + 1]);
-  Bd[1] = R(0.5) * (in.B[1][f1] + in.B[1][f1 + b.N[0]]);
-  Bd[2] = R(0.5) * (in.B[2][f2] + in.B[2][f2 + (long long)b.N[0] * b.N[1]]);
-  CellFluid<R> fl;
-  cell_fluid<R, EOS>(M, kp, wv, Bd, fl);
   R src[6];
-  cell_sources<R>(M, fl, dm, kzero, src);
-  src[5] = R(0);   // D Y_e has no source (Sec. 2.2.1)
+  cell_sources_at<R, EOS>(b, in, kp, i, j, k, c, src, M);
   constexpr int NQ = EOS ? 6 : 5;
 #pragma unroll
   for (int v = 0; v < NQ; ++v) q[v] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, v, src[v]);
@@ -456,29 +406,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
       const R t = a0[1] - a0[0] + a1[b.N[0]] - a1[0] + a2[(long long)b.N[0] * b.N[1]] - a2[0];
       finite = finite && isfinite(t) && isfinite(s.U[v][c]);
     }
-    // the cell field of the updated faces in FP32 (the reset needs only calB^2 in FP32)
-    R Bf[3], Bl[3];
-    {
-      const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
-      const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-      Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
-      Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + b.N[0]])));
-      Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + (long long)b.N[0] * b.N[1]])));
-    }
-    lower3(gam, Bf, Bl);
-    const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
-    q[0] = sg32 * kp.rho_atm;
-    q[1] = q[2] = q[3] = 0.0;
-    q[4] = sg32 * kp.eint_atm + to64(R(0.5) * rdiv(BBd, sg));
-    wn[0] = kp.rho_atm;
-    wn[1] = wn[2] = wn[3] = 0.0;
-    wn[4] = kp.p_atm;
-    if constexpr (EOS == GR_EOS_TABLE) {
-      q[5] = q[0] * kp.Ye_atm;
-      wn[5] = kp.Ye_atm;
-      wn[6] = kp.T_atm;
-    }
-    write_cell<EOS>(s, c, q, wn, finite ? GR_ST_ATM_THRESHOLD : GR_ST_FAILED);
+    mixed_atm_reset<R, EOS>(b, s, kp, i, j, k, c, gam, sg, finite);
     return false;
   } else {
     CellMet<R> M;
@@ -794,6 +722,32 @@ cudaError_t launch_cast_pool(const double* src, float* dst, long long n, cudaStr
   return cudaGetLastError();
 }
 
+// The mixed stage through the fused sweep: cell prep, k_fused (faces, EMFs, CT, update), con2prim of the
+// queued cells from their U' in Uo
+static cudaError_t stage_fused(const DBlock* blocks, int nblocks, const KLaunch kl[SK_N], const InView<float>& in,
+                               const InView<double>& in64, const StateView& s, const Workspace& ws, const KParams& kp,
+                               cudaStream_t st, cudaEvent_t* ev) {
+  cudaError_t e = launch_cellprep_sweep<float>(blocks, in, ws, st);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[2], st);
+  e = cudaMemsetAsync(ws.njobs, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = launch_fused(blocks, nblocks, in, s, ws, kp, st);
+  if (e != cudaSuccess) return e;
+  if (ev) {
+    for (int k = 3; k <= 6; ++k) cudaEventRecord(ev[k], st);
+  }
+  const KLaunch& q = kl[SK_C2P];
+  if (q.nwork) {
+    KLaunch qq = q;
+    qq.nwork = (q.nwork + q.threads - 1) / q.threads;
+    k_c2p<GR_EOS_IDEAL, double><<<stage_grid(k_c2p<GR_EOS_IDEAL, double>, qq, 0), q.threads, 0, st>>>(blocks, in64, in64,
+                                                                                                    s, ws, kp);
+  }
+  if (ev) cudaEventRecord(ev[7], st);
+  return cudaGetLastError();
+}
+
 template <class R, int EOS>
 static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], const InView<R>& in,
                               const InView<double>& in64, const StateView& s, const Workspace& ws, const KParams& kp,
@@ -843,7 +797,7 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
 
 cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[SK_N], const MetricView& m,
                          const StateView& s, const Workspace& ws, const Shadow& sh, const KParams& kp,
-                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric) {
+                         cudaStream_t st, cudaEvent_t* ev, bool cast_metric, int nfused) {
   if (ev) cudaEventRecord(ev[0], st);
   const InView<double> in64 = view64(m, &s);
   const bool tab = kp.eos == GR_EOS_TABLE;
@@ -852,6 +806,7 @@ cudaError_t launch_stage(int precision, const DBlock* blocks, const KLaunch kl[S
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     const InView<float> in32 = view32(m, s, sh);
+    if (nfused > 0 && !tab) return stage_fused(blocks, nfused, kl, in32, in64, s, ws, kp, st, ev);
     return tab ? stage_impl<float, GR_EOS_TABLE>(blocks, kl, in32, in64, s, ws, kp, st, ev)
                : stage_impl<float, GR_EOS_IDEAL>(blocks, kl, in32, in64, s, ws, kp, st, ev);
   }
