@@ -761,14 +761,15 @@ def main():
     # ---- the mixed stage through each path: separate kernels and the fused sweep ------------------
     paths = None
     if "mixed" in results:
-        chosen = G.gr_mesh_get_fused(mesh)
+        chosen = G.gr_mesh_get_path(mesh)
         pm = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
                                  gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                  atm_band=G.GR_MIXED_ATM_BAND)
-        paths = {"autotuner_chose": "fused sweep" if chosen == 1 else "separate kernels"}
-        try:
-            for name_, f in (("separate_kernels", False), ("fused_sweep", True)):
-                G.gr_mesh_set_fused(mesh, f)
+        paths = {"autotuner_chose": G.PATH_NAMES[chosen]}
+        for name_, f in (("separate_kernels", G.GR_PATH_SEPARATE), ("fused_sweep", G.GR_PATH_FUSED),
+                         ("tiled_face_sweep", G.GR_PATH_TILED_FACES)):
+            try:
+                G.gr_mesh_set_path(mesh, f)
                 for _ in range(a.warmup):
                     G.gr_stage(mesh, metric32, state32, dt, pm, stream)
                 G.gr_profile_begin(mesh, a.steps)
@@ -782,9 +783,9 @@ def main():
                 kms_, nst_ = G.gr_profile_end(mesh)
                 paths[name_] = {"ms_per_step": e0.elapsed_time(e1) / a.steps,
                                 "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst_) for k in kms_]))}
-        except G.GrstageError as ex:
-            paths["fused_sweep"] = {"unavailable": str(ex)}
-        G.gr_mesh_set_fused(mesh, chosen == 1)
+            except G.GrstageError as ex:
+                paths[name_] = {"unavailable": str(ex)}
+        G.gr_mesh_set_path(mesh, chosen)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None

@@ -235,16 +235,22 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
 int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]);
 int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_shape in[GR_NSTAGE_KERNELS]);
 
-/* Fused sweep of the mixed path (the reconstruction, HLLE fluxes, corner EMFs, CT update and flux divergence
- * of Sec. 3.3-3.4 and Eq. claw in one pass per block, fluxes and EMFs kept in shared memory; con2prim then
- * runs on the queued cells as before): one CTA per block walks it along z with rings of planes in shared
- * memory.  It applies to meshes whose blocks all have 3 ghosts and at most 16 x 16 cells in x and y, with
- * the ideal gas, the order-2 metric and no level faces; elsewhere the separate kernels run.  Results are
- * those of the separate kernels, bitwise.  gr_autotune enables it where it measures faster;
- * gr_mesh_set_fused(mesh, 1 / 0) forces it on / off (GR_EUNSUPPORTED if a block does not qualify);
- * gr_mesh_get_fused returns the setting (-1 for a NULL mesh). */
-int gr_mesh_set_fused(gr_mesh* mesh, int32_t enable);
-int gr_mesh_get_fused(const gr_mesh* mesh);
+/* Path of the mixed stage with the ideal gas, the order-2 metric and no level faces (elsewhere the separate
+ * kernels run).  All paths give bitwise the same results.
+ *   GR_PATH_SEPARATE     the stage kernels one after another, fluxes and EMFs through the mesh's workspace
+ *   GR_PATH_FUSED        the fused sweep: the reconstruction, HLLE fluxes, corner EMFs, CT update and flux
+ *                        divergence of Sec. 3.3-3.4 and Eq. claw in one pass per block, one CTA per block
+ *                        walking it along z with rings of planes in shared memory (fluxes and EMFs never leave
+ *                        it); con2prim then runs on the queued cells; blocks with 3 ghosts and at most 16 x 16
+ *                        cells in x and y
+ *   GR_PATH_TILED_FACES  the separate kernels with the face fluxes from tiles of at most 8 rows of a block
+ *                        walked along z, their stencils and face metric staged in shared memory; blocks with
+ *                        3 ghosts and at most 16 cells along x
+ * gr_autotune times every path that applies and keeps the fastest; gr_mesh_set_path forces one
+ * (GR_EUNSUPPORTED if a block does not qualify); gr_mesh_get_path returns it (-1 for a NULL mesh). */
+enum { GR_PATH_SEPARATE = 0, GR_PATH_FUSED = 1, GR_PATH_TILED_FACES = 2 };
+int gr_mesh_set_path(gr_mesh* mesh, int32_t path);
+int gr_mesh_get_path(const gr_mesh* mesh);
 
 /* ---- one stage on host-resident pools ----------------------------------------------------------------
  * gr_host_stage: the stage of gr_stage on a mesh whose pools live in host memory.  metric and state hold

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgrstage.so")
 SOURCES = ["capi.cu", "stage_kernels.cu", "faces_f32.cu", "faces_f64.cu", "driver.cu", "adm.cu", "amr.cu",
-           "hostio.cu", "noalloc.cu", "mlp.cu", "peaks.cu", "fused.cu"]
+           "hostio.cu", "noalloc.cu", "mlp.cu", "peaks.cu", "fused.cu", "faces_tile.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

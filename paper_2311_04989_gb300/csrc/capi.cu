@@ -125,10 +125,14 @@ struct gr_mesh {
   int tn[kNumTiles][2][R_NREGION] = {};
   // launch shape of each stage kernel per (precision, EOS), set by gr_autotune or gr_mesh_set_shapes
   gr_shape shapes[2][2][SK_N];
-  // fused sweep of the mixed path (ideal gas, order-2 metric): every block qualifies (fused_ok), and the
-  // path is in use (fused: set by gr_autotune where it is faster, or by gr_mesh_set_fused)
+  // path of the mixed stage with the ideal gas and the order-2 metric (GR_PATH_*: set by gr_autotune where
+  // faster, or by gr_mesh_set_path): the fused sweep where every block qualifies (fused_ok), the tiled face
+  // sweep where every block qualifies (tiles_ok; its tile list d_ftiles)
   bool fused_ok = false;
-  int fused = 0;
+  bool tiles_ok = false;
+  int path = GR_PATH_SEPARATE;
+  FaceTile* d_ftiles = nullptr;
+  int nftiles = 0;
   int nint = 0;   // interior cells of all blocks
   Workspace ws{};
   Shadow sh{};
@@ -430,6 +434,20 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   m->nint = (int)nint;
   m->fused_ok = nblocks > 0;
   for (const DBlock& d : m->h_blocks) m->fused_ok = m->fused_ok && fused_block_ok(d);
+  // tiles of the face sweep: rows of each block in equal tiles of at most kTY (3 ghosts, <= 16 cells along x)
+  m->tiles_ok = nblocks > 0;
+  for (const DBlock& d : m->h_blocks) m->tiles_ok = m->tiles_ok && d.g == 3 && d.n[0] <= 16;
+  if (m->tiles_ok && e == cudaSuccess) {
+    std::vector<FaceTile> ft;
+    for (int b = 0; b < nblocks; ++b) {
+      const int n1 = m->h_blocks[b].n[1];
+      const int nt = (n1 + kTY - 1) / kTY;
+      for (int t = 0; t < nt; ++t) ft.push_back(FaceTile{b, (int)((long long)n1 * t / nt), (int)((long long)n1 * (t + 1) / nt), 0});
+    }
+    e = dalloc(sizeof(FaceTile) * ft.size(), (void**)&m->d_ftiles);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_ftiles, ft.data(), sizeof(FaceTile) * ft.size(), cudaMemcpyHostToDevice);
+    m->nftiles = (int)ft.size();
+  }
   if (e == cudaSuccess) e = dalloc(sizeof(int2) * std::max<long long>(1, nint), (void**)&m->ws.jobs);
   if (e == cudaSuccess) e = dalloc(sizeof(int) * 4, (void**)&m->ws.njobs);
   if (e != cudaSuccess) {
@@ -524,12 +542,28 @@ struct gr_graph {
 static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                       const gr_params* params, void* stream, bool allow_profile);
 
-// blocks of the fused sweep for a call (0: the separate kernels): the mesh qualifies, the mixed path with
-// the ideal gas and the order-2 metric, no level-boundary corrections, and `want` (the mesh's choice)
-static int fused_blocks(const gr_mesh* mesh, const gr_params* p, const MetricView& mv, int want) {
-  const bool ok = want && mesh->fused_ok && p->precision == GR_PREC_MIXED && p->eos == GR_EOS_IDEAL &&
-                  mv.order == 2 && mesh->ws.nlvl == 0 && mesh->ws.nsweep > 0;
-  return ok ? mesh->nblocks : 0;
+// The stage variant of a call for path `path` (GR_PATH_*): where the call is the mixed path with the ideal
+// gas, the order-2 metric and no level-boundary corrections, the fused sweep (*nfused = blocks) or the
+// tiled face sweep (ws->nftiles) if the mesh qualifies; otherwise (and for GR_PATH_SEPARATE) the separate
+// kernels.  Returns whether the requested variant applies.
+static bool stage_variant(const gr_mesh* mesh, const gr_params* p, const MetricView& mv, int path, int* nfused,
+                          Workspace* ws) {
+  *ws = mesh->ws;
+  ws->ftiles = nullptr;
+  ws->nftiles = 0;
+  *nfused = 0;
+  const bool mixed_ideal = p->precision == GR_PREC_MIXED && p->eos == GR_EOS_IDEAL && mv.order == 2 &&
+                           mesh->ws.nlvl == 0;
+  if (path == GR_PATH_FUSED && mixed_ideal && mesh->fused_ok && mesh->ws.nsweep > 0) {
+    *nfused = mesh->nblocks;
+    return true;
+  }
+  if (path == GR_PATH_TILED_FACES && mixed_ideal && mesh->tiles_ok) {
+    ws->ftiles = mesh->d_ftiles;
+    ws->nftiles = mesh->nftiles;
+    return true;
+  }
+  return path == GR_PATH_SEPARATE;
 }
 static int stage_prepare(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt,
                          const gr_params* params, MetricView& mv, StateView& s);
@@ -837,7 +871,7 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
     }
     sd.status = h->status + c0;
     std::memcpy(sm->shapes, mesh->shapes, sizeof(mesh->shapes));
-    sm->fused = mesh->fused;
+    sm->path = mesh->path;
     if ((r = stage_impl(sm, &md, &sd, dt, params, h->st[1], false))) return r;
     e = cudaEventRecord(h->ev_out[k], h->st[1]);
     // its outputs, the elements the stage writes: interior cells of U', W', status, faces of interior
@@ -954,22 +988,26 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
   cudaEvent_t* ev = nullptr;
   if (allow_profile && mesh->prof_used < mesh->prof_capacity)
     ev = &mesh->prof_events[(GR_NKERNELS + 1) * mesh->prof_used++];
-  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh,
-                               kparams(params, dt), (cudaStream_t)stream, ev, true,
-                               fused_blocks(mesh, params, mv, mesh->fused));
+  int nf = 0;
+  Workspace ws;
+  stage_variant(mesh, params, mv, mesh->path, &nf, &ws);
+  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kparams(params, dt),
+                               (cudaStream_t)stream, ev, true, nf);
   if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
   return GR_OK;
 }
 
-int gr_mesh_set_fused(gr_mesh* mesh, int32_t enable) {
-  if (!mesh || (enable != 0 && enable != 1)) return fail(GR_EINVAL, "gr_mesh_set_fused: bad argument");
-  if (enable && !mesh->fused_ok)
-    return fail(GR_EUNSUPPORTED, "gr_mesh_set_fused: a block is wider than 16 cells in x or y or has ghosts != 3");
-  mesh->fused = enable;
+int gr_mesh_set_path(gr_mesh* mesh, int32_t path) {
+  if (!mesh || path < GR_PATH_SEPARATE || path > GR_PATH_TILED_FACES) return fail(GR_EINVAL, "gr_mesh_set_path: bad argument");
+  if (path == GR_PATH_FUSED && !mesh->fused_ok)
+    return fail(GR_EUNSUPPORTED, "gr_mesh_set_path: a block is wider than 16 cells in x or y or has ghosts != 3");
+  if (path == GR_PATH_TILED_FACES && !mesh->tiles_ok)
+    return fail(GR_EUNSUPPORTED, "gr_mesh_set_path: a block is wider than 16 cells in x or has ghosts != 3");
+  mesh->path = path;
   return GR_OK;
 }
 
-int gr_mesh_get_fused(const gr_mesh* mesh) { return mesh ? mesh->fused : -1; }
+int gr_mesh_get_path(const gr_mesh* mesh) { return mesh ? mesh->path : -1; }
 
 int gr_mesh_get_shapes(const gr_mesh* mesh, int32_t precision, int32_t eos, gr_shape out[GR_NSTAGE_KERNELS]) {
   if (!mesh || !out || (precision != GR_PREC_FP64 && precision != GR_PREC_MIXED) ||
@@ -1044,29 +1082,34 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
     best[k] = cand[bi];
     if (best_ms) best_ms[k] = ms[bi][k];
   }
-  // where the fused sweep applies: the whole stage through it against the separate kernels in their
-  // chosen shapes; the faster is kept for later stages on this mesh
-  if (fused_blocks(mesh, params, mv, 1)) {
+  // the whole stage through every path that applies (separate kernels in their chosen shapes, the fused
+  // sweep, the tiled face sweep); the fastest is kept for later stages on this mesh
+  {
     KLaunch kl[SK_N];
     stage_launches(mesh, best, kl);
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    float tm[2] = {0.f, 0.f};
-    for (int path = 0; path < 2 && e == cudaSuccess; ++path) {
-      const int nf = path ? mesh->nblocks : 0;
-      e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st, nullptr, true, nf);
+    float best_t = -1.f;
+    int best_path = GR_PATH_SEPARATE;
+    for (int path = GR_PATH_SEPARATE; path <= GR_PATH_TILED_FACES && e == cudaSuccess; ++path) {
+      int nf = 0;
+      Workspace ws;
+      if (!stage_variant(mesh, params, mv, path, &nf, &ws)) continue;
+      e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kp, st, nullptr, true, nf);
       if (e == cudaSuccess) e = cudaEventRecord(t0, st);
       for (int rp = 0; rp < reps && e == cudaSuccess; ++rp)
-        e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, mesh->ws, mesh->sh, kp, st, nullptr, true, nf);
+        e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kp, st, nullptr, true, nf);
       if (e == cudaSuccess) e = cudaEventRecord(t1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&tm[path], t0, t1);
+      float tm = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&tm, t0, t1);
+      if (e == cudaSuccess && (best_t < 0.f || tm < best_t)) { best_t = tm; best_path = path; }
     }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
-    if (e != cudaSuccess) return cuda_fail(e, "gr_autotune (fused sweep)");
-    mesh->fused = tm[1] < tm[0] ? 1 : 0;
+    if (e != cudaSuccess) return cuda_fail(e, "gr_autotune (stage paths)");
+    mesh->path = best_path;
   }
   return GR_OK;
 }
@@ -1556,8 +1599,10 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
     KParams kp = kparams(&ps, 0.0);
     kp.dt_dev = d->d_dt;
     // the stages of a step share the metric: its FP32 shadow (mixed path) is made by the first one
-    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, m->ws, m->sh, kp, st, nullptr, s == 0,
-                                 fused_blocks(m, &ps, mv, m->fused));
+    int nf = 0;
+    Workspace wsv;
+    stage_variant(m, &ps, mv, m->path, &nf, &wsv);
+    cudaError_t e = launch_stage(params->precision, m->d_blocks, kl, mv, sv, wsv, m->sh, kp, st, nullptr, s == 0, nf);
     if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step stage");
     if (!last) {
       for (int v = 0; v < nq; ++v) inU[v] = d->U[s % 2][v];

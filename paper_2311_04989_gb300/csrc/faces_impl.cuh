@@ -5,6 +5,7 @@
 // carries the code of one method only.
 #pragma once
 
+#include "faces_core.cuh"
 #include "internal.h"
 #include "physics.cuh"
 #include "stage_common.cuh"
@@ -47,48 +48,20 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
     st[6][t] = bc2[c];
     if constexpr (EOS == GR_EOS_TABLE) st[7][t] = wp[5][c];
   }
-  const R eps = (sizeof(R) == 4) ? R(1e-30f) : R(kp.weno_eps);
   R L[NV], Rr[NV];
-  // density and pressure with power-of-two scaling in FP32 (they reach the atmosphere values);
-  // velocities, the transverse field and Y_e without
-  recon<R, METHOD, true>(st[0], eps, &L[0], &Rr[0]);
-  recon<R, METHOD, true>(st[4], eps, &L[4], &Rr[4]);
-#pragma unroll
-  for (int v = 1; v < NV; ++v)
-    if (v != 4) recon<R, METHOD, false>(st[v], eps, &L[v], &Rr[v]);
-  // a non-physical reconstructed state (rho <= 0 or p <= 0) drops the face to first order
-  if (!(L[0] > R(0)) || !(Rr[0] > R(0)) || !(L[4] > R(0)) || !(Rr[4] > R(0))) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
-  }
-  // face states (rho, u~^i, p[, Y_e])
-  R wl[6], wr[6];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) { wl[v] = L[v]; wr[v] = Rr[v]; }
-  wl[5] = EOS ? L[NV - 1] : R(0);
-  wr[5] = EOS ? Rr[NV - 1] : R(0);
+  face_recon<R, EOS, METHOD>(st, kp, L, Rr);
   R met[10];
   face_metric<R>(b, in, in.order, D, p, met);
-  const R det = det3(met + 4);
-  const R sg = rsqrt_(det);
-  const R gdd = inv_dd(met + 4, D, det);
   const long long fi = fix(b, D, p[0], p[1], p[2]);
   const R Bn = in.B[D][b.face[D] + fi];
-  R BL[3], BR[3];
-  BL[D] = Bn; BR[D] = Bn;
-  BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
-  BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
-  R UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
-  face_state<R, EOS>(D, met, sg, gdd, kp, wl, BL, UL, FL, &lmL, &lpL);
-  face_state<R, EOS>(D, met, sg, gdd, kp, wr, BR, UR, FR, &lmR, &lpR);
-  R F[7];
-  hlle<R>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
+  R F[7], ye_up;
+  face_flux<R, EOS, D>(L, Rr, met, Bn, kp, F, &ye_up);
   R* out = reinterpret_cast<R*>(ws.flux[D]);
   const long long o = b.wface[D] + fi;
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
   // D Y_e: the D equation times Y_e (Sec. 2.2.1), Y_e taken from the upwind state of the mass flux
-  if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * (F[0] > R(0) ? wl[5] : wr[5]);
+  if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * ye_up;
 }
 
 // FP32: at most 85 registers (three 256-thread CTAs per SM); the packed reconstruction would otherwise

@@ -16,6 +16,7 @@
 // (face_body, edge_body, ct_body, update_cell with k_c2p's U'), so the two paths agree bitwise.  Made for
 // blocks of up to 16 x 16 cells in x-y with 3 ghosts (any length in z), the ideal-gas EOS and the order-2
 // metric; the host uses it only where every block of the mesh qualifies.
+#include "faces_core.cuh"
 #include "internal.h"
 #include "physics.cuh"
 #include "stage_common.cuh"
@@ -118,7 +119,6 @@ __device__ __forceinline__ void load_efield_plane(float* dst, const Workspace& w
 template <int EOS, int METHOD, int D>
 __device__ __forceinline__ void fused_face(const float* sm, const DBlock& b, const InView<float>& in, const KParams& kp,
                                            int i, int j, int p, float* out, int ostride) {
-  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   constexpr int NV = 7;
   float st[NV][6];
 #pragma unroll
@@ -135,22 +135,8 @@ __device__ __forceinline__ void fused_face(const float* sm, const DBlock& b, con
     else if constexpr (D == 1) { st[5][t] = bz[c]; st[6][t] = wp[5 * kFPA + c]; }
     else { st[5][t] = wp[5 * kFPA + c]; st[6][t] = wp[6 * kFPA + c]; }
   }
-  const float eps = 1e-30f;
   float L[NV], Rr[NV];
-  recon<float, METHOD, true>(st[0], eps, &L[0], &Rr[0]);
-  recon<float, METHOD, true>(st[4], eps, &L[4], &Rr[4]);
-#pragma unroll
-  for (int v = 1; v < NV; ++v)
-    if (v != 4) recon<float, METHOD, false>(st[v], eps, &L[v], &Rr[v]);
-  if (!(L[0] > 0.f) || !(Rr[0] > 0.f) || !(L[4] > 0.f) || !(Rr[4] > 0.f)) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { L[v] = st[v][2]; Rr[v] = st[v][3]; }
-  }
-  float wl[6], wr[6];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) { wl[v] = L[v]; wr[v] = Rr[v]; }
-  wl[5] = 0.f;
-  wr[5] = 0.f;
+  face_recon<float, EOS, METHOD>(st, kp, L, Rr);
   // face metric: the mean of the face's four vertices in face_metric's order
   float met[10];
   {
@@ -176,19 +162,9 @@ __device__ __forceinline__ void fused_face(const float* sm, const DBlock& b, con
       met[c] = 0.25f * ((f0 + f1) + (f2 + f3));
     }
   }
-  const float det = det3(met + 4);
-  const float sg = rsqrt_(det);
-  const float gdd = inv_dd(met + 4, D, det);
   const float Bn = in.B[D][b.face[D] + fix(b, D, i, j, p)];
-  float BL[3], BR[3];
-  BL[D] = Bn; BR[D] = Bn;
-  BL[t1] = L[5] * sg; BL[t2] = L[6] * sg;
-  BR[t1] = Rr[5] * sg; BR[t2] = Rr[6] * sg;
-  float UL[7], FL[7], UR[7], FR[7], lmL, lpL, lmR, lpR;
-  face_state<float, EOS>(D, met, sg, gdd, kp, wl, BL, UL, FL, &lmL, &lpL);
-  face_state<float, EOS>(D, met, sg, gdd, kp, wr, BR, UR, FR, &lmR, &lpR);
-  float F[7];
-  hlle<float>(UL, UR, FL, FR, lmL, lpL, lmR, lpR, F);
+  float F[7], ye_up;
+  face_flux<float, EOS, D>(L, Rr, met, Bn, kp, F, &ye_up);
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v * ostride] = F[v];
 }

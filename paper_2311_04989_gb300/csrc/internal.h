@@ -89,6 +89,12 @@ struct SweepWork {
   int block, x0, y0, txy;
 };
 
+// k_faces_tile: a tile of at most kTY interior rows [j0, j1) of one block, walked along z
+constexpr int kTY = 8;
+struct FaceTile {
+  int block, j0, j1, pad;
+};
+
 // Level-boundary records (same layouts as gr_level_face / gr_level_map)
 struct LevelFace {
   int coarse, fine, dir, side, o1, o2;
@@ -112,6 +118,8 @@ struct Workspace {
   int nsweep;
   int* njobs;          // con2prim job list: cells (block, interior index) that need the root find
   int2* jobs;
+  const FaceTile* ftiles;  // tiles of k_faces_tile when the stage computes its fluxes with it, else nftiles 0
+  int nftiles;
 };
 
 // Device view of an EOS table (Sec. 2.2.1) in precision R: node arrays of log p, log e, c_s^2, node
@@ -166,6 +174,10 @@ cudaError_t launch_faces(const KLaunch& f, const DBlock* blocks, const InView<do
 cudaError_t launch_fused(const DBlock* blocks, int nblocks, const InView<float>& in, const StateView& s,
                          const Workspace& ws, const KParams& kp, cudaStream_t st);
 bool fused_block_ok(const DBlock& b);
+// Face fluxes of the mixed path by k_faces_tile (faces_tile.cu): stencils and metric staged in shared
+// memory per tile of a block; blocks with 3 ghosts and at most 16 cells along x, ideal gas, order-2 metric.
+cudaError_t launch_faces_tile(const DBlock* blocks, const FaceTile* tiles, int ntiles, const InView<float>& in,
+                              const Workspace& ws, const KParams& kp, cudaStream_t st);
 
 // Launchers (stage_kernels.cu).  Each returns the cudaError_t of its launch.
 // ev: nullptr, or GR_NKERNELS + 1 events recorded before the input cast (mixed path) and after

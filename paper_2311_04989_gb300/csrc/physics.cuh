@@ -235,25 +235,37 @@ __device__ __forceinline__ void cell_metric(const DBlock& b, const InView<R>& m,
 // Reconstruction (Sec. 3.4): van Leer PLM and WENOZ (Borges et al.).
 // s[0..5] = cells f-3 .. f+2 around the face f (between s[2] and s[3]).
 // ------------------------------------------------------------------------------------------------
+// Arithmetic of the PLM, WENO5 and PPM reconstructions.  FP32 (mixed path): explicit round-to-nearest
+// operations that the compiler never fuses into an FMA, so a stencil evaluates to the same bits in every
+// kernel that reconstructs it (a fused multiply-add is otherwise chosen per kernel, where a common
+// subexpression of the two face states can change which product gets fused).  FP64: the plain operators
+// in the oracle's order.
+template <class R> __device__ __forceinline__ R xm(R a, R b) { return a * b; }
+template <> __device__ __forceinline__ float xm(float a, float b) { return __fmul_rn(a, b); }
+template <class R> __device__ __forceinline__ R xa(R a, R b) { return a + b; }
+template <> __device__ __forceinline__ float xa(float a, float b) { return __fadd_rn(a, b); }
+template <class R> __device__ __forceinline__ R xs(R a, R b) { return a - b; }
+template <> __device__ __forceinline__ float xs(float a, float b) { return __fsub_rn(a, b); }
+
 template <class R>
 __device__ __forceinline__ R vl_slope(R wm, R w0, R wp) {
-  const R dL = w0 - wm, dR = wp - w0;
-  const R pr = dL * dR;
-  return pr > R(0) ? R(2) * pr / (dL + dR) : R(0);
+  const R dL = xs(w0, wm), dR = xs(wp, w0);
+  const R pr = xm(dL, dR);
+  return pr > R(0) ? xm(R(2), pr) / xa(dL, dR) : R(0);
 }
 
 // smoothness indicators and candidate values shared by both weight forms
 template <class R>
 __device__ __forceinline__ void wenoz_parts(R v0, R v1, R v2, R v3, R v4, R q[3], R bk[3]) {
-  q[0] = (R(2) * v0 - R(7) * v1 + R(11) * v2) * R(1.0 / 6.0);
-  q[1] = (-v1 + R(5) * v2 + R(2) * v3) * R(1.0 / 6.0);
-  q[2] = (R(2) * v2 + R(5) * v3 - v4) * R(1.0 / 6.0);
-  const R a0 = v0 - R(2) * v1 + v2, c0 = v0 - R(4) * v1 + R(3) * v2;
-  const R a1 = v1 - R(2) * v2 + v3, c1 = v1 - v3;
-  const R a2 = v2 - R(2) * v3 + v4, c2 = R(3) * v2 - R(4) * v3 + v4;
-  bk[0] = R(13.0 / 12.0) * a0 * a0 + R(0.25) * c0 * c0;
-  bk[1] = R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
-  bk[2] = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
+  q[0] = xm(xa(xs(xm(R(2), v0), xm(R(7), v1)), xm(R(11), v2)), R(1.0 / 6.0));
+  q[1] = xm(xa(xa(-v1, xm(R(5), v2)), xm(R(2), v3)), R(1.0 / 6.0));
+  q[2] = xm(xs(xa(xm(R(2), v2), xm(R(5), v3)), v4), R(1.0 / 6.0));
+  const R a0 = xa(xs(v0, xm(R(2), v1)), v2), c0 = xa(xs(v0, xm(R(4), v1)), xm(R(3), v2));
+  const R a1 = xa(xs(v1, xm(R(2), v2)), v3), c1 = xs(v1, v3);
+  const R a2 = xa(xs(v2, xm(R(2), v3)), v4), c2 = xa(xs(xm(R(3), v2), xm(R(4), v3)), v4);
+  bk[0] = xa(xm(xm(R(13.0 / 12.0), a0), a0), xm(xm(R(0.25), c0), c0));
+  bk[1] = xa(xm(xm(R(13.0 / 12.0), a1), a1), xm(xm(R(0.25), c1), c1));
+  bk[2] = xa(xm(xm(R(13.0 / 12.0), a2), a2), xm(xm(R(0.25), c2), c2));
 }
 
 // WENOZ value at the right edge of the middle cell of v0..v4.
@@ -325,10 +337,10 @@ __device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, floa
   float q[3], bk[3];
   wenoz_parts(v0, v1, v2, v3, v4, q, bk);
   const float e = 1e-18f;
-  const float w0 = __fdividef(0.1f, (bk[0] + e) * (bk[0] + e));
-  const float w1 = __fdividef(0.6f, (bk[1] + e) * (bk[1] + e));
-  const float w2 = __fdividef(0.3f, (bk[2] + e) * (bk[2] + e));
-  return __fdividef(w0 * q[0] + w1 * q[1] + w2 * q[2], w0 + w1 + w2);
+  const float w0 = __fdividef(0.1f, xm(xa(bk[0], e), xa(bk[0], e)));
+  const float w1 = __fdividef(0.6f, xm(xa(bk[1], e), xa(bk[1], e)));
+  const float w2 = __fdividef(0.3f, xm(xa(bk[2], e), xa(bk[2], e)));
+  return __fdividef(xa(xa(xm(w0, q[0]), xm(w1, q[1])), xm(w2, q[2])), xa(xa(w0, w1), w2));
 }
 
 // PPM: fourth-order interface values limited by the extremum-preserving criterion of Colella & Sekora,
@@ -337,16 +349,16 @@ template <class R> __device__ __forceinline__ R rsgn(R x) { return x > R(0) ? R(
 
 template <class R>
 __device__ __forceinline__ R ppm_iface(R q0, R q1, R q2, R q3) {
-  R qf = R(7.0 / 12.0) * (q1 + q2) - R(1.0 / 12.0) * (q0 + q3);
-  if ((qf - q1) * (q2 - qf) < R(0)) {
-    const R d2f = R(3) * (q1 - R(2) * qf + q2);
-    const R d2l = q0 - R(2) * q1 + q2;
-    const R d2r = q1 - R(2) * q2 + q3;
+  R qf = xs(xm(R(7.0 / 12.0), xa(q1, q2)), xm(R(1.0 / 12.0), xa(q0, q3)));
+  if (xm(xs(qf, q1), xs(q2, qf)) < R(0)) {
+    const R d2f = xm(R(3), xa(xs(q1, xm(R(2), qf)), q2));
+    const R d2l = xa(xs(q0, xm(R(2), q1)), q2);
+    const R d2r = xa(xs(q1, xm(R(2), q2)), q3);
     const R sf = rsgn(d2f);
     R d2lim = R(0);
     if (sf == rsgn(d2l) && sf == rsgn(d2r) && d2f != R(0))
-      d2lim = sf * rmin(rmin(R(1.25) * rabs(d2l), R(1.25) * rabs(d2r)), rabs(d2f));
-    qf = R(0.5) * (q1 + q2) - d2lim * R(1.0 / 6.0);
+      d2lim = xm(sf, rmin(rmin(xm(R(1.25), rabs(d2l)), xm(R(1.25), rabs(d2r))), rabs(d2f)));
+    qf = xs(xm(R(0.5), xa(q1, q2)), xm(d2lim, R(1.0 / 6.0)));
   }
   return qf;
 }
@@ -355,26 +367,27 @@ template <class R>
 __device__ __forceinline__ void ppm_cell(R v0, R v1, R v2, R v3, R v4, R* qm, R* qp) {
   R l = ppm_iface(v0, v1, v2, v3), r = ppm_iface(v1, v2, v3, v4);
   const R q = v2;
-  if ((r - q) * (q - l) <= R(0) || (v1 - q) * (q - v3) <= R(0)) {
-    const R d2 = R(6) * (l - R(2) * q + r);
-    const R d2c = v1 - R(2) * q + v3;
-    const R d2l = v0 - R(2) * v1 + q;
-    const R d2r = q - R(2) * v3 + v4;
+  if (xm(xs(r, q), xs(q, l)) <= R(0) || xm(xs(v1, q), xs(q, v3)) <= R(0)) {
+    const R d2 = xm(R(6), xa(xs(l, xm(R(2), q)), r));
+    const R d2c = xa(xs(v1, xm(R(2), q)), v3);
+    const R d2l = xa(xs(v0, xm(R(2), v1)), q);
+    const R d2r = xa(xs(q, xm(R(2), v3)), v4);
     const R s2 = rsgn(d2);
     R d2lim = R(0);
     if (s2 == rsgn(d2c) && s2 == rsgn(d2l) && s2 == rsgn(d2r) && d2 != R(0))
-      d2lim = s2 * rmin(rmin(rmin(R(1.25) * rabs(d2l), R(1.25) * rabs(d2r)), R(1.25) * rabs(d2c)), rabs(d2));
+      d2lim = xm(s2, rmin(rmin(rmin(xm(R(1.25), rabs(d2l)), xm(R(1.25), rabs(d2r))), xm(R(1.25), rabs(d2c))),
+                          rabs(d2)));
     if (d2 == R(0)) {
       l = q;
       r = q;
     } else {
       const R ratio = d2lim / d2;
-      l = q + (l - q) * ratio;
-      r = q + (r - q) * ratio;
+      l = xa(q, xm(xs(l, q), ratio));
+      r = xa(q, xm(xs(r, q), ratio));
     }
   } else {
-    if (rabs(r - q) >= R(2) * rabs(l - q)) r = q - R(2) * (l - q);
-    if (rabs(l - q) >= R(2) * rabs(r - q)) l = q - R(2) * (r - q);
+    if (rabs(xs(r, q)) >= xm(R(2), rabs(xs(l, q)))) r = xs(q, xm(R(2), xs(l, q)));
+    if (rabs(xs(l, q)) >= xm(R(2), rabs(xs(r, q)))) l = xs(q, xm(R(2), xs(r, q)));
   }
   *qm = l;
   *qp = r;
@@ -427,8 +440,8 @@ template <class R, int METHOD>
 __device__ __forceinline__ void recon_plain(const R s[6], R eps, R* L, R* Rr) {
   constexpr int method = METHOD;
   if constexpr (method == GR_RECON_PLM) {
-    *L = s[2] + R(0.5) * vl_slope(s[1], s[2], s[3]);
-    *Rr = s[3] - R(0.5) * vl_slope(s[2], s[3], s[4]);
+    *L = xa(s[2], xm(R(0.5), vl_slope(s[1], s[2], s[3])));
+    *Rr = xs(s[3], xm(R(0.5), vl_slope(s[2], s[3], s[4])));
   } else if constexpr (method == GR_RECON_WENOZ) {
     if constexpr (sizeof(R) == sizeof(float)) {
       wenoz_pair(s, eps, L, Rr);

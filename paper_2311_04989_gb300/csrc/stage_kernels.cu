@@ -761,7 +761,15 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
   }
   if (ev) cudaEventRecord(ev[2], st);
   const KLaunch& f = kl[SK_FACES];
-  if (f.nwork) {
+  if constexpr (sizeof(R) == sizeof(float) && EOS == GR_EOS_IDEAL) {
+    if (ws.nftiles > 0 && in.order == 2) {   // the tiled face sweep (the host checked that every block qualifies)
+      const cudaError_t e = launch_faces_tile(blocks, ws.ftiles, ws.nftiles, in, ws, kp, st);
+      if (e != cudaSuccess) return e;
+    } else if (f.nwork) {
+      const cudaError_t e = launch_faces(f, blocks, in, ws, kp, st);
+      if (e != cudaSuccess) return e;
+    }
+  } else if (f.nwork) {
     const cudaError_t e = launch_faces(f, blocks, in, ws, kp, st);
     if (e != cudaSuccess) return e;
   }

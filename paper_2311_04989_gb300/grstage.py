@@ -37,7 +37,7 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
            "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
            "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong", "gr_host_stage", "gr_cast_f32",
-           "gr_peak_alu", "gr_mesh_set_fused", "gr_mesh_get_fused"]
+           "gr_peak_alu", "gr_mesh_set_path", "gr_mesh_get_path"]
 GR_ABI_VERSION = 3
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
@@ -138,8 +138,8 @@ def load(path: str = LIB_PATH):
     L.gr_eos_h0.restype = C.c_double
     L.gr_diag.argtypes = [vp, C.c_void_p * 5, C.c_void_p * 3, C.POINTER(C.c_double), vp]
     L.gr_cast_f32.argtypes = [vp, vp, C.c_int64, vp]
-    L.gr_mesh_set_fused.argtypes = [vp, i32]
-    L.gr_mesh_get_fused.argtypes = [vp]
+    L.gr_mesh_set_path.argtypes = [vp, i32]
+    L.gr_mesh_get_path.argtypes = [vp]
     L.gr_peak_alu.argtypes = [i32, i32, i32, C.c_int64, vp, C.POINTER(C.c_double), vp]
     L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
                                   C.POINTER(C.c_double), vp]
@@ -301,12 +301,16 @@ def gr_cast_f32(src, dst, stream=None):
                               _stream(stream)), "gr_cast_f32")
 
 
-def gr_mesh_set_fused(mesh, enable: bool):
-    _check(load().gr_mesh_set_fused(mesh, 1 if enable else 0), "gr_mesh_set_fused")
+GR_PATH_SEPARATE, GR_PATH_FUSED, GR_PATH_TILED_FACES = 0, 1, 2
+PATH_NAMES = {GR_PATH_SEPARATE: "separate kernels", GR_PATH_FUSED: "fused sweep", GR_PATH_TILED_FACES: "tiled face sweep"}
 
 
-def gr_mesh_get_fused(mesh) -> int:
-    return int(load().gr_mesh_get_fused(mesh))
+def gr_mesh_set_path(mesh, path: int):
+    _check(load().gr_mesh_set_path(mesh, int(path)), "gr_mesh_set_path")
+
+
+def gr_mesh_get_path(mesh) -> int:
+    return int(load().gr_mesh_get_path(mesh))
 
 
 def gr_peak_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream=None) -> float:

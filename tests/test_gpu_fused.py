@@ -1,6 +1,7 @@
 """The fused sweep of the mixed path (k_fused: reconstruction, HLLE fluxes, corner EMFs, CT update and flux
-divergence of a block in one pass, fluxes and EMFs in shared memory) against the separate kernels: the two
-paths must give bitwise the same stage (U', W', status, B' and the FP32 copies of W', B'), on uneven
+divergence of a block in one pass, fluxes and EMFs in shared memory) and the tiled face sweep (k_faces_tile:
+face fluxes from stencils and metric staged in shared memory) against the separate kernels: the paths must
+give bitwise the same stage (U', W', status, B' and the FP32 copies of W', B'), on uneven
 blocks of every size the sweep takes (ragged x-y extents up to 16, any length in z), for every
 reconstruction method, both RK forms and both corner-EMF rules, on smooth random states and across a star
 surface (atmosphere resets and root-find cells in one block).  And against the oracle on the bench's
@@ -26,7 +27,7 @@ def built():
     B.build()
 
 
-def _run(blocks, P, fused, dt, rk=False):
+def _run(blocks, P, path, dt, rk=False):
     import torch
     pools = GH.Pools(blocks)
     U = pools.cells([H.cons_from_prims(b, P) for b in blocks], 5)
@@ -46,8 +47,8 @@ def _run(blocks, P, fused, dt, rk=False):
             gp.rk_g0, gp.rk_g1, gp.rk_beta = 0.75, 0.25, 0.25
         state = G.state_struct(U, U0, B, B0, W, Uo, Bo, Wo, st)
         G.set_fp32_copies(state, Wo32=Wo32, Bo32=Bo32)
-        G.gr_mesh_set_fused(mesh, fused)
-        assert G.gr_mesh_get_fused(mesh) == int(fused)
+        G.gr_mesh_set_path(mesh, path)
+        assert G.gr_mesh_get_path(mesh) == path
         G.gr_stage(mesh, G.metric_struct(M), state, dt, gp, torch.cuda.current_stream())
         torch.cuda.synchronize()
     finally:
@@ -68,9 +69,9 @@ def test_fused_sweep_equals_the_separate_kernels_bitwise(recon, rk):
     blocks = [I.random_block(n=n, g=3, seed=120 + k, metric_amp=0.03) for k, n in enumerate(shapes)]
     P = GH.mixed_params(O.Params(gamma_ad=2.0, recon=recon, rho_atm=1e-14, tol=1e-12))
     dt = 0.2 * min(min(b.dx) for b in blocks)
-    sep, _ = _run(blocks, P, False, dt, rk)
-    fus, _ = _run(blocks, P, True, dt, rk)
-    _same(sep, fus)
+    sep, _ = _run(blocks, P, G.GR_PATH_SEPARATE, dt, rk)
+    for path in (G.GR_PATH_FUSED, G.GR_PATH_TILED_FACES):
+        _same(sep, _run(blocks, P, path, dt, rk)[0])
 
 
 @pytest.mark.parametrize("emf", [0, 1])
@@ -80,11 +81,11 @@ def test_fused_sweep_across_a_star_surface_bitwise(emf):
     blocks = I.split_block(star, (2, 2, 2))
     P = GH.mixed_params(O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-10, emf=emf))
     dt = 0.25 * star.dx[0]
-    sep, pools = _run(blocks, P, False, dt)
-    fus, _ = _run(blocks, P, True, dt)
+    sep, pools = _run(blocks, P, G.GR_PATH_SEPARATE, dt)
     st = sep[2].numpy()
     assert np.any(st & 1) and np.any(st == 0)     # both atmosphere resets and solved cells
-    _same(sep, fus)
+    for path in (G.GR_PATH_FUSED, G.GR_PATH_TILED_FACES):
+        _same(sep, _run(blocks, P, path, dt)[0])
 
 
 def test_fused_sweep_refuses_blocks_it_does_not_take():
@@ -92,9 +93,10 @@ def test_fused_sweep_refuses_blocks_it_does_not_take():
     pools = GH.Pools(big)
     mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
     try:
-        with pytest.raises(G.GrstageError, match="wider than 16"):
-            G.gr_mesh_set_fused(mesh, True)
-        assert G.gr_mesh_get_fused(mesh) == 0
+        for path in (G.GR_PATH_FUSED, G.GR_PATH_TILED_FACES):
+            with pytest.raises(G.GrstageError, match="wider than 16"):
+                G.gr_mesh_set_path(mesh, path)
+        assert G.gr_mesh_get_path(mesh) == G.GR_PATH_SEPARATE
     finally:
         G.gr_mesh_destroy(mesh)
 
@@ -109,7 +111,7 @@ def test_fused_sweep_on_two_star_blocks_against_the_oracle():
     blocks = [mi.block(b) for b in sample]
     P = GH.mixed_params(O.Params(gamma_ad=2.0, recon=1, rho_atm=mi.rho_atm, p_atm=mi.p_atm, tol=1e-10))
     dt = 0.25 * mi.dx
-    got, pools = _run(blocks, P, True, dt)
+    got, pools = _run(blocks, P, G.GR_PATH_FUSED, dt)
     Uo, Wo, st = (pools.unpack_cells(got[k].cuda(), n) for k, n in ((0, 5), (1, 5), (2, 1)))
     Bo = pools.unpack_faces([x.cuda() for x in got[4:7]])
     out = [dict(U=Uo[b], W=Wo[b], B=Bo[b], status=st[b]) for b in range(len(blocks))]
