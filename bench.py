@@ -934,8 +934,10 @@ def main():
     c2p = None
     if not a.no_c2p:
         from paper_2311_04989_gb300 import learned_bracket as LB
+        # the stage output is the mixed path's: its atmosphere cells sit at the threshold up to its FP32
+        # sqrt(gamma), so con2prim classifies them with the mixed path's band
         p64 = G.gr_params_default(recon=G.GR_RECON_WENOZ, gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm,
-                                  tol=1e-10)
+                                  tol=1e-10, atm_band=G.GR_MIXED_ATM_BAND)
         Uref = snap[head][2]
         Bref = snap[head][1]
         # training samples: the solves of this workload's stage output ("prior solves" of the run)
@@ -951,7 +953,7 @@ def main():
                "mlp_loss_first_last": [losses[0], losses[-1]]}
         for name, guess in (("none", G.GR_GUESS_NONE), ("fp32", G.GR_GUESS_FP32), ("mlp", G.GR_GUESS_MLP)):
             pc = G.gr_params_default(recon=G.GR_RECON_WENOZ, gamma_ad=2.0, rho_atm=mesh_in.rho_atm,
-                                     p_atm=mesh_in.p_atm, tol=1e-10, c2p_guess=guess)
+                                     p_atm=mesh_in.p_atm, tol=1e-10, c2p_guess=guess, atm_band=G.GR_MIXED_ATM_BAND)
             pc.mlp = int(Pm.data_ptr())
             Uc = Uref.clone(); Wc = torch.zeros_like(W)
             stc = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)

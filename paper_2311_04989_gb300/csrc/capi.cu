@@ -322,6 +322,8 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
       d.N[a] = s.n[a] + 2 * s.ng;
       d.dx[a] = s.dx[a];
       d.idx[a] = 1.0 / s.dx[a];
+      for (int k = 0; k < 3; ++k) d.mdiv[a][k] = mdiv_of((unsigned)(s.n[a] + k));
+      d.mdiv[a][3] = mdiv_of((unsigned)d.N[a]);
     }
     if (s.cell_off < 0 || s.vert_off < 0 || s.face_off[0] < 0 || s.face_off[1] < 0 || s.face_off[2] < 0) {
       mesh_free(m);
@@ -493,6 +495,9 @@ static KParams kparams(const gr_params* p, double dt) {
   k.c2p_guess = p->c2p_guess;
   k.eos = p->eos;
   k.gamma_ad = p->gamma_ad; k.rho_atm = p->rho_atm; k.p_atm = p->p_atm; k.f_thr = p->f_thr;
+  k.gamma_f = (float)p->gamma_ad;
+  k.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
+  k.vmax2_f = (float)k.vmax2;
   k.W_max = p->W_max; k.M_max = p->M_max; k.tol = p->tol; k.weno_eps = p->weno_eps;
   k.rk_g0 = p->rk_g0; k.rk_g1 = p->rk_g1; k.rk_beta = p->rk_beta;
   k.rk_form = (p->rk_g0 != 0.0 ? RK_G0 : 0) | (p->rk_g1 != 1.0 ? RK_G1 : 0);
@@ -514,6 +519,10 @@ static KParams kparams(const gr_params* p, double dt) {
     k.t64 = tab_view<double>(t, t.d64);
     k.t32 = tab_view<float>(t, t.d32);
   }
+  k.top = 1.0 / k.h0;
+  k.h0sq = k.h0 * k.h0;
+  k.top_f = (float)k.top;
+  k.h0sq_f = (float)k.h0sq;
   return k;
 }
 

@@ -26,7 +26,15 @@ struct DBlock {
   double idx[3];       // 1/dx
   long long cell, face[3], vert;         // caller pools
   long long wcell, wface[3], wvert;      // workspace pools
+  // quotients by the per-axis element counts n, n + 1, n + 2 and N without integer division (which the
+  // compiler turns into conversions on the FP64 pipe): q = floor(e / d) = umulhi(2 e, mdiv) for 32-bit e,
+  // mdiv = ceil(2^63 / d)
+  unsigned long long mdiv[3][4];
 };
+
+__host__ __device__ __forceinline__ unsigned long long mdiv_of(unsigned d) {
+  return (0x7FFFFFFFFFFFFFFFull) / d + 1ull;   // ceil(2^63 / d) for d >= 1
+}
 
 // One CTA's slice of work: elements [start, start + tile) of region `kind` of block `block`
 // in direction `dir` (faces, edges) or 0, tile = the CTA size it was built for.
@@ -95,6 +103,14 @@ struct FaceTile {
   int block, j0, j1, pad;
 };
 
+#ifdef __CUDACC__
+// floor(e / d) for 32-bit e from mdiv = mdiv_of(d): exact (e (2^63 / d + eps) / 2^63 exceeds e / d by less
+// than 2^33 / 2^63, far below 1 / d)
+__device__ __forceinline__ unsigned udiv_m(unsigned e, unsigned long long mdiv) {
+  return (unsigned)__umul64hi((unsigned long long)e << 1, mdiv);
+}
+#endif
+
 // Level-boundary records (same layouts as gr_level_face / gr_level_map)
 struct LevelFace {
   int coarse, fine, dir, side, o1, o2;
@@ -136,6 +152,12 @@ enum { RK_G0 = 1, RK_G1 = 2 };   // bits of KParams::rk_form
 struct KParams {   // gr_params flattened for the device
   int recon, emf, ceiling, max_iter, c2p_guess, eos;
   double gamma_ad, rho_atm, p_atm, f_thr, W_max, M_max, tol, weno_eps;
+  float gamma_f;      // gamma_ad rounded to FP32 once on the host (an FP64 -> FP32 conversion on the device
+                      // would run on the narrow FP64 pipe in every FP32 face evaluation)
+  // con2prim constants formed once on the host: the velocity cap v_max^2 = 1 - 1/W_max^2, the bracket top
+  // 1/h0 and h0^2, in FP64 and (for the FP32 pre-solve) FP32
+  double vmax2, top, h0sq;
+  float vmax2_f, top_f, h0sq_f;
   double rk_g0, rk_g1, rk_beta;
   int rk_form;        // RK_G0 | RK_G1: which of rk_g0 != 0, rk_g1 != 1 hold (set on the host)
   double rho_thr;     // atmosphere threshold f_thr rho_atm (1 + atm_band): within the band counts as reached

@@ -496,7 +496,9 @@ __device__ __forceinline__ void recon(const R s[6], R eps, R* L, R* Rr) {
 template <class R, int EOS>
 __device__ __forceinline__ void eos_rhoh_cs2(const KParams& kp, R rho, R p, R ye, R* rhoh, R* cs2) {
   if constexpr (EOS == GR_EOS_IDEAL) {
-    const R gam = R(kp.gamma_ad);
+    R gam;
+    if constexpr (sizeof(R) == sizeof(float)) gam = kp.gamma_f;
+    else gam = kp.gamma_ad;
     *rhoh = rho + gam * rdiv(p, gam - R(1));
     *cs2 = rdiv(gam * p, *rhoh);
   } else {
@@ -871,8 +873,8 @@ __device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<d
   I.D = (float)I64.D; I.q = (float)I64.q; I.r2 = (float)I64.r2; I.b2 = (float)I64.b2; I.rb = (float)I64.rb;
   I.ye = (float)I64.ye;
   if (!(I.D > 0.f) || !isfinite(I.q) || !isfinite(I.r2) || !isfinite(I.b2)) return 0.f;
-  const float gam = (float)P.gamma_ad, vmax2 = (float)(1.0 - 1.0 / (P.W_max * P.W_max));
-  const float top = EOS ? (float)(1.0 / P.h0) : 1.f, h0sq = EOS ? (float)(P.h0 * P.h0) : 1.f;
+  const float gam = P.gamma_f, vmax2 = P.vmax2_f;
+  const float top = EOS ? P.top_f : 1.f, h0sq = EOS ? P.h0sq_f : 1.f;
   float mup = top, root, hi;
   int it;
   const float f1 = c2p_aux<float>(I, h0sq, top);
@@ -1006,9 +1008,9 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     I.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
     I.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     I.b2 = BB * iD;
-    const double gam = P.gamma_ad, vmax2 = 1.0 - 1.0 / (P.W_max * P.W_max);
+    const double gam = P.gamma_ad, vmax2 = P.vmax2;
     // upper end of the bracket search: mu <= 1/h0
-    const double top = EOS ? 1.0 / P.h0 : 1.0, h0sq = EOS ? P.h0 * P.h0 : 1.0;
+    const double top = EOS ? P.top : 1.0, h0sq = EOS ? P.h0sq : 1.0;
     C2PVal<double> E;
     int nevals = 0;   // FP64 master-function evaluations (reported through *iters)
     int kh = -1;      // temperature interval of the last evaluation (table)

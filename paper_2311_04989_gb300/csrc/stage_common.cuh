@@ -18,20 +18,23 @@ __device__ __forceinline__ double stage_bdt(const KParams& kp) {
 // ------------------------------------------------------------------------------------------------
 template <int KIND, int DIR>
 __device__ __forceinline__ bool decode(const Work& w, const DBlock& b, int p[3]) {
-  int lo[3], cnt[3];
+  int lo[3], cnt[3], k[3];   // k: which of n, n + 1, n + 2, N the count is (its entry of b.mdiv)
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (KIND == R_CELLS_ALL) { lo[a] = -b.g; cnt[a] = b.N[a]; }
-    else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a] + 2; }
-    else if (KIND == R_EDGES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] : b.n[a] + 1; }
-    else if (KIND == R_CTFACES) { lo[a] = 0; cnt[a] = (a == DIR) ? b.n[a] + 1 : b.n[a]; }
-    else { lo[a] = 0; cnt[a] = b.n[a]; }
+    if (KIND == R_CELLS_ALL) { lo[a] = -b.g; k[a] = 3; }
+    else if (KIND == R_FACES) { lo[a] = (a == DIR) ? 0 : -1; k[a] = (a == DIR) ? 1 : 2; }
+    else if (KIND == R_EDGES) { lo[a] = 0; k[a] = (a == DIR) ? 0 : 1; }
+    else if (KIND == R_CTFACES) { lo[a] = 0; k[a] = (a == DIR) ? 1 : 0; }
+    else { lo[a] = 0; k[a] = 0; }
+    cnt[a] = k[a] == 3 ? b.N[a] : b.n[a] + k[a];
   }
   const int e = w.start + threadIdx.x;
   if (e >= cnt[0] * cnt[1] * cnt[2]) return false;
-  p[0] = lo[0] + e % cnt[0];
-  p[1] = lo[1] + (e / cnt[0]) % cnt[1];
-  p[2] = lo[2] + e / (cnt[0] * cnt[1]);
+  const unsigned q0 = udiv_m((unsigned)e, b.mdiv[0][k[0]]);
+  const unsigned q1 = udiv_m(q0, b.mdiv[1][k[1]]);
+  p[0] = lo[0] + (e - (int)q0 * cnt[0]);
+  p[1] = lo[1] + ((int)q0 - (int)q1 * cnt[1]);
+  p[2] = lo[2] + (int)q1;
   return true;
 }
 

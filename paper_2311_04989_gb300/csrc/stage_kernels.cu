@@ -470,7 +470,8 @@ __global__ void __maxnreg__(168) k_c2p(const DBlock* __restrict__ blocks,
     const int2 job = ws.jobs[jdx];
     const DBlock b = blocks[job.x];
     const int e = job.y;
-    const int i = e % b.n[0], j = (e / b.n[0]) % b.n[1], k = e / (b.n[0] * b.n[1]);
+    const unsigned q0 = udiv_m((unsigned)e, b.mdiv[0][0]), q1 = udiv_m(q0, b.mdiv[1][0]);
+    const int i = e - (int)q0 * b.n[0], j = (int)q0 - (int)q1 * b.n[1], k = (int)q1;
     const long long c = b.cell + cix(b, i, j, k);
     constexpr int NQ = EOS ? 6 : 5;
     double q[6], Bn[3], wn[7];
