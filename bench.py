@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "GRMHD cell-updates/s per RK stage"
 UNIT = "cell-updates/s"
 WORKLOAD = "two-star full-stage throughput: 4096 blocks of 16^3 (ng=3), WENOZ+HLLE, CT, con2prim"
+# con2prim bracket proposal of the timed mixed stage: none.  The FP32 pre-solve and the learned bracket
+# (both timed in the con2prim_guess / con2prim_table sections) cut FP64 master-function evaluations but
+# cost more than they save on GB300 (measured on both workloads), so the headline solves without a guess.
+MIXED_GUESS = 0   # GR_GUESS_NONE
 FP64_NOMINAL_TFLOPS = 1.25      # nominal dense FP64 of the GB300 (context only; the roofline uses the measured rate)
 
 
@@ -85,6 +89,8 @@ def parse():
     ap.add_argument("--no-rk", action="store_true", help="skip the timing of a whole RK3 driver step")
     ap.add_argument("--no-adm", action="store_true", help="skip the timing of the matter-source outputs")
     ap.add_argument("--no-configs", action="store_true", help="skip the smaller configurations (C1-C3)")
+    ap.add_argument("--path", default="auto", choices=["auto", "separate", "fused", "tiled"],
+                    help="path of the mixed stage: the autotuner's choice, or one forced")
     ap.add_argument("--e2e-batches", type=int, default=8, help="block batches of the host-buffer stage")
     a = ap.parse_args()
     if a.warmup < 3:
@@ -326,8 +332,8 @@ def run_reference(a):
 # ---------------------------------------------------------------------------------------------
 # the sources the stage kernels are compiled from (a change to any of them invalidates the
 # committed DRAM traffic; the driver, matter-source and level-boundary kernels do not enter)
-STAGE_SOURCES = ("eos.cuh", "faces_f32.cu", "faces_f64.cu", "faces_impl.cuh", "internal.h", "mlp.cuh", "physics.cuh",
-                 "stage_common.cuh", "stage_kernels.cu")
+STAGE_SOURCES = ("eos.cuh", "faces_core.cuh", "faces_f32.cu", "faces_f64.cu", "faces_impl.cuh", "internal.h", "mlp.cuh",
+                 "physics.cuh", "stage_common.cuh", "stage_kernels.cu", "update_common.cuh")
 
 
 def strip_comments(src):
@@ -455,7 +461,7 @@ def config_timings(a, ctx, dev, G, configs):
             p = G.gr_params_default(recon=cp["recon"], gamma_ad=cp["gamma"], rho_atm=cp["rho_atm"],
                                     p_atm=100.0 * cp["rho_atm"] ** cp["gamma"], tol=1e-10,
                                     precision=G.GR_PREC_MIXED if mixed else G.GR_PREC_FP64,
-                                    c2p_guess=G.GR_GUESS_FP32 if mixed else G.GR_GUESS_NONE,
+                                    c2p_guess=MIXED_GUESS if mixed else G.GR_GUESS_NONE,
                                     atm_band=G.GR_MIXED_ATM_BAND if mixed else 1e-12)
             G.gr_prim2con(mesh, metric, list(W), B, list(U), p, stream)
             Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
@@ -467,15 +473,19 @@ def config_timings(a, ctx, dev, G, configs):
             steps = max(a.steps, 10)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            G.gr_profile_begin(mesh, steps)
             e0.record(stream)
             for _ in range(steps):
                 G.gr_stage(mesh, metric, state, dt, p, stream)
             e1.record(stream)
             torch.cuda.synchronize()
+            kms, nst = G.gr_profile_end(mesh)
             ms = e0.elapsed_time(e1) / steps
             stv = st.to(torch.int32)
             row[prec] = {"ms_per_stage": ms, "cell_updates_per_s": cells / (ms / 1e3),
-                         "atmosphere_fraction": float(((stv & 1) != 0).sum().item()) / cells}
+                         "atmosphere_fraction": float(((stv & 1) != 0).sum().item()) / cells,
+                         "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst) for k in kms])),
+                         "path": G.PATH_NAMES[G.gr_mesh_get_path(mesh)] if mixed else "separate kernels"}
             del Uo, Wo, Bo, st, state
         row["ratio_mixed_over_fp64"] = row["fp64"]["ms_per_stage"] / row["mixed"]["ms_per_stage"]
         G.gr_mesh_destroy(mesh)
@@ -700,7 +710,7 @@ def main():
 
     def timed(precision, copies=False):
         mt, stt = (metric32, state32) if copies else (metric, state)
-        guess = G.GR_GUESS_FP32 if precision == G.GR_PREC_MIXED else G.GR_GUESS_NONE
+        guess = MIXED_GUESS if precision == G.GR_PREC_MIXED else G.GR_GUESS_NONE
         p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=precision, gamma_ad=2.0, c2p_guess=guess,
                                 rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                 atm_band=G.GR_MIXED_ATM_BAND if precision == G.GR_PREC_MIXED else 1e-12)
@@ -708,6 +718,9 @@ def main():
         shapes = None
         if not a.no_autotune:
             shapes, _ = G.gr_autotune(mesh, mt, stt, dt, p, 1 if precision == G.GR_PREC_FP64 else 3, stream)
+        if a.path != "auto" and precision == G.GR_PREC_MIXED:
+            G.gr_mesh_set_path(mesh, {"separate": G.GR_PATH_SEPARATE, "fused": G.GR_PATH_FUSED,
+                                      "tiled": G.GR_PATH_TILED_FACES}[a.path])
         for _ in range(a.warmup):
             G.gr_stage(mesh, mt, stt, dt, p, stream)
         torch.cuda.synchronize()
@@ -762,7 +775,7 @@ def main():
     paths = None
     if "mixed" in results:
         chosen = G.gr_mesh_get_path(mesh)
-        pm = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+        pm = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=MIXED_GUESS,
                                  gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                  atm_band=G.GR_MIXED_ATM_BAND)
         paths = {"autotuner_chose": G.PATH_NAMES[chosen]}
@@ -792,7 +805,7 @@ def main():
     if not a.no_e2e:
         hm = head == "mixed"
         p = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=(G.GR_PREC_MIXED if hm else G.GR_PREC_FP64),
-                                c2p_guess=(G.GR_GUESS_FP32 if hm else G.GR_GUESS_NONE),
+                                c2p_guess=(MIXED_GUESS if hm else G.GR_GUESS_NONE),
                                 gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                 atm_band=G.GR_MIXED_ATM_BAND if hm else 1e-12)
         # the host-buffer entry: pinned host pools in, pinned host pools out; the library copies batches
@@ -838,7 +851,7 @@ def main():
     # ---- the same stage replayed as a CUDA graph ------------------------------------------------
     graph_ms = None
     if head == "mixed":
-        pg = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+        pg = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=MIXED_GUESS,
                                  gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                  atm_band=G.GR_MIXED_ATM_BAND)
         gph = G.gr_graph_capture(mesh, metric, state, dt, pg)
@@ -857,7 +870,7 @@ def main():
     # ---- a whole RK3 step (ghost exchange + dt + 3 stages) replayed as one CUDA graph -------------
     rk = None
     if head == "mixed" and not a.no_rk:
-        pr = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=G.GR_GUESS_FP32,
+        pr = G.gr_params_default(recon=G.GR_RECON_WENOZ, precision=G.GR_PREC_MIXED, c2p_guess=MIXED_GUESS,
                                  gamma_ad=2.0, rho_atm=mesh_in.rho_atm, p_atm=mesh_in.p_atm, tol=1e-10,
                                  atm_band=G.GR_MIXED_ATM_BAND)
         nbr = I.block_grid_neighbours((a.nb,) * 3, periodic=(False,) * 3)

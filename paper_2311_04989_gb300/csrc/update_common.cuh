@@ -94,9 +94,16 @@ __device__ __forceinline__ void mixed_atm_reset(const DBlock& b, const StateView
   {
     const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
     const long long f2 = b.face[2] + fix(b, 2, i, j, k);
-    Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
-    Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + b.N[0]])));
-    Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + (long long)b.N[0] * b.N[1]])));
+    const long long oy = b.N[0], oz = (long long)b.N[0] * b.N[1];
+    if (s.Bo32[0]) {   // the FP32 copies the CT update wrote: the same values as converting Bo here
+      Bf[0] = R(0.5) * (R(s.Bo32[0][f0]) + R(s.Bo32[0][f0 + 1]));
+      Bf[1] = R(0.5) * (R(s.Bo32[1][f1]) + R(s.Bo32[1][f1 + oy]));
+      Bf[2] = R(0.5) * (R(s.Bo32[2][f2]) + R(s.Bo32[2][f2 + oz]));
+    } else {
+      Bf[0] = R(0.5) * (R(d2f_rn(s.Bo[0][f0])) + R(d2f_rn(s.Bo[0][f0 + 1])));
+      Bf[1] = R(0.5) * (R(d2f_rn(s.Bo[1][f1])) + R(d2f_rn(s.Bo[1][f1 + oy])));
+      Bf[2] = R(0.5) * (R(d2f_rn(s.Bo[2][f2])) + R(d2f_rn(s.Bo[2][f2 + oz])));
+    }
   }
   lower3(gam, Bf, Bl);
   const R BBd = Bf[0] * Bl[0] + Bf[1] * Bl[1] + Bf[2] * Bl[2];
