@@ -92,6 +92,10 @@ def parse():
     ap.add_argument("--path", default="auto", choices=["auto", "separate", "fused", "tiled"],
                     help="path of the mixed stage: the autotuner's choice, or one forced")
     ap.add_argument("--e2e-batches", type=int, default=8, help="block batches of the host-buffer stage")
+    ap.add_argument("--only-config", default=None, choices=["C1", "C2", "C3"],
+                    help="time only this smaller configuration (GPU, --precision, --no-autotune honoured) and "
+                         "print its figures (no headline line); for profiling one configuration's kernels")
+    ap.add_argument("--config-blocks", type=int, default=1024, help="blocks of the AMR-like batch (C3)")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -430,21 +434,30 @@ def per_variable_errors(torch, got, ref, interior):
     return out
 
 
-def config_inputs(I):
-    """The smaller benchmark configurations as seeded inputs: (name, blocks, oracle-style parameters)."""
-    tov = I.solve_tov()
-    c1 = [I.shock_tube_block(n=(16, 16, 16), g=3)]
-    c2 = [I.star_block(n=(64, 64, 64), g=3, half_width=10.02, tov=tov, A_b=0.05)]
-    c3 = I.amr_like_batch(nblocks=1024, workers=os.cpu_count() or 4)
-    return [("C1 shock tube, 1 block of 16^3, PLM, Gamma 5/3", c1, dict(gamma=5.0 / 3.0, recon=0, rho_atm=1e-10)),
-            ("C2 magnetised 64^3 star (A0), WENOZ", c2, dict(gamma=2.0, recon=1, rho_atm=1e-13 * tov.rho[0])),
-            ("C3 AMR-like batch, 1024 blocks of 16^3/24^3/32^3, WENOZ", c3, dict(gamma=5.0 / 3.0, recon=1, rho_atm=1e-14))]
+def config_inputs(I, only=None, c3_blocks=1024):
+    """The smaller benchmark configurations as seeded inputs: (name, blocks, oracle-style parameters);
+    only = "C1" / "C2" / "C3" builds that one alone (c3_blocks: the AMR-like batch's block count)."""
+    out = []
+    tov = I.solve_tov() if only in (None, "C2") else None
+    if only in (None, "C1"):
+        out.append(("C1 shock tube, 1 block of 16^3, PLM, Gamma 5/3", [I.shock_tube_block(n=(16, 16, 16), g=3)],
+                    dict(gamma=5.0 / 3.0, recon=0, rho_atm=1e-10)))
+    if only in (None, "C2"):
+        out.append(("C2 magnetised 64^3 star (A0), WENOZ",
+                    [I.star_block(n=(64, 64, 64), g=3, half_width=10.02, tov=tov, A_b=0.05)],
+                    dict(gamma=2.0, recon=1, rho_atm=1e-13 * tov.rho[0])))
+    if only in (None, "C3"):
+        out.append((f"C3 AMR-like batch, {c3_blocks} blocks of 16^3/24^3/32^3, WENOZ",
+                    I.amr_like_batch(nblocks=c3_blocks, workers=os.cpu_count() or 4),
+                    dict(gamma=5.0 / 3.0, recon=1, rho_atm=1e-14)))
+    return out
 
 
 def config_timings(a, ctx, dev, G, configs):
-    """Stage throughput of the smaller configurations on the GPU, FP64 and mixed, autotuned launch
-    shapes, a step = one gr_stage over all blocks of the configuration (inputs resident; the sizes are far
-    below L2, so these are L2-warm figures and say so)."""
+    """Stage throughput of the smaller configurations on the GPU, FP64 and mixed (or the one --precision
+    names), autotuned launch shapes unless --no-autotune, a step = one gr_stage over all blocks of the
+    configuration, inputs resident (C1 and C2 fit in L2, so theirs are L2-warm figures; C3's inputs,
+    several GB, do not)."""
     import torch
     out = {}
     stream = torch.cuda.current_stream()
@@ -457,6 +470,8 @@ def config_timings(a, ctx, dev, G, configs):
         dt = 0.25 * min(min(b.dx) for b in blocks)
         row = {"cells": cells, "blocks": len(blocks)}
         for prec in ("fp64", "mixed"):
+            if a.precision not in ("both", prec):
+                continue
             mixed = prec == "mixed"
             p = G.gr_params_default(recon=cp["recon"], gamma_ad=cp["gamma"], rho_atm=cp["rho_atm"],
                                     p_atm=100.0 * cp["rho_atm"] ** cp["gamma"], tol=1e-10,
@@ -467,7 +482,8 @@ def config_timings(a, ctx, dev, G, configs):
             Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
             st = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
             state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
-            G.gr_autotune(mesh, metric, state, dt, p, 1, stream)
+            if not a.no_autotune:
+                G.gr_autotune(mesh, metric, state, dt, p, 1, stream)
             for _ in range(a.warmup):
                 G.gr_stage(mesh, metric, state, dt, p, stream)
             steps = max(a.steps, 10)
@@ -487,7 +503,8 @@ def config_timings(a, ctx, dev, G, configs):
                          "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst) for k in kms])),
                          "path": G.PATH_NAMES[G.gr_mesh_get_path(mesh)] if mixed else "separate kernels"}
             del Uo, Wo, Bo, st, state
-        row["ratio_mixed_over_fp64"] = row["fp64"]["ms_per_stage"] / row["mixed"]["ms_per_stage"]
+        if "fp64" in row and "mixed" in row:
+            row["ratio_mixed_over_fp64"] = row["fp64"]["ms_per_stage"] / row["mixed"]["ms_per_stage"]
         G.gr_mesh_destroy(mesh)
         out[name] = row
         del L, W, B, M, U
@@ -655,6 +672,15 @@ def main():
     def barrier():
         if dist:
             dist.barrier()
+
+    if a.only_config:
+        ctx = G.gr_context_create(lrank)
+        cfg = config_inputs(I, a.only_config, a.config_blocks)
+        res = config_timings(a, ctx, torch.device("cuda", lrank), G, cfg)
+        G.gr_context_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"configs": res}))
+        return
 
     # ---- workload ------------------------------------------------------------------------------
     t_gen = time.time()
