@@ -96,6 +96,8 @@ def parse():
                     help="time only this smaller configuration (GPU, --precision, --no-autotune honoured) and "
                          "print its figures (no headline line); for profiling one configuration's kernels")
     ap.add_argument("--config-blocks", type=int, default=1024, help="blocks of the AMR-like batch (C3)")
+    ap.add_argument("--config-guess", default="none", choices=["none", "fp32"],
+                    help="con2prim guess of the mixed stage in the smaller configurations")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -476,7 +478,8 @@ def config_timings(a, ctx, dev, G, configs):
             p = G.gr_params_default(recon=cp["recon"], gamma_ad=cp["gamma"], rho_atm=cp["rho_atm"],
                                     p_atm=100.0 * cp["rho_atm"] ** cp["gamma"], tol=1e-10,
                                     precision=G.GR_PREC_MIXED if mixed else G.GR_PREC_FP64,
-                                    c2p_guess=MIXED_GUESS if mixed else G.GR_GUESS_NONE,
+                                    c2p_guess=({"none": G.GR_GUESS_NONE, "fp32": G.GR_GUESS_FP32}[a.config_guess]
+                                               if mixed else G.GR_GUESS_NONE),
                                     atm_band=G.GR_MIXED_ATM_BAND if mixed else 1e-12)
             G.gr_prim2con(mesh, metric, list(W), B, list(U), p, stream)
             Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
@@ -502,6 +505,9 @@ def config_timings(a, ctx, dev, G, configs):
                          "atmosphere_fraction": float(((stv & 1) != 0).sum().item()) / cells,
                          "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst) for k in kms])),
                          "path": G.PATH_NAMES[G.gr_mesh_get_path(mesh)] if mixed else "separate kernels"}
+            if mixed:
+                row[prec]["c2p_guess"] = a.config_guess
+                row[prec]["guess_rejected"] = int(((stv & 64) != 0).sum().item())
             del Uo, Wo, Bo, st, state
         if "fp64" in row and "mixed" in row:
             row["ratio_mixed_over_fp64"] = row["fp64"]["ms_per_stage"] / row["mixed"]["ms_per_stage"]

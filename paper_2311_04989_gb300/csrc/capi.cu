@@ -1405,6 +1405,7 @@ struct gr_driver {
   gr_mesh* mesh = nullptr;
   int device = 0;
   int* d_nbr = nullptr;
+  GhostMap gmap{};   // gather map of the same-level ghost fill (device arrays in allocs)
   double* d_rate = nullptr;
   double* d_dt = nullptr;
   double* U[2][6] = {};
@@ -1451,6 +1452,11 @@ int gr_driver_create(gr_mesh* mesh, const int32_t* nbr, gr_driver** out) {
       }
     }
   }
+  std::vector<int2> gent;
+  std::vector<int> gout;
+  std::vector<int4> goff;
+  if (build_ghost_map(mesh->h_blocks.data(), nb, gent, gout, goff) != 0)
+    return fail(GR_EINVAL, "gr_driver_create: a block's ghost-padded arrays must hold fewer than 2^27 elements");
   DeviceGuard g(mesh->ctx->device);
   gr_driver* d = new gr_driver();
   d->mesh = mesh;
@@ -1462,6 +1468,18 @@ int gr_driver_create(gr_mesh* mesh, const int32_t* nbr, gr_driver** out) {
   };
   cudaError_t e = dalloc(sizeof(int) * 27 * std::max(1, nb), (void**)&d->d_nbr);
   if (e == cudaSuccess && nb) e = cudaMemcpy(d->d_nbr, nbr, sizeof(int) * 27 * nb, cudaMemcpyHostToDevice);
+  {
+    int2* ge = nullptr;
+    int* go = nullptr;
+    int4* gf = nullptr;
+    if (e == cudaSuccess) e = dalloc(sizeof(int2) * std::max<size_t>(gent.size(), 1), (void**)&ge);
+    if (e == cudaSuccess) e = dalloc(sizeof(int) * std::max<size_t>(gout.size(), 1), (void**)&go);
+    if (e == cudaSuccess) e = dalloc(sizeof(int4) * std::max<size_t>(goff.size(), 1), (void**)&gf);
+    if (e == cudaSuccess && !gent.empty()) e = cudaMemcpy(ge, gent.data(), sizeof(int2) * gent.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !gout.empty()) e = cudaMemcpy(go, gout.data(), sizeof(int) * gout.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !goff.empty()) e = cudaMemcpy(gf, goff.data(), sizeof(int4) * goff.size(), cudaMemcpyHostToDevice);
+    d->gmap = GhostMap{ge, go, gf};
+  }
   if (e == cudaSuccess) e = dalloc(sizeof(double) * 2, (void**)&d->d_rate);
   if (e == cudaSuccess) e = dalloc(sizeof(double) * 2, (void**)&d->d_dt);
   const long long nc = mesh->sh.ncell;
@@ -1494,7 +1512,7 @@ int gr_ghost_fill(gr_driver* d, double* const W[7], int32_t nw, double* const B[
   gr_mesh* m = d->mesh;
   if (m->nblocks == 0) return GR_OK;
   DeviceGuard g(d->device);
-  cudaError_t e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, W, nw, B, (cudaStream_t)stream);
+  cudaError_t e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, d->gmap, W, nw, B, (cudaStream_t)stream);
   return e == cudaSuccess ? GR_OK : cuda_fail(e, "gr_ghost_fill");
 }
 
@@ -1618,7 +1636,7 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
       for (int v = 0; v < nw; ++v) inW[v] = d->W[s % 2][v];
       for (int a = 0; a < 3; ++a) inB[a] = d->B[s % 2][a];
       if (chain32) {   // same-level ghosts of the FP64 buffers and their FP32 copies in one pass
-        e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, inW, nw, inB, st, d->W32[s % 2], d->B32[s % 2]);
+        e = launch_ghost_fill(m->d_blocks, m->nblocks, d->d_nbr, d->gmap, inW, nw, inB, st, d->W32[s % 2], d->B32[s % 2]);
         if (e != cudaSuccess) return cuda_fail(e, "gr_driver_step ghost fill");
       } else if ((r = driver_fill(d, inW, nw, inB, stream))) {
         return r;

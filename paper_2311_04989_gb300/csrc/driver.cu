@@ -10,6 +10,9 @@
 //   k_cfl_rate   max over interior cells and directions of max(|lambda-|, |lambda+|)/dx_d (the fast
 //                speeds of Sec. 2.2 at the cell state), warp-reduced, one atomic max per warp
 //   k_cfl_dt     dt = CFL / rate, left on the device for the stages to read
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 #include "physics.cuh"
 #include "stage_common.cuh"
@@ -21,11 +24,12 @@ struct GhostArgs {
   int nw;
   double* B[3];
   const int* nbr;   // 27 entries per block
+  GhostMap map;
   float* W32[6];    // optional FP32 copies of W[0..5] and B (the mixed path's reconstruction input): their
   float* B32[3];    // ghosts get the FP32 conversion of the copied FP64 value
 };
 
-__device__ __forceinline__ int nbr_slot(const int o[3]) { return (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1); }
+__host__ __device__ __forceinline__ int nbr_slot(const int o[3]) { return (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1); }
 
 // Ghost shell of a box: the elements of the full array (extent F[a] from -g) outside the owned box
 // (extent O[a] from 0), F[a] - O[a] = 2g.  Enumerated as the two z slabs (full x-y planes), then the
@@ -35,7 +39,7 @@ __host__ __device__ __forceinline__ int shell_count(const int F[3], const int O[
   return F[0] * F[1] * F[2] - O[0] * O[1] * O[2];
 }
 
-__device__ __forceinline__ void shell_decode(int e, const int F[3], const int O[3], int g, int p[3]) {
+static void shell_decode(int e, const int F[3], const int O[3], int g, int p[3]) {
   const int nz = (F[2] - O[2]) * F[1] * F[0];
   if (e < nz) {
     const int t = e / (F[1] * F[0]), r = e - t * F[1] * F[0];
@@ -63,51 +67,76 @@ __device__ __forceinline__ void shell_decode(int e, const int F[3], const int O[
 }
 
 // side of coordinate x of an axis with owned extent own: -1 below, 0 inside, +1 above
-__device__ __forceinline__ int side(int x, int own) { return x < 0 ? -1 : (x >= own ? 1 : 0); }
+static inline int side(int x, int own) { return x < 0 ? -1 : (x >= own ? 1 : 0); }
 
-// One CTA per (block, kind), kind 0 = cells, 1 + D = D-faces; its threads stride over the block's
-// ghost shell.  Neighbours have the block's own sizes (checked when the driver is made), so a source
-// element is the neighbour's base offset plus this block's index of the shifted coordinate: the 27
-// base offsets are staged in shared memory once, and each element costs one load and one store per
-// field, all independent.
-// source and destination offsets (within the pool) of ghost element e of the shell
-template <int D>
-__device__ __forceinline__ void ghost_pair(const DBlock& b, const long long* sbase, long long own, const int F[3],
-                                           const int O[3], int e, long long* dst, long long* src) {
-  int p[3], o[3], q[3];
-  shell_decode(e, F, O, b.g, p);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) o[d] = side(p[d], O[d]);
-  long long base = sbase[nbr_slot(o)];
-  if (base >= 0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = p[d] - o[d] * b.n[d];
-  } else {   // outflow: nearest owned element of this block
-    base = own;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = min(max(p[d], 0), O[d] - 1);
-  }
-  if constexpr (D < 0) {
-    *dst = own + cix(b, p[0], p[1], p[2]);
-    *src = base + cix(b, q[0], q[1], q[2]);
-  } else {
-    *dst = own + fix(b, D, p[0], p[1], p[2]);
-    *src = base + fix(b, D, q[0], q[1], q[2]);
-  }
-}
-
-// Each thread copies U elements per pass, all loads before all stores: sources are owned elements
-// and destinations ghosts, so they never alias, but the compiler cannot know that and would
-// otherwise wait for each store before the next load.
-template <int D>
-__device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sbase, const GhostArgs& a) {
-  constexpr int U = D < 0 ? 2 : 6;
-  int F[3], O[3];
-#pragma unroll
+// full (F) and owned (O) extents of element kind D (-1 cells, 0..2 faces) of a block
+__host__ __device__ __forceinline__ void shell_extents(const DBlock& b, int D, int F[3], int O[3]) {
   for (int d = 0; d < 3; ++d) {
     F[d] = b.N[d] + (d == D);
     O[d] = b.n[d] + (d == D);
   }
+}
+
+int build_ghost_map(const DBlock* hb, int nblocks, std::vector<int2>& ent, std::vector<int>& out,
+                    std::vector<int4>& off) {
+  ent.clear();
+  out.clear();
+  off.assign(nblocks, int4{0, 0, 0, 0});
+  std::vector<int> rep;   // first block of each distinct shape
+  for (int b = 0; b < nblocks; ++b) {
+    const DBlock& x = hb[b];
+    int found = -1;
+    for (size_t r = 0; r < rep.size() && found < 0; ++r) {
+      const DBlock& y = hb[rep[r]];
+      if (x.g == y.g && x.n[0] == y.n[0] && x.n[1] == y.n[1] && x.n[2] == y.n[2]) found = (int)r;
+    }
+    if (found >= 0) {
+      off[b] = off[rep[found]];
+      continue;
+    }
+    rep.push_back(b);
+    int o4[4];
+    for (int D = -1; D < 3; ++D) {
+      int F[3], O[3];
+      shell_extents(x, D, F, O);
+      if ((long long)F[0] * F[1] * F[2] >= kGhostMapMaxLocal) return -1;
+      o4[D + 1] = (int)ent.size();
+      const int cnt = shell_count(F, O);
+      for (int e = 0; e < cnt; ++e) {
+        int p[3], o[3], qn[3], qo[3];
+        shell_decode(e, F, O, x.g, p);
+        for (int d = 0; d < 3; ++d) {
+          o[d] = side(p[d], O[d]);
+          qn[d] = p[d] - o[d] * x.n[d];                // in the neighbour across o
+          qo[d] = std::min(std::max(p[d], 0), O[d] - 1);   // outflow: nearest owned element
+        }
+        const long long dst = D < 0 ? cix(x, p[0], p[1], p[2]) : fix(x, D, p[0], p[1], p[2]);
+        const long long srn = D < 0 ? cix(x, qn[0], qn[1], qn[2]) : fix(x, D, qn[0], qn[1], qn[2]);
+        const long long sro = D < 0 ? cix(x, qo[0], qo[1], qo[2]) : fix(x, D, qo[0], qo[1], qo[2]);
+        const unsigned packed = ((unsigned)nbr_slot(o) << 27) | (unsigned)srn;
+        ent.push_back(int2{(int)dst, (int)packed});
+        out.push_back((int)sro);
+      }
+    }
+    off[b] = int4{o4[0], o4[1], o4[2], o4[3]};
+  }
+  return 0;
+}
+
+// One CTA per (block, kind), kind 0 = cells, 1 + D = D-faces; its threads stride over the block's
+// ghost shell, each element's destination, neighbour slot and source offset read from the gather map
+// of the block's shape (shared by all blocks of that shape, so it stays in L2).  Neighbours have the
+// block's own sizes (checked when the driver is made), so a source element is the neighbour's base
+// offset (the 27 bases staged in shared memory) plus the mapped offset.  Each thread copies U elements
+// per pass, all loads before all stores: sources are owned elements and destinations ghosts, so they
+// never alias, but the compiler cannot know that and would otherwise wait for each store before the
+// next load.
+template <int D>
+__device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sbase, const GhostArgs& a,
+                                           const int2* __restrict__ ent, const int* __restrict__ outm) {
+  constexpr int U = D < 0 ? 2 : 6;
+  int F[3], O[3];
+  shell_extents(b, D, F, O);
   const int cnt = shell_count(F, O);
   const long long own = D < 0 ? b.cell : b.face[D < 0 ? 0 : D];
   for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kGhostTile) {
@@ -115,8 +144,14 @@ __device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sba
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kGhostTile;
-      if (e < cnt) ghost_pair<D>(b, sbase, own, F, O, e, dst + u, src + u);
-      else dst[u] = -1;
+      if (e < cnt) {
+        const int2 t = __ldg(ent + e);
+        const long long base = sbase[(unsigned)t.y >> 27];
+        dst[u] = own + t.x;
+        src[u] = base >= 0 ? base + (t.y & (int)(kGhostMapMaxLocal - 1)) : own + __ldg(outm + e);
+      } else {
+        dst[u] = -1;
+      }
     }
     if constexpr (D < 0) {
       double v[U][7];
@@ -164,10 +199,14 @@ __global__ void __launch_bounds__(kGhostTile) k_ghost(const DBlock* __restrict__
     sbase[threadIdx.x] = src < 0 ? -1 : (kind == 0 ? blocks[src].cell : blocks[src].face[kind - 1]);
   }
   __syncthreads();
-  if (kind == 0) ghost_body<-1>(b, sbase, a);
-  else if (kind == 1) ghost_body<0>(b, sbase, a);
-  else if (kind == 2) ghost_body<1>(b, sbase, a);
-  else ghost_body<2>(b, sbase, a);
+  const int4 o = __ldg(a.map.off + blk);
+  const int eo = kind == 0 ? o.x : (kind == 1 ? o.y : (kind == 2 ? o.z : o.w));
+  const int2* ent = a.map.ent + eo;
+  const int* outm = a.map.out + eo;
+  if (kind == 0) ghost_body<-1>(b, sbase, a, ent, outm);
+  else if (kind == 1) ghost_body<0>(b, sbase, a, ent, outm);
+  else if (kind == 2) ghost_body<1>(b, sbase, a, ent, outm);
+  else ghost_body<2>(b, sbase, a, ent, outm);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -236,9 +275,11 @@ __global__ void k_cfl_dt(const double* rate, double cfl, double* dt) {
   *dt = r > 0.0 ? cfl / r : 0.0;
 }
 
-cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
-                              double* const B[3], cudaStream_t st, float* const* W32, float* const* B32) {
+cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, const GhostMap& gm,
+                              double* const W[7], int nw, double* const B[3], cudaStream_t st,
+                              float* const* W32, float* const* B32) {
   GhostArgs a{};
+  a.map = gm;
   for (int v = 0; v < 7; ++v) a.W[v] = v < nw ? W[v] : nullptr;
   a.nw = nw;
   for (int d = 0; d < 3; ++d) a.B[d] = B[d];

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "grstage.h"
 
@@ -239,10 +240,26 @@ cudaError_t launch_adm(int precision, const DBlock* blocks, const Work* cw, int 
                        size_t smem, const MetricView& m, const double* const W[7], const double* const B[3],
                        const KParams& kp, int vc_order, void* const cv[10], double* const out[10], cudaStream_t st);
 constexpr int kGhostTile = 512;
+// Gather map of the same-level ghost fill, made once per distinct block shape (n, g) when the driver is
+// made: for element e of the ghost shell of a block of that shape and element kind (cells, x-, y-,
+// z-faces; shell order of shell_decode), ent[e] = {destination offset within the block's pool segment,
+// (neighbour slot << 27) | source offset within the neighbour's segment} and out[e] = the source offset
+// within the block itself when that neighbour is an outflow boundary.  off[block] = the entry offsets of
+// the block's shape for the four kinds.
+struct GhostMap {
+  const int2* ent;
+  const int* out;
+  const int4* off;
+};
+constexpr long long kGhostMapMaxLocal = 1ll << 27;   // local offsets must fit 27 bits
+// host: the map of a mesh's blocks (entries of equal shapes shared); 0, or -1 when a block's padded arrays
+// hold kGhostMapMaxLocal elements or more
+int build_ghost_map(const DBlock* hb, int nblocks, std::vector<int2>& ent, std::vector<int>& out,
+                    std::vector<int4>& off);
 // W32/B32 (optional): FP32 copies of W (up to 6 pools) and B whose ghosts get the converted copied values
-cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, double* const W[7], int nw,
-                              double* const B[3], cudaStream_t st, float* const* W32 = nullptr,
-                              float* const* B32 = nullptr);
+cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr, const GhostMap& gm,
+                              double* const W[7], int nw, double* const B[3], cudaStream_t st,
+                              float* const* W32 = nullptr, float* const* B32 = nullptr);
 cudaError_t launch_cfl_dt(const DBlock* blocks, const Work* wi, int nwi, const MetricView& m,
                           const double* const W[7], const double* const B[3], const KParams& kp, double cfl,
                           double* rate, double* dt, cudaStream_t st);

@@ -120,14 +120,14 @@ __device__ __forceinline__ void inv3(const R g[6], R det, R gi[6]) {
 // ------------------------------------------------------------------------------------------------
 // Layout helpers (ghost-padded, x fastest)
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ long long cix(const DBlock& b, int i, int j, int k) {
+__host__ __device__ __forceinline__ long long cix(const DBlock& b, int i, int j, int k) {
   return ((long long)(k + b.g) * b.N[1] + (j + b.g)) * b.N[0] + (i + b.g);
 }
-__device__ __forceinline__ long long fix(const DBlock& b, int d, int i, int j, int k) {
+__host__ __device__ __forceinline__ long long fix(const DBlock& b, int d, int i, int j, int k) {
   const int sx = b.N[0] + (d == 0), sy = b.N[1] + (d == 1);
   return ((long long)(k + b.g) * sy + (j + b.g)) * sx + (i + b.g);
 }
-__device__ __forceinline__ long long vix(const DBlock& b, int i, int j, int k) {
+__host__ __device__ __forceinline__ long long vix(const DBlock& b, int i, int j, int k) {
   return ((long long)(k + b.g) * (b.N[1] + 1) + (j + b.g)) * (b.N[0] + 1) + (i + b.g);
 }
 
@@ -763,6 +763,7 @@ template <class R>
 struct C2PVal {
   R x, rbar2, v2, iW, eps, f;
   R rho, p, lT;   // table: density (inside the table), pressure, log T at mu
+  R en, ed;       // c2p_master_fast: eps = en / ed, formed only where eps itself is needed
   bool vcap, eclamp;
 };
 
@@ -788,6 +789,36 @@ __device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R
   const R nuB = rdiv(ge * (R(1) + qm), R(1) + E.eps);
   const R nu = nuA > nuB ? nuA : nuB;
   E.f = mu - rdiv(R(1), nu + mu * E.rbar2);
+}
+
+// The same f(mu) for the ideal gas with two FP64 divisions instead of four (the mixed stage's
+// con2prim): eps = n/d with n = qm (1 + iW) + v^2, d = iW (1 + iW) > 0, so eps < 0 iff n < 0,
+// 1 + Gamma eps = G/d with G = d + Gamma n, 1 + eps = (d + n)/d, and
+//   nu_A = G iW / d,  nu_B = G (1 + qm) / (d + n),  nu_A > nu_B  iff  iW (d + n) > (1 + qm) d;
+// with nu = G P / Q for the larger one, f = mu - 1/(nu + mu rbar^2) = mu - Q / (G P + mu rbar^2 Q).
+// The same function as c2p_master up to rounding; eps itself (needed only at the root) is left as
+// E.en / E.ed.
+template <class R>
+__device__ __forceinline__ void c2p_master_fast(R gam, R vmax2, const C2PInv<R>& I, R mu, C2PVal<R>& E) {
+  E.x = rdiv(R(1), R(1) + mu * I.b2);
+  E.rbar2 = E.x * E.x * I.r2 + mu * E.x * (R(1) + E.x) * I.rb * I.rb;
+  const R qbar = I.q - R(0.5) * I.b2 - R(0.5) * mu * mu * E.x * E.x * (I.b2 * I.r2 - I.rb * I.rb);
+  E.v2 = mu * mu * E.rbar2;
+  E.vcap = E.v2 > vmax2;
+  if (E.vcap) E.v2 = vmax2;
+  E.iW = rsqrt_(R(1) - E.v2);
+  const R qm = qbar - mu * E.rbar2;
+  const R d = E.iW * (R(1) + E.iW);
+  R n = qm * (R(1) + E.iW) + E.v2;
+  E.eclamp = n < R(0);
+  if (E.eclamp) n = R(0);
+  E.en = n;
+  E.ed = d;
+  const R G = d + gam * n;
+  const R dn = d + n, q1 = R(1) + qm;
+  const bool a_wins = E.iW * dn > q1 * d;
+  const R P = a_wins ? E.iW : q1, Q = a_wins ? d : dn;
+  E.f = mu - rdiv(Q, G * P + mu * E.rbar2 * Q);
 }
 
 // The same master function with the tabulated EOS (Sec. 2.2.1, App. A): rho = D/W moved into the
@@ -836,10 +867,12 @@ __device__ __forceinline__ R c2p_aux(const C2PInv<R>& I, R h0sq, R mu) {
 }
 
 // Illinois on [a,b] (f(a) < 0 < f(b) or reverse).  Returns 0 (root), -1 (no sign change), -2 (cap).
+// *fresh (optional): whether the root is the point f was last evaluated at.
 template <class R, class Fn>
 __device__ __forceinline__ int illinois(Fn f, R a, R b, R fa, R fb, R tol, int max_iter, R* root, R* hi_out,
-                                        int* iters) {
+                                        int* iters, bool* fresh = nullptr) {
   *iters = 0;
+  if (fresh) *fresh = false;
   if (fa == R(0)) { *root = a; *hi_out = a; return 0; }
   if (fb == R(0)) { *root = b; *hi_out = b; return 0; }
   if ((fa < R(0)) == (fb < R(0))) return -1;
@@ -847,9 +880,14 @@ __device__ __forceinline__ int illinois(Fn f, R a, R b, R fa, R fb, R tol, int m
   for (int it = 1; it <= max_iter; ++it) {
     R c = rdiv(a * fb - b * fa, fb - fa);
     if (!(c > a && c < b)) c = R(0.5) * (a + b);
-    if (!(c > a && c < b)) { *root = c; *hi_out = b; *iters = it; return 0; }
+    if (!(c > a && c < b)) {
+      *root = c; *hi_out = b; *iters = it;
+      if (fresh) *fresh = false;   // c itself was not evaluated
+      return 0;
+    }
     const R fc = f(c);
     *iters = it;
+    if (fresh) *fresh = true;
     if (fc == R(0)) { *root = c; *hi_out = c; return 0; }
     if ((fc < R(0)) == (fa < R(0))) {
       a = c; fa = fc;
@@ -947,7 +985,12 @@ __device__ __forceinline__ void atm_cell(const C2PMet& M, const KParams& P, cons
 // guess: GR_GUESS_NONE (bracket (0, mu+]) or GR_GUESS_FP32 (an FP32 pre-solve proposes a bracket of
 // relative half-width 2e-5 around its root; it is used only if the FP64 master function changes
 // sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set) or GR_GUESS_MLP.
-template <int EOS>
+// FAST (the mixed stage): the upper end mu+ of the bracket from the auxiliary function in FP32 (its
+// tolerance is 1e-3; a bound that turns out too low is caught by the sign test and replaced by 1/h0),
+// and for the ideal gas the two-division form of the master function (c2p_master_fast).  The root is
+// still bracketed in FP64 to the same tolerance; only the bracket's upper end and the rounding of f
+// differ from the plain form.
+template <int EOS, bool FAST = false>
 __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, double q[6],
                                              const double Bd[3], double w[7], int* iters,
                                              C2PRecord* rec = nullptr) {
@@ -1014,9 +1057,11 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     C2PVal<double> E;
     int nevals = 0;   // FP64 master-function evaluations (reported through *iters)
     int kh = -1;      // temperature interval of the last evaluation (table)
+    bool fresh = false;   // E holds f's values at the root (the solve's last evaluation was there)
     auto fm = [&](double mu) {
       ++nevals;
-      if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
+      if constexpr (EOS == GR_EOS_IDEAL && FAST) c2p_master_fast<double>(gam, vmax2, I, mu, E);
+      else if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
       else c2p_master_tab<double>(P.t64, vmax2, I, mu, E, &kh);
       return E.f;
     };
@@ -1028,7 +1073,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       if (mu32 > 0.0) {
         const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), top);
         const double flo = fm(lo), fup = fm(up);
-        if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, &it_master);
+        if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, &it_master, &fresh);
       }
       if (r != 0) st |= GR_ST_GUESS_REJECTED;
     } else if (P.c2p_guess == GR_GUESS_MLP && P.mlp) {
@@ -1047,6 +1092,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
         if (f0 == 0.0) {
           root = m0;
           r = 0;
+          fresh = true;
         } else {
           const double dir = f0 < 0.0 ? 1.0 : -1.0;   // f < 0 below the root
           double step = dl;
@@ -1057,7 +1103,7 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
             if ((f1 < 0.0) != (f0 < 0.0) || f1 == 0.0) {
               const double a = fmin(m0, m1), bnd = fmax(m0, m1);
               const double fa = (a == m0) ? f0 : f1, fb = (a == m0) ? f1 : f0;
-              r = illinois<double>(fm, a, bnd, fa, fb, P.tol, P.max_iter, &root, &hi, &it_master);
+              r = illinois<double>(fm, a, bnd, fa, fb, P.tol, P.max_iter, &root, &hi, &it_master, &fresh);
               break;
             }
             m0 = m1;
@@ -1071,15 +1117,34 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
       // bracket (0, mu+], mu+ from the auxiliary function on (0, 1/h0]
       double mup = top;
       int it_aux;
-      const double f1 = c2p_aux<double>(I, h0sq, top);
-      if (f1 > 0.0) {
-        auto fa = [&](double mu) { return c2p_aux<double>(I, h0sq, mu); };
-        if (illinois<double>(fa, 0.0, top, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+      bool aux_done = false;
+      if constexpr (FAST) {
+        C2PInv<float> If;
+        If.D = d2f_rn(I.D); If.q = d2f_rn(I.q); If.r2 = d2f_rn(I.r2); If.b2 = d2f_rn(I.b2); If.rb = d2f_rn(I.rb);
+        If.ye = 0.f;
+        if (isfinite(If.r2) && isfinite(If.b2) && isfinite(If.rb * If.rb)) {
+          const float topf = EOS ? P.top_f : 1.f, h0sqf = EOS ? P.h0sq_f : 1.f;
+          const float f1 = c2p_aux<float>(If, h0sqf, topf);
+          float rootf, hif;
+          if (f1 > 0.f) {
+            auto fa = [&](float mu) { return c2p_aux<float>(If, h0sqf, mu); };
+            if (illinois<float>(fa, 0.f, topf, -1.f, f1, 1e-3f, P.max_iter, &rootf, &hif, &it_aux) == 0)
+              mup = fmin(f2d_exact(hif), top);
+          }
+          aux_done = true;
+        }
+      }
+      if (!aux_done) {
+        const double f1 = c2p_aux<double>(I, h0sq, top);
+        if (f1 > 0.0) {
+          auto fa = [&](double mu) { return c2p_aux<double>(I, h0sq, mu); };
+          if (illinois<double>(fa, 0.0, top, -1.0, f1, 1e-3, P.max_iter, &root, &hi, &it_aux) == 0) mup = hi;
+        }
       }
       const double f0 = fm(0.0);
       double fp = fm(mup);
       if ((f0 < 0.0) == (fp < 0.0) && mup < top) { mup = top; fp = fm(mup); }
-      r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, &it_master);
+      r = illinois<double>(fm, 0.0, mup, f0, fp, P.tol, P.max_iter, &root, &hi, &it_master, &fresh);
     }
     *iters = nevals;
     if (r != 0) {
@@ -1091,8 +1156,16 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
         rec->q = I.q; rec->r2 = I.r2; rec->b2 = I.b2; rec->rb = I.rb; rec->mu = mu; rec->D = D; rec->ye = ye;
         rec->solved = true;
       }
-      if constexpr (EOS == GR_EOS_IDEAL) c2p_master<double>(gam, vmax2, I, mu, E);
-      else c2p_master_tab<double>(P.t64, vmax2, I, mu, E, &kh);
+      // E at the root: the solve's last evaluation is usually there already (the ideal-gas master
+      // function is a pure function of mu, so the values are the ones a new evaluation would give)
+      if constexpr (EOS == GR_EOS_IDEAL && FAST) {
+        if (!fresh) c2p_master_fast<double>(gam, vmax2, I, mu, E);
+        E.eps = E.en / E.ed;
+      } else if constexpr (EOS == GR_EOS_IDEAL) {
+        if (!fresh) c2p_master<double>(gam, vmax2, I, mu, E);
+      } else {
+        c2p_master_tab<double>(P.t64, vmax2, I, mu, E, &kh);
+      }
       double vu[3];
       for (int i = 0; i < 3; ++i) vu[i] = mu * E.x * (ru[i] + mu * I.rb * bu[i]);
       if (E.vcap) {

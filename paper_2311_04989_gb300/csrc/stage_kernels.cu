@@ -458,7 +458,9 @@ __global__ void __launch_bounds__(kMaxTile, sizeof(R) == sizeof(float) ? 4 : 0) 
 // pattern of atmosphere and matter cells: thread t of the grid takes jobs t, t + grid size, ...
 // R = float (the mixed stage): the cell's U' is formed here first (update_all on the FP32 inputs);
 // R = double: U' is read from Uo (left there by k_update or by the caller of gr_con2prim).
-template <int EOS, class R = double>
+// FAST: con2prim_cell's mixed-stage form (FP32 bracket search, two-division master function); every
+// mixed stage uses it, the fused sweep's k_c2p (R = double) included, so that both paths agree bitwise.
+template <int EOS, class R = double, bool FAST = (sizeof(R) == sizeof(float))>
 __global__ void __maxnreg__(168) k_c2p(const DBlock* __restrict__ blocks,
                                                   const __grid_constant__ InView<R> in,
                                                   const __grid_constant__ InView<double> in64,
@@ -487,7 +489,7 @@ __global__ void __maxnreg__(168) k_c2p(const DBlock* __restrict__ blocks,
     C2PMet M;
     cell_gamma64(b, in64, i, j, k, M);
     int iters;
-    const int st = con2prim_cell<EOS>(M, kp, q, Bn, wn, &iters);
+    const int st = con2prim_cell<EOS, FAST>(M, kp, q, Bn, wn, &iters);
     write_cell<EOS>(s, c, q, wn, st);
     if (s.evals) s.evals[c] = iters;
   }
@@ -742,8 +744,8 @@ static cudaError_t stage_fused(const DBlock* blocks, int nblocks, const KLaunch 
   if (q.nwork) {
     KLaunch qq = q;
     qq.nwork = (q.nwork + q.threads - 1) / q.threads;
-    k_c2p<GR_EOS_IDEAL, double><<<stage_grid(k_c2p<GR_EOS_IDEAL, double>, qq, 0), q.threads, 0, st>>>(blocks, in64, in64,
-                                                                                                    s, ws, kp);
+    k_c2p<GR_EOS_IDEAL, double, true><<<stage_grid(k_c2p<GR_EOS_IDEAL, double, true>, qq, 0), q.threads, 0, st>>>(
+        blocks, in64, in64, s, ws, kp);
   }
   if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();

@@ -6,7 +6,7 @@ primitives are held by their backward error on regular solves (gpu_harness.backw
 and B' reproduce the GPU's U' through the oracle's prim2con within 1e-12) and forward on the cells a floor,
 clamp or the atmosphere set (closed forms), since on these workloads some are
 ill-conditioned functions of U' (cold gas where p is a small part of the energy, static stars whose
-velocities are rounding-sized): their forward errors are printed.
+velocities are rounding-sized); their forward errors are printed and held to the looser FW64 bounds.
 
 * the 1D magnetised shock tube (16^3, Gamma 5/3, PLM + HLLE): 10 RK2 steps at CFL 0.4 through the driver,
   FP64 against the oracle's driver after every step
@@ -77,9 +77,16 @@ def _block_out(pools, out, b):
     return dict(U=U, W=W, B=Bf, status=st)
 
 
+# Forward bounds of the FP64 primitives (compare()'s measures), beside the backward error: a few times
+# above the largest forward differences these workloads show (measured: rho 1.2e-15, p 6.8e-12 in the
+# stars' cold outer layers, u~ 9.1e-11 where a static star's velocities are rounding-sized), so that a
+# regression in W' cannot pass on the backward error alone.
+FW64 = {"W0": 1e-13, "W1": 5e-10, "W2": 5e-10, "W3": 5e-10, "W4": 5e-11}
+
+
 def _check64(got, ref, bi, P, label):
     """FP64 output of one block against the oracle's: U', B' forward, status exact, W' by backward
-    error; returns the largest number asserted on."""
+    error and forward within FW64; returns the largest number asserted on."""
     e = GH.compare([got], [ref], blocks=[bi])
     assert e.pop("status_mismatch") == 0, label
     fw = {k: v for k, v in e.items() if k.startswith("W")}
@@ -89,6 +96,8 @@ def _check64(got, ref, bi, P, label):
     print(f"{label}: U', B' max {max(cons.values()):.1e}; W' backward {be:.1e}, on policy cells {pe:.1e}; "
           f"W' forward " + ", ".join(f"{k} {v:.1e}" for k, v in sorted(fw.items())))
     assert max(cons.values()) < TOL64 and be < TOL64 and pe < TOL64, (label, cons, be, pe)
+    bad = {k: (v, FW64[k]) for k, v in fw.items() if k in FW64 and not v < FW64[k]}
+    assert not bad, (label, "W' forward", bad)
     return max(max(cons.values()), be, pe)
 
 
