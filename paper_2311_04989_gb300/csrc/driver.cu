@@ -123,76 +123,68 @@ int build_ghost_map(const DBlock* hb, int nblocks, std::vector<int2>& ent, std::
   return 0;
 }
 
-// One CTA per (block, kind), kind 0 = cells, 1 + D = D-faces; its threads stride over the block's
-// ghost shell, each element's destination, neighbour slot and source offset read from the gather map
-// of the block's shape (shared by all blocks of that shape, so it stays in L2).  Neighbours have the
-// block's own sizes (checked when the driver is made), so a source element is the neighbour's base
-// offset (the 27 bases staged in shared memory) plus the mapped offset.  Each thread copies U elements
-// per pass, all loads before all stores: sources are owned elements and destinations ghosts, so they
-// never alias, but the compiler cannot know that and would otherwise wait for each store before the
-// next load.
+// One CTA per (block, array): the nw cell fields, then the x-, y- and z-face fields, so that every CTA
+// copies one 8-byte array over its block's ghost shell (the same amount of work for all of them).  Each
+// element's destination, neighbour slot and source offset come from the gather map of the block's shape
+// (shared by all blocks of that shape, so it stays in L2).  Neighbours have the block's own sizes
+// (checked when the driver is made), so a source element is the neighbour's base offset (the 27 bases
+// staged in shared memory) plus the mapped offset.  Each thread copies kGhostU elements per pass, all
+// loads before all stores: sources are owned elements and destinations ghosts, so they never alias, but
+// the compiler cannot know that and would otherwise wait for each store before the next load.
+constexpr int kGhostU = 8;
+
 template <int D>
-__device__ __forceinline__ void ghost_body(const DBlock& b, const long long* sbase, const GhostArgs& a,
-                                           const int2* __restrict__ ent, const int* __restrict__ outm) {
-  constexpr int U = D < 0 ? 2 : 6;
+__device__ __forceinline__ void ghost_copy(const DBlock& b, const long long* sbase, const int2* __restrict__ ent,
+                                           const int* __restrict__ outm, const double* src_arr, double* dst_arr,
+                                           float* dst32) {
   int F[3], O[3];
   shell_extents(b, D, F, O);
   const int cnt = shell_count(F, O);
   const long long own = D < 0 ? b.cell : b.face[D < 0 ? 0 : D];
-  for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kGhostTile) {
-    long long dst[U], src[U];
+  constexpr int kStride = kGhostU * kGhostTile;
+  // the map entries of the next pass are loaded while this pass's copies are in flight
+  int2 t[kGhostU];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * kGhostTile;
-      if (e < cnt) {
-        const int2 t = __ldg(ent + e);
-        const long long base = sbase[(unsigned)t.y >> 27];
-        dst[u] = own + t.x;
-        src[u] = base >= 0 ? base + (t.y & (int)(kGhostMapMaxLocal - 1)) : own + __ldg(outm + e);
-      } else {
-        dst[u] = -1;
+  for (int u = 0; u < kGhostU; ++u) {
+    const int e = (int)threadIdx.x + u * kGhostTile;
+    t[u] = e < cnt ? __ldg(ent + e) : int2{-1, 0};
+  }
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += kStride) {
+    long long dst[kGhostU];
+    double v[kGhostU];
+#pragma unroll
+    for (int u = 0; u < kGhostU; ++u) {
+      dst[u] = -1;
+      if (t[u].x >= 0) {
+        const long long base = sbase[(unsigned)t[u].y >> 27];
+        const long long src = base >= 0 ? base + (t[u].y & (int)(kGhostMapMaxLocal - 1))
+                                        : own + __ldg(outm + e0 + u * kGhostTile);
+        dst[u] = own + t[u].x;
+        v[u] = src_arr[src];
       }
     }
-    if constexpr (D < 0) {
-      double v[U][7];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+    for (int u = 0; u < kGhostU; ++u) {
+      const int e = e0 + kStride + u * kGhostTile;
+      t[u] = e < cnt ? __ldg(ent + e) : int2{-1, 0};
+    }
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-          if (k < a.nw && dst[u] >= 0) v[u][k] = a.W[k][src[u]];
+    for (int u = 0; u < kGhostU; ++u)
+      if (dst[u] >= 0) dst_arr[dst[u]] = v[u];
+    if (dst32) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int k = 0; k < 7; ++k)
-          if (k < a.nw && dst[u] >= 0) a.W[k][dst[u]] = v[u][k];
-      if (a.W32[0]) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int k = 0; k < 6; ++k)
-            if (k < a.nw && dst[u] >= 0) a.W32[k][dst[u]] = d2f_rn(v[u][k]);
-      }
-    } else {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (dst[u] >= 0) v[u] = a.B[D][src[u]];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (dst[u] >= 0) a.B[D][dst[u]] = v[u];
-      if (a.B32[D]) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (dst[u] >= 0) a.B32[D][dst[u]] = d2f_rn(v[u]);
-      }
+      for (int u = 0; u < kGhostU; ++u)
+        if (dst[u] >= 0) dst32[dst[u]] = d2f_rn(v[u]);
     }
   }
 }
 
-__global__ void __launch_bounds__(kGhostTile) k_ghost(const DBlock* __restrict__ blocks,
+__global__ void __launch_bounds__(kGhostTile, 4) k_ghost(const DBlock* __restrict__ blocks,
                                                       const __grid_constant__ GhostArgs a) {
   __shared__ long long sbase[27];   // base offset of the source block per direction, -1: outflow
-  const int blk = blockIdx.x >> 2, kind = (int)(blockIdx.x & 3);
+  const int na = a.nw + 3;
+  const int blk = blockIdx.x / na, arr = (int)(blockIdx.x - blk * na);
+  const int kind = arr < a.nw ? 0 : arr - a.nw + 1;   // 0 cells, 1 + D: D-faces
   const DBlock b = blocks[blk];
   if (threadIdx.x < 27) {
     const int src = __ldg(a.nbr + 27 * blk + threadIdx.x);
@@ -203,10 +195,16 @@ __global__ void __launch_bounds__(kGhostTile) k_ghost(const DBlock* __restrict__
   const int eo = kind == 0 ? o.x : (kind == 1 ? o.y : (kind == 2 ? o.z : o.w));
   const int2* ent = a.map.ent + eo;
   const int* outm = a.map.out + eo;
-  if (kind == 0) ghost_body<-1>(b, sbase, a, ent, outm);
-  else if (kind == 1) ghost_body<0>(b, sbase, a, ent, outm);
-  else if (kind == 2) ghost_body<1>(b, sbase, a, ent, outm);
-  else ghost_body<2>(b, sbase, a, ent, outm);
+  if (kind == 0) {
+    float* w32 = arr < 6 ? a.W32[arr] : nullptr;   // no FP32 copy of T (table)
+    ghost_copy<-1>(b, sbase, ent, outm, a.W[arr], a.W[arr], w32);
+  } else if (kind == 1) {
+    ghost_copy<0>(b, sbase, ent, outm, a.B[0], a.B[0], a.B32[0]);
+  } else if (kind == 2) {
+    ghost_copy<1>(b, sbase, ent, outm, a.B[1], a.B[1], a.B32[1]);
+  } else {
+    ghost_copy<2>(b, sbase, ent, outm, a.B[2], a.B[2], a.B32[2]);
+  }
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -288,7 +286,7 @@ cudaError_t launch_ghost_fill(const DBlock* blocks, int nblocks, const int* nbr,
     for (int v = 0; v < 6; ++v) a.W32[v] = v < nw ? W32[v] : nullptr;
     for (int d = 0; d < 3; ++d) a.B32[d] = B32[d];
   }
-  if (nblocks) k_ghost<<<4 * nblocks, kGhostTile, 0, st>>>(blocks, a);
+  if (nblocks) k_ghost<<<(nw + 3) * nblocks, kGhostTile, 0, st>>>(blocks, a);
   return cudaGetLastError();
 }
 

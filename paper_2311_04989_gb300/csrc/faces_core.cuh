@@ -46,7 +46,7 @@ __device__ __forceinline__ void face_flux(const R* L, const R* Rr, const R met[1
   wl[5] = EOS ? L[NV - 1] : R(0);
   wr[5] = EOS ? Rr[NV - 1] : R(0);
   const R det = det3(met + 4);
-  const R sg = rsqrt_(det);
+  const R sg = sqrt_r(det);
   const R gdd = inv_dd(met + 4, D, det);
   R BL[3], BR[3];
   BL[D] = Bn; BR[D] = Bn;

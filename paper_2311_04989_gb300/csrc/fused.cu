@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kFT, 1) k_fused(const DBlock* __restrict__ blo
           float* g = sm + oG + fring(ve, 2) * 7 * kFG + j * kFM + i;
 #pragma unroll
           for (int c = 0; c < 6; ++c) g[c * kFG] = gam[c];
-          g[6 * kFG] = rsqrt_(det3(gam));
+          g[6 * kFG] = sqrt_r(det3(gam));
         }
       }
     }

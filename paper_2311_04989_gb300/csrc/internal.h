@@ -239,7 +239,7 @@ size_t adm_smem_bytes(const int n[3], int Z, int np, size_t elem);
 cudaError_t launch_adm(int precision, const DBlock* blocks, const Work* cw, int ncw, const Work* vw, int nvw,
                        size_t smem, const MetricView& m, const double* const W[7], const double* const B[3],
                        const KParams& kp, int vc_order, void* const cv[10], double* const out[10], cudaStream_t st);
-constexpr int kGhostTile = 512;
+constexpr int kGhostTile = 256;
 // Gather map of the same-level ghost fill, made once per distinct block shape (n, g) when the driver is
 // made: for element e of the ghost shell of a block of that shape and element kind (cells, x-, y-,
 // z-faces; shell order of shell_decode), ent[e] = {destination offset within the block's pool segment,

@@ -16,9 +16,16 @@ namespace grs {
 // ------------------------------------------------------------------------------------------------
 // small helpers
 // ------------------------------------------------------------------------------------------------
-template <class R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+// square root in precision R: the IEEE square root in FP64; in FP32 (the mixed path) the hardware's
+// approximate square root (PTX sqrt.approx.f32, relative error of the order of one FP32 ulp), a single
+// instruction instead of the correctly rounded sequence
+template <class R> __device__ __forceinline__ R sqrt_r(R x);
+template <> __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_r(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // a/b: IEEE division in FP64; the fast approximate FP32 division (2 ulp) on the mixed path
 template <class R> __device__ __forceinline__ R rdiv(R a, R b);
@@ -522,7 +529,7 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   const R ut[3] = {w[1], w[2], w[3]};
   R utl[3];
   lower3(g, ut, utl);
-  const R W = rsqrt_(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R W = sqrt_r(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
   const R iW = rdiv(R(1), W);
   const R ia = rdiv(R(1), alpha);
   const R isg = rdiv(R(1), sg);
@@ -571,7 +578,7 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   const R v2 = v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2];
   R disc = (R(1) - v2) * (gdd * (R(1) - v2 * c2) - v[d] * v[d] * (R(1) - c2));
   disc = disc > R(0) ? disc : R(0);
-  const R cr = rsqrt_(c2) * rsqrt_(disc);
+  const R cr = sqrt_r(c2) * sqrt_r(disc);
   const R iden = rdiv(R(1), R(1) - v2 * c2);
   const R vc = v[d] * (R(1) - c2);
   *lp = alpha * (vc + cr) * iden - beta[d];
@@ -615,7 +622,7 @@ __device__ __forceinline__ void cellmet_from(const R val[16], bool kzero, CellMe
     M.K[c] = kzero ? R(0) : val[10 + c];
   }
   M.det = det3(M.g);
-  M.sg = rsqrt_(M.det);
+  M.sg = sqrt_r(M.det);
   inv3(M.g, M.det, M.gi);
 }
 
@@ -634,7 +641,7 @@ __device__ __forceinline__ void cell_fluid(const CellMet<R>& M, const KParams& k
   #pragma unroll
   for (int i = 0; i < 3; ++i) f.ut[i] = w[1 + i];
   lower3(M.g, f.ut, f.utl);
-  f.W = rsqrt_(R(1) + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
+  f.W = sqrt_r(R(1) + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
   const R iW = rdiv(R(1), f.W), ia = rdiv(R(1), M.alpha), isg = rdiv(R(1), M.sg);
   #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -779,7 +786,7 @@ __device__ __forceinline__ void c2p_master(R gam, R vmax2, const C2PInv<R>& I, R
   E.v2 = mu * mu * E.rbar2;
   E.vcap = E.v2 > vmax2;
   if (E.vcap) E.v2 = vmax2;
-  E.iW = rsqrt_(R(1) - E.v2);
+  E.iW = sqrt_r(R(1) - E.v2);
   const R qm = qbar - mu * E.rbar2;
   E.eps = rdiv(qm * (R(1) + E.iW) + E.v2, E.iW * (R(1) + E.iW));
   E.eclamp = E.eps < R(0);
@@ -806,7 +813,7 @@ __device__ __forceinline__ void c2p_master_fast(R gam, R vmax2, const C2PInv<R>&
   E.v2 = mu * mu * E.rbar2;
   E.vcap = E.v2 > vmax2;
   if (E.vcap) E.v2 = vmax2;
-  E.iW = rsqrt_(R(1) - E.v2);
+  E.iW = sqrt_r(R(1) - E.v2);
   const R qm = qbar - mu * E.rbar2;
   const R d = E.iW * (R(1) + E.iW);
   R n = qm * (R(1) + E.iW) + E.v2;
@@ -834,7 +841,7 @@ __device__ __forceinline__ void c2p_master_tab(const TabView<R>& t, R vmax2, con
   E.v2 = mu * mu * E.rbar2;
   E.vcap = E.v2 > vmax2;
   if (E.vcap) E.v2 = vmax2;
-  E.iW = rsqrt_(R(1) - E.v2);
+  E.iW = sqrt_r(R(1) - E.v2);
   const R qm = qbar - mu * E.rbar2;
   E.eps = rdiv(qm * (R(1) + E.iW) + E.v2, E.iW * (R(1) + E.iW));
   E.rho = I.D * E.iW;
@@ -863,7 +870,7 @@ template <class R>
 __device__ __forceinline__ R c2p_aux(const C2PInv<R>& I, R h0sq, R mu) {
   const R x = rdiv(R(1), R(1) + mu * I.b2);
   const R rbar2 = x * x * I.r2 + mu * x * (R(1) + x) * I.rb * I.rb;
-  return mu * rsqrt_(h0sq + rbar2) - R(1);
+  return mu * sqrt_r(h0sq + rbar2) - R(1);
 }
 
 // Illinois on [a,b] (f(a) < 0 < f(b) or reverse).  Returns 0 (root), -1 (no sign change), -2 (cap).

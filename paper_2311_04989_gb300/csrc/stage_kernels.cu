@@ -72,7 +72,7 @@ template <class R>
 __device__ __forceinline__ void cellprep_cell(const DBlock& b, const InView<R>& in, const Workspace& ws, int i,
                                               int j, int k, const R val[10]) {
   const R* g6 = val + 4;
-  const R sg = rsqrt_(det3(g6));
+  const R sg = sqrt_r(det3(g6));
   R Bd[3];
   const long long f0 = b.face[0] + fix(b, 0, i, j, k), f1 = b.face[1] + fix(b, 1, i, j, k);
   const long long f2 = b.face[2] + fix(b, 2, i, j, k);
@@ -89,7 +89,7 @@ __device__ __forceinline__ void cellprep_cell(const DBlock& b, const InView<R>& 
   const R ut[3] = {in.W[1][c], in.W[2][c], in.W[3][c]};
   R utl[3];
   lower3(g6, ut, utl);
-  const R iW = rdiv(R(1), rsqrt_(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]));
+  const R iW = rdiv(R(1), sqrt_r(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]));
   const R ia = rdiv(R(1), val[0]);
   R vt[3];
 #pragma unroll
@@ -391,7 +391,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
     R gv[10];
     cell_metric<R>(b, in, in.order, i, j, k, 4, 10, gv, nullptr);
     const R* gam = gv + 4;
-    const R sg = rsqrt_(det3(gam));
+    const R sg = sqrt_r(det3(gam));
     q[0] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, 0, R(0));
     const double sg32 = to64(sg);
     if (!(isfinite(q[0]) && q[0] < kp.rho_thr * sg32)) return true;
