@@ -26,6 +26,11 @@ template <> __device__ __forceinline__ float sqrt_r(float x) {
   asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// the Lorentz factor W = sqrt(1 + u~^2), correctly rounded in both precisions: tau is formed as
+// (rho h + b^2) W^2 - rho W - ..., where the rest mass cancels, so an ulp of W costs an ulp of rho
+// against the much smaller tau
+template <class R> __device__ __forceinline__ R sqrt_w(R x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_w(float x) { return sqrtf(x); }
 
 // a/b: IEEE division in FP64; the fast approximate FP32 division (2 ulp) on the mixed path
 template <class R> __device__ __forceinline__ R rdiv(R a, R b);
@@ -529,7 +534,7 @@ __device__ __forceinline__ void face_state(int d, const R met[10], R sg, R gdd, 
   const R ut[3] = {w[1], w[2], w[3]};
   R utl[3];
   lower3(g, ut, utl);
-  const R W = sqrt_r(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R W = sqrt_w(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
   const R iW = rdiv(R(1), W);
   const R ia = rdiv(R(1), alpha);
   const R isg = rdiv(R(1), sg);
@@ -641,7 +646,7 @@ __device__ __forceinline__ void cell_fluid(const CellMet<R>& M, const KParams& k
   #pragma unroll
   for (int i = 0; i < 3; ++i) f.ut[i] = w[1 + i];
   lower3(M.g, f.ut, f.utl);
-  f.W = sqrt_r(R(1) + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
+  f.W = sqrt_w(R(1) + f.ut[0] * f.utl[0] + f.ut[1] * f.utl[1] + f.ut[2] * f.utl[2]);
   const R iW = rdiv(R(1), f.W), ia = rdiv(R(1), M.alpha), isg = rdiv(R(1), M.sg);
   #pragma unroll
   for (int i = 0; i < 3; ++i) {

@@ -89,7 +89,7 @@ __device__ __forceinline__ void cellprep_cell(const DBlock& b, const InView<R>& 
   const R ut[3] = {in.W[1][c], in.W[2][c], in.W[3][c]};
   R utl[3];
   lower3(g6, ut, utl);
-  const R iW = rdiv(R(1), sqrt_r(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]));
+  const R iW = rdiv(R(1), sqrt_w(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]));
   const R ia = rdiv(R(1), val[0]);
   R vt[3];
 #pragma unroll
