@@ -31,11 +31,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GRMHD cell-updates/s per RK stage"
 UNIT = "cell-updates/s"
+GUESS_NAMES = {0: "none", 1: "fp32"}
 WORKLOAD = "two-star full-stage throughput: 4096 blocks of 16^3 (ng=3), WENOZ+HLLE, CT, con2prim"
-# con2prim bracket proposal of the timed mixed stage: none.  The FP32 pre-solve and the learned bracket
-# (both timed in the con2prim_guess / con2prim_table sections) cut FP64 master-function evaluations but
-# cost more than they save on GB300 (measured on both workloads), so the headline solves without a guess.
-MIXED_GUESS = 0   # GR_GUESS_NONE
+# con2prim bracket proposal of the timed mixed stage (--guess; the con2prim_guess / con2prim_table
+# sections time every proposal on their own workloads)
+MIXED_GUESS = 3   # GR_GUESS_AUTO, set from --guess in main()
 FP64_NOMINAL_TFLOPS = 1.25      # nominal dense FP64 of the GB300 (context only; the roofline uses the measured rate)
 
 
@@ -96,8 +96,9 @@ def parse():
                     help="time only this smaller configuration (GPU, --precision, --no-autotune honoured) and "
                          "print its figures (no headline line); for profiling one configuration's kernels")
     ap.add_argument("--config-blocks", type=int, default=1024, help="blocks of the AMR-like batch (C3)")
-    ap.add_argument("--config-guess", default="none", choices=["none", "fp32"],
-                    help="con2prim guess of the mixed stage in the smaller configurations")
+    ap.add_argument("--guess", default="auto", choices=["auto", "none", "fp32"],
+                    help="con2prim bracket proposal of the mixed stage (headline and smaller configurations); "
+                         "auto: the autotuner times none and the FP32 pre-solve on the workload and keeps the faster")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -478,8 +479,7 @@ def config_timings(a, ctx, dev, G, configs):
             p = G.gr_params_default(recon=cp["recon"], gamma_ad=cp["gamma"], rho_atm=cp["rho_atm"],
                                     p_atm=100.0 * cp["rho_atm"] ** cp["gamma"], tol=1e-10,
                                     precision=G.GR_PREC_MIXED if mixed else G.GR_PREC_FP64,
-                                    c2p_guess=({"none": G.GR_GUESS_NONE, "fp32": G.GR_GUESS_FP32}[a.config_guess]
-                                               if mixed else G.GR_GUESS_NONE),
+                                    c2p_guess=MIXED_GUESS if mixed else G.GR_GUESS_NONE,
                                     atm_band=G.GR_MIXED_ATM_BAND if mixed else 1e-12)
             G.gr_prim2con(mesh, metric, list(W), B, list(U), p, stream)
             Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
@@ -506,7 +506,8 @@ def config_timings(a, ctx, dev, G, configs):
                          "kernel_ms": dict(zip(G.KERNEL_NAMES, [k / max(1, nst) for k in kms])),
                          "path": G.PATH_NAMES[G.gr_mesh_get_path(mesh)] if mixed else "separate kernels"}
             if mixed:
-                row[prec]["c2p_guess"] = a.config_guess
+                row[prec]["c2p_guess"] = GUESS_NAMES[G.gr_mesh_get_guess(mesh, G.GR_PREC_MIXED, 0)] \
+                    if a.guess == "auto" else a.guess
                 row[prec]["guess_rejected"] = int(((stv & 64) != 0).sum().item())
             del Uo, Wo, Bo, st, state
         if "fp64" in row and "mixed" in row:
@@ -653,7 +654,9 @@ def con2prim_table_workload(a, ctx, dev, G, I):
 
 
 def main():
+    global MIXED_GUESS
     a = parse()
+    MIXED_GUESS = {"none": 0, "fp32": 1, "auto": 3}[a.guess]   # GR_GUESS_NONE, GR_GUESS_FP32, GR_GUESS_AUTO
     if a.impl == "reference":
         run_reference(a)
         return
@@ -785,6 +788,9 @@ def main():
         ms, kms, clocks, shapes = timed(prec, copies=name == "mixed")
         results[name] = dict(ms=ms, kernel_ms=kms, clocks=clocks,
                              shapes=dict(zip(G.KERNEL_NAMES[1:], shapes)) if shapes else None)
+        if prec == G.GR_PREC_MIXED:   # the bracket proposal the stage ran with (auto: the autotuner's choice)
+            results[name]["c2p_guess"] = GUESS_NAMES[G.gr_mesh_get_guess(mesh, prec, 0)] if a.guess == "auto" \
+                else a.guess
         snap[name] = (Wo.clone(), [x.clone() for x in Bo], Uo.clone(), st.clone())
         stv = st.to(torch.int32)
         results[name]["status"] = {"atmosphere": int(((stv & 1) != 0).sum().item()),
@@ -1150,6 +1156,8 @@ def main():
                       "fp32_copies": ("mixed stage in its steady state: reads FP32 copies of W and B (as the previous "
                                       "stage writes them) and of the static metric (made once), writes FP64 outputs "
                                       "and the FP32 copies of W' and B' for the next stage"),
+                      "c2p_guess": (results[head].get("c2p_guess", a.guess) + (" (autotuned)" if a.guess == "auto" else ""))
+                                   if head == "mixed" else "none",
                       "atmosphere_fraction": (results[head]["status"]["atmosphere"] / cells),
                       "input_gen_s": round(t_gen, 1)},
            "roofline": roofline(head, peaks), "clocks": results[head]["clocks"], "alu_peaks": peaks,

@@ -66,8 +66,11 @@ enum { GR_EOS_IDEAL = 0, GR_EOS_TABLE = 1 };            /* Sec. 2.2.1 */
 #define GR_ST_GUESS_REJECTED 0x40 /* a proposed root bracket showed no sign change: full bracket used */
 
 /* Source of a proposed con2prim root bracket (the FP64 solve always verifies it by a sign change):
- * none, an FP32 pre-solve, or the learned bracket of a small network (gr_mlp_*). */
-enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1, GR_GUESS_MLP = 2 };
+ * none, an FP32 pre-solve (the bracket narrowed in FP32 to 1e-4 of its upper end, then widened by 4e-6),
+ * the learned bracket of a small network (gr_mlp_*), or GR_GUESS_AUTO: the mesh's choice between none and
+ * the FP32 pre-solve for the call's precision and EOS, made by gr_autotune by timing the stage with each
+ * (none until the mesh is tuned; gr_mesh_get_guess reads it). */
+enum { GR_GUESS_NONE = 0, GR_GUESS_FP32 = 1, GR_GUESS_MLP = 2, GR_GUESS_AUTO = 3 };
 
 /* Atmosphere band (gr_params.atm_band) for the mixed path: its atmosphere test compares D' with the
  * threshold times an FP32 sqrt(gamma) (relative error ~1e-7), so a band of 1e-6 classifies the cells at
@@ -251,6 +254,9 @@ int gr_mesh_set_shapes(gr_mesh* mesh, int32_t precision, int32_t eos, const gr_s
 enum { GR_PATH_SEPARATE = 0, GR_PATH_FUSED = 1, GR_PATH_TILED_FACES = 2 };
 int gr_mesh_set_path(gr_mesh* mesh, int32_t path);
 int gr_mesh_get_path(const gr_mesh* mesh);
+/* The bracket proposal GR_GUESS_AUTO stands for on this mesh (GR_GUESS_NONE or GR_GUESS_FP32) for a
+ * precision and EOS; -1 for a NULL mesh or a bad precision / EOS. */
+int gr_mesh_get_guess(const gr_mesh* mesh, int32_t precision, int32_t eos);
 
 /* ---- one stage on host-resident pools ----------------------------------------------------------------
  * gr_host_stage: the stage of gr_stage on a mesh whose pools live in host memory.  metric and state hold

@@ -131,6 +131,8 @@ struct gr_mesh {
   bool fused_ok = false;
   bool tiles_ok = false;
   int path = GR_PATH_SEPARATE;
+  // what GR_GUESS_AUTO stands for per (precision, EOS): set by gr_autotune
+  int guess[2][2] = {{GR_GUESS_NONE, GR_GUESS_NONE}, {GR_GUESS_NONE, GR_GUESS_NONE}};
   FaceTile* d_ftiles = nullptr;
   int nftiles = 0;
   int nint = 0;   // interior cells of all blocks
@@ -471,7 +473,8 @@ static int check_params(const gr_params* p) {
   if (p->emf != GR_EMF_UPWIND && p->emf != GR_EMF_MEAN) return fail(GR_EINVAL, "bad emf");
   if (p->ceiling != GR_CEIL_CLAMP && p->ceiling != GR_CEIL_ATMOSPHERE) return fail(GR_EINVAL, "bad ceiling");
   if (p->max_iter < 1 || p->max_iter > 10000) return fail(GR_EINVAL, "max_iter out of range");
-  if (p->c2p_guess != GR_GUESS_NONE && p->c2p_guess != GR_GUESS_FP32 && p->c2p_guess != GR_GUESS_MLP)
+  if (p->c2p_guess != GR_GUESS_NONE && p->c2p_guess != GR_GUESS_FP32 && p->c2p_guess != GR_GUESS_MLP &&
+      p->c2p_guess != GR_GUESS_AUTO)
     return fail(GR_EINVAL, "bad c2p_guess");
   if (p->c2p_guess == GR_GUESS_MLP && (!p->mlp || (((uintptr_t)p->mlp) & 15u)))
     return fail(GR_EINVAL, "GR_GUESS_MLP needs a 16-byte aligned device parameter vector in params.mlp");
@@ -488,6 +491,15 @@ static int check_params(const gr_params* p) {
   return GR_OK;
 }
 
+
+static KParams kparams(const gr_params* p, double dt);
+
+// kparams with GR_GUESS_AUTO replaced by the mesh's choice for the call's precision and EOS
+static KParams kparams_m(const gr_mesh* m, const gr_params* p, double dt) {
+  KParams k = kparams(p, dt);
+  if (p->c2p_guess == GR_GUESS_AUTO) k.c2p_guess = m->guess[p->precision][p->eos];
+  return k;
+}
 
 static KParams kparams(const gr_params* p, double dt) {
   KParams k{};
@@ -880,6 +892,7 @@ int gr_host_stage(gr_mesh* mesh, const gr_metric* metric, const gr_state* state,
     }
     sd.status = h->status + c0;
     std::memcpy(sm->shapes, mesh->shapes, sizeof(mesh->shapes));
+    std::memcpy(sm->guess, mesh->guess, sizeof(mesh->guess));
     sm->path = mesh->path;
     if ((r = stage_impl(sm, &md, &sd, dt, params, h->st[1], false))) return r;
     e = cudaEventRecord(h->ev_out[k], h->st[1]);
@@ -1000,7 +1013,7 @@ static int stage_impl(gr_mesh* mesh, const gr_metric* metric, const gr_state* st
   int nf = 0;
   Workspace ws;
   stage_variant(mesh, params, mv, mesh->path, &nf, &ws);
-  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kparams(params, dt),
+  cudaError_t e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kparams_m(mesh, params, dt),
                                (cudaStream_t)stream, ev, true, nf);
   if (e != cudaSuccess) return cuda_fail(e, "gr_stage launch");
   return GR_OK;
@@ -1048,7 +1061,7 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
   if (mesh->nblocks == 0) return GR_OK;
   DeviceGuard g(mesh->ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const KParams kp = kparams(params, dt);
+  KParams kp = kparams_m(mesh, params, dt);
   // candidates: CTA size x work-list order x persistent grid, the same for all five kernels in one
   // run; each kernel's time is read from its own events
   std::vector<gr_shape> cand;
@@ -1120,7 +1133,43 @@ int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, d
     if (e != cudaSuccess) return cuda_fail(e, "gr_autotune (stage paths)");
     mesh->path = best_path;
   }
+  // GR_GUESS_AUTO: the whole stage (chosen shapes and path) with no bracket proposal and with the FP32
+  // pre-solve; the faster stands for AUTO on this mesh
+  if (params->c2p_guess == GR_GUESS_AUTO) {
+    KLaunch kl[SK_N];
+    stage_launches(mesh, best, kl);
+    int nf = 0;
+    Workspace ws;
+    stage_variant(mesh, params, mv, mesh->path, &nf, &ws);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    float best_t = -1.f;
+    int best_guess = GR_GUESS_NONE;
+    for (int gs : {GR_GUESS_NONE, GR_GUESS_FP32}) {
+      if (e != cudaSuccess) break;
+      kp.c2p_guess = gs;
+      e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kp, st, nullptr, true, nf);
+      if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+      for (int rp = 0; rp < reps && e == cudaSuccess; ++rp)
+        e = launch_stage(params->precision, mesh->d_blocks, kl, mv, s, ws, mesh->sh, kp, st, nullptr, true, nf);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float tm = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&tm, t0, t1);
+      if (e == cudaSuccess && (best_t < 0.f || tm < best_t)) { best_t = tm; best_guess = gs; }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e != cudaSuccess) return cuda_fail(e, "gr_autotune (bracket proposal)");
+    mesh->guess[params->precision][params->eos] = best_guess;
+  }
   return GR_OK;
+}
+
+int gr_mesh_get_guess(const gr_mesh* mesh, int32_t precision, int32_t eos) {
+  if (!mesh || precision < 0 || precision > 1 || eos < 0 || eos > 1) return -1;
+  return mesh->guess[precision][eos];
 }
 
 int gr_prim2con(gr_mesh* mesh, const gr_metric* metric, const double* const W[7], const double* const B[3],
@@ -1370,7 +1419,7 @@ int gr_con2prim(gr_mesh* mesh, const gr_metric* metric, double* const U[6], cons
   if (mesh->nblocks == 0) return GR_OK;
   DeviceGuard g(mesh->ctx->device);
   cudaError_t e = launch_con2prim(mesh->d_blocks, mesh->d_work[R_INTERIOR], mesh->nwork[R_INTERIOR], mesh->nint,
-                                  mv, U, B, W, status, evals, mesh->ws, kparams(params, 0.0), (cudaStream_t)stream);
+                                  mv, U, B, W, status, evals, mesh->ws, kparams_m(mesh, params, 0.0), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gr_con2prim launch");
   return GR_OK;
 }
@@ -1623,7 +1672,7 @@ static int driver_step_impl(gr_driver* d, const gr_metric* metric, double* const
     if ((r = stage_prepare(m, metric, &state, 0.0, &ps, mv, sv))) return r;
     KLaunch kl[SK_N];
     stage_launches(m, m->shapes[params->precision][params->eos], kl);
-    KParams kp = kparams(&ps, 0.0);
+    KParams kp = kparams_m(m, &ps, 0.0);
     kp.dt_dev = d->d_dt;
     // the stages of a step share the metric: its FP32 shadow (mixed path) is made by the first one
     int nf = 0;

@@ -916,34 +916,57 @@ __device__ __forceinline__ int illinois(Fn f, R a, R b, R fa, R fb, R tol, int m
   return -2;
 }
 
-// FP32 pre-solve of the master root: returns mu32 > 0, or 0 when it did not converge
+// FP32 pre-solve: the bracket (0, mu+] of the master root narrowed by Illinois steps in FP32 until its
+// width is below 1e-4 of its upper end (at most 12 steps; FP32 evaluations of f carry rounding noise of
+// ~1e-7 of their terms, so a tighter FP32 tolerance would only spend steps on noise).  Returns false when
+// the FP32 invariants are not finite or f shows no sign change; else [*lo, *hi] with f32(lo) <= 0 <=
+// f32(hi), which the FP64 solve widens slightly and verifies by the signs of the FP64 f.
 template <int EOS>
-__device__ __forceinline__ float c2p_presolve32(const KParams& P, const C2PInv<double>& I64) {
+__device__ __forceinline__ bool c2p_presolve32(const KParams& P, const C2PInv<double>& I64, float* lo, float* hi) {
   C2PInv<float> I;
-  I.D = (float)I64.D; I.q = (float)I64.q; I.r2 = (float)I64.r2; I.b2 = (float)I64.b2; I.rb = (float)I64.rb;
-  I.ye = (float)I64.ye;
-  if (!(I.D > 0.f) || !isfinite(I.q) || !isfinite(I.r2) || !isfinite(I.b2)) return 0.f;
+  I.D = d2f_rn(I64.D); I.q = d2f_rn(I64.q); I.r2 = d2f_rn(I64.r2); I.b2 = d2f_rn(I64.b2); I.rb = d2f_rn(I64.rb);
+  I.ye = d2f_rn(I64.ye);
+  if (!(I.D > 0.f) || !isfinite(I.q) || !isfinite(I.r2) || !isfinite(I.b2) || !isfinite(I.rb * I.rb)) return false;
   const float gam = P.gamma_f, vmax2 = P.vmax2_f;
   const float top = EOS ? P.top_f : 1.f, h0sq = EOS ? P.h0sq_f : 1.f;
-  float mup = top, root, hi;
+  float mup = top, root, hiv;
   int it;
   const float f1 = c2p_aux<float>(I, h0sq, top);
   if (f1 > 0.f) {
     auto fa = [&](float mu) { return c2p_aux<float>(I, h0sq, mu); };
-    if (illinois<float>(fa, 0.f, top, -1.f, f1, 1e-3f, 40, &root, &hi, &it) == 0) mup = hi;
+    if (illinois<float>(fa, 0.f, top, -1.f, f1, 1e-3f, 40, &root, &hiv, &it) == 0) mup = hiv;
   }
   C2PVal<float> E;
   int kh = -1;   // temperature interval of the last evaluation (table)
   auto fm = [&](float mu) {
-    if constexpr (EOS == GR_EOS_IDEAL) c2p_master<float>(gam, vmax2, I, mu, E);
+    if constexpr (EOS == GR_EOS_IDEAL) c2p_master_fast<float>(gam, vmax2, I, mu, E);
     else c2p_master_tab<float>(P.t32, vmax2, I, mu, E, &kh);
     return E.f;
   };
-  const float f0 = fm(0.f);
-  float fp = fm(mup);
-  if ((f0 < 0.f) == (fp < 0.f) && mup < top) { mup = top; fp = fm(mup); }
-  if (illinois<float>(fm, 0.f, mup, f0, fp, 1e-6f, 60, &root, &hi, &it) != 0) return 0.f;
-  return root;
+  float a = 0.f, b = mup;
+  float fa = fm(a), fb = fm(b);
+  if (!(fb >= 0.f) && mup < top) { b = top; fb = fm(b); }
+  if (!(fa < 0.f) || !(fb >= 0.f)) return false;
+  int side = 0;
+  for (int k = 0; k < 12 && b - a > 1e-4f * b; ++k) {
+    float c = __fdividef(a * fb - b * fa, fb - fa);
+    if (!(c > a && c < b)) c = 0.5f * (a + b);
+    if (!(c > a && c < b)) break;
+    const float fc = fm(c);
+    if (fc == 0.f) { a = c; b = c; break; }
+    if (fc < 0.f) {
+      a = c; fa = fc;
+      if (side == -1) fb *= 0.5f;
+      side = -1;
+    } else {
+      b = c; fb = fc;
+      if (side == +1) fa *= 0.5f;
+      side = +1;
+    }
+  }
+  *lo = a;
+  *hi = b;
+  return true;
 }
 
 // Invariants and root of a bracketed solve (training samples for the learned bracket)
@@ -1081,9 +1104,10 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     int r = -1;
     int it_master = 0;
     if (P.c2p_guess == GR_GUESS_FP32) {
-      const double mu32 = (double)c2p_presolve32<EOS>(P, I);
-      if (mu32 > 0.0) {
-        const double lo = mu32 * (1.0 - 2e-5), up = fmin(mu32 * (1.0 + 2e-5), top);
+      float lo32, hi32;
+      if (c2p_presolve32<EOS>(P, I, &lo32, &hi32)) {
+        // the FP32 bracket widened by 4e-6 of its ends (a few FP32 roundings of f near the root)
+        const double lo = f2d_exact(lo32) * (1.0 - 4e-6), up = fmin(f2d_exact(hi32) * (1.0 + 4e-6), top);
         const double flo = fm(lo), fup = fm(up);
         if (flo <= 0.0 && fup >= 0.0) r = illinois<double>(fm, lo, up, flo, fup, P.tol, P.max_iter, &root, &hi, &it_master, &fresh);
       }

@@ -25,7 +25,7 @@ GR_EOS_IDEAL, GR_EOS_TABLE = 0, 1
 GR_ST_ATM_THRESHOLD, GR_ST_FAILED, GR_ST_W_CLAMPED = 0x01, 0x02, 0x04
 GR_ST_TAU_FLOOR, GR_ST_BD_LIMIT, GR_ST_EOS_CLAMP = 0x08, 0x10, 0x20
 GR_ST_GUESS_REJECTED = 0x40
-GR_GUESS_NONE, GR_GUESS_FP32, GR_GUESS_MLP = 0, 1, 2
+GR_GUESS_NONE, GR_GUESS_FP32, GR_GUESS_MLP, GR_GUESS_AUTO = 0, 1, 2, 3
 
 # every symbol include/grstage.h declares
 EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default", "gr_context_create",
@@ -37,7 +37,7 @@ EXPORTS = ["gr_strerror", "gr_last_error", "gr_abi_version", "gr_params_default"
            "gr_mesh_get_shapes", "gr_mesh_set_shapes", "gr_driver_create", "gr_driver_destroy", "gr_ghost_fill",
            "gr_cfl_dt", "gr_driver_step", "gr_driver_capture", "gr_driver_dt", "gr_driver_dt_device",
            "gr_adm_sources", "gr_mesh_set_levels", "gr_restrict", "gr_prolong", "gr_host_stage", "gr_cast_f32",
-           "gr_peak_alu", "gr_mesh_set_path", "gr_mesh_get_path"]
+           "gr_peak_alu", "gr_mesh_set_path", "gr_mesh_get_path", "gr_mesh_get_guess"]
 GR_ABI_VERSION = 3
 GR_MLP_NPARAM = 4689
 GR_MLP_NIN = 6
@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH):
     L.gr_cast_f32.argtypes = [vp, vp, C.c_int64, vp]
     L.gr_mesh_set_path.argtypes = [vp, i32]
     L.gr_mesh_get_path.argtypes = [vp]
+    L.gr_mesh_get_guess.argtypes = [vp, i32, i32]
     L.gr_peak_alu.argtypes = [i32, i32, i32, C.c_int64, vp, C.POINTER(C.c_double), vp]
     L.gr_diag_noalloc.argtypes = [C.POINTER(gr_block), i32, C.c_void_p * 5, C.c_void_p * 3,
                                   C.POINTER(C.c_double), vp]
@@ -311,6 +312,11 @@ def gr_mesh_set_path(mesh, path: int):
 
 def gr_mesh_get_path(mesh) -> int:
     return int(load().gr_mesh_get_path(mesh))
+
+
+def gr_mesh_get_guess(mesh, precision: int, eos: int = 0) -> int:
+    """The bracket proposal GR_GUESS_AUTO stands for on this mesh (set by gr_autotune)."""
+    return int(load().gr_mesh_get_guess(mesh, int(precision), int(eos)))
 
 
 def gr_peak_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream=None) -> float:

@@ -432,3 +432,44 @@ def test_autotune_and_shape_arguments():
         assert G.gr_mesh_get_shapes(mesh, G.GR_PREC_FP64) == [(128, 0, 0)] * 6   # other precision untouched
     finally:
         G.gr_mesh_destroy(mesh)
+
+
+def test_autotuned_bracket_proposal_is_one_of_the_two_and_gives_its_stage():
+    """GR_GUESS_AUTO: gr_autotune times the stage with no proposal and with the FP32 pre-solve and keeps the
+    faster for the mesh (none before tuning); a stage with AUTO then equals, bitwise, the stage run with the
+    chosen proposal explicitly."""
+    import torch
+    blocks = [I.random_block(n=s, g=3, seed=120 + k, rho_range=(1e-14, 1e-3)) for k, s in
+              enumerate([(16, 16, 16), (12, 8, 10)])]
+    P = O.Params(gamma_ad=2.0, rho_atm=1e-12, tol=1e-10)
+    pools = GH.Pools(blocks)
+    mesh = G.gr_mesh_create(GH.ctx(), pools.L.descriptors())
+    try:
+        assert G.gr_mesh_get_guess(mesh, G.GR_PREC_MIXED, 0) == G.GR_GUESS_NONE
+        assert G.gr_mesh_get_guess(mesh, 5, 0) == -1
+        U = pools.cells([H.cons_from_prims(b, P) for b in blocks], 5)
+        W, B, M = pools.cells([b.W for b in blocks], 5), pools.faces([b.B for b in blocks]), pools.verts(
+            [b.metric for b in blocks])
+        metric = G.metric_struct(M)
+        dt = 0.1 * min(blocks[0].dx)
+
+        def run(guess, tune=False):
+            Uo, Wo, Bo = U.clone(), W.clone(), [x.clone() for x in B]
+            st = torch.zeros(pools.L.ncell, dtype=torch.uint8, device="cuda")
+            state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+            gp = GH.gr_params_from(GH.mixed_params(P), G.GR_PREC_MIXED, guess)
+            if tune:
+                G.gr_autotune(mesh, metric, state, dt, gp, 2)
+            G.gr_stage(mesh, metric, state, dt, gp)
+            torch.cuda.synchronize()
+            return [t.cpu().numpy() for t in (Uo, Wo, st)] + [b.cpu().numpy() for b in Bo]
+
+        auto = run(G.GR_GUESS_AUTO, tune=True)
+        chosen = G.gr_mesh_get_guess(mesh, G.GR_PREC_MIXED, 0)
+        assert chosen in (G.GR_GUESS_NONE, G.GR_GUESS_FP32)
+        assert G.gr_mesh_get_guess(mesh, G.GR_PREC_FP64, 0) == G.GR_GUESS_NONE   # other precision untouched
+        explicit = run(chosen)
+        for a, b in zip(auto, explicit):
+            assert np.array_equal(a, b)
+    finally:
+        G.gr_mesh_destroy(mesh)
