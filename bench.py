@@ -460,7 +460,8 @@ def config_timings(a, ctx, dev, G, configs):
     """Stage throughput of the smaller configurations on the GPU, FP64 and mixed (or the one --precision
     names), autotuned launch shapes unless --no-autotune, a step = one gr_stage over all blocks of the
     configuration, inputs resident (C1 and C2 fit in L2, so theirs are L2-warm figures; C3's inputs,
-    several GB, do not)."""
+    several GB, do not); the mixed stage in its steady state, as for the headline (FP32 copies of W, B and
+    the metric in, of W' and B' out)."""
     import torch
     out = {}
     stream = torch.cuda.current_stream()
@@ -485,17 +486,29 @@ def config_timings(a, ctx, dev, G, configs):
             Uo, Wo, Bo = torch.zeros_like(U), torch.zeros_like(W), [torch.zeros_like(x) for x in B]
             st = torch.zeros(L.ncell, dtype=torch.uint8, device=dev)
             state = G.state_struct(U, U, B, B, W, Uo, Bo, Wo, st)
+            mt = metric
+            if mixed:   # the steady state, as for the headline: FP32 copies of the inputs in, of W' and B' out
+                def f32(x):
+                    y = torch.empty(x.shape, dtype=torch.float32, device=dev)
+                    G.gr_cast_f32(x.contiguous(), y, stream)
+                    return y
+                M32 = f32(M)
+                mt = G.metric_struct(M, metric32=M32)
+                W32, B32 = f32(W), [f32(x) for x in B]
+                G.set_fp32_copies(state, W32=W32, B32=B32, Wo32=torch.empty_like(W32),
+                                  Bo32=[torch.empty_like(x) for x in B32])
+            metric_run = mt
             if not a.no_autotune:
-                G.gr_autotune(mesh, metric, state, dt, p, 1, stream)
+                G.gr_autotune(mesh, metric_run, state, dt, p, 1, stream)
             for _ in range(a.warmup):
-                G.gr_stage(mesh, metric, state, dt, p, stream)
+                G.gr_stage(mesh, metric_run, state, dt, p, stream)
             steps = max(a.steps, 10)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             G.gr_profile_begin(mesh, steps)
             e0.record(stream)
             for _ in range(steps):
-                G.gr_stage(mesh, metric, state, dt, p, stream)
+                G.gr_stage(mesh, metric_run, state, dt, p, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             kms, nst = G.gr_profile_end(mesh)
