@@ -694,7 +694,12 @@ static int host_stage_setup(gr_mesh* m, int nbatch) {
   } else {
     m->hs = new HostStage();
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&m->hs->st[i], cudaStreamNonBlocking);
+    // the transfer streams (0: in, 2: out) at the highest priority the device offers, so that their
+    // transfer kernels are scheduled ahead of the waiting CTAs of another batch's stage (stream 1)
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithPriority(&m->hs->st[i], cudaStreamNonBlocking, i == 1 ? lo : hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hs->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hs->ev_end, cudaEventDisableTiming);
     if (e != cudaSuccess) {
