@@ -39,6 +39,10 @@ template <> __device__ __forceinline__ float rdiv(float a, float b) { return __f
 
 template <class R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 
+// whether x is finite, from the exponent bits of its high word (integer operations only: on GB300 an
+// FP64 comparison is an instruction of the narrow FP64 pipe)
+__device__ __forceinline__ bool finite64(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+
 // Precision conversions without the FP64 pipe (on GB300 an F2F conversion is an FP64-pipe
 // instruction, ~1/64 of the FP32 rate), in integer arithmetic on the IEEE-754 encodings.
 // FP64 -> FP32: round to nearest, ties to even, with gradual underflow (float subnormals) and
@@ -1017,9 +1021,9 @@ __device__ __forceinline__ void atm_cell(const C2PMet& M, const KParams& P, cons
 
 // Full con2prim of one cell.  q: densitised conserved (in/out; q[5] = D Y_e with a table), Bd:
 // densitised cell field, w: primitives out (w[5], w[6] = Y_e, T with a table).
-// guess: GR_GUESS_NONE (bracket (0, mu+]) or GR_GUESS_FP32 (an FP32 pre-solve proposes a bracket of
-// relative half-width 2e-5 around its root; it is used only if the FP64 master function changes
-// sign across it, else the full bracket is used and GR_ST_GUESS_REJECTED is set) or GR_GUESS_MLP.
+// guess: GR_GUESS_NONE (bracket (0, mu+]), GR_GUESS_FP32 (c2p_presolve32's FP32 bracket widened by 4e-6
+// of its ends; it is used only if the FP64 master function changes sign across it, else the full bracket
+// is used and GR_ST_GUESS_REJECTED is set) or GR_GUESS_MLP (GR_GUESS_AUTO is resolved on the host).
 // FAST (the mixed stage): the upper end mu+ of the bracket from the auxiliary function in FP32 (its
 // tolerance is 1e-3; a bound that turns out too low is caught by the sign test and replaced by 1/h0),
 // and for the ideal gas the two-division form of the master function (c2p_master_fast).  The root is

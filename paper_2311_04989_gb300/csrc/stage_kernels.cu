@@ -394,7 +394,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
     const R sg = sqrt_r(det3(gam));
     q[0] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, 0, R(0));
     const double sg32 = to64(sg);
-    if (!(isfinite(q[0]) && q[0] < kp.rho_thr * sg32)) return true;
+    if (!(finite64(q[0]) && q[0] < kp.rho_thr * sg32)) return true;
     // atmosphere: failed instead if any other variable's update is not finite
     bool finite = true;
 #pragma unroll
@@ -404,7 +404,7 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
       const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
       const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
       const R t = a0[1] - a0[0] + a1[b.N[0]] - a1[0] + a2[(long long)b.N[0] * b.N[1]] - a2[0];
-      finite = finite && isfinite(t) && isfinite(s.U[v][c]);
+      finite = finite && isfinite(t) && finite64(s.U[v][c]);
     }
     mixed_atm_reset<R, EOS>(b, s, kp, i, j, k, c, gam, sg, finite);
     return false;
