@@ -195,8 +195,8 @@ __device__ __forceinline__ float fused_edge(const float* Fa1, const float* Fa0, 
 // CT of one face (ct_body's operations): curl = idx1 dE2 - idx2 dE1, B' = g1 B - beta dt curl (+ g0 B0)
 __device__ __forceinline__ void fused_ct(const StateView& s, const KParams& kp, int D, long long f, double idx1,
                                          double idx2, float E2hi, float E2lo, float E1hi, float E1lo) {
-  const double dE2 = to64(E2hi) - to64(E2lo);
-  const double dE1 = to64(E1hi) - to64(E1lo);
+  const double dE2 = diff64(E2hi, E2lo);
+  const double dE1 = diff64(E1hi, E1lo);
   const double curl = fma(idx1, dE2, -(idx2 * dE1));
   const double B = s.B[D][f];
   double Bn = fma(-stage_bdt(kp), curl, (kp.rk_form & RK_G1) ? kp.rk_g1 * B : B);

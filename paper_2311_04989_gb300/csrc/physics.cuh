@@ -88,6 +88,21 @@ __device__ __forceinline__ double f2d_exact(float f) {
 template <class R> __device__ __forceinline__ double to64(R x);
 template <> __device__ __forceinline__ double to64(double x) { return x; }
 template <> __device__ __forceinline__ double to64(float x) { return f2d_exact(x); }
+
+// a - b in FP64.  For two FP32 values the difference is exact in FP64; it is formed in FP32 when it is
+// exact there too (Knuth's two-sum of a and -b has a zero error term, as for values within a factor 2
+// of each other by Sterbenz's lemma) and widened by integer operations, else by an FP64 subtraction:
+// the same value either way, mostly without the narrow FP64 pipe.
+template <class R> __device__ __forceinline__ double diff64(R a, R b);
+template <> __device__ __forceinline__ double diff64(double a, double b) { return a - b; }
+template <> __device__ __forceinline__ double diff64(float a, float b) {
+  const float s = __fsub_rn(a, b);
+  const float bp = __fsub_rn(s, a);               // the part of s that came from -b
+  const float ap = __fsub_rn(s, bp);              // the part of s that came from a
+  const float err = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(__fsub_rn(0.f, b), bp));
+  if (err == 0.f && isfinite(s)) return f2d_exact(s);
+  return f2d_exact(a) - f2d_exact(b);
+}
 template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 template <class R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 

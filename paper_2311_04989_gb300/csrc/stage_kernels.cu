@@ -295,8 +295,8 @@ __device__ __forceinline__ void ct_body(const Work& w, const DBlock& b, const St
   // ~1/64 of FP32, so the operation count is kept minimal: curl = idx1 dE2 - idx2 dE1 by one
   // multiply and one FMA, then B' = g1 B - beta dt curl by one FMA, with the RK form (RKF) fixed at
   // compile time so that g1 = 1 and g0 = 0 cost no FP64 instruction
-  const double dE2 = to64(E2[v0 + vs1]) - to64(E2[v0]);
-  const double dE1 = to64(E1[v0 + vs2]) - to64(E1[v0]);
+  const double dE2 = diff64(E2[v0 + vs1], E2[v0]);
+  const double dE1 = diff64(E1[v0 + vs2], E1[v0]);
   const double curl = fma(b.idx[t1], dE2, -(b.idx[t2] * dE1));
   const long long f = b.face[D] + fix(b, D, p[0], p[1], p[2]);
   const double B = s.B[D][f];

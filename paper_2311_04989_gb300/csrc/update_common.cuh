@@ -48,9 +48,9 @@ __device__ __forceinline__ double accumulate_vals(const DBlock& b, const StateVi
   const double bdt = stage_bdt(kp);
   const double U = s.U[v][c];
   double u = fma(bdt, to64(src), (kp.rk_form & RK_G1) ? kp.rk_g1 * U : U);
-  u -= (bdt * b.idx[0]) * (to64(x1) - to64(x0));
-  u -= (bdt * b.idx[1]) * (to64(y1) - to64(y0));
-  u -= (bdt * b.idx[2]) * (to64(z1) - to64(z0));
+  u -= (bdt * b.idx[0]) * diff64(x1, x0);
+  u -= (bdt * b.idx[1]) * diff64(y1, y0);
+  u -= (bdt * b.idx[2]) * diff64(z1, z0);
   if (kp.rk_form & RK_G0) u += kp.rk_g0 * s.U0[v][c];
   return u;
 }
