@@ -230,8 +230,11 @@ typedef struct {
 /* Autotuner (project-written; the paper has no counterpart): runs the stage on this mesh and state with
  * every shape (3 tiles x 2 orders x 2 grids), reps timed runs each after one warm-up, times each kernel
  * with CUDA events on `stream`, and keeps per kernel the fastest shape for (params->precision,
- * params->eos); later gr_stage and gr_graph_capture calls use it.  Writes the stage outputs.
- * best_ms (may be NULL) receives the mean time of each kernel's chosen shape.  Synchronises the stream. */
+ * params->eos); later gr_stage and gr_graph_capture calls use it.  Then it times the whole stage through
+ * every path that applies (gr_mesh_set_path) and keeps the fastest, and, when params->c2p_guess is
+ * GR_GUESS_AUTO, times it with no bracket proposal and with the FP32 pre-solve and keeps the faster
+ * (gr_mesh_get_guess).  Writes the stage outputs.  best_ms (may be NULL) receives the mean time of each
+ * kernel's chosen shape.  Synchronises the stream. */
 int gr_autotune(gr_mesh* mesh, const gr_metric* metric, const gr_state* state, double dt, const gr_params* params,
                 int32_t reps, void* stream, double best_ms[GR_NSTAGE_KERNELS]);
 /* Shapes in use for (precision, eos); defaults {128, 0, 0}.  set validates every entry (GR_EINVAL). */
