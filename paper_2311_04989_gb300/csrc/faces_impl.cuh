@@ -64,10 +64,12 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * ye_up;
 }
 
-// FP32: at most 85 registers (three 256-thread CTAs per SM); the packed reconstruction would otherwise
-// take ~94 and the lost occupancy costs more than the few spilled words (measured)
+// FP32: at most 72 registers, so that 14 CTAs of 64 threads (the autotuned shape) fit on an SM: 28
+// warps instead of 24 at the ~80 the kernel would take, for 28 spilled bytes (measured on the two-star
+// workload: 3.60 ms at 80 registers, 3.47 ms at 72, 3.55 ms at 68); with a table, whose face physics
+// holds more, 80.  FP64: 168, about what the compiler takes for it unconstrained (166)
 template <class R, int EOS, int METHOD>
-__global__ void __launch_bounds__(kMaxTile, sizeof(R) == sizeof(float) ? 3 : 0) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
+__global__ void __maxnreg__(sizeof(R) == sizeof(float) ? (EOS == GR_EOS_TABLE ? 80 : 72) : 168) k_faces(const DBlock* __restrict__ blocks, const Work* __restrict__ work,
                                                     int nwork, const __grid_constant__ InView<R> in,
                                                     const __grid_constant__ Workspace ws,
                                                     const __grid_constant__ KParams kp) {
