@@ -138,6 +138,16 @@ __device__ __forceinline__ R inv_dd(const R g[6], int d, R det) {
 
 // full inverse
 template <class R>
+__device__ __forceinline__ void inv3_id(const R g[6], R id, R gi[6]) {
+  gi[0] = (g[3] * g[5] - g[4] * g[4]) * id;
+  gi[1] = (g[2] * g[4] - g[1] * g[5]) * id;
+  gi[2] = (g[1] * g[4] - g[2] * g[3]) * id;
+  gi[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gi[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gi[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+}
+
+template <class R>
 __device__ __forceinline__ void inv3(const R g[6], R det, R gi[6]) {
   const R id = rdiv(R(1), det);
   gi[0] = (g[3] * g[5] - g[4] * g[4]) * id;
@@ -773,12 +783,21 @@ __device__ __forceinline__ void cell_sources(const CellMet<R>& M, const CellFlui
 // formed only for cells that are solved
 struct C2PMet {
   double g[6], sg, det;
+  double isg;   // 1/sqrt(gamma), formed only by the FAST form
 };
 
+// FAST (the mixed stage's con2prim): sqrt(gamma) and its inverse from one reciprocal square root,
+// sg = det rsqrt(det), in place of a square root and a division
+template <bool FAST = false>
 __device__ __forceinline__ void c2pmet_from(const double g6[6], C2PMet& M) {
   for (int c = 0; c < 6; ++c) M.g[c] = g6[c];
   M.det = det3(M.g);
-  M.sg = sqrt(M.det);
+  if constexpr (FAST) {
+    M.isg = rsqrt(M.det);
+    M.sg = M.det * M.isg;
+  } else {
+    M.sg = sqrt(M.det);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1070,7 +1089,8 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
   else if (q[0] < rho_thr * M.sg) { st |= GR_ST_ATM_THRESHOLD; atm = true; }   // D~ < rho_thr
   double isg = 0.0;
   if (!atm) {
-    isg = 1.0 / M.sg;
+    if constexpr (FAST) isg = M.isg;
+    else isg = 1.0 / M.sg;
     double D = q[0] * isg, tau = q[4] * isg, S[3], Bu[3];
     for (int i = 0; i < 3; ++i) {
       S[i] = q[1 + i] * isg;
@@ -1090,14 +1110,21 @@ __device__ __forceinline__ int con2prim_cell(const C2PMet& M, const KParams& P, 
     const double tau_min = D * eps_min + 0.5 * BB;
     if (tau < tau_min) { tau = tau_min; st |= GR_ST_TAU_FLOOR; qmod = true; }
     double gi[6];
-    inv3(M.g, M.det, gi);
+    if constexpr (FAST) inv3_id(M.g, isg * isg, gi);   // 1/det = (1/sqrt(gamma))^2
+    else inv3(M.g, M.det, gi);
     C2PInv<double> I;
     I.D = D;
     I.ye = ye;
-    const double iD = 1.0 / D;
+    double iD, isD;
+    if constexpr (FAST) {   // 1/sqrt(D) from one reciprocal square root, 1/D its square
+      isD = rsqrt(D);
+      iD = isD * isD;
+    } else {
+      iD = 1.0 / D;
+      isD = sqrt(iD);
+    }
     I.q = tau * iD;
     double rl[3], ru[3], bu[3];
-    const double isD = sqrt(iD);
     for (int i = 0; i < 3; ++i) { rl[i] = S[i] * iD; bu[i] = Bu[i] * isD; }
     ru[0] = gi[0] * rl[0] + gi[1] * rl[1] + gi[2] * rl[2];
     ru[1] = gi[1] * rl[0] + gi[3] * rl[1] + gi[4] * rl[2];

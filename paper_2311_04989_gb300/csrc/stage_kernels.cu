@@ -334,12 +334,13 @@ __global__ void __launch_bounds__(kMaxTile) k_ct(const DBlock* __restrict__ bloc
 // ------------------------------------------------------------------------------------------------
 // k_update<R>: U' (sources in R, FP64 accumulation) and FP64 con2prim on interior cells
 // ------------------------------------------------------------------------------------------------
-// FP64 gamma_ij at a cell centre (con2prim's metric)
+// FP64 gamma_ij at a cell centre (con2prim's metric; FAST: c2pmet_from's form for the mixed stage)
+template <bool FAST = false>
 __device__ __forceinline__ void cell_gamma64(const DBlock& b, const InView<double>& m, int i, int j, int k,
                                              C2PMet& M) {
   double val[10];
   cell_metric<double>(b, m, m.order, i, j, k, 4, 10, val, nullptr);
-  c2pmet_from(val + 4, M);
+  c2pmet_from<FAST>(val + 4, M);
 }
 
 // Conserved variable v of interior cell (i, j, k) after the stage from the workspace's face fluxes
@@ -487,7 +488,7 @@ __global__ void __maxnreg__(168) k_c2p(const DBlock* __restrict__ blocks,
     }
     cell_field(b, s.Bo, i, j, k, Bn);
     C2PMet M;
-    cell_gamma64(b, in64, i, j, k, M);
+    cell_gamma64<FAST>(b, in64, i, j, k, M);
     int iters;
     const int st = con2prim_cell<EOS, FAST>(M, kp, q, Bn, wn, &iters);
     write_cell<EOS>(s, c, q, wn, st);
