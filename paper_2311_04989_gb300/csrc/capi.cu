@@ -454,6 +454,9 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   }
   if (e == cudaSuccess) e = dalloc(sizeof(int2) * std::max<long long>(1, nint), (void**)&m->ws.jobs);
   if (e == cudaSuccess) e = dalloc(sizeof(int) * 4, (void**)&m->ws.njobs);
+  if (e == cudaSuccess) e = dalloc(std::max(1, nblocks), (void**)&m->ws.fbad);
+  if (e == cudaSuccess) e = cudaMemset(m->ws.fbad, 1, std::max(1, nblocks));
+  m->ws.nfbad = nblocks;
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
     std::string msg = std::string("gr_mesh_create: ") + cudaGetErrorString(e);

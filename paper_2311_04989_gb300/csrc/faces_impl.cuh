@@ -62,10 +62,15 @@ __device__ __forceinline__ void face_body(const Work& w, const DBlock& b, const 
   for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
   // D Y_e: the D equation times Y_e (Sec. 2.2.1), Y_e taken from the upwind state of the mass flux
   if constexpr (EOS == GR_EOS_TABLE) out[7 * ws.fstride[D] + o] = F[0] * ye_up;
+  if constexpr (sizeof(R) == sizeof(float)) {   // the block's flux flag (NaN and inf fail the test too)
+    R a = fabs(F[1]) + fabs(F[2]) + fabs(F[3]) + fabs(F[4]);
+    if constexpr (EOS == GR_EOS_TABLE) a += fabs(F[0] * ye_up);
+    if (!(a < kFluxSafe)) ws.fbad[w.block] = 1;
+  }
 }
 
 // FP32: at most 72 registers, so that 14 CTAs of 64 threads (the autotuned shape) fit on an SM: 28
-// warps instead of 24 at the ~80 the kernel would take, for 28 spilled bytes (measured on the two-star
+// warps instead of 24 at the ~80 the kernel would take, for 16-44 spilled bytes (measured on the two-star
 // workload: 3.60 ms at 80 registers, 3.47 ms at 72, 3.55 ms at 68); with a table, whose face physics
 // holds more, 80.  FP64: 168, about what the compiler takes for it unconstrained (166)
 template <class R, int EOS, int METHOD>

@@ -74,7 +74,7 @@ __device__ __forceinline__ void tile_metric_plane(float* dst, const InView<float
 
 template <int METHOD, int D>
 __device__ __forceinline__ void tile_face(const float* sm, const DBlock& b, const InView<float>& in, const Workspace& ws,
-                                          const KParams& kp, int j0, int i, int j, int p) {
+                                          const KParams& kp, uint8_t* bad, int j0, int i, int j, int p) {
   float st[7][6];
   const int r = j - j0 + 3;   // stored row of cell row j
   const float* bz = sm + tBz + tring(p, 2) * kTP;
@@ -123,6 +123,8 @@ __device__ __forceinline__ void tile_face(const float* sm, const DBlock& b, cons
   const long long o = b.wface[D] + fi;
 #pragma unroll
   for (int v = 0; v < 7; ++v) out[v * ws.fstride[D] + o] = F[v];
+  // the block's flux flag (NaN and inf fail the test too)
+  if (!(fabsf(F[1]) + fabsf(F[2]) + fabsf(F[3]) + fabsf(F[4]) < kFluxSafe)) *bad = 1;
 }
 
 template <int METHOD>
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kTT, 3) k_faces_tile(const DBlock* __restrict_
   extern __shared__ __align__(16) float sm[];
   const FaceTile tl = tiles[blockIdx.x];
   const DBlock b = blocks[tl.block];
+  uint8_t* bad = ws.fbad + tl.block;
   const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
   const int j0 = tl.j0, j1 = tl.j1;
   const int rows = j1 - j0 + 6, vrows = j1 - j0 + 3;
@@ -160,15 +163,15 @@ __global__ void __launch_bounds__(kTT, 3) k_faces_tile(const DBlock* __restrict_
     for (int q = threadIdx.x; q < nx + ny + nz; q += kTT) {
       if (q < nx) {
         const int i = q % (n0 + 1), j = jlo + q / (n0 + 1);
-        tile_face<METHOD, 0>(sm, b, in, ws, kp, j0, i, j, pf);
+        tile_face<METHOD, 0>(sm, b, in, ws, kp, bad, j0, i, j, pf);
       } else if (q < nx + ny) {
         const int e = q - nx;
         const int i = e % (n0 + 2) - 1, j = j0 + e / (n0 + 2);
-        tile_face<METHOD, 1>(sm, b, in, ws, kp, j0, i, j, pf);
+        tile_face<METHOD, 1>(sm, b, in, ws, kp, bad, j0, i, j, pf);
       } else {
         const int e = q - nx - ny;
         const int i = e % (n0 + 2) - 1, j = jlo + e / (n0 + 2);
-        tile_face<METHOD, 2>(sm, b, in, ws, kp, j0, i, j, t);
+        tile_face<METHOD, 2>(sm, b, in, ws, kp, bad, j0, i, j, t);
       }
     }
     __syncthreads();

@@ -137,7 +137,16 @@ struct Workspace {
   int2* jobs;
   const FaceTile* ftiles;  // tiles of k_faces_tile when the stage computes its fluxes with it, else nftiles 0
   int nftiles;
+  // mixed path, one byte per block: cleared before the face fluxes, set to 1 by the face kernels when a
+  // flux of S_j, tau or D Y_e of the block is not finite or has |F| summed over them >= kFluxSafe (and set
+  // for every block on a refined mesh, whose coarse fluxes the level fix rewrites).  A clear byte lets the
+  // atmosphere test skip those fluxes: any six of them then sum to a finite FP32 value.
+  uint8_t* fbad;
+  int nfbad;
 };
+// Bound on |F_S1| + |F_S2| + |F_S3| + |F_tau| (+ |F_DYe|) of one face below which six such fluxes of
+// one variable, each smaller, add and subtract to a finite FP32 value (6 x 4e37 < 3.4e38)
+constexpr float kFluxSafe = 4e37f;
 
 // Device view of an EOS table (Sec. 2.2.1) in precision R: node arrays of log p, log e, c_s^2, node
 // (ir, iT, iy) at (iy * n[1] + iT) * n[0] + ir; uniform axes log rho, log T, Y_e.

@@ -396,16 +396,22 @@ __device__ __forceinline__ bool update_cell(const Work& w, const DBlock& b, cons
     q[0] = accumulate_cell<R>(b, s, ws, kp, i, j, k, c, 0, R(0));
     const double sg32 = to64(sg);
     if (!(finite64(q[0]) && q[0] < kp.rho_thr * sg32)) return true;
-    // atmosphere: failed instead if any other variable's update is not finite
+    // atmosphere: failed instead if any other variable's update is not finite.  The flux divergence of
+    // those variables is finite for certain when the face kernel left the block's flag clear, so their
+    // fluxes are read only in a flagged block
     bool finite = true;
+    const bool fchk = ws.fbad[w.block] != 0;
 #pragma unroll
     for (int v = 1; v < NQ; ++v) {
-      const int cv = v < 5 ? v : 7;
-      const R* a0 = reinterpret_cast<const R*>(ws.flux[0]) + cv * ws.fstride[0] + b.wface[0] + fix(b, 0, i, j, k);
-      const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
-      const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
-      const R t = a0[1] - a0[0] + a1[b.N[0]] - a1[0] + a2[(long long)b.N[0] * b.N[1]] - a2[0];
-      finite = finite && isfinite(t) && finite64(s.U[v][c]);
+      if (fchk) {
+        const int cv = v < 5 ? v : 7;
+        const R* a0 = reinterpret_cast<const R*>(ws.flux[0]) + cv * ws.fstride[0] + b.wface[0] + fix(b, 0, i, j, k);
+        const R* a1 = reinterpret_cast<const R*>(ws.flux[1]) + cv * ws.fstride[1] + b.wface[1] + fix(b, 1, i, j, k);
+        const R* a2 = reinterpret_cast<const R*>(ws.flux[2]) + cv * ws.fstride[2] + b.wface[2] + fix(b, 2, i, j, k);
+        const R t = a0[1] - a0[0] + a1[b.N[0]] - a1[0] + a2[(long long)b.N[0] * b.N[1]] - a2[0];
+        finite = finite && isfinite(t);
+      }
+      finite = finite && finite64(s.U[v][c]);
     }
     mixed_atm_reset<R, EOS>(b, s, kp, i, j, k, c, gam, sg, finite);
     return false;
@@ -765,6 +771,10 @@ static cudaError_t stage_impl(const DBlock* blocks, const KLaunch kl[SK_N], cons
   }
   if (ev) cudaEventRecord(ev[2], st);
   const KLaunch& f = kl[SK_FACES];
+  if constexpr (sizeof(R) == sizeof(float)) {   // the per-block flux flags: set for all on a refined mesh
+    const cudaError_t eb = cudaMemsetAsync(ws.fbad, ws.nlvl ? 1 : 0, ws.nfbad, st);
+    if (eb != cudaSuccess) return eb;
+  }
   if constexpr (sizeof(R) == sizeof(float) && EOS == GR_EOS_IDEAL) {
     if (ws.nftiles > 0 && in.order == 2) {   // the tiled face sweep (the host checked that every block qualifies)
       const cudaError_t e = launch_faces_tile(blocks, ws.ftiles, ws.nftiles, in, ws, kp, st);

@@ -88,6 +88,41 @@ def test_fused_sweep_across_a_star_surface_bitwise(emf):
         _same(sep, _run(blocks, P, path, dt)[0])
 
 
+def _same_nan(a, b):
+    """Bitwise equality that takes NaN for NaN (the positions must match)."""
+    import torch
+    for x, y in zip(a, b):
+        if x.is_floating_point():
+            mx, my = torch.isnan(x), torch.isnan(y)
+            assert torch.equal(mx, my), int((mx != my).sum())
+            assert torch.equal(x[~mx], y[~my]), (x[~mx] - y[~my]).abs().max()
+        else:
+            assert torch.equal(x, y), int((x != y).sum())
+
+
+@pytest.mark.parametrize("face_b", [3e18, 3e19])
+def test_paths_agree_bitwise_beside_an_overflowing_field(face_b):
+    """One x-face in the atmosphere corner of a star block carries a field so large that the FP32 momentum
+    and energy fluxes about it reach ~1e36 (first case) or overflow (second case) while the atmosphere
+    around it stays below the threshold.  The cells beside it must take the same decision (atmosphere
+    reset, or failed for a non-finite update of S_j or tau) on the separate kernels -- whose atmosphere
+    test reads the fluxes of S_j and tau only in a block that the face kernel flagged -- and on the tiled
+    faces, as on the fused sweep, which always reads them."""
+    tov = I.solve_tov()
+    star = I.star_block(n=(32, 32, 32), g=3, half_width=10.02, tov=tov, A_b=0.05)
+    g = star.ng
+    star.B[0][g + 1, g + 1, g + 2] = face_b
+    blocks = I.split_block(star, (2, 2, 2))
+    P = GH.mixed_params(O.Params(gamma_ad=2.0, recon=1, rho_atm=1e-13 * tov.rho[0], tol=1e-10))
+    dt = 0.25 * star.dx[0]
+    sep, _ = _run(blocks, P, G.GR_PATH_SEPARATE, dt)
+    st = sep[2].numpy()
+    print("statuses beside the planted face:", np.unique(st, return_counts=True))
+    assert np.any(st & G.GR_ST_ATM_THRESHOLD)
+    for path in (G.GR_PATH_FUSED, G.GR_PATH_TILED_FACES):
+        _same_nan(sep, _run(blocks, P, path, dt)[0])
+
+
 def test_fused_sweep_refuses_blocks_it_does_not_take():
     big = [I.random_block(n=(24, 8, 8), g=3, seed=5)]
     pools = GH.Pools(big)
