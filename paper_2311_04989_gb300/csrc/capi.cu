@@ -468,6 +468,10 @@ int gr_mesh_create(gr_ctx* ctx, const gr_block* blocks, int32_t nblocks, int32_t
   return GR_OK;
 }
 
+// the per-block flux flag of the mixed stage relies on this: six fluxes of one variable, each below the
+// bound, add and subtract to a finite FP32 value
+static_assert(6.0 * kFluxSafe < 3.4e38, "kFluxSafe too large for the flux flag");
+
 static int check_params(const gr_params* p) {
   if (!p) return fail(GR_EINVAL, "params is NULL");
   if (p->size != sizeof(gr_params)) return fail(GR_EINVAL, "gr_params.size does not match this library");
